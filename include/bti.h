@@ -1,0 +1,167 @@
+/*
+ * bti.h -- C ABI of libbti, a single-GPU (NVIDIA GB300, sm_103a) implementation
+ * of the data-parallel hot path of goal-oriented real-time Bayesian inversion
+ * for linear autonomous dynamical systems (Henneking, Venkat, Ghattas,
+ * arXiv 2501.14911).
+ *
+ * Problem (Sec. 2): the parameter-to-observable map F and the parameter-to-QoI
+ * map F_q are block lower-triangular Toeplitz in time (Eq. (2.5), Eq. (2.16)):
+ * block (t, s) of F is F_{t-s} (t >= s), with F_0 the diagonal block.  With a
+ * time-invariant prior Gamma_prior = I_t (x) C_s and diagonal noise
+ * Gamma_noise, the library forms G^* = Gamma_prior F^T (Sec. 4, Phase 2),
+ * K = Gamma_noise + F G^* and its Cholesky factor, and computes the MAP point
+ * m_map = G^* K^{-1} d_obs (Eq. (4.13) with zero prior mean, simplified using
+ * K - F G^* = Gamma_noise) and the QoI prediction q_map = F_q m_map (Eq. (4.2)).
+ *
+ * Conventions for every call:
+ *  - Indices are 0-based.  A parameter vector is m[b][t][j] (b < B, t < N_t,
+ *    j < N_m), a data vector d[b][t][i] (i < N_d), a QoI vector q[b][t][l]
+ *    (l < N_q); all dense row-major.  The data-space index of (t, i) is
+ *    t * N_d + i, so K is (N_t N_d) x (N_t N_d).
+ *  - Every pointer argument is a DEVICE pointer on the handle's device unless
+ *    stated otherwise.  The caller owns all pointers it passes; the library
+ *    copies what it keeps (set_blocks copies) and owns every buffer it
+ *    allocates, freeing them in bti_destroy.
+ *  - Calls are asynchronous on the handle's CUDA stream (the stream passed to
+ *    bti_create, which the caller may change with bti_set_stream).  Argument,
+ *    shape and call-order errors are detected on the host and returned at once;
+ *    nothing is launched in that case.  Device-side failures (a non-positive
+ *    pivot in the Cholesky factorisation) are recorded in a device status word
+ *    and returned by bti_sync, and by bti_factor_K, which synchronises.
+ *  - A handle must not be used from two host threads at the same time.
+ *  - bti_last_error returns a message for the last non-OK status (valid until
+ *    the next call on the handle).
+ */
+#ifndef BTI_H
+#define BTI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bti_ctx* bti_handle;
+
+typedef enum {
+  BTI_OK = 0,
+  BTI_ERR_ARG = 1,      /* null pointer, negative or unsupported size or enum */
+  BTI_ERR_SHAPE = 2,    /* sizes inconsistent with the handle */
+  BTI_ERR_STATE = 3,    /* call order violated (e.g. apply before set_blocks) */
+  BTI_ERR_CUDA = 4,     /* a CUDA runtime call failed */
+  BTI_ERR_OOM = 5,      /* device allocation failed */
+  BTI_ERR_NOT_SPD = 6,  /* Cholesky met a non-positive or non-finite pivot */
+  BTI_ERR_TIMEOUT = 7   /* reserved: a bounded device wait gave up */
+} bti_status;
+
+/* Which block-Toeplitz operator a call refers to.
+ * BTI_OP_F : p2o map F, blocks F_k (N_d x N_m), Eq. (2.5).
+ * BTI_OP_G : blocks G_k = F_k C_s of G^* = Gamma_prior F^T (Sec. 4, Phase 2).
+ * BTI_OP_FQ: p2q map F_q, blocks (N_q x N_m), Eq. (2.15)-(2.16). */
+typedef enum { BTI_OP_F = 0, BTI_OP_G = 1, BTI_OP_FQ = 2 } bti_op;
+
+/* Storage / arithmetic tier of the spectral blocks and vector precision.
+ * BTI_P_F64: spectral blocks complex FP64, FFTs and products FP64.
+ * BTI_P_F32: spectral blocks complex FP32, FFTs and products FP32. */
+typedef enum { BTI_P_F64 = 0, BTI_P_F32 = 1 } bti_prec;
+
+/* Create a handle for N_m spatial parameters, N_d sensors, N_q QoI points and
+ * N_t time steps on CUDA device `device`, issuing work on `cuda_stream`
+ * (a cudaStream_t, or NULL for the legacy default stream).  N_q may be 0 when
+ * no QoI map is used.  The circulant embedding length is L = 2 N_t (any
+ * L >= 2 N_t - 1 is exact, Sec. 4 "FFT-based ... matvecs"); L must factor into
+ * 2, 3, 5 and 7 and be at most 4096.  Returns BTI_ERR_ARG for sizes <= 0 or an
+ * unsupported L. */
+bti_status bti_create(int64_t Nm, int64_t Nd, int64_t Nq, int64_t Nt, int device,
+                      void* cuda_stream, bti_handle* out);
+
+/* Free every device buffer of the handle (synchronises its stream first). */
+bti_status bti_destroy(bti_handle h);
+
+/* Replace the stream subsequent calls are issued on. */
+bti_status bti_set_stream(bti_handle h, void* cuda_stream);
+
+/* Store operator `op` from its time-domain blocks and precompute its spectral
+ * blocks once (Sec. 4: "the DFT only needs to be done once for each matrix").
+ * blocks: device, FP64, [N_t][R][N_m] row-major, R = N_d for F and G, N_q for
+ * FQ; block k is F_k.  The spectral blocks hat_F_w = sum_k F_k e^{-2 pi i k w / L}
+ * (w = 0..N_t) are kept in `store` precision, layout [N_t+1][R][N_m] complex.
+ * The caller's buffer is read during the call's stream work only.  Calling
+ * again replaces the operator (and invalidates K for OP_F / OP_G). */
+bti_status bti_set_blocks(bti_handle h, bti_op op, const double* blocks, bti_prec store);
+
+/* Build the G operator from the stored F time-domain blocks and a squared-
+ * exponential spatial prior on a gx x gy grid (gx * gy = N_m, node index
+ * j = ix * gy + iy, unit cell spacing):
+ *   C_s[a, b] = sigma^2 exp(-|x_a - x_b|^2 / (2 ell^2)),   G_k = F_k C_s.
+ * Requires a prior bti_set_blocks(BTI_OP_F, ...); G is stored in `store`
+ * precision.  The separable structure C_s = C_x (x) C_y is used on the device. */
+bti_status bti_set_prior_se_grid(bti_handle h, int gx, int gy, double ell, double sigma,
+                                 bti_prec store);
+
+/* Gamma_noise: sigma2 * I if `diag` is NULL, otherwise diag (device, FP64,
+ * [N_t][N_d] variances, all > 0).  Invalidates K. */
+bti_status bti_set_noise(bti_handle h, double sigma2, const double* diag);
+
+/* d = F m for B vectors: m [B][N_t][N_m] -> d [B][N_t][N_d] (Eq. (2.6)),
+ * computed as zero-padded FFT along time, per-frequency block product
+ * hat_d_w = hat_F_w hat_m_w, inverse FFT truncated to the first N_t steps.
+ * `io` is the element type of m and d (BTI_P_F64: double, BTI_P_F32: float);
+ * the arithmetic follows the stored tier of F.  m and d must not overlap. */
+bti_status bti_apply_F(bti_handle h, const void* m, void* d, int64_t B, bti_prec io);
+
+/* m = F^T d (the exact transpose of bti_apply_F) using the conjugate-transposed
+ * spectral blocks (Sec. 4): d [B][N_t][N_d] -> m [B][N_t][N_m]. */
+bti_status bti_apply_FT(bti_handle h, const void* d, void* m, int64_t B, bti_prec io);
+
+/* q = F_q m (Eq. (2.15)): m [B][N_t][N_m] -> q [B][N_t][N_q]. */
+bti_status bti_apply_Fq(bti_handle h, const void* m, void* q, int64_t B, bti_prec io);
+
+/* m = G^* d = Gamma_prior F^T d using the G spectral blocks:
+ * d [B][N_t][N_d] -> m [B][N_t][N_m]. */
+bti_status bti_apply_Gstar(bti_handle h, const void* d, void* m, int64_t B, bti_prec io);
+
+/* Assemble K = Gamma_noise + F G^* in FP64 on the device (Sec. 4, Phase 2),
+ * lower triangle only (the strict upper triangle is left undefined).
+ * Requires F and G (either tier; the FP64 time-domain blocks kept by
+ * set_blocks are used) and set_noise.  col_block (> 0) is the column-panel
+ * width of the assembly; 512 is the default when 0 is passed. */
+bti_status bti_build_K(bti_handle h, int64_t col_block);
+
+/* Cholesky-factor K = L L^T in place (FP64, lower).  Synchronises; returns
+ * BTI_ERR_NOT_SPD (message names the 1-based pivot) if a pivot is <= 0 or
+ * not finite. */
+bti_status bti_factor_K(bti_handle h);
+
+/* Copy the (N_t N_d) x (N_t N_d) row-major K buffer to dst (device, double):
+ * its lower triangle holds K after bti_build_K and the Cholesky factor L after
+ * bti_factor_K; the strict upper triangle is undefined.  Requires build_K. */
+bti_status bti_copy_K(bti_handle h, double* dst);
+
+/* m_map = G^* K^{-1} d_obs for B observation vectors (Eq. (4.13), zero prior
+ * mean): d_obs [B][N_t][N_d] (double) -> m_map [B][N_t][N_m] (double).
+ * K^{-1} is applied by the two triangular solves with the factor; with
+ * refine_iters > 0 that many steps of iterative refinement x += K^{-1}(d - K x)
+ * follow, the residual evaluated with the FP64 spectral operators.
+ * Requires factor_K. */
+bti_status bti_infer_map(bti_handle h, const double* d_obs, double* m_map, int64_t B,
+                         int refine_iters);
+
+/* q_map = F_q m_map (Eq. (4.2)): m_map [B][N_t][N_m] -> q_map [B][N_t][N_q],
+ * both double.  Requires FQ. */
+bti_status bti_predict_qoi(bti_handle h, const double* m_map, double* q_map, int64_t B);
+
+/* Wait for the handle's stream and return any device-side error status. */
+bti_status bti_sync(bti_handle h);
+
+/* Message for the last non-OK status on this handle ("" if none). */
+const char* bti_last_error(bti_handle h);
+
+/* Library version string. */
+const char* bti_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BTI_H */

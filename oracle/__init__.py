@@ -33,6 +33,8 @@ from .toeplitz import (
     p2o_apply,
     p2o_apply_adjoint,
     p2o_dense,
+    p2o_apply_block,
+    p2o_apply_adjoint_block,
     lti_blocks,
     lti_simulate,
 )
@@ -56,7 +58,8 @@ from .inversion import (
 )
 
 __all__ = [
-    "p2o_apply", "p2o_apply_adjoint", "p2o_dense", "lti_blocks", "lti_simulate",
+    "p2o_apply", "p2o_apply_adjoint", "p2o_dense", "p2o_apply_block",
+    "p2o_apply_adjoint_block", "lti_blocks", "lti_simulate",
     "se_covariance_1d", "se_covariance", "prior_blocks", "prior_sample",
     "elliptic_operator",
     "assemble_K", "assemble_K_columns", "cholesky_lower", "solve_K",

@@ -95,3 +95,27 @@ def lti_simulate(A, B, C, m):
         w = A @ w + C @ m[k]
         d[k] = B @ w
     return d
+
+
+def p2o_apply_block(blocks, m, t):
+    """Output block d[t] = sum_{k=0}^{t} F_k m[t-k] alone (Eq. (2.3)); m: [N_t, N_m].
+
+    For spot checks of large problems, where the whole product is too costly.
+    """
+    blocks = np.asarray(blocks)
+    m = np.asarray(m, dtype=np.float64)
+    out = np.zeros(blocks.shape[1], dtype=np.float64)
+    for k in range(t + 1):
+        out += blocks[k].astype(np.float64) @ m[t - k]
+    return out
+
+
+def p2o_apply_adjoint_block(blocks, d, s):
+    """Output block m[s] = sum_{k=0}^{N_t-1-s} F_k^T d[s+k] alone; d: [N_t, R]."""
+    blocks = np.asarray(blocks)
+    d = np.asarray(d, dtype=np.float64)
+    Nt = blocks.shape[0]
+    out = np.zeros(blocks.shape[2], dtype=np.float64)
+    for k in range(Nt - s):
+        out += d[s + k] @ blocks[k].astype(np.float64)
+    return out

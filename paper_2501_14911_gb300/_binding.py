@@ -1,0 +1,247 @@
+"""ctypes marshalling for libbti's C ABI (include/bti.h).  No arithmetic here."""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(PKG)
+HEADER = os.path.join(ROOT, "include", "bti.h")
+
+OP_F, OP_G, OP_FQ = 0, 1, 2
+F64, F32 = 0, 1
+
+STATUS = {
+    0: "BTI_OK", 1: "BTI_ERR_ARG", 2: "BTI_ERR_SHAPE", 3: "BTI_ERR_STATE", 4: "BTI_ERR_CUDA",
+    5: "BTI_ERR_OOM", 6: "BTI_ERR_NOT_SPD", 7: "BTI_ERR_TIMEOUT",
+}
+
+_lib = None
+
+
+class BtiError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+        self.message = message
+
+
+def lib_path():
+    return os.path.join(PKG, "libbti.so")
+
+
+def header_symbols():
+    """Names of every function the public header declares."""
+    with open(HEADER) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"^\s*(?:bti_status|const char\*)\s+(bti_\w+)\s*\(", text, re.M)))
+
+
+def lib():
+    """The loaded libbti (ctypes.CDLL) with argument types set.  Raises if not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libbti.so is not built ({path}); run __graft_entry__.build() first")
+    L = ctypes.CDLL(path)
+    i64, vp, dp, ip = ctypes.c_int64, ctypes.c_void_p, ctypes.c_double, ctypes.c_int
+    st = ctypes.c_int
+    sig = {
+        "bti_create": ([i64, i64, i64, i64, ip, vp, ctypes.POINTER(vp)], st),
+        "bti_destroy": ([vp], st),
+        "bti_set_stream": ([vp, vp], st),
+        "bti_set_blocks": ([vp, ip, vp, ip], st),
+        "bti_set_prior_se_grid": ([vp, ip, ip, dp, dp, ip], st),
+        "bti_set_noise": ([vp, dp, vp], st),
+        "bti_apply_F": ([vp, vp, vp, i64, ip], st),
+        "bti_apply_FT": ([vp, vp, vp, i64, ip], st),
+        "bti_apply_Fq": ([vp, vp, vp, i64, ip], st),
+        "bti_apply_Gstar": ([vp, vp, vp, i64, ip], st),
+        "bti_build_K": ([vp, i64], st),
+        "bti_factor_K": ([vp], st),
+        "bti_copy_K": ([vp, vp], st),
+        "bti_infer_map": ([vp, vp, vp, i64, ip], st),
+        "bti_predict_qoi": ([vp, vp, vp, i64], st),
+        "bti_sync": ([vp], st),
+        "bti_last_error": ([vp], ctypes.c_char_p),
+        "bti_version": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def _ptr(x):
+    """Device pointer of a torch tensor (or an int address)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+class Handle:
+    """One problem instance on one GPU: owns the library handle (bti_create/destroy).
+
+    Methods mirror the C entry points (set_blocks, apply_F, apply_FT, apply_Fq,
+    apply_Gstar, build_K, factor_K, infer_map, predict_qoi, sync) and take torch
+    CUDA tensors; they check dtype, device, contiguity and shape, pass raw
+    pointers, and raise BtiError on a non-OK status.
+    """
+
+    def __init__(self, Nm, Nd, Nq, Nt, device=0, stream=None):
+        import torch
+
+        self.Nm, self.Nd, self.Nq, self.Nt = int(Nm), int(Nd), int(Nq), int(Nt)
+        self.device = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self._stream = stream
+        h = ctypes.c_void_p()
+        st = lib().bti_create(self.Nm, self.Nd, self.Nq, self.Nt, self.device.index or 0,
+                              ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h))
+        if st != 0:
+            raise BtiError(st, f"bti_create({Nm}, {Nd}, {Nq}, {Nt}) failed")
+        self._h = h
+
+    # -- plumbing
+    @property
+    def raw(self):
+        return self._h
+
+    def _check(self, st):
+        if st != 0:
+            msg = lib().bti_last_error(self._h)
+            raise BtiError(st, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().bti_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        self._stream = stream
+        self._check(lib().bti_set_stream(self._h, ctypes.c_void_p(stream.cuda_stream)))
+
+    def _tensor(self, x, shape_tail, name, dtypes=None):
+        import torch
+
+        if not isinstance(x, torch.Tensor):
+            raise TypeError(f"{name} must be a torch tensor")
+        if x.device != self.device:
+            raise ValueError(f"{name} is on {x.device}, handle is on {self.device}")
+        if not x.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        dtypes = dtypes or (torch.float64,)
+        if x.dtype not in dtypes:
+            raise TypeError(f"{name} has dtype {x.dtype}, expected one of {dtypes}")
+        tail = tuple(shape_tail)
+        if tuple(x.shape[-len(tail):]) != tail:
+            raise ValueError(f"{name} has shape {tuple(x.shape)}, expected [..., {', '.join(map(str, tail))}]")
+        return x
+
+    @staticmethod
+    def _io(x):
+        import torch
+
+        return F64 if x.dtype == torch.float64 else F32
+
+    def _batch(self, x, tail_len):
+        n = 1
+        for s in x.shape[:-tail_len]:
+            n *= int(s)
+        return n
+
+    # -- operators
+    def set_blocks(self, op, blocks, store=F64):
+        R = self.Nq if op == OP_FQ else self.Nd
+        self._tensor(blocks, (self.Nt, R, self.Nm), "blocks")
+        self._check(lib().bti_set_blocks(self._h, op, _ptr(blocks), store))
+
+    def set_prior_se_grid(self, gx, gy, ell, sigma, store=F64):
+        self._check(lib().bti_set_prior_se_grid(self._h, gx, gy, float(ell), float(sigma), store))
+
+    def set_noise(self, sigma2, diag=None):
+        if diag is not None:
+            self._tensor(diag, (self.Nt, self.Nd), "diag")
+        self._check(lib().bti_set_noise(self._h, float(sigma2), _ptr(diag)))
+
+    def _apply(self, fn, x, y, tin, tout):
+        import torch
+
+        dts = (torch.float64, torch.float32)
+        self._tensor(x, tin, "input", dts)
+        self._tensor(y, tout, "output", dts)
+        if x.dtype != y.dtype:
+            raise TypeError("input and output must have the same dtype")
+        B = self._batch(x, len(tin))
+        if self._batch(y, len(tout)) != B:
+            raise ValueError("input and output batch sizes differ")
+        self._check(fn(self._h, _ptr(x), _ptr(y), B, self._io(x)))
+        return y
+
+    def apply_F(self, m, d):
+        return self._apply(lib().bti_apply_F, m, d, (self.Nt, self.Nm), (self.Nt, self.Nd))
+
+    def apply_FT(self, d, m):
+        return self._apply(lib().bti_apply_FT, d, m, (self.Nt, self.Nd), (self.Nt, self.Nm))
+
+    def apply_Fq(self, m, q):
+        return self._apply(lib().bti_apply_Fq, m, q, (self.Nt, self.Nm), (self.Nt, self.Nq))
+
+    def apply_Gstar(self, d, m):
+        return self._apply(lib().bti_apply_Gstar, d, m, (self.Nt, self.Nd), (self.Nt, self.Nm))
+
+    def build_K(self, col_block=512):
+        self._check(lib().bti_build_K(self._h, int(col_block)))
+
+    def factor_K(self):
+        self._check(lib().bti_factor_K(self._h))
+
+    def copy_K(self, out=None):
+        import torch
+
+        n = self.Nt * self.Nd
+        if out is None:
+            out = torch.empty((n, n), dtype=torch.float64, device=self.device)
+        self._tensor(out, (n, n), "out")
+        self._check(lib().bti_copy_K(self._h, _ptr(out)))
+        return out
+
+    def infer_map(self, d_obs, m_map, refine_iters=0):
+        self._tensor(d_obs, (self.Nt, self.Nd), "d_obs")
+        self._tensor(m_map, (self.Nt, self.Nm), "m_map")
+        B = self._batch(d_obs, 2)
+        if self._batch(m_map, 2) != B:
+            raise ValueError("d_obs and m_map batch sizes differ")
+        self._check(lib().bti_infer_map(self._h, _ptr(d_obs), _ptr(m_map), B, int(refine_iters)))
+        return m_map
+
+    def predict_qoi(self, m_map, q_map):
+        self._tensor(m_map, (self.Nt, self.Nm), "m_map")
+        self._tensor(q_map, (self.Nt, self.Nq), "q_map")
+        B = self._batch(m_map, 2)
+        if self._batch(q_map, 2) != B:
+            raise ValueError("m_map and q_map batch sizes differ")
+        self._check(lib().bti_predict_qoi(self._h, _ptr(m_map), _ptr(q_map), B))
+        return q_map
+
+    def sync(self):
+        self._check(lib().bti_sync(self._h))
+
+    @property
+    def last_error(self):
+        return lib().bti_last_error(self._h).decode()

@@ -1,0 +1,524 @@
+// C ABI of libbti: handle, state checks, buffer ownership and orchestration of
+// the kernels in fft.cu, spectral.cu and dense.cu.  See include/bti.h for the
+// contract of every entry point.
+#include "bti_internal.cuh"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+using namespace bti;
+
+namespace {
+
+struct OpStore {
+  bool set = false;
+  bti_prec prec = BTI_P_F64;
+  int64_t R = 0;
+  void* hat = nullptr;     // [nf][R][Nm] complex, storage tier
+  double* time = nullptr;  // [Nt][R][Nm] FP64 time-domain copy (F and G only)
+};
+
+}  // namespace
+
+struct bti_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int64_t Nm = 0, Nd = 0, Nq = 0, Nt = 0, L = 0, nf = 0;
+  FftPlan plan;
+  OpStore op[3];
+  bool noise_set = false;
+  double sigma2 = 0.0;
+  double* noise_diag = nullptr;  // [Nt][Nd] or null
+  double* K = nullptr;           // [n][n], lower triangle: K, then L after factor_K
+  double* Linv = nullptr;        // inverses of the factor's diagonal blocks
+  bool K_built = false, K_factored = false;
+  int* status = nullptr;  // device status word
+  void* ws = nullptr;     // spectral workspace
+  size_t ws_bytes = 0;
+  double* wsolve = nullptr;  // dense-solve workspace
+  size_t wsolve_bytes = 0;
+  std::string err;
+};
+
+namespace {
+
+bti_status fail(bti_ctx* h, bti_status st, const std::string& msg) {
+  if (h) h->err = msg;
+  return st;
+}
+
+bti_status cuda_check(bti_ctx* h, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return BTI_OK;
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return fail(h, BTI_ERR_OOM, std::string(what) + ": " + cudaGetErrorString(e));
+  }
+  return fail(h, BTI_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+bti_status launched(bti_ctx* h, const char* what) {
+  return cuda_check(h, cudaGetLastError(), what);
+}
+
+bti_status dev_alloc(bti_ctx* h, void** p, size_t bytes, const char* what) {
+  *p = nullptr;
+  if (bytes == 0) return BTI_OK;
+  return cuda_check(h, cudaMalloc(p, bytes), what);
+}
+
+void dev_free(void*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+template <typename P> void dev_freep(P*& p) {
+  void* v = p;
+  dev_free(v);
+  p = nullptr;
+}
+
+bti_status ensure(bti_ctx* h, void** buf, size_t* have, size_t need, const char* what) {
+  if (need <= *have) return BTI_OK;
+  cudaStreamSynchronize(h->stream);
+  dev_free(*buf);
+  *have = 0;
+  bti_status st = dev_alloc(h, buf, need, what);
+  if (st == BTI_OK) *have = need;
+  return st;
+}
+
+size_t elem_size(bti_prec p) { return p == BTI_P_F64 ? sizeof(double) : sizeof(float); }
+size_t celem_size(bti_prec p) { return 2 * elem_size(p); }
+bool prec_ok(int p) { return p == BTI_P_F64 || p == BTI_P_F32; }
+
+int64_t rows_of(bti_ctx* h, bti_op op) { return op == BTI_OP_FQ ? h->Nq : h->Nd; }
+
+bti_status check_handle(bti_ctx* h) {
+  if (!h) return BTI_ERR_ARG;
+  cudaError_t e = cudaSetDevice(h->device);
+  return cuda_check(h, e, "cudaSetDevice");
+}
+
+// spectral blocks of an op from FP64 time-domain blocks [Nt][R][Nm] (device)
+bti_status make_spectral(bti_ctx* h, OpStore& o, const double* time_blocks) {
+  const int64_t cols = o.R * h->Nm;
+  if (o.prec == BTI_P_F64)
+    launch_rfft_cols<double, double, double>(h->plan, (int)h->Nt, time_blocks, cols, 0,
+                                             (double2*)o.hat, 0, cols, 1, h->stream);
+  else
+    launch_rfft_cols<double, double, float>(h->plan, (int)h->Nt, time_blocks, cols, 0,
+                                            (float2*)o.hat, 0, cols, 1, h->stream);
+  return launched(h, "spectral blocks");
+}
+
+bti_status store_op(bti_ctx* h, bti_op opi, const double* blocks, bti_prec store, bool keep_time) {
+  OpStore& o = h->op[opi];
+  const int64_t R = rows_of(h, opi);
+  if (R <= 0) return fail(h, BTI_ERR_SHAPE, "operator has zero rows (N_q = 0?)");
+  dev_free(o.hat);
+  dev_freep(o.time);
+  o.set = false;
+  o.R = R;
+  o.prec = store;
+  size_t hat_bytes = (size_t)h->nf * R * h->Nm * celem_size(store);
+  bti_status st = dev_alloc(h, &o.hat, hat_bytes, "alloc spectral blocks");
+  if (st != BTI_OK) return st;
+  const double* src = blocks;
+  if (keep_time) {
+    size_t tb = (size_t)h->Nt * R * h->Nm * sizeof(double);
+    st = dev_alloc(h, (void**)&o.time, tb, "alloc time-domain blocks");
+    if (st != BTI_OK) return st;
+    if (blocks != o.time) {
+      st = cuda_check(h, cudaMemcpyAsync(o.time, blocks, tb, cudaMemcpyDeviceToDevice, h->stream),
+                      "copy blocks");
+      if (st != BTI_OK) return st;
+    }
+    src = o.time;
+  }
+  st = make_spectral(h, o, src);
+  if (st != BTI_OK) return st;
+  o.set = true;
+  if (opi != BTI_OP_FQ) {
+    h->K_built = false;
+    h->K_factored = false;
+  }
+  return BTI_OK;
+}
+
+// forward-type product: out[b] = T(op) in[b]; in [B][Nt][Nm] (io) -> out [B][Nt][R] (io)
+template <typename T>
+bti_status apply_fwd_t(bti_ctx* h, const OpStore& o, const void* in, void* out, int64_t B, bti_prec io) {
+  const int64_t nf = h->nf, Nm = h->Nm, R = o.R, Nt = h->Nt;
+  size_t n_mhat = (size_t)B * nf * Nm;
+  size_t n_part = prod_fwd_partial_elems(nf, R, Nm, B);
+  size_t n_dhat = (size_t)B * nf * R;
+  bti_status st = ensure(h, &h->ws, &h->ws_bytes, sizeof(C2<T>) * (n_mhat + n_part + n_dhat), "workspace");
+  if (st != BTI_OK) return st;
+  C2<T>* mhat = (C2<T>*)h->ws;
+  C2<T>* part = mhat + n_mhat;
+  C2<T>* dhat = part + n_part;
+  cudaStream_t s = h->stream;
+  if (io == BTI_P_F64)
+    launch_rfft_cols<T, double, T>(h->plan, (int)Nt, (const double*)in, Nm, Nt * Nm, mhat, nf * Nm, Nm, B, s);
+  else
+    launch_rfft_cols<T, float, T>(h->plan, (int)Nt, (const float*)in, Nm, Nt * Nm, mhat, nf * Nm, Nm, B, s);
+  launch_prod_fwd<T, T>((const C2<T>*)o.hat, mhat, part, dhat, nf, R, Nm, B, s);
+  const T scale = (T)(1.0 / (double)h->L);
+  if (io == BTI_P_F64)
+    launch_irfft_cols<T, double>(h->plan, (int)Nt, dhat, R, nf * R, (double*)out, Nt * R, R, B, scale, s);
+  else
+    launch_irfft_cols<T, float>(h->plan, (int)Nt, dhat, R, nf * R, (float*)out, Nt * R, R, B, scale, s);
+  return launched(h, "forward Toeplitz product");
+}
+
+// adjoint-type product: out[b] = T(op)^T in[b]; in [B][Nt][R] -> out [B][Nt][Nm]
+template <typename T>
+bti_status apply_adj_t(bti_ctx* h, const OpStore& o, const void* in, void* out, int64_t B, bti_prec io) {
+  const int64_t nf = h->nf, Nm = h->Nm, R = o.R, Nt = h->Nt;
+  size_t n_dhat = (size_t)B * nf * R;
+  size_t n_mhat = (size_t)B * nf * Nm;
+  bti_status st = ensure(h, &h->ws, &h->ws_bytes, sizeof(C2<T>) * (n_mhat + n_dhat), "workspace");
+  if (st != BTI_OK) return st;
+  C2<T>* dhat = (C2<T>*)h->ws;
+  C2<T>* mhat = dhat + n_dhat;
+  cudaStream_t s = h->stream;
+  if (io == BTI_P_F64)
+    launch_rfft_cols<T, double, T>(h->plan, (int)Nt, (const double*)in, R, Nt * R, dhat, nf * R, R, B, s);
+  else
+    launch_rfft_cols<T, float, T>(h->plan, (int)Nt, (const float*)in, R, Nt * R, dhat, nf * R, R, B, s);
+  launch_prod_adj<T, T>((const C2<T>*)o.hat, dhat, mhat, nf, R, Nm, B, s);
+  const T scale = (T)(1.0 / (double)h->L);
+  if (io == BTI_P_F64)
+    launch_irfft_cols<T, double>(h->plan, (int)Nt, mhat, Nm, nf * Nm, (double*)out, Nt * Nm, Nm, B, scale, s);
+  else
+    launch_irfft_cols<T, float>(h->plan, (int)Nt, mhat, Nm, nf * Nm, (float*)out, Nt * Nm, Nm, B, scale, s);
+  return launched(h, "adjoint Toeplitz product");
+}
+
+bti_status apply_op(bti_ctx* h, bti_op opi, bool adjoint, const void* in, void* out, int64_t B,
+                    bti_prec io, const char* name) {
+  bti_status st = check_handle(h);
+  if (st != BTI_OK) return st;
+  if (!prec_ok(io)) return fail(h, BTI_ERR_ARG, std::string(name) + ": bad io precision");
+  if (B < 0) return fail(h, BTI_ERR_ARG, std::string(name) + ": B < 0");
+  const OpStore& o = h->op[opi];
+  if (!o.set) return fail(h, BTI_ERR_STATE, std::string(name) + ": operator blocks not set");
+  if (B == 0) return BTI_OK;
+  if (!in || !out) return fail(h, BTI_ERR_ARG, std::string(name) + ": null pointer");
+  if (o.prec == BTI_P_F64)
+    return adjoint ? apply_adj_t<double>(h, o, in, out, B, io) : apply_fwd_t<double>(h, o, in, out, B, io);
+  return adjoint ? apply_adj_t<float>(h, o, in, out, B, io) : apply_fwd_t<float>(h, o, in, out, B, io);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* bti_version(void) { return "libbti 0.1 (sm_103a)"; }
+
+bti_status bti_create(int64_t Nm, int64_t Nd, int64_t Nq, int64_t Nt, int device, void* cuda_stream,
+                      bti_handle* out) {
+  if (!out) return BTI_ERR_ARG;
+  *out = nullptr;
+  if (Nm <= 0 || Nd <= 0 || Nq < 0 || Nt <= 0) return BTI_ERR_ARG;
+  if (2 * Nt > kMaxL) return BTI_ERR_ARG;
+  if (Nm > ((int64_t)1 << 40) || Nd > (1 << 20) || Nq > (1 << 20)) return BTI_ERR_ARG;
+  {  // L = 2 N_t must factor into 2, 3, 5, 7 (checked before touching the device)
+    int64_t n = 2 * Nt;
+    const int r[4] = {2, 3, 5, 7};
+    for (int i = 0; i < 4; ++i)
+      while (n % r[i] == 0) n /= r[i];
+    if (n != 1) return BTI_ERR_ARG;
+  }
+  bti_ctx* h = new (std::nothrow) bti_ctx();
+  if (!h) return BTI_ERR_OOM;
+  h->device = device;
+  h->stream = (cudaStream_t)cuda_stream;
+  h->Nm = Nm;
+  h->Nd = Nd;
+  h->Nq = Nq;
+  h->Nt = Nt;
+  h->L = 2 * Nt;
+  h->nf = Nt + 1;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return BTI_ERR_CUDA;
+  }
+  if (!fft_plan_make(h->plan, (int)h->L)) {
+    cudaGetLastError();
+    delete h;
+    return BTI_ERR_OOM;
+  }
+  if (cudaMalloc(&h->status, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(h->plan.tw64);
+    cudaFree(h->plan.tw32);
+    delete h;
+    return BTI_ERR_OOM;
+  }
+  cudaMemset(h->status, 0, sizeof(int));
+  *out = h;
+  return BTI_OK;
+}
+
+bti_status bti_destroy(bti_handle h) {
+  if (!h) return BTI_ERR_ARG;
+  cudaSetDevice(h->device);
+  cudaStreamSynchronize(h->stream);
+  for (auto& o : h->op) {
+    dev_free(o.hat);
+    dev_freep(o.time);
+  }
+  dev_freep(h->noise_diag);
+  dev_freep(h->K);
+  dev_freep(h->Linv);
+  dev_freep(h->status);
+  dev_free(h->ws);
+  dev_freep(h->wsolve);
+  dev_freep(h->plan.tw64);
+  dev_freep(h->plan.tw32);
+  delete h;
+  return BTI_OK;
+}
+
+bti_status bti_set_stream(bti_handle h, void* cuda_stream) {
+  if (!h) return BTI_ERR_ARG;
+  h->stream = (cudaStream_t)cuda_stream;
+  return BTI_OK;
+}
+
+bti_status bti_set_blocks(bti_handle h, bti_op op, const double* blocks, bti_prec store) {
+  bti_status st = check_handle(h);
+  if (st != BTI_OK) return st;
+  if (op < BTI_OP_F || op > BTI_OP_FQ) return fail(h, BTI_ERR_ARG, "set_blocks: bad op");
+  if (!prec_ok(store)) return fail(h, BTI_ERR_ARG, "set_blocks: bad precision");
+  if (!blocks) return fail(h, BTI_ERR_ARG, "set_blocks: null blocks");
+  return store_op(h, op, blocks, store, op != BTI_OP_FQ);
+}
+
+bti_status bti_set_prior_se_grid(bti_handle h, int gx, int gy, double ell, double sigma, bti_prec store) {
+  bti_status st = check_handle(h);
+  if (st != BTI_OK) return st;
+  if (gx <= 0 || gy <= 0 || !(ell > 0.0) || !(sigma > 0.0) || !prec_ok(store))
+    return fail(h, BTI_ERR_ARG, "set_prior_se_grid: bad argument");
+  if ((int64_t)gx * gy != h->Nm) return fail(h, BTI_ERR_SHAPE, "set_prior_se_grid: gx * gy != N_m");
+  OpStore& F = h->op[BTI_OP_F];
+  if (!F.set || !F.time) return fail(h, BTI_ERR_STATE, "set_prior_se_grid: F blocks not set");
+  const int64_t rows = h->Nt * h->Nd;
+  double* Cx = nullptr;
+  double* Cy = nullptr;
+  double* U = nullptr;
+  double* G = nullptr;
+  st = dev_alloc(h, (void**)&Cx, sizeof(double) * ((size_t)gx * gx + (size_t)gy * gy), "alloc prior axes");
+  if (st != BTI_OK) return st;
+  Cy = Cx + (size_t)gx * gx;
+  st = dev_alloc(h, (void**)&U, sizeof(double) * (size_t)rows * h->Nm, "alloc prior temp");
+  if (st != BTI_OK) { dev_freep(Cx); return st; }
+  st = dev_alloc(h, (void**)&G, sizeof(double) * (size_t)rows * h->Nm, "alloc G blocks");
+  if (st != BTI_OK) { dev_freep(Cx); dev_freep(U); return st; }
+  cudaStream_t s = h->stream;
+  // C_s = C_x (x) C_y with sigma on each axis, node index ix * gy + iy
+  se_axis_matrix(Cx, gx, ell, sigma, s);
+  se_axis_matrix(Cy, gy, ell, sigma, s);
+  // row r of the blocks viewed as X_r [gx][gy]: G_r = C_x X_r C_y
+  gemm_f64(false, rows * gx, gy, gy, 1.0, F.time, gy, 0, Cy, gy, 0, 0.0, U, gy, 0, 1, false, s);
+  gemm_f64(false, gx, gy, gx, 1.0, Cx, gx, 0, U, gy, (int64_t)gx * gy, 0.0, G, gy, (int64_t)gx * gy,
+           rows, false, s);
+  st = launched(h, "prior blocks");
+  if (st == BTI_OK) {
+    OpStore& o = h->op[BTI_OP_G];
+    dev_free(o.hat);
+    dev_freep(o.time);
+    o.set = false;
+    o.R = h->Nd;
+    o.prec = store;
+    o.time = G;
+    G = nullptr;
+    st = dev_alloc(h, &o.hat, (size_t)h->nf * o.R * h->Nm * celem_size(store), "alloc spectral blocks");
+    if (st == BTI_OK) st = make_spectral(h, o, o.time);
+    if (st == BTI_OK) {
+      o.set = true;
+      h->K_built = false;
+      h->K_factored = false;
+    }
+  }
+  cudaStreamSynchronize(s);
+  dev_freep(Cx);
+  dev_freep(U);
+  dev_freep(G);
+  return st;
+}
+
+bti_status bti_set_noise(bti_handle h, double sigma2, const double* diag) {
+  bti_status st = check_handle(h);
+  if (st != BTI_OK) return st;
+  if (!diag && !(sigma2 > 0.0)) return fail(h, BTI_ERR_ARG, "set_noise: sigma2 must be > 0");
+  dev_freep(h->noise_diag);
+  h->sigma2 = sigma2;
+  if (diag) {
+    size_t bytes = sizeof(double) * (size_t)h->Nt * h->Nd;
+    st = dev_alloc(h, (void**)&h->noise_diag, bytes, "alloc noise");
+    if (st != BTI_OK) return st;
+    st = cuda_check(h, cudaMemcpyAsync(h->noise_diag, diag, bytes, cudaMemcpyDeviceToDevice, h->stream),
+                    "copy noise");
+    if (st != BTI_OK) return st;
+  }
+  h->noise_set = true;
+  h->K_built = false;
+  h->K_factored = false;
+  return BTI_OK;
+}
+
+bti_status bti_apply_F(bti_handle h, const void* m, void* d, int64_t B, bti_prec io) {
+  return apply_op(h, BTI_OP_F, false, m, d, B, io, "apply_F");
+}
+bti_status bti_apply_FT(bti_handle h, const void* d, void* m, int64_t B, bti_prec io) {
+  return apply_op(h, BTI_OP_F, true, d, m, B, io, "apply_FT");
+}
+bti_status bti_apply_Fq(bti_handle h, const void* m, void* q, int64_t B, bti_prec io) {
+  return apply_op(h, BTI_OP_FQ, false, m, q, B, io, "apply_Fq");
+}
+bti_status bti_apply_Gstar(bti_handle h, const void* d, void* m, int64_t B, bti_prec io) {
+  return apply_op(h, BTI_OP_G, true, d, m, B, io, "apply_Gstar");
+}
+
+bti_status bti_build_K(bti_handle h, int64_t col_block) {
+  bti_status st = check_handle(h);
+  if (st != BTI_OK) return st;
+  if (col_block < 0) return fail(h, BTI_ERR_ARG, "build_K: col_block < 0");
+  if (col_block == 0) col_block = 512;
+  const OpStore& F = h->op[BTI_OP_F];
+  const OpStore& G = h->op[BTI_OP_G];
+  if (!F.set || !G.set || !F.time || !G.time) return fail(h, BTI_ERR_STATE, "build_K: F and G blocks required");
+  if (!h->noise_set) return fail(h, BTI_ERR_STATE, "build_K: noise not set");
+  const int64_t n = h->Nt * h->Nd;
+  if (!h->K) {
+    st = dev_alloc(h, (void**)&h->K, sizeof(double) * (size_t)n * n, "alloc K");
+    if (st != BTI_OK) return st;
+  }
+  cudaStream_t s = h->stream;
+  // W = F_stack G_stack^T (lower block triangle), by column panels
+  for (int64_t c0 = 0; c0 < n; c0 += col_block) {
+    int64_t nc = (n - c0) < col_block ? (n - c0) : col_block;
+    gemm_f64(true, n - c0, nc, h->Nm, 1.0, F.time + c0 * h->Nm, h->Nm, 0, G.time + c0 * h->Nm, h->Nm, 0,
+             0.0, h->K + c0 * n + c0, n, 0, 1, true, s);
+  }
+  k_diag_cumsum(h->K, h->Nt, h->Nd, h->sigma2, h->noise_diag, s);
+  st = launched(h, "build_K");
+  if (st != BTI_OK) return st;
+  h->K_built = true;
+  h->K_factored = false;
+  return BTI_OK;
+}
+
+bti_status bti_factor_K(bti_handle h) {
+  bti_status st = check_handle(h);
+  if (st != BTI_OK) return st;
+  if (!h->K_built) return fail(h, BTI_ERR_STATE, "factor_K: K not built");
+  if (h->K_factored) return BTI_OK;
+  const int64_t n = h->Nt * h->Nd;
+  const int64_t nblk = (n + kCholNB - 1) / kCholNB;
+  if (!h->Linv) {
+    st = dev_alloc(h, (void**)&h->Linv, sizeof(double) * (size_t)nblk * kCholNB * kCholNB, "alloc Linv");
+    if (st != BTI_OK) return st;
+  }
+  st = ensure(h, (void**)&h->wsolve, &h->wsolve_bytes, sizeof(double) * (size_t)n * kCholNB, "solve workspace");
+  if (st != BTI_OK) return st;
+  cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
+  cholesky_f64(h->K, n, h->Linv, h->wsolve, h->status, h->stream);
+  st = launched(h, "factor_K");
+  if (st != BTI_OK) return st;
+  int stat = 0;
+  st = cuda_check(h, cudaMemcpyAsync(&stat, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "status");
+  if (st != BTI_OK) return st;
+  st = cuda_check(h, cudaStreamSynchronize(h->stream), "factor_K sync");
+  if (st != BTI_OK) return st;
+  if (stat != 0) {
+    h->K_built = false;  // K was overwritten
+    char buf[128];
+    snprintf(buf, sizeof buf, "factor_K: K is not positive definite (pivot %d)", stat);
+    return fail(h, BTI_ERR_NOT_SPD, buf);
+  }
+  h->K_factored = true;
+  return BTI_OK;
+}
+
+bti_status bti_copy_K(bti_handle h, double* dst) {
+  bti_status st = check_handle(h);
+  if (st != BTI_OK) return st;
+  if (!dst) return fail(h, BTI_ERR_ARG, "copy_K: null pointer");
+  if (!h->K || !(h->K_built || h->K_factored)) return fail(h, BTI_ERR_STATE, "copy_K: K not built");
+  const int64_t n = h->Nt * h->Nd;
+  return cuda_check(h, cudaMemcpyAsync(dst, h->K, sizeof(double) * (size_t)n * n, cudaMemcpyDeviceToDevice,
+                                       h->stream), "copy_K");
+}
+
+bti_status bti_infer_map(bti_handle h, const double* d_obs, double* m_map, int64_t B, int refine_iters) {
+  bti_status st = check_handle(h);
+  if (st != BTI_OK) return st;
+  if (B < 0 || refine_iters < 0) return fail(h, BTI_ERR_ARG, "infer_map: bad B or refine_iters");
+  if (!h->K_factored) return fail(h, BTI_ERR_STATE, "infer_map: K not factored");
+  if (!h->op[BTI_OP_G].set) return fail(h, BTI_ERR_STATE, "infer_map: G blocks not set");
+  if (B == 0) return BTI_OK;
+  if (!d_obs || !m_map) return fail(h, BTI_ERR_ARG, "infer_map: null pointer");
+  const int64_t n = h->Nt * h->Nd;
+  // solve workspace: x [B][n], r [B][n], trsm work [B][nb], and Cholesky panel work
+  size_t need = sizeof(double) * ((size_t)2 * B * n + trsm_work_elems(n, B));
+  size_t chol = sizeof(double) * (size_t)n * kCholNB;
+  st = ensure(h, (void**)&h->wsolve, &h->wsolve_bytes, need > chol ? need : chol, "solve workspace");
+  if (st != BTI_OK) return st;
+  double* x = h->wsolve;
+  double* r = x + (size_t)B * n;
+  double* work = r + (size_t)B * n;
+  cudaStream_t s = h->stream;
+  st = cuda_check(h, cudaMemcpyAsync(x, d_obs, sizeof(double) * B * n, cudaMemcpyDeviceToDevice, s), "copy d_obs");
+  if (st != BTI_OK) return st;
+  trsm_lower_f64(h->K, h->Linv, n, x, B, work, h->status, s);
+  st = launched(h, "triangular solves");
+  if (st != BTI_OK) return st;
+  for (int it = 0; it < refine_iters; ++it) {
+    // r = d - (Gamma_n x + F (G^* x)), evaluated with the spectral operators;
+    // m_map serves as the parameter-space temporary.
+    st = apply_op(h, BTI_OP_G, true, x, m_map, B, BTI_P_F64, "refine G*");
+    if (st != BTI_OK) return st;
+    st = apply_op(h, BTI_OP_F, false, m_map, r, B, BTI_P_F64, "refine F");
+    if (st != BTI_OK) return st;
+    // r = d - r - Gamma_n x
+    axpby_f64(r, d_obs, 1.0, -1.0, B * n, s);
+    if (h->noise_diag)
+      noise_residual_f64(r, x, h->noise_diag, n, B, s);
+    else
+      axpby_f64(r, x, -h->sigma2, 1.0, B * n, s);
+    trsm_lower_f64(h->K, h->Linv, n, r, B, work, h->status, s);
+    axpby_f64(x, r, 1.0, 1.0, B * n, s);
+    st = launched(h, "refinement");
+    if (st != BTI_OK) return st;
+  }
+  return apply_op(h, BTI_OP_G, true, x, m_map, B, BTI_P_F64, "infer_map G*");
+}
+
+bti_status bti_predict_qoi(bti_handle h, const double* m_map, double* q_map, int64_t B) {
+  return apply_op(h, BTI_OP_FQ, false, m_map, q_map, B, BTI_P_F64, "predict_qoi");
+}
+
+bti_status bti_sync(bti_handle h) {
+  bti_status st = check_handle(h);
+  if (st != BTI_OK) return st;
+  int stat = 0;
+  st = cuda_check(h, cudaMemcpyAsync(&stat, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "status");
+  if (st != BTI_OK) return st;
+  st = cuda_check(h, cudaStreamSynchronize(h->stream), "sync");
+  if (st != BTI_OK) return st;
+  st = launched(h, "sync");
+  if (st != BTI_OK) return st;
+  if (stat != 0) return fail(h, BTI_ERR_NOT_SPD, "device status: non-positive pivot " + std::to_string(stat));
+  return BTI_OK;
+}
+
+const char* bti_last_error(bti_handle h) { return h ? h->err.c_str() : "null handle"; }
+
+}  // extern "C"
+

@@ -1,0 +1,89 @@
+// Internal declarations shared by the libbti translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+
+#include "../../include/bti.h"
+
+namespace bti {
+
+// ----------------------------------------------------------------- complex helpers
+template <typename T> struct cplx;
+template <> struct cplx<double> { using type = double2; };
+template <> struct cplx<float> { using type = float2; };
+template <typename T> using C2 = typename cplx<T>::type;
+
+template <typename T> __host__ __device__ __forceinline__ C2<T> mk(T re, T im) {
+  C2<T> z; z.x = re; z.y = im; return z;
+}
+template <typename T> __device__ __forceinline__ C2<T> cadd(C2<T> a, C2<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
+template <typename T> __device__ __forceinline__ C2<T> csub(C2<T> a, C2<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
+template <typename T> __device__ __forceinline__ C2<T> cmul(C2<T> a, C2<T> b) {
+  return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * b where b is conjugated when CONJ
+template <typename T> __device__ __forceinline__ C2<T> cmulc(C2<T> a, C2<T> b) {
+  return mk<T>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);  // a * conj(b)
+}
+
+// ----------------------------------------------------------------- FFT plan
+constexpr int kMaxPasses = 12;
+constexpr int kMaxL = 4096;
+
+struct FftPlan {
+  int L = 0;              // transform length (2 N_t)
+  int npass = 0;
+  int radix[kMaxPasses];  // radices in pass order (8, 4, 2, 7, 5, 3)
+  int P = 1;              // complex transforms per CTA (2 P real columns)
+  double2* tw64 = nullptr;  // e^{-2 pi i n / L}, n < L (device)
+  float2* tw32 = nullptr;
+};
+
+bool fft_plan_make(FftPlan& p, int L);   // host: factor L, choose P; false if unsupported
+
+// Kernel launchers (fft.cu).  All act on "columns": element (t, c) of a real
+// column array sits at x[t * ld + c]; a spectrum element (w, c) at X[w * ld + c].
+// batch b offsets by x_bstride / X_bstride elements.
+template <typename T, typename TI, typename TO>
+void launch_rfft_cols(const FftPlan& p, int Nt, const TI* x, int64_t ld, int64_t x_bstride,
+                      C2<TO>* X, int64_t X_bstride, int64_t ncols, int64_t B, cudaStream_t s);
+template <typename T, typename TO>
+void launch_irfft_cols(const FftPlan& p, int Nt, const C2<T>* X, int64_t ld, int64_t X_bstride,
+                       TO* y, int64_t y_bstride, int64_t ncols, int64_t B, T scale, cudaStream_t s);
+
+// Spectral block products (spectral.cu).
+// Forward: dhat[b][w][i] = sum_j Fhat[w][i][j] mhat[b][w][j]  (T compute, TS storage)
+template <typename T, typename TS>
+void launch_prod_fwd(const C2<TS>* Fhat, const C2<T>* mhat, C2<T>* partial, C2<T>* dhat,
+                     int64_t nf, int64_t R, int64_t Nm, int64_t B, cudaStream_t s);
+size_t prod_fwd_partial_elems(int64_t nf, int64_t R, int64_t Nm, int64_t B);
+// Adjoint: mhat[b][w][j] = sum_i conj(Fhat[w][i][j]) dhat[b][w][i]
+template <typename T, typename TS>
+void launch_prod_adj(const C2<TS>* Fhat, const C2<T>* dhat, C2<T>* mhat,
+                     int64_t nf, int64_t R, int64_t Nm, int64_t B, cudaStream_t s);
+
+// Dense FP64 (dense.cu)
+// C[b] = alpha * A[b] * op(B[b]) + beta * C[b]; A is M x K (lda), op(B) is K x N:
+// TRANSB=false: B stored K x N (ldb); TRANSB=true: B stored N x K (ldb).
+// lower_only: skip output tiles strictly above the diagonal (row tile < col tile).
+void gemm_f64(bool transB, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
+              int64_t lda, int64_t sA, const double* Bm, int64_t ldb, int64_t sB, double beta,
+              double* C, int64_t ldc, int64_t sC, int64_t batch, bool lower_only, cudaStream_t s);
+void se_axis_matrix(double* C, int n, double ell, double scale, cudaStream_t s);
+void k_diag_cumsum(double* WK, int64_t Nt, int64_t R, double sigma2, const double* diag,
+                   cudaStream_t s);
+// Blocked Cholesky, lower, in place; Linv receives the inverses of the diagonal blocks
+// ([nblk][nb][nb]); status receives the first failing 1-based pivot (0 if none).
+void cholesky_f64(double* A, int64_t n, double* Linv, double* work, int* status, cudaStream_t s);
+constexpr int kCholNB = 64;
+// X [B][n] rows: X := L^{-1} X (forward) then L^{-T} X (backward), in place.
+void trsm_lower_f64(const double* Lm, const double* Linv, int64_t n, double* X, int64_t B,
+                    double* work, const int* status, cudaStream_t s);
+size_t trsm_work_elems(int64_t n, int64_t B);
+void axpby_f64(double* y, const double* x, double a, double b, int64_t n, cudaStream_t s);
+void noise_residual_f64(double* r, const double* x, const double* diag, int64_t n, int64_t B,
+                        cudaStream_t s);
+
+}  // namespace bti

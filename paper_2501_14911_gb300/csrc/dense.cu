@@ -1,0 +1,373 @@
+// Dense FP64 kernels of the data-space solve: the Gram product and block-
+// diagonal accumulation that assemble K = Gamma_noise + F G^* (Sec. 4,
+// Phase 2), the blocked Cholesky factorisation of K, the triangular solves of
+// the online phase (Eq. (4.13)), and the separable SE prior used to form the
+// G blocks.
+#include "bti_internal.cuh"
+
+#include <algorithm>
+
+namespace bti {
+
+// ------------------------------------------------------------------ GEMM (FP64)
+// 64 x 64 output tile per CTA, k-step 16, 256 threads each owning a 4 x 4
+// sub-tile at rows ty + 16 a and columns tx + 16 b (conflict-free smem reads).
+constexpr int GBM = 64, GBN = 64, GBK = 16;
+
+template <bool TRANSB>
+__global__ void __launch_bounds__(256)
+gemm_f64_kernel(int64_t M, int64_t N, int64_t K, double alpha, const double* __restrict__ A,
+                int64_t lda, int64_t sA, const double* __restrict__ Bm, int64_t ldb, int64_t sB,
+                double beta, double* __restrict__ C, int64_t ldc, int64_t sC, int64_t batch,
+                bool lower_only) {
+  __shared__ double As[GBK][GBM + 1];
+  __shared__ double Bs[GBK][GBN + 1];
+  const int64_t m0 = (int64_t)blockIdx.x * GBM;
+  const int64_t n0 = (int64_t)blockIdx.y * GBN;
+  if (lower_only && blockIdx.x < blockIdx.y) return;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  for (int64_t bz = blockIdx.z; bz < batch; bz += gridDim.z) {
+    const double* Ab = A + bz * sA;
+    const double* Bb = Bm + bz * sB;
+    double* Cb = C + bz * sC;
+    double acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+    for (int64_t k0 = 0; k0 < K; k0 += GBK) {
+      // A tile: 64 rows x 16 k, element (r, c) at A[m0 + r][k0 + c]
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        int idx = threadIdx.x + 256 * e;
+        int r = idx >> 4, c = idx & 15;
+        int64_t gm = m0 + r, gk = k0 + c;
+        As[c][r] = (gm < M && gk < K) ? Ab[gm * lda + gk] : 0.0;
+      }
+      if (TRANSB) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          int idx = threadIdx.x + 256 * e;
+          int r = idx >> 4, c = idx & 15;
+          int64_t gn = n0 + r, gk = k0 + c;
+          Bs[c][r] = (gn < N && gk < K) ? Bb[gn * ldb + gk] : 0.0;
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          int idx = threadIdx.x + 256 * e;
+          int r = idx >> 6, c = idx & 63;
+          int64_t gk = k0 + r, gn = n0 + c;
+          Bs[r][c] = (gn < N && gk < K) ? Bb[gk * ldb + gn] : 0.0;
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < GBK; ++kk) {
+        double av[4], bv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) av[a] = As[kk][ty + 16 * a];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][tx + 16 * b];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      int64_t gm = m0 + ty + 16 * a;
+      if (gm >= M) continue;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        int64_t gn = n0 + tx + 16 * b;
+        if (gn >= N) continue;
+        double* cp = Cb + gm * ldc + gn;
+        double v = alpha * acc[a][b];
+        if (beta != 0.0) v = fma(beta, *cp, v);
+        *cp = v;
+      }
+    }
+  }
+}
+
+// Small-M products (M <= 8 rows, e.g. a handful of right-hand sides).
+// NN: C[m][n] (+)= alpha sum_k A[m][k] B[k][n]; one thread per column n.
+template <int MM>
+__global__ void __launch_bounds__(256)
+gemm_smallm_nn_kernel(int64_t M, int64_t N, int64_t K, double alpha, const double* __restrict__ A,
+                      int64_t lda, const double* __restrict__ Bm, int64_t ldb, double beta,
+                      double* __restrict__ C, int64_t ldc) {
+  __shared__ double As[MM][64];
+  const int64_t n = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  double acc[MM];
+#pragma unroll
+  for (int m = 0; m < MM; ++m) acc[m] = 0.0;
+  for (int64_t k0 = 0; k0 < K; k0 += 64) {
+    for (int idx = threadIdx.x; idx < MM * 64; idx += 256) {
+      int m = idx >> 6, c = idx & 63;
+      As[m][c] = (m < M && k0 + c < K) ? A[m * lda + k0 + c] : 0.0;
+    }
+    __syncthreads();
+    if (n < N) {
+      int kn = (int)std::min<int64_t>(64, K - k0);
+      for (int c = 0; c < kn; ++c) {
+        double b = Bm[(k0 + c) * ldb + n];
+#pragma unroll
+        for (int m = 0; m < MM; ++m) acc[m] = fma(As[m][c], b, acc[m]);
+      }
+    }
+    __syncthreads();
+  }
+  if (n < N) {
+#pragma unroll
+    for (int m = 0; m < MM; ++m) {
+      if (m >= M) break;
+      double* cp = C + m * ldc + n;
+      double v = alpha * acc[m];
+      if (beta != 0.0) v = fma(beta, *cp, v);
+      *cp = v;
+    }
+  }
+}
+
+// NT: C[m][n] (+)= alpha sum_k A[m][k] B[n][k]; one warp per column n.
+template <int MM>
+__global__ void __launch_bounds__(256)
+gemm_smallm_nt_kernel(int64_t M, int64_t N, int64_t K, double alpha, const double* __restrict__ A,
+                      int64_t lda, const double* __restrict__ Bm, int64_t ldb, double beta,
+                      double* __restrict__ C, int64_t ldc) {
+  const int lane = threadIdx.x & 31;
+  const int64_t n = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (n >= N) return;
+  double acc[MM];
+#pragma unroll
+  for (int m = 0; m < MM; ++m) acc[m] = 0.0;
+  const double* brow = Bm + n * ldb;
+  for (int64_t k = lane; k < K; k += 32) {
+    double b = brow[k];
+#pragma unroll
+    for (int m = 0; m < MM; ++m)
+      if (m < M) acc[m] = fma(A[m * lda + k], b, acc[m]);
+  }
+#pragma unroll
+  for (int m = 0; m < MM; ++m)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[m] += __shfl_xor_sync(0xffffffffu, acc[m], o);
+  if (lane == 0) {
+#pragma unroll
+    for (int m = 0; m < MM; ++m) {
+      if (m >= M) break;
+      double* cp = C + m * ldc + n;
+      double v = alpha * acc[m];
+      if (beta != 0.0) v = fma(beta, *cp, v);
+      *cp = v;
+    }
+  }
+}
+
+void gemm_f64(bool transB, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
+              int64_t lda, int64_t sA, const double* Bm, int64_t ldb, int64_t sB, double beta,
+              double* C, int64_t ldc, int64_t sC, int64_t batch, bool lower_only, cudaStream_t s) {
+  if (M <= 0 || N <= 0 || batch <= 0) return;
+  if (M <= 8 && batch == 1 && !lower_only && K > 0) {
+    if (transB) {
+      unsigned g = (unsigned)((N + 7) / 8);
+      if (M <= 1) gemm_smallm_nt_kernel<1><<<g, 256, 0, s>>>(M, N, K, alpha, A, lda, Bm, ldb, beta, C, ldc);
+      else gemm_smallm_nt_kernel<8><<<g, 256, 0, s>>>(M, N, K, alpha, A, lda, Bm, ldb, beta, C, ldc);
+    } else {
+      unsigned g = (unsigned)((N + 255) / 256);
+      if (M <= 1) gemm_smallm_nn_kernel<1><<<g, 256, 0, s>>>(M, N, K, alpha, A, lda, Bm, ldb, beta, C, ldc);
+      else gemm_smallm_nn_kernel<8><<<g, 256, 0, s>>>(M, N, K, alpha, A, lda, Bm, ldb, beta, C, ldc);
+    }
+    return;
+  }
+  dim3 grid((unsigned)((M + GBM - 1) / GBM), (unsigned)((N + GBN - 1) / GBN),
+            (unsigned)std::min<int64_t>(batch, 65535));
+  if (transB)
+    gemm_f64_kernel<true><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, sA, Bm, ldb, sB, beta, C, ldc, sC, batch, lower_only);
+  else
+    gemm_f64_kernel<false><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, sA, Bm, ldb, sB, beta, C, ldc, sC, batch, lower_only);
+}
+
+// ------------------------------------------------------------------ SE prior, one axis
+// C[a][b] = scale * exp(-(a - b)^2 / (2 ell^2)); the 2-D SE covariance on a grid
+// with node index ix * gy + iy is C_x (x) C_y with scale = sigma on each axis.
+__global__ void se_axis_kernel(double* C, int n, double ell, double scale) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  int a = idx / n, b = idx - a * n;
+  double r = (double)(a - b);
+  C[idx] = scale * exp(-(r * r) / (2.0 * ell * ell));
+}
+void se_axis_matrix(double* C, int n, double ell, double scale, cudaStream_t s) {
+  se_axis_kernel<<<(n * n + 255) / 256, 256, 0, s>>>(C, n, ell, scale);
+}
+
+// ------------------------------------------------------------------ K from the Gram matrix
+// On entry WK holds (at least the lower triangle of) W = F_stack G_stack^T,
+// W[(k,i),(k',i')] = F_k[i,:] . G_k'[i',:].  Block (t, t') of F G^* is
+// sum_{u=0}^{min(t,t')} W(t-u, t'-u), so along each block diagonal
+// delta = t - t' >= 0 the blocks are prefix sums of W's blocks.  One thread per
+// (delta, i, i') walks its diagonal and overwrites W with K, adding the noise
+// variance on the main diagonal.
+__global__ void k_diag_cumsum_kernel(double* WK, int64_t Nt, int64_t R, double sigma2,
+                                     const double* __restrict__ diag) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t RR = R * R;
+  if (idx >= Nt * RR) return;
+  int64_t delta = idx / RR;
+  int64_t rem = idx - delta * RR;
+  int64_t i = rem / R, ip = rem - i * R;
+  if (delta == 0 && ip > i) return;  // strict upper triangle of a diagonal block: unused
+  const int64_t n = Nt * R;
+  double acc = 0.0;
+  for (int64_t u = 0; u + delta < Nt; ++u) {
+    int64_t row = (u + delta) * R + i, col = u * R + ip;
+    double* p = WK + row * n + col;
+    acc += *p;
+    double v = acc;
+    if (delta == 0 && i == ip) v += diag ? diag[u * R + i] : sigma2;
+    *p = v;
+  }
+}
+void k_diag_cumsum(double* WK, int64_t Nt, int64_t R, double sigma2, const double* diag,
+                   cudaStream_t s) {
+  int64_t total = Nt * R * R;
+  k_diag_cumsum_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(WK, Nt, R, sigma2, diag);
+}
+
+// ------------------------------------------------------------------ Cholesky
+// Factor the kb x kb diagonal block in shared memory (right-looking, unblocked),
+// write L back, and write its inverse (lower, zeros above) to Linv (ld nb).
+__global__ void __launch_bounds__(256)
+potrf_diag_kernel(double* A, int64_t lda, int kb, double* Linv, int* status, int64_t k0) {
+  __shared__ double S[kCholNB][kCholNB + 1];
+  __shared__ int failed;
+  if (*status != 0) return;  // an earlier block already failed
+  if (threadIdx.x == 0) failed = 0;
+  for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
+    int r = idx / kb, c = idx - r * kb;
+    S[r][c] = (c <= r) ? A[r * lda + c] : 0.0;
+  }
+  __syncthreads();
+  for (int j = 0; j < kb; ++j) {
+    if (threadIdx.x == 0) {
+      double d = S[j][j];
+      if (!(d > 0.0) || !isfinite(d)) {
+        failed = 1;
+        atomicCAS(status, 0, (int)(k0 + j + 1));
+      } else {
+        S[j][j] = sqrt(d);
+      }
+    }
+    __syncthreads();
+    if (failed) return;
+    double piv = S[j][j];
+    for (int i = j + 1 + threadIdx.x; i < kb; i += blockDim.x) S[i][j] /= piv;
+    __syncthreads();
+    int w = kb - j - 1;
+    for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
+      int r = j + 1 + idx / w, c = j + 1 + idx % w;
+      if (c <= r) S[r][c] = fma(-S[r][j], S[c][j], S[r][c]);
+    }
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
+    int r = idx / kb, c = idx - r * kb;
+    if (c <= r) A[r * lda + c] = S[r][c];
+  }
+  // inverse of the lower-triangular block, written to Linv (ld kCholNB, zeros
+  // elsewhere): thread c solves L x = e_c by forward substitution.
+  if (threadIdx.x < kCholNB) {
+    const int c = threadIdx.x;
+    for (int r = 0; r < kCholNB; ++r) {
+      double v = 0.0;
+      if (c < kb && r < kb && r >= c) {
+        v = (r == c) ? 1.0 : 0.0;
+        for (int l = c; l < r; ++l) v = fma(-S[r][l], Linv[l * kCholNB + c], v);
+        v = v / S[r][r];
+      }
+      Linv[r * kCholNB + c] = v;
+    }
+  }
+}
+
+void cholesky_f64(double* A, int64_t n, double* Linv, double* work, int* status, cudaStream_t s) {
+  const int nb = kCholNB;
+  for (int64_t k = 0; k < n; k += nb) {
+    int kb = (int)std::min<int64_t>(nb, n - k);
+    double* Lk = Linv + (k / nb) * nb * nb;
+    potrf_diag_kernel<<<1, 256, 0, s>>>(A + k * n + k, n, kb, Lk, status, k);
+    int64_t m = n - k - kb;
+    if (m <= 0) continue;
+    // panel: P = A[k+kb:, k:k+kb] L_kk^{-T}
+    gemm_f64(true, m, kb, kb, 1.0, A + (k + kb) * n + k, n, 0, Lk, nb, 0, 0.0, work, kb, 0, 1,
+             false, s);
+    cudaMemcpy2DAsync(A + (k + kb) * n + k, n * sizeof(double), work, kb * sizeof(double),
+                      kb * sizeof(double), m, cudaMemcpyDeviceToDevice, s);
+    // trailing update of the lower triangle: A22 -= P P^T
+    gemm_f64(true, m, m, kb, -1.0, work, kb, 0, work, kb, 0, 1.0, A + (k + kb) * n + (k + kb), n,
+             0, 1, true, s);
+  }
+}
+
+// ------------------------------------------------------------------ triangular solves
+size_t trsm_work_elems(int64_t n, int64_t B) { return (size_t)B * kCholNB; }
+
+// Right-hand sides are the rows of X ([B][n]).  Forward: L Y = X, then
+// backward: L^T Z = Y; both blocked by the factor's diagonal blocks, whose
+// inverses Linv come from the factorisation.
+void trsm_lower_f64(const double* Lm, const double* Linv, int64_t n, double* X, int64_t B,
+                    double* work, const int* status, cudaStream_t s) {
+  (void)status;
+  const int nb = kCholNB;
+  for (int64_t k = 0; k < n; k += nb) {
+    int kb = (int)std::min<int64_t>(nb, n - k);
+    const double* Lk = Linv + (k / nb) * nb * nb;
+    // Y_k = X_k L_kk^{-T}
+    gemm_f64(true, B, kb, kb, 1.0, X + k, n, 0, Lk, nb, 0, 0.0, work, kb, 0, 1, false, s);
+    cudaMemcpy2DAsync(X + k, n * sizeof(double), work, kb * sizeof(double), kb * sizeof(double), B,
+                      cudaMemcpyDeviceToDevice, s);
+    int64_t m = n - k - kb;
+    if (m > 0)  // X[:, k+kb:] -= Y_k L[k+kb:, k:k+kb]^T
+      gemm_f64(true, B, m, kb, -1.0, X + k, n, 0, Lm + (k + kb) * n + k, n, 0, 1.0, X + k + kb, n,
+               0, 1, false, s);
+  }
+  int64_t last = ((n - 1) / nb) * nb;
+  for (int64_t k = last; k >= 0; k -= nb) {
+    int kb = (int)std::min<int64_t>(nb, n - k);
+    const double* Lk = Linv + (k / nb) * nb * nb;
+    // Z_k = X_k L_kk^{-1}
+    gemm_f64(false, B, kb, kb, 1.0, X + k, n, 0, Lk, nb, 0, 0.0, work, kb, 0, 1, false, s);
+    cudaMemcpy2DAsync(X + k, n * sizeof(double), work, kb * sizeof(double), kb * sizeof(double), B,
+                      cudaMemcpyDeviceToDevice, s);
+    if (k > 0)  // X[:, 0:k] -= Z_k L[k:k+kb, 0:k]
+      gemm_f64(false, B, k, kb, -1.0, X + k, n, 0, Lm + k * n, n, 0, 1.0, X, n, 0, 1, false, s);
+  }
+}
+
+__global__ void axpby_kernel(double* y, const double* x, double a, double b, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = fma(a, x[i], b * y[i]);
+}
+void axpby_f64(double* y, const double* x, double a, double b, int64_t n, cudaStream_t s) {
+  if (n > 0) axpby_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(y, x, a, b, n);
+}
+
+// r[b][i] -= diag[i] x[b][i] for B rows of length n (diagonal noise term of K x)
+__global__ void noise_residual_kernel(double* r, const double* x, const double* diag, int64_t n,
+                                      int64_t total) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < total) r[i] = fma(-diag[i % n], x[i], r[i]);
+}
+void noise_residual_f64(double* r, const double* x, const double* diag, int64_t n, int64_t B,
+                        cudaStream_t s) {
+  int64_t total = n * B;
+  if (total > 0)
+    noise_residual_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(r, x, diag, n, total);
+}
+
+}  // namespace bti

@@ -1,0 +1,353 @@
+// Batched zero-padded real FFTs along time for many spatial columns.
+//
+// Sec. 4 ("FFT-based GPU-accelerated p2o and p2q matvecs") embeds the block
+// Toeplitz map in a block circulant of length L and diagonalises it with the
+// DFT.  With L = 2 N_t the circulant product reproduces the truncated causal
+// convolution exactly, so every transform here is:
+//   forward : X[w] = sum_{t < N_t} x[t] e^{-2 pi i w t / L},  w = 0..N_t
+//             (real input, second half zero, Hermitian half spectrum kept)
+//   inverse : y[t] = scale * sum_{w < L} Y[w] e^{+2 pi i w t / L}, t < N_t only,
+//             with Y extended by Hermitian symmetry from w = 0..N_t.
+// A "column" is one spatial index; time runs along the strided axis and
+// columns are contiguous, so every global access is a coalesced row segment.
+//
+// Each CTA transforms 2P real columns as P complex transforms (column 2p in the
+// real part, 2p+1 in the imaginary part), in shared memory with a mixed-radix
+// (8, 4, 2, 7, 5, 3) Stockham pass sequence; twiddles e^{-2 pi i n / L} come from
+// a table computed in FP64 on the host with std::cos / std::sin.
+#include "bti_internal.cuh"
+
+#include <cmath>
+#include <vector>
+
+namespace bti {
+
+struct FftDesc {
+  int L;
+  int npass;
+  int P;
+  int radix[kMaxPasses];
+};
+
+bool fft_plan_make(FftPlan& p, int L) {
+  if (L < 2 || L > kMaxL) return false;
+  int n = L, np = 0;
+  const int order[6] = {8, 4, 2, 7, 5, 3};
+  for (int oi = 0; oi < 6; ++oi) {
+    int r = order[oi];
+    while (n % r == 0) {
+      if (np >= kMaxPasses) return false;
+      p.radix[np++] = r;
+      n /= r;
+    }
+  }
+  if (n != 1) return false;
+  p.L = L;
+  p.npass = np;
+  int P = 4096 / L;
+  if (P > 16) P = 16;
+  if (P < 1) P = 1;
+  p.P = P;
+  std::vector<double2> t64(L);
+  std::vector<float2> t32(L);
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int k = 0; k < L; ++k) {
+    double a = two_pi * (double)k / (double)L;
+    t64[k] = make_double2(std::cos(a), -std::sin(a));
+    t32[k] = make_float2((float)t64[k].x, (float)t64[k].y);
+  }
+  if (cudaMalloc(&p.tw64, sizeof(double2) * L) != cudaSuccess) return false;
+  if (cudaMalloc(&p.tw32, sizeof(float2) * L) != cudaSuccess) return false;
+  cudaMemcpy(p.tw64, t64.data(), sizeof(double2) * L, cudaMemcpyHostToDevice);
+  cudaMemcpy(p.tw32, t32.data(), sizeof(float2) * L, cudaMemcpyHostToDevice);
+  return true;
+}
+
+template <typename T> __device__ __forceinline__ const C2<T>* twtab(const double2* t64, const float2* t32);
+template <> __device__ __forceinline__ const double2* twtab<double>(const double2* t64, const float2*) { return t64; }
+template <> __device__ __forceinline__ const float2* twtab<float>(const double2*, const float2* t32) { return t32; }
+
+template <typename T, bool INV>
+__device__ __forceinline__ C2<T> tw_get(const C2<T>* __restrict__ tw, int n) {
+  C2<T> w = __ldg(&tw[n]);
+  if (INV) w.y = -w.y;
+  return w;
+}
+
+// multiply by -i (forward) or +i (inverse)
+template <typename T, bool INV>
+__device__ __forceinline__ C2<T> rot90(C2<T> a) {
+  return INV ? mk<T>(-a.y, a.x) : mk<T>(a.y, -a.x);
+}
+
+template <typename T, bool INV>
+__device__ __forceinline__ void dft4(C2<T>& a0, C2<T>& a1, C2<T>& a2, C2<T>& a3) {
+  C2<T> t0 = cadd<T>(a0, a2), t1 = csub<T>(a0, a2);
+  C2<T> t2 = cadd<T>(a1, a3), t3 = rot90<T, INV>(csub<T>(a1, a3));
+  a0 = cadd<T>(t0, t2);
+  a2 = csub<T>(t0, t2);
+  a1 = cadd<T>(t1, t3);
+  a3 = csub<T>(t1, t3);
+}
+
+// One radix-R Stockham butterfly: inputs s[q*Lr], q < R; outputs d[m*Ns], m < R.
+template <int R, typename T, bool INV>
+__device__ __forceinline__ void butterfly(const C2<T>* s, int Lr, C2<T>* d, int Ns,
+                                          const C2<T>* __restrict__ tw, int twstep, int L) {
+  C2<T> a[R];
+#pragma unroll
+  for (int q = 0; q < R; ++q) a[q] = s[q * Lr];
+  if (twstep != 0) {
+#pragma unroll
+    for (int q = 1; q < R; ++q) a[q] = cmul<T>(a[q], tw_get<T, INV>(tw, q * twstep));
+  }
+  if (R == 2) {
+    C2<T> b0 = cadd<T>(a[0], a[1]), b1 = csub<T>(a[0], a[1]);
+    a[0] = b0;
+    a[1] = b1;
+  } else if (R == 4) {
+    dft4<T, INV>(a[0], a[1], a[2], a[3]);
+  } else if (R == 8) {
+    // even / odd radix-4 halves, combined with powers of w8 = e^{-+ i pi / 4}
+    C2<T> e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6];
+    C2<T> o0 = a[1], o1 = a[3], o2 = a[5], o3 = a[7];
+    dft4<T, INV>(e0, e1, e2, e3);
+    dft4<T, INV>(o0, o1, o2, o3);
+    const T h = (T)0.70710678118654752440084436210485;  // sqrt(1/2)
+    C2<T> w1 = INV ? mk<T>(h, h) : mk<T>(h, -h);
+    C2<T> w3 = INV ? mk<T>(-h, h) : mk<T>(-h, -h);
+    o1 = cmul<T>(o1, w1);
+    o2 = rot90<T, INV>(o2);
+    o3 = cmul<T>(o3, w3);
+    a[0] = cadd<T>(e0, o0);
+    a[4] = csub<T>(e0, o0);
+    a[1] = cadd<T>(e1, o1);
+    a[5] = csub<T>(e1, o1);
+    a[2] = cadd<T>(e2, o2);
+    a[6] = csub<T>(e2, o2);
+    a[3] = cadd<T>(e3, o3);
+    a[7] = csub<T>(e3, o3);
+  } else {
+    // generic small DFT (R = 3, 5, 7): b_m = sum_q a_q w_R^{q m}, w_R^n = tw[(n mod R) L / R]
+    C2<T> b[R];
+    const int LR = L / R;
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      C2<T> acc = a[0];
+#pragma unroll
+      for (int q = 1; q < R; ++q) {
+        int e = (q * m) % R;
+        C2<T> w = tw_get<T, INV>(tw, e * LR);
+        acc = cadd<T>(acc, cmul<T>(a[q], w));
+      }
+      b[m] = acc;
+    }
+#pragma unroll
+    for (int m = 0; m < R; ++m) a[m] = b[m];
+  }
+#pragma unroll
+  for (int m = 0; m < R; ++m) d[m * Ns] = a[m];
+}
+
+// All passes; data starts in buf0, result pointer returned (buf0 or buf1).
+template <typename T, bool INV>
+__device__ C2<T>* run_passes(const FftDesc& D, C2<T>* buf0, C2<T>* buf1, const C2<T>* __restrict__ tw) {
+  C2<T>* src = buf0;
+  C2<T>* dst = buf1;
+  const int L = D.L;
+  int Ns = 1;
+  for (int ps = 0; ps < D.npass; ++ps) {
+    const int r = D.radix[ps];
+    const int Lr = L / r;
+    const int nbf = D.P * Lr;
+    for (int bi = threadIdx.x; bi < nbf; bi += blockDim.x) {
+      int p = bi / Lr;
+      int j = bi - p * Lr;
+      int k = j % Ns;
+      const C2<T>* s = src + p * L + j;
+      C2<T>* d = dst + p * L + (j - k) * r + k;
+      int twstep = k * (L / (Ns * r));
+      switch (r) {
+        case 8: butterfly<8, T, INV>(s, Lr, d, Ns, tw, twstep, L); break;
+        case 4: butterfly<4, T, INV>(s, Lr, d, Ns, tw, twstep, L); break;
+        case 2: butterfly<2, T, INV>(s, Lr, d, Ns, tw, twstep, L); break;
+        case 7: butterfly<7, T, INV>(s, Lr, d, Ns, tw, twstep, L); break;
+        case 5: butterfly<5, T, INV>(s, Lr, d, Ns, tw, twstep, L); break;
+        default: butterfly<3, T, INV>(s, Lr, d, Ns, tw, twstep, L); break;
+      }
+    }
+    __syncthreads();
+    C2<T>* tmp = src;
+    src = dst;
+    dst = tmp;
+    Ns *= r;
+  }
+  return src;
+}
+
+template <typename TO, typename T> __device__ __forceinline__ C2<TO> cvt2(C2<T> z) {
+  return mk<TO>((TO)z.x, (TO)z.y);
+}
+
+template <typename T, typename TI, typename TO>
+__global__ void __launch_bounds__(256)
+rfft_cols_kernel(FftDesc D, int Nt, const TI* __restrict__ x, int64_t ld, int64_t xbs,
+                 C2<TO>* __restrict__ X, int64_t Xbs, int64_t ncols,
+                 const double2* __restrict__ tw64, const float2* __restrict__ tw32) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int L = D.L, P = D.P, W2 = 2 * P;
+  C2<T>* buf0 = reinterpret_cast<C2<T>*>(smem_raw);
+  C2<T>* buf1 = buf0 + P * L;
+  const C2<T>* tw = twtab<T>(tw64, tw32);
+  const int64_t col0 = (int64_t)blockIdx.x * W2;
+  const TI* xb = x + (int64_t)blockIdx.y * xbs;
+  C2<TO>* Xb = X + (int64_t)blockIdx.y * Xbs;
+
+  for (int idx = threadIdx.x; idx < Nt * W2; idx += blockDim.x) {
+    int t = idx / W2, c = idx - t * W2;
+    int64_t col = col0 + c;
+    T v = (col < ncols) ? (T)xb[(int64_t)t * ld + col] : (T)0;
+    reinterpret_cast<T*>(&buf0[(c >> 1) * L + t])[c & 1] = v;
+  }
+  const int pad = L - Nt;
+  for (int idx = threadIdx.x; idx < P * pad; idx += blockDim.x) {
+    int p = idx / pad, t = Nt + (idx - p * pad);
+    buf0[p * L + t] = mk<T>((T)0, (T)0);
+  }
+  __syncthreads();
+  C2<T>* Z = run_passes<T, false>(D, buf0, buf1, tw);
+  // unpack the two real spectra of each pair and store bins 0..N_t
+  const int nf = Nt + 1;
+  for (int idx = threadIdx.x; idx < nf * W2; idx += blockDim.x) {
+    int k = idx / W2, c = idx - k * W2;
+    int64_t col = col0 + c;
+    if (col >= ncols) continue;
+    int p = c >> 1;
+    C2<T> z = Z[p * L + k];
+    C2<T> zc = Z[p * L + (k == 0 ? 0 : L - k)];
+    C2<T> out;
+    if ((c & 1) == 0) {
+      out = mk<T>((T)0.5 * (z.x + zc.x), (T)0.5 * (z.y - zc.y));   // (Z + conj Zc) / 2
+    } else {
+      out = mk<T>((T)0.5 * (z.y + zc.y), (T)0.5 * (zc.x - z.x));   // (Z - conj Zc) / 2i
+    }
+    Xb[(int64_t)k * ncols + col] = cvt2<TO, T>(out);
+  }
+}
+
+template <typename T, typename TO>
+__global__ void __launch_bounds__(256)
+irfft_cols_kernel(FftDesc D, int Nt, const C2<T>* __restrict__ Y, int64_t ld, int64_t Ybs,
+                  TO* __restrict__ y, int64_t ybs, int64_t ncols, T scale,
+                  const double2* __restrict__ tw64, const float2* __restrict__ tw32) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int L = D.L, P = D.P, W2 = 2 * P;
+  C2<T>* buf0 = reinterpret_cast<C2<T>*>(smem_raw);
+  C2<T>* buf1 = buf0 + P * L;
+  const C2<T>* tw = twtab<T>(tw64, tw32);
+  const int64_t col0 = (int64_t)blockIdx.x * W2;
+  const C2<T>* Yb = Y + (int64_t)blockIdx.y * Ybs;
+  TO* yb = y + (int64_t)blockIdx.y * ybs;
+  const int nf = Nt + 1;
+  // stage spectrum a (even column) in buf0, spectrum b (odd column) in buf1
+  for (int idx = threadIdx.x; idx < nf * W2; idx += blockDim.x) {
+    int k = idx / W2, c = idx - k * W2;
+    int64_t col = col0 + c;
+    C2<T> v = (col < ncols) ? Yb[(int64_t)k * ld + col] : mk<T>((T)0, (T)0);
+    C2<T>* dst = (c & 1) ? buf1 : buf0;
+    dst[(c >> 1) * L + k] = v;
+  }
+  __syncthreads();
+  // Z[k] = A[k] + i B[k] for k <= N_t and Z[L-k] = conj(A[k]) + i conj(B[k]);
+  // bins 0 and N_t of a real signal's spectrum are real: their imaginary parts are dropped.
+  for (int idx = threadIdx.x; idx < P * nf; idx += blockDim.x) {
+    int p = idx / nf, k = idx - p * nf;
+    C2<T> a = buf0[p * L + k];
+    C2<T> b = buf1[p * L + k];
+    if (k == 0 || k == Nt) {
+      buf0[p * L + k] = mk<T>(a.x, b.x);
+    } else {
+      buf0[p * L + k] = mk<T>(a.x - b.y, a.y + b.x);
+      buf0[p * L + (L - k)] = mk<T>(a.x + b.y, b.x - a.y);
+    }
+  }
+  __syncthreads();
+  C2<T>* Z = run_passes<T, true>(D, buf0, buf1, tw);
+  for (int idx = threadIdx.x; idx < Nt * W2; idx += blockDim.x) {
+    int t = idx / W2, c = idx - t * W2;
+    int64_t col = col0 + c;
+    if (col >= ncols) continue;
+    C2<T> z = Z[(c >> 1) * L + t];
+    T v = ((c & 1) ? z.y : z.x) * scale;
+    yb[(int64_t)t * ld + col] = (TO)v;
+  }
+}
+
+static FftDesc desc_of(const FftPlan& p) {
+  FftDesc d;
+  d.L = p.L;
+  d.npass = p.npass;
+  d.P = p.P;
+  for (int i = 0; i < kMaxPasses; ++i) d.radix[i] = (i < p.npass) ? p.radix[i] : 1;
+  return d;
+}
+
+template <typename T, typename TI, typename TO>
+void launch_rfft_cols(const FftPlan& p, int Nt, const TI* x, int64_t ld, int64_t x_bstride,
+                      C2<TO>* X, int64_t X_bstride, int64_t ncols, int64_t B, cudaStream_t s) {
+  if (ncols <= 0 || B <= 0) return;
+  FftDesc D = desc_of(p);
+  size_t smem = 2 * sizeof(C2<T>) * (size_t)p.P * p.L;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(rfft_cols_kernel<T, TI, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  int64_t gx = (ncols + 2 * p.P - 1) / (2 * p.P);
+  for (int64_t b0 = 0; b0 < B; b0 += 65535) {
+    int64_t nb = B - b0 < 65535 ? B - b0 : 65535;
+    dim3 grid((unsigned)gx, (unsigned)nb);
+    rfft_cols_kernel<T, TI, TO><<<grid, 256, smem, s>>>(D, Nt, x + b0 * x_bstride, ld, x_bstride,
+                                                        X + b0 * X_bstride, X_bstride, ncols,
+                                                        p.tw64, p.tw32);
+  }
+}
+
+template <typename T, typename TO>
+void launch_irfft_cols(const FftPlan& p, int Nt, const C2<T>* X, int64_t ld, int64_t X_bstride,
+                       TO* y, int64_t y_bstride, int64_t ncols, int64_t B, T scale, cudaStream_t s) {
+  if (ncols <= 0 || B <= 0) return;
+  FftDesc D = desc_of(p);
+  size_t smem = 2 * sizeof(C2<T>) * (size_t)p.P * p.L;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(irfft_cols_kernel<T, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  int64_t gx = (ncols + 2 * p.P - 1) / (2 * p.P);
+  for (int64_t b0 = 0; b0 < B; b0 += 65535) {
+    int64_t nb = B - b0 < 65535 ? B - b0 : 65535;
+    dim3 grid((unsigned)gx, (unsigned)nb);
+    irfft_cols_kernel<T, TO><<<grid, 256, smem, s>>>(D, Nt, X + b0 * X_bstride, ld, X_bstride,
+                                                     y + b0 * y_bstride, y_bstride, ncols, scale,
+                                                     p.tw64, p.tw32);
+  }
+}
+
+#define INST_R(T, TI, TO)                                                                    \
+  template void launch_rfft_cols<T, TI, TO>(const FftPlan&, int, const TI*, int64_t, int64_t, \
+                                            C2<TO>*, int64_t, int64_t, int64_t, cudaStream_t);
+INST_R(double, double, double)
+INST_R(double, double, float)
+INST_R(double, float, double)
+INST_R(float, float, float)
+INST_R(float, double, float)
+#define INST_I(T, TO)                                                                             \
+  template void launch_irfft_cols<T, TO>(const FftPlan&, int, const C2<T>*, int64_t, int64_t, TO*, \
+                                         int64_t, int64_t, int64_t, T, cudaStream_t);
+INST_I(double, double)
+INST_I(double, float)
+INST_I(float, float)
+INST_I(float, double)
+
+}  // namespace bti

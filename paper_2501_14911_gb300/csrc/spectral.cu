@@ -1,0 +1,202 @@
+// Per-frequency block products of the FFT-based Toeplitz matvecs.
+//
+// In Fourier space the block circulant embedding is block diagonal (Sec. 4,
+// "FFT-based GPU-accelerated p2o and p2q matvecs"), so for every frequency w
+//   forward : hat_d_w = hat_F_w hat_m_w             (reduction over j < N_m)
+//   adjoint : hat_m_w = hat_F_w^H hat_d_w           (reduction over i < R)
+// The spectral blocks are stored [w][i][j] with j contiguous: both products
+// stream each block row once with coalesced loads, and the reduction over j of
+// the forward product stays within contiguous rows (the strided alternative the
+// paper's footnote warns against is never used).  The forward reduction is
+// deterministic: per-chunk partial sums, then a fixed-order second pass.
+#include "bti_internal.cuh"
+
+namespace bti {
+
+template <typename T> struct FwdCfg;
+template <> struct FwdCfg<double> { static constexpr int JC1 = 2048, JC4 = 512; };
+template <> struct FwdCfg<float> { static constexpr int JC1 = 4096, JC4 = 1024; };
+
+template <typename T, typename TS> __device__ __forceinline__ C2<T> ldF(const C2<TS>* p) {
+  C2<TS> v = __ldg(p);
+  return mk<T>((T)v.x, (T)v.y);
+}
+
+// grid (nchunk, nf, ceil(B / BG)), 256 threads.  Warp w handles rows i = w, w + 8, ...
+template <typename T, typename TS, int BG>
+__global__ void __launch_bounds__(256)
+prod_fwd_kernel(const C2<TS>* __restrict__ Fhat, const C2<T>* __restrict__ mhat,
+                C2<T>* __restrict__ partial, int64_t nf, int64_t R, int64_t Nm, int64_t B,
+                int JC, int nchunk) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2<T>* sm = reinterpret_cast<C2<T>*>(smem_raw);  // [BG][JC]
+  const int ch = blockIdx.x;
+  const int64_t w = blockIdx.y;
+  const int64_t b0 = (int64_t)blockIdx.z * BG;
+  const int64_t j0 = (int64_t)ch * JC;
+  const int jn = (int)((Nm - j0) < JC ? (Nm - j0) : JC);
+  for (int idx = threadIdx.x; idx < BG * JC; idx += blockDim.x) {
+    int bb = idx / JC, jj = idx - bb * JC;
+    C2<T> v = mk<T>((T)0, (T)0);
+    if (jj < jn && b0 + bb < B) v = mhat[((b0 + bb) * nf + w) * Nm + j0 + jj];
+    sm[idx] = v;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t i = warp; i < R; i += 8) {
+    const C2<TS>* row = Fhat + (w * R + i) * Nm + j0;
+    T ar[BG], ai[BG];
+#pragma unroll
+    for (int bb = 0; bb < BG; ++bb) { ar[bb] = (T)0; ai[bb] = (T)0; }
+#pragma unroll 8
+    for (int jj = lane; jj < jn; jj += 32) {
+      C2<T> f = ldF<T, TS>(row + jj);
+#pragma unroll
+      for (int bb = 0; bb < BG; ++bb) {
+        C2<T> x = sm[bb * JC + jj];
+        ar[bb] = fma(f.x, x.x, ar[bb]);
+        ar[bb] = fma(-f.y, x.y, ar[bb]);
+        ai[bb] = fma(f.x, x.y, ai[bb]);
+        ai[bb] = fma(f.y, x.x, ai[bb]);
+      }
+    }
+#pragma unroll
+    for (int bb = 0; bb < BG; ++bb) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        ar[bb] += __shfl_xor_sync(0xffffffffu, ar[bb], o);
+        ai[bb] += __shfl_xor_sync(0xffffffffu, ai[bb], o);
+      }
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int bb = 0; bb < BG; ++bb)
+        if (b0 + bb < B) partial[(((b0 + bb) * nf + w) * nchunk + ch) * R + i] = mk<T>(ar[bb], ai[bb]);
+    }
+  }
+}
+
+// dhat[b][w][i] = sum over chunks, fixed order
+template <typename T>
+__global__ void reduce_chunks_kernel(const C2<T>* __restrict__ partial, C2<T>* __restrict__ dhat,
+                                     int64_t total, int64_t R, int nchunk) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  int64_t bw = idx / R, i = idx - bw * R;
+  const C2<T>* p = partial + bw * nchunk * R + i;
+  T sr = 0, si = 0;
+  for (int c = 0; c < nchunk; ++c) {
+    C2<T> v = p[(int64_t)c * R];
+    sr += v.x;
+    si += v.y;
+  }
+  dhat[idx] = mk<T>(sr, si);
+}
+
+template <typename T> static int fwd_bg(int64_t B) { return B >= 4 ? 4 : 1; }
+template <typename T> static int fwd_jc(int bg) { return bg == 4 ? FwdCfg<T>::JC4 : FwdCfg<T>::JC1; }
+
+size_t prod_fwd_partial_elems(int64_t nf, int64_t R, int64_t Nm, int64_t B) {
+  // worst case over the two tiers: the smallest chunk (FP64, BG = 4)
+  int64_t nchunk = (Nm + FwdCfg<double>::JC4 - 1) / FwdCfg<double>::JC4;
+  return (size_t)(B * nf * nchunk * R);
+}
+
+template <typename T, typename TS>
+void launch_prod_fwd(const C2<TS>* Fhat, const C2<T>* mhat, C2<T>* partial, C2<T>* dhat,
+                     int64_t nf, int64_t R, int64_t Nm, int64_t B, cudaStream_t s) {
+  int bg = fwd_bg<T>(B);
+  int JC = fwd_jc<T>(bg);
+  if (Nm < JC) JC = (int)(((Nm + 31) / 32) * 32);
+  int nchunk = (int)((Nm + JC - 1) / JC);
+  size_t smem = sizeof(C2<T>) * (size_t)bg * JC;
+  dim3 grid((unsigned)nchunk, (unsigned)nf, (unsigned)((B + bg - 1) / bg));
+  if (bg == 4)
+    prod_fwd_kernel<T, TS, 4><<<grid, 256, smem, s>>>(Fhat, mhat, partial, nf, R, Nm, B, JC, nchunk);
+  else
+    prod_fwd_kernel<T, TS, 1><<<grid, 256, smem, s>>>(Fhat, mhat, partial, nf, R, Nm, B, JC, nchunk);
+  int64_t total = B * nf * R;
+  reduce_chunks_kernel<T><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(partial, dhat, total, R, nchunk);
+}
+
+// grid (ceil(Nm / (256 VPT)), nf, ceil(B / BG)); thread owns j = j0 + tid + 256 v
+template <typename T, typename TS, int BG, int VPT>
+__global__ void __launch_bounds__(256)
+prod_adj_kernel(const C2<TS>* __restrict__ Fhat, const C2<T>* __restrict__ dhat,
+                C2<T>* __restrict__ mhat, int64_t nf, int64_t R, int64_t Nm, int64_t B) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2<T>* sd = reinterpret_cast<C2<T>*>(smem_raw);  // [BG][R]
+  const int64_t w = blockIdx.y;
+  const int64_t b0 = (int64_t)blockIdx.z * BG;
+  for (int64_t idx = threadIdx.x; idx < BG * R; idx += blockDim.x) {
+    int64_t bb = idx / R, i = idx - bb * R;
+    C2<T> v = mk<T>((T)0, (T)0);
+    if (b0 + bb < B) v = dhat[((b0 + bb) * nf + w) * R + i];
+    sd[idx] = v;
+  }
+  __syncthreads();
+  const int64_t jbase = (int64_t)blockIdx.x * (256 * VPT) + threadIdx.x;
+  T ar[BG][VPT], ai[BG][VPT];
+#pragma unroll
+  for (int bb = 0; bb < BG; ++bb)
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) { ar[bb][v] = (T)0; ai[bb][v] = (T)0; }
+  const C2<TS>* base = Fhat + w * R * Nm;
+  for (int64_t i = 0; i < R; ++i) {
+    const C2<TS>* row = base + i * Nm;
+    C2<T> f[VPT];
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      int64_t j = jbase + 256 * v;
+      f[v] = (j < Nm) ? ldF<T, TS>(row + j) : mk<T>((T)0, (T)0);
+    }
+#pragma unroll
+    for (int bb = 0; bb < BG; ++bb) {
+      C2<T> x = sd[bb * R + i];
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) {
+        // conj(f) * x
+        ar[bb][v] = fma(f[v].x, x.x, ar[bb][v]);
+        ar[bb][v] = fma(f[v].y, x.y, ar[bb][v]);
+        ai[bb][v] = fma(f[v].x, x.y, ai[bb][v]);
+        ai[bb][v] = fma(-f[v].y, x.x, ai[bb][v]);
+      }
+    }
+  }
+#pragma unroll
+  for (int bb = 0; bb < BG; ++bb) {
+    if (b0 + bb >= B) continue;
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      int64_t j = jbase + 256 * v;
+      if (j < Nm) mhat[((b0 + bb) * nf + w) * Nm + j] = mk<T>(ar[bb][v], ai[bb][v]);
+    }
+  }
+}
+
+template <typename T, typename TS>
+void launch_prod_adj(const C2<TS>* Fhat, const C2<T>* dhat, C2<T>* mhat,
+                     int64_t nf, int64_t R, int64_t Nm, int64_t B, cudaStream_t s) {
+  if (B >= 4) {
+    constexpr int BG = 4, VPT = 2;
+    size_t smem = sizeof(C2<T>) * (size_t)BG * R;
+    dim3 grid((unsigned)((Nm + 256 * VPT - 1) / (256 * VPT)), (unsigned)nf, (unsigned)((B + BG - 1) / BG));
+    prod_adj_kernel<T, TS, BG, VPT><<<grid, 256, smem, s>>>(Fhat, dhat, mhat, nf, R, Nm, B);
+  } else {
+    constexpr int BG = 1, VPT = 4;
+    size_t smem = sizeof(C2<T>) * (size_t)BG * R;
+    dim3 grid((unsigned)((Nm + 256 * VPT - 1) / (256 * VPT)), (unsigned)nf, (unsigned)B);
+    prod_adj_kernel<T, TS, BG, VPT><<<grid, 256, smem, s>>>(Fhat, dhat, mhat, nf, R, Nm, B);
+  }
+}
+
+template void launch_prod_fwd<double, double>(const double2*, const double2*, double2*, double2*,
+                                              int64_t, int64_t, int64_t, int64_t, cudaStream_t);
+template void launch_prod_fwd<float, float>(const float2*, const float2*, float2*, float2*,
+                                            int64_t, int64_t, int64_t, int64_t, cudaStream_t);
+template void launch_prod_adj<double, double>(const double2*, const double2*, double2*,
+                                              int64_t, int64_t, int64_t, int64_t, cudaStream_t);
+template void launch_prod_adj<float, float>(const float2*, const float2*, float2*,
+                                            int64_t, int64_t, int64_t, int64_t, cudaStream_t);
+
+}  // namespace bti

@@ -1,0 +1,263 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances are normwise relative errors per right-hand side, the maximum over
+the batch: 1e-12 for the FP64 tier, 1e-5 for the FP32 tier (products and FFTs
+in FP32), 1e-12 for K, its factor, m_map and q_map at the tiny inversion
+(kappa(K) is a few hundred, so FP64 rounding stays far below that bound).
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2501_14911_gb300 import synthetic
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2501_14911_gb300 as bti  # noqa: E402
+
+TOL = {bti.F64: 1e-12, bti.F32: 1e-5}
+
+
+def relb(a, b):
+    """max over the leading batch axis of ||a_b - b_b|| / ||b_b||."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    a = a.reshape(a.shape[0], -1)
+    b = b.reshape(b.shape[0], -1)
+    num = np.linalg.norm(a - b, axis=1)
+    den = np.maximum(np.linalg.norm(b, axis=1), 1e-300)
+    return float(np.max(num / den))
+
+
+def cuda(x, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(x)).to(device="cuda", dtype=dtype)
+
+
+def host(x):
+    torch.cuda.synchronize()
+    return x.detach().cpu().numpy().astype(np.float64)
+
+
+def make_handle(F, Fq=None, store=bti.F64):
+    Nt, Nd, Nm = F.shape
+    Nq = 0 if Fq is None else Fq.shape[1]
+    h = bti.Handle(Nm, Nd, Nq, Nt)
+    h.set_blocks(bti.OP_F, cuda(F), store)
+    if Fq is not None:
+        h.set_blocks(bti.OP_FQ, cuda(Fq), store)
+    return h
+
+
+CASES = [
+    # (name, Nm, Nd, Nq, Nt, B): ragged chunks / warps / column pairs, several radices
+    ("L90_ragged", 3000, 13, 5, 45, 3),
+    ("L128_b6", 1024, 8, 4, 64, 6),
+    ("L420", 700, 6, 3, 210, 2),
+    ("L400_batched_shape", 4096, 100, 32, 200, 1),
+    ("L840_odd", 333, 7, 2, 420, 1),
+    ("Nt1_gemv", 257, 5, 3, 1, 2),
+    ("scalar", 1, 1, 1, 16, 2),
+]
+
+
+@pytest.mark.parametrize("store", [bti.F64, bti.F32], ids=["f64", "f32"])
+@pytest.mark.parametrize("name,Nm,Nd,Nq,Nt,B", CASES, ids=[c[0] for c in CASES])
+def test_apply_F_FT_Fq_match_oracle(name, Nm, Nd, Nq, Nt, B, store):
+    p = synthetic.small(name, 1, Nm, Nd, Nt, Nq=Nq)
+    F = p.blocks_F()
+    Fq = p.blocks_Fq()
+    m = p.vectors_m(B)
+    d = p.vectors_d(B)
+    h = make_handle(F, Fq, store)
+    dt = torch.float64 if store == bti.F64 else torch.float32
+    m_g, d_g = cuda(m, dt), cuda(d, dt)
+    out_d = torch.empty((B, Nt, Nd), dtype=dt, device="cuda")
+    out_m = torch.empty((B, Nt, Nm), dtype=dt, device="cuda")
+    out_q = torch.empty((B, Nt, Nq), dtype=dt, device="cuda")
+    h.apply_F(m_g, out_d)
+    h.apply_FT(d_g, out_m)
+    h.apply_Fq(m_g, out_q)
+    h.sync()
+    # the oracle sees the inputs exactly as the GPU does (rounded to the io type)
+    m_in, d_in = host(m_g), host(d_g)
+    tol = TOL[store]
+    assert relb(host(out_d), oracle.p2o_apply(F, m_in)) < tol
+    assert relb(host(out_m), oracle.p2o_apply_adjoint(F, d_in)) < tol
+    assert relb(host(out_q), oracle.p2o_apply(Fq, m_in)) < tol
+    h.close()
+
+
+@pytest.mark.parametrize("store,io", [(bti.F64, torch.float32), (bti.F32, torch.float64)],
+                         ids=["f64tier_f32io", "f32tier_f64io"])
+def test_mixed_io_types(store, io):
+    p = synthetic.small("mixed_io", 40, 50, 9, 32)
+    F = p.blocks_F()
+    m = p.vectors_m(2)
+    h = make_handle(F, None, store)
+    m_g = cuda(m, io)
+    d = torch.empty((2, 32, 9), dtype=io, device="cuda")
+    h.apply_F(m_g, d)
+    assert relb(host(d), oracle.p2o_apply(F, host(m_g))) < 1e-5
+
+
+def test_impulse_response_and_causality():
+    p = synthetic.small("impulse", 8, 8, 4, 24)
+    F = p.blocks_F()
+    h = make_handle(F)
+    Nt, Nd, Nm = F.shape
+    m = np.zeros((1, Nt, Nm))
+    s, j = 5, 17
+    m[0, s, j] = 1.0
+    d = torch.empty((1, Nt, Nd), dtype=torch.float64, device="cuda")
+    h.apply_F(cuda(m), d)
+    dh = host(d)[0]
+    scale = np.abs(F).max()
+    np.testing.assert_allclose(dh[:s], 0.0, atol=1e-14 * scale)
+    for t in range(s, Nt):
+        np.testing.assert_allclose(dh[t], F[t - s][:, j], rtol=0, atol=1e-14 * scale)
+
+
+def test_adjoint_identity_on_gpu():
+    p = synthetic.small("adjoint", 32, 32, 16, 100)
+    F = p.blocks_F()
+    h = make_handle(F)
+    m = cuda(p.vectors_m(1))
+    dv = cuda(p.vectors_d(1))
+    Fm = torch.empty((1, 100, 16), dtype=torch.float64, device="cuda")
+    FTd = torch.empty((1, 100, 1024), dtype=torch.float64, device="cuda")
+    h.apply_F(m, Fm)
+    h.apply_FT(dv, FTd)
+    lhs = float((Fm * dv).sum())
+    rhs = float((m * FTd).sum())
+    assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), float(Fm.abs().sum() * dv.abs().max()))
+
+
+def test_zero_batch_is_noop_and_errors_are_reported():
+    p = synthetic.small("errs", 4, 4, 3, 8)
+    F = p.blocks_F()
+    h = bti.Handle(16, 3, 2, 8)
+    m = torch.zeros((1, 8, 16), dtype=torch.float64, device="cuda")
+    d = torch.zeros((1, 8, 3), dtype=torch.float64, device="cuda")
+    with pytest.raises(bti.BtiError) as e:
+        h.apply_F(m, d)  # blocks not set
+    assert e.value.status == 3
+    with pytest.raises(bti.BtiError) as e:
+        h.build_K()
+    assert e.value.status == 3
+    with pytest.raises(bti.BtiError) as e:
+        h.infer_map(d, m)
+    assert e.value.status == 3
+    h.set_blocks(bti.OP_F, cuda(F))
+    L = bti.lib()
+    assert L.bti_apply_F(h.raw, m.data_ptr(), d.data_ptr(), 0, 0) == 0
+    assert L.bti_apply_F(h.raw, m.data_ptr(), d.data_ptr(), -1, 0) == 1
+    assert L.bti_apply_F(h.raw, m.data_ptr(), d.data_ptr(), 1, 7) == 1
+    assert L.bti_apply_F(h.raw, None, d.data_ptr(), 1, 0) == 1
+    assert L.bti_set_prior_se_grid(h.raw, 3, 3, 3.0, 1.0, 0) == 2  # 3 x 3 != 16
+    assert "gx * gy" in h.last_error
+    h.close()
+
+
+def tiny_problem():
+    p = synthetic.TINY
+    F = p.blocks_F()
+    Fq = p.blocks_Fq()
+    Cs = oracle.se_covariance(p.gx, p.gy, p.ell, p.sigma_p)
+    G = oracle.prior_blocks(F, Cs)
+    m_true = oracle.prior_sample(p.z_true(1), p.gx, p.gy, p.ell, p.sigma_p)
+    d_obs = oracle.p2o_apply(F, m_true) + np.sqrt(p.sigma2) * p.noise(1)
+    return p, F, Fq, G, d_obs
+
+
+def test_tiny_inversion_end_to_end():
+    p, F, Fq, G, d_obs = tiny_problem()
+    h = make_handle(F, Fq)
+    h.set_prior_se_grid(p.gx, p.gy, p.ell, p.sigma_p)
+    # G^* from the device-built SE prior matches Gamma_prior F^T
+    dv = p.vectors_d(2)
+    mg = torch.empty((2, p.Nt, p.Nm), dtype=torch.float64, device="cuda")
+    h.apply_Gstar(cuda(dv), mg)
+    assert relb(host(mg), oracle.p2o_apply_adjoint(G, dv)) < 1e-12
+    h.set_noise(p.sigma2)
+    h.build_K()
+    K_gpu = host(h.copy_K())
+    K_or = oracle.assemble_K(F, G, p.sigma2)
+    low = np.tril_indices(K_or.shape[0])
+    assert np.linalg.norm(K_gpu[low] - K_or[low]) / np.linalg.norm(K_or[low]) < 1e-12
+    h.factor_K()
+    L_gpu = host(h.copy_K())
+    L_or = oracle.cholesky_lower(K_or)
+    assert np.linalg.norm(L_gpu[low] - L_or[low]) / np.linalg.norm(L_or[low]) < 1e-12
+    m_map = torch.empty((1, p.Nt, p.Nm), dtype=torch.float64, device="cuda")
+    h.infer_map(cuda(d_obs), m_map)
+    q_map = torch.empty((1, p.Nt, p.Nq), dtype=torch.float64, device="cuda")
+    h.predict_qoi(m_map, q_map)
+    m_or = oracle.map_point(F, G, p.sigma2, d_obs)
+    assert relb(host(m_map), m_or) < 1e-12
+    assert relb(host(q_map), oracle.qoi_map(Fq, m_or)) < 1e-12
+    # iterative refinement keeps the answer (and is exercised)
+    m_ref = torch.empty_like(m_map)
+    h.infer_map(cuda(d_obs), m_ref, refine_iters=2)
+    assert relb(host(m_ref), m_or) < 1e-12
+
+
+def test_diagonal_noise_and_batched_obs():
+    p = synthetic.small("diagnoise", 6, 6, 5, 30, Nq=3)
+    F = p.blocks_F()
+    Cs = oracle.se_covariance(6, 6, 2.0, 1.0)
+    G = oracle.prior_blocks(F, Cs)
+    var = 1e-3 * (1.0 + np.arange(30 * 5).reshape(30, 5) % 7)
+    d_obs = p.vectors_d(5)
+    h = make_handle(F, p.blocks_Fq())
+    h.set_prior_se_grid(6, 6, 2.0, 1.0)
+    h.set_noise(0.0, cuda(var))
+    h.build_K(col_block=37)
+    h.factor_K()
+    m_map = torch.empty((5, 30, 36), dtype=torch.float64, device="cuda")
+    h.infer_map(cuda(d_obs), m_map, refine_iters=1)
+    assert relb(host(m_map), oracle.map_point(F, G, var, d_obs)) < 1e-11
+
+
+def test_not_spd_is_reported_with_pivot():
+    """A negative noise variance injected on the host makes K indefinite."""
+    p = synthetic.small("notspd", 4, 4, 3, 10)
+    F = p.blocks_F() * 1e-3
+    var = np.full((10, 3), 1e-4)
+    var[4, 1] = -10.0  # data index 4 * 3 + 1 = 13 -> pivot 14 (1-based) or earlier
+    h = make_handle(F)
+    h.set_prior_se_grid(4, 4, 3.0, 1.0)
+    h.set_noise(0.0, cuda(var))
+    h.build_K()
+    with pytest.raises(bti.BtiError) as e:
+        h.factor_K()
+    assert e.value.status == 6
+    assert "pivot 14" in e.value.message
+    # the handle stays usable: a valid noise makes it factorable again
+    h.set_noise(1e-4)
+    h.build_K()
+    h.factor_K()
+    h.sync()
+
+
+def test_autograd_gradient_matches_oracle_and_fd():
+    p = synthetic.small("grad", 8, 16, 6, 32)
+    F = p.blocks_F()
+    h = make_handle(F)
+    m0 = p.vectors_m(1)
+    dobs = p.vectors_d(1)
+    s2 = 0.05
+    m = cuda(m0).requires_grad_(True)
+    d = cuda(dobs)
+    r = bti.apply_F_autograd(h, m) - d
+    loss = 0.5 * (r * r).sum() / s2
+    loss.backward()
+    g_or = oracle.loss_gradient(F, m0[0], dobs[0], s2)
+    assert relb(host(m.grad), g_or[None]) < 1e-12
+    v = np.random.default_rng(0).standard_normal(m0.shape)
+    hstep = 1e-6
+    lp = oracle.loss(F, (m0 + hstep * v)[0], dobs[0], s2)
+    lm = oracle.loss(F, (m0 - hstep * v)[0], dobs[0], s2)
+    fd = (lp - lm) / (2 * hstep)
+    assert abs(fd - float(np.vdot(host(m.grad), v))) <= 1e-6 * abs(fd) + 1e-8 * abs(float(loss))

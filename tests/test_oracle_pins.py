@@ -352,3 +352,16 @@ def test_synthetic_blocks_recipe():
     big = synthetic.toeplitz_blocks(5, 4, 64, 512, 2.0)
     std = big.reshape(4, -1).std(axis=1)
     np.testing.assert_allclose(std, np.exp(-np.arange(4) / 2.0), rtol=0.02)
+
+
+def test_single_block_outputs_match_full_products():
+    blocks, rng = micro(Nt=9, R=3, Nm=7)
+    m = rng.standard_normal((9, 7))
+    d = rng.standard_normal((9, 3))
+    full = oracle.p2o_apply(blocks, m)
+    fullT = oracle.p2o_apply_adjoint(blocks, d)
+    P = oracle.p2o_dense(blocks)
+    for t in (0, 4, 8):
+        assert rel(oracle.p2o_apply_block(blocks, m, t), full[t]) < 1e-15
+        assert rel(oracle.p2o_apply_block(blocks, m, t), (P @ m.reshape(-1)).reshape(9, 3)[t]) < 1e-14
+        assert rel(oracle.p2o_apply_adjoint_block(blocks, d, t), fullT[t]) < 1e-15
