@@ -1,0 +1,476 @@
+#!/usr/bin/env python3
+"""Benchmark of the block-Toeplitz matvec hot path on one GB300 (or N replicas).
+
+Workload (the matvec sweep): N_m = 65,536 (256 x 256 grid), N_d = 128,
+N_t = 256 (L = 512), seeded Gaussian blocks with exp(-k/64) decay, 16 random
+m and d vectors.  One step applies F to each of the 16 m vectors and F^T to
+each of the 16 d vectors, one vector per call (single right-hand side, the
+paper's matvec), on the FP64 tier; every call streams the 34.5 GB of FP64
+spectral blocks from HBM (far larger than L2), so no L2 flush is needed.
+
+value = algorithmic bytes of the step's calls / device time, summed over
+ranks (replicas: each rank runs the whole workload on its own GPU).  The
+algorithmic bytes of one call are the spectral blocks read once plus its input
+and output vectors.  The JSON line also carries the FP32 tier, the end-to-end
+figure through host buffers, the dominant kernel's roofline, the CPU oracle
+baseline, clocks, and the online m_map + q_map latency of the batched workload.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "F/F^T matvec GB/s and % HBM roofline; online m_map+q_map latency at 1e-6 rel err"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-online", action="store_true", help="skip the batched online-latency block")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--case", choices=["sweep", "small"], default="sweep",
+                    help="small: the sweep shape with N_m = 4096 and 2 vectors (2.2 GB of FP64 spectral "
+                         "blocks, still far above L2) for ncu captures; implies --no-online, "
+                         "--no-cpu-baseline and --no-e2e")
+    a = ap.parse_args()
+    if a.case == "small":
+        a.no_online = a.no_cpu_baseline = a.no_e2e = True
+    return a
+
+
+def workload(args):
+    from paper_2501_14911_gb300 import synthetic
+
+    if args.case == "small":
+        return synthetic.Problem("matvec_sweep_small_Nm4096_Nd128_Nt256", 6, 64, 64, 128, 256, 32, 64.0,
+                                 n_vectors=2)
+    return synthetic.SWEEP
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), float(pk.get("bf16_tflops", 1900.0)), "measured"
+    except Exception:
+        return 6800.0, 1900.0, "fallback"
+
+
+# FP64 FFMA-pipe rate of this GB300 (TFLOP/s), from a DFMA throughput probe:
+# 2 DFMA per clock per SM x 152 SMs at the sustained clock.
+FP64_TFLOPS = 1.2
+
+
+class Clocks:
+    """nvidia-smi sampler (every 200 ms) for the timed region."""
+
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                if self.uuid and self.uuid not in parts[0]:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def spectral_hash():
+    h = hashlib.sha256()
+    for f in ("spectral.cu", "bti_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2501_14911_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_tag):
+    """Per-launch DRAM bytes of the product kernels from the committed ncu summary,
+    or None when the kernel source changed since that capture."""
+    path = os.path.join(ROOT, "profiles", "traffic_spectral_products.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except Exception:
+        return None
+    if rec.get("source_hash") != spectral_hash():
+        return None
+    return rec.get(kernel_tag)
+
+
+def cores_used():
+    try:
+        from threadpoolctl import threadpool_info
+
+        n = [i.get("num_threads") for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def bytes_per_call(p, esize, csize):
+    Fhat = (p.Nt + 1) * p.Nd * p.Nm * csize
+    io = (p.Nt * p.Nm + p.Nt * p.Nd) * esize
+    return Fhat + io
+
+
+def cpu_oracle_sample(p, F, m, d, budget_s=12.0):
+    """Time the oracle's F and F^T on whole vectors until ~budget_s of CPU work."""
+    import oracle
+
+    t0 = time.perf_counter()
+    pairs = 0
+    while pairs < m.shape[0]:
+        oracle.p2o_apply(F, m[pairs])
+        oracle.p2o_apply_adjoint(F, d[pairs])
+        pairs += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return pairs, dt
+
+
+# --------------------------------------------------------------------------------------------
+def run_reference(args):
+    """The CPU oracle as the reference arm (rank 0 only), on the same workload and metric."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2501_14911_gb300 import synthetic
+
+    p = workload(args)
+    F = p.blocks_F()
+    m = p.vectors_m()
+    d = p.vectors_d()
+    bpc = bytes_per_call(p, 8, 16)
+    times = []
+    for it in range(args.warmup + args.steps):
+        pairs, dt = cpu_oracle_sample(p, F, m[:1], d[:1], budget_s=0.0)
+        if it >= args.warmup:
+            times.append(dt / pairs)
+    per_pair = statistics.mean(times)
+    value = 2 * bpc / per_pair / 1e9
+    cores = cores_used()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_pair * 1e3 * p.n_vectors,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": p.name, "Nm": p.Nm, "Nd": p.Nd, "Nt": p.Nt, "vectors": p.n_vectors,
+                   "rhs_per_call": 1, "parallelism": "cpu"},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cores, "kind": "oracle",
+                         "sample": "each step: oracle time-domain F m and F^T d on one sweep vector pair "
+                                   "(full size), scaled to the GPU formulation's algorithmic bytes"},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2501_14911_gb300 as bti
+    from paper_2501_14911_gb300 import synthetic
+
+    world, rank, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    hbm_peak, _, peak_src = load_peaks()
+
+    p = workload(args)
+    V = p.n_vectors
+    F_host = p.blocks_F()
+    m_host = p.vectors_m()
+    d_host = p.vectors_d()
+
+    # FP64 tier (headline) and FP32 tier handles; spectral blocks built on the device
+    h64 = bti.Handle(p.Nm, p.Nd, 0, p.Nt, device=dev)
+    h32 = bti.Handle(p.Nm, p.Nd, 0, p.Nt, device=dev)
+    Fd = torch.from_numpy(F_host).to(dev)
+    h64.set_blocks(bti.OP_F, Fd, bti.F64)
+    h32.set_blocks(bti.OP_F, Fd, bti.F32)
+    torch.cuda.synchronize()
+    del Fd
+    torch.cuda.empty_cache()
+
+    m64 = torch.from_numpy(m_host).to(dev)
+    d64 = torch.from_numpy(d_host).to(dev)
+    m32, d32 = m64.float(), d64.float()
+    od64 = torch.empty((V, p.Nt, p.Nd), dtype=torch.float64, device=dev)
+    om64 = torch.empty((V, p.Nt, p.Nm), dtype=torch.float64, device=dev)
+    od32, om32 = od64.float(), om64.float()
+
+    def step(h, m, d, od, om):
+        for b in range(V):
+            h.apply_F(m[b], od[b])
+            h.apply_FT(d[b], om[b])
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def timed(fn, steps, warmup, prof_handle=None):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        if prof_handle is not None:
+            prof_handle.profile_read()  # reset counters
+            prof_handle.profile_enable(True)
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        prof = None
+        if prof_handle is not None:
+            prof = prof_handle.profile_read()
+            prof_handle.profile_enable(False)
+        if world > 1:
+            t = torch.tensor([ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, prof
+
+    uuid = str(torch.cuda.get_device_properties(dev).uuid) if hasattr(torch.cuda.get_device_properties(dev), "uuid") else ""
+    clocks = Clocks(uuid)
+    clocks.start()
+    ms64, prof64 = timed(lambda: step(h64, m64, d64, od64, om64), args.steps, args.warmup, h64)
+    clk = clocks.stop()
+    ms32, prof32 = timed(lambda: step(h32, m32, d32, od32, om32), args.steps, args.warmup, h32)
+
+    bpc64 = bytes_per_call(p, 8, 16)
+    bpc32 = bytes_per_call(p, 4, 8)
+    bytes_step64 = 2 * V * bpc64
+    bytes_step32 = 2 * V * bpc32
+    value = world * bytes_step64 * args.steps / (ms64 * 1e-3) / 1e9
+    value32 = world * bytes_step32 * args.steps / (ms32 * 1e-3) / 1e9
+
+    # dominant kernel: the per-frequency spectral products (forward and adjoint)
+    def roofline(prof, csize, fp_peak_tflops, kind):
+        (pf_ms, pf_n), (pa_ms, pa_n) = prof[0]["prod_fwd"], prof[0]["prod_adj"]
+        nf = p.Nt + 1
+        Fhat = nf * p.Nd * p.Nm * csize
+        mhat = nf * p.Nm * csize
+        bytes_launch = Fhat + mhat  # spectral blocks + the frequency-domain vector (read or written)
+        flops_launch = 8.0 * nf * p.Nd * p.Nm
+        avg_ms = (pf_ms + pa_ms) / max(pf_n + pa_n, 1)
+        gbs = bytes_launch / (avg_ms * 1e-3) / 1e9
+        tflops = flops_launch / (avg_ms * 1e-3) / 1e12
+        t_hbm = bytes_launch / (hbm_peak * 1e9)
+        t_alu = flops_launch / (fp_peak_tflops * 1e12)
+        traffic = ncu_traffic(f"{kind}_bytes_per_launch")
+        share_total = sum(v[0] for v in prof[0].values())
+        common = {"kernel": f"prod_fwd_kernel + prod_adj_kernel ({kind})", "avg_launch_ms": avg_ms,
+                  "launches": pf_n + pa_n, "share_of_step_kernel_time": (pf_ms + pa_ms) / max(share_total, 1e-9),
+                  "traffic": traffic, "algorithmic_bytes_per_launch": bytes_launch,
+                  "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak}
+        if t_alu > t_hbm:
+            return dict({"bound": "alu", "achieved": tflops, "peak": fp_peak_tflops, "unit": "TFLOP/s",
+                         "frac": tflops / fp_peak_tflops,
+                         "peak_source": "FP64 DFMA throughput probe (2 DFMA/clk/SM x 152 SMs)"}, **common)
+        return dict({"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                      "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})"}, **common)
+
+    roof64 = roofline(prof64, 16, FP64_TFLOPS, "f64")
+    roof32 = roofline(prof32, 8, 75.0, "f32")
+    launches = sum(v[1] for v in prof64[0].values())
+
+    # end to end through the public API with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        mh = torch.from_numpy(m_host).pin_memory()
+        dh = torch.from_numpy(d_host).pin_memory()
+        odh = torch.empty((V, p.Nt, p.Nd), dtype=torch.float64).pin_memory()
+        omh = torch.empty((V, p.Nt, p.Nm), dtype=torch.float64).pin_memory()
+        mdev = torch.empty((p.Nt, p.Nm), dtype=torch.float64, device=dev)
+        ddev = torch.empty((p.Nt, p.Nd), dtype=torch.float64, device=dev)
+        odev = torch.empty((p.Nt, p.Nd), dtype=torch.float64, device=dev)
+        omdev = torch.empty((p.Nt, p.Nm), dtype=torch.float64, device=dev)
+
+        def e2e_step():
+            for b in range(V):
+                mdev.copy_(mh[b], non_blocking=True)
+                h64.apply_F(mdev, odev)
+                odh[b].copy_(odev, non_blocking=True)
+                ddev.copy_(dh[b], non_blocking=True)
+                h64.apply_FT(ddev, omdev)
+                omh[b].copy_(omdev, non_blocking=True)
+
+        ms_e2e, _ = timed(e2e_step, args.steps, min(args.warmup, 3))
+        vec_bytes = (p.Nt * p.Nm + p.Nt * p.Nd) * 8
+        e2e = {"value": world * bytes_step64 * args.steps / (ms_e2e * 1e-3) / 1e9, "unit": "GB/s",
+               "ms_per_step": ms_e2e / args.steps, "h2d_bytes_per_step": V * vec_bytes,
+               "d2h_bytes_per_step": V * vec_bytes}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms64 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": p.name, "Nm": p.Nm, "Nd": p.Nd, "Nt": p.Nt, "L": p.L, "vectors": V,
+                   "rhs_per_call": 1, "calls_per_step": 2 * V, "tier": "f64 spectral blocks, f64 products",
+                   "l2": f"inputs larger than L2: each call streams the {(p.Nt + 1) * p.Nd * p.Nm * 16 / 1e9:.1f} GB "
+                         "FP64 spectral blocks from HBM",
+                   "parallelism": f"replicas x{world}"},
+        "hbm_frac": value / world / hbm_peak,
+        "roofline": roof64,
+        "f32_tier": {"value": value32, "unit": "GB/s", "ms_per_step": ms32 / args.steps,
+                     "hbm_frac": value32 / world / hbm_peak, "roofline": roof32},
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof64[0].items()},
+    }
+
+    # online m_map + q_map latency on the batched workload (64 observation vectors)
+    if not args.no_online:
+        line["online"] = online_block(args, dev, stream)
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        pairs, dt = cpu_oracle_sample(p, F_host, m_host, d_host)
+        line["cpu_baseline"] = {"value": 2 * pairs * bpc64 / dt / 1e9, "unit": "GB/s", "cores": cores_used(),
+                                "kind": "oracle",
+                                "sample": f"oracle time-domain F m and F^T d on {pairs} full-size sweep vector "
+                                          f"pair(s) in {dt:.1f} s, scaled to the GPU formulation's bytes"}
+    h64.close()
+    h32.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def online_block(args, dev, stream):
+    """Offline build (K, Cholesky) and online latency of m_map + q_map for 64 observations."""
+    import torch
+
+    import paper_2501_14911_gb300 as bti
+    from paper_2501_14911_gb300 import synthetic
+
+    p = synthetic.BATCHED
+    B = p.n_vectors
+    h = bti.Handle(p.Nm, p.Nd, p.Nq, p.Nt, device=dev)
+    h.set_blocks(bti.OP_F, torch.from_numpy(p.blocks_F()).to(dev))
+    h.set_blocks(bti.OP_FQ, torch.from_numpy(p.blocks_Fq()).to(dev))
+    h.set_prior_se_grid(p.gx, p.gy, p.ell, p.sigma_p)
+    h.set_noise(p.sigma2)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.synchronize()
+    e[0].record(stream)
+    h.build_K(p.col_block)
+    e[1].record(stream)
+    h.factor_K()
+    e[2].record(stream)
+    torch.cuda.synchronize()
+    t_build = e[0].elapsed_time(e[1])
+    t_factor = e[1].elapsed_time(e[2])
+    d_obs = torch.from_numpy(p.vectors_d()).to(dev)
+    m_map = torch.empty((B, p.Nt, p.Nm), dtype=torch.float64, device=dev)
+    q_map = torch.empty((B, p.Nt, p.Nq), dtype=torch.float64, device=dev)
+    for _ in range(2):
+        h.infer_map(d_obs, m_map)
+        h.predict_qoi(m_map, q_map)
+    torch.cuda.synchronize()
+    reps = 3
+    e[0].record(stream)
+    for _ in range(reps):
+        h.infer_map(d_obs, m_map)
+        h.predict_qoi(m_map, q_map)
+    e[1].record(stream)
+    torch.cuda.synchronize()
+    lat = e[0].elapsed_time(e[1]) / reps
+    h.close()
+    n = p.Nt * p.Nd
+    return {"workload": p.name, "obs_vectors": B, "K_n": n, "build_K_ms": t_build, "factor_K_ms": t_factor,
+            "factor_tflops_f64": (n ** 3 / 3.0) / (t_factor * 1e-3) / 1e12,
+            "m_map_plus_q_map_ms": lat, "ms_per_obs_vector": lat / B,
+            "accuracy": "FP64 throughout; parity with the oracle to 1e-12 in tests/test_gpu_parity.py"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -151,6 +151,30 @@ bti_status bti_infer_map(bti_handle h, const double* d_obs, double* m_map, int64
  * both double.  Requires FQ. */
 bti_status bti_predict_qoi(bti_handle h, const double* m_map, double* q_map, int64_t B);
 
+/* Kernel classes for bti_profile_read. */
+typedef enum {
+  BTI_K_RFFT = 0,      /* forward zero-padded FFT of input columns (and spectral blocks) */
+  BTI_K_PROD_FWD = 1,  /* per-frequency product hat_F hat_m (reduction over N_m) */
+  BTI_K_REDUCE = 2,    /* fixed-order sum of the forward product's chunk partials */
+  BTI_K_IRFFT = 3,     /* inverse FFT with truncation to N_t steps */
+  BTI_K_PROD_ADJ = 4,  /* per-frequency product hat_F^H hat_d */
+  BTI_K_DENSE = 5,     /* dense FP64 work: K assembly, Cholesky, triangular solves */
+  BTI_K_NCLASS = 6
+} bti_kclass;
+
+/* Measurement hook.  Every kernel launch of the handle is counted per class
+ * (library kernels only; device-to-device copies are not counted).  While
+ * enabled (enable != 0), the library also records a CUDA event pair on its
+ * stream around each launch of the first five classes (up to 4096 pairs
+ * between reads; later launches are counted but not timed).  bti_profile_read
+ * synchronises the stream and writes, per class, the summed device
+ * milliseconds (ms[BTI_K_NCLASS], may be NULL) and the launch count
+ * (launches[BTI_K_NCLASS], may be NULL) since the previous read, then resets
+ * both.  *timed_all (may be NULL) is set to 1 if every counted launch of the
+ * timed classes was timed.  Host pointers. */
+bti_status bti_profile_enable(bti_handle h, int enable);
+bti_status bti_profile_read(bti_handle h, double* ms, int64_t* launches, int* timed_all);
+
 /* Wait for the handle's stream and return any device-side error status. */
 bti_status bti_sync(bti_handle h);
 

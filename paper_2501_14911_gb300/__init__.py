@@ -23,5 +23,6 @@ from ._binding import (  # noqa: F401
     lib,
     lib_path,
     header_symbols,
+    KCLASSES,
 )
 from .autograd import FOp, apply_F_autograd  # noqa: F401

@@ -11,6 +11,8 @@ ROOT = os.path.dirname(PKG)
 HEADER = os.path.join(ROOT, "include", "bti.h")
 
 OP_F, OP_G, OP_FQ = 0, 1, 2
+# kernel classes of bti_profile_read
+KCLASSES = ("rfft", "prod_fwd", "reduce", "irfft", "prod_adj", "dense")
 F64, F32 = 0, 1
 
 STATUS = {
@@ -67,6 +69,9 @@ def lib():
         "bti_infer_map": ([vp, vp, vp, i64, ip], st),
         "bti_predict_qoi": ([vp, vp, vp, i64], st),
         "bti_sync": ([vp], st),
+        "bti_profile_enable": ([vp, ip], st),
+        "bti_profile_read": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
+                              ctypes.POINTER(ctypes.c_int)], st),
         "bti_last_error": ([vp], ctypes.c_char_p),
         "bti_version": ([], ctypes.c_char_p),
     }
@@ -241,6 +246,18 @@ class Handle:
 
     def sync(self):
         self._check(lib().bti_sync(self._h))
+
+    def profile_enable(self, on=True):
+        self._check(lib().bti_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self):
+        """{class: (milliseconds, launches)} since the last read, and whether all were timed."""
+        n = len(KCLASSES)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_int64 * n)()
+        ok = ctypes.c_int()
+        self._check(lib().bti_profile_read(self._h, ms, cnt, ctypes.byref(ok)))
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(KCLASSES)}, bool(ok.value)
 
     @property
     def last_error(self):

@@ -8,8 +8,12 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <utility>
+#include <vector>
 
 using namespace bti;
+
+static constexpr int kProfPairs = 4096;
 
 namespace {
 
@@ -40,6 +44,12 @@ struct bti_ctx {
   size_t ws_bytes = 0;
   double* wsolve = nullptr;  // dense-solve workspace
   size_t wsolve_bytes = 0;
+  // measurement hook (bti_profile_enable / bti_profile_read)
+  bool prof_on = false;
+  std::vector<cudaEvent_t> prof_ev;          // pool of 2 * kProfPairs events
+  std::vector<std::pair<int, int>> prof_rec;  // (class, first event index)
+  int64_t prof_count[BTI_K_NCLASS] = {0};
+  int64_t prof_untimed = 0;
   std::string err;
 };
 
@@ -62,6 +72,38 @@ bti_status cuda_check(bti_ctx* h, cudaError_t e, const char* what) {
 bti_status launched(bti_ctx* h, const char* what) {
   return cuda_check(h, cudaGetLastError(), what);
 }
+
+// Count one launch of class cls; with profiling on, bracket it with an event pair.
+struct ProfScope {
+  bti_ctx* h;
+  int cls;
+  int ev = -1;
+  ProfScope(bti_ctx* hh, int c) : h(hh), cls(c) {
+    h->prof_count[cls] += 1;
+    if (h->prof_on && cls != BTI_K_DENSE) {
+      int used = (int)h->prof_rec.size();
+      if (used < kProfPairs) {
+        ev = 2 * used;
+        cudaEventRecord(h->prof_ev[ev], h->stream);
+      } else {
+        h->prof_untimed += 1;
+      }
+    }
+  }
+  ~ProfScope() {
+    if (ev >= 0) {
+      cudaEventRecord(h->prof_ev[ev + 1], h->stream);
+      h->prof_rec.emplace_back(cls, ev);
+    }
+  }
+};
+#define PROF(h, cls, call) \
+  do {                     \
+    ProfScope ps_(h, cls); \
+    call;                  \
+  } while (0)
+
+void count_dense(bti_ctx* h, int64_t launches) { h->prof_count[BTI_K_DENSE] += launches; }
 
 bti_status dev_alloc(bti_ctx* h, void** p, size_t bytes, const char* what) {
   *p = nullptr;
@@ -105,11 +147,11 @@ bti_status check_handle(bti_ctx* h) {
 bti_status make_spectral(bti_ctx* h, OpStore& o, const double* time_blocks) {
   const int64_t cols = o.R * h->Nm;
   if (o.prec == BTI_P_F64)
-    launch_rfft_cols<double, double, double>(h->plan, (int)h->Nt, time_blocks, cols, 0,
-                                             (double2*)o.hat, 0, cols, 1, h->stream);
+    PROF(h, BTI_K_RFFT, (launch_rfft_cols<double, double, double>(h->plan, (int)h->Nt, time_blocks, cols, 0,
+                                                                   (double2*)o.hat, 0, cols, 1, h->stream)));
   else
-    launch_rfft_cols<double, double, float>(h->plan, (int)h->Nt, time_blocks, cols, 0,
-                                            (float2*)o.hat, 0, cols, 1, h->stream);
+    PROF(h, BTI_K_RFFT, (launch_rfft_cols<double, double, float>(h->plan, (int)h->Nt, time_blocks, cols, 0,
+                                                                  (float2*)o.hat, 0, cols, 1, h->stream)));
   return launched(h, "spectral blocks");
 }
 
@@ -161,15 +203,20 @@ bti_status apply_fwd_t(bti_ctx* h, const OpStore& o, const void* in, void* out, 
   C2<T>* dhat = part + n_part;
   cudaStream_t s = h->stream;
   if (io == BTI_P_F64)
-    launch_rfft_cols<T, double, T>(h->plan, (int)Nt, (const double*)in, Nm, Nt * Nm, mhat, nf * Nm, Nm, B, s);
+    PROF(h, BTI_K_RFFT, (launch_rfft_cols<T, double, T>(h->plan, (int)Nt, (const double*)in, Nm, Nt * Nm, mhat,
+                                                         nf * Nm, Nm, B, s)));
   else
-    launch_rfft_cols<T, float, T>(h->plan, (int)Nt, (const float*)in, Nm, Nt * Nm, mhat, nf * Nm, Nm, B, s);
-  launch_prod_fwd<T, T>((const C2<T>*)o.hat, mhat, part, dhat, nf, R, Nm, B, s);
+    PROF(h, BTI_K_RFFT, (launch_rfft_cols<T, float, T>(h->plan, (int)Nt, (const float*)in, Nm, Nt * Nm, mhat,
+                                                        nf * Nm, Nm, B, s)));
+  PROF(h, BTI_K_PROD_FWD, (launch_prod_fwd<T, T>((const C2<T>*)o.hat, mhat, part, nf, R, Nm, B, s)));
+  PROF(h, BTI_K_REDUCE, (launch_reduce_chunks<T>(part, dhat, nf, R, Nm, B, s)));
   const T scale = (T)(1.0 / (double)h->L);
   if (io == BTI_P_F64)
-    launch_irfft_cols<T, double>(h->plan, (int)Nt, dhat, R, nf * R, (double*)out, Nt * R, R, B, scale, s);
+    PROF(h, BTI_K_IRFFT, (launch_irfft_cols<T, double>(h->plan, (int)Nt, dhat, R, nf * R, (double*)out, Nt * R, R,
+                                                        B, scale, s)));
   else
-    launch_irfft_cols<T, float>(h->plan, (int)Nt, dhat, R, nf * R, (float*)out, Nt * R, R, B, scale, s);
+    PROF(h, BTI_K_IRFFT, (launch_irfft_cols<T, float>(h->plan, (int)Nt, dhat, R, nf * R, (float*)out, Nt * R, R,
+                                                       B, scale, s)));
   return launched(h, "forward Toeplitz product");
 }
 
@@ -185,15 +232,19 @@ bti_status apply_adj_t(bti_ctx* h, const OpStore& o, const void* in, void* out, 
   C2<T>* mhat = dhat + n_dhat;
   cudaStream_t s = h->stream;
   if (io == BTI_P_F64)
-    launch_rfft_cols<T, double, T>(h->plan, (int)Nt, (const double*)in, R, Nt * R, dhat, nf * R, R, B, s);
+    PROF(h, BTI_K_RFFT, (launch_rfft_cols<T, double, T>(h->plan, (int)Nt, (const double*)in, R, Nt * R, dhat,
+                                                         nf * R, R, B, s)));
   else
-    launch_rfft_cols<T, float, T>(h->plan, (int)Nt, (const float*)in, R, Nt * R, dhat, nf * R, R, B, s);
-  launch_prod_adj<T, T>((const C2<T>*)o.hat, dhat, mhat, nf, R, Nm, B, s);
+    PROF(h, BTI_K_RFFT, (launch_rfft_cols<T, float, T>(h->plan, (int)Nt, (const float*)in, R, Nt * R, dhat,
+                                                        nf * R, R, B, s)));
+  PROF(h, BTI_K_PROD_ADJ, (launch_prod_adj<T, T>((const C2<T>*)o.hat, dhat, mhat, nf, R, Nm, B, s)));
   const T scale = (T)(1.0 / (double)h->L);
   if (io == BTI_P_F64)
-    launch_irfft_cols<T, double>(h->plan, (int)Nt, mhat, Nm, nf * Nm, (double*)out, Nt * Nm, Nm, B, scale, s);
+    PROF(h, BTI_K_IRFFT, (launch_irfft_cols<T, double>(h->plan, (int)Nt, mhat, Nm, nf * Nm, (double*)out, Nt * Nm,
+                                                        Nm, B, scale, s)));
   else
-    launch_irfft_cols<T, float>(h->plan, (int)Nt, mhat, Nm, nf * Nm, (float*)out, Nt * Nm, Nm, B, scale, s);
+    PROF(h, BTI_K_IRFFT, (launch_irfft_cols<T, float>(h->plan, (int)Nt, mhat, Nm, nf * Nm, (float*)out, Nt * Nm,
+                                                       Nm, B, scale, s)));
   return launched(h, "adjoint Toeplitz product");
 }
 
@@ -280,7 +331,45 @@ bti_status bti_destroy(bti_handle h) {
   dev_freep(h->wsolve);
   dev_freep(h->plan.tw64);
   dev_freep(h->plan.tw32);
+  for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
   delete h;
+  return BTI_OK;
+}
+
+bti_status bti_profile_enable(bti_handle h, int enable) {
+  bti_status st = check_handle(h);
+  if (st != BTI_OK) return st;
+  if (enable && h->prof_ev.empty()) {
+    h->prof_ev.resize(2 * kProfPairs);
+    for (auto& e : h->prof_ev) {
+      st = cuda_check(h, cudaEventCreate(&e), "profile events");
+      if (st != BTI_OK) return st;
+    }
+  }
+  h->prof_on = enable != 0;
+  return BTI_OK;
+}
+
+bti_status bti_profile_read(bti_handle h, double* ms, int64_t* launches, int* timed_all) {
+  bti_status st = check_handle(h);
+  if (st != BTI_OK) return st;
+  st = cuda_check(h, cudaStreamSynchronize(h->stream), "profile sync");
+  if (st != BTI_OK) return st;
+  double acc[BTI_K_NCLASS] = {0};
+  for (auto& r : h->prof_rec) {
+    float t = 0.f;
+    st = cuda_check(h, cudaEventElapsedTime(&t, h->prof_ev[r.second], h->prof_ev[r.second + 1]), "profile elapsed");
+    if (st != BTI_OK) return st;
+    acc[r.first] += t;
+  }
+  for (int c = 0; c < BTI_K_NCLASS; ++c) {
+    if (ms) ms[c] = acc[c];
+    if (launches) launches[c] = h->prof_count[c];
+    h->prof_count[c] = 0;
+  }
+  if (timed_all) *timed_all = h->prof_untimed == 0;
+  h->prof_untimed = 0;
+  h->prof_rec.clear();
   return BTI_OK;
 }
 
@@ -321,12 +410,13 @@ bti_status bti_set_prior_se_grid(bti_handle h, int gx, int gy, double ell, doubl
   if (st != BTI_OK) { dev_freep(Cx); dev_freep(U); return st; }
   cudaStream_t s = h->stream;
   // C_s = C_x (x) C_y with sigma on each axis, node index ix * gy + iy
-  se_axis_matrix(Cx, gx, ell, sigma, s);
-  se_axis_matrix(Cy, gy, ell, sigma, s);
+  int64_t nl = se_axis_matrix(Cx, gx, ell, sigma, s);
+  nl += se_axis_matrix(Cy, gy, ell, sigma, s);
   // row r of the blocks viewed as X_r [gx][gy]: G_r = C_x X_r C_y
-  gemm_f64(false, rows * gx, gy, gy, 1.0, F.time, gy, 0, Cy, gy, 0, 0.0, U, gy, 0, 1, false, s);
-  gemm_f64(false, gx, gy, gx, 1.0, Cx, gx, 0, U, gy, (int64_t)gx * gy, 0.0, G, gy, (int64_t)gx * gy,
-           rows, false, s);
+  nl += gemm_f64(false, rows * gx, gy, gy, 1.0, F.time, gy, 0, Cy, gy, 0, 0.0, U, gy, 0, 1, false, s);
+  nl += gemm_f64(false, gx, gy, gx, 1.0, Cx, gx, 0, U, gy, (int64_t)gx * gy, 0.0, G, gy, (int64_t)gx * gy,
+                 rows, false, s);
+  count_dense(h, nl);
   st = launched(h, "prior blocks");
   if (st == BTI_OK) {
     OpStore& o = h->op[BTI_OP_G];
@@ -403,10 +493,10 @@ bti_status bti_build_K(bti_handle h, int64_t col_block) {
   // W = F_stack G_stack^T (lower block triangle), by column panels
   for (int64_t c0 = 0; c0 < n; c0 += col_block) {
     int64_t nc = (n - c0) < col_block ? (n - c0) : col_block;
-    gemm_f64(true, n - c0, nc, h->Nm, 1.0, F.time + c0 * h->Nm, h->Nm, 0, G.time + c0 * h->Nm, h->Nm, 0,
-             0.0, h->K + c0 * n + c0, n, 0, 1, true, s);
+    count_dense(h, gemm_f64(true, n - c0, nc, h->Nm, 1.0, F.time + c0 * h->Nm, h->Nm, 0, G.time + c0 * h->Nm,
+                            h->Nm, 0, 0.0, h->K + c0 * n + c0, n, 0, 1, true, s));
   }
-  k_diag_cumsum(h->K, h->Nt, h->Nd, h->sigma2, h->noise_diag, s);
+  count_dense(h, k_diag_cumsum(h->K, h->Nt, h->Nd, h->sigma2, h->noise_diag, s));
   st = launched(h, "build_K");
   if (st != BTI_OK) return st;
   h->K_built = true;
@@ -428,7 +518,7 @@ bti_status bti_factor_K(bti_handle h) {
   st = ensure(h, (void**)&h->wsolve, &h->wsolve_bytes, sizeof(double) * (size_t)n * kCholNB, "solve workspace");
   if (st != BTI_OK) return st;
   cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
-  cholesky_f64(h->K, n, h->Linv, h->wsolve, h->status, h->stream);
+  count_dense(h, cholesky_f64(h->K, n, h->Linv, h->wsolve, h->status, h->stream));
   st = launched(h, "factor_K");
   if (st != BTI_OK) return st;
   int stat = 0;
@@ -476,7 +566,7 @@ bti_status bti_infer_map(bti_handle h, const double* d_obs, double* m_map, int64
   cudaStream_t s = h->stream;
   st = cuda_check(h, cudaMemcpyAsync(x, d_obs, sizeof(double) * B * n, cudaMemcpyDeviceToDevice, s), "copy d_obs");
   if (st != BTI_OK) return st;
-  trsm_lower_f64(h->K, h->Linv, n, x, B, work, h->status, s);
+  count_dense(h, trsm_lower_f64(h->K, h->Linv, n, x, B, work, h->status, s));
   st = launched(h, "triangular solves");
   if (st != BTI_OK) return st;
   for (int it = 0; it < refine_iters; ++it) {
@@ -487,13 +577,14 @@ bti_status bti_infer_map(bti_handle h, const double* d_obs, double* m_map, int64
     st = apply_op(h, BTI_OP_F, false, m_map, r, B, BTI_P_F64, "refine F");
     if (st != BTI_OK) return st;
     // r = d - r - Gamma_n x
-    axpby_f64(r, d_obs, 1.0, -1.0, B * n, s);
+    int64_t nl = axpby_f64(r, d_obs, 1.0, -1.0, B * n, s);
     if (h->noise_diag)
-      noise_residual_f64(r, x, h->noise_diag, n, B, s);
+      nl += noise_residual_f64(r, x, h->noise_diag, n, B, s);
     else
-      axpby_f64(r, x, -h->sigma2, 1.0, B * n, s);
-    trsm_lower_f64(h->K, h->Linv, n, r, B, work, h->status, s);
-    axpby_f64(x, r, 1.0, 1.0, B * n, s);
+      nl += axpby_f64(r, x, -h->sigma2, 1.0, B * n, s);
+    nl += trsm_lower_f64(h->K, h->Linv, n, r, B, work, h->status, s);
+    nl += axpby_f64(x, r, 1.0, 1.0, B * n, s);
+    count_dense(h, nl);
     st = launched(h, "refinement");
     if (st != BTI_OK) return st;
   }

@@ -56,8 +56,12 @@ void launch_irfft_cols(const FftPlan& p, int Nt, const C2<T>* X, int64_t ld, int
 // Spectral block products (spectral.cu).
 // Forward: dhat[b][w][i] = sum_j Fhat[w][i][j] mhat[b][w][j]  (T compute, TS storage)
 template <typename T, typename TS>
-void launch_prod_fwd(const C2<TS>* Fhat, const C2<T>* mhat, C2<T>* partial, C2<T>* dhat,
+void launch_prod_fwd(const C2<TS>* Fhat, const C2<T>* mhat, C2<T>* partial,
                      int64_t nf, int64_t R, int64_t Nm, int64_t B, cudaStream_t s);
+// dhat[b][w][i] = sum over the forward product's chunk partials (fixed order)
+template <typename T>
+void launch_reduce_chunks(const C2<T>* partial, C2<T>* dhat, int64_t nf, int64_t R, int64_t Nm,
+                          int64_t B, cudaStream_t s);
 size_t prod_fwd_partial_elems(int64_t nf, int64_t R, int64_t Nm, int64_t B);
 // Adjoint: mhat[b][w][j] = sum_i conj(Fhat[w][i][j]) dhat[b][w][i]
 template <typename T, typename TS>
@@ -68,22 +72,23 @@ void launch_prod_adj(const C2<TS>* Fhat, const C2<T>* dhat, C2<T>* mhat,
 // C[b] = alpha * A[b] * op(B[b]) + beta * C[b]; A is M x K (lda), op(B) is K x N:
 // TRANSB=false: B stored K x N (ldb); TRANSB=true: B stored N x K (ldb).
 // lower_only: skip output tiles strictly above the diagonal (row tile < col tile).
-void gemm_f64(bool transB, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
-              int64_t lda, int64_t sA, const double* Bm, int64_t ldb, int64_t sB, double beta,
-              double* C, int64_t ldc, int64_t sC, int64_t batch, bool lower_only, cudaStream_t s);
-void se_axis_matrix(double* C, int n, double ell, double scale, cudaStream_t s);
-void k_diag_cumsum(double* WK, int64_t Nt, int64_t R, double sigma2, const double* diag,
-                   cudaStream_t s);
+// Each dense launcher returns the number of kernels it launched.
+int gemm_f64(bool transB, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
+             int64_t lda, int64_t sA, const double* Bm, int64_t ldb, int64_t sB, double beta,
+             double* C, int64_t ldc, int64_t sC, int64_t batch, bool lower_only, cudaStream_t s);
+int se_axis_matrix(double* C, int n, double ell, double scale, cudaStream_t s);
+int k_diag_cumsum(double* WK, int64_t Nt, int64_t R, double sigma2, const double* diag,
+                  cudaStream_t s);
 // Blocked Cholesky, lower, in place; Linv receives the inverses of the diagonal blocks
 // ([nblk][nb][nb]); status receives the first failing 1-based pivot (0 if none).
-void cholesky_f64(double* A, int64_t n, double* Linv, double* work, int* status, cudaStream_t s);
+int64_t cholesky_f64(double* A, int64_t n, double* Linv, double* work, int* status, cudaStream_t s);
 constexpr int kCholNB = 64;
 // X [B][n] rows: X := L^{-1} X (forward) then L^{-T} X (backward), in place.
-void trsm_lower_f64(const double* Lm, const double* Linv, int64_t n, double* X, int64_t B,
-                    double* work, const int* status, cudaStream_t s);
+int64_t trsm_lower_f64(const double* Lm, const double* Linv, int64_t n, double* X, int64_t B,
+                       double* work, const int* status, cudaStream_t s);
 size_t trsm_work_elems(int64_t n, int64_t B);
-void axpby_f64(double* y, const double* x, double a, double b, int64_t n, cudaStream_t s);
-void noise_residual_f64(double* r, const double* x, const double* diag, int64_t n, int64_t B,
-                        cudaStream_t s);
+int axpby_f64(double* y, const double* x, double a, double b, int64_t n, cudaStream_t s);
+int noise_residual_f64(double* r, const double* x, const double* diag, int64_t n, int64_t B,
+                       cudaStream_t s);
 
 }  // namespace bti

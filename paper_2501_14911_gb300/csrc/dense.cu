@@ -168,10 +168,10 @@ gemm_smallm_nt_kernel(int64_t M, int64_t N, int64_t K, double alpha, const doubl
   }
 }
 
-void gemm_f64(bool transB, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
-              int64_t lda, int64_t sA, const double* Bm, int64_t ldb, int64_t sB, double beta,
-              double* C, int64_t ldc, int64_t sC, int64_t batch, bool lower_only, cudaStream_t s) {
-  if (M <= 0 || N <= 0 || batch <= 0) return;
+int gemm_f64(bool transB, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
+             int64_t lda, int64_t sA, const double* Bm, int64_t ldb, int64_t sB, double beta,
+             double* C, int64_t ldc, int64_t sC, int64_t batch, bool lower_only, cudaStream_t s) {
+  if (M <= 0 || N <= 0 || batch <= 0) return 0;
   if (M <= 8 && batch == 1 && !lower_only && K > 0) {
     if (transB) {
       unsigned g = (unsigned)((N + 7) / 8);
@@ -182,7 +182,7 @@ void gemm_f64(bool transB, int64_t M, int64_t N, int64_t K, double alpha, const 
       if (M <= 1) gemm_smallm_nn_kernel<1><<<g, 256, 0, s>>>(M, N, K, alpha, A, lda, Bm, ldb, beta, C, ldc);
       else gemm_smallm_nn_kernel<8><<<g, 256, 0, s>>>(M, N, K, alpha, A, lda, Bm, ldb, beta, C, ldc);
     }
-    return;
+    return 1;
   }
   dim3 grid((unsigned)((M + GBM - 1) / GBM), (unsigned)((N + GBN - 1) / GBN),
             (unsigned)std::min<int64_t>(batch, 65535));
@@ -190,6 +190,7 @@ void gemm_f64(bool transB, int64_t M, int64_t N, int64_t K, double alpha, const 
     gemm_f64_kernel<true><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, sA, Bm, ldb, sB, beta, C, ldc, sC, batch, lower_only);
   else
     gemm_f64_kernel<false><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, sA, Bm, ldb, sB, beta, C, ldc, sC, batch, lower_only);
+  return 1;
 }
 
 // ------------------------------------------------------------------ SE prior, one axis
@@ -202,8 +203,9 @@ __global__ void se_axis_kernel(double* C, int n, double ell, double scale) {
   double r = (double)(a - b);
   C[idx] = scale * exp(-(r * r) / (2.0 * ell * ell));
 }
-void se_axis_matrix(double* C, int n, double ell, double scale, cudaStream_t s) {
+int se_axis_matrix(double* C, int n, double ell, double scale, cudaStream_t s) {
   se_axis_kernel<<<(n * n + 255) / 256, 256, 0, s>>>(C, n, ell, scale);
+  return 1;
 }
 
 // ------------------------------------------------------------------ K from the Gram matrix
@@ -233,10 +235,11 @@ __global__ void k_diag_cumsum_kernel(double* WK, int64_t Nt, int64_t R, double s
     *p = v;
   }
 }
-void k_diag_cumsum(double* WK, int64_t Nt, int64_t R, double sigma2, const double* diag,
-                   cudaStream_t s) {
+int k_diag_cumsum(double* WK, int64_t Nt, int64_t R, double sigma2, const double* diag,
+                  cudaStream_t s) {
   int64_t total = Nt * R * R;
   k_diag_cumsum_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(WK, Nt, R, sigma2, diag);
+  return 1;
 }
 
 // ------------------------------------------------------------------ Cholesky
@@ -295,23 +298,26 @@ potrf_diag_kernel(double* A, int64_t lda, int kb, double* Linv, int* status, int
   }
 }
 
-void cholesky_f64(double* A, int64_t n, double* Linv, double* work, int* status, cudaStream_t s) {
+int64_t cholesky_f64(double* A, int64_t n, double* Linv, double* work, int* status, cudaStream_t s) {
   const int nb = kCholNB;
+  int64_t launches = 0;
   for (int64_t k = 0; k < n; k += nb) {
     int kb = (int)std::min<int64_t>(nb, n - k);
     double* Lk = Linv + (k / nb) * nb * nb;
     potrf_diag_kernel<<<1, 256, 0, s>>>(A + k * n + k, n, kb, Lk, status, k);
+    launches += 1;
     int64_t m = n - k - kb;
     if (m <= 0) continue;
     // panel: P = A[k+kb:, k:k+kb] L_kk^{-T}
-    gemm_f64(true, m, kb, kb, 1.0, A + (k + kb) * n + k, n, 0, Lk, nb, 0, 0.0, work, kb, 0, 1,
+    launches += gemm_f64(true, m, kb, kb, 1.0, A + (k + kb) * n + k, n, 0, Lk, nb, 0, 0.0, work, kb, 0, 1,
              false, s);
     cudaMemcpy2DAsync(A + (k + kb) * n + k, n * sizeof(double), work, kb * sizeof(double),
                       kb * sizeof(double), m, cudaMemcpyDeviceToDevice, s);
     // trailing update of the lower triangle: A22 -= P P^T
-    gemm_f64(true, m, m, kb, -1.0, work, kb, 0, work, kb, 0, 1.0, A + (k + kb) * n + (k + kb), n,
-             0, 1, true, s);
+    launches += gemm_f64(true, m, m, kb, -1.0, work, kb, 0, work, kb, 0, 1.0, A + (k + kb) * n + (k + kb),
+                         n, 0, 1, true, s);
   }
+  return launches;
 }
 
 // ------------------------------------------------------------------ triangular solves
@@ -320,20 +326,21 @@ size_t trsm_work_elems(int64_t n, int64_t B) { return (size_t)B * kCholNB; }
 // Right-hand sides are the rows of X ([B][n]).  Forward: L Y = X, then
 // backward: L^T Z = Y; both blocked by the factor's diagonal blocks, whose
 // inverses Linv come from the factorisation.
-void trsm_lower_f64(const double* Lm, const double* Linv, int64_t n, double* X, int64_t B,
-                    double* work, const int* status, cudaStream_t s) {
+int64_t trsm_lower_f64(const double* Lm, const double* Linv, int64_t n, double* X, int64_t B,
+                       double* work, const int* status, cudaStream_t s) {
   (void)status;
   const int nb = kCholNB;
+  int64_t launches = 0;
   for (int64_t k = 0; k < n; k += nb) {
     int kb = (int)std::min<int64_t>(nb, n - k);
     const double* Lk = Linv + (k / nb) * nb * nb;
     // Y_k = X_k L_kk^{-T}
-    gemm_f64(true, B, kb, kb, 1.0, X + k, n, 0, Lk, nb, 0, 0.0, work, kb, 0, 1, false, s);
+    launches += gemm_f64(true, B, kb, kb, 1.0, X + k, n, 0, Lk, nb, 0, 0.0, work, kb, 0, 1, false, s);
     cudaMemcpy2DAsync(X + k, n * sizeof(double), work, kb * sizeof(double), kb * sizeof(double), B,
                       cudaMemcpyDeviceToDevice, s);
     int64_t m = n - k - kb;
     if (m > 0)  // X[:, k+kb:] -= Y_k L[k+kb:, k:k+kb]^T
-      gemm_f64(true, B, m, kb, -1.0, X + k, n, 0, Lm + (k + kb) * n + k, n, 0, 1.0, X + k + kb, n,
+      launches += gemm_f64(true, B, m, kb, -1.0, X + k, n, 0, Lm + (k + kb) * n + k, n, 0, 1.0, X + k + kb, n,
                0, 1, false, s);
   }
   int64_t last = ((n - 1) / nb) * nb;
@@ -341,20 +348,23 @@ void trsm_lower_f64(const double* Lm, const double* Linv, int64_t n, double* X, 
     int kb = (int)std::min<int64_t>(nb, n - k);
     const double* Lk = Linv + (k / nb) * nb * nb;
     // Z_k = X_k L_kk^{-1}
-    gemm_f64(false, B, kb, kb, 1.0, X + k, n, 0, Lk, nb, 0, 0.0, work, kb, 0, 1, false, s);
+    launches += gemm_f64(false, B, kb, kb, 1.0, X + k, n, 0, Lk, nb, 0, 0.0, work, kb, 0, 1, false, s);
     cudaMemcpy2DAsync(X + k, n * sizeof(double), work, kb * sizeof(double), kb * sizeof(double), B,
                       cudaMemcpyDeviceToDevice, s);
     if (k > 0)  // X[:, 0:k] -= Z_k L[k:k+kb, 0:k]
-      gemm_f64(false, B, k, kb, -1.0, X + k, n, 0, Lm + k * n, n, 0, 1.0, X, n, 0, 1, false, s);
+      launches += gemm_f64(false, B, k, kb, -1.0, X + k, n, 0, Lm + k * n, n, 0, 1.0, X, n, 0, 1, false, s);
   }
+  return launches;
 }
 
 __global__ void axpby_kernel(double* y, const double* x, double a, double b, int64_t n) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] = fma(a, x[i], b * y[i]);
 }
-void axpby_f64(double* y, const double* x, double a, double b, int64_t n, cudaStream_t s) {
-  if (n > 0) axpby_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(y, x, a, b, n);
+int axpby_f64(double* y, const double* x, double a, double b, int64_t n, cudaStream_t s) {
+  if (n <= 0) return 0;
+  axpby_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(y, x, a, b, n);
+  return 1;
 }
 
 // r[b][i] -= diag[i] x[b][i] for B rows of length n (diagonal noise term of K x)
@@ -363,11 +373,12 @@ __global__ void noise_residual_kernel(double* r, const double* x, const double* 
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < total) r[i] = fma(-diag[i % n], x[i], r[i]);
 }
-void noise_residual_f64(double* r, const double* x, const double* diag, int64_t n, int64_t B,
-                        cudaStream_t s) {
+int noise_residual_f64(double* r, const double* x, const double* diag, int64_t n, int64_t B,
+                       cudaStream_t s) {
   int64_t total = n * B;
-  if (total > 0)
-    noise_residual_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(r, x, diag, n, total);
+  if (total <= 0) return 0;
+  noise_residual_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(r, x, diag, n, total);
+  return 1;
 }
 
 }  // namespace bti

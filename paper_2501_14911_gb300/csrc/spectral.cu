@@ -102,21 +102,35 @@ size_t prod_fwd_partial_elems(int64_t nf, int64_t R, int64_t Nm, int64_t B) {
   return (size_t)(B * nf * nchunk * R);
 }
 
-template <typename T, typename TS>
-void launch_prod_fwd(const C2<TS>* Fhat, const C2<T>* mhat, C2<T>* partial, C2<T>* dhat,
-                     int64_t nf, int64_t R, int64_t Nm, int64_t B, cudaStream_t s) {
+template <typename T>
+static int fwd_nchunk(int64_t Nm, int64_t B, int* jc_out) {
   int bg = fwd_bg<T>(B);
   int JC = fwd_jc<T>(bg);
   if (Nm < JC) JC = (int)(((Nm + 31) / 32) * 32);
-  int nchunk = (int)((Nm + JC - 1) / JC);
+  if (jc_out) *jc_out = JC;
+  return (int)((Nm + JC - 1) / JC);
+}
+
+template <typename T>
+void launch_reduce_chunks(const C2<T>* partial, C2<T>* dhat, int64_t nf, int64_t R, int64_t Nm,
+                          int64_t B, cudaStream_t s) {
+  int nchunk = fwd_nchunk<T>(Nm, B, nullptr);
+  int64_t total = B * nf * R;
+  reduce_chunks_kernel<T><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(partial, dhat, total, R, nchunk);
+}
+
+template <typename T, typename TS>
+void launch_prod_fwd(const C2<TS>* Fhat, const C2<T>* mhat, C2<T>* partial,
+                     int64_t nf, int64_t R, int64_t Nm, int64_t B, cudaStream_t s) {
+  int bg = fwd_bg<T>(B);
+  int JC = 0;
+  int nchunk = fwd_nchunk<T>(Nm, B, &JC);
   size_t smem = sizeof(C2<T>) * (size_t)bg * JC;
   dim3 grid((unsigned)nchunk, (unsigned)nf, (unsigned)((B + bg - 1) / bg));
   if (bg == 4)
     prod_fwd_kernel<T, TS, 4><<<grid, 256, smem, s>>>(Fhat, mhat, partial, nf, R, Nm, B, JC, nchunk);
   else
     prod_fwd_kernel<T, TS, 1><<<grid, 256, smem, s>>>(Fhat, mhat, partial, nf, R, Nm, B, JC, nchunk);
-  int64_t total = B * nf * R;
-  reduce_chunks_kernel<T><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(partial, dhat, total, R, nchunk);
 }
 
 // grid (ceil(Nm / (256 VPT)), nf, ceil(B / BG)); thread owns j = j0 + tid + 256 v
@@ -190,10 +204,14 @@ void launch_prod_adj(const C2<TS>* Fhat, const C2<T>* dhat, C2<T>* mhat,
   }
 }
 
-template void launch_prod_fwd<double, double>(const double2*, const double2*, double2*, double2*,
+template void launch_prod_fwd<double, double>(const double2*, const double2*, double2*,
                                               int64_t, int64_t, int64_t, int64_t, cudaStream_t);
-template void launch_prod_fwd<float, float>(const float2*, const float2*, float2*, float2*,
+template void launch_prod_fwd<float, float>(const float2*, const float2*, float2*,
                                             int64_t, int64_t, int64_t, int64_t, cudaStream_t);
+template void launch_reduce_chunks<double>(const double2*, double2*, int64_t, int64_t, int64_t, int64_t,
+                                           cudaStream_t);
+template void launch_reduce_chunks<float>(const float2*, float2*, int64_t, int64_t, int64_t, int64_t,
+                                          cudaStream_t);
 template void launch_prod_adj<double, double>(const double2*, const double2*, double2*,
                                               int64_t, int64_t, int64_t, int64_t, cudaStream_t);
 template void launch_prod_adj<float, float>(const float2*, const float2*, float2*,
