@@ -181,6 +181,33 @@ bti_status bti_sync(bti_handle h);
 /* Message for the last non-OK status on this handle ("" if none). */
 const char* bti_last_error(bti_handle h);
 
+/* Size of the device scratch array used by bti_apply_F_noalloc (64 MiB). */
+#define BTI_NOALLOC_SCRATCH_BYTES (64ull << 20)
+
+/* d = F m (FP64) without allocating any device memory.  The paper has no
+ * counterpart: this entry point exists for callers that may not call
+ * cudaMalloc / cudaFree -- code whose device memory belongs to another
+ * allocator (a framework's pool or a budget fixed at start-up), and online
+ * callers with latency deadlines, for which cudaFree's device-wide
+ * synchronisation and cudaMalloc's unbounded cost are unacceptable.
+ *
+ * No handle: blocks (device, FP64, [N_t][N_d][N_m], block k = F_k), m (device,
+ * FP64, [B][N_t][N_m]) and d (device, FP64, [B][N_t][N_d]) are the caller's;
+ * the work is queued on cuda_stream (a cudaStream_t, or NULL).  The spectral
+ * blocks are recomputed on every call.  All intermediates live in one static
+ * device array of BTI_NOALLOC_SCRATCH_BYTES that the library holds on every
+ * GPU where it is loaded until the process exits; a problem needing more
+ * (about 16 (N_t+1) N_m (N_d + B) bytes plus small terms) returns
+ * BTI_ERR_SHAPE before anything is launched.  The first call on a device
+ * resolves that array's device address (cudaGetSymbolAddress, with the device
+ * current); make that first call before any stream capture.  Every call on a
+ * device shares the array, so calls that overlap on the GPU (other streams or
+ * host threads) race and must be serialised by the caller.  Returns BTI_ERR_ARG
+ * for null pointers, sizes <= 0 or an unsupported L = 2 N_t, BTI_ERR_CUDA if a
+ * launch fails. */
+bti_status bti_apply_F_noalloc(const double* blocks, const double* m, double* d, int64_t Nm,
+                               int64_t Nd, int64_t Nt, int64_t B, void* cuda_stream);
+
 /* Library version string. */
 const char* bti_version(void);
 

@@ -74,6 +74,7 @@ def lib():
                               ctypes.POINTER(ctypes.c_int)], st),
         "bti_last_error": ([vp], ctypes.c_char_p),
         "bti_version": ([], ctypes.c_char_p),
+        "bti_apply_F_noalloc": ([vp, vp, vp, i64, i64, i64, i64, vp], st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)

@@ -42,6 +42,8 @@ struct FftPlan {
 };
 
 bool fft_plan_make(FftPlan& p, int L);   // host: factor L, choose P; false if unsupported
+// The same factorisation without the twiddle tables (tw64 / tw32 left null for the caller to set).
+bool fft_plan_factor(FftPlan& p, int L);
 
 // Kernel launchers (fft.cu).  All act on "columns": element (t, c) of a real
 // column array sits at x[t * ld + c]; a spectrum element (w, c) at X[w * ld + c].

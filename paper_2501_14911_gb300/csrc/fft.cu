@@ -63,6 +63,30 @@ bool fft_plan_make(FftPlan& p, int L) {
   return true;
 }
 
+bool fft_plan_factor(FftPlan& p, int L) {
+  if (L < 2 || L > kMaxL) return false;
+  int n = L, np = 0;
+  const int order[6] = {8, 4, 2, 7, 5, 3};
+  for (int oi = 0; oi < 6; ++oi) {
+    int r = order[oi];
+    while (n % r == 0) {
+      if (np >= kMaxPasses) return false;
+      p.radix[np++] = r;
+      n /= r;
+    }
+  }
+  if (n != 1) return false;
+  p.L = L;
+  p.npass = np;
+  int P = 4096 / L;
+  if (P > 16) P = 16;
+  if (P < 1) P = 1;
+  p.P = P;
+  p.tw64 = nullptr;
+  p.tw32 = nullptr;
+  return true;
+}
+
 template <typename T> __device__ __forceinline__ const C2<T>* twtab(const double2* t64, const float2* t32);
 template <> __device__ __forceinline__ const double2* twtab<double>(const double2* t64, const float2*) { return t64; }
 template <> __device__ __forceinline__ const float2* twtab<float>(const double2*, const float2* t32) { return t32; }
