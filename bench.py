@@ -83,6 +83,8 @@ def load_peaks():
 # FP64 FFMA-pipe rate of this GB300 (TFLOP/s), from a DFMA throughput probe:
 # 2 DFMA per clock per SM x 152 SMs at the sustained clock.
 FP64_TFLOPS = 1.2
+# FP32 FFMA rate (TFLOP/s) from the same probe: 128 lanes/clk/SM x 152 SMs x 2 flop.
+FP32_TFLOPS = 75.0
 
 
 class Clocks:
@@ -255,16 +257,10 @@ def run_ours(args):
     m_host = p.vectors_m()
     d_host = p.vectors_d()
 
-    # FP64 tier (headline) and FP32 tier handles; spectral blocks built on the device
-    h64 = bti.Handle(p.Nm, p.Nd, 0, p.Nt, device=dev)
-    h32 = bti.Handle(p.Nm, p.Nd, 0, p.Nt, device=dev)
+    # One handle per tier, built and timed in turn (the device keeps one set of spectral
+    # blocks at a time).  Headline: the double-FP32 tier (FP64-accurate products on the
+    # FP32 pipes, FP64 FFTs and vectors); the native FP64 and the FP32 tiers follow.
     Fd = torch.from_numpy(F_host).to(dev)
-    h64.set_blocks(bti.OP_F, Fd, bti.F64)
-    h32.set_blocks(bti.OP_F, Fd, bti.F32)
-    torch.cuda.synchronize()
-    del Fd
-    torch.cuda.empty_cache()
-
     m64 = torch.from_numpy(m_host).to(dev)
     d64 = torch.from_numpy(d_host).to(dev)
     m32, d32 = m64.float(), d64.float()
@@ -309,95 +305,97 @@ def run_ours(args):
             ms = float(t.item())
         return ms, prof
 
-    uuid = str(torch.cuda.get_device_properties(dev).uuid) if hasattr(torch.cuda.get_device_properties(dev), "uuid") else ""
-    clocks = Clocks(uuid)
-    clocks.start()
-    ms64, prof64 = timed(lambda: step(h64, m64, d64, od64, om64), args.steps, args.warmup, h64)
-    clk = clocks.stop()
-    ms32, prof32 = timed(lambda: step(h32, m32, d32, od32, om32), args.steps, args.warmup, h32)
-
-    bpc64 = bytes_per_call(p, 8, 16)
-    bpc32 = bytes_per_call(p, 4, 8)
-    bytes_step64 = 2 * V * bpc64
-    bytes_step32 = 2 * V * bpc32
-    value = world * bytes_step64 * args.steps / (ms64 * 1e-3) / 1e9
-    value32 = world * bytes_step32 * args.steps / (ms32 * 1e-3) / 1e9
+    props = torch.cuda.get_device_properties(dev)
+    uuid = str(getattr(props, "uuid", ""))
 
     # dominant kernel: the per-frequency spectral products (forward and adjoint)
-    def roofline(prof, csize, fp_peak_tflops, kind):
+    def roofline(prof, csize, kind):
         (pf_ms, pf_n), (pa_ms, pa_n) = prof[0]["prod_fwd"], prof[0]["prod_adj"]
         nf = p.Nt + 1
         Fhat = nf * p.Nd * p.Nm * csize
-        mhat = nf * p.Nm * csize
-        bytes_launch = Fhat + mhat  # spectral blocks + the frequency-domain vector (read or written)
-        flops_launch = 8.0 * nf * p.Nd * p.Nm
+        mhat = nf * p.Nm * 16  # the frequency-domain vector (FP64 for f64/df64, read or written)
+        if kind == "f32":
+            mhat = nf * p.Nm * 8
+        bytes_launch = Fhat + mhat
+        elems = nf * p.Nd * p.Nm
         avg_ms = (pf_ms + pa_ms) / max(pf_n + pa_n, 1)
         gbs = bytes_launch / (avg_ms * 1e-3) / 1e9
-        tflops = flops_launch / (avg_ms * 1e-3) / 1e12
         t_hbm = bytes_launch / (hbm_peak * 1e9)
-        t_alu = flops_launch / (fp_peak_tflops * 1e12)
+        # arithmetic: f64 = 8 DP flop per element on the FP64 pipe; f32 = 4 FFMA; df64 = 48 FP32
+        # instructions per element (4 float-pair multiply-accumulates of 12 operations)
+        if kind == "f64":
+            work, peak, unit, src = 8.0 * elems, FP64_TFLOPS * 1e12, "TFLOP/s", \
+                "FP64 DFMA throughput probe (2 DFMA/clk/SM x 152 SMs)"
+        elif kind == "f32":
+            work, peak, unit, src = 8.0 * elems, FP32_TFLOPS * 1e12, "TFLOP/s", \
+                "FP32 FFMA: 128 lanes/clk/SM x 152 SMs x 2 flop at ~1.93 GHz (probe: 75 TFLOP/s)"
+        else:
+            work, peak, unit, src = 48.0 * elems, FP32_TFLOPS / 2 * 1e12, "Tinstr/s", \
+                "FP32 pipe issue: 128 lanes/clk/SM x 152 SMs at ~1.93 GHz (probe)"
+        t_alu = work / peak
         traffic = ncu_traffic(f"{kind}_bytes_per_launch")
         share_total = sum(v[0] for v in prof[0].values())
-        common = {"kernel": f"prod_fwd_kernel + prod_adj_kernel ({kind})", "avg_launch_ms": avg_ms,
+        common = {"kernel": f"prod_fwd + prod_adj ({kind})", "avg_launch_ms": avg_ms,
                   "launches": pf_n + pa_n, "share_of_step_kernel_time": (pf_ms + pa_ms) / max(share_total, 1e-9),
                   "traffic": traffic, "algorithmic_bytes_per_launch": bytes_launch,
                   "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak}
         if t_alu > t_hbm:
-            return dict({"bound": "alu", "achieved": tflops, "peak": fp_peak_tflops, "unit": "TFLOP/s",
-                         "frac": tflops / fp_peak_tflops,
-                         "peak_source": "FP64 DFMA throughput probe (2 DFMA/clk/SM x 152 SMs)"}, **common)
+            ach = work / (avg_ms * 1e-3) / 1e12
+            return dict({"bound": "alu", "achieved": ach, "peak": peak / 1e12, "unit": unit,
+                         "frac": ach * 1e12 / peak, "peak_source": src}, **common)
         return dict({"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                       "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})"}, **common)
 
-    roof64 = roofline(prof64, 16, FP64_TFLOPS, "f64")
-    roof32 = roofline(prof32, 8, 75.0, "f32")
-    launches = sum(v[1] for v in prof64[0].values())
-
-    # end to end through the public API with pinned host buffers
+    tiers = {"df64": (bti.DF64, 16, 8), "f64": (bti.F64, 16, 8), "f32": (bti.F32, 8, 4)}
+    res = {}
+    clk = None
     e2e = None
-    if not args.no_e2e:
-        mh = torch.from_numpy(m_host).pin_memory()
-        dh = torch.from_numpy(d_host).pin_memory()
-        odh = torch.empty((V, p.Nt, p.Nd), dtype=torch.float64).pin_memory()
-        omh = torch.empty((V, p.Nt, p.Nm), dtype=torch.float64).pin_memory()
-        mdev = torch.empty((p.Nt, p.Nm), dtype=torch.float64, device=dev)
-        ddev = torch.empty((p.Nt, p.Nd), dtype=torch.float64, device=dev)
-        odev = torch.empty((p.Nt, p.Nd), dtype=torch.float64, device=dev)
-        omdev = torch.empty((p.Nt, p.Nm), dtype=torch.float64, device=dev)
+    for name, (prec, csize, esize) in tiers.items():
+        h = bti.Handle(p.Nm, p.Nd, 0, p.Nt, device=dev)
+        h.set_blocks(bti.OP_F, Fd, prec)
+        torch.cuda.synchronize()
+        vecs = (m32, d32, od32, om32) if name == "f32" else (m64, d64, od64, om64)
+        headline = name == "df64"
+        if headline:
+            clocks = Clocks(uuid)
+            clocks.start()
+        ms, prof = timed(lambda: step(h, *vecs), args.steps, args.warmup, h)
+        if headline:
+            clk = clocks.stop()
+        bytes_step = 2 * V * bytes_per_call(p, esize, csize)
+        res[name] = {"ms": ms, "prof": prof, "bytes_step": bytes_step,
+                     "value": world * bytes_step * args.steps / (ms * 1e-3) / 1e9,
+                     "roofline": roofline(prof, csize, name)}
+        if headline and not args.no_e2e:
+            e2e = e2e_block(args, h, p, m_host, d_host, dev, timed, world, bytes_step)
+        h.close()
+    del Fd
+    torch.cuda.empty_cache()
 
-        def e2e_step():
-            for b in range(V):
-                mdev.copy_(mh[b], non_blocking=True)
-                h64.apply_F(mdev, odev)
-                odh[b].copy_(odev, non_blocking=True)
-                ddev.copy_(dh[b], non_blocking=True)
-                h64.apply_FT(ddev, omdev)
-                omh[b].copy_(omdev, non_blocking=True)
-
-        ms_e2e, _ = timed(e2e_step, args.steps, min(args.warmup, 3))
-        vec_bytes = (p.Nt * p.Nm + p.Nt * p.Nd) * 8
-        e2e = {"value": world * bytes_step64 * args.steps / (ms_e2e * 1e-3) / 1e9, "unit": "GB/s",
-               "ms_per_step": ms_e2e / args.steps, "h2d_bytes_per_step": V * vec_bytes,
-               "d2h_bytes_per_step": V * vec_bytes}
-
+    head = res["df64"]
+    launches = sum(v[1] for v in head["prof"][0].values())
     line = {
-        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms64 / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "metric": METRIC, "value": head["value"], "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "df64", "data": "synthetic",
         "config": {"workload": p.name, "Nm": p.Nm, "Nd": p.Nd, "Nt": p.Nt, "L": p.L, "vectors": V,
-                   "rhs_per_call": 1, "calls_per_step": 2 * V, "tier": "f64 spectral blocks, f64 products",
+                   "rhs_per_call": 1, "calls_per_step": 2 * V,
+                   "tier": "double-FP32: spectral blocks as FP32 hi+lo pairs (16 B/complex), products in "
+                           "float-pair arithmetic on the FP32 pipes; FFTs and vectors FP64; 1e-12 vs the FP64 oracle",
                    "l2": f"inputs larger than L2: each call streams the {(p.Nt + 1) * p.Nd * p.Nm * 16 / 1e9:.1f} GB "
-                         "FP64 spectral blocks from HBM",
+                         "spectral blocks from HBM",
                    "parallelism": f"replicas x{world}"},
-        "hbm_frac": value / world / hbm_peak,
-        "roofline": roof64,
-        "f32_tier": {"value": value32, "unit": "GB/s", "ms_per_step": ms32 / args.steps,
-                     "hbm_frac": value32 / world / hbm_peak, "roofline": roof32},
+        "hbm_frac": head["value"] / world / hbm_peak,
+        "roofline": head["roofline"],
+        "tiers": {k: {"value": v["value"], "unit": "GB/s", "ms_per_step": v["ms"] / args.steps,
+                      "hbm_frac": v["value"] / world / hbm_peak, "roofline": v["roofline"]}
+                  for k, v in res.items() if k != "df64"},
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk,
-        "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof64[0].items()},
+        "kernel_ms_per_step": {k: v[0] / args.steps for k, v in head["prof"][0].items()},
     }
+    bpc64 = bytes_per_call(p, 8, 16)
 
     # online m_map + q_map latency on the batched workload (64 observation vectors)
     if not args.no_online:
@@ -409,13 +407,42 @@ def run_ours(args):
                                 "kind": "oracle",
                                 "sample": f"oracle time-domain F m and F^T d on {pairs} full-size sweep vector "
                                           f"pair(s) in {dt:.1f} s, scaled to the GPU formulation's bytes"}
-    h64.close()
-    h32.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def e2e_block(args, h, p, m_host, d_host, dev, timed, world, bytes_step):
+    """The headline step through the public API with pinned host buffers: every call's input
+    is copied host->device and its output device->host inside the timed region."""
+    import torch
+
+    V = p.n_vectors
+    mh = torch.from_numpy(m_host).pin_memory()
+    dh = torch.from_numpy(d_host).pin_memory()
+    odh = torch.empty((V, p.Nt, p.Nd), dtype=torch.float64).pin_memory()
+    omh = torch.empty((V, p.Nt, p.Nm), dtype=torch.float64).pin_memory()
+    mdev = torch.empty((p.Nt, p.Nm), dtype=torch.float64, device=dev)
+    ddev = torch.empty((p.Nt, p.Nd), dtype=torch.float64, device=dev)
+    odev = torch.empty((p.Nt, p.Nd), dtype=torch.float64, device=dev)
+    omdev = torch.empty((p.Nt, p.Nm), dtype=torch.float64, device=dev)
+
+    def e2e_step():
+        for b in range(V):
+            mdev.copy_(mh[b], non_blocking=True)
+            h.apply_F(mdev, odev)
+            odh[b].copy_(odev, non_blocking=True)
+            ddev.copy_(dh[b], non_blocking=True)
+            h.apply_FT(ddev, omdev)
+            omh[b].copy_(omdev, non_blocking=True)
+
+    ms, _ = timed(e2e_step, args.steps, min(args.warmup, 3))
+    vec_bytes = (p.Nt * p.Nm + p.Nt * p.Nd) * 8
+    return {"value": world * bytes_step * args.steps / (ms * 1e-3) / 1e9, "unit": "GB/s",
+            "ms_per_step": ms / args.steps, "h2d_bytes_per_step": V * vec_bytes,
+            "d2h_bytes_per_step": V * vec_bytes}
 
 
 def online_block(args, dev, stream):
@@ -428,9 +455,9 @@ def online_block(args, dev, stream):
     p = synthetic.BATCHED
     B = p.n_vectors
     h = bti.Handle(p.Nm, p.Nd, p.Nq, p.Nt, device=dev)
-    h.set_blocks(bti.OP_F, torch.from_numpy(p.blocks_F()).to(dev))
-    h.set_blocks(bti.OP_FQ, torch.from_numpy(p.blocks_Fq()).to(dev))
-    h.set_prior_se_grid(p.gx, p.gy, p.ell, p.sigma_p)
+    h.set_blocks(bti.OP_F, torch.from_numpy(p.blocks_F()).to(dev), bti.DF64)
+    h.set_blocks(bti.OP_FQ, torch.from_numpy(p.blocks_Fq()).to(dev), bti.DF64)
+    h.set_prior_se_grid(p.gx, p.gy, p.ell, p.sigma_p, bti.DF64)
     h.set_noise(p.sigma2)
     e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     torch.cuda.synchronize()
@@ -462,7 +489,8 @@ def online_block(args, dev, stream):
     return {"workload": p.name, "obs_vectors": B, "K_n": n, "build_K_ms": t_build, "factor_K_ms": t_factor,
             "factor_tflops_f64": (n ** 3 / 3.0) / (t_factor * 1e-3) / 1e12,
             "m_map_plus_q_map_ms": lat, "ms_per_obs_vector": lat / B,
-            "accuracy": "FP64 throughout; parity with the oracle to 1e-12 in tests/test_gpu_parity.py"}
+            "accuracy": "K, Cholesky and solves FP64; G* and F_q products double-FP32; parity with the "
+                        "oracle to 1e-12 in tests/test_gpu_parity.py"}
 
 
 def main():

@@ -60,10 +60,16 @@ typedef enum {
  * BTI_OP_FQ: p2q map F_q, blocks (N_q x N_m), Eq. (2.15)-(2.16). */
 typedef enum { BTI_OP_F = 0, BTI_OP_G = 1, BTI_OP_FQ = 2 } bti_op;
 
-/* Storage / arithmetic tier of the spectral blocks and vector precision.
- * BTI_P_F64: spectral blocks complex FP64, FFTs and products FP64.
- * BTI_P_F32: spectral blocks complex FP32, FFTs and products FP32. */
-typedef enum { BTI_P_F64 = 0, BTI_P_F32 = 1 } bti_prec;
+/* Storage / arithmetic tier of the spectral blocks, and (F64, F32 only) vector precision.
+ * BTI_P_F64 : spectral blocks complex FP64, FFTs and products FP64.
+ * BTI_P_F32 : spectral blocks complex FP32, FFTs and products FP32.
+ * BTI_P_DF64: spectral blocks as pairs of FP32 (hi + lo, about 48 significant
+ *             bits; 16 bytes per complex like FP64), products in double-FP32
+ *             arithmetic on the FP32 pipes with error-free accumulation; FFTs
+ *             and vectors FP64.  FP64-level accuracy (well inside 1e-12) at
+ *             the HBM rate, where GB300's FP64 pipe would bind first.
+ *             Valid as a storage tier only, not as an io type. */
+typedef enum { BTI_P_F64 = 0, BTI_P_F32 = 1, BTI_P_DF64 = 2 } bti_prec;
 
 /* Create a handle for N_m spatial parameters, N_d sensors, N_q QoI points and
  * N_t time steps on CUDA device `device`, issuing work on `cuda_stream`

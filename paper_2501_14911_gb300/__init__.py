@@ -20,6 +20,7 @@ from ._binding import (  # noqa: F401
     OP_FQ,
     F64,
     F32,
+    DF64,
     lib,
     lib_path,
     header_symbols,

@@ -13,7 +13,7 @@ HEADER = os.path.join(ROOT, "include", "bti.h")
 OP_F, OP_G, OP_FQ = 0, 1, 2
 # kernel classes of bti_profile_read
 KCLASSES = ("rfft", "prod_fwd", "reduce", "irfft", "prod_adj", "dense")
-F64, F32 = 0, 1
+F64, F32, DF64 = 0, 1, 2
 
 STATUS = {
     0: "BTI_OK", 1: "BTI_ERR_ARG", 2: "BTI_ERR_SHAPE", 3: "BTI_ERR_STATE", 4: "BTI_ERR_CUDA",

@@ -131,9 +131,9 @@ bti_status ensure(bti_ctx* h, void** buf, size_t* have, size_t need, const char*
   return st;
 }
 
-size_t elem_size(bti_prec p) { return p == BTI_P_F64 ? sizeof(double) : sizeof(float); }
-size_t celem_size(bti_prec p) { return 2 * elem_size(p); }
-bool prec_ok(int p) { return p == BTI_P_F64 || p == BTI_P_F32; }
+size_t celem_size(bti_prec p) { return p == BTI_P_F32 ? 2 * sizeof(float) : 16; }
+bool prec_ok(int p) { return p == BTI_P_F64 || p == BTI_P_F32 || p == BTI_P_DF64; }
+bool io_ok(int p) { return p == BTI_P_F64 || p == BTI_P_F32; }
 
 int64_t rows_of(bti_ctx* h, bti_op op) { return op == BTI_OP_FQ ? h->Nq : h->Nd; }
 
@@ -146,12 +146,14 @@ bti_status check_handle(bti_ctx* h) {
 // spectral blocks of an op from FP64 time-domain blocks [Nt][R][Nm] (device)
 bti_status make_spectral(bti_ctx* h, OpStore& o, const double* time_blocks) {
   const int64_t cols = o.R * h->Nm;
-  if (o.prec == BTI_P_F64)
+  if (o.prec != BTI_P_F32)
     PROF(h, BTI_K_RFFT, (launch_rfft_cols<double, double, double>(h->plan, (int)h->Nt, time_blocks, cols, 0,
                                                                    (double2*)o.hat, 0, cols, 1, h->stream)));
   else
     PROF(h, BTI_K_RFFT, (launch_rfft_cols<double, double, float>(h->plan, (int)h->Nt, time_blocks, cols, 0,
                                                                   (float2*)o.hat, 0, cols, 1, h->stream)));
+  if (o.prec == BTI_P_DF64)  // each FP64 complex becomes a (hi, lo) float pair per part, in place
+    PROF(h, BTI_K_RFFT, launch_split_df64(o.hat, h->nf * cols, h->stream));
   return launched(h, "spectral blocks");
 }
 
@@ -208,7 +210,11 @@ bti_status apply_fwd_t(bti_ctx* h, const OpStore& o, const void* in, void* out, 
   else
     PROF(h, BTI_K_RFFT, (launch_rfft_cols<T, float, T>(h->plan, (int)Nt, (const float*)in, Nm, Nt * Nm, mhat,
                                                         nf * Nm, Nm, B, s)));
-  PROF(h, BTI_K_PROD_FWD, (launch_prod_fwd<T, T>((const C2<T>*)o.hat, mhat, part, nf, R, Nm, B, s)));
+  if (o.prec == BTI_P_DF64)
+    PROF(h, BTI_K_PROD_FWD, launch_prod_fwd_df64((const float4*)o.hat, (const double2*)mhat, (double2*)part, nf,
+                                                 R, Nm, B, s));
+  else
+    PROF(h, BTI_K_PROD_FWD, (launch_prod_fwd<T, T>((const C2<T>*)o.hat, mhat, part, nf, R, Nm, B, s)));
   PROF(h, BTI_K_REDUCE, (launch_reduce_chunks<T>(part, dhat, nf, R, Nm, B, s)));
   const T scale = (T)(1.0 / (double)h->L);
   if (io == BTI_P_F64)
@@ -237,7 +243,11 @@ bti_status apply_adj_t(bti_ctx* h, const OpStore& o, const void* in, void* out, 
   else
     PROF(h, BTI_K_RFFT, (launch_rfft_cols<T, float, T>(h->plan, (int)Nt, (const float*)in, R, Nt * R, dhat,
                                                         nf * R, R, B, s)));
-  PROF(h, BTI_K_PROD_ADJ, (launch_prod_adj<T, T>((const C2<T>*)o.hat, dhat, mhat, nf, R, Nm, B, s)));
+  if (o.prec == BTI_P_DF64)
+    PROF(h, BTI_K_PROD_ADJ, launch_prod_adj_df64((const float4*)o.hat, (const double2*)dhat, (double2*)mhat, nf,
+                                                 R, Nm, B, s));
+  else
+    PROF(h, BTI_K_PROD_ADJ, (launch_prod_adj<T, T>((const C2<T>*)o.hat, dhat, mhat, nf, R, Nm, B, s)));
   const T scale = (T)(1.0 / (double)h->L);
   if (io == BTI_P_F64)
     PROF(h, BTI_K_IRFFT, (launch_irfft_cols<T, double>(h->plan, (int)Nt, mhat, Nm, nf * Nm, (double*)out, Nt * Nm,
@@ -252,13 +262,13 @@ bti_status apply_op(bti_ctx* h, bti_op opi, bool adjoint, const void* in, void* 
                     bti_prec io, const char* name) {
   bti_status st = check_handle(h);
   if (st != BTI_OK) return st;
-  if (!prec_ok(io)) return fail(h, BTI_ERR_ARG, std::string(name) + ": bad io precision");
+  if (!io_ok(io)) return fail(h, BTI_ERR_ARG, std::string(name) + ": bad io precision");
   if (B < 0) return fail(h, BTI_ERR_ARG, std::string(name) + ": B < 0");
   const OpStore& o = h->op[opi];
   if (!o.set) return fail(h, BTI_ERR_STATE, std::string(name) + ": operator blocks not set");
   if (B == 0) return BTI_OK;
   if (!in || !out) return fail(h, BTI_ERR_ARG, std::string(name) + ": null pointer");
-  if (o.prec == BTI_P_F64)
+  if (o.prec != BTI_P_F32)  // FP64 and double-FP32 tiers: FFTs and vectors in FP64
     return adjoint ? apply_adj_t<double>(h, o, in, out, B, io) : apply_fwd_t<double>(h, o, in, out, B, io);
   return adjoint ? apply_adj_t<float>(h, o, in, out, B, io) : apply_fwd_t<float>(h, o, in, out, B, io);
 }

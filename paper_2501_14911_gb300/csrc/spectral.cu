@@ -217,4 +217,222 @@ template void launch_prod_adj<double, double>(const double2*, const double2*, do
 template void launch_prod_adj<float, float>(const float2*, const float2*, float2*,
                                             int64_t, int64_t, int64_t, int64_t, cudaStream_t);
 
+
+// ------------------------------------------------------------------ double-FP32 tier
+// GB300's FP64 pipe issues 1/64 of the FP32 rate, so an FP64 product of the
+// spectral blocks is bound by FP64 arithmetic at about a third of the HBM rate.
+// The double-FP32 tier keeps FP64-level accuracy on the FP32 pipes instead:
+// every real number of a spectral block is stored as an unevaluated sum
+// hi + lo of two floats (|lo| <= ulp(hi) / 2, about 48 significant bits,
+// 16 bytes per complex element like FP64), the frequency-domain vector is split
+// the same way in shared memory, and products are accumulated in float pairs:
+//   x * y = xh*yh (exact: rounded product plus its FMA error) + xh*yl + xl*yh,
+// with the high parts summed by Knuth's error-free two-sum and every error term
+// gathered in the low float.  The relative error of a sum of n terms is about
+// n * 2^-48 of the sum of magnitudes, far below the FP64 tier's 1e-12 bound.
+
+namespace {
+
+struct ff { float h, l; };
+
+__device__ __forceinline__ ff split_d(double x) {
+  float h = __double2float_rn(x);
+  float l = __double2float_rn(x - (double)h);
+  return {h, l};
+}
+
+// S += x * y  (S, x, y float pairs); 12 FP32 operations
+__device__ __forceinline__ void ff_mac(float& Sh, float& Sl, float xh, float xl, float yh, float yl) {
+  float p = xh * yh;
+  float pe = fmaf(xh, yh, -p);
+  pe = fmaf(xh, yl, pe);
+  pe = fmaf(xl, yh, pe);
+  float s = Sh + p;
+  float bb = s - Sh;
+  float e = (Sh - (s - bb)) + (p - bb);
+  Sh = s;
+  Sl += e + pe;
+}
+
+// (ah, al) + (bh, bl) -> normalised pair
+__device__ __forceinline__ void ff_add(float& ah, float& al, float bh, float bl) {
+  float s = ah + bh;
+  float bb = s - ah;
+  float e = (ah - (s - bb)) + (bh - bb);
+  e += al + bl;
+  ah = s + e;
+  al = e - (ah - s);
+}
+
+__device__ __forceinline__ double ff_to_d(float h, float l) { return (double)h + (double)l; }
+
+}  // namespace
+
+// In place: a complex FP64 array becomes (re_hi, re_lo, im_hi, im_lo) float quads.
+__global__ void split_df64_kernel(double2* a, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double2 v = a[i];
+  ff re = split_d(v.x), im = split_d(v.y);
+  reinterpret_cast<float4*>(a)[i] = make_float4(re.h, re.l, im.h, im.l);
+}
+
+void launch_split_df64(void* hat, int64_t n, cudaStream_t s) {
+  if (n > 0) split_df64_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((double2*)hat, n);
+}
+
+// Forward product, double-FP32 arithmetic.  Same decomposition as prod_fwd_kernel:
+// grid (nchunk, nf, ceil(B / BG)), warp w handles rows i = w, w + 8, ...
+template <int BG>
+__global__ void __launch_bounds__(256)
+prod_fwd_df64_kernel(const float4* __restrict__ Fhat, const double2* __restrict__ mhat,
+                     double2* __restrict__ partial, int64_t nf, int64_t R, int64_t Nm, int64_t B,
+                     int JC, int nchunk) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float4* sm = reinterpret_cast<float4*>(smem_raw);  // [BG][JC] split m-hat
+  const int ch = blockIdx.x;
+  const int64_t w = blockIdx.y;
+  const int64_t b0 = (int64_t)blockIdx.z * BG;
+  const int64_t j0 = (int64_t)ch * JC;
+  const int jn = (int)((Nm - j0) < JC ? (Nm - j0) : JC);
+  for (int idx = threadIdx.x; idx < BG * JC; idx += blockDim.x) {
+    int bb = idx / JC, jj = idx - bb * JC;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (jj < jn && b0 + bb < B) {
+      double2 x = mhat[((b0 + bb) * nf + w) * Nm + j0 + jj];
+      ff re = split_d(x.x), im = split_d(x.y);
+      v = make_float4(re.h, re.l, im.h, im.l);
+    }
+    sm[idx] = v;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t i = warp; i < R; i += 8) {
+    const float4* row = Fhat + (w * R + i) * Nm + j0;
+    float rh[BG], rl[BG], ih[BG], il[BG];
+#pragma unroll
+    for (int bb = 0; bb < BG; ++bb) { rh[bb] = rl[bb] = ih[bb] = il[bb] = 0.f; }
+#pragma unroll 4
+    for (int jj = lane; jj < jn; jj += 32) {
+      float4 f = __ldg(row + jj);  // (a_h, a_l, b_h, b_l): F = a + i b
+#pragma unroll
+      for (int bb = 0; bb < BG; ++bb) {
+        float4 x = sm[bb * JC + jj];  // (c_h, c_l, d_h, d_l): m = c + i d
+        ff_mac(rh[bb], rl[bb], f.x, f.y, x.x, x.y);    // + a c
+        ff_mac(rh[bb], rl[bb], -f.z, -f.w, x.z, x.w);  // - b d
+        ff_mac(ih[bb], il[bb], f.x, f.y, x.z, x.w);    // + a d
+        ff_mac(ih[bb], il[bb], f.z, f.w, x.x, x.y);    // + b c
+      }
+    }
+#pragma unroll
+    for (int bb = 0; bb < BG; ++bb) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        float oh = __shfl_xor_sync(0xffffffffu, rh[bb], o);
+        float ol = __shfl_xor_sync(0xffffffffu, rl[bb], o);
+        ff_add(rh[bb], rl[bb], oh, ol);
+        oh = __shfl_xor_sync(0xffffffffu, ih[bb], o);
+        ol = __shfl_xor_sync(0xffffffffu, il[bb], o);
+        ff_add(ih[bb], il[bb], oh, ol);
+      }
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int bb = 0; bb < BG; ++bb)
+        if (b0 + bb < B)
+          partial[(((b0 + bb) * nf + w) * nchunk + ch) * R + i] =
+              make_double2(ff_to_d(rh[bb], rl[bb]), ff_to_d(ih[bb], il[bb]));
+    }
+  }
+}
+
+void launch_prod_fwd_df64(const float4* Fhat, const double2* mhat, double2* partial, int64_t nf,
+                          int64_t R, int64_t Nm, int64_t B, cudaStream_t s) {
+  // chunking identical to the FP64 tier (the reduce pass and workspace sizes are shared)
+  int bg = fwd_bg<double>(B);
+  int JC = 0;
+  int nchunk = fwd_nchunk<double>(Nm, B, &JC);
+  size_t smem = sizeof(float4) * (size_t)bg * JC;
+  dim3 grid((unsigned)nchunk, (unsigned)nf, (unsigned)((B + bg - 1) / bg));
+  if (bg == 4)
+    prod_fwd_df64_kernel<4><<<grid, 256, smem, s>>>(Fhat, mhat, partial, nf, R, Nm, B, JC, nchunk);
+  else
+    prod_fwd_df64_kernel<1><<<grid, 256, smem, s>>>(Fhat, mhat, partial, nf, R, Nm, B, JC, nchunk);
+}
+
+// Adjoint product, double-FP32 arithmetic; thread owns j = j0 + tid + 256 v.
+template <int BG, int VPT>
+__global__ void __launch_bounds__(256)
+prod_adj_df64_kernel(const float4* __restrict__ Fhat, const double2* __restrict__ dhat,
+                     double2* __restrict__ mhat, int64_t nf, int64_t R, int64_t Nm, int64_t B) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float4* sd = reinterpret_cast<float4*>(smem_raw);  // [BG][R] split d-hat
+  const int64_t w = blockIdx.y;
+  const int64_t b0 = (int64_t)blockIdx.z * BG;
+  for (int64_t idx = threadIdx.x; idx < BG * R; idx += blockDim.x) {
+    int64_t bb = idx / R, i = idx - bb * R;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (b0 + bb < B) {
+      double2 x = dhat[((b0 + bb) * nf + w) * R + i];
+      ff re = split_d(x.x), im = split_d(x.y);
+      v = make_float4(re.h, re.l, im.h, im.l);
+    }
+    sd[idx] = v;
+  }
+  __syncthreads();
+  const int64_t jbase = (int64_t)blockIdx.x * (256 * VPT) + threadIdx.x;
+  float rh[BG][VPT], rl[BG][VPT], ih[BG][VPT], il[BG][VPT];
+#pragma unroll
+  for (int bb = 0; bb < BG; ++bb)
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) rh[bb][v] = rl[bb][v] = ih[bb][v] = il[bb][v] = 0.f;
+  const float4* base = Fhat + w * R * Nm;
+  for (int64_t i = 0; i < R; ++i) {
+    const float4* row = base + i * Nm;
+    float4 f[VPT];
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      int64_t j = jbase + 256 * v;
+      f[v] = (j < Nm) ? __ldg(row + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int bb = 0; bb < BG; ++bb) {
+      float4 x = sd[bb * R + i];  // d = c + i e
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) {
+        // conj(F) d = (a - i b)(c + i e) = (a c + b e) + i (a e - b c)
+        ff_mac(rh[bb][v], rl[bb][v], f[v].x, f[v].y, x.x, x.y);
+        ff_mac(rh[bb][v], rl[bb][v], f[v].z, f[v].w, x.z, x.w);
+        ff_mac(ih[bb][v], il[bb][v], f[v].x, f[v].y, x.z, x.w);
+        ff_mac(ih[bb][v], il[bb][v], -f[v].z, -f[v].w, x.x, x.y);
+      }
+    }
+  }
+#pragma unroll
+  for (int bb = 0; bb < BG; ++bb) {
+    if (b0 + bb >= B) continue;
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      int64_t j = jbase + 256 * v;
+      if (j < Nm)
+        mhat[((b0 + bb) * nf + w) * Nm + j] = make_double2(ff_to_d(rh[bb][v], rl[bb][v]), ff_to_d(ih[bb][v], il[bb][v]));
+    }
+  }
+}
+
+void launch_prod_adj_df64(const float4* Fhat, const double2* dhat, double2* mhat, int64_t nf, int64_t R,
+                          int64_t Nm, int64_t B, cudaStream_t s) {
+  if (B >= 4) {
+    constexpr int BG = 4, VPT = 2;
+    size_t smem = sizeof(float4) * (size_t)BG * R;
+    dim3 grid((unsigned)((Nm + 256 * VPT - 1) / (256 * VPT)), (unsigned)nf, (unsigned)((B + BG - 1) / BG));
+    prod_adj_df64_kernel<BG, VPT><<<grid, 256, smem, s>>>(Fhat, dhat, mhat, nf, R, Nm, B);
+  } else {
+    constexpr int BG = 1, VPT = 4;
+    size_t smem = sizeof(float4) * (size_t)BG * R;
+    dim3 grid((unsigned)((Nm + 256 * VPT - 1) / (256 * VPT)), (unsigned)nf, (unsigned)B);
+    prod_adj_df64_kernel<BG, VPT><<<grid, 256, smem, s>>>(Fhat, dhat, mhat, nf, R, Nm, B);
+  }
+}
+
 }  // namespace bti

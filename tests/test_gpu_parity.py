@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 
 import paper_2501_14911_gb300 as bti  # noqa: E402
 
-TOL = {bti.F64: 1e-12, bti.F32: 1e-5}
+TOL = {bti.F64: 1e-12, bti.F32: 1e-5, bti.DF64: 1e-12}
 
 
 def relb(a, b):
@@ -62,7 +62,7 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("store", [bti.F64, bti.F32], ids=["f64", "f32"])
+@pytest.mark.parametrize("store", [bti.F64, bti.F32, bti.DF64], ids=["f64", "f32", "df64"])
 @pytest.mark.parametrize("name,Nm,Nd,Nq,Nt,B", CASES, ids=[c[0] for c in CASES])
 def test_apply_F_FT_Fq_match_oracle(name, Nm, Nd, Nq, Nt, B, store):
     p = synthetic.small(name, 1, Nm, Nd, Nt, Nq=Nq)
@@ -71,7 +71,7 @@ def test_apply_F_FT_Fq_match_oracle(name, Nm, Nd, Nq, Nt, B, store):
     m = p.vectors_m(B)
     d = p.vectors_d(B)
     h = make_handle(F, Fq, store)
-    dt = torch.float64 if store == bti.F64 else torch.float32
+    dt = torch.float32 if store == bti.F32 else torch.float64
     m_g, d_g = cuda(m, dt), cuda(d, dt)
     out_d = torch.empty((B, Nt, Nd), dtype=dt, device="cuda")
     out_m = torch.empty((B, Nt, Nm), dtype=dt, device="cuda")
@@ -89,8 +89,9 @@ def test_apply_F_FT_Fq_match_oracle(name, Nm, Nd, Nq, Nt, B, store):
     h.close()
 
 
-@pytest.mark.parametrize("store,io", [(bti.F64, torch.float32), (bti.F32, torch.float64)],
-                         ids=["f64tier_f32io", "f32tier_f64io"])
+@pytest.mark.parametrize("store,io", [(bti.F64, torch.float32), (bti.F32, torch.float64),
+                                      (bti.DF64, torch.float32)],
+                         ids=["f64tier_f32io", "f32tier_f64io", "df64tier_f32io"])
 def test_mixed_io_types(store, io):
     p = synthetic.small("mixed_io", 40, 50, 9, 32)
     F = p.blocks_F()
@@ -171,10 +172,11 @@ def tiny_problem():
     return p, F, Fq, G, d_obs
 
 
-def test_tiny_inversion_end_to_end():
+@pytest.mark.parametrize("store", [bti.F64, bti.DF64], ids=["f64", "df64"])
+def test_tiny_inversion_end_to_end(store):
     p, F, Fq, G, d_obs = tiny_problem()
-    h = make_handle(F, Fq)
-    h.set_prior_se_grid(p.gx, p.gy, p.ell, p.sigma_p)
+    h = make_handle(F, Fq, store)
+    h.set_prior_se_grid(p.gx, p.gy, p.ell, p.sigma_p, store)
     # G^* from the device-built SE prior matches Gamma_prior F^T
     dv = p.vectors_d(2)
     mg = torch.empty((2, p.Nt, p.Nm), dtype=torch.float64, device="cuda")
@@ -261,3 +263,12 @@ def test_autograd_gradient_matches_oracle_and_fd():
     lm = oracle.loss(F, (m0 - hstep * v)[0], dobs[0], s2)
     fd = (lp - lm) / (2 * hstep)
     assert abs(fd - float(np.vdot(host(m.grad), v))) <= 1e-6 * abs(fd) + 1e-8 * abs(float(loss))
+
+
+def test_df64_is_not_an_io_type():
+    p = synthetic.small("df64io", 4, 4, 3, 8)
+    h = make_handle(p.blocks_F(), None, bti.DF64)
+    m = torch.zeros((1, 8, 16), dtype=torch.float64, device="cuda")
+    d = torch.zeros((1, 8, 3), dtype=torch.float64, device="cuda")
+    assert bti.lib().bti_apply_F(h.raw, m.data_ptr(), d.data_ptr(), 1, bti.DF64) == 1
+    h.close()
