@@ -65,6 +65,12 @@ template <typename T>
 void launch_reduce_chunks(const C2<T>* partial, C2<T>* dhat, int64_t nf, int64_t R, int64_t Nm,
                           int64_t B, cudaStream_t s);
 size_t prod_fwd_partial_elems(int64_t nf, int64_t R, int64_t Nm, int64_t B);
+// Double-FP32 tier: spectral blocks as (re_hi, re_lo, im_hi, im_lo) float quads.
+void launch_split_df64(void* hat, int64_t n, cudaStream_t s);  // in place, from complex FP64
+void launch_prod_fwd_df64(const float4* Fhat, const double2* mhat, double2* partial, int64_t nf,
+                          int64_t R, int64_t Nm, int64_t B, cudaStream_t s);
+void launch_prod_adj_df64(const float4* Fhat, const double2* dhat, double2* mhat, int64_t nf, int64_t R,
+                          int64_t Nm, int64_t B, cudaStream_t s);
 // Adjoint: mhat[b][w][j] = sum_i conj(Fhat[w][i][j]) dhat[b][w][i]
 template <typename T, typename TS>
 void launch_prod_adj(const C2<TS>* Fhat, const C2<T>* dhat, C2<T>* mhat,
