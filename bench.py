@@ -143,7 +143,7 @@ class Clocks:
 
 def spectral_hash():
     h = hashlib.sha256()
-    for f in ("spectral.cu", "bti_internal.cuh"):
+    for f in ("spectral.cu",):
         with open(os.path.join(ROOT, "paper_2501_14911_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
