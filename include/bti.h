@@ -76,7 +76,7 @@ typedef enum { BTI_P_F64 = 0, BTI_P_F32 = 1, BTI_P_DF64 = 2 } bti_prec;
  * (a cudaStream_t, or NULL for the legacy default stream).  N_q may be 0 when
  * no QoI map is used.  The circulant embedding length is L = 2 N_t (any
  * L >= 2 N_t - 1 is exact, Sec. 4 "FFT-based ... matvecs"); L must factor into
- * 2, 3, 5 and 7 and be at most 4096.  Returns BTI_ERR_ARG for sizes <= 0 or an
+ * 2, 3, 5 and 7 and be at most 2048 (N_t <= 1024).  Returns BTI_ERR_ARG for sizes <= 0 or an
  * unsupported L. */
 bti_status bti_create(int64_t Nm, int64_t Nd, int64_t Nq, int64_t Nt, int device,
                       void* cuda_stream, bti_handle* out);

@@ -191,6 +191,53 @@ bti_status store_op(bti_ctx* h, bti_op opi, const double* blocks, bti_prec store
   return BTI_OK;
 }
 
+// Forward FFT of B input vectors (io element type) into a spectrum of C2<T> elements.
+// The double-FP32 tier transforms in float pairs (FP64 accuracy on the FP32 pipes);
+// its spectra are stored as complex FP64.
+template <typename T>
+void rfft_in(bti_ctx* h, const OpStore& o, const void* in, int64_t ld, int64_t bstride, C2<T>* X,
+             int64_t Xbstride, int64_t ncols, int64_t B, bti_prec io) {
+  const int Nt = (int)h->Nt;
+  cudaStream_t s = h->stream;
+  if (o.prec == BTI_P_DF64) {
+    if (io == BTI_P_F64)
+      PROF(h, BTI_K_RFFT, (launch_rfft_cols<ffloat, double, double>(h->plan, Nt, (const double*)in, ld, bstride,
+                                                                     (double2*)X, Xbstride, ncols, B, s)));
+    else
+      PROF(h, BTI_K_RFFT, (launch_rfft_cols<ffloat, float, double>(h->plan, Nt, (const float*)in, ld, bstride,
+                                                                    (double2*)X, Xbstride, ncols, B, s)));
+  } else if (io == BTI_P_F64) {
+    PROF(h, BTI_K_RFFT, (launch_rfft_cols<T, double, T>(h->plan, Nt, (const double*)in, ld, bstride, X, Xbstride,
+                                                         ncols, B, s)));
+  } else {
+    PROF(h, BTI_K_RFFT, (launch_rfft_cols<T, float, T>(h->plan, Nt, (const float*)in, ld, bstride, X, Xbstride,
+                                                        ncols, B, s)));
+  }
+}
+
+// Inverse FFT with truncation to N_t steps and the 1/L scale, output in the io type.
+template <typename T>
+void irfft_out(bti_ctx* h, const OpStore& o, const C2<T>* Y, int64_t ld, int64_t Ybstride, void* out,
+               int64_t obstride, int64_t ncols, int64_t B, bti_prec io) {
+  const int Nt = (int)h->Nt;
+  cudaStream_t s = h->stream;
+  const double scale = 1.0 / (double)h->L;
+  if (o.prec == BTI_P_DF64) {
+    if (io == BTI_P_F64)
+      PROF(h, BTI_K_IRFFT, (launch_irfft_cols<ffloat, double, double>(h->plan, Nt, (const double2*)Y, ld, Ybstride,
+                                                                       (double*)out, obstride, ncols, B, scale, s)));
+    else
+      PROF(h, BTI_K_IRFFT, (launch_irfft_cols<ffloat, double, float>(h->plan, Nt, (const double2*)Y, ld, Ybstride,
+                                                                      (float*)out, obstride, ncols, B, scale, s)));
+  } else if (io == BTI_P_F64) {
+    PROF(h, BTI_K_IRFFT, (launch_irfft_cols<T, T, double>(h->plan, Nt, Y, ld, Ybstride, (double*)out, obstride,
+                                                           ncols, B, scale, s)));
+  } else {
+    PROF(h, BTI_K_IRFFT, (launch_irfft_cols<T, T, float>(h->plan, Nt, Y, ld, Ybstride, (float*)out, obstride,
+                                                          ncols, B, scale, s)));
+  }
+}
+
 // forward-type product: out[b] = T(op) in[b]; in [B][Nt][Nm] (io) -> out [B][Nt][R] (io)
 template <typename T>
 bti_status apply_fwd_t(bti_ctx* h, const OpStore& o, const void* in, void* out, int64_t B, bti_prec io) {
@@ -204,25 +251,14 @@ bti_status apply_fwd_t(bti_ctx* h, const OpStore& o, const void* in, void* out, 
   C2<T>* part = mhat + n_mhat;
   C2<T>* dhat = part + n_part;
   cudaStream_t s = h->stream;
-  if (io == BTI_P_F64)
-    PROF(h, BTI_K_RFFT, (launch_rfft_cols<T, double, T>(h->plan, (int)Nt, (const double*)in, Nm, Nt * Nm, mhat,
-                                                         nf * Nm, Nm, B, s)));
-  else
-    PROF(h, BTI_K_RFFT, (launch_rfft_cols<T, float, T>(h->plan, (int)Nt, (const float*)in, Nm, Nt * Nm, mhat,
-                                                        nf * Nm, Nm, B, s)));
+  rfft_in<T>(h, o, in, Nm, Nt * Nm, mhat, nf * Nm, Nm, B, io);
   if (o.prec == BTI_P_DF64)
     PROF(h, BTI_K_PROD_FWD, launch_prod_fwd_df64((const float4*)o.hat, (const double2*)mhat, (double2*)part, nf,
                                                  R, Nm, B, s));
   else
     PROF(h, BTI_K_PROD_FWD, (launch_prod_fwd<T, T>((const C2<T>*)o.hat, mhat, part, nf, R, Nm, B, s)));
   PROF(h, BTI_K_REDUCE, (launch_reduce_chunks<T>(part, dhat, nf, R, Nm, B, s)));
-  const T scale = (T)(1.0 / (double)h->L);
-  if (io == BTI_P_F64)
-    PROF(h, BTI_K_IRFFT, (launch_irfft_cols<T, double>(h->plan, (int)Nt, dhat, R, nf * R, (double*)out, Nt * R, R,
-                                                        B, scale, s)));
-  else
-    PROF(h, BTI_K_IRFFT, (launch_irfft_cols<T, float>(h->plan, (int)Nt, dhat, R, nf * R, (float*)out, Nt * R, R,
-                                                       B, scale, s)));
+  irfft_out<T>(h, o, dhat, R, nf * R, out, Nt * R, R, B, io);
   return launched(h, "forward Toeplitz product");
 }
 
@@ -237,24 +273,13 @@ bti_status apply_adj_t(bti_ctx* h, const OpStore& o, const void* in, void* out, 
   C2<T>* dhat = (C2<T>*)h->ws;
   C2<T>* mhat = dhat + n_dhat;
   cudaStream_t s = h->stream;
-  if (io == BTI_P_F64)
-    PROF(h, BTI_K_RFFT, (launch_rfft_cols<T, double, T>(h->plan, (int)Nt, (const double*)in, R, Nt * R, dhat,
-                                                         nf * R, R, B, s)));
-  else
-    PROF(h, BTI_K_RFFT, (launch_rfft_cols<T, float, T>(h->plan, (int)Nt, (const float*)in, R, Nt * R, dhat,
-                                                        nf * R, R, B, s)));
+  rfft_in<T>(h, o, in, R, Nt * R, dhat, nf * R, R, B, io);
   if (o.prec == BTI_P_DF64)
     PROF(h, BTI_K_PROD_ADJ, launch_prod_adj_df64((const float4*)o.hat, (const double2*)dhat, (double2*)mhat, nf,
                                                  R, Nm, B, s));
   else
     PROF(h, BTI_K_PROD_ADJ, (launch_prod_adj<T, T>((const C2<T>*)o.hat, dhat, mhat, nf, R, Nm, B, s)));
-  const T scale = (T)(1.0 / (double)h->L);
-  if (io == BTI_P_F64)
-    PROF(h, BTI_K_IRFFT, (launch_irfft_cols<T, double>(h->plan, (int)Nt, mhat, Nm, nf * Nm, (double*)out, Nt * Nm,
-                                                        Nm, B, scale, s)));
-  else
-    PROF(h, BTI_K_IRFFT, (launch_irfft_cols<T, float>(h->plan, (int)Nt, mhat, Nm, nf * Nm, (float*)out, Nt * Nm,
-                                                       Nm, B, scale, s)));
+  irfft_out<T>(h, o, mhat, Nm, nf * Nm, out, Nt * Nm, Nm, B, io);
   return launched(h, "adjoint Toeplitz product");
 }
 
@@ -341,6 +366,7 @@ bti_status bti_destroy(bti_handle h) {
   dev_freep(h->wsolve);
   dev_freep(h->plan.tw64);
   dev_freep(h->plan.tw32);
+  dev_freep(h->plan.twff);
   for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
   delete h;
   return BTI_OK;

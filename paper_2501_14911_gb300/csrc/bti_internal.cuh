@@ -13,6 +13,9 @@ namespace bti {
 template <typename T> struct cplx;
 template <> struct cplx<double> { using type = double2; };
 template <> struct cplx<float> { using type = float2; };
+struct ffloat;
+struct ffc;
+template <> struct cplx<ffloat> { using type = ffc; };
 template <typename T> using C2 = typename cplx<T>::type;
 
 template <typename T> __host__ __device__ __forceinline__ C2<T> mk(T re, T im) {
@@ -28,9 +31,46 @@ template <typename T> __device__ __forceinline__ C2<T> cmulc(C2<T> a, C2<T> b) {
   return mk<T>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);  // a * conj(b)
 }
 
+// ----------------------------------------------------------------- double-FP32 scalar
+// An unevaluated sum h + l of two floats (|l| <= ulp(h)/2): about 48 significant
+// bits carried on the FP32 pipes.  Addition uses Knuth's error-free two-sum and
+// multiplication the FMA-exact product; both renormalise.  The intrinsics keep
+// the compiler from contracting or reassociating the error terms away.
+struct ffloat {
+  float h, l;
+  ffloat() = default;
+  __host__ __device__ constexpr ffloat(float hh, float ll) : h(hh), l(ll) {}
+  __host__ __device__ constexpr explicit ffloat(double x) : h((float)x), l((float)(x - (double)(float)x)) {}
+  __host__ __device__ constexpr explicit ffloat(float x) : h(x), l(0.f) {}
+  __host__ __device__ constexpr explicit ffloat(int x) : h((float)x), l(0.f) {}
+  __host__ __device__ explicit operator double() const { return (double)h + (double)l; }
+  __host__ __device__ explicit operator float() const { return h + l; }
+};
+__device__ __forceinline__ ffloat operator+(ffloat a, ffloat b) {
+  float s = __fadd_rn(a.h, b.h);
+  float bb = __fsub_rn(s, a.h);
+  float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));
+  e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+  float h = __fadd_rn(s, e);
+  return ffloat(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+__device__ __forceinline__ ffloat operator-(ffloat a) { return ffloat(-a.h, -a.l); }
+__device__ __forceinline__ ffloat operator-(ffloat a, ffloat b) { return a + (-b); }
+__device__ __forceinline__ ffloat operator*(ffloat a, ffloat b) {
+  float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  float h = __fadd_rn(p, e);
+  return ffloat(h, __fsub_rn(e, __fsub_rn(h, p)));
+}
+struct __align__(16) ffc {
+  ffloat x, y;
+};
+
 // ----------------------------------------------------------------- FFT plan
 constexpr int kMaxPasses = 12;
-constexpr int kMaxL = 4096;
+constexpr int kMaxL = 2048;  // longest transform (N_t <= 1024); also the per-CTA FFT size
 
 struct FftPlan {
   int L = 0;              // transform length (2 N_t)
@@ -39,6 +79,7 @@ struct FftPlan {
   int P = 1;              // complex transforms per CTA (2 P real columns)
   double2* tw64 = nullptr;  // e^{-2 pi i n / L}, n < L (device)
   float2* tw32 = nullptr;
+  ffc* twff = nullptr;      // the same table as double-FP32 pairs
 };
 
 bool fft_plan_make(FftPlan& p, int L);   // host: factor L, choose P; false if unsupported
@@ -51,9 +92,10 @@ bool fft_plan_factor(FftPlan& p, int L);
 template <typename T, typename TI, typename TO>
 void launch_rfft_cols(const FftPlan& p, int Nt, const TI* x, int64_t ld, int64_t x_bstride,
                       C2<TO>* X, int64_t X_bstride, int64_t ncols, int64_t B, cudaStream_t s);
-template <typename T, typename TO>
-void launch_irfft_cols(const FftPlan& p, int Nt, const C2<T>* X, int64_t ld, int64_t X_bstride,
-                       TO* y, int64_t y_bstride, int64_t ncols, int64_t B, T scale, cudaStream_t s);
+// Inverse: spectrum stored as C2<TYI>, arithmetic in T, output TO.
+template <typename T, typename TYI, typename TO>
+void launch_irfft_cols(const FftPlan& p, int Nt, const C2<TYI>* X, int64_t ld, int64_t X_bstride,
+                       TO* y, int64_t y_bstride, int64_t ncols, int64_t B, double scale, cudaStream_t s);
 
 // Spectral block products (spectral.cu).
 // Forward: dhat[b][w][i] = sum_j Fhat[w][i][j] mhat[b][w][j]  (T compute, TS storage)

@@ -14,7 +14,9 @@
 // Each CTA transforms 2P real columns as P complex transforms (column 2p in the
 // real part, 2p+1 in the imaginary part), in shared memory with a mixed-radix
 // (8, 4, 2, 7, 5, 3) Stockham pass sequence; twiddles e^{-2 pi i n / L} come from
-// a table computed in FP64 on the host with std::cos / std::sin.
+// a table computed in FP64 on the host with std::cos / std::sin.  The arithmetic
+// type T is float, double, or the double-FP32 pair (ffloat), which carries FP64-
+// level accuracy on the FP32 pipes (GB300 issues FP64 at 1/64 of the FP32 rate).
 #include "bti_internal.cuh"
 
 #include <cmath>
@@ -44,7 +46,7 @@ bool fft_plan_make(FftPlan& p, int L) {
   if (n != 1) return false;
   p.L = L;
   p.npass = np;
-  int P = 4096 / L;
+  int P = kMaxL / L;  // P L <= kMaxL complex elements per CTA (two buffers)
   if (P > 16) P = 16;
   if (P < 1) P = 1;
   p.P = P;
@@ -56,10 +58,17 @@ bool fft_plan_make(FftPlan& p, int L) {
     t64[k] = make_double2(std::cos(a), -std::sin(a));
     t32[k] = make_float2((float)t64[k].x, (float)t64[k].y);
   }
+  std::vector<ffc> tff(L);
+  for (int k = 0; k < L; ++k) {
+    tff[k].x = ffloat(t64[k].x);
+    tff[k].y = ffloat(t64[k].y);
+  }
   if (cudaMalloc(&p.tw64, sizeof(double2) * L) != cudaSuccess) return false;
   if (cudaMalloc(&p.tw32, sizeof(float2) * L) != cudaSuccess) return false;
+  if (cudaMalloc(&p.twff, sizeof(ffc) * L) != cudaSuccess) return false;
   cudaMemcpy(p.tw64, t64.data(), sizeof(double2) * L, cudaMemcpyHostToDevice);
   cudaMemcpy(p.tw32, t32.data(), sizeof(float2) * L, cudaMemcpyHostToDevice);
+  cudaMemcpy(p.twff, tff.data(), sizeof(ffc) * L, cudaMemcpyHostToDevice);
   return true;
 }
 
@@ -78,22 +87,40 @@ bool fft_plan_factor(FftPlan& p, int L) {
   if (n != 1) return false;
   p.L = L;
   p.npass = np;
-  int P = 4096 / L;
+  int P = kMaxL / L;  // P L <= kMaxL complex elements per CTA (two buffers)
   if (P > 16) P = 16;
   if (P < 1) P = 1;
   p.P = P;
   p.tw64 = nullptr;
   p.tw32 = nullptr;
+  p.twff = nullptr;
   return true;
 }
 
-template <typename T> __device__ __forceinline__ const C2<T>* twtab(const double2* t64, const float2* t32);
-template <> __device__ __forceinline__ const double2* twtab<double>(const double2* t64, const float2*) { return t64; }
-template <> __device__ __forceinline__ const float2* twtab<float>(const double2*, const float2* t32) { return t32; }
+struct TwTabs {
+  const double2* t64;
+  const float2* t32;
+  const ffc* tff;
+};
+template <typename T> __device__ __forceinline__ const C2<T>* twtab(const TwTabs& t);
+template <> __device__ __forceinline__ const double2* twtab<double>(const TwTabs& t) { return t.t64; }
+template <> __device__ __forceinline__ const float2* twtab<float>(const TwTabs& t) { return t.t32; }
+template <> __device__ __forceinline__ const ffc* twtab<ffloat>(const TwTabs& t) { return t.tff; }
+
+template <typename T> __device__ __forceinline__ C2<T> tw_load(const C2<T>* __restrict__ tw, int n) {
+  return __ldg(&tw[n]);
+}
+template <> __device__ __forceinline__ ffc tw_load<ffloat>(const ffc* __restrict__ tw, int n) {
+  float4 v = __ldg(reinterpret_cast<const float4*>(tw) + n);
+  ffc z;
+  z.x = ffloat(v.x, v.y);
+  z.y = ffloat(v.z, v.w);
+  return z;
+}
 
 template <typename T, bool INV>
 __device__ __forceinline__ C2<T> tw_get(const C2<T>* __restrict__ tw, int n) {
-  C2<T> w = __ldg(&tw[n]);
+  C2<T> w = tw_load<T>(tw, n);
   if (INV) w.y = -w.y;
   return w;
 }
@@ -212,17 +239,17 @@ __device__ C2<T>* run_passes(const FftDesc& D, C2<T>* buf0, C2<T>* buf1, const C
 template <typename TO, typename T> __device__ __forceinline__ C2<TO> cvt2(C2<T> z) {
   return mk<TO>((TO)z.x, (TO)z.y);
 }
+template <typename T> __device__ __forceinline__ C2<T> czero() { return mk<T>((T)0, (T)0); }
 
 template <typename T, typename TI, typename TO>
 __global__ void __launch_bounds__(256)
 rfft_cols_kernel(FftDesc D, int Nt, const TI* __restrict__ x, int64_t ld, int64_t xbs,
-                 C2<TO>* __restrict__ X, int64_t Xbs, int64_t ncols,
-                 const double2* __restrict__ tw64, const float2* __restrict__ tw32) {
+                 C2<TO>* __restrict__ X, int64_t Xbs, int64_t ncols, TwTabs tabs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int L = D.L, P = D.P, W2 = 2 * P;
   C2<T>* buf0 = reinterpret_cast<C2<T>*>(smem_raw);
   C2<T>* buf1 = buf0 + P * L;
-  const C2<T>* tw = twtab<T>(tw64, tw32);
+  const C2<T>* tw = twtab<T>(tabs);
   const int64_t col0 = (int64_t)blockIdx.x * W2;
   const TI* xb = x + (int64_t)blockIdx.y * xbs;
   C2<TO>* Xb = X + (int64_t)blockIdx.y * Xbs;
@@ -236,7 +263,7 @@ rfft_cols_kernel(FftDesc D, int Nt, const TI* __restrict__ x, int64_t ld, int64_
   const int pad = L - Nt;
   for (int idx = threadIdx.x; idx < P * pad; idx += blockDim.x) {
     int p = idx / pad, t = Nt + (idx - p * pad);
-    buf0[p * L + t] = mk<T>((T)0, (T)0);
+    buf0[p * L + t] = czero<T>();
   }
   __syncthreads();
   C2<T>* Z = run_passes<T, false>(D, buf0, buf1, tw);
@@ -250,34 +277,35 @@ rfft_cols_kernel(FftDesc D, int Nt, const TI* __restrict__ x, int64_t ld, int64_
     C2<T> z = Z[p * L + k];
     C2<T> zc = Z[p * L + (k == 0 ? 0 : L - k)];
     C2<T> out;
+    const T half = (T)0.5;
     if ((c & 1) == 0) {
-      out = mk<T>((T)0.5 * (z.x + zc.x), (T)0.5 * (z.y - zc.y));   // (Z + conj Zc) / 2
+      out = mk<T>(half * (z.x + zc.x), half * (z.y - zc.y));   // (Z + conj Zc) / 2
     } else {
-      out = mk<T>((T)0.5 * (z.y + zc.y), (T)0.5 * (zc.x - z.x));   // (Z - conj Zc) / 2i
+      out = mk<T>(half * (z.y + zc.y), half * (zc.x - z.x));   // (Z - conj Zc) / 2i
     }
     Xb[(int64_t)k * ncols + col] = cvt2<TO, T>(out);
   }
 }
 
-template <typename T, typename TO>
+template <typename T, typename TYI, typename TO>
 __global__ void __launch_bounds__(256)
-irfft_cols_kernel(FftDesc D, int Nt, const C2<T>* __restrict__ Y, int64_t ld, int64_t Ybs,
-                  TO* __restrict__ y, int64_t ybs, int64_t ncols, T scale,
-                  const double2* __restrict__ tw64, const float2* __restrict__ tw32) {
+irfft_cols_kernel(FftDesc D, int Nt, const C2<TYI>* __restrict__ Y, int64_t ld, int64_t Ybs,
+                  TO* __restrict__ y, int64_t ybs, int64_t ncols, double scale_d, TwTabs tabs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int L = D.L, P = D.P, W2 = 2 * P;
   C2<T>* buf0 = reinterpret_cast<C2<T>*>(smem_raw);
   C2<T>* buf1 = buf0 + P * L;
-  const C2<T>* tw = twtab<T>(tw64, tw32);
+  const C2<T>* tw = twtab<T>(tabs);
+  const T scale = (T)scale_d;
   const int64_t col0 = (int64_t)blockIdx.x * W2;
-  const C2<T>* Yb = Y + (int64_t)blockIdx.y * Ybs;
+  const C2<TYI>* Yb = Y + (int64_t)blockIdx.y * Ybs;
   TO* yb = y + (int64_t)blockIdx.y * ybs;
   const int nf = Nt + 1;
   // stage spectrum a (even column) in buf0, spectrum b (odd column) in buf1
   for (int idx = threadIdx.x; idx < nf * W2; idx += blockDim.x) {
     int k = idx / W2, c = idx - k * W2;
     int64_t col = col0 + c;
-    C2<T> v = (col < ncols) ? Yb[(int64_t)k * ld + col] : mk<T>((T)0, (T)0);
+    C2<T> v = (col < ncols) ? cvt2<T, TYI>(Yb[(int64_t)k * ld + col]) : czero<T>();
     C2<T>* dst = (c & 1) ? buf1 : buf0;
     dst[(c >> 1) * L + k] = v;
   }
@@ -316,6 +344,8 @@ static FftDesc desc_of(const FftPlan& p) {
   return d;
 }
 
+static TwTabs tabs_of(const FftPlan& p) { return TwTabs{p.tw64, p.tw32, p.twff}; }
+
 template <typename T, typename TI, typename TO>
 void launch_rfft_cols(const FftPlan& p, int Nt, const TI* x, int64_t ld, int64_t x_bstride,
                       C2<TO>* X, int64_t X_bstride, int64_t ncols, int64_t B, cudaStream_t s) {
@@ -332,29 +362,28 @@ void launch_rfft_cols(const FftPlan& p, int Nt, const TI* x, int64_t ld, int64_t
     int64_t nb = B - b0 < 65535 ? B - b0 : 65535;
     dim3 grid((unsigned)gx, (unsigned)nb);
     rfft_cols_kernel<T, TI, TO><<<grid, 256, smem, s>>>(D, Nt, x + b0 * x_bstride, ld, x_bstride,
-                                                        X + b0 * X_bstride, X_bstride, ncols,
-                                                        p.tw64, p.tw32);
+                                                        X + b0 * X_bstride, X_bstride, ncols, tabs_of(p));
   }
 }
 
-template <typename T, typename TO>
-void launch_irfft_cols(const FftPlan& p, int Nt, const C2<T>* X, int64_t ld, int64_t X_bstride,
-                       TO* y, int64_t y_bstride, int64_t ncols, int64_t B, T scale, cudaStream_t s) {
+template <typename T, typename TYI, typename TO>
+void launch_irfft_cols(const FftPlan& p, int Nt, const C2<TYI>* X, int64_t ld, int64_t X_bstride,
+                       TO* y, int64_t y_bstride, int64_t ncols, int64_t B, double scale, cudaStream_t s) {
   if (ncols <= 0 || B <= 0) return;
   FftDesc D = desc_of(p);
   size_t smem = 2 * sizeof(C2<T>) * (size_t)p.P * p.L;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(irfft_cols_kernel<T, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(irfft_cols_kernel<T, TYI, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
   int64_t gx = (ncols + 2 * p.P - 1) / (2 * p.P);
   for (int64_t b0 = 0; b0 < B; b0 += 65535) {
     int64_t nb = B - b0 < 65535 ? B - b0 : 65535;
     dim3 grid((unsigned)gx, (unsigned)nb);
-    irfft_cols_kernel<T, TO><<<grid, 256, smem, s>>>(D, Nt, X + b0 * X_bstride, ld, X_bstride,
-                                                     y + b0 * y_bstride, y_bstride, ncols, scale,
-                                                     p.tw64, p.tw32);
+    irfft_cols_kernel<T, TYI, TO><<<grid, 256, smem, s>>>(D, Nt, X + b0 * X_bstride, ld, X_bstride,
+                                                          y + b0 * y_bstride, y_bstride, ncols, scale,
+                                                          tabs_of(p));
   }
 }
 
@@ -366,12 +395,16 @@ INST_R(double, double, float)
 INST_R(double, float, double)
 INST_R(float, float, float)
 INST_R(float, double, float)
-#define INST_I(T, TO)                                                                             \
-  template void launch_irfft_cols<T, TO>(const FftPlan&, int, const C2<T>*, int64_t, int64_t, TO*, \
-                                         int64_t, int64_t, int64_t, T, cudaStream_t);
-INST_I(double, double)
-INST_I(double, float)
-INST_I(float, float)
-INST_I(float, double)
+INST_R(ffloat, double, double)
+INST_R(ffloat, float, double)
+#define INST_I(T, TYI, TO)                                                                             \
+  template void launch_irfft_cols<T, TYI, TO>(const FftPlan&, int, const C2<TYI>*, int64_t, int64_t, TO*, \
+                                              int64_t, int64_t, int64_t, double, cudaStream_t);
+INST_I(double, double, double)
+INST_I(double, double, float)
+INST_I(float, float, float)
+INST_I(float, float, double)
+INST_I(ffloat, double, double)
+INST_I(ffloat, double, float)
 
 }  // namespace bti

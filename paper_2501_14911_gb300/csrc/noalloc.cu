@@ -92,7 +92,7 @@ extern "C" bti_status bti_apply_F_noalloc(const double* blocks, const double* m,
   launch_rfft_cols<double, double, double>(plan, (int)Nt, m, Nm, Nt * Nm, mhat, nf * Nm, Nm, B, s);
   launch_prod_fwd<double, double>(Fhat, mhat, part, nf, Nd, Nm, B, s);
   launch_reduce_chunks<double>(part, dhat, nf, Nd, Nm, B, s);
-  launch_irfft_cols<double, double>(plan, (int)Nt, dhat, Nd, nf * Nd, d, Nt * Nd, Nd, B, 1.0 / (double)L, s);
+  launch_irfft_cols<double, double, double>(plan, (int)Nt, dhat, Nd, nf * Nd, d, Nt * Nd, Nd, B, 1.0 / (double)L, s);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? BTI_OK : BTI_ERR_CUDA;
 }

@@ -23,7 +23,9 @@ template <typename T, typename TS> __device__ __forceinline__ C2<T> ldF(const C2
 }
 
 // grid (nchunk, nf, ceil(B / BG)), 256 threads.  Warp w handles rows i = w, w + 8, ...
-template <typename T, typename TS, int BG>
+// Each lane streams its row segment U elements at a time with the next U loads
+// in flight while the current U are consumed (register double buffering).
+template <typename T, typename TS, int BG, int U>
 __global__ void __launch_bounds__(256)
 prod_fwd_kernel(const C2<TS>* __restrict__ Fhat, const C2<T>* __restrict__ mhat,
                 C2<T>* __restrict__ partial, int64_t nf, int64_t R, int64_t Nm, int64_t B,
@@ -43,22 +45,41 @@ prod_fwd_kernel(const C2<TS>* __restrict__ Fhat, const C2<T>* __restrict__ mhat,
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int STEP = 32 * U;
+  const C2<T> z = mk<T>((T)0, (T)0);
   for (int64_t i = warp; i < R; i += 8) {
     const C2<TS>* row = Fhat + (w * R + i) * Nm + j0;
     T ar[BG], ai[BG];
 #pragma unroll
     for (int bb = 0; bb < BG; ++bb) { ar[bb] = (T)0; ai[bb] = (T)0; }
-#pragma unroll 8
-    for (int jj = lane; jj < jn; jj += 32) {
-      C2<T> f = ldF<T, TS>(row + jj);
+    C2<T> cur[U], nxt[U];
 #pragma unroll
-      for (int bb = 0; bb < BG; ++bb) {
-        C2<T> x = sm[bb * JC + jj];
-        ar[bb] = fma(f.x, x.x, ar[bb]);
-        ar[bb] = fma(-f.y, x.y, ar[bb]);
-        ai[bb] = fma(f.x, x.y, ai[bb]);
-        ai[bb] = fma(f.y, x.x, ai[bb]);
+    for (int u = 0; u < U; ++u) {
+      int jj = lane + 32 * u;
+      cur[u] = (jj < jn) ? ldF<T, TS>(row + jj) : z;
+    }
+    for (int base = 0; base < jn; base += STEP) {
+      const int nb = base + STEP;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        int jj = nb + lane + 32 * u;
+        nxt[u] = (jj < jn) ? ldF<T, TS>(row + jj) : z;
       }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int jj = base + lane + 32 * u;
+        const C2<T> f = cur[u];
+#pragma unroll
+        for (int bb = 0; bb < BG; ++bb) {
+          C2<T> x = sm[bb * JC + (jj < JC ? jj : 0)];
+          ar[bb] = fma(f.x, x.x, ar[bb]);
+          ar[bb] = fma(-f.y, x.y, ar[bb]);
+          ai[bb] = fma(f.x, x.y, ai[bb]);
+          ai[bb] = fma(f.y, x.x, ai[bb]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) cur[u] = nxt[u];
     }
 #pragma unroll
     for (int bb = 0; bb < BG; ++bb) {
@@ -127,10 +148,11 @@ void launch_prod_fwd(const C2<TS>* Fhat, const C2<T>* mhat, C2<T>* partial,
   int nchunk = fwd_nchunk<T>(Nm, B, &JC);
   size_t smem = sizeof(C2<T>) * (size_t)bg * JC;
   dim3 grid((unsigned)nchunk, (unsigned)nf, (unsigned)((B + bg - 1) / bg));
+  constexpr int U1 = sizeof(C2<TS>) >= 16 ? 8 : 16;  // 128 bytes of loads per lane per step
   if (bg == 4)
-    prod_fwd_kernel<T, TS, 4><<<grid, 256, smem, s>>>(Fhat, mhat, partial, nf, R, Nm, B, JC, nchunk);
+    prod_fwd_kernel<T, TS, 4, 4><<<grid, 256, smem, s>>>(Fhat, mhat, partial, nf, R, Nm, B, JC, nchunk);
   else
-    prod_fwd_kernel<T, TS, 1><<<grid, 256, smem, s>>>(Fhat, mhat, partial, nf, R, Nm, B, JC, nchunk);
+    prod_fwd_kernel<T, TS, 1, U1><<<grid, 256, smem, s>>>(Fhat, mhat, partial, nf, R, Nm, B, JC, nchunk);
 }
 
 // grid (ceil(Nm / (256 VPT)), nf, ceil(B / BG)); thread owns j = j0 + tid + 256 v
@@ -282,8 +304,12 @@ void launch_split_df64(void* hat, int64_t n, cudaStream_t s) {
 }
 
 // Forward product, double-FP32 arithmetic.  Same decomposition as prod_fwd_kernel:
-// grid (nchunk, nf, ceil(B / BG)), warp w handles rows i = w, w + 8, ...
-template <int BG>
+// grid (nchunk, nf, ceil(B / BG)), warp w handles rows i = w, w + 8, ...  Each lane
+// streams its row segment U elements at a time with the next U loads issued before
+// the current U are consumed (register double buffering keeps 2 U 16-byte loads in
+// flight per lane), and the four real products of a complex multiply-accumulate go
+// to four independent float-pair accumulators so their two-sum chains overlap.
+template <int BG, int U>
 __global__ void __launch_bounds__(256)
 prod_fwd_df64_kernel(const float4* __restrict__ Fhat, const double2* __restrict__ mhat,
                      double2* __restrict__ partial, int64_t nf, int64_t R, int64_t Nm, int64_t B,
@@ -307,41 +333,62 @@ prod_fwd_df64_kernel(const float4* __restrict__ Fhat, const double2* __restrict_
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int STEP = 32 * U;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   for (int64_t i = warp; i < R; i += 8) {
     const float4* row = Fhat + (w * R + i) * Nm + j0;
-    float rh[BG], rl[BG], ih[BG], il[BG];
+    // accumulators: [0] +a c, [1] -b d, [2] +a d, [3] +b c (high and low floats)
+    float ah[BG][4], al[BG][4];
 #pragma unroll
-    for (int bb = 0; bb < BG; ++bb) { rh[bb] = rl[bb] = ih[bb] = il[bb] = 0.f; }
-#pragma unroll 4
-    for (int jj = lane; jj < jn; jj += 32) {
-      float4 f = __ldg(row + jj);  // (a_h, a_l, b_h, b_l): F = a + i b
+    for (int bb = 0; bb < BG; ++bb)
 #pragma unroll
-      for (int bb = 0; bb < BG; ++bb) {
-        float4 x = sm[bb * JC + jj];  // (c_h, c_l, d_h, d_l): m = c + i d
-        ff_mac(rh[bb], rl[bb], f.x, f.y, x.x, x.y);    // + a c
-        ff_mac(rh[bb], rl[bb], -f.z, -f.w, x.z, x.w);  // - b d
-        ff_mac(ih[bb], il[bb], f.x, f.y, x.z, x.w);    // + a d
-        ff_mac(ih[bb], il[bb], f.z, f.w, x.x, x.y);    // + b c
+      for (int q = 0; q < 4; ++q) ah[bb][q] = al[bb][q] = 0.f;
+    float4 cur[U], nxt[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      int jj = lane + 32 * u;
+      cur[u] = (jj < jn) ? __ldg(row + jj) : z4;
+    }
+    for (int base = 0; base < jn; base += STEP) {
+      const int nb = base + STEP;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        int jj = nb + lane + 32 * u;
+        nxt[u] = (jj < jn) ? __ldg(row + jj) : z4;
       }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int jj = base + lane + 32 * u;
+        const float4 f = cur[u];  // (a_h, a_l, b_h, b_l): F = a + i b
+#pragma unroll
+        for (int bb = 0; bb < BG; ++bb) {
+          // zero-padded columns past jn hold zeros in both f and sm
+          const float4 x = sm[bb * JC + (jj < JC ? jj : 0)];  // (c_h, c_l, d_h, d_l)
+          ff_mac(ah[bb][0], al[bb][0], f.x, f.y, x.x, x.y);
+          ff_mac(ah[bb][1], al[bb][1], -f.z, -f.w, x.z, x.w);
+          ff_mac(ah[bb][2], al[bb][2], f.x, f.y, x.z, x.w);
+          ff_mac(ah[bb][3], al[bb][3], f.z, f.w, x.x, x.y);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) cur[u] = nxt[u];
     }
 #pragma unroll
     for (int bb = 0; bb < BG; ++bb) {
+      float rh = ah[bb][0], rl = al[bb][0], ih = ah[bb][2], il = al[bb][2];
+      ff_add(rh, rl, ah[bb][1], al[bb][1]);
+      ff_add(ih, il, ah[bb][3], al[bb][3]);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        float oh = __shfl_xor_sync(0xffffffffu, rh[bb], o);
-        float ol = __shfl_xor_sync(0xffffffffu, rl[bb], o);
-        ff_add(rh[bb], rl[bb], oh, ol);
-        oh = __shfl_xor_sync(0xffffffffu, ih[bb], o);
-        ol = __shfl_xor_sync(0xffffffffu, il[bb], o);
-        ff_add(ih[bb], il[bb], oh, ol);
+        float oh = __shfl_xor_sync(0xffffffffu, rh, o);
+        float ol = __shfl_xor_sync(0xffffffffu, rl, o);
+        ff_add(rh, rl, oh, ol);
+        oh = __shfl_xor_sync(0xffffffffu, ih, o);
+        ol = __shfl_xor_sync(0xffffffffu, il, o);
+        ff_add(ih, il, oh, ol);
       }
-    }
-    if (lane == 0) {
-#pragma unroll
-      for (int bb = 0; bb < BG; ++bb)
-        if (b0 + bb < B)
-          partial[(((b0 + bb) * nf + w) * nchunk + ch) * R + i] =
-              make_double2(ff_to_d(rh[bb], rl[bb]), ff_to_d(ih[bb], il[bb]));
+      if (lane == 0 && b0 + bb < B)
+        partial[(((b0 + bb) * nf + w) * nchunk + ch) * R + i] = make_double2(ff_to_d(rh, rl), ff_to_d(ih, il));
     }
   }
 }
@@ -355,9 +402,9 @@ void launch_prod_fwd_df64(const float4* Fhat, const double2* mhat, double2* part
   size_t smem = sizeof(float4) * (size_t)bg * JC;
   dim3 grid((unsigned)nchunk, (unsigned)nf, (unsigned)((B + bg - 1) / bg));
   if (bg == 4)
-    prod_fwd_df64_kernel<4><<<grid, 256, smem, s>>>(Fhat, mhat, partial, nf, R, Nm, B, JC, nchunk);
+    prod_fwd_df64_kernel<4, 4><<<grid, 256, smem, s>>>(Fhat, mhat, partial, nf, R, Nm, B, JC, nchunk);
   else
-    prod_fwd_df64_kernel<1><<<grid, 256, smem, s>>>(Fhat, mhat, partial, nf, R, Nm, B, JC, nchunk);
+    prod_fwd_df64_kernel<1, 8><<<grid, 256, smem, s>>>(Fhat, mhat, partial, nf, R, Nm, B, JC, nchunk);
 }
 
 // Adjoint product, double-FP32 arithmetic; thread owns j = j0 + tid + 256 v.

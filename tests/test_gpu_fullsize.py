@@ -1,0 +1,134 @@
+"""Parity at the workloads' full sizes, in the launch configuration the bench times.
+
+- Matvec sweep (N_m = 65,536, N_d = 128, N_t = 256): single-vector F and F^T
+  calls on every tier; the oracle computes sampled output blocks one by one.
+- Batched online (N_m = 4,096, N_d = 100, N_t = 200, K = 20,000^2, 64
+  observation vectors): K (sampled entries and the whole lower triangle), the
+  Cholesky factor, m_map and q_map against the oracle's complete inversion.
+- Differentiation (N_m = 8,192, N_d = 64, N_t = 256): the autograd gradient of
+  the data misfit against the oracle gradient.
+
+Minutes of host time for the oracle; GPU only.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2501_14911_gb300 import synthetic
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+import paper_2501_14911_gb300 as bti  # noqa: E402
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def relb(a, b):
+    a = np.asarray(a, dtype=np.float64).reshape(a.shape[0], -1)
+    b = np.asarray(b, dtype=np.float64).reshape(b.shape[0], -1)
+    return float(np.max(np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)))
+
+
+@pytest.fixture(scope="module")
+def sweep():
+    p = synthetic.SWEEP
+    return p, p.blocks_F(), p.vectors_m(2), p.vectors_d(2)
+
+
+@pytest.mark.parametrize("store,tol", [(bti.DF64, 1e-12), (bti.F64, 1e-12), (bti.F32, 1e-5)],
+                         ids=["df64", "f64", "f32"])
+def test_sweep_sampled_outputs(sweep, store, tol):
+    p, F, m, d = sweep
+    dt = torch.float32 if store == bti.F32 else torch.float64
+    h = bti.Handle(p.Nm, p.Nd, 0, p.Nt)
+    Fd = torch.from_numpy(F).cuda()
+    h.set_blocks(bti.OP_F, Fd, store)
+    del Fd
+    m_g = torch.from_numpy(m).cuda().to(dt)
+    d_g = torch.from_numpy(d).cuda().to(dt)
+    outd = torch.empty((2, p.Nt, p.Nd), dtype=dt, device="cuda")
+    outm = torch.empty((2, p.Nt, p.Nm), dtype=dt, device="cuda")
+    for b in range(2):  # one vector per call, as the bench runs it
+        h.apply_F(m_g[b], outd[b])
+        h.apply_FT(d_g[b], outm[b])
+    torch.cuda.synchronize()
+    m_in = m_g.double().cpu().numpy()
+    d_in = d_g.double().cpu().numpy()
+    od = outd.double().cpu().numpy()
+    om = outm.double().cpu().numpy()
+    h.close()
+    for b in range(2):
+        for t in (0, 1, 97, 255):
+            assert rel(od[b, t], oracle.p2o_apply_block(F, m_in[b], t)) < tol, (b, t)
+        for s in (0, 128, 255):
+            assert rel(om[b, s], oracle.p2o_apply_adjoint_block(F, d_in[b], s)) < tol, (b, s)
+
+
+def test_batched_inversion_full_size():
+    p = synthetic.BATCHED
+    F = p.blocks_F()
+    Fq = p.blocks_Fq()
+    d_obs = p.vectors_d()  # 64 observation vectors (synthetic data; the solve does not care)
+    h = bti.Handle(p.Nm, p.Nd, p.Nq, p.Nt)
+    h.set_blocks(bti.OP_F, torch.from_numpy(F).cuda(), bti.DF64)
+    h.set_blocks(bti.OP_FQ, torch.from_numpy(Fq).cuda(), bti.DF64)
+    h.set_prior_se_grid(p.gx, p.gy, p.ell, p.sigma_p, bti.DF64)
+    h.set_noise(p.sigma2)
+    h.build_K(p.col_block)
+    K_gpu = h.copy_K().cpu().numpy()
+    h.factor_K()
+    L_gpu = h.copy_K().cpu().numpy()
+    m_map = torch.empty((p.n_vectors, p.Nt, p.Nm), dtype=torch.float64, device="cuda")
+    q_map = torch.empty((p.n_vectors, p.Nt, p.Nq), dtype=torch.float64, device="cuda")
+    h.infer_map(torch.from_numpy(d_obs).cuda(), m_map)
+    h.predict_qoi(m_map, q_map)
+    m_gpu = m_map.cpu().numpy()
+    q_gpu = q_map.cpu().numpy()
+    h.close()
+
+    Cs = oracle.se_covariance(p.gx, p.gy, p.ell, p.sigma_p)
+    G = oracle.prior_blocks(F, Cs)
+    # sampled entries of K one by one from the block definition
+    rng = np.random.default_rng(0)
+    n = p.Nt * p.Nd
+    for _ in range(200):
+        r, c = sorted(rng.integers(0, n, size=2))[::-1]
+        t, i = divmod(int(r), p.Nd)
+        tp, ip = divmod(int(c), p.Nd)
+        v = sum(float(F[t - s, i] @ G[tp - s, ip]) for s in range(min(t, tp) + 1))
+        if r == c:
+            v += p.sigma2
+        assert abs(K_gpu[r, c] - v) <= 1e-12 * abs(K_gpu[r, r]), (r, c)
+    K_or = oracle.assemble_K(F, G, p.sigma2)
+    low = np.tril_indices(n)
+    assert rel(K_gpu[low], K_or[low]) < 1e-12
+    del K_gpu
+    L_or = oracle.cholesky_lower(K_or)
+    assert rel(L_gpu[low], L_or[low]) < 1e-12
+    del L_gpu, low
+    m_or = oracle.map_point(F, G, p.sigma2, d_obs, L=L_or)
+    assert relb(m_gpu, m_or) < 1e-11
+    assert relb(q_gpu, oracle.qoi_map(Fq, m_or)) < 1e-11
+
+
+def test_diff_gradient_full_size():
+    p = synthetic.DIFF
+    F = p.blocks_F()
+    m0 = p.vectors_m(1)
+    dobs = p.vectors_d(1)
+    h = bti.Handle(p.Nm, p.Nd, 0, p.Nt)
+    h.set_blocks(bti.OP_F, torch.from_numpy(F).cuda(), bti.DF64)
+    m = torch.from_numpy(m0).cuda().requires_grad_(True)
+    r = bti.apply_F_autograd(h, m) - torch.from_numpy(dobs).cuda()
+    loss = 0.5 * (r * r).sum() / p.sigma2
+    loss.backward()
+    g = m.grad.detach().cpu().numpy()
+    h.close()
+    g_or = oracle.loss_gradient(F, m0[0], dobs[0], p.sigma2)
+    assert relb(g, g_or[None]) < 1e-12
