@@ -141,24 +141,30 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def spectral_hash():
+def kernel_source_hash(names):
+    """Hash of the source text of the named kernels in spectral.cu (template line to
+    closing brace), so a traffic record stays valid exactly as long as those kernels do."""
+    with open(os.path.join(ROOT, "paper_2501_14911_gb300", "csrc", "spectral.cu")) as f:
+        src = f.read()
     h = hashlib.sha256()
-    for f in ("spectral.cu",):
-        with open(os.path.join(ROOT, "paper_2501_14911_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    for name in names:
+        i = src.index(name + "(")
+        j = src.rfind("template <", 0, i)
+        k = src.index("\n}\n", i) + 3
+        h.update(src[j:k].encode())
     return h.hexdigest()[:16]
 
 
 def ncu_traffic(kernel_tag):
     """Per-launch DRAM bytes of the product kernels from the committed ncu summary,
-    or None when the kernel source changed since that capture."""
+    or None when the kernels changed since that capture."""
     path = os.path.join(ROOT, "profiles", "traffic_spectral_products.json")
     try:
         with open(path) as f:
             rec = json.load(f)
+        if rec.get("source_hash") != kernel_source_hash(rec["kernels"]):
+            return None
     except Exception:
-        return None
-    if rec.get("source_hash") != spectral_hash():
         return None
     return rec.get(kernel_tag)
 
