@@ -153,9 +153,33 @@ bti_status bti_copy_K(bti_handle h, double* dst);
 bti_status bti_infer_map(bti_handle h, const double* d_obs, double* m_map, int64_t B,
                          int refine_iters);
 
+/* The online phase of Sec. 4, Phase 4 as one CUDA graph launch: m_map = G^* K^{-1}
+ * d_obs (with refine_iters refinement steps, as bti_infer_map) followed, when q_map
+ * is not NULL, by q_map = F_q m_map (as bti_predict_qoi), for B observation
+ * vectors.  The first call for a given (d_obs, m_map, q_map, B, refine_iters,
+ * stream) captures every launch of that sequence into a CUDA graph on the handle's
+ * stream, which must not be the legacy default stream (BTI_ERR_STATE otherwise);
+ * later calls with the same arguments replay it with a single graph launch.  The
+ * graph is rebuilt automatically after the operators, the noise or K change.  The
+ * buffers' contents may change between calls; their addresses may not (a new
+ * address triggers a new capture).  Kernel launches inside the graph are not
+ * counted or timed by bti_profile_read. */
+bti_status bti_online(bti_handle h, const double* d_obs, double* m_map, double* q_map, int64_t B,
+                      int refine_iters);
+
 /* q_map = F_q m_map (Eq. (4.2)): m_map [B][N_t][N_m] -> q_map [B][N_t][N_q],
  * both double.  Requires FQ. */
 bti_status bti_predict_qoi(bti_handle h, const double* m_map, double* q_map, int64_t B);
+
+/* Project autotuner: time candidate launch shapes of the hot kernels for operator
+ * `op` with B vectors per call, on this handle's stored operator and device, and
+ * keep the fastest for every later call of the same storage tier: column pairs per
+ * FFT CTA, columns per CTA of the forward product, columns per thread of the
+ * single-vector adjoint product (coordinate search, median of 3 timed runs).
+ * Uses zeroed stand-in vectors it allocates and frees itself; synchronises.
+ * report (host, may be NULL) receives a JSON summary of the timings and choices,
+ * truncated to report_len - 1 bytes. */
+bti_status bti_autotune(bti_handle h, bti_op op, int64_t B, char* report, int64_t report_len);
 
 /* Kernel classes for bti_profile_read. */
 typedef enum {

@@ -68,6 +68,8 @@ def lib():
         "bti_copy_K": ([vp, vp], st),
         "bti_infer_map": ([vp, vp, vp, i64, ip], st),
         "bti_predict_qoi": ([vp, vp, vp, i64], st),
+        "bti_online": ([vp, vp, vp, vp, i64, ip], st),
+        "bti_autotune": ([vp, ip, i64, ctypes.c_char_p, i64], st),
         "bti_sync": ([vp], st),
         "bti_profile_enable": ([vp, ip], st),
         "bti_profile_read": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
@@ -244,6 +246,28 @@ class Handle:
             raise ValueError("m_map and q_map batch sizes differ")
         self._check(lib().bti_predict_qoi(self._h, _ptr(m_map), _ptr(q_map), B))
         return q_map
+
+    def online(self, d_obs, m_map, q_map=None, refine_iters=0):
+        """m_map (and q_map) for a batch of observations as one CUDA-graph launch (bti_online)."""
+        self._tensor(d_obs, (self.Nt, self.Nd), "d_obs")
+        self._tensor(m_map, (self.Nt, self.Nm), "m_map")
+        B = self._batch(d_obs, 2)
+        if self._batch(m_map, 2) != B:
+            raise ValueError("d_obs and m_map batch sizes differ")
+        if q_map is not None:
+            self._tensor(q_map, (self.Nt, self.Nq), "q_map")
+            if self._batch(q_map, 2) != B:
+                raise ValueError("m_map and q_map batch sizes differ")
+        self._check(lib().bti_online(self._h, _ptr(d_obs), _ptr(m_map), _ptr(q_map), B, int(refine_iters)))
+        return m_map
+
+    def autotune(self, op=OP_F, B=1):
+        """Pick launch shapes for operator `op` with B vectors per call; returns the timing report."""
+        import json
+
+        buf = ctypes.create_string_buffer(4096)
+        self._check(lib().bti_autotune(self._h, int(op), int(B), buf, len(buf)))
+        return json.loads(buf.value.decode())
 
     def sync(self):
         self._check(lib().bti_sync(self._h))

@@ -27,12 +27,20 @@ struct OpStore {
 
 }  // namespace
 
+// Launch shapes chosen by bti_autotune (0 = library default), per storage tier.
+struct Tune {
+  int fft_p = 0;  // column pairs per FFT CTA
+  int jc = 0;     // columns per CTA of the forward product
+  int vpt = 0;    // columns per thread of the adjoint product
+};
+
 struct bti_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   int64_t Nm = 0, Nd = 0, Nq = 0, Nt = 0, L = 0, nf = 0;
   FftPlan plan;
   OpStore op[3];
+  Tune tune[3];  // indexed by bti_prec
   bool noise_set = false;
   double sigma2 = 0.0;
   double* noise_diag = nullptr;  // [Nt][Nd] or null
@@ -44,6 +52,14 @@ struct bti_ctx {
   size_t ws_bytes = 0;
   double* wsolve = nullptr;  // dense-solve workspace
   size_t wsolve_bytes = 0;
+  // online phase captured as a CUDA graph (bti_online)
+  cudaGraphExec_t online_exec = nullptr;
+  const void* og_d = nullptr;
+  void* og_m = nullptr;
+  void* og_q = nullptr;
+  int64_t og_B = -1;
+  int og_refine = -1;
+  cudaStream_t og_stream = nullptr;
   // measurement hook (bti_profile_enable / bti_profile_read)
   bool prof_on = false;
   std::vector<cudaEvent_t> prof_ev;          // pool of 2 * kProfPairs events
@@ -157,7 +173,14 @@ bti_status make_spectral(bti_ctx* h, OpStore& o, const double* time_blocks) {
   return launched(h, "spectral blocks");
 }
 
+void drop_online_graph_any(bti_ctx* h) {
+  if (h->online_exec) cudaGraphExecDestroy(h->online_exec);
+  h->online_exec = nullptr;
+  h->og_B = -1;
+}
+
 bti_status store_op(bti_ctx* h, bti_op opi, const double* blocks, bti_prec store, bool keep_time) {
+  drop_online_graph_any(h);
   OpStore& o = h->op[opi];
   const int64_t R = rows_of(h, opi);
   if (R <= 0) return fail(h, BTI_ERR_SHAPE, "operator has zero rows (N_q = 0?)");
@@ -194,23 +217,30 @@ bti_status store_op(bti_ctx* h, bti_op opi, const double* blocks, bti_prec store
 // Forward FFT of B input vectors (io element type) into a spectrum of C2<T> elements.
 // The double-FP32 tier transforms in float pairs (FP64 accuracy on the FP32 pipes);
 // its spectra are stored as complex FP64.
+FftPlan tuned_plan(bti_ctx* h, const OpStore& o) {
+  FftPlan p = h->plan;
+  if (h->tune[o.prec].fft_p > 0 && h->tune[o.prec].fft_p <= p.P) p.P = h->tune[o.prec].fft_p;
+  return p;
+}
+
 template <typename T>
 void rfft_in(bti_ctx* h, const OpStore& o, const void* in, int64_t ld, int64_t bstride, C2<T>* X,
              int64_t Xbstride, int64_t ncols, int64_t B, bti_prec io) {
   const int Nt = (int)h->Nt;
   cudaStream_t s = h->stream;
+  const FftPlan plan = tuned_plan(h, o);
   if (o.prec == BTI_P_DF64) {
     if (io == BTI_P_F64)
-      PROF(h, BTI_K_RFFT, (launch_rfft_cols<ffloat, double, double>(h->plan, Nt, (const double*)in, ld, bstride,
+      PROF(h, BTI_K_RFFT, (launch_rfft_cols<ffloat, double, double>(plan, Nt, (const double*)in, ld, bstride,
                                                                      (double2*)X, Xbstride, ncols, B, s)));
     else
-      PROF(h, BTI_K_RFFT, (launch_rfft_cols<ffloat, float, double>(h->plan, Nt, (const float*)in, ld, bstride,
+      PROF(h, BTI_K_RFFT, (launch_rfft_cols<ffloat, float, double>(plan, Nt, (const float*)in, ld, bstride,
                                                                     (double2*)X, Xbstride, ncols, B, s)));
   } else if (io == BTI_P_F64) {
-    PROF(h, BTI_K_RFFT, (launch_rfft_cols<T, double, T>(h->plan, Nt, (const double*)in, ld, bstride, X, Xbstride,
+    PROF(h, BTI_K_RFFT, (launch_rfft_cols<T, double, T>(plan, Nt, (const double*)in, ld, bstride, X, Xbstride,
                                                          ncols, B, s)));
   } else {
-    PROF(h, BTI_K_RFFT, (launch_rfft_cols<T, float, T>(h->plan, Nt, (const float*)in, ld, bstride, X, Xbstride,
+    PROF(h, BTI_K_RFFT, (launch_rfft_cols<T, float, T>(plan, Nt, (const float*)in, ld, bstride, X, Xbstride,
                                                         ncols, B, s)));
   }
 }
@@ -221,19 +251,20 @@ void irfft_out(bti_ctx* h, const OpStore& o, const C2<T>* Y, int64_t ld, int64_t
                int64_t obstride, int64_t ncols, int64_t B, bti_prec io) {
   const int Nt = (int)h->Nt;
   cudaStream_t s = h->stream;
+  const FftPlan plan = tuned_plan(h, o);
   const double scale = 1.0 / (double)h->L;
   if (o.prec == BTI_P_DF64) {
     if (io == BTI_P_F64)
-      PROF(h, BTI_K_IRFFT, (launch_irfft_cols<ffloat, double, double>(h->plan, Nt, (const double2*)Y, ld, Ybstride,
+      PROF(h, BTI_K_IRFFT, (launch_irfft_cols<ffloat, double, double>(plan, Nt, (const double2*)Y, ld, Ybstride,
                                                                        (double*)out, obstride, ncols, B, scale, s)));
     else
-      PROF(h, BTI_K_IRFFT, (launch_irfft_cols<ffloat, double, float>(h->plan, Nt, (const double2*)Y, ld, Ybstride,
+      PROF(h, BTI_K_IRFFT, (launch_irfft_cols<ffloat, double, float>(plan, Nt, (const double2*)Y, ld, Ybstride,
                                                                       (float*)out, obstride, ncols, B, scale, s)));
   } else if (io == BTI_P_F64) {
-    PROF(h, BTI_K_IRFFT, (launch_irfft_cols<T, T, double>(h->plan, Nt, Y, ld, Ybstride, (double*)out, obstride,
+    PROF(h, BTI_K_IRFFT, (launch_irfft_cols<T, T, double>(plan, Nt, Y, ld, Ybstride, (double*)out, obstride,
                                                            ncols, B, scale, s)));
   } else {
-    PROF(h, BTI_K_IRFFT, (launch_irfft_cols<T, T, float>(h->plan, Nt, Y, ld, Ybstride, (float*)out, obstride,
+    PROF(h, BTI_K_IRFFT, (launch_irfft_cols<T, T, float>(plan, Nt, Y, ld, Ybstride, (float*)out, obstride,
                                                           ncols, B, scale, s)));
   }
 }
@@ -254,10 +285,11 @@ bti_status apply_fwd_t(bti_ctx* h, const OpStore& o, const void* in, void* out, 
   rfft_in<T>(h, o, in, Nm, Nt * Nm, mhat, nf * Nm, Nm, B, io);
   if (o.prec == BTI_P_DF64)
     PROF(h, BTI_K_PROD_FWD, launch_prod_fwd_df64((const float4*)o.hat, (const double2*)mhat, (double2*)part, nf,
-                                                 R, Nm, B, s));
+                                                 R, Nm, B, s, h->tune[o.prec].jc));
   else
-    PROF(h, BTI_K_PROD_FWD, (launch_prod_fwd<T, T>((const C2<T>*)o.hat, mhat, part, nf, R, Nm, B, s)));
-  PROF(h, BTI_K_REDUCE, (launch_reduce_chunks<T>(part, dhat, nf, R, Nm, B, s)));
+    PROF(h, BTI_K_PROD_FWD, (launch_prod_fwd<T, T>((const C2<T>*)o.hat, mhat, part, nf, R, Nm, B, s,
+                                                   h->tune[o.prec].jc)));
+  PROF(h, BTI_K_REDUCE, (launch_reduce_chunks<T>(part, dhat, nf, R, Nm, B, s, h->tune[o.prec].jc)));
   irfft_out<T>(h, o, dhat, R, nf * R, out, Nt * R, R, B, io);
   return launched(h, "forward Toeplitz product");
 }
@@ -276,9 +308,10 @@ bti_status apply_adj_t(bti_ctx* h, const OpStore& o, const void* in, void* out, 
   rfft_in<T>(h, o, in, R, Nt * R, dhat, nf * R, R, B, io);
   if (o.prec == BTI_P_DF64)
     PROF(h, BTI_K_PROD_ADJ, launch_prod_adj_df64((const float4*)o.hat, (const double2*)dhat, (double2*)mhat, nf,
-                                                 R, Nm, B, s));
+                                                 R, Nm, B, s, h->tune[o.prec].vpt));
   else
-    PROF(h, BTI_K_PROD_ADJ, (launch_prod_adj<T, T>((const C2<T>*)o.hat, dhat, mhat, nf, R, Nm, B, s)));
+    PROF(h, BTI_K_PROD_ADJ, (launch_prod_adj<T, T>((const C2<T>*)o.hat, dhat, mhat, nf, R, Nm, B, s,
+                                                   h->tune[o.prec].vpt)));
   irfft_out<T>(h, o, mhat, Nm, nf * Nm, out, Nt * Nm, Nm, B, io);
   return launched(h, "adjoint Toeplitz product");
 }
@@ -296,6 +329,33 @@ bti_status apply_op(bti_ctx* h, bti_op opi, bool adjoint, const void* in, void* 
   if (o.prec != BTI_P_F32)  // FP64 and double-FP32 tiers: FFTs and vectors in FP64
     return adjoint ? apply_adj_t<double>(h, o, in, out, B, io) : apply_fwd_t<double>(h, o, in, out, B, io);
   return adjoint ? apply_adj_t<float>(h, o, in, out, B, io) : apply_fwd_t<float>(h, o, in, out, B, io);
+}
+
+}  // namespace
+
+namespace {
+
+// Median device time (ms) of `reps` runs of fn on the handle's stream, after one warm-up.
+template <typename Fn>
+float time_ms(bti_ctx* h, Fn fn, int reps) {
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  fn();
+  float t[8];
+  for (int r = 0; r < reps; ++r) {
+    cudaEventRecord(e0, h->stream);
+    fn();
+    cudaEventRecord(e1, h->stream);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&t[r], e0, e1);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (int i = 0; i < reps; ++i)
+    for (int j = i + 1; j < reps; ++j)
+      if (t[j] < t[i]) { float x = t[i]; t[i] = t[j]; t[j] = x; }
+  return t[reps / 2];
 }
 
 }  // namespace
@@ -364,6 +424,7 @@ bti_status bti_destroy(bti_handle h) {
   dev_freep(h->status);
   dev_free(h->ws);
   dev_freep(h->wsolve);
+  drop_online_graph_any(h);
   dev_freep(h->plan.tw64);
   dev_freep(h->plan.tw32);
   dev_freep(h->plan.twff);
@@ -482,6 +543,7 @@ bti_status bti_set_noise(bti_handle h, double sigma2, const double* diag) {
   bti_status st = check_handle(h);
   if (st != BTI_OK) return st;
   if (!diag && !(sigma2 > 0.0)) return fail(h, BTI_ERR_ARG, "set_noise: sigma2 must be > 0");
+  drop_online_graph_any(h);
   dev_freep(h->noise_diag);
   h->sigma2 = sigma2;
   if (diag) {
@@ -516,6 +578,7 @@ bti_status bti_build_K(bti_handle h, int64_t col_block) {
   if (st != BTI_OK) return st;
   if (col_block < 0) return fail(h, BTI_ERR_ARG, "build_K: col_block < 0");
   if (col_block == 0) col_block = 512;
+  drop_online_graph_any(h);
   const OpStore& F = h->op[BTI_OP_F];
   const OpStore& G = h->op[BTI_OP_G];
   if (!F.set || !G.set || !F.time || !G.time) return fail(h, BTI_ERR_STATE, "build_K: F and G blocks required");
@@ -582,7 +645,7 @@ bti_status bti_copy_K(bti_handle h, double* dst) {
                                        h->stream), "copy_K");
 }
 
-bti_status bti_infer_map(bti_handle h, const double* d_obs, double* m_map, int64_t B, int refine_iters) {
+static bti_status infer_map_impl(bti_handle h, const double* d_obs, double* m_map, int64_t B, int refine_iters) {
   bti_status st = check_handle(h);
   if (st != BTI_OK) return st;
   if (B < 0 || refine_iters < 0) return fail(h, BTI_ERR_ARG, "infer_map: bad B or refine_iters");
@@ -627,8 +690,176 @@ bti_status bti_infer_map(bti_handle h, const double* d_obs, double* m_map, int64
   return apply_op(h, BTI_OP_G, true, x, m_map, B, BTI_P_F64, "infer_map G*");
 }
 
+bti_status bti_infer_map(bti_handle h, const double* d_obs, double* m_map, int64_t B, int refine_iters) {
+  return infer_map_impl(h, d_obs, m_map, B, refine_iters);
+}
+
 bti_status bti_predict_qoi(bti_handle h, const double* m_map, double* q_map, int64_t B) {
   return apply_op(h, BTI_OP_FQ, false, m_map, q_map, B, BTI_P_F64, "predict_qoi");
+}
+
+// Workspace the online phase needs for B vectors, allocated before a capture.
+static bti_status reserve_online(bti_ctx* h, int64_t B) {
+  const int64_t n = h->Nt * h->Nd;
+  size_t need = sizeof(double) * ((size_t)2 * B * n + trsm_work_elems(n, B));
+  size_t chol = sizeof(double) * (size_t)n * kCholNB;
+  bti_status st = ensure(h, (void**)&h->wsolve, &h->wsolve_bytes, need > chol ? need : chol, "solve workspace");
+  if (st != BTI_OK) return st;
+  // spectral workspace: the larger of an adjoint (G*) and a forward (F, F_q) product
+  const int64_t nf = h->nf, Nm = h->Nm;
+  size_t adj = 16 * ((size_t)B * nf * Nm + (size_t)B * nf * h->Nd);
+  size_t fwd = 0;
+  for (int op = 0; op < 3; ++op) {
+    if (op == BTI_OP_G || !h->op[op].set) continue;
+    int64_t R = h->op[op].R;
+    size_t f = 16 * ((size_t)B * nf * Nm + prod_fwd_partial_elems(nf, R, Nm, B) + (size_t)B * nf * R);
+    if (f > fwd) fwd = f;
+  }
+  size_t ws = adj > fwd ? adj : fwd;
+  return ensure(h, &h->ws, &h->ws_bytes, ws, "workspace");
+}
+
+bti_status bti_online(bti_handle h, const double* d_obs, double* m_map, double* q_map, int64_t B,
+                      int refine_iters) {
+  bti_status st = check_handle(h);
+  if (st != BTI_OK) return st;
+  if (B <= 0 || refine_iters < 0) return fail(h, BTI_ERR_ARG, "online: B must be > 0 and refine_iters >= 0");
+  if (!d_obs || !m_map) return fail(h, BTI_ERR_ARG, "online: null pointer");
+  if (!h->K_factored) return fail(h, BTI_ERR_STATE, "online: K not factored");
+  if (!h->op[BTI_OP_G].set) return fail(h, BTI_ERR_STATE, "online: G blocks not set");
+  if (q_map && !h->op[BTI_OP_FQ].set) return fail(h, BTI_ERR_STATE, "online: F_q blocks not set");
+  if (!h->stream) return fail(h, BTI_ERR_STATE, "online: graph capture needs a non-default stream");
+  const bool same = h->online_exec && h->og_d == d_obs && h->og_m == m_map && h->og_q == q_map && h->og_B == B &&
+                    h->og_refine == refine_iters && h->og_stream == h->stream;
+  if (!same) {
+    drop_online_graph_any(h);
+    st = reserve_online(h, B);
+    if (st != BTI_OK) return st;
+    const bool prof = h->prof_on;
+    h->prof_on = false;  // no event records inside the graph
+    st = cuda_check(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    if (st != BTI_OK) {
+      h->prof_on = prof;
+      return st;
+    }
+    bti_status run = infer_map_impl(h, d_obs, m_map, B, refine_iters);
+    if (run == BTI_OK && q_map) run = apply_op(h, BTI_OP_FQ, false, m_map, q_map, B, BTI_P_F64, "online F_q");
+    cudaGraph_t graph = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(h->stream, &graph);
+    h->prof_on = prof;
+    if (run != BTI_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return run;
+    }
+    st = cuda_check(h, ee, "end capture");
+    if (st != BTI_OK) return st;
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    st = cuda_check(h, ie, "instantiate online graph");
+    if (st != BTI_OK) return st;
+    h->online_exec = exec;
+    h->og_d = d_obs;
+    h->og_m = m_map;
+    h->og_q = q_map;
+    h->og_B = B;
+    h->og_refine = refine_iters;
+    h->og_stream = h->stream;
+  }
+  return cuda_check(h, cudaGraphLaunch(h->online_exec, h->stream), "launch online graph");
+}
+
+bti_status bti_autotune(bti_handle h, bti_op op, int64_t B, char* report, int64_t report_len) {
+  bti_status st = check_handle(h);
+  if (st != BTI_OK) return st;
+  if (op < BTI_OP_F || op > BTI_OP_FQ || B <= 0) return fail(h, BTI_ERR_ARG, "autotune: bad op or B");
+  OpStore& o = h->op[op];
+  if (!o.set) return fail(h, BTI_ERR_STATE, "autotune: operator blocks not set");
+  const int64_t Nt = h->Nt, Nm = h->Nm, R = o.R;
+  // zeroed stand-in vectors (values do not affect the timing of these kernels)
+  double *vin = nullptr, *vout = nullptr;
+  size_t nvec = (size_t)B * Nt * Nm;
+  st = dev_alloc(h, (void**)&vin, sizeof(double) * nvec, "autotune vectors");
+  if (st != BTI_OK) return st;
+  st = dev_alloc(h, (void**)&vout, sizeof(double) * nvec, "autotune vectors");
+  if (st != BTI_OK) { dev_freep(vin); return st; }
+  cudaMemsetAsync(vin, 0, sizeof(double) * nvec, h->stream);
+  cudaMemsetAsync(vout, 0, sizeof(double) * nvec, h->stream);
+  const bool prof = h->prof_on;
+  h->prof_on = false;
+  Tune& t = h->tune[o.prec];
+  const Tune saved = t;
+  auto fwd = [&]() { apply_op(h, op, false, vin, vout, B, BTI_P_F64, "autotune"); };
+  auto adj = [&]() { apply_op(h, op, true, vout, vin, B, BTI_P_F64, "autotune"); };
+  std::string rep = "{\"op\": " + std::to_string((int)op) + ", \"tier\": " + std::to_string((int)o.prec) +
+                    ", \"B\": " + std::to_string(B);
+  // 1. column pairs per FFT CTA (forward call: dominated by the FFT of the long vector)
+  {
+    int best = 0;
+    float best_ms = 1e30f;
+    rep += ", \"fft_p\": {";
+    bool first = true;
+    for (int p = h->plan.P; p >= 1; p /= 2) {
+      t.fft_p = p;
+      float ms = time_ms(h, fwd, 3);
+      rep += std::string(first ? "" : ", ") + "\"" + std::to_string(p) + "\": " + std::to_string(ms);
+      first = false;
+      if (ms < best_ms) { best_ms = ms; best = p; }
+      if (p <= h->plan.P / 4) break;
+    }
+    t.fft_p = best;
+    rep += "}, \"fft_p_chosen\": " + std::to_string(best);
+  }
+  // 2. columns per CTA of the forward product
+  {
+    const int cand[4] = {512, 1024, 2048, 4096};
+    int best = 0;
+    float best_ms = 1e30f;
+    rep += ", \"jc\": {";
+    for (int c = 0; c < 4; ++c) {
+      if (c > 0 && cand[c - 1] >= Nm) break;
+      t.jc = cand[c];
+      float ms = time_ms(h, fwd, 3);
+      rep += std::string(c ? ", " : "") + "\"" + std::to_string(cand[c]) + "\": " + std::to_string(ms);
+      if (ms < best_ms) { best_ms = ms; best = cand[c]; }
+    }
+    t.jc = best;
+    rep += "}, \"jc_chosen\": " + std::to_string(best);
+  }
+  // 3. columns per thread of the adjoint product (single-vector kernel)
+  if (B < 4) {
+    const int cand[3] = {2, 4, 8};
+    int best = 0;
+    float best_ms = 1e30f;
+    rep += ", \"vpt\": {";
+    for (int c = 0; c < 3; ++c) {
+      t.vpt = cand[c];
+      float ms = time_ms(h, adj, 3);
+      rep += std::string(c ? ", " : "") + "\"" + std::to_string(cand[c]) + "\": " + std::to_string(ms);
+      if (ms < best_ms) { best_ms = ms; best = cand[c]; }
+    }
+    t.vpt = best;
+    rep += "}, \"vpt_chosen\": " + std::to_string(best);
+  }
+  rep += "}";
+  h->prof_on = prof;
+  (void)R;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  dev_freep(vin);
+  dev_freep(vout);
+  st = launched(h, "autotune");
+  if (st == BTI_OK && e != cudaSuccess) st = cuda_check(h, e, "autotune sync");
+  if (st != BTI_OK) {
+    t = saved;
+    return st;
+  }
+  if (report && report_len > 0) {
+    size_t nc = rep.size() < (size_t)(report_len - 1) ? rep.size() : (size_t)(report_len - 1);
+    memcpy(report, rep.data(), nc);
+    report[nc] = 0;
+  }
+  return BTI_OK;
 }
 
 bti_status bti_sync(bti_handle h) {

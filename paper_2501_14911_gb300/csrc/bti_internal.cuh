@@ -99,24 +99,26 @@ void launch_irfft_cols(const FftPlan& p, int Nt, const C2<TYI>* X, int64_t ld, i
 
 // Spectral block products (spectral.cu).
 // Forward: dhat[b][w][i] = sum_j Fhat[w][i][j] mhat[b][w][j]  (T compute, TS storage)
+// jc: columns per CTA (0 = tier default; else a multiple of 256, >= 512), the tuning knob
 template <typename T, typename TS>
 void launch_prod_fwd(const C2<TS>* Fhat, const C2<T>* mhat, C2<T>* partial,
-                     int64_t nf, int64_t R, int64_t Nm, int64_t B, cudaStream_t s);
-// dhat[b][w][i] = sum over the forward product's chunk partials (fixed order)
+                     int64_t nf, int64_t R, int64_t Nm, int64_t B, cudaStream_t s, int jc = 0);
+// dhat[b][w][i] = sum over the forward product's chunk partials (fixed order); jc as above
 template <typename T>
 void launch_reduce_chunks(const C2<T>* partial, C2<T>* dhat, int64_t nf, int64_t R, int64_t Nm,
-                          int64_t B, cudaStream_t s);
+                          int64_t B, cudaStream_t s, int jc = 0);
 size_t prod_fwd_partial_elems(int64_t nf, int64_t R, int64_t Nm, int64_t B);
 // Double-FP32 tier: spectral blocks as (re_hi, re_lo, im_hi, im_lo) float quads.
 void launch_split_df64(void* hat, int64_t n, cudaStream_t s);  // in place, from complex FP64
 void launch_prod_fwd_df64(const float4* Fhat, const double2* mhat, double2* partial, int64_t nf,
-                          int64_t R, int64_t Nm, int64_t B, cudaStream_t s);
+                          int64_t R, int64_t Nm, int64_t B, cudaStream_t s, int jc = 0);
 void launch_prod_adj_df64(const float4* Fhat, const double2* dhat, double2* mhat, int64_t nf, int64_t R,
-                          int64_t Nm, int64_t B, cudaStream_t s);
+                          int64_t Nm, int64_t B, cudaStream_t s, int vpt = 0);
 // Adjoint: mhat[b][w][j] = sum_i conj(Fhat[w][i][j]) dhat[b][w][i]
+// vpt: columns per thread for single-vector calls (2, 4, 8; 0 = default)
 template <typename T, typename TS>
 void launch_prod_adj(const C2<TS>* Fhat, const C2<T>* dhat, C2<T>* mhat,
-                     int64_t nf, int64_t R, int64_t Nm, int64_t B, cudaStream_t s);
+                     int64_t nf, int64_t R, int64_t Nm, int64_t B, cudaStream_t s, int vpt = 0);
 
 // Dense FP64 (dense.cu)
 // C[b] = alpha * A[b] * op(B[b]) + beta * C[b]; A is M x K (lda), op(B) is K x N:

@@ -9,36 +9,53 @@
 
 namespace bti {
 
-// ------------------------------------------------------------------ GEMM (FP64)
-// 64 x 64 output tile per CTA, k-step 16, 256 threads each owning a 4 x 4
-// sub-tile at rows ty + 16 a and columns tx + 16 b (conflict-free smem reads).
-constexpr int GBM = 64, GBN = 64, GBK = 16;
+// 0: choose the GEMM tile by grid size; 16 / 32 / 64: force that tile (tuning hook).
+int g_gemm_tile_override = 0;
 
-template <bool TRANSB>
+static int num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+// ------------------------------------------------------------------ GEMM (FP64)
+// BM x BN output tile per CTA, k-step 16, 256 threads each owning a TM x TN
+// sub-tile at rows ty + (BM/TM) a and columns tx + (BN/TN) b (conflict-free smem
+// reads).  Three shapes: 64x64 (4x4 per thread) for large products, 32x32 (2x2)
+// and 16x16 (1x1) so that small outputs still spread over many SMs.
+constexpr int GBK = 16;
+
+template <bool TRANSB, int BM, int BN>
 __global__ void __launch_bounds__(256)
 gemm_f64_kernel(int64_t M, int64_t N, int64_t K, double alpha, const double* __restrict__ A,
                 int64_t lda, int64_t sA, const double* __restrict__ Bm, int64_t ldb, int64_t sB,
                 double beta, double* __restrict__ C, int64_t ldc, int64_t sC, int64_t batch,
                 bool lower_only) {
-  __shared__ double As[GBK][GBM + 1];
-  __shared__ double Bs[GBK][GBN + 1];
-  const int64_t m0 = (int64_t)blockIdx.x * GBM;
-  const int64_t n0 = (int64_t)blockIdx.y * GBN;
-  if (lower_only && blockIdx.x < blockIdx.y) return;
+  constexpr int TM = BM / 16, TN = BN / 16;
+  __shared__ double As[GBK][BM + 1];
+  __shared__ double Bs[GBK][BN + 1];
+  const int64_t m0 = (int64_t)blockIdx.x * BM;
+  const int64_t n0 = (int64_t)blockIdx.y * BN;
+  if (lower_only && m0 + BM - 1 < n0) return;  // tile strictly above the diagonal
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   for (int64_t bz = blockIdx.z; bz < batch; bz += gridDim.z) {
     const double* Ab = A + bz * sA;
     const double* Bb = Bm + bz * sB;
     double* Cb = C + bz * sC;
-    double acc[4][4];
+    double acc[TM][TN];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < TM; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+      for (int b = 0; b < TN; ++b) acc[a][b] = 0.0;
     for (int64_t k0 = 0; k0 < K; k0 += GBK) {
-      // A tile: 64 rows x 16 k, element (r, c) at A[m0 + r][k0 + c]
+      // A tile: BM rows x 16 k, element (r, c) at A[m0 + r][k0 + c]
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
+      for (int e = 0; e < (BM * GBK) / 256; ++e) {
         int idx = threadIdx.x + 256 * e;
         int r = idx >> 4, c = idx & 15;
         int64_t gm = m0 + r, gk = k0 + c;
@@ -46,7 +63,7 @@ gemm_f64_kernel(int64_t M, int64_t N, int64_t K, double alpha, const double* __r
       }
       if (TRANSB) {
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
+        for (int e = 0; e < (BN * GBK) / 256; ++e) {
           int idx = threadIdx.x + 256 * e;
           int r = idx >> 4, c = idx & 15;
           int64_t gn = n0 + r, gk = k0 + c;
@@ -54,9 +71,9 @@ gemm_f64_kernel(int64_t M, int64_t N, int64_t K, double alpha, const double* __r
         }
       } else {
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
+        for (int e = 0; e < (BN * GBK) / 256; ++e) {
           int idx = threadIdx.x + 256 * e;
-          int r = idx >> 6, c = idx & 63;
+          int r = idx / BN, c = idx % BN;
           int64_t gk = k0 + r, gn = n0 + c;
           Bs[r][c] = (gn < N && gk < K) ? Bb[gk * ldb + gn] : 0.0;
         }
@@ -64,24 +81,24 @@ gemm_f64_kernel(int64_t M, int64_t N, int64_t K, double alpha, const double* __r
       __syncthreads();
 #pragma unroll
       for (int kk = 0; kk < GBK; ++kk) {
-        double av[4], bv[4];
+        double av[TM], bv[TN];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) av[a] = As[kk][ty + 16 * a];
+        for (int a = 0; a < TM; ++a) av[a] = As[kk][ty + 16 * a];
 #pragma unroll
-        for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][tx + 16 * b];
+        for (int b = 0; b < TN; ++b) bv[b] = Bs[kk][tx + 16 * b];
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < TM; ++a)
 #pragma unroll
-          for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+          for (int b = 0; b < TN; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
       }
       __syncthreads();
     }
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
+    for (int a = 0; a < TM; ++a) {
       int64_t gm = m0 + ty + 16 * a;
       if (gm >= M) continue;
 #pragma unroll
-      for (int b = 0; b < 4; ++b) {
+      for (int b = 0; b < TN; ++b) {
         int64_t gn = n0 + tx + 16 * b;
         if (gn >= N) continue;
         double* cp = Cb + gm * ldc + gn;
@@ -184,12 +201,36 @@ int gemm_f64(bool transB, int64_t M, int64_t N, int64_t K, double alpha, const d
     }
     return 1;
   }
-  dim3 grid((unsigned)((M + GBM - 1) / GBM), (unsigned)((N + GBN - 1) / GBN),
-            (unsigned)std::min<int64_t>(batch, 65535));
-  if (transB)
-    gemm_f64_kernel<true><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, sA, Bm, ldb, sB, beta, C, ldc, sC, batch, lower_only);
+  // tile shape: the largest whose grid still gives every SM work, unless overridden
+  int tile = g_gemm_tile_override;
+  if (tile == 0) {
+    const int64_t want = 2 * (int64_t)num_sms();
+    tile = 16;
+    for (int t : {64, 32}) {
+      if (((M + t - 1) / t) * ((N + t - 1) / t) * std::min<int64_t>(batch, 65535) >= want) {
+        tile = t;
+        break;
+      }
+    }
+  }
+  const unsigned gz = (unsigned)std::min<int64_t>(batch, 65535);
+#define BTI_GEMM_LAUNCH(T_)                                                                                  \
+  {                                                                                                          \
+    dim3 grid((unsigned)((M + T_ - 1) / T_), (unsigned)((N + T_ - 1) / T_), gz);                            \
+    if (transB)                                                                                              \
+      gemm_f64_kernel<true, T_, T_><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, sA, Bm, ldb, sB, beta, C,   \
+                                                          ldc, sC, batch, lower_only);                       \
+    else                                                                                                     \
+      gemm_f64_kernel<false, T_, T_><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, sA, Bm, ldb, sB, beta, C,  \
+                                                           ldc, sC, batch, lower_only);                      \
+  }
+  if (tile == 64)
+    BTI_GEMM_LAUNCH(64)
+  else if (tile == 32)
+    BTI_GEMM_LAUNCH(32)
   else
-    gemm_f64_kernel<false><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, sA, Bm, ldb, sB, beta, C, ldc, sC, batch, lower_only);
+    BTI_GEMM_LAUNCH(16)
+#undef BTI_GEMM_LAUNCH
   return 1;
 }
 

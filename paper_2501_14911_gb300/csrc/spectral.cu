@@ -123,10 +123,12 @@ size_t prod_fwd_partial_elems(int64_t nf, int64_t R, int64_t Nm, int64_t B) {
   return (size_t)(B * nf * nchunk * R);
 }
 
+// Chunk of columns per CTA of the forward product: the tier default, or jc (a
+// multiple of 256, at least 512 so the partial-buffer bound holds) when given.
 template <typename T>
-static int fwd_nchunk(int64_t Nm, int64_t B, int* jc_out) {
+static int fwd_nchunk(int64_t Nm, int64_t B, int* jc_out, int jc = 0) {
   int bg = fwd_bg<T>(B);
-  int JC = fwd_jc<T>(bg);
+  int JC = jc > 0 ? jc : fwd_jc<T>(bg);
   if (Nm < JC) JC = (int)(((Nm + 31) / 32) * 32);
   if (jc_out) *jc_out = JC;
   return (int)((Nm + JC - 1) / JC);
@@ -134,21 +136,27 @@ static int fwd_nchunk(int64_t Nm, int64_t B, int* jc_out) {
 
 template <typename T>
 void launch_reduce_chunks(const C2<T>* partial, C2<T>* dhat, int64_t nf, int64_t R, int64_t Nm,
-                          int64_t B, cudaStream_t s) {
-  int nchunk = fwd_nchunk<T>(Nm, B, nullptr);
+                          int64_t B, cudaStream_t s, int jc) {
+  int nchunk = fwd_nchunk<T>(Nm, B, nullptr, jc);
   int64_t total = B * nf * R;
   reduce_chunks_kernel<T><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(partial, dhat, total, R, nchunk);
 }
 
 template <typename T, typename TS>
 void launch_prod_fwd(const C2<TS>* Fhat, const C2<T>* mhat, C2<T>* partial,
-                     int64_t nf, int64_t R, int64_t Nm, int64_t B, cudaStream_t s) {
+                     int64_t nf, int64_t R, int64_t Nm, int64_t B, cudaStream_t s, int jc) {
   int bg = fwd_bg<T>(B);
   int JC = 0;
-  int nchunk = fwd_nchunk<T>(Nm, B, &JC);
+  int nchunk = fwd_nchunk<T>(Nm, B, &JC, jc);
   size_t smem = sizeof(C2<T>) * (size_t)bg * JC;
   dim3 grid((unsigned)nchunk, (unsigned)nf, (unsigned)((B + bg - 1) / bg));
   constexpr int U1 = sizeof(C2<TS>) >= 16 ? 8 : 16;  // 128 bytes of loads per lane per step
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(prod_fwd_kernel<T, TS, 4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    cudaFuncSetAttribute(prod_fwd_kernel<T, TS, 1, U1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    attr = true;
+  }
   if (bg == 4)
     prod_fwd_kernel<T, TS, 4, 4><<<grid, 256, smem, s>>>(Fhat, mhat, partial, nf, R, Nm, B, JC, nchunk);
   else
@@ -210,34 +218,40 @@ prod_adj_kernel(const C2<TS>* __restrict__ Fhat, const C2<T>* __restrict__ dhat,
   }
 }
 
+template <typename T, typename TS, int BG, int VPT>
+static void adj_launch(const C2<TS>* Fhat, const C2<T>* dhat, C2<T>* mhat, int64_t nf, int64_t R, int64_t Nm,
+                       int64_t B, cudaStream_t s) {
+  size_t smem = sizeof(C2<T>) * (size_t)BG * R;
+  dim3 grid((unsigned)((Nm + 256 * VPT - 1) / (256 * VPT)), (unsigned)nf, (unsigned)((B + BG - 1) / BG));
+  prod_adj_kernel<T, TS, BG, VPT><<<grid, 256, smem, s>>>(Fhat, dhat, mhat, nf, R, Nm, B);
+}
+
+// vpt: columns per thread of the single-vector kernel (2, 4 or 8; 0 = default 4)
 template <typename T, typename TS>
 void launch_prod_adj(const C2<TS>* Fhat, const C2<T>* dhat, C2<T>* mhat,
-                     int64_t nf, int64_t R, int64_t Nm, int64_t B, cudaStream_t s) {
-  if (B >= 4) {
-    constexpr int BG = 4, VPT = 2;
-    size_t smem = sizeof(C2<T>) * (size_t)BG * R;
-    dim3 grid((unsigned)((Nm + 256 * VPT - 1) / (256 * VPT)), (unsigned)nf, (unsigned)((B + BG - 1) / BG));
-    prod_adj_kernel<T, TS, BG, VPT><<<grid, 256, smem, s>>>(Fhat, dhat, mhat, nf, R, Nm, B);
-  } else {
-    constexpr int BG = 1, VPT = 4;
-    size_t smem = sizeof(C2<T>) * (size_t)BG * R;
-    dim3 grid((unsigned)((Nm + 256 * VPT - 1) / (256 * VPT)), (unsigned)nf, (unsigned)B);
-    prod_adj_kernel<T, TS, BG, VPT><<<grid, 256, smem, s>>>(Fhat, dhat, mhat, nf, R, Nm, B);
-  }
+                     int64_t nf, int64_t R, int64_t Nm, int64_t B, cudaStream_t s, int vpt) {
+  if (B >= 4)
+    adj_launch<T, TS, 4, 2>(Fhat, dhat, mhat, nf, R, Nm, B, s);
+  else if (vpt == 2)
+    adj_launch<T, TS, 1, 2>(Fhat, dhat, mhat, nf, R, Nm, B, s);
+  else if (vpt == 8)
+    adj_launch<T, TS, 1, 8>(Fhat, dhat, mhat, nf, R, Nm, B, s);
+  else
+    adj_launch<T, TS, 1, 4>(Fhat, dhat, mhat, nf, R, Nm, B, s);
 }
 
 template void launch_prod_fwd<double, double>(const double2*, const double2*, double2*,
-                                              int64_t, int64_t, int64_t, int64_t, cudaStream_t);
+                                              int64_t, int64_t, int64_t, int64_t, cudaStream_t, int);
 template void launch_prod_fwd<float, float>(const float2*, const float2*, float2*,
-                                            int64_t, int64_t, int64_t, int64_t, cudaStream_t);
+                                            int64_t, int64_t, int64_t, int64_t, cudaStream_t, int);
 template void launch_reduce_chunks<double>(const double2*, double2*, int64_t, int64_t, int64_t, int64_t,
-                                           cudaStream_t);
+                                           cudaStream_t, int);
 template void launch_reduce_chunks<float>(const float2*, float2*, int64_t, int64_t, int64_t, int64_t,
-                                          cudaStream_t);
+                                          cudaStream_t, int);
 template void launch_prod_adj<double, double>(const double2*, const double2*, double2*,
-                                              int64_t, int64_t, int64_t, int64_t, cudaStream_t);
+                                              int64_t, int64_t, int64_t, int64_t, cudaStream_t, int);
 template void launch_prod_adj<float, float>(const float2*, const float2*, float2*,
-                                            int64_t, int64_t, int64_t, int64_t, cudaStream_t);
+                                            int64_t, int64_t, int64_t, int64_t, cudaStream_t, int);
 
 
 // ------------------------------------------------------------------ double-FP32 tier
@@ -394,13 +408,19 @@ prod_fwd_df64_kernel(const float4* __restrict__ Fhat, const double2* __restrict_
 }
 
 void launch_prod_fwd_df64(const float4* Fhat, const double2* mhat, double2* partial, int64_t nf,
-                          int64_t R, int64_t Nm, int64_t B, cudaStream_t s) {
+                          int64_t R, int64_t Nm, int64_t B, cudaStream_t s, int jc) {
   // chunking identical to the FP64 tier (the reduce pass and workspace sizes are shared)
   int bg = fwd_bg<double>(B);
   int JC = 0;
-  int nchunk = fwd_nchunk<double>(Nm, B, &JC);
+  int nchunk = fwd_nchunk<double>(Nm, B, &JC, jc);
   size_t smem = sizeof(float4) * (size_t)bg * JC;
   dim3 grid((unsigned)nchunk, (unsigned)nf, (unsigned)((B + bg - 1) / bg));
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(prod_fwd_df64_kernel<4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    cudaFuncSetAttribute(prod_fwd_df64_kernel<1, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    attr = true;
+  }
   if (bg == 4)
     prod_fwd_df64_kernel<4, 4><<<grid, 256, smem, s>>>(Fhat, mhat, partial, nf, R, Nm, B, JC, nchunk);
   else
@@ -467,19 +487,24 @@ prod_adj_df64_kernel(const float4* __restrict__ Fhat, const double2* __restrict_
   }
 }
 
+template <int BG, int VPT>
+static void adj_df64_launch(const float4* Fhat, const double2* dhat, double2* mhat, int64_t nf, int64_t R,
+                            int64_t Nm, int64_t B, cudaStream_t s) {
+  size_t smem = sizeof(float4) * (size_t)BG * R;
+  dim3 grid((unsigned)((Nm + 256 * VPT - 1) / (256 * VPT)), (unsigned)nf, (unsigned)((B + BG - 1) / BG));
+  prod_adj_df64_kernel<BG, VPT><<<grid, 256, smem, s>>>(Fhat, dhat, mhat, nf, R, Nm, B);
+}
+
 void launch_prod_adj_df64(const float4* Fhat, const double2* dhat, double2* mhat, int64_t nf, int64_t R,
-                          int64_t Nm, int64_t B, cudaStream_t s) {
-  if (B >= 4) {
-    constexpr int BG = 4, VPT = 2;
-    size_t smem = sizeof(float4) * (size_t)BG * R;
-    dim3 grid((unsigned)((Nm + 256 * VPT - 1) / (256 * VPT)), (unsigned)nf, (unsigned)((B + BG - 1) / BG));
-    prod_adj_df64_kernel<BG, VPT><<<grid, 256, smem, s>>>(Fhat, dhat, mhat, nf, R, Nm, B);
-  } else {
-    constexpr int BG = 1, VPT = 4;
-    size_t smem = sizeof(float4) * (size_t)BG * R;
-    dim3 grid((unsigned)((Nm + 256 * VPT - 1) / (256 * VPT)), (unsigned)nf, (unsigned)B);
-    prod_adj_df64_kernel<BG, VPT><<<grid, 256, smem, s>>>(Fhat, dhat, mhat, nf, R, Nm, B);
-  }
+                          int64_t Nm, int64_t B, cudaStream_t s, int vpt) {
+  if (B >= 4)
+    adj_df64_launch<4, 2>(Fhat, dhat, mhat, nf, R, Nm, B, s);
+  else if (vpt == 2)
+    adj_df64_launch<1, 2>(Fhat, dhat, mhat, nf, R, Nm, B, s);
+  else if (vpt == 8)
+    adj_df64_launch<1, 8>(Fhat, dhat, mhat, nf, R, Nm, B, s);
+  else
+    adj_df64_launch<1, 4>(Fhat, dhat, mhat, nf, R, Nm, B, s);
 }
 
 }  // namespace bti

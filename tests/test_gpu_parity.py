@@ -272,3 +272,67 @@ def test_df64_is_not_an_io_type():
     d = torch.zeros((1, 8, 3), dtype=torch.float64, device="cuda")
     assert bti.lib().bti_apply_F(h.raw, m.data_ptr(), d.data_ptr(), 1, bti.DF64) == 1
     h.close()
+
+
+def test_online_graph_matches_separate_calls_and_replays():
+    p, F, Fq, G, d_obs = tiny_problem()
+    h = make_handle(F, Fq, bti.DF64)
+    h.set_prior_se_grid(p.gx, p.gy, p.ell, p.sigma_p, bti.DF64)
+    h.set_noise(p.sigma2)
+    h.build_K()
+    h.factor_K()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        h.set_stream(stream)
+        d = cuda(np.concatenate([d_obs, 2.0 * d_obs]))
+        m = torch.empty((2, p.Nt, p.Nm), dtype=torch.float64, device="cuda")
+        q = torch.empty((2, p.Nt, p.Nq), dtype=torch.float64, device="cuda")
+        h.online(d, m, q)  # capture + first launch
+        m_or = oracle.map_point(F, G, p.sigma2, np.concatenate([d_obs, 2.0 * d_obs]))
+        assert relb(host(m), m_or) < 1e-12
+        assert relb(host(q), oracle.qoi_map(Fq, m_or)) < 1e-12
+        d.mul_(-0.5)  # same buffers, new contents: the graph is replayed
+        h.online(d, m, q)
+        assert relb(host(m), -0.5 * m_or) < 1e-12
+        assert relb(host(q), oracle.qoi_map(Fq, -0.5 * m_or)) < 1e-12
+        m2 = torch.empty_like(m)
+        h.online(d, m2, None, refine_iters=1)  # other arguments: a new capture
+        assert relb(host(m2), -0.5 * m_or) < 1e-12
+    torch.cuda.synchronize()
+    h.set_stream(torch.cuda.current_stream())
+    h.close()
+
+
+def test_online_graph_refuses_the_legacy_stream():
+    p, F, Fq, G, d_obs = tiny_problem()
+    h = make_handle(F, Fq)
+    h.set_prior_se_grid(p.gx, p.gy, p.ell, p.sigma_p)
+    h.set_noise(p.sigma2)
+    h.build_K()
+    h.factor_K()
+    d = cuda(d_obs)
+    m = torch.empty((1, p.Nt, p.Nm), dtype=torch.float64, device="cuda")
+    L = bti.lib()
+    assert L.bti_set_stream(h.raw, None) == 0
+    assert L.bti_online(h.raw, d.data_ptr(), m.data_ptr(), None, 1, 0) == 3
+    h.close()
+
+
+@pytest.mark.parametrize("store", [bti.DF64, bti.F32], ids=["df64", "f32"])
+def test_autotune_keeps_results(store):
+    p = synthetic.small("tune", 8, 300, 13, 45, Nq=3)
+    F = p.blocks_F()
+    h = make_handle(F, None, store)
+    rep = h.autotune(bti.OP_F, 1)
+    assert rep["op"] == 0 and rep["fft_p_chosen"] >= 1 and rep["jc_chosen"] >= 512 and rep["vpt_chosen"] in (2, 4, 8)
+    dt = torch.float32 if store == bti.F32 else torch.float64
+    m = p.vectors_m(1)
+    d = p.vectors_d(1)
+    od = torch.empty((1, p.Nt, p.Nd), dtype=dt, device="cuda")
+    om = torch.empty((1, p.Nt, p.Nm), dtype=dt, device="cuda")
+    mg, dg = cuda(m, dt), cuda(d, dt)
+    h.apply_F(mg, od)
+    h.apply_FT(dg, om)
+    assert relb(host(od), oracle.p2o_apply(F, host(mg))) < TOL[store]
+    assert relb(host(om), oracle.p2o_apply_adjoint(F, host(dg))) < TOL[store]
+    h.close()
