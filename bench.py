@@ -320,7 +320,7 @@ def run_ours(args):
         nf = p.Nt + 1
         Fhat = nf * p.Nd * p.Nm * csize
         mhat = nf * p.Nm * 16  # the frequency-domain vector (FP64 for f64/df64, read or written)
-        if kind == "f32":
+        if kind in ("f32", "f16"):
             mhat = nf * p.Nm * 8
         bytes_launch = Fhat + mhat
         elems = nf * p.Nd * p.Nm
@@ -332,7 +332,7 @@ def run_ours(args):
         if kind == "f64":
             work, peak, unit, src = 8.0 * elems, FP64_TFLOPS * 1e12, "TFLOP/s", \
                 "FP64 DFMA throughput probe (2 DFMA/clk/SM x 152 SMs)"
-        elif kind == "f32":
+        elif kind in ("f32", "f16"):
             work, peak, unit, src = 8.0 * elems, FP32_TFLOPS * 1e12, "TFLOP/s", \
                 "FP32 FFMA: 128 lanes/clk/SM x 152 SMs x 2 flop at ~1.93 GHz (probe: 75 TFLOP/s)"
         else:
@@ -352,7 +352,7 @@ def run_ours(args):
         return dict({"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                       "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})"}, **common)
 
-    tiers = {"df64": (bti.DF64, 16, 8), "f64": (bti.F64, 16, 8), "f32": (bti.F32, 8, 4)}
+    tiers = {"df64": (bti.DF64, 16, 8), "f64": (bti.F64, 16, 8), "f32": (bti.F32, 8, 4), "f16": (bti.F16, 4, 4)}
     res = {}
     clk = None
     e2e = None
@@ -361,7 +361,7 @@ def run_ours(args):
         h.set_blocks(bti.OP_F, Fd, prec)
         tune = h.autotune(bti.OP_F, 1)  # launch shapes for single-vector calls (outside the timed region)
         torch.cuda.synchronize()
-        vecs = (m32, d32, od32, om32) if name == "f32" else (m64, d64, od64, om64)
+        vecs = (m32, d32, od32, om32) if name in ("f32", "f16") else (m64, d64, od64, om64)
         headline = name == "df64"
         if headline:
             clocks = Clocks(uuid)
@@ -531,12 +531,42 @@ def online_block(args, dev, stream):
         torch.cuda.synchronize()
     lat_graph = g0.elapsed_time(g1) / reps
     h.set_stream(stream)
+    # mixed-precision form: K assembled with FP32 products, FP64 Cholesky, and
+    # refinement of the solve with double-FP32 operators (FP64-level result)
+    refine = 3
+    torch.cuda.synchronize()
+    e[0].record(stream)
+    h.build_K_prec(p.col_block, bti.F32)
+    e[1].record(stream)
+    h.factor_K()
+    e[2].record(stream)
+    torch.cuda.synchronize()
+    t_build_mixed = e[0].elapsed_time(e[1])
+    t_factor_mixed = e[1].elapsed_time(e[2])
+    for _ in range(2):
+        h.infer_map(d_obs, m_map, refine_iters=refine)
+        h.predict_qoi(m_map, q_map)
+    torch.cuda.synchronize()
+    e[0].record(stream)
+    for _ in range(reps):
+        h.infer_map(d_obs, m_map, refine_iters=refine)
+        h.predict_qoi(m_map, q_map)
+    e[1].record(stream)
+    torch.cuda.synchronize()
+    lat_mixed = e[0].elapsed_time(e[1]) / reps
     h.close()
     n = p.Nt * p.Nd
     return {"workload": p.name, "obs_vectors": B, "K_n": n, "build_K_ms": t_build, "factor_K_ms": t_factor,
             "factor_tflops_f64": (n ** 3 / 3.0) / (t_factor * 1e-3) / 1e12,
             "m_map_plus_q_map_ms": lat, "ms_per_obs_vector": lat / B,
             "m_map_plus_q_map_graph_ms": lat_graph, "graph_ms_per_obs_vector": lat_graph / B,
+            "mixed": {"build_K_f32_ms": t_build_mixed, "factor_K_ms": t_factor_mixed, "refine_iters": refine,
+                      "m_map_plus_q_map_ms": lat_mixed,
+                      "offline_plus_online_ms": t_build_mixed + t_factor_mixed + lat_mixed,
+                      "plain_f64_offline_plus_online_ms": t_build + t_factor + lat,
+                      "accuracy": "FP64-level after refinement; tests/test_gpu_parity.py::"
+                                  "test_mixed_precision_solve_recovers_fp64 and tests/test_gpu_fullsize.py::"
+                                  "test_batched_mixed_precision_solve_full_size check 1e-12 / 1e-11 vs the oracle"},
             "accuracy": "K, Cholesky and solves FP64; G* and F_q products double-FP32; parity with the "
                         "oracle to 1e-12 in tests/test_gpu_parity.py"}
 

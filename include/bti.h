@@ -68,8 +68,13 @@ typedef enum { BTI_OP_F = 0, BTI_OP_G = 1, BTI_OP_FQ = 2 } bti_op;
  *             arithmetic on the FP32 pipes with error-free accumulation; FFTs
  *             and vectors FP64.  FP64-level accuracy (well inside 1e-12) at
  *             the HBM rate, where GB300's FP64 pipe would bind first.
- *             Valid as a storage tier only, not as an io type. */
-typedef enum { BTI_P_F64 = 0, BTI_P_F32 = 1, BTI_P_DF64 = 2 } bti_prec;
+ *             Valid as a storage tier only, not as an io type.
+ * BTI_P_F16 : spectral blocks as FP16 complex pairs (4 bytes per complex) with one
+ *             power-of-two FP32 scale per frequency row; products with FP32
+ *             accumulation, FFTs and vectors FP32.  About 1e-3 relative: the
+ *             low-precision operator of mixed-precision solves.  Storage tier only.
+ */
+typedef enum { BTI_P_F64 = 0, BTI_P_F32 = 1, BTI_P_DF64 = 2, BTI_P_F16 = 3 } bti_prec;
 
 /* Create a handle for N_m spatial parameters, N_d sensors, N_q QoI points and
  * N_t time steps on CUDA device `device`, issuing work on `cuda_stream`
@@ -133,6 +138,16 @@ bti_status bti_apply_Gstar(bti_handle h, const void* d, void* m, int64_t B, bti_
  * set_blocks are used) and set_noise.  col_block (> 0) is the column-panel
  * width of the assembly; 512 is the default when 0 is passed. */
 bti_status bti_build_K(bti_handle h, int64_t col_block);
+
+/* As bti_build_K, with the Gram product that assembles K computed in `assembly`
+ * precision: BTI_P_F64 (same as bti_build_K) or BTI_P_F32 (FP32 products and
+ * accumulation over N_m, about 1e-6 relative; K itself, its block-diagonal
+ * accumulation and the noise stay FP64).  The FP32 form is the low-precision half
+ * of a mixed-precision solve: factor it with bti_factor_K and call bti_infer_map
+ * with refine_iters > 0 and FP64-level (BTI_P_DF64 or BTI_P_F64) F and G operators,
+ * which recovers FP64-level m_map when kappa(K) times the assembly error is well
+ * below one. */
+bti_status bti_build_K_prec(bti_handle h, int64_t col_block, bti_prec assembly);
 
 /* Cholesky-factor K = L L^T in place (FP64, lower).  Synchronises; returns
  * BTI_ERR_NOT_SPD (message names the 1-based pivot) if a pivot is <= 0 or

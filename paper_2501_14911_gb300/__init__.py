@@ -21,6 +21,7 @@ from ._binding import (  # noqa: F401
     F64,
     F32,
     DF64,
+    F16,
     lib,
     lib_path,
     header_symbols,

@@ -13,7 +13,7 @@ HEADER = os.path.join(ROOT, "include", "bti.h")
 OP_F, OP_G, OP_FQ = 0, 1, 2
 # kernel classes of bti_profile_read
 KCLASSES = ("rfft", "prod_fwd", "reduce", "irfft", "prod_adj", "dense")
-F64, F32, DF64 = 0, 1, 2
+F64, F32, DF64, F16 = 0, 1, 2, 3
 
 STATUS = {
     0: "BTI_OK", 1: "BTI_ERR_ARG", 2: "BTI_ERR_SHAPE", 3: "BTI_ERR_STATE", 4: "BTI_ERR_CUDA",
@@ -64,6 +64,7 @@ def lib():
         "bti_apply_Fq": ([vp, vp, vp, i64, ip], st),
         "bti_apply_Gstar": ([vp, vp, vp, i64, ip], st),
         "bti_build_K": ([vp, i64], st),
+        "bti_build_K_prec": ([vp, i64, ip], st),
         "bti_factor_K": ([vp], st),
         "bti_copy_K": ([vp, vp], st),
         "bti_infer_map": ([vp, vp, vp, i64, ip], st),
@@ -215,6 +216,9 @@ class Handle:
 
     def build_K(self, col_block=512):
         self._check(lib().bti_build_K(self._h, int(col_block)))
+
+    def build_K_prec(self, col_block=512, assembly=F64):
+        self._check(lib().bti_build_K_prec(self._h, int(col_block), int(assembly)))
 
     def factor_K(self):
         self._check(lib().bti_factor_K(self._h))

@@ -22,6 +22,7 @@ struct OpStore {
   bti_prec prec = BTI_P_F64;
   int64_t R = 0;
   void* hat = nullptr;     // [nf][R][Nm] complex, storage tier
+  float* scale = nullptr;  // [nf][R] row scales of the FP16 tier
   double* time = nullptr;  // [Nt][R][Nm] FP64 time-domain copy (F and G only)
 };
 
@@ -40,7 +41,7 @@ struct bti_ctx {
   int64_t Nm = 0, Nd = 0, Nq = 0, Nt = 0, L = 0, nf = 0;
   FftPlan plan;
   OpStore op[3];
-  Tune tune[3];  // indexed by bti_prec
+  Tune tune[4];  // indexed by bti_prec
   bool noise_set = false;
   double sigma2 = 0.0;
   double* noise_diag = nullptr;  // [Nt][Nd] or null
@@ -147,8 +148,9 @@ bti_status ensure(bti_ctx* h, void** buf, size_t* have, size_t need, const char*
   return st;
 }
 
-size_t celem_size(bti_prec p) { return p == BTI_P_F32 ? 2 * sizeof(float) : 16; }
-bool prec_ok(int p) { return p == BTI_P_F64 || p == BTI_P_F32 || p == BTI_P_DF64; }
+size_t celem_size(bti_prec p) { return p == BTI_P_F32 ? 8 : (p == BTI_P_F16 ? 4 : 16); }
+bool prec_ok(int p) { return p == BTI_P_F64 || p == BTI_P_F32 || p == BTI_P_DF64 || p == BTI_P_F16; }
+bool double_path(bti_prec p) { return p == BTI_P_F64 || p == BTI_P_DF64; }  // FP64 FFTs and spectra
 bool io_ok(int p) { return p == BTI_P_F64 || p == BTI_P_F32; }
 
 int64_t rows_of(bti_ctx* h, bti_op op) { return op == BTI_OP_FQ ? h->Nq : h->Nd; }
@@ -162,6 +164,20 @@ bti_status check_handle(bti_ctx* h) {
 // spectral blocks of an op from FP64 time-domain blocks [Nt][R][Nm] (device)
 bti_status make_spectral(bti_ctx* h, OpStore& o, const double* time_blocks) {
   const int64_t cols = o.R * h->Nm;
+  if (o.prec == BTI_P_F16) {
+    // FP64 spectrum in a temporary, then per-row scaled FP16
+    double2* tmp = nullptr;
+    bti_status st = dev_alloc(h, (void**)&tmp, sizeof(double2) * (size_t)h->nf * cols, "spectral temporary");
+    if (st != BTI_OK) return st;
+    st = dev_alloc(h, (void**)&o.scale, sizeof(float) * (size_t)h->nf * o.R, "row scales");
+    if (st != BTI_OK) { dev_freep(tmp); return st; }
+    PROF(h, BTI_K_RFFT, (launch_rfft_cols<double, double, double>(h->plan, (int)h->Nt, time_blocks, cols, 0, tmp, 0,
+                                                                   cols, 1, h->stream)));
+    PROF(h, BTI_K_RFFT, launch_quantize_f16(tmp, o.hat, o.scale, h->nf * o.R, h->Nm, h->stream));
+    cudaStreamSynchronize(h->stream);
+    dev_freep(tmp);
+    return launched(h, "spectral blocks");
+  }
   if (o.prec != BTI_P_F32)
     PROF(h, BTI_K_RFFT, (launch_rfft_cols<double, double, double>(h->plan, (int)h->Nt, time_blocks, cols, 0,
                                                                    (double2*)o.hat, 0, cols, 1, h->stream)));
@@ -186,6 +202,7 @@ bti_status store_op(bti_ctx* h, bti_op opi, const double* blocks, bti_prec store
   if (R <= 0) return fail(h, BTI_ERR_SHAPE, "operator has zero rows (N_q = 0?)");
   dev_free(o.hat);
   dev_freep(o.time);
+  dev_freep(o.scale);
   o.set = false;
   o.R = R;
   o.prec = store;
@@ -286,6 +303,9 @@ bti_status apply_fwd_t(bti_ctx* h, const OpStore& o, const void* in, void* out, 
   if (o.prec == BTI_P_DF64)
     PROF(h, BTI_K_PROD_FWD, launch_prod_fwd_df64((const float4*)o.hat, (const double2*)mhat, (double2*)part, nf,
                                                  R, Nm, B, s, h->tune[o.prec].jc));
+  else if (o.prec == BTI_P_F16)
+    PROF(h, BTI_K_PROD_FWD, launch_prod_fwd_f16(o.hat, o.scale, (const float2*)mhat, (float2*)part, nf, R, Nm, B,
+                                                s, h->tune[o.prec].jc));
   else
     PROF(h, BTI_K_PROD_FWD, (launch_prod_fwd<T, T>((const C2<T>*)o.hat, mhat, part, nf, R, Nm, B, s,
                                                    h->tune[o.prec].jc)));
@@ -309,6 +329,9 @@ bti_status apply_adj_t(bti_ctx* h, const OpStore& o, const void* in, void* out, 
   if (o.prec == BTI_P_DF64)
     PROF(h, BTI_K_PROD_ADJ, launch_prod_adj_df64((const float4*)o.hat, (const double2*)dhat, (double2*)mhat, nf,
                                                  R, Nm, B, s, h->tune[o.prec].vpt));
+  else if (o.prec == BTI_P_F16)
+    PROF(h, BTI_K_PROD_ADJ, launch_prod_adj_f16(o.hat, o.scale, (const float2*)dhat, (float2*)mhat, nf, R, Nm, B,
+                                                s, h->tune[o.prec].vpt));
   else
     PROF(h, BTI_K_PROD_ADJ, (launch_prod_adj<T, T>((const C2<T>*)o.hat, dhat, mhat, nf, R, Nm, B, s,
                                                    h->tune[o.prec].vpt)));
@@ -326,7 +349,7 @@ bti_status apply_op(bti_ctx* h, bti_op opi, bool adjoint, const void* in, void* 
   if (!o.set) return fail(h, BTI_ERR_STATE, std::string(name) + ": operator blocks not set");
   if (B == 0) return BTI_OK;
   if (!in || !out) return fail(h, BTI_ERR_ARG, std::string(name) + ": null pointer");
-  if (o.prec != BTI_P_F32)  // FP64 and double-FP32 tiers: FFTs and vectors in FP64
+  if (double_path(o.prec))  // FP64 and double-FP32 tiers: FFT spectra in FP64
     return adjoint ? apply_adj_t<double>(h, o, in, out, B, io) : apply_fwd_t<double>(h, o, in, out, B, io);
   return adjoint ? apply_adj_t<float>(h, o, in, out, B, io) : apply_fwd_t<float>(h, o, in, out, B, io);
 }
@@ -417,6 +440,7 @@ bti_status bti_destroy(bti_handle h) {
   for (auto& o : h->op) {
     dev_free(o.hat);
     dev_freep(o.time);
+    dev_freep(o.scale);
   }
   dev_freep(h->noise_diag);
   dev_freep(h->K);
@@ -519,6 +543,7 @@ bti_status bti_set_prior_se_grid(bti_handle h, int gx, int gy, double ell, doubl
     OpStore& o = h->op[BTI_OP_G];
     dev_free(o.hat);
     dev_freep(o.time);
+    dev_freep(o.scale);
     o.set = false;
     o.R = h->Nd;
     o.prec = store;
@@ -573,7 +598,17 @@ bti_status bti_apply_Gstar(bti_handle h, const void* d, void* m, int64_t B, bti_
   return apply_op(h, BTI_OP_G, true, d, m, B, io, "apply_Gstar");
 }
 
-bti_status bti_build_K(bti_handle h, int64_t col_block) {
+static bti_status build_K_impl(bti_handle h, int64_t col_block, bti_prec assembly);
+
+bti_status bti_build_K(bti_handle h, int64_t col_block) { return build_K_impl(h, col_block, BTI_P_F64); }
+
+bti_status bti_build_K_prec(bti_handle h, int64_t col_block, bti_prec assembly) {
+  if (h && assembly != BTI_P_F64 && assembly != BTI_P_F32)
+    return fail(h, BTI_ERR_ARG, "build_K_prec: assembly precision must be BTI_P_F64 or BTI_P_F32");
+  return build_K_impl(h, col_block, assembly);
+}
+
+static bti_status build_K_impl(bti_handle h, int64_t col_block, bti_prec assembly) {
   bti_status st = check_handle(h);
   if (st != BTI_OK) return st;
   if (col_block < 0) return fail(h, BTI_ERR_ARG, "build_K: col_block < 0");
@@ -589,11 +624,27 @@ bti_status bti_build_K(bti_handle h, int64_t col_block) {
     if (st != BTI_OK) return st;
   }
   cudaStream_t s = h->stream;
-  // W = F_stack G_stack^T (lower block triangle), by column panels
-  for (int64_t c0 = 0; c0 < n; c0 += col_block) {
-    int64_t nc = (n - c0) < col_block ? (n - c0) : col_block;
-    count_dense(h, gemm_f64(true, n - c0, nc, h->Nm, 1.0, F.time + c0 * h->Nm, h->Nm, 0, G.time + c0 * h->Nm,
-                            h->Nm, 0, 0.0, h->K + c0 * n + c0, n, 0, 1, true, s));
+  if (assembly == BTI_P_F32) {
+    // low-precision assembly: W in FP32 from FP32 copies of the blocks (K stays FP64)
+    float* Ff = nullptr;
+    float* Gf = nullptr;
+    const size_t ne = (size_t)n * h->Nm;
+    st = dev_alloc(h, (void**)&Ff, sizeof(float) * 2 * ne, "FP32 blocks");
+    if (st != BTI_OK) return st;
+    Gf = Ff + ne;
+    int64_t nl = convert_f64_to_f32(F.time, Ff, (int64_t)ne, s);
+    nl += convert_f64_to_f32(G.time, Gf, (int64_t)ne, s);
+    nl += sgemm_nt_lower_to_f64(n, n, h->Nm, Ff, h->Nm, Gf, h->Nm, h->K, n, s);
+    count_dense(h, nl);
+    cudaStreamSynchronize(s);
+    dev_freep(Ff);
+  } else {
+    // W = F_stack G_stack^T (lower block triangle), by column panels
+    for (int64_t c0 = 0; c0 < n; c0 += col_block) {
+      int64_t nc = (n - c0) < col_block ? (n - c0) : col_block;
+      count_dense(h, gemm_f64(true, n - c0, nc, h->Nm, 1.0, F.time + c0 * h->Nm, h->Nm, 0, G.time + c0 * h->Nm,
+                              h->Nm, 0, 0.0, h->K + c0 * n + c0, n, 0, 1, true, s));
+    }
   }
   count_dense(h, k_diag_cumsum(h->K, h->Nt, h->Nd, h->sigma2, h->noise_diag, s));
   st = launched(h, "build_K");

@@ -114,6 +114,12 @@ void launch_prod_fwd_df64(const float4* Fhat, const double2* mhat, double2* part
                           int64_t R, int64_t Nm, int64_t B, cudaStream_t s, int jc = 0);
 void launch_prod_adj_df64(const float4* Fhat, const double2* dhat, double2* mhat, int64_t nf, int64_t R,
                           int64_t Nm, int64_t B, cudaStream_t s, int vpt = 0);
+// FP16 tier: spectral blocks as FP16 complex pairs with one FP32 power-of-two scale per row.
+void launch_quantize_f16(const double2* src, void* dst, float* scale, int64_t rows, int64_t Nm, cudaStream_t s);
+void launch_prod_fwd_f16(const void* Fhat, const float* scale, const float2* mhat, float2* partial, int64_t nf,
+                         int64_t R, int64_t Nm, int64_t B, cudaStream_t s, int jc = 0);
+void launch_prod_adj_f16(const void* Fhat, const float* scale, const float2* dhat, float2* mhat, int64_t nf,
+                         int64_t R, int64_t Nm, int64_t B, cudaStream_t s, int vpt = 0);
 // Adjoint: mhat[b][w][j] = sum_i conj(Fhat[w][i][j]) dhat[b][w][i]
 // vpt: columns per thread for single-vector calls (2, 4, 8; 0 = default)
 template <typename T, typename TS>
@@ -140,6 +146,10 @@ int64_t trsm_lower_f64(const double* Lm, const double* Linv, int64_t n, double* 
                        double* work, const int* status, cudaStream_t s);
 size_t trsm_work_elems(int64_t n, int64_t B);
 int axpby_f64(double* y, const double* x, double a, double b, int64_t n, cudaStream_t s);
+// FP32 Gram product W = A B^T into an FP64 matrix (lower tiles) and the FP64 -> FP32 copy
+int sgemm_nt_lower_to_f64(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* Bm,
+                          int64_t ldb, double* C, int64_t ldc, cudaStream_t s);
+int convert_f64_to_f32(const double* x, float* y, int64_t n, cudaStream_t s);
 int noise_residual_f64(double* r, const double* x, const double* diag, int64_t n, int64_t B,
                        cudaStream_t s);
 

@@ -423,3 +423,84 @@ int noise_residual_f64(double* r, const double* x, const double* diag, int64_t n
 }
 
 }  // namespace bti
+
+namespace bti {
+
+// ------------------------------------------------------------------ FP32 Gram product
+// W = A B^T (A: M x K, B: N x K, both row-major FP32), FP32 accumulation, written to
+// an FP64 matrix C (ldc), lower tiles only.  128 x 128 tile per CTA, k-step 8, 256
+// threads each owning an 8 x 8 sub-tile; the low-precision assembly of K for
+// mixed-precision solves (FP32 issues 64x the FP64 rate on GB300).
+constexpr int SBM = 128, SBN = 128, SBK = 8;
+
+__global__ void __launch_bounds__(256)
+sgemm_nt_lower_kernel(int64_t M, int64_t N, int64_t K, const float* __restrict__ A, int64_t lda,
+                      const float* __restrict__ Bm, int64_t ldb, double* __restrict__ C, int64_t ldc) {
+  __shared__ float As[SBK][SBM + 4];
+  __shared__ float Bs[SBK][SBN + 4];
+  const int64_t m0 = (int64_t)blockIdx.x * SBM;
+  const int64_t n0 = (int64_t)blockIdx.y * SBN;
+  if (m0 + SBM - 1 < n0) return;  // strictly above the diagonal
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float acc[8][8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+  for (int64_t k0 = 0; k0 < K; k0 += SBK) {
+    // 128 rows x 8 k of A and of B: 1024 elements each, 4 per thread
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      int idx = threadIdx.x + 256 * e;
+      int r = idx >> 3, c = idx & 7;
+      int64_t gk = k0 + c;
+      int64_t gm = m0 + r, gn = n0 + r;
+      As[c][r] = (gm < M && gk < K) ? A[gm * lda + gk] : 0.f;
+      Bs[c][r] = (gn < N && gk < K) ? Bm[gn * ldb + gk] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < SBK; ++kk) {
+      float av[8], bv[8];
+#pragma unroll
+      for (int a = 0; a < 8; ++a) av[a] = As[kk][ty + 16 * a];
+#pragma unroll
+      for (int b = 0; b < 8; ++b) bv[b] = Bs[kk][tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    int64_t gm = m0 + ty + 16 * a;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      int64_t gn = n0 + tx + 16 * b;
+      if (gn < N) C[gm * ldc + gn] = (double)acc[a][b];
+    }
+  }
+}
+
+int sgemm_nt_lower_to_f64(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* Bm,
+                          int64_t ldb, double* C, int64_t ldc, cudaStream_t s) {
+  if (M <= 0 || N <= 0) return 0;
+  dim3 grid((unsigned)((M + SBM - 1) / SBM), (unsigned)((N + SBN - 1) / SBN));
+  sgemm_nt_lower_kernel<<<grid, 256, 0, s>>>(M, N, K, A, lda, Bm, ldb, C, ldc);
+  return 1;
+}
+
+__global__ void f64_to_f32_kernel(const double* __restrict__ x, float* __restrict__ y, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (float)x[i];
+}
+int convert_f64_to_f32(const double* x, float* y, int64_t n, cudaStream_t s) {
+  if (n <= 0) return 0;
+  f64_to_f32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, y, n);
+  return 1;
+}
+
+}  // namespace bti

@@ -11,6 +11,8 @@
 // deterministic: per-chunk partial sums, then a fixed-order second pass.
 #include "bti_internal.cuh"
 
+#include <cuda_fp16.h>
+
 namespace bti {
 
 template <typename T> struct FwdCfg;
@@ -505,6 +507,229 @@ void launch_prod_adj_df64(const float4* Fhat, const double2* dhat, double2* mhat
     adj_df64_launch<1, 8>(Fhat, dhat, mhat, nf, R, Nm, B, s);
   else
     adj_df64_launch<1, 4>(Fhat, dhat, mhat, nf, R, Nm, B, s);
+}
+
+
+// ------------------------------------------------------------------ FP16 tier
+// Spectral blocks stored as FP16 complex pairs (4 bytes per element, a quarter of
+// FP64) with one power-of-two FP32 scale per row (w, i), so each row uses the FP16
+// range fully: F-hat[w][i][j] = scale[w][i] * h[w][i][j].  Products and
+// accumulation in FP32 (the scale is applied to the row sum, or folded into d-hat
+// for the adjoint); FFTs and vectors in FP32.  Relative error about 2^-11 per
+// element: the low-precision tier of mixed-precision solves, whose final accuracy
+// comes from refinement with the double-FP32 operators.
+
+// One CTA per row (w, i): max |re|, |im| over the row, then scale and round.
+__global__ void quantize_f16_rows_kernel(const double2* __restrict__ src, __half2* __restrict__ dst,
+                                         float* __restrict__ scale, int64_t Nm) {
+  const int64_t row = blockIdx.x;
+  const double2* s = src + row * Nm;
+  double mx = 0.0;
+  for (int64_t j = threadIdx.x; j < Nm; j += blockDim.x) {
+    double2 v = s[j];
+    mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+  }
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    mx = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (threadIdx.x == 0) red[0] = mx;
+  }
+  __syncthreads();
+  mx = red[0];
+  // power of two p with mx / p <= 2^14 (FP16 max is 65504)
+  int e = 0;
+  if (mx > 0.0) {
+    frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1)
+    e -= 14;
+  }
+  const double p = ldexp(1.0, e);
+  const double inv = ldexp(1.0, -e);
+  if (threadIdx.x == 0) scale[row] = (float)p;
+  for (int64_t j = threadIdx.x; j < Nm; j += blockDim.x) {
+    double2 v = s[j];
+    dst[row * Nm + j] = __floats2half2_rn((float)(v.x * inv), (float)(v.y * inv));
+  }
+}
+
+void launch_quantize_f16(const double2* src, void* dst, float* scale, int64_t rows, int64_t Nm, cudaStream_t s) {
+  if (rows > 0) quantize_f16_rows_kernel<<<(unsigned)rows, 256, 0, s>>>(src, (__half2*)dst, scale, Nm);
+}
+
+// Forward product: grid (nchunk, nf, ceil(B / BG)); warp w handles rows w, w + 8, ...
+template <int BG, int U>
+__global__ void __launch_bounds__(256)
+prod_fwd_f16_kernel(const __half2* __restrict__ Fhat, const float* __restrict__ scale,
+                    const float2* __restrict__ mhat, float2* __restrict__ partial, int64_t nf, int64_t R,
+                    int64_t Nm, int64_t B, int JC, int nchunk) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* sm = reinterpret_cast<float2*>(smem_raw);  // [BG][JC]
+  const int ch = blockIdx.x;
+  const int64_t w = blockIdx.y;
+  const int64_t b0 = (int64_t)blockIdx.z * BG;
+  const int64_t j0 = (int64_t)ch * JC;
+  const int jn = (int)((Nm - j0) < JC ? (Nm - j0) : JC);
+  for (int idx = threadIdx.x; idx < BG * JC; idx += blockDim.x) {
+    int bb = idx / JC, jj = idx - bb * JC;
+    float2 v = make_float2(0.f, 0.f);
+    if (jj < jn && b0 + bb < B) v = mhat[((b0 + bb) * nf + w) * Nm + j0 + jj];
+    sm[idx] = v;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int STEP = 32 * U;
+  const __half2 hz = __floats2half2_rn(0.f, 0.f);
+  for (int64_t i = warp; i < R; i += 8) {
+    const __half2* row = Fhat + (w * R + i) * Nm + j0;
+    float ar[BG], ai[BG];
+#pragma unroll
+    for (int bb = 0; bb < BG; ++bb) ar[bb] = ai[bb] = 0.f;
+    __half2 cur[U], nxt[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      int jj = lane + 32 * u;
+      cur[u] = (jj < jn) ? __ldg(row + jj) : hz;
+    }
+    for (int base = 0; base < jn; base += STEP) {
+      const int nb = base + STEP;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        int jj = nb + lane + 32 * u;
+        nxt[u] = (jj < jn) ? __ldg(row + jj) : hz;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int jj = base + lane + 32 * u;
+        const float2 f = __half22float2(cur[u]);
+#pragma unroll
+        for (int bb = 0; bb < BG; ++bb) {
+          float2 x = sm[bb * JC + (jj < JC ? jj : 0)];
+          ar[bb] = fmaf(f.x, x.x, ar[bb]);
+          ar[bb] = fmaf(-f.y, x.y, ar[bb]);
+          ai[bb] = fmaf(f.x, x.y, ai[bb]);
+          ai[bb] = fmaf(f.y, x.x, ai[bb]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) cur[u] = nxt[u];
+    }
+    const float sc = scale[w * R + i];
+#pragma unroll
+    for (int bb = 0; bb < BG; ++bb) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        ar[bb] += __shfl_xor_sync(0xffffffffu, ar[bb], o);
+        ai[bb] += __shfl_xor_sync(0xffffffffu, ai[bb], o);
+      }
+      if (lane == 0 && b0 + bb < B)
+        partial[(((b0 + bb) * nf + w) * nchunk + ch) * R + i] = make_float2(sc * ar[bb], sc * ai[bb]);
+    }
+  }
+}
+
+void launch_prod_fwd_f16(const void* Fhat, const float* scale, const float2* mhat, float2* partial, int64_t nf,
+                         int64_t R, int64_t Nm, int64_t B, cudaStream_t s, int jc) {
+  int bg = fwd_bg<float>(B);
+  int JC = 0;
+  int nchunk = fwd_nchunk<float>(Nm, B, &JC, jc);
+  size_t smem = sizeof(float2) * (size_t)bg * JC;
+  dim3 grid((unsigned)nchunk, (unsigned)nf, (unsigned)((B + bg - 1) / bg));
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(prod_fwd_f16_kernel<4, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    cudaFuncSetAttribute(prod_fwd_f16_kernel<1, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    attr = true;
+  }
+  if (bg == 4)
+    prod_fwd_f16_kernel<4, 8><<<grid, 256, smem, s>>>((const __half2*)Fhat, scale, mhat, partial, nf, R, Nm, B,
+                                                      JC, nchunk);
+  else
+    prod_fwd_f16_kernel<1, 32><<<grid, 256, smem, s>>>((const __half2*)Fhat, scale, mhat, partial, nf, R, Nm, B,
+                                                       JC, nchunk);
+}
+
+// Adjoint product; the row scale is folded into d-hat as it is staged.
+template <int BG, int VPT>
+__global__ void __launch_bounds__(256)
+prod_adj_f16_kernel(const __half2* __restrict__ Fhat, const float* __restrict__ scale,
+                    const float2* __restrict__ dhat, float2* __restrict__ mhat, int64_t nf, int64_t R, int64_t Nm,
+                    int64_t B) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* sd = reinterpret_cast<float2*>(smem_raw);  // [BG][R]
+  const int64_t w = blockIdx.y;
+  const int64_t b0 = (int64_t)blockIdx.z * BG;
+  for (int64_t idx = threadIdx.x; idx < BG * R; idx += blockDim.x) {
+    int64_t bb = idx / R, i = idx - bb * R;
+    float2 v = make_float2(0.f, 0.f);
+    if (b0 + bb < B) {
+      v = dhat[((b0 + bb) * nf + w) * R + i];
+      float sc = scale[w * R + i];
+      v.x *= sc;
+      v.y *= sc;
+    }
+    sd[idx] = v;
+  }
+  __syncthreads();
+  const int64_t jbase = (int64_t)blockIdx.x * (256 * VPT) + threadIdx.x;
+  float ar[BG][VPT], ai[BG][VPT];
+#pragma unroll
+  for (int bb = 0; bb < BG; ++bb)
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) ar[bb][v] = ai[bb][v] = 0.f;
+  const __half2* base = Fhat + w * R * Nm;
+  const __half2 hz = __floats2half2_rn(0.f, 0.f);
+  for (int64_t i = 0; i < R; ++i) {
+    const __half2* row = base + i * Nm;
+    float2 f[VPT];
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      int64_t j = jbase + 256 * v;
+      f[v] = __half22float2((j < Nm) ? __ldg(row + j) : hz);
+    }
+#pragma unroll
+    for (int bb = 0; bb < BG; ++bb) {
+      float2 x = sd[bb * R + i];
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) {
+        ar[bb][v] = fmaf(f[v].x, x.x, ar[bb][v]);
+        ar[bb][v] = fmaf(f[v].y, x.y, ar[bb][v]);
+        ai[bb][v] = fmaf(f[v].x, x.y, ai[bb][v]);
+        ai[bb][v] = fmaf(-f[v].y, x.x, ai[bb][v]);
+      }
+    }
+  }
+#pragma unroll
+  for (int bb = 0; bb < BG; ++bb) {
+    if (b0 + bb >= B) continue;
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      int64_t j = jbase + 256 * v;
+      if (j < Nm) mhat[((b0 + bb) * nf + w) * Nm + j] = make_float2(ar[bb][v], ai[bb][v]);
+    }
+  }
+}
+
+template <int BG, int VPT>
+static void adj_f16_launch(const void* Fhat, const float* scale, const float2* dhat, float2* mhat, int64_t nf,
+                           int64_t R, int64_t Nm, int64_t B, cudaStream_t s) {
+  size_t smem = sizeof(float2) * (size_t)BG * R;
+  dim3 grid((unsigned)((Nm + 256 * VPT - 1) / (256 * VPT)), (unsigned)nf, (unsigned)((B + BG - 1) / BG));
+  prod_adj_f16_kernel<BG, VPT><<<grid, 256, smem, s>>>((const __half2*)Fhat, scale, dhat, mhat, nf, R, Nm, B);
+}
+
+void launch_prod_adj_f16(const void* Fhat, const float* scale, const float2* dhat, float2* mhat, int64_t nf,
+                         int64_t R, int64_t Nm, int64_t B, cudaStream_t s, int vpt) {
+  if (B >= 4)
+    adj_f16_launch<4, 4>(Fhat, scale, dhat, mhat, nf, R, Nm, B, s);
+  else if (vpt == 2)
+    adj_f16_launch<1, 2>(Fhat, scale, dhat, mhat, nf, R, Nm, B, s);
+  else if (vpt == 4)
+    adj_f16_launch<1, 4>(Fhat, scale, dhat, mhat, nf, R, Nm, B, s);
+  else
+    adj_f16_launch<1, 8>(Fhat, scale, dhat, mhat, nf, R, Nm, B, s);
 }
 
 }  // namespace bti

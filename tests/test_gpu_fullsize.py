@@ -7,6 +7,8 @@
   Cholesky factor, m_map and q_map against the oracle's complete inversion.
 - Differentiation (N_m = 8,192, N_d = 64, N_t = 256): the autograd gradient of
   the data misfit against the oracle gradient.
+- The batched workload again as a mixed-precision solve (K assembled in FP32,
+  refinement with double-FP32 operators).
 
 Minutes of host time for the oracle; GPU only.
 """
@@ -41,11 +43,11 @@ def sweep():
     return p, p.blocks_F(), p.vectors_m(2), p.vectors_d(2)
 
 
-@pytest.mark.parametrize("store,tol", [(bti.DF64, 1e-12), (bti.F64, 1e-12), (bti.F32, 1e-5)],
-                         ids=["df64", "f64", "f32"])
+@pytest.mark.parametrize("store,tol", [(bti.DF64, 1e-12), (bti.F64, 1e-12), (bti.F32, 1e-5), (bti.F16, 1e-3)],
+                         ids=["df64", "f64", "f32", "f16"])
 def test_sweep_sampled_outputs(sweep, store, tol):
     p, F, m, d = sweep
-    dt = torch.float32 if store == bti.F32 else torch.float64
+    dt = torch.float32 if store in (bti.F32, bti.F16) else torch.float64
     h = bti.Handle(p.Nm, p.Nd, 0, p.Nt)
     Fd = torch.from_numpy(F).cuda()
     h.set_blocks(bti.OP_F, Fd, store)
@@ -132,3 +134,30 @@ def test_diff_gradient_full_size():
     h.close()
     g_or = oracle.loss_gradient(F, m0[0], dobs[0], p.sigma2)
     assert relb(g, g_or[None]) < 1e-12
+
+
+def test_batched_mixed_precision_solve_full_size():
+    """The batched workload with K assembled in FP32, FP64 Cholesky, and refinement
+    with double-FP32 operators: FP64-level m_map and q_map against the oracle."""
+    p = synthetic.BATCHED
+    F = p.blocks_F()
+    Fq = p.blocks_Fq()
+    d_obs = p.vectors_d()
+    h = bti.Handle(p.Nm, p.Nd, p.Nq, p.Nt)
+    h.set_blocks(bti.OP_F, torch.from_numpy(F).cuda(), bti.DF64)
+    h.set_blocks(bti.OP_FQ, torch.from_numpy(Fq).cuda(), bti.DF64)
+    h.set_prior_se_grid(p.gx, p.gy, p.ell, p.sigma_p, bti.DF64)
+    h.set_noise(p.sigma2)
+    h.build_K_prec(p.col_block, bti.F32)
+    h.factor_K()
+    m_map = torch.empty((p.n_vectors, p.Nt, p.Nm), dtype=torch.float64, device="cuda")
+    q_map = torch.empty((p.n_vectors, p.Nt, p.Nq), dtype=torch.float64, device="cuda")
+    h.infer_map(torch.from_numpy(d_obs).cuda(), m_map, refine_iters=4)
+    h.predict_qoi(m_map, q_map)
+    m_gpu = m_map.cpu().numpy()
+    q_gpu = q_map.cpu().numpy()
+    h.close()
+    G = oracle.prior_blocks(F, oracle.se_covariance(p.gx, p.gy, p.ell, p.sigma_p))
+    m_or = oracle.map_point(F, G, p.sigma2, d_obs)
+    assert relb(m_gpu, m_or) < 1e-11
+    assert relb(q_gpu, oracle.qoi_map(Fq, m_or)) < 1e-11

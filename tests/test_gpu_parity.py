@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 
 import paper_2501_14911_gb300 as bti  # noqa: E402
 
-TOL = {bti.F64: 1e-12, bti.F32: 1e-5, bti.DF64: 1e-12}
+TOL = {bti.F64: 1e-12, bti.F32: 1e-5, bti.DF64: 1e-12, bti.F16: 1e-3}
 
 
 def relb(a, b):
@@ -62,7 +62,7 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("store", [bti.F64, bti.F32, bti.DF64], ids=["f64", "f32", "df64"])
+@pytest.mark.parametrize("store", [bti.F64, bti.F32, bti.DF64, bti.F16], ids=["f64", "f32", "df64", "f16"])
 @pytest.mark.parametrize("name,Nm,Nd,Nq,Nt,B", CASES, ids=[c[0] for c in CASES])
 def test_apply_F_FT_Fq_match_oracle(name, Nm, Nd, Nq, Nt, B, store):
     p = synthetic.small(name, 1, Nm, Nd, Nt, Nq=Nq)
@@ -71,7 +71,7 @@ def test_apply_F_FT_Fq_match_oracle(name, Nm, Nd, Nq, Nt, B, store):
     m = p.vectors_m(B)
     d = p.vectors_d(B)
     h = make_handle(F, Fq, store)
-    dt = torch.float32 if store == bti.F32 else torch.float64
+    dt = torch.float32 if store in (bti.F32, bti.F16) else torch.float64
     m_g, d_g = cuda(m, dt), cuda(d, dt)
     out_d = torch.empty((B, Nt, Nd), dtype=dt, device="cuda")
     out_m = torch.empty((B, Nt, Nm), dtype=dt, device="cuda")
@@ -335,4 +335,44 @@ def test_autotune_keeps_results(store):
     h.apply_FT(dg, om)
     assert relb(host(od), oracle.p2o_apply(F, host(mg))) < TOL[store]
     assert relb(host(om), oracle.p2o_apply_adjoint(F, host(dg))) < TOL[store]
+    h.close()
+
+
+@pytest.mark.parametrize("case", ["tiny", "diagnoise"])
+def test_mixed_precision_solve_recovers_fp64(case):
+    """K assembled with FP32 products, FP64 Cholesky, refinement with double-FP32
+    operators: m_map and q_map reach the FP64 tolerance against the oracle."""
+    if case == "tiny":
+        p, F, Fq, G, d_obs = tiny_problem()
+        noise = p.sigma2
+        h = make_handle(F, Fq, bti.DF64)
+        h.set_prior_se_grid(p.gx, p.gy, p.ell, p.sigma_p, bti.DF64)
+        h.set_noise(p.sigma2)
+    else:
+        p = synthetic.small("mixed_solve", 6, 6, 5, 30, Nq=3)
+        F, Fq = p.blocks_F(), p.blocks_Fq()
+        G = oracle.prior_blocks(F, oracle.se_covariance(6, 6, 2.0, 1.0))
+        noise = 1e-3 * (1.0 + np.arange(30 * 5).reshape(30, 5) % 7)
+        d_obs = p.vectors_d(3)
+        h = make_handle(F, Fq, bti.DF64)
+        h.set_prior_se_grid(6, 6, 2.0, 1.0, bti.DF64)
+        h.set_noise(0.0, cuda(noise))
+    h.build_K_prec(0, bti.F32)
+    K_low = host(h.copy_K())
+    K_or = oracle.assemble_K(F, G, noise)
+    low = np.tril_indices(K_or.shape[0])
+    err_K = np.linalg.norm(K_low[low] - K_or[low]) / np.linalg.norm(K_or[low])
+    assert 1e-12 < err_K < 1e-5  # genuinely low precision, but close
+    h.factor_K()
+    B = d_obs.shape[0]
+    m0 = torch.empty((B, p.Nt, p.Nm), dtype=torch.float64, device="cuda")
+    h.infer_map(cuda(d_obs), m0, refine_iters=0)
+    m_or = oracle.map_point(F, G, noise, d_obs)
+    assert relb(host(m0), m_or) > 1e-11  # without refinement the assembly error shows
+    m = torch.empty_like(m0)
+    q = torch.empty((B, p.Nt, p.Nq), dtype=torch.float64, device="cuda")
+    h.infer_map(cuda(d_obs), m, refine_iters=4)
+    h.predict_qoi(m, q)
+    assert relb(host(m), m_or) < 1e-12
+    assert relb(host(q), oracle.qoi_map(Fq, m_or)) < 1e-12
     h.close()
