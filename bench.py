@@ -477,7 +477,11 @@ def e2e_block(args, h, p, m_host, d_host, dev, timed, world, bytes_step):
 
 
 def online_block(args, dev, stream):
-    """Offline build (K, Cholesky) and online latency of m_map + q_map for 64 observations."""
+    """Offline build (K, Cholesky) and online latency of m_map + q_map for the 64
+    observation vectors of the batched workload, in four forms: plain FP64; the dense
+    work (Gram product, Cholesky updates, triangular solves) in double-FP32
+    arithmetic; K assembled in FP32 with refinement; and both.  All forms reach FP64-
+    level m_map (tests/test_gpu_parity.py, tests/test_gpu_fullsize.py)."""
     import torch
 
     import paper_2501_14911_gb300 as bti
@@ -490,85 +494,48 @@ def online_block(args, dev, stream):
     h.set_blocks(bti.OP_FQ, torch.from_numpy(p.blocks_Fq()).to(dev), bti.DF64)
     h.set_prior_se_grid(p.gx, p.gy, p.ell, p.sigma_p, bti.DF64)
     h.set_noise(p.sigma2)
-    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    torch.cuda.synchronize()
-    e[0].record(stream)
-    h.build_K(p.col_block)
-    e[1].record(stream)
-    h.factor_K()
-    e[2].record(stream)
-    torch.cuda.synchronize()
-    t_build = e[0].elapsed_time(e[1])
-    t_factor = e[1].elapsed_time(e[2])
     d_obs = torch.from_numpy(p.vectors_d()).to(dev)
     m_map = torch.empty((B, p.Nt, p.Nm), dtype=torch.float64, device=dev)
     q_map = torch.empty((B, p.Nt, p.Nq), dtype=torch.float64, device=dev)
-    for _ in range(2):
-        h.infer_map(d_obs, m_map)
-        h.predict_qoi(m_map, q_map)
-    torch.cuda.synchronize()
-    reps = 3
-    e[0].record(stream)
-    for _ in range(reps):
-        h.infer_map(d_obs, m_map)
-        h.predict_qoi(m_map, q_map)
-    e[1].record(stream)
-    torch.cuda.synchronize()
-    lat = e[0].elapsed_time(e[1]) / reps
-    # the same online phase as one CUDA-graph launch per batch (bti_online)
     gs = torch.cuda.Stream(dev)
-    h.set_stream(gs)
-    with torch.cuda.stream(gs):
-        for _ in range(2):
-            h.online(d_obs, m_map, q_map)
-        torch.cuda.synchronize()
-        g0 = torch.cuda.Event(enable_timing=True)
-        g1 = torch.cuda.Event(enable_timing=True)
-        g0.record(gs)
-        for _ in range(reps):
-            h.online(d_obs, m_map, q_map)
-        g1.record(gs)
-        torch.cuda.synchronize()
-    lat_graph = g0.elapsed_time(g1) / reps
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    reps = 3
+    forms = [("plain_f64", bti.F64, bti.F64, 0), ("dense_df64", bti.DF64, bti.F64, 1),
+             ("f32_assembly", bti.F64, bti.F32, 3), ("f32_assembly_dense_df64", bti.DF64, bti.F32, 3)]
+    out = {"workload": p.name, "obs_vectors": B, "K_n": p.Nt * p.Nd}
+    for name, dense, assembly, refine in forms:
+        h.set_stream(gs)
+        with torch.cuda.stream(gs):
+            h.set_dense_precision(dense)
+            torch.cuda.synchronize()
+            e[0].record(gs)
+            h.build_K_prec(p.col_block, assembly)
+            e[1].record(gs)
+            h.factor_K()
+            e[2].record(gs)
+            torch.cuda.synchronize()
+            t_build, t_factor = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+            for _ in range(2):
+                h.online(d_obs, m_map, q_map, refine_iters=refine)
+            torch.cuda.synchronize()
+            e[0].record(gs)
+            for _ in range(reps):
+                h.online(d_obs, m_map, q_map, refine_iters=refine)
+            e[1].record(gs)
+            torch.cuda.synchronize()
+            lat = e[0].elapsed_time(e[1]) / reps
+        n = p.Nt * p.Nd
+        out[name] = {"dense": "f64" if dense == bti.F64 else "df64",
+                     "K_assembly": "f64" if assembly == bti.F64 else "f32", "refine_iters": refine,
+                     "build_K_ms": t_build, "factor_K_ms": t_factor,
+                     "factor_tflops_fp64_equiv": (n ** 3 / 3.0) / (t_factor * 1e-3) / 1e12,
+                     "m_map_plus_q_map_graph_ms": lat, "ms_per_obs_vector": lat / B,
+                     "offline_plus_online_ms": t_build + t_factor + lat}
     h.set_stream(stream)
-    # mixed-precision form: K assembled with FP32 products, FP64 Cholesky, and
-    # refinement of the solve with double-FP32 operators (FP64-level result)
-    refine = 3
-    torch.cuda.synchronize()
-    e[0].record(stream)
-    h.build_K_prec(p.col_block, bti.F32)
-    e[1].record(stream)
-    h.factor_K()
-    e[2].record(stream)
-    torch.cuda.synchronize()
-    t_build_mixed = e[0].elapsed_time(e[1])
-    t_factor_mixed = e[1].elapsed_time(e[2])
-    for _ in range(2):
-        h.infer_map(d_obs, m_map, refine_iters=refine)
-        h.predict_qoi(m_map, q_map)
-    torch.cuda.synchronize()
-    e[0].record(stream)
-    for _ in range(reps):
-        h.infer_map(d_obs, m_map, refine_iters=refine)
-        h.predict_qoi(m_map, q_map)
-    e[1].record(stream)
-    torch.cuda.synchronize()
-    lat_mixed = e[0].elapsed_time(e[1]) / reps
     h.close()
-    n = p.Nt * p.Nd
-    return {"workload": p.name, "obs_vectors": B, "K_n": n, "build_K_ms": t_build, "factor_K_ms": t_factor,
-            "factor_tflops_f64": (n ** 3 / 3.0) / (t_factor * 1e-3) / 1e12,
-            "m_map_plus_q_map_ms": lat, "ms_per_obs_vector": lat / B,
-            "m_map_plus_q_map_graph_ms": lat_graph, "graph_ms_per_obs_vector": lat_graph / B,
-            "mixed": {"build_K_f32_ms": t_build_mixed, "factor_K_ms": t_factor_mixed, "refine_iters": refine,
-                      "m_map_plus_q_map_ms": lat_mixed,
-                      "offline_plus_online_ms": t_build_mixed + t_factor_mixed + lat_mixed,
-                      "plain_f64_offline_plus_online_ms": t_build + t_factor + lat,
-                      "accuracy": "FP64-level after refinement; tests/test_gpu_parity.py::"
-                                  "test_mixed_precision_solve_recovers_fp64 and tests/test_gpu_fullsize.py::"
-                                  "test_batched_mixed_precision_solve_full_size check 1e-12 / 1e-11 vs the oracle"},
-            "accuracy": "K, Cholesky and solves FP64; G* and F_q products double-FP32; parity with the "
-                        "oracle to 1e-12 in tests/test_gpu_parity.py"}
+    out["accuracy"] = ("every form reaches FP64-level m_map and q_map: tests/test_gpu_parity.py (tiny, 1e-12) "
+                       "and tests/test_gpu_fullsize.py (batched full size, 1e-11) against the oracle")
+    return out
 
 
 def main():

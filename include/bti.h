@@ -110,6 +110,15 @@ bti_status bti_set_blocks(bti_handle h, bti_op op, const double* blocks, bti_pre
 bti_status bti_set_prior_se_grid(bti_handle h, int gx, int gy, double ell, double sigma,
                                  bti_prec store);
 
+/* Arithmetic of the dense data-space work that follows (the Gram product of
+ * bti_build_K, the panel and trailing updates of bti_factor_K, and the block
+ * updates of the triangular solves): BTI_P_F64 (default; FP64 FMA) or BTI_P_DF64
+ * (float pairs on the FP32 pipes, about 48 significant bits; GB300 issues FP32 at
+ * 64x its FP64 rate).  The 64 x 64 diagonal-block factorisations and inverses are
+ * FP64 either way.  With BTI_P_DF64 one refinement step (refine_iters = 1)
+ * restores the last digits of m_map for ill-conditioned K. */
+bti_status bti_set_dense_precision(bti_handle h, bti_prec arith);
+
 /* Gamma_noise: sigma2 * I if `diag` is NULL, otherwise diag (device, FP64,
  * [N_t][N_d] variances, all > 0).  Invalidates K. */
 bti_status bti_set_noise(bti_handle h, double sigma2, const double* diag);
@@ -181,6 +190,17 @@ bti_status bti_infer_map(bti_handle h, const double* d_obs, double* m_map, int64
  * counted or timed by bti_profile_read. */
 bti_status bti_online(bti_handle h, const double* d_obs, double* m_map, double* q_map, int64_t B,
                       int refine_iters);
+
+/* Elliptic prior operator of Eq. (5.1), per time block: out = A_s m with
+ * A_s = alpha1 I - alpha2 Delta_h on the gx x gy grid (gx * gy = N_m, node
+ * ix * gy + iy, unit spacing), Delta_h the 5-point Laplacian with homogeneous
+ * Neumann boundaries in graph form (the paper's Robin coefficient is not given).
+ * Eq. (5.1) takes A_s^{-2} as the prior covariance, so 0.5 ||A_s m_t||^2 summed over
+ * t is the prior term of the negative log-posterior and A_s^2 m its gradient.
+ * m, out: device, double, [B][N_t][N_m], not aliased.  squared != 0 returns A_s^2 m
+ * (A_s is symmetric); that form allocates and frees one temporary and synchronises. */
+bti_status bti_apply_elliptic(bti_handle h, int gx, int gy, double alpha1, double alpha2, const double* m,
+                              double* out, int64_t B, int squared);
 
 /* q_map = F_q m_map (Eq. (4.2)): m_map [B][N_t][N_m] -> q_map [B][N_t][N_q],
  * both double.  Requires FQ. */

@@ -27,4 +27,4 @@ from ._binding import (  # noqa: F401
     header_symbols,
     KCLASSES,
 )
-from .autograd import FOp, apply_F_autograd  # noqa: F401
+from .autograd import EllipticOp, FOp, apply_F_autograd, map_loss  # noqa: F401

@@ -59,6 +59,7 @@ def lib():
         "bti_set_blocks": ([vp, ip, vp, ip], st),
         "bti_set_prior_se_grid": ([vp, ip, ip, dp, dp, ip], st),
         "bti_set_noise": ([vp, dp, vp], st),
+        "bti_set_dense_precision": ([vp, ip], st),
         "bti_apply_F": ([vp, vp, vp, i64, ip], st),
         "bti_apply_FT": ([vp, vp, vp, i64, ip], st),
         "bti_apply_Fq": ([vp, vp, vp, i64, ip], st),
@@ -70,6 +71,7 @@ def lib():
         "bti_infer_map": ([vp, vp, vp, i64, ip], st),
         "bti_predict_qoi": ([vp, vp, vp, i64], st),
         "bti_online": ([vp, vp, vp, vp, i64, ip], st),
+        "bti_apply_elliptic": ([vp, ip, ip, dp, dp, vp, vp, i64, ip], st),
         "bti_autotune": ([vp, ip, i64, ctypes.c_char_p, i64], st),
         "bti_sync": ([vp], st),
         "bti_profile_enable": ([vp, ip], st),
@@ -183,6 +185,10 @@ class Handle:
     def set_prior_se_grid(self, gx, gy, ell, sigma, store=F64):
         self._check(lib().bti_set_prior_se_grid(self._h, gx, gy, float(ell), float(sigma), store))
 
+    def set_dense_precision(self, arith=F64):
+        """Arithmetic of K assembly, Cholesky and solves: F64 (FP64 FMA) or DF64 (float pairs)."""
+        self._check(lib().bti_set_dense_precision(self._h, int(arith)))
+
     def set_noise(self, sigma2, diag=None):
         if diag is not None:
             self._tensor(diag, (self.Nt, self.Nd), "diag")
@@ -264,6 +270,15 @@ class Handle:
                 raise ValueError("m_map and q_map batch sizes differ")
         self._check(lib().bti_online(self._h, _ptr(d_obs), _ptr(m_map), _ptr(q_map), B, int(refine_iters)))
         return m_map
+
+    def apply_elliptic(self, gx, gy, alpha1, alpha2, m, out, squared=False):
+        """out = A_s m (or A_s^2 m) per time block: the elliptic prior operator of Eq. (5.1)."""
+        self._tensor(m, (self.Nt, self.Nm), "m")
+        self._tensor(out, (self.Nt, self.Nm), "out")
+        B = self._batch(m, 2)
+        self._check(lib().bti_apply_elliptic(self._h, int(gx), int(gy), float(alpha1), float(alpha2), _ptr(m),
+                                             _ptr(out), B, 1 if squared else 0))
+        return out
 
     def autotune(self, op=OP_F, B=1):
         """Pick launch shapes for operator `op` with B vectors per call; returns the timing report."""

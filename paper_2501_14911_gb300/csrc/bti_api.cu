@@ -42,6 +42,7 @@ struct bti_ctx {
   FftPlan plan;
   OpStore op[3];
   Tune tune[4];  // indexed by bti_prec
+  bti_prec dense_prec = BTI_P_F64;  // arithmetic of K assembly, Cholesky and solves
   bool noise_set = false;
   double sigma2 = 0.0;
   double* noise_diag = nullptr;  // [Nt][Nd] or null
@@ -564,6 +565,16 @@ bti_status bti_set_prior_se_grid(bti_handle h, int gx, int gy, double ell, doubl
   return st;
 }
 
+bti_status bti_set_dense_precision(bti_handle h, bti_prec arith) {
+  bti_status st = check_handle(h);
+  if (st != BTI_OK) return st;
+  if (arith != BTI_P_F64 && arith != BTI_P_DF64)
+    return fail(h, BTI_ERR_ARG, "set_dense_precision: BTI_P_F64 or BTI_P_DF64 only");
+  if (arith != h->dense_prec) drop_online_graph_any(h);
+  h->dense_prec = arith;
+  return BTI_OK;
+}
+
 bti_status bti_set_noise(bti_handle h, double sigma2, const double* diag) {
   bti_status st = check_handle(h);
   if (st != BTI_OK) return st;
@@ -640,10 +651,12 @@ static bti_status build_K_impl(bti_handle h, int64_t col_block, bti_prec assembl
     dev_freep(Ff);
   } else {
     // W = F_stack G_stack^T (lower block triangle), by column panels
+    const bool dd = h->dense_prec == BTI_P_DF64;
     for (int64_t c0 = 0; c0 < n; c0 += col_block) {
       int64_t nc = (n - c0) < col_block ? (n - c0) : col_block;
-      count_dense(h, gemm_f64(true, n - c0, nc, h->Nm, 1.0, F.time + c0 * h->Nm, h->Nm, 0, G.time + c0 * h->Nm,
-                              h->Nm, 0, 0.0, h->K + c0 * n + c0, n, 0, 1, true, s));
+      count_dense(h, (dd ? gemm_df64 : gemm_f64)(true, n - c0, nc, h->Nm, 1.0, F.time + c0 * h->Nm, h->Nm, 0,
+                                                 G.time + c0 * h->Nm, h->Nm, 0, 0.0, h->K + c0 * n + c0, n, 0, 1,
+                                                 true, s));
     }
   }
   count_dense(h, k_diag_cumsum(h->K, h->Nt, h->Nd, h->sigma2, h->noise_diag, s));
@@ -668,7 +681,7 @@ bti_status bti_factor_K(bti_handle h) {
   st = ensure(h, (void**)&h->wsolve, &h->wsolve_bytes, sizeof(double) * (size_t)n * kCholNB, "solve workspace");
   if (st != BTI_OK) return st;
   cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
-  count_dense(h, cholesky_f64(h->K, n, h->Linv, h->wsolve, h->status, h->stream));
+  count_dense(h, cholesky_f64(h->K, n, h->Linv, h->wsolve, h->status, h->stream, h->dense_prec == BTI_P_DF64));
   st = launched(h, "factor_K");
   if (st != BTI_OK) return st;
   int stat = 0;
@@ -716,7 +729,7 @@ static bti_status infer_map_impl(bti_handle h, const double* d_obs, double* m_ma
   cudaStream_t s = h->stream;
   st = cuda_check(h, cudaMemcpyAsync(x, d_obs, sizeof(double) * B * n, cudaMemcpyDeviceToDevice, s), "copy d_obs");
   if (st != BTI_OK) return st;
-  count_dense(h, trsm_lower_f64(h->K, h->Linv, n, x, B, work, h->status, s));
+  count_dense(h, trsm_lower_f64(h->K, h->Linv, n, x, B, work, h->status, s, h->dense_prec == BTI_P_DF64));
   st = launched(h, "triangular solves");
   if (st != BTI_OK) return st;
   for (int it = 0; it < refine_iters; ++it) {
@@ -732,7 +745,7 @@ static bti_status infer_map_impl(bti_handle h, const double* d_obs, double* m_ma
       nl += noise_residual_f64(r, x, h->noise_diag, n, B, s);
     else
       nl += axpby_f64(r, x, -h->sigma2, 1.0, B * n, s);
-    nl += trsm_lower_f64(h->K, h->Linv, n, r, B, work, h->status, s);
+    nl += trsm_lower_f64(h->K, h->Linv, n, r, B, work, h->status, s, h->dense_prec == BTI_P_DF64);
     nl += axpby_f64(x, r, 1.0, 1.0, B * n, s);
     count_dense(h, nl);
     st = launched(h, "refinement");
@@ -743,6 +756,33 @@ static bti_status infer_map_impl(bti_handle h, const double* d_obs, double* m_ma
 
 bti_status bti_infer_map(bti_handle h, const double* d_obs, double* m_map, int64_t B, int refine_iters) {
   return infer_map_impl(h, d_obs, m_map, B, refine_iters);
+}
+
+bti_status bti_apply_elliptic(bti_handle h, int gx, int gy, double alpha1, double alpha2, const double* m,
+                              double* out, int64_t B, int squared) {
+  bti_status st = check_handle(h);
+  if (st != BTI_OK) return st;
+  if (gx <= 0 || gy <= 0 || B < 0 || !(alpha1 > 0.0) || !(alpha2 >= 0.0))
+    return fail(h, BTI_ERR_ARG, "apply_elliptic: bad argument");
+  if ((int64_t)gx * gy != h->Nm) return fail(h, BTI_ERR_SHAPE, "apply_elliptic: gx * gy != N_m");
+  if (B == 0) return BTI_OK;
+  if (!m || !out || m == out) return fail(h, BTI_ERR_ARG, "apply_elliptic: null or aliased pointers");
+  const int64_t nblocks = B * h->Nt;
+  if (!squared) {
+    count_dense(h, elliptic_apply(m, out, gx, gy, alpha1, alpha2, nblocks, h->stream));
+    return launched(h, "apply_elliptic");
+  }
+  // A_s^2 m = A_s (A_s m) through a temporary (A_s is symmetric, so this is A_s^T A_s m)
+  double* tmp = nullptr;
+  st = dev_alloc(h, (void**)&tmp, sizeof(double) * (size_t)nblocks * h->Nm, "elliptic temporary");
+  if (st != BTI_OK) return st;
+  int64_t nl = elliptic_apply(m, tmp, gx, gy, alpha1, alpha2, nblocks, h->stream);
+  nl += elliptic_apply(tmp, out, gx, gy, alpha1, alpha2, nblocks, h->stream);
+  count_dense(h, nl);
+  st = launched(h, "apply_elliptic");
+  cudaStreamSynchronize(h->stream);
+  dev_freep(tmp);
+  return st;
 }
 
 bti_status bti_predict_qoi(bti_handle h, const double* m_map, double* q_map, int64_t B) {

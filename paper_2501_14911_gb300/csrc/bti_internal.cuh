@@ -134,22 +134,31 @@ void launch_prod_adj(const C2<TS>* Fhat, const C2<T>* dhat, C2<T>* mhat,
 int gemm_f64(bool transB, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
              int64_t lda, int64_t sA, const double* Bm, int64_t ldb, int64_t sB, double beta,
              double* C, int64_t ldc, int64_t sC, int64_t batch, bool lower_only, cudaStream_t s);
+// Same contract as gemm_f64, computed in double-FP32 arithmetic on the FP32 pipes.
+int gemm_df64(bool transB, int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda,
+              int64_t sA, const double* Bm, int64_t ldb, int64_t sB, double beta, double* C, int64_t ldc,
+              int64_t sC, int64_t batch, bool lower_only, cudaStream_t s);
 int se_axis_matrix(double* C, int n, double ell, double scale, cudaStream_t s);
 int k_diag_cumsum(double* WK, int64_t Nt, int64_t R, double sigma2, const double* diag,
                   cudaStream_t s);
 // Blocked Cholesky, lower, in place; Linv receives the inverses of the diagonal blocks
 // ([nblk][nb][nb]); status receives the first failing 1-based pivot (0 if none).
-int64_t cholesky_f64(double* A, int64_t n, double* Linv, double* work, int* status, cudaStream_t s);
+// dd: run the panel and trailing-update GEMMs in double-FP32 arithmetic (FP32 pipes)
+int64_t cholesky_f64(double* A, int64_t n, double* Linv, double* work, int* status, cudaStream_t s,
+                     bool dd = false);
 constexpr int kCholNB = 64;
 // X [B][n] rows: X := L^{-1} X (forward) then L^{-T} X (backward), in place.
 int64_t trsm_lower_f64(const double* Lm, const double* Linv, int64_t n, double* X, int64_t B,
-                       double* work, const int* status, cudaStream_t s);
+                       double* work, const int* status, cudaStream_t s, bool dd = false);
 size_t trsm_work_elems(int64_t n, int64_t B);
 int axpby_f64(double* y, const double* x, double a, double b, int64_t n, cudaStream_t s);
 // FP32 Gram product W = A B^T into an FP64 matrix (lower tiles) and the FP64 -> FP32 copy
 int sgemm_nt_lower_to_f64(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* Bm,
                           int64_t ldb, double* C, int64_t ldc, cudaStream_t s);
 int convert_f64_to_f32(const double* x, float* y, int64_t n, cudaStream_t s);
+// out = (alpha1 I - alpha2 Delta_h) m for nblocks grids of gx x gy (5-point, Neumann)
+int elliptic_apply(const double* m, double* out, int gx, int gy, double a1, double a2, int64_t nblocks,
+                   cudaStream_t s);
 int noise_residual_f64(double* r, const double* x, const double* diag, int64_t n, int64_t B,
                        cudaStream_t s);
 

@@ -110,6 +110,155 @@ gemm_f64_kernel(int64_t M, int64_t N, int64_t K, double alpha, const double* __r
   }
 }
 
+// ------------------------------------------------------------------ GEMM (double-FP32)
+// Same interface and tiling as gemm_f64_kernel, for GB300 where FP64 issues at 1/64
+// of the FP32 rate: operand tiles are split on load into float pairs hi + lo (one
+// FP64 subtraction per loaded element, reused BM or BN times), products are formed
+// exactly in float pairs (FMA error of hi*hi plus the two cross terms) and summed
+// with Knuth's two-sum, and the epilogue applies alpha and beta in FP64.  About 48
+// significant bits per operation: FP64-level results for the Gram product, the
+// Cholesky updates and the triangular solves.
+namespace {
+__device__ __forceinline__ void dd_split(double x, float& h, float& l) {
+  h = __double2float_rn(x);
+  l = __double2float_rn(x - (double)h);
+}
+__device__ __forceinline__ void dd_mac(float& Sh, float& Sl, float ah, float al, float bh, float bl) {
+  float p = __fmul_rn(ah, bh);
+  float pe = __fmaf_rn(ah, bh, -p);
+  pe = __fmaf_rn(ah, bl, pe);
+  pe = __fmaf_rn(al, bh, pe);
+  float s = __fadd_rn(Sh, p);
+  float bb = __fsub_rn(s, Sh);
+  float e = __fadd_rn(__fsub_rn(Sh, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  Sh = s;
+  Sl = __fadd_rn(Sl, __fadd_rn(e, pe));
+}
+}  // namespace
+
+template <bool TRANSB, int BM, int BN>
+__global__ void __launch_bounds__(256)
+gemm_df64_kernel(int64_t M, int64_t N, int64_t K, double alpha, const double* __restrict__ A,
+                 int64_t lda, int64_t sA, const double* __restrict__ Bm, int64_t ldb, int64_t sB,
+                 double beta, double* __restrict__ C, int64_t ldc, int64_t sC, int64_t batch,
+                 bool lower_only) {
+  constexpr int TM = BM / 16, TN = BN / 16;
+  __shared__ float2 As[GBK][BM + 1];  // (hi, lo)
+  __shared__ float2 Bs[GBK][BN + 1];
+  const int64_t m0 = (int64_t)blockIdx.x * BM;
+  const int64_t n0 = (int64_t)blockIdx.y * BN;
+  if (lower_only && m0 + BM - 1 < n0) return;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  for (int64_t bz = blockIdx.z; bz < batch; bz += gridDim.z) {
+    const double* Ab = A + bz * sA;
+    const double* Bb = Bm + bz * sB;
+    double* Cb = C + bz * sC;
+    float ah_[TM][TN], al_[TM][TN];
+#pragma unroll
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+      for (int b = 0; b < TN; ++b) ah_[a][b] = al_[a][b] = 0.f;
+    for (int64_t k0 = 0; k0 < K; k0 += GBK) {
+#pragma unroll
+      for (int e = 0; e < (BM * GBK) / 256; ++e) {
+        int idx = threadIdx.x + 256 * e;
+        int r = idx >> 4, c = idx & 15;
+        int64_t gm = m0 + r, gk = k0 + c;
+        double v = (gm < M && gk < K) ? Ab[gm * lda + gk] : 0.0;
+        float h, l;
+        dd_split(v, h, l);
+        As[c][r] = make_float2(h, l);
+      }
+      if (TRANSB) {
+#pragma unroll
+        for (int e = 0; e < (BN * GBK) / 256; ++e) {
+          int idx = threadIdx.x + 256 * e;
+          int r = idx >> 4, c = idx & 15;
+          int64_t gn = n0 + r, gk = k0 + c;
+          double v = (gn < N && gk < K) ? Bb[gn * ldb + gk] : 0.0;
+          float h, l;
+          dd_split(v, h, l);
+          Bs[c][r] = make_float2(h, l);
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < (BN * GBK) / 256; ++e) {
+          int idx = threadIdx.x + 256 * e;
+          int r = idx / BN, c = idx % BN;
+          int64_t gk = k0 + r, gn = n0 + c;
+          double v = (gn < N && gk < K) ? Bb[gk * ldb + gn] : 0.0;
+          float h, l;
+          dd_split(v, h, l);
+          Bs[r][c] = make_float2(h, l);
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < GBK; ++kk) {
+        float2 av[TM], bv[TN];
+#pragma unroll
+        for (int a = 0; a < TM; ++a) av[a] = As[kk][ty + 16 * a];
+#pragma unroll
+        for (int b = 0; b < TN; ++b) bv[b] = Bs[kk][tx + 16 * b];
+#pragma unroll
+        for (int a = 0; a < TM; ++a)
+#pragma unroll
+          for (int b = 0; b < TN; ++b) dd_mac(ah_[a][b], al_[a][b], av[a].x, av[a].y, bv[b].x, bv[b].y);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < TM; ++a) {
+      int64_t gm = m0 + ty + 16 * a;
+      if (gm >= M) continue;
+#pragma unroll
+      for (int b = 0; b < TN; ++b) {
+        int64_t gn = n0 + tx + 16 * b;
+        if (gn >= N) continue;
+        double* cp = Cb + gm * ldc + gn;
+        double v = alpha * ((double)ah_[a][b] + (double)al_[a][b]);
+        if (beta != 0.0) v = fma(beta, *cp, v);
+        *cp = v;
+      }
+    }
+  }
+}
+
+int gemm_df64(bool transB, int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda,
+              int64_t sA, const double* Bm, int64_t ldb, int64_t sB, double beta, double* C, int64_t ldc,
+              int64_t sC, int64_t batch, bool lower_only, cudaStream_t s) {
+  if (M <= 0 || N <= 0 || batch <= 0) return 0;
+  int tile = 16;
+  {
+    const int64_t want = 2 * (int64_t)num_sms();
+    for (int t : {64, 32}) {
+      if (((M + t - 1) / t) * ((N + t - 1) / t) * std::min<int64_t>(batch, 65535) >= want) {
+        tile = t;
+        break;
+      }
+    }
+  }
+  const unsigned gz = (unsigned)std::min<int64_t>(batch, 65535);
+#define BTI_DF_LAUNCH(T_)                                                                                    \
+  {                                                                                                          \
+    dim3 grid((unsigned)((M + T_ - 1) / T_), (unsigned)((N + T_ - 1) / T_), gz);                            \
+    if (transB)                                                                                              \
+      gemm_df64_kernel<true, T_, T_><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, sA, Bm, ldb, sB, beta, C,  \
+                                                           ldc, sC, batch, lower_only);                      \
+    else                                                                                                     \
+      gemm_df64_kernel<false, T_, T_><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, sA, Bm, ldb, sB, beta, C, \
+                                                            ldc, sC, batch, lower_only);                     \
+  }
+  if (tile == 64)
+    BTI_DF_LAUNCH(64)
+  else if (tile == 32)
+    BTI_DF_LAUNCH(32)
+  else
+    BTI_DF_LAUNCH(16)
+#undef BTI_DF_LAUNCH
+  return 1;
+}
+
 // Small-M products (M <= 8 rows, e.g. a handful of right-hand sides).
 // NN: C[m][n] (+)= alpha sum_k A[m][k] B[k][n]; one thread per column n.
 template <int MM>
@@ -339,7 +488,17 @@ potrf_diag_kernel(double* A, int64_t lda, int kb, double* Linv, int* status, int
   }
 }
 
-int64_t cholesky_f64(double* A, int64_t n, double* Linv, double* work, int* status, cudaStream_t s) {
+// GEMM used by the blocked factorisation and solves: FP64, or double-FP32 for products
+// with more than 8 rows when dd is set (tiny ones stay on the FP64 small-M kernels).
+static int gemm_sel(bool dd, bool transB, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
+                    int64_t lda, const double* Bm, int64_t ldb, double beta, double* C, int64_t ldc, bool lower_only,
+                    cudaStream_t s) {
+  if (dd && M > 8)
+    return gemm_df64(transB, M, N, K, alpha, A, lda, 0, Bm, ldb, 0, beta, C, ldc, 0, 1, lower_only, s);
+  return gemm_f64(transB, M, N, K, alpha, A, lda, 0, Bm, ldb, 0, beta, C, ldc, 0, 1, lower_only, s);
+}
+
+int64_t cholesky_f64(double* A, int64_t n, double* Linv, double* work, int* status, cudaStream_t s, bool dd) {
   const int nb = kCholNB;
   int64_t launches = 0;
   for (int64_t k = 0; k < n; k += nb) {
@@ -350,13 +509,12 @@ int64_t cholesky_f64(double* A, int64_t n, double* Linv, double* work, int* stat
     int64_t m = n - k - kb;
     if (m <= 0) continue;
     // panel: P = A[k+kb:, k:k+kb] L_kk^{-T}
-    launches += gemm_f64(true, m, kb, kb, 1.0, A + (k + kb) * n + k, n, 0, Lk, nb, 0, 0.0, work, kb, 0, 1,
-             false, s);
+    launches += gemm_sel(dd, true, m, kb, kb, 1.0, A + (k + kb) * n + k, n, Lk, nb, 0.0, work, kb, false, s);
     cudaMemcpy2DAsync(A + (k + kb) * n + k, n * sizeof(double), work, kb * sizeof(double),
                       kb * sizeof(double), m, cudaMemcpyDeviceToDevice, s);
     // trailing update of the lower triangle: A22 -= P P^T
-    launches += gemm_f64(true, m, m, kb, -1.0, work, kb, 0, work, kb, 0, 1.0, A + (k + kb) * n + (k + kb),
-                         n, 0, 1, true, s);
+    launches += gemm_sel(dd, true, m, m, kb, -1.0, work, kb, work, kb, 1.0, A + (k + kb) * n + (k + kb), n, true,
+                         s);
   }
   return launches;
 }
@@ -368,7 +526,7 @@ size_t trsm_work_elems(int64_t n, int64_t B) { return (size_t)B * kCholNB; }
 // backward: L^T Z = Y; both blocked by the factor's diagonal blocks, whose
 // inverses Linv come from the factorisation.
 int64_t trsm_lower_f64(const double* Lm, const double* Linv, int64_t n, double* X, int64_t B,
-                       double* work, const int* status, cudaStream_t s) {
+                       double* work, const int* status, cudaStream_t s, bool dd) {
   (void)status;
   const int nb = kCholNB;
   int64_t launches = 0;
@@ -376,24 +534,24 @@ int64_t trsm_lower_f64(const double* Lm, const double* Linv, int64_t n, double* 
     int kb = (int)std::min<int64_t>(nb, n - k);
     const double* Lk = Linv + (k / nb) * nb * nb;
     // Y_k = X_k L_kk^{-T}
-    launches += gemm_f64(true, B, kb, kb, 1.0, X + k, n, 0, Lk, nb, 0, 0.0, work, kb, 0, 1, false, s);
+    launches += gemm_sel(dd, true, B, kb, kb, 1.0, X + k, n, Lk, nb, 0.0, work, kb, false, s);
     cudaMemcpy2DAsync(X + k, n * sizeof(double), work, kb * sizeof(double), kb * sizeof(double), B,
                       cudaMemcpyDeviceToDevice, s);
     int64_t m = n - k - kb;
     if (m > 0)  // X[:, k+kb:] -= Y_k L[k+kb:, k:k+kb]^T
-      launches += gemm_f64(true, B, m, kb, -1.0, X + k, n, 0, Lm + (k + kb) * n + k, n, 0, 1.0, X + k + kb, n,
-               0, 1, false, s);
+      launches += gemm_sel(dd, true, B, m, kb, -1.0, X + k, n, Lm + (k + kb) * n + k, n, 1.0, X + k + kb, n, false,
+                           s);
   }
   int64_t last = ((n - 1) / nb) * nb;
   for (int64_t k = last; k >= 0; k -= nb) {
     int kb = (int)std::min<int64_t>(nb, n - k);
     const double* Lk = Linv + (k / nb) * nb * nb;
     // Z_k = X_k L_kk^{-1}
-    launches += gemm_f64(false, B, kb, kb, 1.0, X + k, n, 0, Lk, nb, 0, 0.0, work, kb, 0, 1, false, s);
+    launches += gemm_sel(dd, false, B, kb, kb, 1.0, X + k, n, Lk, nb, 0.0, work, kb, false, s);
     cudaMemcpy2DAsync(X + k, n * sizeof(double), work, kb * sizeof(double), kb * sizeof(double), B,
                       cudaMemcpyDeviceToDevice, s);
     if (k > 0)  // X[:, 0:k] -= Z_k L[k:k+kb, 0:k]
-      launches += gemm_f64(false, B, k, kb, -1.0, X + k, n, 0, Lm + k * n, n, 0, 1.0, X, n, 0, 1, false, s);
+      launches += gemm_sel(dd, false, B, k, kb, -1.0, X + k, n, Lm + k * n, n, 1.0, X, n, false, s);
   }
   return launches;
 }
@@ -500,6 +658,42 @@ __global__ void f64_to_f32_kernel(const double* __restrict__ x, float* __restric
 int convert_f64_to_f32(const double* x, float* y, int64_t n, cudaStream_t s) {
   if (n <= 0) return 0;
   f64_to_f32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, y, n);
+  return 1;
+}
+
+}  // namespace bti
+
+namespace bti {
+
+// ------------------------------------------------------------------ elliptic prior operator
+// out = A_s m per time block, A_s = alpha1 I - alpha2 Delta_h on the gx x gy grid
+// (node ix * gy + iy), Delta_h the 5-point graph Laplacian with homogeneous Neumann
+// boundaries: (A_s u)_p = (alpha1 + alpha2 deg(p)) u_p - alpha2 sum_{q ~ p} u_q.
+// Eq. (5.1) uses A_s^{-2} as the prior covariance, so 0.5 ||A_s m_t||^2 is the prior
+// term of the negative log-posterior for each time block.
+__global__ void elliptic_apply_kernel(const double* __restrict__ m, double* __restrict__ out, int gx, int gy,
+                                      double a1, double a2, int64_t nblocks) {
+  const int64_t Nm = (int64_t)gx * gy;
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nblocks * Nm) return;
+  const int64_t blk = idx / Nm;
+  const int p = (int)(idx - blk * Nm);
+  const int ix = p / gy, iy = p - ix * gy;
+  const double* u = m + blk * Nm;
+  double nb = 0.0;
+  int deg = 0;
+  if (ix > 0) { nb += u[p - gy]; ++deg; }
+  if (ix + 1 < gx) { nb += u[p + gy]; ++deg; }
+  if (iy > 0) { nb += u[p - 1]; ++deg; }
+  if (iy + 1 < gy) { nb += u[p + 1]; ++deg; }
+  out[idx] = fma(a1 + a2 * deg, u[p], -a2 * nb);
+}
+
+int elliptic_apply(const double* m, double* out, int gx, int gy, double a1, double a2, int64_t nblocks,
+                   cudaStream_t s) {
+  int64_t total = nblocks * gx * gy;
+  if (total <= 0) return 0;
+  elliptic_apply_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(m, out, gx, gy, a1, a2, nblocks);
   return 1;
 }
 

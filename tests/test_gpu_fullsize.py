@@ -120,6 +120,9 @@ def test_batched_inversion_full_size():
 
 
 def test_diff_gradient_full_size():
+    """The differentiation workload: loss 0.5 ||F m - d||^2 / sigma^2 plus the elliptic
+    prior term (reading R13, alpha1 = alpha2 = 1) through autograd, against the oracle
+    gradient; the misfit-only gradient as well."""
     p = synthetic.DIFF
     F = p.blocks_F()
     m0 = p.vectors_m(1)
@@ -131,14 +134,23 @@ def test_diff_gradient_full_size():
     loss = 0.5 * (r * r).sum() / p.sigma2
     loss.backward()
     g = m.grad.detach().cpu().numpy()
+    m2 = torch.from_numpy(m0).cuda().requires_grad_(True)
+    full = bti.map_loss(h, m2, torch.from_numpy(dobs).cuda(), p.sigma2, p.gx, p.gy)
+    full.backward()
+    g_full = m2.grad.detach().cpu().numpy()
     h.close()
     g_or = oracle.loss_gradient(F, m0[0], dobs[0], p.sigma2)
     assert relb(g, g_or[None]) < 1e-12
+    A = oracle.elliptic_operator(p.gx, p.gy, 1.0, 1.0)
+    g_full_or = oracle.loss_gradient(F, m0[0], dobs[0], p.sigma2, A)
+    assert relb(g_full, g_full_or[None]) < 1e-12
 
 
-def test_batched_mixed_precision_solve_full_size():
-    """The batched workload with K assembled in FP32, FP64 Cholesky, and refinement
-    with double-FP32 operators: FP64-level m_map and q_map against the oracle."""
+@pytest.mark.parametrize("dense", ["f64", "df64"])
+def test_batched_mixed_precision_solve_full_size(dense):
+    """The batched workload with K assembled in FP32, Cholesky and solves in FP64 (or
+    double-FP32), and refinement with double-FP32 operators: FP64-level m_map and
+    q_map against the oracle."""
     p = synthetic.BATCHED
     F = p.blocks_F()
     Fq = p.blocks_Fq()
@@ -148,6 +160,8 @@ def test_batched_mixed_precision_solve_full_size():
     h.set_blocks(bti.OP_FQ, torch.from_numpy(Fq).cuda(), bti.DF64)
     h.set_prior_se_grid(p.gx, p.gy, p.ell, p.sigma_p, bti.DF64)
     h.set_noise(p.sigma2)
+    if dense == "df64":
+        h.set_dense_precision(bti.DF64)
     h.build_K_prec(p.col_block, bti.F32)
     h.factor_K()
     m_map = torch.empty((p.n_vectors, p.Nt, p.Nm), dtype=torch.float64, device="cuda")

@@ -376,3 +376,59 @@ def test_mixed_precision_solve_recovers_fp64(case):
     assert relb(host(m), m_or) < 1e-12
     assert relb(host(q), oracle.qoi_map(Fq, m_or)) < 1e-12
     h.close()
+
+
+def test_dense_double_fp32_path():
+    """K assembly, Cholesky and solves in double-FP32 arithmetic: K and L close to the
+    oracle's, and m_map / q_map at the FP64 tolerance after one refinement step."""
+    p, F, Fq, G, d_obs = tiny_problem()
+    h = make_handle(F, Fq, bti.DF64)
+    h.set_prior_se_grid(p.gx, p.gy, p.ell, p.sigma_p, bti.DF64)
+    h.set_noise(p.sigma2)
+    h.set_dense_precision(bti.DF64)
+    h.build_K()
+    K_gpu = host(h.copy_K())
+    K_or = oracle.assemble_K(F, G, p.sigma2)
+    low = np.tril_indices(K_or.shape[0])
+    assert np.linalg.norm(K_gpu[low] - K_or[low]) / np.linalg.norm(K_or[low]) < 1e-12
+    h.factor_K()
+    L_gpu = host(h.copy_K())
+    L_or = oracle.cholesky_lower(K_or)
+    assert np.linalg.norm(L_gpu[low] - L_or[low]) / np.linalg.norm(L_or[low]) < 1e-11
+    m = torch.empty((1, p.Nt, p.Nm), dtype=torch.float64, device="cuda")
+    q = torch.empty((1, p.Nt, p.Nq), dtype=torch.float64, device="cuda")
+    h.infer_map(cuda(d_obs), m, refine_iters=1)
+    h.predict_qoi(m, q)
+    m_or = oracle.map_point(F, G, p.sigma2, d_obs)
+    assert relb(host(m), m_or) < 1e-12
+    assert relb(host(q), oracle.qoi_map(Fq, m_or)) < 1e-12
+    assert bti.lib().bti_set_dense_precision(h.raw, bti.F32) == 1
+    h.close()
+
+
+def test_elliptic_prior_operator_and_full_map_loss_gradient():
+    """A_s m (Eq. (5.1) operator) and the gradient of the full negative log-posterior
+    (misfit + elliptic prior term) through the library kernels, against the oracle."""
+    p = synthetic.small("elliptic", 6, 9, 4, 12)
+    F = p.blocks_F()
+    h = make_handle(F, None, bti.DF64)
+    A = oracle.elliptic_operator(p.gx, p.gy, 1.3, 0.7)
+    m = p.vectors_m(2)
+    out = torch.empty((2, p.Nt, p.Nm), dtype=torch.float64, device="cuda")
+    h.apply_elliptic(p.gx, p.gy, 1.3, 0.7, cuda(m), out)
+    ref = (A @ m.reshape(-1, p.Nm).T).T.reshape(m.shape)
+    assert relb(host(out), ref) < 1e-14
+    h.apply_elliptic(p.gx, p.gy, 1.3, 0.7, cuda(m), out, squared=True)
+    ref2 = (A @ (A @ m.reshape(-1, p.Nm).T)).T.reshape(m.shape)
+    assert relb(host(out), ref2) < 1e-14
+    # full loss with the prior term, alpha1 = alpha2 = 1 (reading R13)
+    A1 = oracle.elliptic_operator(p.gx, p.gy, 1.0, 1.0)
+    d = p.vectors_d(1)
+    s2 = 0.05
+    mg = cuda(m[:1]).requires_grad_(True)
+    loss = bti.map_loss(h, mg, cuda(d), s2, p.gx, p.gy)
+    loss.backward()
+    g_or = oracle.loss_gradient(F, m[0], d[0], s2, A1)
+    assert relb(host(mg.grad), g_or[None]) < 1e-12
+    assert abs(float(loss.detach()) - oracle.loss(F, m[0], d[0], s2, A1)) <= 1e-12 * abs(float(loss.detach()))
+    h.close()
