@@ -70,6 +70,42 @@ def dist_env():
     return world, rank, local
 
 
+class Replicas:
+    """Host-side plumbing for N independent replicas (one process per GPU): a barrier
+    around the timed region and the max of the per-rank times.  No data-path
+    collective: every rank runs the whole workload on its own device."""
+
+    def __init__(self, world, rank, backend="nccl"):
+        import torch.distributed as dist
+
+        self.world, self.rank, self.dist = world, rank, dist
+        if world > 1 and not dist.is_initialized():
+            dist.init_process_group(backend, init_method="env://")
+
+    def barrier(self):
+        if self.world > 1:
+            self.dist.barrier()
+
+    def max_ms(self, ms, device=None):
+        if self.world == 1:
+            return ms
+        import torch
+
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.world > 1 and self.dist.is_initialized():
+            self.dist.destroy_process_group()
+
+
+def aggregate_gbs(world, bytes_per_step, steps, max_ms):
+    """Whole-job throughput: every replica moves bytes_per_step per step; the slowest
+    rank's time bounds the job."""
+    return world * bytes_per_step * steps / (max_ms * 1e-3) / 1e9
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -242,17 +278,14 @@ def run_reference(args):
 
 # --------------------------------------------------------------------------------------------
 def run_ours(args):
-    import numpy as np
     import torch
-    import torch.distributed as dist
 
     import paper_2501_14911_gb300 as bti
     from paper_2501_14911_gb300 import synthetic
 
     world, rank, local = dist_env()
-    if world > 1:
-        dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
+    reps = Replicas(world, rank, "nccl")
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     hbm_peak, _, peak_src = load_peaks()
@@ -280,8 +313,7 @@ def run_ours(args):
             h.apply_FT(d[b], om[b])
 
     def barrier():
-        if world > 1:
-            dist.barrier()
+        reps.barrier()
 
     def timed(fn, steps, warmup, prof_handle=None):
         for _ in range(warmup):
@@ -305,10 +337,7 @@ def run_ours(args):
         if prof_handle is not None:
             prof = prof_handle.profile_read()
             prof_handle.profile_enable(False)
-        if world > 1:
-            t = torch.tensor([ms], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = reps.max_ms(ms, dev)
         return ms, prof
 
     props = torch.cuda.get_device_properties(dev)
@@ -371,7 +400,7 @@ def run_ours(args):
             clk = clocks.stop()
         bytes_step = 2 * V * bytes_per_call(p, esize, csize)
         res[name] = {"ms": ms, "prof": prof, "bytes_step": bytes_step, "autotune": tune,
-                     "value": world * bytes_step * args.steps / (ms * 1e-3) / 1e9,
+                     "value": aggregate_gbs(world, bytes_step, args.steps, ms),
                      "roofline": roofline(prof, csize, name)}
         if headline and not args.no_e2e:
             e2e = e2e_block(args, h, p, m_host, d_host, dev, timed, world, bytes_step)
@@ -418,8 +447,7 @@ def run_ours(args):
                                           f"pair(s) in {dt:.1f} s, scaled to the GPU formulation's bytes"}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+    reps.close()
     return 0
 
 
@@ -470,7 +498,7 @@ def e2e_block(args, h, p, m_host, d_host, dev, timed, world, bytes_step):
 
     ms, _ = timed(e2e_step, args.steps, min(args.warmup, 3))
     vec_bytes = (p.Nt * p.Nm + p.Nt * p.Nd) * 8
-    return {"value": world * bytes_step * args.steps / (ms * 1e-3) / 1e9, "unit": "GB/s",
+    return {"value": aggregate_gbs(world, bytes_step, args.steps, ms), "unit": "GB/s",
             "ms_per_step": ms / args.steps, "h2d_bytes_per_step": V * vec_bytes,
             "d2h_bytes_per_step": V * vec_bytes,
             "note": "pinned host buffers; H2D and D2H on two copy streams, double-buffered against compute"}

@@ -432,3 +432,20 @@ def test_elliptic_prior_operator_and_full_map_loss_gradient():
     assert relb(host(mg.grad), g_or[None]) < 1e-12
     assert abs(float(loss.detach()) - oracle.loss(F, m[0], d[0], s2, A1)) <= 1e-12 * abs(float(loss.detach()))
     h.close()
+
+
+def test_non_finite_input_is_reported_not_spd():
+    """A NaN injected on the host (in the noise variances) reaches the first Cholesky
+    pivot it touches, which the factorisation reports instead of producing NaN factors."""
+    p = synthetic.small("nan_noise", 4, 4, 3, 10)
+    F = p.blocks_F()
+    var = np.full((10, 3), 1e-2)
+    var[2, 0] = np.nan  # data index 6 -> pivot 7
+    h = make_handle(F)
+    h.set_prior_se_grid(4, 4, 3.0, 1.0)
+    h.set_noise(0.0, cuda(var))
+    h.build_K()
+    with pytest.raises(bti.BtiError) as e:
+        h.factor_K()
+    assert e.value.status == 6 and "pivot 7" in e.value.message
+    h.close()
