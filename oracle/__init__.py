@@ -53,6 +53,9 @@ from .inversion import (
     map_point,
     map_point_woodbury_form,
     qoi_map,
+    qoi_data_gram,
+    d2q_map,
+    qoi_posterior_covariance,
     loss,
     loss_gradient,
 )
@@ -63,5 +66,6 @@ __all__ = [
     "se_covariance_1d", "se_covariance", "prior_blocks", "prior_sample",
     "elliptic_operator",
     "assemble_K", "assemble_K_columns", "cholesky_lower", "solve_K",
-    "map_point", "map_point_woodbury_form", "qoi_map", "loss", "loss_gradient",
+    "map_point", "map_point_woodbury_form", "qoi_map", "qoi_data_gram", "d2q_map",
+    "qoi_posterior_covariance", "loss", "loss_gradient",
 ]

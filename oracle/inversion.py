@@ -152,3 +152,53 @@ def loss_gradient(F_blocks, m, d, noise, A_s=None):
         flat = m.reshape(-1, Nm).T
         g = g + (A_s.T @ (A_s @ flat)).T.reshape(m.shape)
     return g
+
+
+def qoi_data_gram(Fq_blocks, G_blocks):
+    """X = F_q G^* as a dense (N_q N_t) x (N_d N_t) matrix.
+
+    Block (t, t') is sum_{s=0}^{min(t,t')} (F_q)_{t-s} G_{t'-s}^T (both maps are block
+    lower-triangular Toeplitz in time); with W(k, k') = (F_q)_k G_{k'}^T the blocks
+    accumulate along block diagonals exactly as in assemble_K, on both sides of the
+    diagonal since X is not symmetric.
+    """
+    Fq_blocks = np.asarray(Fq_blocks, dtype=np.float64)
+    G_blocks = np.asarray(G_blocks, dtype=np.float64)
+    Nt, Rq, Nm = Fq_blocks.shape
+    R = G_blocks.shape[1]
+    W = Fq_blocks.reshape(Nt * Rq, Nm) @ G_blocks.reshape(Nt * R, Nm).T
+    X = W.copy()
+    for t in range(1, Nt):
+        rows = slice(t * Rq, (t + 1) * Rq)
+        prev = slice((t - 1) * Rq, t * Rq)
+        X[rows, R:] += X[prev, : (Nt - 1) * R]
+    return X
+
+
+def d2q_map(Fq_blocks, F_blocks, G_blocks, noise, L=None):
+    """The data-to-QoI map Q of Eq. (4.11) with zero prior mean, (N_q N_t) x (N_d N_t).
+
+    Eq. (4.11): Q = F_q (I - G^* K^{-1} F) G^* Gamma_n^{-1}.  Since F G^* = K - Gamma_n,
+    K^{-1} F G^* Gamma_n^{-1} = Gamma_n^{-1} - K^{-1}, hence Q = F_q G^* K^{-1}; the rows
+    of Q are the rows of F_q G^* times K^{-1} (K symmetric).  The long form is pinned
+    against this in the tests.
+    """
+    F_blocks = np.asarray(F_blocks, dtype=np.float64)
+    Nt, R, Nm = F_blocks.shape
+    if L is None:
+        L = cholesky_lower(assemble_K(F_blocks, G_blocks, noise))
+    X = qoi_data_gram(Fq_blocks, G_blocks)
+    return solve_K(L, X)
+
+
+def qoi_posterior_covariance(Fq_blocks, Gq_blocks, F_blocks, G_blocks, noise, L=None):
+    """Gamma_post(q) of Eq. (4.10): F_q (I - G^* K^{-1} F) G_q^*, with G_q^* = Gamma_prior F_q^T.
+
+    Expanded: F_q G_q^* - (F_q G^*) K^{-1} (F G_q^*), and F G_q^* = (F_q G^*)^T because
+    Gamma_prior is symmetric; so Gamma_post(q) = X_qq - Q X^T with X = F_q G^* and
+    X_qq = F_q Gamma_prior F_q^T (the same Gram accumulation with G_q blocks).
+    """
+    X_qq = qoi_data_gram(Fq_blocks, Gq_blocks)
+    X = qoi_data_gram(Fq_blocks, G_blocks)
+    Q = d2q_map(Fq_blocks, F_blocks, G_blocks, noise, L)
+    return X_qq - Q @ X.T

@@ -365,3 +365,42 @@ def test_single_block_outputs_match_full_products():
         assert rel(oracle.p2o_apply_block(blocks, m, t), full[t]) < 1e-15
         assert rel(oracle.p2o_apply_block(blocks, m, t), (P @ m.reshape(-1)).reshape(9, 3)[t]) < 1e-14
         assert rel(oracle.p2o_apply_adjoint_block(blocks, d, t), fullT[t]) < 1e-15
+
+
+# ---------------------------------------------------------------- d2q map and QoI covariance
+
+def test_d2q_map_equals_eq_4_11_long_form_and_reproduces_q_map():
+    F, G, Cs, s2, rng = _tiny_problem(gx=4, gy=3, Nd=3, Nt=6, sigma2=0.02)
+    Nt, Nd, Nm = F.shape
+    Fq = rng.standard_normal((Nt, 2, Nm)) * np.exp(-np.arange(Nt) / 3.0)[:, None, None]
+    Q = oracle.d2q_map(Fq, F, G, s2)
+    # Eq. (4.11) term by term with dense matrices
+    P, Pq = oracle.p2o_dense(F), oracle.p2o_dense(Fq)
+    Gstar = np.kron(np.eye(Nt), Cs) @ P.T
+    K = s2 * np.eye(Nt * Nd) + P @ Gstar
+    long = Pq @ (np.eye(Nt * Nm) - Gstar @ np.linalg.solve(K, P)) @ Gstar / s2
+    assert rel(Q, long) < 1e-10
+    # q_map = Q d_obs equals the push-forward of m_map (Eq. (4.14) vs Eq. (4.2))
+    d = rng.standard_normal((Nt, Nd))
+    q_push = oracle.qoi_map(Fq, oracle.map_point(F, G, s2, d))
+    assert rel(Q @ d.reshape(-1), q_push.reshape(-1)) < 1e-12
+    # the Gram accumulation equals the dense F_q G^*
+    assert rel(oracle.qoi_data_gram(Fq, G), Pq @ Gstar) < 1e-14
+
+
+def test_qoi_posterior_covariance_equals_eq_4_10_and_push_forward():
+    F, G, Cs, s2, rng = _tiny_problem(gx=3, gy=3, Nd=2, Nt=5, sigma2=0.05)
+    Nt, Nd, Nm = F.shape
+    Fq = rng.standard_normal((Nt, 2, Nm))
+    Gq = oracle.prior_blocks(Fq, Cs)
+    C = oracle.qoi_posterior_covariance(Fq, Gq, F, G, s2)
+    P, Pq = oracle.p2o_dense(F), oracle.p2o_dense(Fq)
+    Gp = np.kron(np.eye(Nt), Cs)
+    K = s2 * np.eye(Nt * Nd) + P @ Gp @ P.T
+    # Eq. (4.10): F_q (I - G* K^-1 F) G_q*
+    ref = Pq @ (np.eye(Nt * Nm) - Gp @ P.T @ np.linalg.solve(K, P)) @ Gp @ Pq.T
+    assert rel(C, ref) < 1e-11
+    np.testing.assert_allclose(C, C.T, rtol=0, atol=1e-10 * np.abs(C).max())
+    # Gamma_post(q) = F_q Gamma_post(m) F_q^T with the Woodbury Gamma_post(m) of Eq. (4.6)
+    Gpost = Gp @ (np.eye(Nt * Nm) - P.T @ np.linalg.solve(K, P @ Gp))
+    assert rel(C, Pq @ Gpost @ Pq.T) < 1e-10
