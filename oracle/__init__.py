@@ -56,6 +56,9 @@ from .inversion import (
     qoi_data_gram,
     d2q_map,
     qoi_posterior_covariance,
+    prior_apply,
+    posterior_cov_apply,
+    map_point_with_prior_mean,
     loss,
     loss_gradient,
 )
@@ -67,5 +70,6 @@ __all__ = [
     "elliptic_operator",
     "assemble_K", "assemble_K_columns", "cholesky_lower", "solve_K",
     "map_point", "map_point_woodbury_form", "qoi_map", "qoi_data_gram", "d2q_map",
-    "qoi_posterior_covariance", "loss", "loss_gradient",
+    "qoi_posterior_covariance", "prior_apply", "posterior_cov_apply", "map_point_with_prior_mean",
+    "loss", "loss_gradient",
 ]

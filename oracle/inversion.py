@@ -202,3 +202,38 @@ def qoi_posterior_covariance(Fq_blocks, Gq_blocks, F_blocks, G_blocks, noise, L=
     X = qoi_data_gram(Fq_blocks, G_blocks)
     Q = d2q_map(Fq_blocks, F_blocks, G_blocks, noise, L)
     return X_qq - Q @ X.T
+
+
+def prior_apply(Cs, v):
+    """Gamma_prior v = (I_t (x) C_s) v: the spatial covariance applied to each time block."""
+    v = np.asarray(v, dtype=np.float64)
+    return v @ np.asarray(Cs, dtype=np.float64).T
+
+
+def posterior_cov_apply(F_blocks, G_blocks, Cs, noise, v, L=None):
+    """Gamma_post(m) v by Eq. (4.7): (I - G^* K^{-1} F) Gamma_prior v, v: [..., N_t, N_m]."""
+    F_blocks = np.asarray(F_blocks, dtype=np.float64)
+    Nt, R, Nm = F_blocks.shape
+    if L is None:
+        L = cholesky_lower(assemble_K(F_blocks, G_blocks, noise))
+    w = prior_apply(Cs, v)
+    y = p2o_apply(F_blocks, w)
+    x = solve_K(L, y.reshape(-1, Nt * R)).reshape(y.shape)
+    return w - p2o_apply_adjoint(G_blocks, x)
+
+
+def map_point_with_prior_mean(F_blocks, G_blocks, noise, d_obs, m_prior, L=None):
+    """m_map of Eq. (4.13) with the prior-mean term of Eq. (4.8).
+
+    Eq. (4.13): m_map = (I - G^* K^{-1} F) G^* Gamma_n^{-1} d + m_map^prior with
+    Eq. (4.8): m_map^prior = (I - G^* K^{-1} F) m_prior.  Using the identity of
+    map_point for the first term: m_map = G^* K^{-1} d + m_prior - G^* K^{-1} F m_prior.
+    """
+    F_blocks = np.asarray(F_blocks, dtype=np.float64)
+    Nt, R, Nm = F_blocks.shape
+    if L is None:
+        L = cholesky_lower(assemble_K(F_blocks, G_blocks, noise))
+    m_prior = np.asarray(m_prior, dtype=np.float64)
+    r = np.asarray(d_obs, dtype=np.float64) - p2o_apply(F_blocks, m_prior)
+    x = solve_K(L, r.reshape(-1, Nt * R)).reshape(r.shape)
+    return m_prior + p2o_apply_adjoint(G_blocks, x)

@@ -404,3 +404,45 @@ def test_qoi_posterior_covariance_equals_eq_4_10_and_push_forward():
     # Gamma_post(q) = F_q Gamma_post(m) F_q^T with the Woodbury Gamma_post(m) of Eq. (4.6)
     Gpost = Gp @ (np.eye(Nt * Nm) - P.T @ np.linalg.solve(K, P @ Gp))
     assert rel(C, Pq @ Gpost @ Pq.T) < 1e-10
+
+
+# ---------------------------------------------------------------- posterior covariance actions, prior mean
+
+def _elliptic_problem(seed=41, gx=3, gy=4, Nd=2, Nt=5, s2=0.03):
+    rng = np.random.default_rng(seed)
+    Nm = gx * gy
+    F = rng.standard_normal((Nt, Nd, Nm)) * np.exp(-np.arange(Nt) / 2.0)[:, None, None]
+    A = oracle.elliptic_operator(gx, gy, 1.0, 1.0).toarray()
+    Cs = np.linalg.inv(A @ A)
+    Cs = 0.5 * (Cs + Cs.T)
+    return F, oracle.prior_blocks(F, Cs), Cs, A, s2, rng
+
+
+def test_posterior_covariance_action_is_inverse_hessian():
+    """Gamma_post(m) of Eq. (4.7) equals H^{-1} of Eq. (2.13) with an invertible prior."""
+    F, G, Cs, A, s2, rng = _elliptic_problem()
+    Nt, Nd, Nm = F.shape
+    P = oracle.p2o_dense(F)
+    H = P.T @ P / s2 + np.kron(np.eye(Nt), A @ A)
+    V = rng.standard_normal((3, Nt, Nm))
+    got = oracle.posterior_cov_apply(F, G, Cs, s2, V)
+    for b in range(3):
+        assert rel(got[b].reshape(-1), np.linalg.solve(H, V[b].reshape(-1))) < 1e-10
+    np.testing.assert_allclose(oracle.prior_apply(Cs, V[0]), (np.kron(np.eye(Nt), Cs) @ V[0].reshape(-1)).reshape(Nt, Nm),
+                               rtol=1e-13, atol=1e-14)
+
+
+def test_map_point_with_prior_mean_is_closed_form():
+    """Eq. (4.13) + Eq. (4.8) against the normal equations of Eq. (2.12) with m_prior != 0."""
+    F, G, Cs, A, s2, rng = _elliptic_problem(seed=43)
+    Nt, Nd, Nm = F.shape
+    P = oracle.p2o_dense(F)
+    Gpi = np.kron(np.eye(Nt), A @ A)
+    d = rng.standard_normal((Nt, Nd))
+    m0 = rng.standard_normal((Nt, Nm))
+    H = P.T @ P / s2 + Gpi
+    closed = np.linalg.solve(H, P.T @ d.reshape(-1) / s2 + Gpi @ m0.reshape(-1))
+    got = oracle.map_point_with_prior_mean(F, G, s2, d, m0)
+    assert rel(got.reshape(-1), closed) < 1e-10
+    # zero prior mean reduces to map_point
+    assert rel(oracle.map_point_with_prior_mean(F, G, s2, d, np.zeros_like(m0)), oracle.map_point(F, G, s2, d)) < 1e-14
