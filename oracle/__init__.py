@@ -59,6 +59,8 @@ from .inversion import (
     prior_apply,
     posterior_cov_apply,
     map_point_with_prior_mean,
+    qoi_time_steps,
+    qoi_rows,
     loss,
     loss_gradient,
 )
@@ -71,5 +73,5 @@ __all__ = [
     "assemble_K", "assemble_K_columns", "cholesky_lower", "solve_K",
     "map_point", "map_point_woodbury_form", "qoi_map", "qoi_data_gram", "d2q_map",
     "qoi_posterior_covariance", "prior_apply", "posterior_cov_apply", "map_point_with_prior_mean",
-    "loss", "loss_gradient",
+    "qoi_time_steps", "qoi_rows", "loss", "loss_gradient",
 ]

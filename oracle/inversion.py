@@ -237,3 +237,25 @@ def map_point_with_prior_mean(F_blocks, G_blocks, noise, d_obs, m_prior, L=None)
     r = np.asarray(d_obs, dtype=np.float64) - p2o_apply(F_blocks, m_prior)
     x = solve_K(L, r.reshape(-1, Nt * R)).reshape(r.shape)
     return m_prior + p2o_apply_adjoint(G_blocks, x)
+
+
+def qoi_time_steps(Nt, stride):
+    """0-based fine time steps that carry the QoIs on a grid of N_t^q = N_t / stride points.
+
+    The Remark after Eq. (2.15) lets the QoI time grid be coarser than the time-stepping
+    grid, and the example of Sec. 5 takes parameters and data at 10 Hz on (0, 50) s
+    (N_t = 500) with QoIs at 1 Hz (N_t^q = 50).  QoI k is read at the end of its
+    interval, time (k + 1) * stride * dt, i.e. fine step stride (k + 1) - 1, so the
+    last QoI falls on the final time T.
+    """
+    if stride < 1 or Nt % stride:
+        raise ValueError(f"stride {stride} must divide N_t = {Nt}")
+    return np.arange(stride - 1, Nt, stride)
+
+
+def qoi_rows(Nt, Nq, stride):
+    """Indices of the coarse-grid QoI entries within a fine-grid QoI vector [N_t][N_q]
+    (flattened): the rows of Q, and the rows and columns of Gamma_post(q), that remain
+    on the QoI grid of qoi_time_steps."""
+    steps = qoi_time_steps(Nt, stride)
+    return (steps[:, None] * Nq + np.arange(Nq)[None, :]).reshape(-1)

@@ -446,3 +446,62 @@ def test_map_point_with_prior_mean_is_closed_form():
     assert rel(got.reshape(-1), closed) < 1e-10
     # zero prior mean reduces to map_point
     assert rel(oracle.map_point_with_prior_mean(F, G, s2, d, np.zeros_like(m0)), oracle.map_point(F, G, s2, d)) < 1e-14
+
+
+# ---------------------------------------------------------------- QoI time grid
+
+def test_qoi_time_steps_match_the_example_grid():
+    """Sec. 5: N_t = 500 steps at 10 Hz on (0, 50) s, QoIs at 1 Hz, N_t^q = 50, and the
+    QoI dimension N_q N_t^q = 800 (golden): one QoI per second, the last at T = 50 s."""
+    with open(os.path.join(HERE, "golden", "paper_storage.json")) as f:
+        g = json.load(f)
+    Nt, Ntq, Nq = g["Nt"], g["Ntq"], g["Nq"]
+    stride = Nt // Ntq
+    steps = oracle.qoi_time_steps(Nt, stride)
+    assert stride == 10 and len(steps) == Ntq
+    dt = 50.0 / Nt
+    times = (steps + 1) * dt  # step t ends at time (t + 1) dt
+    np.testing.assert_allclose(times, np.arange(1, 51), rtol=0, atol=1e-12)
+    assert len(oracle.qoi_rows(Nt, Nq, stride)) == g["qoi_dim"]
+    np.testing.assert_array_equal(oracle.qoi_time_steps(7, 1), np.arange(7))
+    with pytest.raises(ValueError):
+        oracle.qoi_time_steps(10, 3)
+
+
+def _coarse_p2q_dense(Fq, stride):
+    """The p2q matrix on the coarse QoI grid, block by block: block (k, s) is
+    (F_q)_{t_k - s} for s <= t_k with t_k = stride (k + 1) - 1, else zero."""
+    Nt, Rq, Nm = Fq.shape
+    Ntq = Nt // stride
+    P = np.zeros((Ntq * Rq, Nt * Nm))
+    for k in range(Ntq):
+        tk = stride * (k + 1) - 1
+        for s in range(tk + 1):
+            P[k * Rq:(k + 1) * Rq, s * Nm:(s + 1) * Nm] = Fq[tk - s]
+    return P
+
+
+def test_coarse_qoi_grid_selects_from_the_fine_d2q_map_and_covariance():
+    """Q and Gamma_post(q) on a QoI grid of every third step: the selected rows (and
+    columns) of the fine-grid results equal Eqs. (4.10)-(4.11) written with the coarse
+    p2q matrix assembled from its block definition."""
+    F, G, Cs, s2, rng = _tiny_problem(seed=17, gx=3, gy=3, Nd=2, Nt=6, sigma2=0.04)
+    Nt, Nd, Nm = F.shape
+    Fq = rng.standard_normal((Nt, 2, Nm)) * np.exp(-np.arange(Nt) / 4.0)[:, None, None]
+    Gq = oracle.prior_blocks(Fq, Cs)
+    stride = 3
+    rows = oracle.qoi_rows(Nt, 2, stride)
+    Q = oracle.d2q_map(Fq, F, G, s2)[rows]
+    C = oracle.qoi_posterior_covariance(Fq, Gq, F, G, s2)[np.ix_(rows, rows)]
+    P = oracle.p2o_dense(F)
+    Pc = _coarse_p2q_dense(Fq, stride)
+    Gp = np.kron(np.eye(Nt), Cs)
+    K = s2 * np.eye(Nt * Nd) + P @ Gp @ P.T
+    post = np.eye(Nt * Nm) - Gp @ P.T @ np.linalg.solve(K, P)
+    assert rel(Q, Pc @ post @ Gp @ P.T / s2) < 1e-10
+    assert rel(C, Pc @ post @ Gp @ Pc.T) < 1e-10
+    # the coarse q_map is the fine q_map read at the QoI steps
+    d = rng.standard_normal((Nt, Nd))
+    q_fine = oracle.qoi_map(Fq, oracle.map_point(F, G, s2, d))
+    steps = oracle.qoi_time_steps(Nt, stride)
+    assert rel((Q @ d.reshape(-1)).reshape(-1, 2), q_fine[steps]) < 1e-12
