@@ -202,6 +202,26 @@ bti_status bti_online(bti_handle h, const double* d_obs, double* m_map, double* 
 bti_status bti_apply_elliptic(bti_handle h, int gx, int gy, double alpha1, double alpha2, const double* m,
                               double* out, int64_t B, int squared);
 
+/* Precompute the data-to-QoI map Q of Eq. (4.11) (zero prior mean), and with
+ * with_covariance != 0 also the QoI posterior covariance Gamma_post(q) of Eq. (4.10)
+ * (Sec. 4, Phase 3).  Since F G^* = K - Gamma_noise, Eq. (4.11) reduces to
+ * Q = F_q G^* K^{-1}: the block-Toeplitz product F_q G^* is a Gram product of the
+ * stacked time-domain blocks with block-diagonal prefix sums, and its rows are solved
+ * with the Cholesky factor.  Gamma_post(q) = F_q Gamma_prior F_q^T - Q (F_q G^*)^T,
+ * with the stored SE prior applied to F_q.  Q is (N_q N_t) x (N_d N_t), the
+ * covariance (N_q N_t)^2, both FP64 and owned by the handle (arithmetic per
+ * bti_set_dense_precision).  Requires factor_K, F_q and G; synchronises when the
+ * covariance is built. */
+bti_status bti_build_Q(bti_handle h, int with_covariance);
+
+/* q_map = Q d_obs (Eq. (4.14) with zero prior mean) for B observation vectors:
+ * d_obs [B][N_t][N_d] -> q_map [B][N_t][N_q], device doubles.  Requires build_Q. */
+bti_status bti_apply_Q(bti_handle h, const double* d_obs, double* q_map, int64_t B);
+
+/* Copy Q (row-major [N_q N_t][N_d N_t]) and/or Gamma_post(q) ([N_q N_t]^2) to device
+ * buffers; either pointer may be NULL. */
+bti_status bti_copy_Q(bti_handle h, double* Q_out, double* cov_out);
+
 /* q_map = F_q m_map (Eq. (4.2)): m_map [B][N_t][N_m] -> q_map [B][N_t][N_q],
  * both double.  Requires FQ. */
 bti_status bti_predict_qoi(bti_handle h, const double* m_map, double* q_map, int64_t B);

@@ -71,6 +71,9 @@ def lib():
         "bti_infer_map": ([vp, vp, vp, i64, ip], st),
         "bti_predict_qoi": ([vp, vp, vp, i64], st),
         "bti_online": ([vp, vp, vp, vp, i64, ip], st),
+        "bti_build_Q": ([vp, ip], st),
+        "bti_apply_Q": ([vp, vp, vp, i64], st),
+        "bti_copy_Q": ([vp, vp, vp], st),
         "bti_apply_elliptic": ([vp, ip, ip, dp, dp, vp, vp, i64, ip], st),
         "bti_autotune": ([vp, ip, i64, ctypes.c_char_p, i64], st),
         "bti_sync": ([vp], st),
@@ -247,6 +250,30 @@ class Handle:
             raise ValueError("d_obs and m_map batch sizes differ")
         self._check(lib().bti_infer_map(self._h, _ptr(d_obs), _ptr(m_map), B, int(refine_iters)))
         return m_map
+
+    def build_Q(self, with_covariance=False):
+        """Precompute the d2q map Q (Eq. (4.11)) and optionally Gamma_post(q) (Eq. (4.10))."""
+        self._check(lib().bti_build_Q(self._h, 1 if with_covariance else 0))
+
+    def apply_Q(self, d_obs, q_map):
+        """q_map = Q d_obs (Eq. (4.14))."""
+        self._tensor(d_obs, (self.Nt, self.Nd), "d_obs")
+        self._tensor(q_map, (self.Nt, self.Nq), "q_map")
+        B = self._batch(d_obs, 2)
+        if self._batch(q_map, 2) != B:
+            raise ValueError("d_obs and q_map batch sizes differ")
+        self._check(lib().bti_apply_Q(self._h, _ptr(d_obs), _ptr(q_map), B))
+        return q_map
+
+    def copy_Q(self, covariance=False):
+        """(Q, Gamma_post(q) or None) as new device tensors."""
+        import torch
+
+        nq, n = self.Nt * self.Nq, self.Nt * self.Nd
+        Q = torch.empty((nq, n), dtype=torch.float64, device=self.device)
+        C = torch.empty((nq, nq), dtype=torch.float64, device=self.device) if covariance else None
+        self._check(lib().bti_copy_Q(self._h, _ptr(Q), _ptr(C)))
+        return Q, C
 
     def predict_qoi(self, m_map, q_map):
         self._tensor(m_map, (self.Nt, self.Nm), "m_map")

@@ -9,6 +9,7 @@
 #include <new>
 #include <string>
 #include <utility>
+#include <algorithm>
 #include <vector>
 
 using namespace bti;
@@ -46,6 +47,12 @@ struct bti_ctx {
   bool noise_set = false;
   double sigma2 = 0.0;
   double* noise_diag = nullptr;  // [Nt][Nd] or null
+  bool prior_set = false;        // SE prior of bti_set_prior_se_grid (also applied to F_q)
+  int prior_gx = 0, prior_gy = 0;
+  double prior_ell = 0.0, prior_sigma = 0.0;
+  double* Q = nullptr;           // [N_q N_t][N_d N_t] d2q map
+  double* covq = nullptr;        // [N_q N_t][N_q N_t] posterior covariance of the QoI
+  bool Q_built = false, covq_built = false;
   double* K = nullptr;           // [n][n], lower triangle: K, then L after factor_K
   double* Linv = nullptr;        // inverses of the factor's diagonal blocks
   bool K_built = false, K_factored = false;
@@ -445,6 +452,8 @@ bti_status bti_destroy(bti_handle h) {
   }
   dev_freep(h->noise_diag);
   dev_freep(h->K);
+  dev_freep(h->Q);
+  dev_freep(h->covq);
   dev_freep(h->Linv);
   dev_freep(h->status);
   dev_free(h->ws);
@@ -507,7 +516,7 @@ bti_status bti_set_blocks(bti_handle h, bti_op op, const double* blocks, bti_pre
   if (op < BTI_OP_F || op > BTI_OP_FQ) return fail(h, BTI_ERR_ARG, "set_blocks: bad op");
   if (!prec_ok(store)) return fail(h, BTI_ERR_ARG, "set_blocks: bad precision");
   if (!blocks) return fail(h, BTI_ERR_ARG, "set_blocks: null blocks");
-  return store_op(h, op, blocks, store, op != BTI_OP_FQ);
+  return store_op(h, op, blocks, store, true);
 }
 
 bti_status bti_set_prior_se_grid(bti_handle h, int gx, int gy, double ell, double sigma, bti_prec store) {
@@ -531,6 +540,11 @@ bti_status bti_set_prior_se_grid(bti_handle h, int gx, int gy, double ell, doubl
   st = dev_alloc(h, (void**)&G, sizeof(double) * (size_t)rows * h->Nm, "alloc G blocks");
   if (st != BTI_OK) { dev_freep(Cx); dev_freep(U); return st; }
   cudaStream_t s = h->stream;
+  h->prior_set = true;
+  h->prior_gx = gx;
+  h->prior_gy = gy;
+  h->prior_ell = ell;
+  h->prior_sigma = sigma;
   // C_s = C_x (x) C_y with sigma on each axis, node index ix * gy + iy
   int64_t nl = se_axis_matrix(Cx, gx, ell, sigma, s);
   nl += se_axis_matrix(Cy, gy, ell, sigma, s);
@@ -664,6 +678,7 @@ static bti_status build_K_impl(bti_handle h, int64_t col_block, bti_prec assembl
   if (st != BTI_OK) return st;
   h->K_built = true;
   h->K_factored = false;
+  h->Q_built = h->covq_built = false;
   return BTI_OK;
 }
 
@@ -756,6 +771,119 @@ static bti_status infer_map_impl(bti_handle h, const double* d_obs, double* m_ma
 
 bti_status bti_infer_map(bti_handle h, const double* d_obs, double* m_map, int64_t B, int refine_iters) {
   return infer_map_impl(h, d_obs, m_map, B, refine_iters);
+}
+
+// G_q = F_q C_s for the stored SE prior, from F_q's time-domain blocks (device buffer out).
+static bti_status prior_apply_fq(bti_ctx* h, double* out) {
+  const OpStore& Fq = h->op[BTI_OP_FQ];
+  const int gx = h->prior_gx, gy = h->prior_gy;
+  const int64_t rows = h->Nt * h->Nq;
+  double* Cx = nullptr;
+  double* U = nullptr;
+  bti_status st = dev_alloc(h, (void**)&Cx, sizeof(double) * ((size_t)gx * gx + (size_t)gy * gy), "prior axes");
+  if (st != BTI_OK) return st;
+  double* Cy = Cx + (size_t)gx * gx;
+  st = dev_alloc(h, (void**)&U, sizeof(double) * (size_t)rows * h->Nm, "prior temp");
+  if (st != BTI_OK) { dev_freep(Cx); return st; }
+  cudaStream_t s = h->stream;
+  int64_t nl = se_axis_matrix(Cx, gx, h->prior_ell, h->prior_sigma, s);
+  nl += se_axis_matrix(Cy, gy, h->prior_ell, h->prior_sigma, s);
+  nl += gemm_f64(false, rows * gx, gy, gy, 1.0, Fq.time, gy, 0, Cy, gy, 0, 0.0, U, gy, 0, 1, false, s);
+  nl += gemm_f64(false, gx, gy, gx, 1.0, Cx, gx, 0, U, gy, (int64_t)gx * gy, 0.0, out, gy, (int64_t)gx * gy, rows,
+                 false, s);
+  count_dense(h, nl);
+  st = launched(h, "prior on F_q");
+  cudaStreamSynchronize(s);
+  dev_freep(Cx);
+  dev_freep(U);
+  return st;
+}
+
+bti_status bti_build_Q(bti_handle h, int with_covariance) {
+  bti_status st = check_handle(h);
+  if (st != BTI_OK) return st;
+  const OpStore& Fq = h->op[BTI_OP_FQ];
+  const OpStore& G = h->op[BTI_OP_G];
+  if (!h->K_factored) return fail(h, BTI_ERR_STATE, "build_Q: K not factored");
+  if (!Fq.set || !Fq.time) return fail(h, BTI_ERR_STATE, "build_Q: F_q blocks not set");
+  if (!G.set || !G.time) return fail(h, BTI_ERR_STATE, "build_Q: G blocks not set");
+  if (with_covariance && !h->prior_set)
+    return fail(h, BTI_ERR_STATE, "build_Q: the covariance needs the SE prior (bti_set_prior_se_grid)");
+  const int64_t n = h->Nt * h->Nd, nq = h->Nt * h->Nq, Nm = h->Nm;
+  const bool dd = h->dense_prec == BTI_P_DF64;
+  auto gemm = dd ? gemm_df64 : gemm_f64;
+  cudaStream_t s = h->stream;
+  if (!h->Q) {
+    st = dev_alloc(h, (void**)&h->Q, sizeof(double) * (size_t)nq * n, "alloc Q");
+    if (st != BTI_OK) return st;
+  }
+  h->Q_built = h->covq_built = false;
+  // X = F_q G^*: Gram of the stacked blocks, then block-diagonal prefix sums
+  int64_t nl = gemm(true, nq, n, Nm, 1.0, Fq.time, Nm, 0, G.time, Nm, 0, 0.0, h->Q, n, 0, 1, false, s);
+  nl += block_diag_cumsum_all(h->Q, h->Nt, h->Nq, h->Nd, s);
+  double* X = nullptr;
+  if (with_covariance) {
+    st = dev_alloc(h, (void**)&X, sizeof(double) * (size_t)nq * n, "F_q G* copy");
+    if (st != BTI_OK) return st;
+    cudaMemcpyAsync(X, h->Q, sizeof(double) * (size_t)nq * n, cudaMemcpyDeviceToDevice, s);
+  }
+  // Q = X K^{-1}: every row of X is a right-hand side of the two triangular solves
+  st = ensure(h, (void**)&h->wsolve, &h->wsolve_bytes,
+              sizeof(double) * std::max(trsm_work_elems(n, nq), (size_t)n * kCholNB), "solve workspace");
+  if (st != BTI_OK) { dev_freep(X); return st; }
+  nl += trsm_lower_f64(h->K, h->Linv, n, h->Q, nq, h->wsolve, h->status, s, dd);
+  if (with_covariance) {
+    double* Gq = nullptr;
+    st = dev_alloc(h, (void**)&Gq, sizeof(double) * (size_t)nq * Nm, "G_q blocks");
+    if (st == BTI_OK) st = prior_apply_fq(h, Gq);
+    if (st == BTI_OK && !h->covq) st = dev_alloc(h, (void**)&h->covq, sizeof(double) * (size_t)nq * nq, "alloc cov");
+    if (st != BTI_OK) { dev_freep(X); dev_freep(Gq); return st; }
+    // Gamma_post(q) = F_q Gamma_prior F_q^T - Q X^T  (Eq. (4.10) with F G_q^* = X^T)
+    nl += gemm(true, nq, nq, Nm, 1.0, Fq.time, Nm, 0, Gq, Nm, 0, 0.0, h->covq, nq, 0, 1, false, s);
+    nl += block_diag_cumsum_all(h->covq, h->Nt, h->Nq, h->Nq, s);
+    nl += gemm(true, nq, nq, n, -1.0, h->Q, n, 0, X, n, 0, 1.0, h->covq, nq, 0, 1, false, s);
+    cudaStreamSynchronize(s);
+    dev_freep(Gq);
+    dev_freep(X);
+  }
+  count_dense(h, nl);
+  st = launched(h, "build_Q");
+  if (st != BTI_OK) return st;
+  h->Q_built = true;
+  h->covq_built = with_covariance != 0;
+  return BTI_OK;
+}
+
+bti_status bti_apply_Q(bti_handle h, const double* d_obs, double* q_map, int64_t B) {
+  bti_status st = check_handle(h);
+  if (st != BTI_OK) return st;
+  if (B < 0) return fail(h, BTI_ERR_ARG, "apply_Q: B < 0");
+  if (!h->Q_built) return fail(h, BTI_ERR_STATE, "apply_Q: Q not built");
+  if (B == 0) return BTI_OK;
+  if (!d_obs || !q_map) return fail(h, BTI_ERR_ARG, "apply_Q: null pointer");
+  const int64_t n = h->Nt * h->Nd, nq = h->Nt * h->Nq;
+  // q[b] = Q d[b]: rows of d against rows of Q
+  const bool dd = h->dense_prec == BTI_P_DF64 && B > 8;
+  count_dense(h, (dd ? gemm_df64 : gemm_f64)(true, B, nq, n, 1.0, d_obs, n, 0, h->Q, n, 0, 0.0, q_map, nq, 0, 1,
+                                             false, h->stream));
+  return launched(h, "apply_Q");
+}
+
+bti_status bti_copy_Q(bti_handle h, double* Q_out, double* cov_out) {
+  bti_status st = check_handle(h);
+  if (st != BTI_OK) return st;
+  if (!h->Q_built) return fail(h, BTI_ERR_STATE, "copy_Q: Q not built");
+  if (cov_out && !h->covq_built) return fail(h, BTI_ERR_STATE, "copy_Q: covariance not built");
+  const size_t nq = (size_t)h->Nt * h->Nq, n = (size_t)h->Nt * h->Nd;
+  if (Q_out) {
+    st = cuda_check(h, cudaMemcpyAsync(Q_out, h->Q, sizeof(double) * nq * n, cudaMemcpyDeviceToDevice, h->stream),
+                    "copy Q");
+    if (st != BTI_OK) return st;
+  }
+  if (cov_out)
+    st = cuda_check(h, cudaMemcpyAsync(cov_out, h->covq, sizeof(double) * nq * nq, cudaMemcpyDeviceToDevice,
+                                       h->stream), "copy covariance");
+  return st;
 }
 
 bti_status bti_apply_elliptic(bti_handle h, int gx, int gy, double alpha1, double alpha2, const double* m,

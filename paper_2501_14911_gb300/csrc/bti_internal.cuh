@@ -68,6 +68,34 @@ struct __align__(16) ffc {
   ffloat x, y;
 };
 
+// One real part of a float-pair complex product: x1*y1 - x2*y2 (sub) or x1*y1 + x2*y2,
+// with both high products exact (FMA errors), their sum by two-sum, the cross terms
+// and errors gathered in the low float, then one renormalisation (19 FP32 operations).
+__device__ __forceinline__ ffloat ff_dot2(ffloat x1, ffloat y1, ffloat x2, ffloat y2, bool sub) {
+  const float sg = sub ? -1.f : 1.f;
+  float p1 = __fmul_rn(x1.h, y1.h);
+  float p2 = __fmul_rn(sg * x2.h, y2.h);
+  float lo = __fmaf_rn(x1.h, y1.h, -p1);
+  lo = __fadd_rn(lo, __fmaf_rn(sg * x2.h, y2.h, -p2));
+  float s = __fadd_rn(p1, p2);
+  float bb = __fsub_rn(s, p1);
+  float e = __fadd_rn(__fsub_rn(p1, __fsub_rn(s, bb)), __fsub_rn(p2, bb));
+  lo = __fadd_rn(lo, e);
+  lo = __fmaf_rn(x1.h, y1.l, lo);
+  lo = __fmaf_rn(x1.l, y1.h, lo);
+  lo = __fmaf_rn(sg * x2.h, y2.l, lo);
+  lo = __fmaf_rn(sg * x2.l, y2.h, lo);
+  float hh = __fadd_rn(s, lo);
+  return ffloat(hh, __fsub_rn(lo, __fsub_rn(hh, s)));
+}
+
+template <> __device__ __forceinline__ ffc cmul<ffloat>(ffc a, ffc b) {
+  ffc z;
+  z.x = ff_dot2(a.x, b.x, a.y, b.y, true);
+  z.y = ff_dot2(a.x, b.y, a.y, b.x, false);
+  return z;
+}
+
 // ----------------------------------------------------------------- FFT plan
 constexpr int kMaxPasses = 12;
 constexpr int kMaxL = 2048;  // longest transform (N_t <= 1024); also the per-CTA FFT size
@@ -159,6 +187,8 @@ int convert_f64_to_f32(const double* x, float* y, int64_t n, cudaStream_t s);
 // out = (alpha1 I - alpha2 Delta_h) m for nblocks grids of gx x gy (5-point, Neumann)
 int elliptic_apply(const double* m, double* out, int gx, int gy, double a1, double a2, int64_t nblocks,
                    cudaStream_t s);
+// Block-diagonal prefix sums on both sides of the diagonal (block-Toeplitz product A B^*).
+int block_diag_cumsum_all(double* X, int64_t Nt, int64_t R1, int64_t R2, cudaStream_t s);
 int noise_residual_f64(double* r, const double* x, const double* diag, int64_t n, int64_t B,
                        cudaStream_t s);
 

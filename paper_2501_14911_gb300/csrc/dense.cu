@@ -698,3 +698,38 @@ int elliptic_apply(const double* m, double* out, int gx, int gy, double a1, doub
 }
 
 }  // namespace bti
+
+namespace bti {
+
+// ------------------------------------------------------------------ two-sided block-diagonal accumulation
+// X (Nt R1 x Nt R2, ld = Nt R2) holds W(k, k') = A_k B_{k'}^T block by block on entry;
+// on exit block (t, t') = sum_{u=0}^{min(t,t')} W(t-u, t'-u), i.e. prefix sums along every
+// block diagonal delta = t - t' (negative and positive): the block-Toeplitz product
+// A B^* of two causal maps (e.g. F_q G^*).  One thread per (delta, i, i').
+__global__ void block_diag_cumsum_all_kernel(double* X, int64_t Nt, int64_t R1, int64_t R2) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t RR = R1 * R2;
+  if (idx >= (2 * Nt - 1) * RR) return;
+  const int64_t dd = idx / RR;
+  const int64_t rem = idx - dd * RR;
+  const int64_t i = rem / R2, ip = rem - i * R2;
+  const int64_t delta = dd - (Nt - 1);
+  const int64_t t0 = delta > 0 ? delta : 0, tp0 = delta < 0 ? -delta : 0;
+  const int64_t len = Nt - (delta > 0 ? delta : -delta);
+  const int64_t ld = Nt * R2;
+  double acc = 0.0;
+  for (int64_t u = 0; u < len; ++u) {
+    double* p = X + ((t0 + u) * R1 + i) * ld + (tp0 + u) * R2 + ip;
+    acc += *p;
+    *p = acc;
+  }
+}
+
+int block_diag_cumsum_all(double* X, int64_t Nt, int64_t R1, int64_t R2, cudaStream_t s) {
+  int64_t total = (2 * Nt - 1) * R1 * R2;
+  if (total <= 0) return 0;
+  block_diag_cumsum_all_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(X, Nt, R1, R2);
+  return 1;
+}
+
+}  // namespace bti

@@ -200,14 +200,53 @@ __device__ __forceinline__ void butterfly(const C2<T>* s, int Lr, C2<T>* d, int 
   for (int m = 0; m < R; ++m) d[m * Ns] = a[m];
 }
 
-// All passes; data starts in buf0, result pointer returned (buf0 or buf1).
+// First radix-8 pass of a forward transform whose second half is zero padding
+// (L = 2 N_t, so inputs q = 4..7 of every first-pass butterfly vanish; the pass has
+// no twiddles since Ns = 1): the two radix-4 halves reduce to two additions each.
+template <typename T>
+__device__ __forceinline__ void butterfly8_half_zero(const C2<T>* s, int Lr, C2<T>* d) {
+  const C2<T> a0 = s[0], a1 = s[Lr], a2 = s[2 * Lr], a3 = s[3 * Lr];
+  // even half: DFT4(a0, a2, 0, 0); odd half: DFT4(a1, a3, 0, 0)
+  const C2<T> r2 = rot90<T, false>(a2), r3 = rot90<T, false>(a3);
+  C2<T> e0 = cadd<T>(a0, a2), e2 = csub<T>(a0, a2), e1 = cadd<T>(a0, r2), e3 = csub<T>(a0, r2);
+  C2<T> o0 = cadd<T>(a1, a3), o2 = csub<T>(a1, a3), o1 = cadd<T>(a1, r3), o3 = csub<T>(a1, r3);
+  const T h = (T)0.70710678118654752440084436210485;  // sqrt(1/2)
+  o1 = cmul<T>(o1, mk<T>(h, -h));
+  o2 = rot90<T, false>(o2);
+  o3 = cmul<T>(o3, mk<T>(-h, -h));
+  d[0] = cadd<T>(e0, o0);
+  d[4] = csub<T>(e0, o0);
+  d[1] = cadd<T>(e1, o1);
+  d[5] = csub<T>(e1, o1);
+  d[2] = cadd<T>(e2, o2);
+  d[6] = csub<T>(e2, o2);
+  d[3] = cadd<T>(e3, o3);
+  d[7] = csub<T>(e3, o3);
+}
+
+// All passes; data starts in buf0, result pointer returned (buf0 or buf1).  With
+// half_zero, the first pass is radix 8 and only the first half of each input is nonzero.
 template <typename T, bool INV>
-__device__ C2<T>* run_passes(const FftDesc& D, C2<T>* buf0, C2<T>* buf1, const C2<T>* __restrict__ tw) {
+__device__ C2<T>* run_passes(const FftDesc& D, C2<T>* buf0, C2<T>* buf1, const C2<T>* __restrict__ tw,
+                             bool half_zero = false) {
   C2<T>* src = buf0;
   C2<T>* dst = buf1;
   const int L = D.L;
   int Ns = 1;
-  for (int ps = 0; ps < D.npass; ++ps) {
+  if (!INV && half_zero && D.npass > 0 && D.radix[0] == 8) {
+    const int Lr = L / 8;
+    const int nbf = D.P * Lr;
+    for (int bi = threadIdx.x; bi < nbf; bi += blockDim.x) {
+      int p = bi / Lr, j = bi - p * Lr;
+      butterfly8_half_zero<T>(src + p * L + j, Lr, dst + p * L + j * 8);
+    }
+    __syncthreads();
+    C2<T>* tmp = src;
+    src = dst;
+    dst = tmp;
+    Ns = 8;
+  }
+  for (int ps = (Ns == 8 ? 1 : 0); ps < D.npass; ++ps) {
     const int r = D.radix[ps];
     const int Lr = L / r;
     const int nbf = D.P * Lr;
@@ -242,7 +281,7 @@ template <typename TO, typename T> __device__ __forceinline__ C2<TO> cvt2(C2<T> 
 template <typename T> __device__ __forceinline__ C2<T> czero() { return mk<T>((T)0, (T)0); }
 
 template <typename T, typename TI, typename TO>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
 rfft_cols_kernel(FftDesc D, int Nt, const TI* __restrict__ x, int64_t ld, int64_t xbs,
                  C2<TO>* __restrict__ X, int64_t Xbs, int64_t ncols, TwTabs tabs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -266,7 +305,7 @@ rfft_cols_kernel(FftDesc D, int Nt, const TI* __restrict__ x, int64_t ld, int64_
     buf0[p * L + t] = czero<T>();
   }
   __syncthreads();
-  C2<T>* Z = run_passes<T, false>(D, buf0, buf1, tw);
+  C2<T>* Z = run_passes<T, false>(D, buf0, buf1, tw, 2 * Nt == L);
   // unpack the two real spectra of each pair and store bins 0..N_t
   const int nf = Nt + 1;
   for (int idx = threadIdx.x; idx < nf * W2; idx += blockDim.x) {
@@ -288,7 +327,7 @@ rfft_cols_kernel(FftDesc D, int Nt, const TI* __restrict__ x, int64_t ld, int64_
 }
 
 template <typename T, typename TYI, typename TO>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
 irfft_cols_kernel(FftDesc D, int Nt, const C2<TYI>* __restrict__ Y, int64_t ld, int64_t Ybs,
                   TO* __restrict__ y, int64_t ybs, int64_t ncols, double scale_d, TwTabs tabs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -9,6 +9,8 @@
   the data misfit against the oracle gradient.
 - The batched workload again as a mixed-precision solve (K assembled in FP32,
   refinement with double-FP32 operators).
+- The mixed-precision workload's products (N_d = 600, N_t = 420, L = 840) in the
+  FP16, FP32 and double-FP32 tiers.
 
 Minutes of host time for the oracle; GPU only.
 """
@@ -51,7 +53,9 @@ def test_sweep_sampled_outputs(sweep, store, tol):
     h = bti.Handle(p.Nm, p.Nd, 0, p.Nt)
     Fd = torch.from_numpy(F).cuda()
     h.set_blocks(bti.OP_F, Fd, store)
+    torch.cuda.synchronize()
     del Fd
+    torch.cuda.empty_cache()
     m_g = torch.from_numpy(m).cuda().to(dt)
     d_g = torch.from_numpy(d).cuda().to(dt)
     outd = torch.empty((2, p.Nt, p.Nd), dtype=dt, device="cuda")
@@ -92,6 +96,11 @@ def test_batched_inversion_full_size():
     h.predict_qoi(m_map, q_map)
     m_gpu = m_map.cpu().numpy()
     q_gpu = q_map.cpu().numpy()
+    # the d2q map (Eq. (4.11)) and q_map = Q d_obs (Eq. (4.14)) at full size
+    h.build_Q()
+    q_d2q = torch.empty_like(q_map)
+    h.apply_Q(torch.from_numpy(d_obs).cuda(), q_d2q)
+    q_d2q = q_d2q.cpu().numpy()
     h.close()
 
     Cs = oracle.se_covariance(p.gx, p.gy, p.ell, p.sigma_p)
@@ -116,7 +125,9 @@ def test_batched_inversion_full_size():
     del L_gpu, low
     m_or = oracle.map_point(F, G, p.sigma2, d_obs, L=L_or)
     assert relb(m_gpu, m_or) < 1e-11
-    assert relb(q_gpu, oracle.qoi_map(Fq, m_or)) < 1e-11
+    q_or = oracle.qoi_map(Fq, m_or)
+    assert relb(q_gpu, q_or) < 1e-11
+    assert relb(q_d2q, q_or) < 1e-11
 
 
 def test_diff_gradient_full_size():
@@ -175,3 +186,41 @@ def test_batched_mixed_precision_solve_full_size(dense):
     m_or = oracle.map_point(F, G, p.sigma2, d_obs)
     assert relb(m_gpu, m_or) < 1e-11
     assert relb(q_gpu, oracle.qoi_map(Fq, m_or)) < 1e-11
+
+
+@pytest.fixture(scope="module")
+def mixed():
+    p = synthetic.MIXED
+    return p, p.blocks_F(), p.vectors_m(1), p.vectors_d(1)
+
+
+@pytest.mark.parametrize("store,tol", [(bti.F16, 1e-3), (bti.F32, 1e-5), (bti.DF64, 1e-12)],
+                         ids=["f16", "f32", "df64"])
+def test_mixed_workload_products_full_size(mixed, store, tol):
+    """The mixed-precision workload's operators (N_m = 16,384, N_d = 600, N_t = 420, so
+    L = 840 = 8 * 7 * 5 * 3): F and F^T on one vector per call against the oracle's
+    complete products, normwise over the whole vector (the tolerance metric).  The FP16
+    tier is that workload's low-precision product tier, the double-FP32 tier its FP64
+    refinement operator."""
+    p, F, m, d = mixed
+    dt = torch.float32 if store in (bti.F32, bti.F16) else torch.float64
+    h = bti.Handle(p.Nm, p.Nd, 0, p.Nt)
+    Fd = torch.from_numpy(F).cuda()
+    h.set_blocks(bti.OP_F, Fd, store)
+    torch.cuda.synchronize()
+    del Fd
+    torch.cuda.empty_cache()
+    m_g = torch.from_numpy(m).cuda().to(dt)
+    d_g = torch.from_numpy(d).cuda().to(dt)
+    od = torch.empty((1, p.Nt, p.Nd), dtype=dt, device="cuda")
+    om = torch.empty((1, p.Nt, p.Nm), dtype=dt, device="cuda")
+    h.apply_F(m_g, od)
+    h.apply_FT(d_g, om)
+    torch.cuda.synchronize()
+    m_in = m_g.double().cpu().numpy()
+    d_in = d_g.double().cpu().numpy()
+    od = od.double().cpu().numpy()
+    om = om.double().cpu().numpy()
+    h.close()
+    assert relb(od, oracle.p2o_apply(F, m_in)) < tol
+    assert relb(om, oracle.p2o_apply_adjoint(F, d_in)) < tol

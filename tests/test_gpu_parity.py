@@ -449,3 +449,31 @@ def test_non_finite_input_is_reported_not_spd():
         h.factor_K()
     assert e.value.status == 6 and "pivot 7" in e.value.message
     h.close()
+
+
+@pytest.mark.parametrize("dense", ["f64", "df64"])
+def test_d2q_map_and_qoi_covariance(dense):
+    """Q (Eq. (4.11)) and Gamma_post(q) (Eq. (4.10)) against the oracle; q_map = Q d_obs
+    (Eq. (4.14)) equals the push-forward F_q m_map."""
+    p, F, Fq, G, d_obs = tiny_problem()
+    h = make_handle(F, Fq, bti.DF64)
+    h.set_prior_se_grid(p.gx, p.gy, p.ell, p.sigma_p, bti.DF64)
+    h.set_noise(p.sigma2)
+    if dense == "df64":
+        h.set_dense_precision(bti.DF64)
+    h.build_K()
+    h.factor_K()
+    h.build_Q(with_covariance=True)
+    Q, C = h.copy_Q(covariance=True)
+    Cs = oracle.se_covariance(p.gx, p.gy, p.ell, p.sigma_p)
+    Q_or = oracle.d2q_map(Fq, F, G, p.sigma2)
+    C_or = oracle.qoi_posterior_covariance(Fq, oracle.prior_blocks(Fq, Cs), F, G, p.sigma2)
+    tol = 1e-12 if dense == "f64" else 1e-11
+    assert np.linalg.norm(host(Q) - Q_or) / np.linalg.norm(Q_or) < tol
+    assert np.linalg.norm(host(C) - C_or) / np.linalg.norm(C_or) < 1e-10
+    d = cuda(np.concatenate([d_obs, p.vectors_d(2)]))
+    q = torch.empty((3, p.Nt, p.Nq), dtype=torch.float64, device="cuda")
+    h.apply_Q(d, q)
+    q_or = oracle.qoi_map(Fq, oracle.map_point(F, G, p.sigma2, host(d)))
+    assert relb(host(q), q_or) < tol
+    h.close()
