@@ -399,7 +399,14 @@ def run_ours(args):
         if headline:
             clk = clocks.stop()
         bytes_step = 2 * V * bytes_per_call(p, esize, csize)
-        res[name] = {"ms": ms, "prof": prof, "bytes_step": bytes_step, "autotune": tune,
+        # the same 16 vector pairs as one call each way (B = 16): the product kernels
+        # take 4 right-hand sides per CTA, so the spectral blocks stream 4 times per call
+        ms_b, _ = timed(lambda: (h.apply_F(vecs[0], vecs[2]), h.apply_FT(vecs[1], vecs[3])), args.steps, 1)
+        batched = {"ms_per_step": ms_b / args.steps, "vector_pairs_per_s": world * V * args.steps / (ms_b * 1e-3),
+                   "speedup_vs_single_vector_calls": ms / ms_b,
+                   "spectral_stream_gbs": world * 2 * ((V + 3) // 4) * (p.Nt + 1) * p.Nd * p.Nm * csize
+                   * args.steps / (ms_b * 1e-3) / 1e9}
+        res[name] = {"ms": ms, "prof": prof, "bytes_step": bytes_step, "autotune": tune, "batched16": batched,
                      "value": aggregate_gbs(world, bytes_step, args.steps, ms),
                      "roofline": roofline(prof, csize, name)}
         if headline and not args.no_e2e:
@@ -428,6 +435,7 @@ def run_ours(args):
         "tiers": {k: {"value": v["value"], "unit": "GB/s", "ms_per_step": v["ms"] / args.steps,
                       "hbm_frac": v["value"] / world / hbm_peak, "roofline": v["roofline"]}
                   for k, v in res.items() if k != "df64"},
+        "batched16": {k: v["batched16"] for k, v in res.items()},
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk,
@@ -559,6 +567,26 @@ def online_block(args, dev, stream):
                      "factor_tflops_fp64_equiv": (n ** 3 / 3.0) / (t_factor * 1e-3) / 1e12,
                      "m_map_plus_q_map_graph_ms": lat, "ms_per_obs_vector": lat / B,
                      "offline_plus_online_ms": t_build + t_factor + lat}
+        if name == "plain_f64":
+            # q_map straight from the data through the precomputed d2q map (Eq. (4.14))
+            with torch.cuda.stream(gs):
+                e[0].record(gs)
+                h.build_Q(with_covariance=True)
+                e[1].record(gs)
+                torch.cuda.synchronize()
+                t_q = e[0].elapsed_time(e[1])
+                for nb in (1, B):
+                    for _ in range(2):
+                        h.apply_Q(d_obs[:nb], q_map[:nb])
+                    torch.cuda.synchronize()
+                    e[0].record(gs)
+                    for _ in range(reps):
+                        h.apply_Q(d_obs[:nb], q_map[:nb])
+                    e[1].record(gs)
+                    torch.cuda.synchronize()
+                    out[name][f"q_map_via_Q_ms_B{nb}"] = e[0].elapsed_time(e[1]) / reps
+            out[name]["build_Q_and_covariance_ms"] = t_q
+            out[name]["Q_shape"] = [p.Nt * p.Nq, p.Nt * p.Nd]
     h.set_stream(stream)
     h.close()
     out["accuracy"] = ("every form reaches FP64-level m_map and q_map: tests/test_gpu_parity.py (tiny, 1e-12) "

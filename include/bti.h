@@ -134,7 +134,8 @@ bti_status bti_apply_F(bti_handle h, const void* m, void* d, int64_t B, bti_prec
  * spectral blocks (Sec. 4): d [B][N_t][N_d] -> m [B][N_t][N_m]. */
 bti_status bti_apply_FT(bti_handle h, const void* d, void* m, int64_t B, bti_prec io);
 
-/* q = F_q m (Eq. (2.15)): m [B][N_t][N_m] -> q [B][N_t][N_q]. */
+/* q = F_q m (Eq. (2.15)): m [B][N_t][N_m] -> q [B][N_t^q][N_q] (N_t^q = N_t unless
+ * bti_set_qoi_stride). */
 bti_status bti_apply_Fq(bti_handle h, const void* m, void* q, int64_t B, bti_prec io);
 
 /* m = G^* d = Gamma_prior F^T d using the G spectral blocks:
@@ -190,6 +191,34 @@ bti_status bti_infer_map(bti_handle h, const double* d_obs, double* m_map, int64
  * counted or timed by bti_profile_read. */
 bti_status bti_online(bti_handle h, const double* d_obs, double* m_map, double* q_map, int64_t B,
                       int refine_iters);
+
+/* QoI time grid (Sec. 2, the Remark on separate time discretisations): keep every
+ * stride-th step of the QoI, q_k at fine step stride (k + 1) - 1, k < N_t^q = N_t /
+ * stride (stride must divide N_t; 1 restores the full grid).  Affects the QoI vectors
+ * of bti_apply_Fq, bti_predict_qoi, bti_online and bti_apply_Q, which become
+ * [B][N_t^q][N_q], and the rows of Q and Gamma_post(q) (bti_build_Q, rebuild after
+ * a change), which then hold N_q N_t^q rows. */
+bti_status bti_set_qoi_stride(bti_handle h, int stride);
+
+/* out = Gamma_prior v with the SE prior of bti_set_prior_se_grid applied to each
+ * time block (Gamma_prior = I_t (x) C_s): v, out [B][N_t][N_m] device doubles, not
+ * aliased.  Synchronises. */
+bti_status bti_apply_prior(bti_handle h, const double* v, double* out, int64_t B);
+
+/* Action of the parameter posterior covariance, Eq. (4.7):
+ * out = Gamma_post(m) v = (I - G^* K^{-1} F) Gamma_prior v, for B vectors
+ * [B][N_t][N_m] (device doubles, not aliased).  Columns of Gamma_post(m) and its
+ * pointwise variances (Sec. 4, Phase 2) follow from unit vectors.  Requires the SE
+ * prior and factor_K; synchronises. */
+bti_status bti_apply_postcov(bti_handle h, const double* v, double* out, int64_t B);
+
+/* m_map with a nonzero prior mean, Eq. (4.13) with the term of Eq. (4.8):
+ * m_map = G^* K^{-1} d_obs + (I - G^* K^{-1} F) m_prior
+ *       = m_prior + G^* K^{-1} (d_obs - F m_prior).
+ * d_obs [B][N_t][N_d], m_prior and m_map [B][N_t][N_m] (device doubles; m_prior and
+ * m_map not aliased).  refine_iters as bti_infer_map.  Synchronises. */
+bti_status bti_infer_map_prior(bti_handle h, const double* d_obs, const double* m_prior, double* m_map, int64_t B,
+                               int refine_iters);
 
 /* Elliptic prior operator of Eq. (5.1), per time block: out = A_s m with
  * A_s = alpha1 I - alpha2 Delta_h on the gx x gy grid (gx * gy = N_m, node

@@ -72,6 +72,10 @@ def lib():
         "bti_predict_qoi": ([vp, vp, vp, i64], st),
         "bti_online": ([vp, vp, vp, vp, i64, ip], st),
         "bti_build_Q": ([vp, ip], st),
+        "bti_apply_prior": ([vp, vp, vp, i64], st),
+        "bti_set_qoi_stride": ([vp, ip], st),
+        "bti_apply_postcov": ([vp, vp, vp, i64], st),
+        "bti_infer_map_prior": ([vp, vp, vp, vp, i64, ip], st),
         "bti_apply_Q": ([vp, vp, vp, i64], st),
         "bti_copy_Q": ([vp, vp, vp], st),
         "bti_apply_elliptic": ([vp, ip, ip, dp, dp, vp, vp, i64, ip], st),
@@ -114,6 +118,7 @@ class Handle:
         import torch
 
         self.Nm, self.Nd, self.Nq, self.Nt = int(Nm), int(Nd), int(Nq), int(Nt)
+        self.Ntq = self.Nt  # QoI time steps (bti_set_qoi_stride)
         self.device = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
         if stream is None:
             stream = torch.cuda.current_stream(self.device)
@@ -218,7 +223,12 @@ class Handle:
         return self._apply(lib().bti_apply_FT, d, m, (self.Nt, self.Nd), (self.Nt, self.Nm))
 
     def apply_Fq(self, m, q):
-        return self._apply(lib().bti_apply_Fq, m, q, (self.Nt, self.Nm), (self.Nt, self.Nq))
+        return self._apply(lib().bti_apply_Fq, m, q, (self.Nt, self.Nm), (self.Ntq, self.Nq))
+
+    def set_qoi_stride(self, stride):
+        """QoI on every stride-th time step (N_t^q = N_t / stride)."""
+        self._check(lib().bti_set_qoi_stride(self._h, int(stride)))
+        self.Ntq = self.Nt // int(stride)
 
     def apply_Gstar(self, d, m):
         return self._apply(lib().bti_apply_Gstar, d, m, (self.Nt, self.Nd), (self.Nt, self.Nm))
@@ -251,6 +261,35 @@ class Handle:
         self._check(lib().bti_infer_map(self._h, _ptr(d_obs), _ptr(m_map), B, int(refine_iters)))
         return m_map
 
+    def apply_prior(self, v, out):
+        """out = Gamma_prior v (the SE prior per time block)."""
+        return self._param_op(lib().bti_apply_prior, v, out, "apply_prior")
+
+    def apply_postcov(self, v, out):
+        """out = Gamma_post(m) v (Eq. (4.7))."""
+        return self._param_op(lib().bti_apply_postcov, v, out, "apply_postcov")
+
+    def _param_op(self, fn, v, out, name):
+        self._tensor(v, (self.Nt, self.Nm), name + " input")
+        self._tensor(out, (self.Nt, self.Nm), name + " output")
+        B = self._batch(v, 2)
+        if self._batch(out, 2) != B:
+            raise ValueError("batch sizes differ")
+        self._check(fn(self._h, _ptr(v), _ptr(out), B))
+        return out
+
+    def infer_map_prior(self, d_obs, m_prior, m_map, refine_iters=0):
+        """m_map with a nonzero prior mean (Eq. (4.13) with Eq. (4.8))."""
+        self._tensor(d_obs, (self.Nt, self.Nd), "d_obs")
+        self._tensor(m_prior, (self.Nt, self.Nm), "m_prior")
+        self._tensor(m_map, (self.Nt, self.Nm), "m_map")
+        B = self._batch(d_obs, 2)
+        if self._batch(m_prior, 2) != B or self._batch(m_map, 2) != B:
+            raise ValueError("batch sizes differ")
+        self._check(lib().bti_infer_map_prior(self._h, _ptr(d_obs), _ptr(m_prior), _ptr(m_map), B,
+                                              int(refine_iters)))
+        return m_map
+
     def build_Q(self, with_covariance=False):
         """Precompute the d2q map Q (Eq. (4.11)) and optionally Gamma_post(q) (Eq. (4.10))."""
         self._check(lib().bti_build_Q(self._h, 1 if with_covariance else 0))
@@ -258,7 +297,7 @@ class Handle:
     def apply_Q(self, d_obs, q_map):
         """q_map = Q d_obs (Eq. (4.14))."""
         self._tensor(d_obs, (self.Nt, self.Nd), "d_obs")
-        self._tensor(q_map, (self.Nt, self.Nq), "q_map")
+        self._tensor(q_map, (self.Ntq, self.Nq), "q_map")
         B = self._batch(d_obs, 2)
         if self._batch(q_map, 2) != B:
             raise ValueError("d_obs and q_map batch sizes differ")
@@ -269,7 +308,7 @@ class Handle:
         """(Q, Gamma_post(q) or None) as new device tensors."""
         import torch
 
-        nq, n = self.Nt * self.Nq, self.Nt * self.Nd
+        nq, n = self.Ntq * self.Nq, self.Nt * self.Nd
         Q = torch.empty((nq, n), dtype=torch.float64, device=self.device)
         C = torch.empty((nq, nq), dtype=torch.float64, device=self.device) if covariance else None
         self._check(lib().bti_copy_Q(self._h, _ptr(Q), _ptr(C)))
@@ -277,7 +316,7 @@ class Handle:
 
     def predict_qoi(self, m_map, q_map):
         self._tensor(m_map, (self.Nt, self.Nm), "m_map")
-        self._tensor(q_map, (self.Nt, self.Nq), "q_map")
+        self._tensor(q_map, (self.Ntq, self.Nq), "q_map")
         B = self._batch(m_map, 2)
         if self._batch(q_map, 2) != B:
             raise ValueError("m_map and q_map batch sizes differ")
@@ -292,7 +331,7 @@ class Handle:
         if self._batch(m_map, 2) != B:
             raise ValueError("d_obs and m_map batch sizes differ")
         if q_map is not None:
-            self._tensor(q_map, (self.Nt, self.Nq), "q_map")
+            self._tensor(q_map, (self.Ntq, self.Nq), "q_map")
             if self._batch(q_map, 2) != B:
                 raise ValueError("m_map and q_map batch sizes differ")
         self._check(lib().bti_online(self._h, _ptr(d_obs), _ptr(m_map), _ptr(q_map), B, int(refine_iters)))

@@ -32,7 +32,7 @@ struct OpStore {
 // Launch shapes chosen by bti_autotune (0 = library default), per storage tier.
 struct Tune {
   int fft_p = 0;  // column pairs per FFT CTA
-  int jc = 0;     // columns per CTA of the forward product
+  int jc[2] = {0, 0};  // columns per CTA of the forward product: single vectors, groups of 4
   int vpt = 0;    // columns per thread of the adjoint product
 };
 
@@ -53,6 +53,7 @@ struct bti_ctx {
   double* Q = nullptr;           // [N_q N_t][N_d N_t] d2q map
   double* covq = nullptr;        // [N_q N_t][N_q N_t] posterior covariance of the QoI
   bool Q_built = false, covq_built = false;
+  int qstride = 1;               // QoI time grid: every qstride-th step (N_t^q = N_t / qstride)
   double* K = nullptr;           // [n][n], lower triangle: K, then L after factor_K
   double* Linv = nullptr;        // inverses of the factor's diagonal blocks
   bool K_built = false, K_factored = false;
@@ -273,7 +274,7 @@ void rfft_in(bti_ctx* h, const OpStore& o, const void* in, int64_t ld, int64_t b
 // Inverse FFT with truncation to N_t steps and the 1/L scale, output in the io type.
 template <typename T>
 void irfft_out(bti_ctx* h, const OpStore& o, const C2<T>* Y, int64_t ld, int64_t Ybstride, void* out,
-               int64_t obstride, int64_t ncols, int64_t B, bti_prec io) {
+               int64_t obstride, int64_t ncols, int64_t B, bti_prec io, int os = 1) {
   const int Nt = (int)h->Nt;
   cudaStream_t s = h->stream;
   const FftPlan plan = tuned_plan(h, o);
@@ -281,16 +282,16 @@ void irfft_out(bti_ctx* h, const OpStore& o, const C2<T>* Y, int64_t ld, int64_t
   if (o.prec == BTI_P_DF64) {
     if (io == BTI_P_F64)
       PROF(h, BTI_K_IRFFT, (launch_irfft_cols<ffloat, double, double>(plan, Nt, (const double2*)Y, ld, Ybstride,
-                                                                       (double*)out, obstride, ncols, B, scale, s)));
+                                                                       (double*)out, obstride, ncols, B, scale, s, os)));
     else
       PROF(h, BTI_K_IRFFT, (launch_irfft_cols<ffloat, double, float>(plan, Nt, (const double2*)Y, ld, Ybstride,
-                                                                      (float*)out, obstride, ncols, B, scale, s)));
+                                                                      (float*)out, obstride, ncols, B, scale, s, os)));
   } else if (io == BTI_P_F64) {
     PROF(h, BTI_K_IRFFT, (launch_irfft_cols<T, T, double>(plan, Nt, Y, ld, Ybstride, (double*)out, obstride,
-                                                           ncols, B, scale, s)));
+                                                           ncols, B, scale, s, os)));
   } else {
     PROF(h, BTI_K_IRFFT, (launch_irfft_cols<T, T, float>(plan, Nt, Y, ld, Ybstride, (float*)out, obstride,
-                                                          ncols, B, scale, s)));
+                                                          ncols, B, scale, s, os)));
   }
 }
 
@@ -308,17 +309,20 @@ bti_status apply_fwd_t(bti_ctx* h, const OpStore& o, const void* in, void* out, 
   C2<T>* dhat = part + n_part;
   cudaStream_t s = h->stream;
   rfft_in<T>(h, o, in, Nm, Nt * Nm, mhat, nf * Nm, Nm, B, io);
+  const int jc = h->tune[o.prec].jc[fwd_group(B) == 4];
   if (o.prec == BTI_P_DF64)
     PROF(h, BTI_K_PROD_FWD, launch_prod_fwd_df64((const float4*)o.hat, (const double2*)mhat, (double2*)part, nf,
-                                                 R, Nm, B, s, h->tune[o.prec].jc));
+                                                 R, Nm, B, s, jc));
   else if (o.prec == BTI_P_F16)
     PROF(h, BTI_K_PROD_FWD, launch_prod_fwd_f16(o.hat, o.scale, (const float2*)mhat, (float2*)part, nf, R, Nm, B,
-                                                s, h->tune[o.prec].jc));
+                                                s, jc));
   else
     PROF(h, BTI_K_PROD_FWD, (launch_prod_fwd<T, T>((const C2<T>*)o.hat, mhat, part, nf, R, Nm, B, s,
-                                                   h->tune[o.prec].jc)));
-  PROF(h, BTI_K_REDUCE, (launch_reduce_chunks<T>(part, dhat, nf, R, Nm, B, s, h->tune[o.prec].jc)));
-  irfft_out<T>(h, o, dhat, R, nf * R, out, Nt * R, R, B, io);
+                                                   jc)));
+  PROF(h, BTI_K_REDUCE, (launch_reduce_chunks<T>(part, dhat, nf, R, Nm, B, s, jc)));
+  // the QoI map writes every qstride-th time step only (N_t / qstride rows per vector)
+  const int os = (&o == &h->op[BTI_OP_FQ]) ? h->qstride : 1;
+  irfft_out<T>(h, o, dhat, R, nf * R, out, (Nt / os) * R, R, B, io, os);
   return launched(h, "forward Toeplitz product");
 }
 
@@ -773,11 +777,10 @@ bti_status bti_infer_map(bti_handle h, const double* d_obs, double* m_map, int64
   return infer_map_impl(h, d_obs, m_map, B, refine_iters);
 }
 
-// G_q = F_q C_s for the stored SE prior, from F_q's time-domain blocks (device buffer out).
-static bti_status prior_apply_fq(bti_ctx* h, double* out) {
-  const OpStore& Fq = h->op[BTI_OP_FQ];
+// out = in C_s for `rows` grid-shaped rows (row r viewed as X_r [gx][gy]: C_x X_r C_y),
+// with the stored SE prior: the time-invariant Gamma_prior applied block by block.
+static bti_status apply_se_rows(bti_ctx* h, const double* in, double* out, int64_t rows) {
   const int gx = h->prior_gx, gy = h->prior_gy;
-  const int64_t rows = h->Nt * h->Nq;
   double* Cx = nullptr;
   double* U = nullptr;
   bti_status st = dev_alloc(h, (void**)&Cx, sizeof(double) * ((size_t)gx * gx + (size_t)gy * gy), "prior axes");
@@ -788,15 +791,20 @@ static bti_status prior_apply_fq(bti_ctx* h, double* out) {
   cudaStream_t s = h->stream;
   int64_t nl = se_axis_matrix(Cx, gx, h->prior_ell, h->prior_sigma, s);
   nl += se_axis_matrix(Cy, gy, h->prior_ell, h->prior_sigma, s);
-  nl += gemm_f64(false, rows * gx, gy, gy, 1.0, Fq.time, gy, 0, Cy, gy, 0, 0.0, U, gy, 0, 1, false, s);
+  nl += gemm_f64(false, rows * gx, gy, gy, 1.0, in, gy, 0, Cy, gy, 0, 0.0, U, gy, 0, 1, false, s);
   nl += gemm_f64(false, gx, gy, gx, 1.0, Cx, gx, 0, U, gy, (int64_t)gx * gy, 0.0, out, gy, (int64_t)gx * gy, rows,
                  false, s);
   count_dense(h, nl);
-  st = launched(h, "prior on F_q");
+  st = launched(h, "SE prior");
   cudaStreamSynchronize(s);
   dev_freep(Cx);
   dev_freep(U);
   return st;
+}
+
+// G_q = F_q C_s from F_q's time-domain blocks.
+static bti_status prior_apply_fq(bti_ctx* h, double* out) {
+  return apply_se_rows(h, h->op[BTI_OP_FQ].time, out, h->Nt * h->Nq);
 }
 
 bti_status bti_build_Q(bti_handle h, int with_covariance) {
@@ -809,18 +817,33 @@ bti_status bti_build_Q(bti_handle h, int with_covariance) {
   if (!G.set || !G.time) return fail(h, BTI_ERR_STATE, "build_Q: G blocks not set");
   if (with_covariance && !h->prior_set)
     return fail(h, BTI_ERR_STATE, "build_Q: the covariance needs the SE prior (bti_set_prior_se_grid)");
-  const int64_t n = h->Nt * h->Nd, nq = h->Nt * h->Nq, Nm = h->Nm;
+  const int64_t n = h->Nt * h->Nd, nqf = h->Nt * h->Nq, Nm = h->Nm;
+  const int qs = h->qstride;
+  const int64_t nq = (h->Nt / qs) * h->Nq;  // rows of Q on the QoI time grid
   const bool dd = h->dense_prec == BTI_P_DF64;
   auto gemm = dd ? gemm_df64 : gemm_f64;
   cudaStream_t s = h->stream;
-  if (!h->Q) {
-    st = dev_alloc(h, (void**)&h->Q, sizeof(double) * (size_t)nq * n, "alloc Q");
+  dev_freep(h->Q);  // the QoI grid may have changed since the last build
+  dev_freep(h->covq);
+  st = dev_alloc(h, (void**)&h->Q, sizeof(double) * (size_t)nq * n, "alloc Q");
+  if (st != BTI_OK) return st;
+  h->Q_built = h->covq_built = false;
+  // X = F_q G^*: Gram of the stacked blocks, then block-diagonal prefix sums (fine time grid);
+  // the rows at QoI times t = qs (k + 1) - 1 form Q's right-hand sides
+  double* Xf = h->Q;
+  if (qs > 1) {
+    st = dev_alloc(h, (void**)&Xf, sizeof(double) * (size_t)nqf * n, "F_q G* (fine)");
     if (st != BTI_OK) return st;
   }
-  h->Q_built = h->covq_built = false;
-  // X = F_q G^*: Gram of the stacked blocks, then block-diagonal prefix sums
-  int64_t nl = gemm(true, nq, n, Nm, 1.0, Fq.time, Nm, 0, G.time, Nm, 0, 0.0, h->Q, n, 0, 1, false, s);
-  nl += block_diag_cumsum_all(h->Q, h->Nt, h->Nq, h->Nd, s);
+  int64_t nl = gemm(true, nqf, n, Nm, 1.0, Fq.time, Nm, 0, G.time, Nm, 0, 0.0, Xf, n, 0, 1, false, s);
+  nl += block_diag_cumsum_all(Xf, h->Nt, h->Nq, h->Nd, s);
+  if (qs > 1) {
+    const size_t blk = sizeof(double) * (size_t)h->Nq * n;  // one time block of rows
+    cudaMemcpy2DAsync(h->Q, blk, (const char*)Xf + (qs - 1) * blk, qs * blk, blk, h->Nt / qs,
+                      cudaMemcpyDeviceToDevice, s);
+    cudaStreamSynchronize(s);
+    dev_freep(Xf);
+  }
   double* X = nullptr;
   if (with_covariance) {
     st = dev_alloc(h, (void**)&X, sizeof(double) * (size_t)nq * n, "F_q G* copy");
@@ -834,16 +857,21 @@ bti_status bti_build_Q(bti_handle h, int with_covariance) {
   nl += trsm_lower_f64(h->K, h->Linv, n, h->Q, nq, h->wsolve, h->status, s, dd);
   if (with_covariance) {
     double* Gq = nullptr;
-    st = dev_alloc(h, (void**)&Gq, sizeof(double) * (size_t)nq * Nm, "G_q blocks");
+    double* Cf = nullptr;
+    st = dev_alloc(h, (void**)&Gq, sizeof(double) * (size_t)nqf * Nm, "G_q blocks");
     if (st == BTI_OK) st = prior_apply_fq(h, Gq);
-    if (st == BTI_OK && !h->covq) st = dev_alloc(h, (void**)&h->covq, sizeof(double) * (size_t)nq * nq, "alloc cov");
-    if (st != BTI_OK) { dev_freep(X); dev_freep(Gq); return st; }
-    // Gamma_post(q) = F_q Gamma_prior F_q^T - Q X^T  (Eq. (4.10) with F G_q^* = X^T)
-    nl += gemm(true, nq, nq, Nm, 1.0, Fq.time, Nm, 0, Gq, Nm, 0, 0.0, h->covq, nq, 0, 1, false, s);
-    nl += block_diag_cumsum_all(h->covq, h->Nt, h->Nq, h->Nq, s);
+    if (st == BTI_OK) st = dev_alloc(h, (void**)&h->covq, sizeof(double) * (size_t)nq * nq, "alloc cov");
+    if (st == BTI_OK && qs > 1) st = dev_alloc(h, (void**)&Cf, sizeof(double) * (size_t)nqf * nqf, "cov (fine)");
+    if (st != BTI_OK) { dev_freep(X); dev_freep(Gq); dev_freep(Cf); return st; }
+    // Gamma_post(q) = F_q Gamma_prior F_q^T - Q X^T  (Eq. (4.10) with F G_q^* = X^T), on the QoI grid
+    double* C0 = qs > 1 ? Cf : h->covq;
+    nl += gemm(true, nqf, nqf, Nm, 1.0, Fq.time, Nm, 0, Gq, Nm, 0, 0.0, C0, nqf, 0, 1, false, s);
+    nl += block_diag_cumsum_all(C0, h->Nt, h->Nq, h->Nq, s);
+    if (qs > 1) nl += select_time_blocks_sq(Cf, h->covq, h->Nt, h->Nq, qs, s);
     nl += gemm(true, nq, nq, n, -1.0, h->Q, n, 0, X, n, 0, 1.0, h->covq, nq, 0, 1, false, s);
     cudaStreamSynchronize(s);
     dev_freep(Gq);
+    dev_freep(Cf);
     dev_freep(X);
   }
   count_dense(h, nl);
@@ -861,7 +889,7 @@ bti_status bti_apply_Q(bti_handle h, const double* d_obs, double* q_map, int64_t
   if (!h->Q_built) return fail(h, BTI_ERR_STATE, "apply_Q: Q not built");
   if (B == 0) return BTI_OK;
   if (!d_obs || !q_map) return fail(h, BTI_ERR_ARG, "apply_Q: null pointer");
-  const int64_t n = h->Nt * h->Nd, nq = h->Nt * h->Nq;
+  const int64_t n = h->Nt * h->Nd, nq = (h->Nt / h->qstride) * h->Nq;
   // q[b] = Q d[b]: rows of d against rows of Q
   const bool dd = h->dense_prec == BTI_P_DF64 && B > 8;
   count_dense(h, (dd ? gemm_df64 : gemm_f64)(true, B, nq, n, 1.0, d_obs, n, 0, h->Q, n, 0, 0.0, q_map, nq, 0, 1,
@@ -874,7 +902,7 @@ bti_status bti_copy_Q(bti_handle h, double* Q_out, double* cov_out) {
   if (st != BTI_OK) return st;
   if (!h->Q_built) return fail(h, BTI_ERR_STATE, "copy_Q: Q not built");
   if (cov_out && !h->covq_built) return fail(h, BTI_ERR_STATE, "copy_Q: covariance not built");
-  const size_t nq = (size_t)h->Nt * h->Nq, n = (size_t)h->Nt * h->Nd;
+  const size_t nq = (size_t)(h->Nt / h->qstride) * h->Nq, n = (size_t)h->Nt * h->Nd;
   if (Q_out) {
     st = cuda_check(h, cudaMemcpyAsync(Q_out, h->Q, sizeof(double) * nq * n, cudaMemcpyDeviceToDevice, h->stream),
                     "copy Q");
@@ -883,6 +911,83 @@ bti_status bti_copy_Q(bti_handle h, double* Q_out, double* cov_out) {
   if (cov_out)
     st = cuda_check(h, cudaMemcpyAsync(cov_out, h->covq, sizeof(double) * nq * nq, cudaMemcpyDeviceToDevice,
                                        h->stream), "copy covariance");
+  return st;
+}
+
+bti_status bti_set_qoi_stride(bti_handle h, int stride) {
+  bti_status st = check_handle(h);
+  if (st != BTI_OK) return st;
+  if (stride < 1 || h->Nt % stride != 0) return fail(h, BTI_ERR_ARG, "set_qoi_stride: stride must divide N_t");
+  if (stride != h->qstride) {
+    drop_online_graph_any(h);
+    h->Q_built = h->covq_built = false;
+  }
+  h->qstride = stride;
+  return BTI_OK;
+}
+
+bti_status bti_apply_prior(bti_handle h, const double* v, double* out, int64_t B) {
+  bti_status st = check_handle(h);
+  if (st != BTI_OK) return st;
+  if (B < 0) return fail(h, BTI_ERR_ARG, "apply_prior: B < 0");
+  if (!h->prior_set) return fail(h, BTI_ERR_STATE, "apply_prior: no SE prior set");
+  if (B == 0) return BTI_OK;
+  if (!v || !out || v == out) return fail(h, BTI_ERR_ARG, "apply_prior: null or aliased pointers");
+  return apply_se_rows(h, v, out, B * h->Nt);
+}
+
+bti_status bti_apply_postcov(bti_handle h, const double* v, double* out, int64_t B) {
+  bti_status st = check_handle(h);
+  if (st != BTI_OK) return st;
+  if (B < 0) return fail(h, BTI_ERR_ARG, "apply_postcov: B < 0");
+  if (!h->prior_set) return fail(h, BTI_ERR_STATE, "apply_postcov: no SE prior set");
+  if (!h->K_factored || !h->op[BTI_OP_G].set) return fail(h, BTI_ERR_STATE, "apply_postcov: K not factored");
+  if (B == 0) return BTI_OK;
+  if (!v || !out || v == out) return fail(h, BTI_ERR_ARG, "apply_postcov: null or aliased pointers");
+  const int64_t n = h->Nt * h->Nd, npar = h->Nt * h->Nm;
+  // Eq. (4.7): out = w - G^* K^{-1} F w with w = Gamma_prior v
+  st = apply_se_rows(h, v, out, B * h->Nt);
+  if (st != BTI_OK) return st;
+  double* z = nullptr;
+  st = dev_alloc(h, (void**)&z, sizeof(double) * ((size_t)B * npar + (size_t)B * n), "postcov temporaries");
+  if (st != BTI_OK) return st;
+  double* y = z + (size_t)B * npar;
+  st = apply_op(h, BTI_OP_F, false, out, y, B, BTI_P_F64, "postcov F");
+  if (st == BTI_OK) st = infer_map_impl(h, y, z, B, 0);  // z = G^* K^{-1} y
+  if (st == BTI_OK) {
+    count_dense(h, axpby_f64(out, z, -1.0, 1.0, B * npar, h->stream));
+    st = launched(h, "apply_postcov");
+  }
+  cudaStreamSynchronize(h->stream);
+  dev_freep(z);
+  return st;
+}
+
+bti_status bti_infer_map_prior(bti_handle h, const double* d_obs, const double* m_prior, double* m_map, int64_t B,
+                               int refine_iters) {
+  bti_status st = check_handle(h);
+  if (st != BTI_OK) return st;
+  if (B < 0) return fail(h, BTI_ERR_ARG, "infer_map_prior: B < 0");
+  if (B == 0) return BTI_OK;
+  if (!d_obs || !m_prior || !m_map || m_prior == m_map)
+    return fail(h, BTI_ERR_ARG, "infer_map_prior: null or aliased pointers");
+  if (!h->K_factored || !h->op[BTI_OP_G].set) return fail(h, BTI_ERR_STATE, "infer_map_prior: K not factored");
+  const int64_t n = h->Nt * h->Nd, npar = h->Nt * h->Nm;
+  // Eq. (4.13) + Eq. (4.8): m_map = m_prior + G^* K^{-1} (d_obs - F m_prior)
+  double* r = nullptr;
+  st = dev_alloc(h, (void**)&r, sizeof(double) * (size_t)B * n, "prior-mean residual");
+  if (st != BTI_OK) return st;
+  st = apply_op(h, BTI_OP_F, false, m_prior, r, B, BTI_P_F64, "infer_map_prior F");
+  if (st == BTI_OK) {
+    count_dense(h, axpby_f64(r, d_obs, 1.0, -1.0, B * n, h->stream));
+    st = infer_map_impl(h, r, m_map, B, refine_iters);
+  }
+  if (st == BTI_OK) {
+    count_dense(h, axpby_f64(m_map, m_prior, 1.0, 1.0, B * npar, h->stream));
+    st = launched(h, "infer_map_prior");
+  }
+  cudaStreamSynchronize(h->stream);
+  dev_freep(r);
   return st;
 }
 
@@ -1033,17 +1138,21 @@ bti_status bti_autotune(bti_handle h, bti_op op, int64_t B, char* report, int64_
   // 2. columns per CTA of the forward product
   {
     const int cand[4] = {512, 1024, 2048, 4096};
+    const int g = fwd_group(B);
+    const size_t col_bytes = (o.prec == BTI_P_F64 || o.prec == BTI_P_DF64) ? 16 : 8;  // staged m-hat
+    int& jc = t.jc[g == 4];
     int best = 0;
     float best_ms = 1e30f;
     rep += ", \"jc\": {";
     for (int c = 0; c < 4; ++c) {
       if (c > 0 && cand[c - 1] >= Nm) break;
-      t.jc = cand[c];
+      if ((size_t)g * cand[c] * col_bytes > kFwdSmemMax) break;
+      jc = cand[c];
       float ms = time_ms(h, fwd, 3);
       rep += std::string(c ? ", " : "") + "\"" + std::to_string(cand[c]) + "\": " + std::to_string(ms);
       if (ms < best_ms) { best_ms = ms; best = cand[c]; }
     }
-    t.jc = best;
+    jc = best;
     rep += "}, \"jc_chosen\": " + std::to_string(best);
   }
   // 3. columns per thread of the adjoint product (single-vector kernel)

@@ -121,13 +121,19 @@ template <typename T, typename TI, typename TO>
 void launch_rfft_cols(const FftPlan& p, int Nt, const TI* x, int64_t ld, int64_t x_bstride,
                       C2<TO>* X, int64_t X_bstride, int64_t ncols, int64_t B, cudaStream_t s);
 // Inverse: spectrum stored as C2<TYI>, arithmetic in T, output TO.
+// ostride > 1 keeps only rows t = ostride (k + 1) - 1, written as row k (N_t / ostride rows).
 template <typename T, typename TYI, typename TO>
 void launch_irfft_cols(const FftPlan& p, int Nt, const C2<TYI>* X, int64_t ld, int64_t X_bstride,
-                       TO* y, int64_t y_bstride, int64_t ncols, int64_t B, double scale, cudaStream_t s);
+                       TO* y, int64_t y_bstride, int64_t ncols, int64_t B, double scale, cudaStream_t s,
+                       int ostride = 1);
 
 // Spectral block products (spectral.cu).
 // Forward: dhat[b][w][i] = sum_j Fhat[w][i][j] mhat[b][w][j]  (T compute, TS storage)
-// jc: columns per CTA (0 = tier default; else a multiple of 256, >= 512), the tuning knob
+// jc: columns per CTA (0 = tier default; else a multiple of 256, >= 512), the tuning knob.
+// A CTA takes fwd_group(B) right-hand sides and stages their m-hat chunk in shared memory;
+// a jc whose chunk would exceed kFwdSmemMax falls back to the tier default.
+inline int fwd_group(int64_t B) { return B >= 4 ? 4 : 1; }
+constexpr size_t kFwdSmemMax = 96 * 1024;
 template <typename T, typename TS>
 void launch_prod_fwd(const C2<TS>* Fhat, const C2<T>* mhat, C2<T>* partial,
                      int64_t nf, int64_t R, int64_t Nm, int64_t B, cudaStream_t s, int jc = 0);
@@ -187,6 +193,9 @@ int convert_f64_to_f32(const double* x, float* y, int64_t n, cudaStream_t s);
 // out = (alpha1 I - alpha2 Delta_h) m for nblocks grids of gx x gy (5-point, Neumann)
 int elliptic_apply(const double* m, double* out, int gx, int gy, double a1, double a2, int64_t nblocks,
                    cudaStream_t s);
+// out[k1 R + i][k2 R + j] = in[(s (k1+1) - 1) R + i][(s (k2+1) - 1) R + j]: rows and columns at
+// every s-th time block of an (Nt R)^2 matrix (ld Nt R); out is (Nt/s R)^2.
+int select_time_blocks_sq(const double* in, double* out, int64_t Nt, int64_t R, int s, cudaStream_t st);
 // Block-diagonal prefix sums on both sides of the diagonal (block-Toeplitz product A B^*).
 int block_diag_cumsum_all(double* X, int64_t Nt, int64_t R1, int64_t R2, cudaStream_t s);
 int noise_residual_f64(double* r, const double* x, const double* diag, int64_t n, int64_t B,

@@ -733,3 +733,24 @@ int block_diag_cumsum_all(double* X, int64_t Nt, int64_t R1, int64_t R2, cudaStr
 }
 
 }  // namespace bti
+
+namespace bti {
+
+__global__ void select_time_blocks_sq_kernel(const double* __restrict__ in, double* __restrict__ out, int64_t Nt,
+                                             int64_t R, int s) {
+  const int64_t nc = (Nt / s) * R;
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nc * nc) return;
+  const int64_t r = idx / nc, c = idx - r * nc;
+  const int64_t tr = s * (r / R + 1) - 1, tc = s * (c / R + 1) - 1;
+  out[idx] = in[(tr * R + r % R) * (Nt * R) + tc * R + c % R];
+}
+
+int select_time_blocks_sq(const double* in, double* out, int64_t Nt, int64_t R, int s, cudaStream_t st) {
+  const int64_t nc = (Nt / s) * R;
+  if (nc <= 0) return 0;
+  select_time_blocks_sq_kernel<<<(unsigned)((nc * nc + 255) / 256), 256, 0, st>>>(in, out, Nt, R, s);
+  return 1;
+}
+
+}  // namespace bti

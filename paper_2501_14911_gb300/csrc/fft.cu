@@ -329,7 +329,7 @@ rfft_cols_kernel(FftDesc D, int Nt, const TI* __restrict__ x, int64_t ld, int64_
 template <typename T, typename TYI, typename TO>
 __global__ void __launch_bounds__(256, 2)
 irfft_cols_kernel(FftDesc D, int Nt, const C2<TYI>* __restrict__ Y, int64_t ld, int64_t Ybs,
-                  TO* __restrict__ y, int64_t ybs, int64_t ncols, double scale_d, TwTabs tabs) {
+                  TO* __restrict__ y, int64_t ybs, int64_t ncols, double scale_d, TwTabs tabs, int ostride) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int L = D.L, P = D.P, W2 = 2 * P;
   C2<T>* buf0 = reinterpret_cast<C2<T>*>(smem_raw);
@@ -364,13 +364,16 @@ irfft_cols_kernel(FftDesc D, int Nt, const C2<TYI>* __restrict__ Y, int64_t ld, 
   }
   __syncthreads();
   C2<T>* Z = run_passes<T, true>(D, buf0, buf1, tw);
-  for (int idx = threadIdx.x; idx < Nt * W2; idx += blockDim.x) {
-    int t = idx / W2, c = idx - t * W2;
+  // rows t = ostride (k + 1) - 1 only (every row when ostride == 1), stored as row k
+  const int nout = Nt / ostride;
+  for (int idx = threadIdx.x; idx < nout * W2; idx += blockDim.x) {
+    int k = idx / W2, c = idx - k * W2;
     int64_t col = col0 + c;
     if (col >= ncols) continue;
+    const int t = ostride * (k + 1) - 1;
     C2<T> z = Z[(c >> 1) * L + t];
     T v = ((c & 1) ? z.y : z.x) * scale;
-    yb[(int64_t)t * ld + col] = (TO)v;
+    yb[(int64_t)k * ld + col] = (TO)v;
   }
 }
 
@@ -407,7 +410,8 @@ void launch_rfft_cols(const FftPlan& p, int Nt, const TI* x, int64_t ld, int64_t
 
 template <typename T, typename TYI, typename TO>
 void launch_irfft_cols(const FftPlan& p, int Nt, const C2<TYI>* X, int64_t ld, int64_t X_bstride,
-                       TO* y, int64_t y_bstride, int64_t ncols, int64_t B, double scale, cudaStream_t s) {
+                       TO* y, int64_t y_bstride, int64_t ncols, int64_t B, double scale, cudaStream_t s,
+                       int ostride) {
   if (ncols <= 0 || B <= 0) return;
   FftDesc D = desc_of(p);
   size_t smem = 2 * sizeof(C2<T>) * (size_t)p.P * p.L;
@@ -422,7 +426,7 @@ void launch_irfft_cols(const FftPlan& p, int Nt, const C2<TYI>* X, int64_t ld, i
     dim3 grid((unsigned)gx, (unsigned)nb);
     irfft_cols_kernel<T, TYI, TO><<<grid, 256, smem, s>>>(D, Nt, X + b0 * X_bstride, ld, X_bstride,
                                                           y + b0 * y_bstride, y_bstride, ncols, scale,
-                                                          tabs_of(p));
+                                                          tabs_of(p), ostride < 1 ? 1 : ostride);
   }
 }
 
@@ -438,7 +442,7 @@ INST_R(ffloat, double, double)
 INST_R(ffloat, float, double)
 #define INST_I(T, TYI, TO)                                                                             \
   template void launch_irfft_cols<T, TYI, TO>(const FftPlan&, int, const C2<TYI>*, int64_t, int64_t, TO*, \
-                                              int64_t, int64_t, int64_t, double, cudaStream_t);
+                                              int64_t, int64_t, int64_t, double, cudaStream_t, int);
 INST_I(double, double, double)
 INST_I(double, double, float)
 INST_I(float, float, float)

@@ -15,6 +15,10 @@
 
 namespace bti {
 
+// Rows of d-hat the adjoint kernels stage in shared memory at a time (any R is accepted;
+// 4 x 512 x 16 bytes stays within the default 48 KB of dynamic shared memory).
+constexpr int64_t kAdjRows = 512;
+
 template <typename T> struct FwdCfg;
 template <> struct FwdCfg<double> { static constexpr int JC1 = 2048, JC4 = 512; };
 template <> struct FwdCfg<float> { static constexpr int JC1 = 4096, JC4 = 1024; };
@@ -116,7 +120,7 @@ __global__ void reduce_chunks_kernel(const C2<T>* __restrict__ partial, C2<T>* _
   dhat[idx] = mk<T>(sr, si);
 }
 
-template <typename T> static int fwd_bg(int64_t B) { return B >= 4 ? 4 : 1; }
+template <typename T> static int fwd_bg(int64_t B) { return fwd_group(B); }
 template <typename T> static int fwd_jc(int bg) { return bg == 4 ? FwdCfg<T>::JC4 : FwdCfg<T>::JC1; }
 
 size_t prod_fwd_partial_elems(int64_t nf, int64_t R, int64_t Nm, int64_t B) {
@@ -131,6 +135,8 @@ template <typename T>
 static int fwd_nchunk(int64_t Nm, int64_t B, int* jc_out, int jc = 0) {
   int bg = fwd_bg<T>(B);
   int JC = jc > 0 ? jc : fwd_jc<T>(bg);
+  // the staged m-hat chunk must fit the dynamic shared memory the kernels opt into
+  if ((size_t)bg * JC * sizeof(C2<T>) > kFwdSmemMax) JC = fwd_jc<T>(bg);
   if (Nm < JC) JC = (int)(((Nm + 31) / 32) * 32);
   if (jc_out) *jc_out = JC;
   return (int)((Nm + JC - 1) / JC);
@@ -155,8 +161,8 @@ void launch_prod_fwd(const C2<TS>* Fhat, const C2<T>* mhat, C2<T>* partial,
   constexpr int U1 = sizeof(C2<TS>) >= 16 ? 8 : 16;  // 128 bytes of loads per lane per step
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(prod_fwd_kernel<T, TS, 4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    cudaFuncSetAttribute(prod_fwd_kernel<T, TS, 1, U1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    cudaFuncSetAttribute(prod_fwd_kernel<T, TS, 4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmemMax);
+    cudaFuncSetAttribute(prod_fwd_kernel<T, TS, 1, U1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmemMax);
     attr = true;
   }
   if (bg == 4)
@@ -171,16 +177,9 @@ __global__ void __launch_bounds__(256)
 prod_adj_kernel(const C2<TS>* __restrict__ Fhat, const C2<T>* __restrict__ dhat,
                 C2<T>* __restrict__ mhat, int64_t nf, int64_t R, int64_t Nm, int64_t B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C2<T>* sd = reinterpret_cast<C2<T>*>(smem_raw);  // [BG][R]
+  C2<T>* sd = reinterpret_cast<C2<T>*>(smem_raw);  // [BG][min(R, kAdjRows)]
   const int64_t w = blockIdx.y;
   const int64_t b0 = (int64_t)blockIdx.z * BG;
-  for (int64_t idx = threadIdx.x; idx < BG * R; idx += blockDim.x) {
-    int64_t bb = idx / R, i = idx - bb * R;
-    C2<T> v = mk<T>((T)0, (T)0);
-    if (b0 + bb < B) v = dhat[((b0 + bb) * nf + w) * R + i];
-    sd[idx] = v;
-  }
-  __syncthreads();
   const int64_t jbase = (int64_t)blockIdx.x * (256 * VPT) + threadIdx.x;
   T ar[BG][VPT], ai[BG][VPT];
 #pragma unroll
@@ -188,24 +187,38 @@ prod_adj_kernel(const C2<TS>* __restrict__ Fhat, const C2<T>* __restrict__ dhat,
 #pragma unroll
     for (int v = 0; v < VPT; ++v) { ar[bb][v] = (T)0; ai[bb][v] = (T)0; }
   const C2<TS>* base = Fhat + w * R * Nm;
-  for (int64_t i = 0; i < R; ++i) {
-    const C2<TS>* row = base + i * Nm;
-    C2<T> f[VPT];
-#pragma unroll
-    for (int v = 0; v < VPT; ++v) {
-      int64_t j = jbase + 256 * v;
-      f[v] = (j < Nm) ? ldF<T, TS>(row + j) : mk<T>((T)0, (T)0);
+  // d-hat rows are staged RS at a time; each thread still sums over i in order
+  const int64_t RS = R < kAdjRows ? R : kAdjRows;
+  for (int64_t i0 = 0; i0 < R; i0 += RS) {
+    const int64_t rn = R - i0 < RS ? R - i0 : RS;
+    if (i0 > 0) __syncthreads();  // the previous tile is consumed
+    for (int64_t idx = threadIdx.x; idx < BG * rn; idx += blockDim.x) {
+      int64_t bb = idx / rn, i = i0 + (idx - bb * rn);
+      C2<T> v = mk<T>((T)0, (T)0);
+      if (b0 + bb < B) v = dhat[((b0 + bb) * nf + w) * R + i];
+      sd[bb * RS + (i - i0)] = v;
     }
-#pragma unroll
-    for (int bb = 0; bb < BG; ++bb) {
-      C2<T> x = sd[bb * R + i];
+    __syncthreads();
+    for (int64_t ii = 0; ii < rn; ++ii) {
+      const int64_t i = i0 + ii;
+      const C2<TS>* row = base + i * Nm;
+      C2<T> f[VPT];
 #pragma unroll
       for (int v = 0; v < VPT; ++v) {
-        // conj(f) * x
-        ar[bb][v] = fma(f[v].x, x.x, ar[bb][v]);
-        ar[bb][v] = fma(f[v].y, x.y, ar[bb][v]);
-        ai[bb][v] = fma(f[v].x, x.y, ai[bb][v]);
-        ai[bb][v] = fma(-f[v].y, x.x, ai[bb][v]);
+        int64_t j = jbase + 256 * v;
+        f[v] = (j < Nm) ? ldF<T, TS>(row + j) : mk<T>((T)0, (T)0);
+      }
+#pragma unroll
+      for (int bb = 0; bb < BG; ++bb) {
+        C2<T> x = sd[bb * RS + ii];
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+          // conj(f) * x
+          ar[bb][v] = fma(f[v].x, x.x, ar[bb][v]);
+          ar[bb][v] = fma(f[v].y, x.y, ar[bb][v]);
+          ai[bb][v] = fma(f[v].x, x.y, ai[bb][v]);
+          ai[bb][v] = fma(-f[v].y, x.x, ai[bb][v]);
+        }
       }
     }
   }
@@ -223,7 +236,7 @@ prod_adj_kernel(const C2<TS>* __restrict__ Fhat, const C2<T>* __restrict__ dhat,
 template <typename T, typename TS, int BG, int VPT>
 static void adj_launch(const C2<TS>* Fhat, const C2<T>* dhat, C2<T>* mhat, int64_t nf, int64_t R, int64_t Nm,
                        int64_t B, cudaStream_t s) {
-  size_t smem = sizeof(C2<T>) * (size_t)BG * R;
+  size_t smem = sizeof(C2<T>) * (size_t)BG * (R < kAdjRows ? R : kAdjRows);
   dim3 grid((unsigned)((Nm + 256 * VPT - 1) / (256 * VPT)), (unsigned)nf, (unsigned)((B + BG - 1) / BG));
   prod_adj_kernel<T, TS, BG, VPT><<<grid, 256, smem, s>>>(Fhat, dhat, mhat, nf, R, Nm, B);
 }
@@ -419,8 +432,8 @@ void launch_prod_fwd_df64(const float4* Fhat, const double2* mhat, double2* part
   dim3 grid((unsigned)nchunk, (unsigned)nf, (unsigned)((B + bg - 1) / bg));
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(prod_fwd_df64_kernel<4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    cudaFuncSetAttribute(prod_fwd_df64_kernel<1, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    cudaFuncSetAttribute(prod_fwd_df64_kernel<4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmemMax);
+    cudaFuncSetAttribute(prod_fwd_df64_kernel<1, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmemMax);
     attr = true;
   }
   if (bg == 4)
@@ -435,20 +448,9 @@ __global__ void __launch_bounds__(256)
 prod_adj_df64_kernel(const float4* __restrict__ Fhat, const double2* __restrict__ dhat,
                      double2* __restrict__ mhat, int64_t nf, int64_t R, int64_t Nm, int64_t B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float4* sd = reinterpret_cast<float4*>(smem_raw);  // [BG][R] split d-hat
+  float4* sd = reinterpret_cast<float4*>(smem_raw);  // [BG][min(R, kAdjRows)] split d-hat
   const int64_t w = blockIdx.y;
   const int64_t b0 = (int64_t)blockIdx.z * BG;
-  for (int64_t idx = threadIdx.x; idx < BG * R; idx += blockDim.x) {
-    int64_t bb = idx / R, i = idx - bb * R;
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (b0 + bb < B) {
-      double2 x = dhat[((b0 + bb) * nf + w) * R + i];
-      ff re = split_d(x.x), im = split_d(x.y);
-      v = make_float4(re.h, re.l, im.h, im.l);
-    }
-    sd[idx] = v;
-  }
-  __syncthreads();
   const int64_t jbase = (int64_t)blockIdx.x * (256 * VPT) + threadIdx.x;
   float rh[BG][VPT], rl[BG][VPT], ih[BG][VPT], il[BG][VPT];
 #pragma unroll
@@ -456,24 +458,42 @@ prod_adj_df64_kernel(const float4* __restrict__ Fhat, const double2* __restrict_
 #pragma unroll
     for (int v = 0; v < VPT; ++v) rh[bb][v] = rl[bb][v] = ih[bb][v] = il[bb][v] = 0.f;
   const float4* base = Fhat + w * R * Nm;
-  for (int64_t i = 0; i < R; ++i) {
-    const float4* row = base + i * Nm;
-    float4 f[VPT];
-#pragma unroll
-    for (int v = 0; v < VPT; ++v) {
-      int64_t j = jbase + 256 * v;
-      f[v] = (j < Nm) ? __ldg(row + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+  // d-hat rows are staged RS at a time; each thread still sums over i in order
+  const int64_t RS = R < kAdjRows ? R : kAdjRows;
+  for (int64_t i0 = 0; i0 < R; i0 += RS) {
+    const int64_t rn = R - i0 < RS ? R - i0 : RS;
+    if (i0 > 0) __syncthreads();  // the previous tile is consumed
+    for (int64_t idx = threadIdx.x; idx < BG * rn; idx += blockDim.x) {
+      int64_t bb = idx / rn, i = i0 + (idx - bb * rn);
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (b0 + bb < B) {
+        double2 x = dhat[((b0 + bb) * nf + w) * R + i];
+        ff re = split_d(x.x), im = split_d(x.y);
+        v = make_float4(re.h, re.l, im.h, im.l);
+      }
+      sd[bb * RS + (i - i0)] = v;
     }
-#pragma unroll
-    for (int bb = 0; bb < BG; ++bb) {
-      float4 x = sd[bb * R + i];  // d = c + i e
+    __syncthreads();
+    for (int64_t ii = 0; ii < rn; ++ii) {
+      const int64_t i = i0 + ii;
+      const float4* row = base + i * Nm;
+      float4 f[VPT];
 #pragma unroll
       for (int v = 0; v < VPT; ++v) {
-        // conj(F) d = (a - i b)(c + i e) = (a c + b e) + i (a e - b c)
-        ff_mac(rh[bb][v], rl[bb][v], f[v].x, f[v].y, x.x, x.y);
-        ff_mac(rh[bb][v], rl[bb][v], f[v].z, f[v].w, x.z, x.w);
-        ff_mac(ih[bb][v], il[bb][v], f[v].x, f[v].y, x.z, x.w);
-        ff_mac(ih[bb][v], il[bb][v], -f[v].z, -f[v].w, x.x, x.y);
+        int64_t j = jbase + 256 * v;
+        f[v] = (j < Nm) ? __ldg(row + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int bb = 0; bb < BG; ++bb) {
+        float4 x = sd[bb * RS + ii];  // d = c + i e
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+          // conj(F) d = (a - i b)(c + i e) = (a c + b e) + i (a e - b c)
+          ff_mac(rh[bb][v], rl[bb][v], f[v].x, f[v].y, x.x, x.y);
+          ff_mac(rh[bb][v], rl[bb][v], f[v].z, f[v].w, x.z, x.w);
+          ff_mac(ih[bb][v], il[bb][v], f[v].x, f[v].y, x.z, x.w);
+          ff_mac(ih[bb][v], il[bb][v], -f[v].z, -f[v].w, x.x, x.y);
+        }
       }
     }
   }
@@ -492,7 +512,7 @@ prod_adj_df64_kernel(const float4* __restrict__ Fhat, const double2* __restrict_
 template <int BG, int VPT>
 static void adj_df64_launch(const float4* Fhat, const double2* dhat, double2* mhat, int64_t nf, int64_t R,
                             int64_t Nm, int64_t B, cudaStream_t s) {
-  size_t smem = sizeof(float4) * (size_t)BG * R;
+  size_t smem = sizeof(float4) * (size_t)BG * (R < kAdjRows ? R : kAdjRows);
   dim3 grid((unsigned)((Nm + 256 * VPT - 1) / (256 * VPT)), (unsigned)nf, (unsigned)((B + BG - 1) / BG));
   prod_adj_df64_kernel<BG, VPT><<<grid, 256, smem, s>>>(Fhat, dhat, mhat, nf, R, Nm, B);
 }
@@ -639,8 +659,8 @@ void launch_prod_fwd_f16(const void* Fhat, const float* scale, const float2* mha
   dim3 grid((unsigned)nchunk, (unsigned)nf, (unsigned)((B + bg - 1) / bg));
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(prod_fwd_f16_kernel<4, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    cudaFuncSetAttribute(prod_fwd_f16_kernel<1, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    cudaFuncSetAttribute(prod_fwd_f16_kernel<4, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmemMax);
+    cudaFuncSetAttribute(prod_fwd_f16_kernel<1, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmemMax);
     attr = true;
   }
   if (bg == 4)
@@ -658,21 +678,9 @@ prod_adj_f16_kernel(const __half2* __restrict__ Fhat, const float* __restrict__ 
                     const float2* __restrict__ dhat, float2* __restrict__ mhat, int64_t nf, int64_t R, int64_t Nm,
                     int64_t B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* sd = reinterpret_cast<float2*>(smem_raw);  // [BG][R]
+  float2* sd = reinterpret_cast<float2*>(smem_raw);  // [BG][min(R, kAdjRows)]
   const int64_t w = blockIdx.y;
   const int64_t b0 = (int64_t)blockIdx.z * BG;
-  for (int64_t idx = threadIdx.x; idx < BG * R; idx += blockDim.x) {
-    int64_t bb = idx / R, i = idx - bb * R;
-    float2 v = make_float2(0.f, 0.f);
-    if (b0 + bb < B) {
-      v = dhat[((b0 + bb) * nf + w) * R + i];
-      float sc = scale[w * R + i];
-      v.x *= sc;
-      v.y *= sc;
-    }
-    sd[idx] = v;
-  }
-  __syncthreads();
   const int64_t jbase = (int64_t)blockIdx.x * (256 * VPT) + threadIdx.x;
   float ar[BG][VPT], ai[BG][VPT];
 #pragma unroll
@@ -681,23 +689,42 @@ prod_adj_f16_kernel(const __half2* __restrict__ Fhat, const float* __restrict__ 
     for (int v = 0; v < VPT; ++v) ar[bb][v] = ai[bb][v] = 0.f;
   const __half2* base = Fhat + w * R * Nm;
   const __half2 hz = __floats2half2_rn(0.f, 0.f);
-  for (int64_t i = 0; i < R; ++i) {
-    const __half2* row = base + i * Nm;
-    float2 f[VPT];
-#pragma unroll
-    for (int v = 0; v < VPT; ++v) {
-      int64_t j = jbase + 256 * v;
-      f[v] = __half22float2((j < Nm) ? __ldg(row + j) : hz);
+  // d-hat rows are staged RS at a time; each thread still sums over i in order
+  const int64_t RS = R < kAdjRows ? R : kAdjRows;
+  for (int64_t i0 = 0; i0 < R; i0 += RS) {
+    const int64_t rn = R - i0 < RS ? R - i0 : RS;
+    if (i0 > 0) __syncthreads();  // the previous tile is consumed
+    for (int64_t idx = threadIdx.x; idx < BG * rn; idx += blockDim.x) {
+      int64_t bb = idx / rn, i = i0 + (idx - bb * rn);
+      float2 v = make_float2(0.f, 0.f);
+      if (b0 + bb < B) {
+        v = dhat[((b0 + bb) * nf + w) * R + i];
+        float sc = scale[w * R + i];
+        v.x *= sc;
+        v.y *= sc;
+      }
+      sd[bb * RS + (i - i0)] = v;
     }
-#pragma unroll
-    for (int bb = 0; bb < BG; ++bb) {
-      float2 x = sd[bb * R + i];
+    __syncthreads();
+    for (int64_t ii = 0; ii < rn; ++ii) {
+      const int64_t i = i0 + ii;
+      const __half2* row = base + i * Nm;
+      float2 f[VPT];
 #pragma unroll
       for (int v = 0; v < VPT; ++v) {
-        ar[bb][v] = fmaf(f[v].x, x.x, ar[bb][v]);
-        ar[bb][v] = fmaf(f[v].y, x.y, ar[bb][v]);
-        ai[bb][v] = fmaf(f[v].x, x.y, ai[bb][v]);
-        ai[bb][v] = fmaf(-f[v].y, x.x, ai[bb][v]);
+        int64_t j = jbase + 256 * v;
+        f[v] = __half22float2((j < Nm) ? __ldg(row + j) : hz);
+      }
+#pragma unroll
+      for (int bb = 0; bb < BG; ++bb) {
+        float2 x = sd[bb * RS + ii];
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+          ar[bb][v] = fmaf(f[v].x, x.x, ar[bb][v]);
+          ar[bb][v] = fmaf(f[v].y, x.y, ar[bb][v]);
+          ai[bb][v] = fmaf(f[v].x, x.y, ai[bb][v]);
+          ai[bb][v] = fmaf(-f[v].y, x.x, ai[bb][v]);
+        }
       }
     }
   }
@@ -715,7 +742,7 @@ prod_adj_f16_kernel(const __half2* __restrict__ Fhat, const float* __restrict__ 
 template <int BG, int VPT>
 static void adj_f16_launch(const void* Fhat, const float* scale, const float2* dhat, float2* mhat, int64_t nf,
                            int64_t R, int64_t Nm, int64_t B, cudaStream_t s) {
-  size_t smem = sizeof(float2) * (size_t)BG * R;
+  size_t smem = sizeof(float2) * (size_t)BG * (R < kAdjRows ? R : kAdjRows);
   dim3 grid((unsigned)((Nm + 256 * VPT - 1) / (256 * VPT)), (unsigned)nf, (unsigned)((B + BG - 1) / BG));
   prod_adj_f16_kernel<BG, VPT><<<grid, 256, smem, s>>>((const __half2*)Fhat, scale, dhat, mhat, nf, R, Nm, B);
 }

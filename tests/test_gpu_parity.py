@@ -59,6 +59,7 @@ CASES = [
     ("L840_odd", 333, 7, 2, 420, 1),
     ("Nt1_gemv", 257, 5, 3, 1, 2),
     ("scalar", 1, 1, 1, 16, 2),
+    ("R1100_row_tiles", 600, 1100, 3, 20, 5),  # adjoint stages d-hat in 512-row tiles
 ]
 
 
@@ -101,6 +102,30 @@ def test_mixed_io_types(store, io):
     d = torch.empty((2, 32, 9), dtype=io, device="cuda")
     h.apply_F(m_g, d)
     assert relb(host(d), oracle.p2o_apply(F, host(m_g))) < 1e-5
+
+
+@pytest.mark.parametrize("store", [bti.F64, bti.F32, bti.DF64, bti.F16], ids=["f64", "f32", "df64", "f16"])
+def test_tuned_launch_shapes_serve_every_batch_size(store):
+    """Shapes tuned for single vectors (a forward chunk of up to 4,096 columns) and for
+    groups of four are kept apart: after tuning at B = 1 and at B = 8, calls with 1, 5
+    and 16 right-hand sides all launch and match the oracle."""
+    p = synthetic.small("tuned_batches", 1, 5000, 16, 32)
+    F = p.blocks_F()
+    h = make_handle(F, None, store)
+    dt = torch.float32 if store in (bti.F32, bti.F16) else torch.float64
+    h.autotune(bti.OP_F, 1)
+    for B in (1, 5, 16):
+        if B == 5:
+            h.autotune(bti.OP_F, 8)
+        m_g = cuda(p.vectors_m(B), dt)
+        d_g = cuda(p.vectors_d(B), dt)
+        od = torch.empty((B, 32, 16), dtype=dt, device="cuda")
+        om = torch.empty((B, 32, 5000), dtype=dt, device="cuda")
+        h.apply_F(m_g, od)
+        h.apply_FT(d_g, om)
+        assert relb(host(od), oracle.p2o_apply(F, host(m_g))) < TOL[store], B
+        assert relb(host(om), oracle.p2o_apply_adjoint(F, host(d_g))) < TOL[store], B
+    h.close()
 
 
 def test_impulse_response_and_causality():
@@ -476,4 +501,96 @@ def test_d2q_map_and_qoi_covariance(dense):
     h.apply_Q(d, q)
     q_or = oracle.qoi_map(Fq, oracle.map_point(F, G, p.sigma2, host(d)))
     assert relb(host(q), q_or) < tol
+    h.close()
+
+
+def test_posterior_covariance_actions_and_prior_mean():
+    """Gamma_prior v, Gamma_post(m) v (Eq. (4.7)), pointwise posterior variances from unit
+    vectors, and m_map with a nonzero prior mean (Eq. (4.13) with Eq. (4.8))."""
+    p, F, Fq, G, d_obs = tiny_problem()
+    Cs = oracle.se_covariance(p.gx, p.gy, p.ell, p.sigma_p)
+    h = make_handle(F, Fq, bti.DF64)
+    h.set_prior_se_grid(p.gx, p.gy, p.ell, p.sigma_p, bti.DF64)
+    h.set_noise(p.sigma2)
+    h.build_K()
+    h.factor_K()
+    v = p.vectors_m(3)
+    out = torch.empty((3, p.Nt, p.Nm), dtype=torch.float64, device="cuda")
+    h.apply_prior(cuda(v), out)
+    assert relb(host(out), oracle.prior_apply(Cs, v)) < 1e-13
+    h.apply_postcov(cuda(v), out)
+    assert relb(host(out), oracle.posterior_cov_apply(F, G, Cs, p.sigma2, v)) < 1e-11
+    # two pointwise variances: e^T Gamma_post(m) e for unit vectors e
+    E = np.zeros((2, p.Nt, p.Nm))
+    E[0, 5, 17] = 1.0
+    E[1, 60, 200] = 1.0
+    col = torch.empty((2, p.Nt, p.Nm), dtype=torch.float64, device="cuda")
+    h.apply_postcov(cuda(E), col)
+    col = host(col)
+    ref = oracle.posterior_cov_apply(F, G, Cs, p.sigma2, E)
+    for b, (t, j) in enumerate(((5, 17), (60, 200))):
+        var = col[b, t, j]
+        assert abs(var - ref[b, t, j]) <= 1e-11 * abs(ref[b, t, j])
+        assert 0.0 < var <= p.sigma_p ** 2  # the data can only reduce the prior variance
+    m0 = 0.3 * p.vectors_m(1)
+    mm = torch.empty((1, p.Nt, p.Nm), dtype=torch.float64, device="cuda")
+    h.infer_map_prior(cuda(d_obs), cuda(m0), mm)
+    assert relb(host(mm), oracle.map_point_with_prior_mean(F, G, p.sigma2, d_obs, m0)) < 1e-12
+    h.close()
+
+
+@pytest.mark.parametrize("stride", [4, 16])
+def test_coarse_qoi_grid(stride):
+    """QoIs on every stride-th time step (the Remark after Eq. (2.15); the Sec. 5 example
+    reads them at 1 Hz from a 10 Hz grid): F_q m, predict_qoi, the online graph, Q,
+    Gamma_post(q) and Q d_obs on the coarse grid against the oracle's selected rows."""
+    p, F, Fq, G, d_obs = tiny_problem()
+    steps = oracle.qoi_time_steps(p.Nt, stride)
+    rows = oracle.qoi_rows(p.Nt, p.Nq, stride)
+    Ntq = p.Nt // stride
+    h = make_handle(F, Fq, bti.DF64)
+    h.set_prior_se_grid(p.gx, p.gy, p.ell, p.sigma_p, bti.DF64)
+    h.set_noise(p.sigma2)
+    h.build_K()
+    h.factor_K()
+    h.set_qoi_stride(stride)
+    m = p.vectors_m(2)
+    q = torch.empty((2, Ntq, p.Nq), dtype=torch.float64, device="cuda")
+    h.apply_Fq(cuda(m), q)
+    assert relb(host(q), oracle.qoi_map(Fq, m)[:, steps]) < 1e-12
+    m_or = oracle.map_point(F, G, p.sigma2, d_obs)
+    q_or = oracle.qoi_map(Fq, m_or)[:, steps]
+    mm = torch.empty((1, p.Nt, p.Nm), dtype=torch.float64, device="cuda")
+    q1 = torch.empty((1, Ntq, p.Nq), dtype=torch.float64, device="cuda")
+    h.infer_map(cuda(d_obs), mm)
+    h.predict_qoi(mm, q1)
+    assert relb(host(q1), q_or) < 1e-11
+    stream = torch.cuda.Stream()  # graph capture needs a non-default stream
+    with torch.cuda.stream(stream):
+        h.set_stream(stream)
+        q1.zero_()
+        h.online(cuda(d_obs), mm, q1)
+        assert relb(host(q1), q_or) < 1e-11
+    torch.cuda.synchronize()
+    h.set_stream(torch.cuda.current_stream())
+    h.build_Q(with_covariance=True)
+    Q, C = h.copy_Q(covariance=True)
+    assert tuple(Q.shape) == (Ntq * p.Nq, p.Nt * p.Nd) and tuple(C.shape) == (Ntq * p.Nq,) * 2
+    Cs = oracle.se_covariance(p.gx, p.gy, p.ell, p.sigma_p)
+    Q_or = oracle.d2q_map(Fq, F, G, p.sigma2)[rows]
+    C_or = oracle.qoi_posterior_covariance(Fq, oracle.prior_blocks(Fq, Cs), F, G, p.sigma2)[np.ix_(rows, rows)]
+    assert np.linalg.norm(host(Q) - Q_or) / np.linalg.norm(Q_or) < 1e-11
+    assert np.linalg.norm(host(C) - C_or) / np.linalg.norm(C_or) < 1e-10
+    q1.zero_()
+    h.apply_Q(cuda(d_obs), q1)
+    assert relb(host(q1), q_or) < 1e-11
+    # back to the full grid: Q must be rebuilt, and F_q writes every step again
+    h.set_qoi_stride(1)
+    with pytest.raises(bti.BtiError):
+        h.apply_Q(cuda(d_obs), torch.empty((1, p.Nt, p.Nq), dtype=torch.float64, device="cuda"))
+    qf = torch.empty((2, p.Nt, p.Nq), dtype=torch.float64, device="cuda")
+    h.apply_Fq(cuda(m), qf)
+    assert relb(host(qf), oracle.qoi_map(Fq, m)) < 1e-12
+    with pytest.raises(bti.BtiError):
+        h.set_qoi_stride(3)  # does not divide N_t = 64
     h.close()
