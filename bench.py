@@ -42,15 +42,16 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-online", action="store_true", help="skip the batched online-latency block")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-workload matrix-free solve block")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--case", choices=["sweep", "small"], default="sweep",
                     help="small: the sweep shape with N_m = 4096 and 2 vectors (2.2 GB of FP64 spectral "
                          "blocks, still far above L2) for ncu captures; implies --no-online, "
-                         "--no-cpu-baseline and --no-e2e")
+                         "--no-mixed, --no-cpu-baseline and --no-e2e")
     a = ap.parse_args()
     if a.case == "small":
-        a.no_online = a.no_cpu_baseline = a.no_e2e = True
+        a.no_online = a.no_mixed = a.no_cpu_baseline = a.no_e2e = True
     return a
 
 
@@ -444,8 +445,11 @@ def run_ours(args):
     bpc64 = bytes_per_call(p, 8, 16)
 
     # online m_map + q_map latency on the batched workload (64 observation vectors)
-    if not args.no_online:
+    # single-GPU sidecar measurements (skipped when ranks run replicas)
+    if not args.no_online and world == 1:
         line["online"] = online_block(args, dev, stream)
+    if not args.no_mixed and world == 1:
+        line["mixed"] = mixed_block(args, dev, stream)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         pairs, dt = cpu_oracle_sample(p, F_host, m_host, d_host)
@@ -591,6 +595,65 @@ def online_block(args, dev, stream):
     h.close()
     out["accuracy"] = ("every form reaches FP64-level m_map and q_map: tests/test_gpu_parity.py (tiny, 1e-12) "
                        "and tests/test_gpu_fullsize.py (batched full size, 1e-11) against the oracle")
+    return out
+
+
+def mixed_block(args, dev, stream):
+    """m_map on the mixed-precision workload (N_m = 16,384, N_d = 600, N_t = 420, L = 840),
+    where K would be 252,000^2 (508 GB in FP64) and is never formed.  Plain FP64 conjugate
+    gradients (double-FP32 spectral operators, SE prior applied in FP64) against flexible
+    FP64 CG preconditioned by FP32 CG on FP16 spectral blocks of F and G, both to the same
+    relative residual with the FP64-accurate operator: 1e-6 (the online latency target)
+    and 1e-11 (FP64-level for this K: the double-FP32 operator's rounding floor is about
+    5e-12 at kappa(K) ~ 2e4)."""
+    import torch
+
+    import paper_2501_14911_gb300 as bti
+    from paper_2501_14911_gb300 import synthetic
+
+    p = synthetic.MIXED
+    h = bti.Handle(p.Nm, p.Nd, 0, p.Nt, device=dev)
+    gs = torch.cuda.Stream(dev)
+    h.set_stream(gs)
+    out = {"workload": p.name, "K_n": p.Nt * p.Nd, "K_fp64_GB": (p.Nt * p.Nd) ** 2 * 8 / 1e9,
+           "data": "d = F m + sigma noise for a seeded N(0,1) m, through the library's F"}
+    with torch.cuda.stream(gs):
+        Fd = torch.from_numpy(p.blocks_F()).to(dev)
+        h.set_blocks(bti.OP_F, Fd, bti.DF64)
+        torch.cuda.synchronize()
+        del Fd
+        torch.cuda.empty_cache()
+        h.set_noise(p.sigma2)
+        d_obs = torch.empty((1, p.Nt, p.Nd), dtype=torch.float64, device=dev)
+        h.apply_F(torch.from_numpy(p.vectors_m(1)).to(dev), d_obs)
+        d_obs += p.sigma2 ** 0.5 * torch.from_numpy(p.noise(1)).to(dev)
+        m_map = torch.empty((1, p.Nt, p.Nm), dtype=torch.float64, device=dev)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        h.set_prior_se_grid(p.gx, p.gy, p.ell, p.sigma_p, bti.F16)
+        h.set_shadow(bti.OP_F, bti.F16)
+        forms = (("plain_f64_cg", dict(refine=0, max_inner=6000)),
+                 ("flexible_cg_f16_inner", dict(refine=2, max_outer=400, max_inner=2000, inner_tol=0.1)))
+        for name, kw in forms:
+            rec = {}
+            for tol in (1e-6, 1e-11):
+                torch.cuda.synchronize()
+                e[0].record(gs)
+                try:
+                    info = h.solve_matfree(d_obs, m_map, tol=tol, **kw)
+                except bti.BtiError as ex:  # reported, not fatal: the line says it did not converge
+                    info = dict(h.last_solve, error=str(ex))
+                e[1].record(gs)
+                torch.cuda.synchronize()
+                rec[f"tol_{tol:.0e}"] = dict(info, ms=e[0].elapsed_time(e[1]))
+            out[name] = dict(rec, **{k: v for k, v in kw.items() if k != "refine"})
+    h.set_stream(stream)
+    h.close()
+    torch.cuda.empty_cache()
+    for tol in ("1e-06", "1e-11"):
+        out[f"speedup_at_{tol}"] = (out["plain_f64_cg"][f"tol_{tol}"]["ms"]
+                                    / out["flexible_cg_f16_inner"][f"tol_{tol}"]["ms"])
+    out["accuracy"] = ("both forms stop at ||d - K x|| <= tol ||d|| with K applied by the FP64-accurate "
+                       "operator; tests/test_gpu_fullsize.py re-checks the residual with the oracle")
     return out
 
 

@@ -51,7 +51,8 @@ typedef enum {
   BTI_ERR_CUDA = 4,     /* a CUDA runtime call failed */
   BTI_ERR_OOM = 5,      /* device allocation failed */
   BTI_ERR_NOT_SPD = 6,  /* Cholesky met a non-positive or non-finite pivot */
-  BTI_ERR_TIMEOUT = 7   /* reserved: a bounded device wait gave up */
+  BTI_ERR_TIMEOUT = 7,  /* reserved: a bounded device wait gave up */
+  BTI_ERR_NO_CONVERGENCE = 8  /* an iterative solve missed its tolerance within its iteration limit */
 } bti_status;
 
 /* Which block-Toeplitz operator a call refers to.
@@ -219,6 +220,55 @@ bti_status bti_apply_postcov(bti_handle h, const double* v, double* out, int64_t
  * m_map not aliased).  refine_iters as bti_infer_map.  Synchronises. */
 bti_status bti_infer_map_prior(bti_handle h, const double* d_obs, const double* m_prior, double* m_map, int64_t B,
                                int refine_iters);
+
+/* ---------------------------------------------------------------- matrix-free solve
+ * When K = Gamma_noise + F G^* is too large to form (N_d N_t = 252,000 makes it
+ * 508 GB in FP64), K x = d_obs is solved by conjugate gradients with K applied as
+ * Gamma_noise x + F (G^* x) through the spectral operators, and m_map = G^* x
+ * (Eq. (4.13) with the simplification m_map = G^* K^{-1} d_obs, Sec. 4).  K is
+ * symmetric positive definite (Gamma_noise > 0), so CG applies. */
+
+/* A second, lower-tier copy of the spectral blocks of F or G (from the FP64
+ * time-domain blocks kept by set_blocks / set_prior_se_grid), used by the inner
+ * iteration of bti_solve_matfree with refine = 1.  store: any tier (BTI_P_F16 or
+ * BTI_P_F32 in practice).  A later set_blocks of F or set_prior_se_grid drops the
+ * copy.  Synchronises. */
+bti_status bti_set_shadow(bti_handle h, bti_op op, bti_prec store);
+
+typedef struct {
+  int outer_iters;     /* refinement steps or flexible-CG iterations (0 for refine = 0) */
+  int inner_iters;     /* conjugate-gradient iterations in total */
+  double rel_residual; /* max over the batch of ||d - K x|| / ||d|| with the FP64-accurate operators */
+} bti_solve_info;
+
+/* m_map = G^* K^{-1} d_obs for B observation vectors without forming K.
+ * d_obs [B][N_t][N_d] -> m_map [B][N_t][N_m] (device doubles); x_out (device, may be
+ * NULL) receives x = K^{-1} d_obs [B][N_t][N_d].
+ * The FP64-accurate operator is K x = Gamma_noise x + F (G^* x) with F stored in
+ * BTI_P_F64 or BTI_P_DF64 and G^* from the G store when that is also FP64-accurate,
+ * else Gamma_prior F^T with the SE prior applied separably in FP64.
+ *   refine = 0: conjugate gradients in FP64 with that operator until
+ *     ||d - K x|| <= tol ||d|| for every vector (at most max_inner iterations).
+ * For refine = 0 and 2 the returned residual is recomputed from x, not the recursive one.
+ *   refine = 1: FP64 iterative refinement (at most max_outer steps): the residual
+ *     r = d - K x with the FP64-accurate operator, then K~ delta = r / ||r|| by FP32
+ *     conjugate gradients with the inner operator K~ (the shadow copies of F and G
+ *     where set, else their stores) until the inner residual drops by inner_tol (or
+ *     max_inner iterations), and x += ||r|| delta.  Each step gains about
+ *     -log10(kappa(K) ||K - K~|| / ||K|| + inner_tol) digits.
+ *   refine = 2: the same inner solve as the preconditioner of flexible conjugate
+ *     gradients in FP64 with the FP64-accurate operator (at most max_outer outer
+ *     iterations; beta in the Polak-Ribiere form, which tolerates the inner solve's
+ *     variation).  The Krylov outer iteration keeps converging where plain
+ *     refinement stalls on kappa(K) ||K - K~|| / ||K||, so a loose inner_tol
+ *     (0.1 - 0.3) suffices.
+ * Requires F, the SE prior (set_prior_se_grid, which also sets G) and set_noise.
+ * Returns BTI_ERR_NO_CONVERGENCE (m_map and x_out still written from the last
+ * iterate) when the tolerance is not reached; info (may be NULL) is filled in every
+ * case.  Synchronises. */
+bti_status bti_solve_matfree(bti_handle h, const double* d_obs, double* m_map, double* x_out, int64_t B,
+                             int refine, double tol, int max_outer, int max_inner, double inner_tol,
+                             bti_solve_info* info);
 
 /* Elliptic prior operator of Eq. (5.1), per time block: out = A_s m with
  * A_s = alpha1 I - alpha2 Delta_h on the gx x gy grid (gx * gy = N_m, node

@@ -17,8 +17,17 @@ F64, F32, DF64, F16 = 0, 1, 2, 3
 
 STATUS = {
     0: "BTI_OK", 1: "BTI_ERR_ARG", 2: "BTI_ERR_SHAPE", 3: "BTI_ERR_STATE", 4: "BTI_ERR_CUDA",
-    5: "BTI_ERR_OOM", 6: "BTI_ERR_NOT_SPD", 7: "BTI_ERR_TIMEOUT",
+    5: "BTI_ERR_OOM", 6: "BTI_ERR_NOT_SPD", 7: "BTI_ERR_TIMEOUT", 8: "BTI_ERR_NO_CONVERGENCE",
 }
+
+
+class SolveInfo(ctypes.Structure):
+    """bti_solve_info: refinement steps, CG iterations, final relative residual."""
+
+    _fields_ = [("outer_iters", ctypes.c_int), ("inner_iters", ctypes.c_int), ("rel_residual", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"outer_iters": self.outer_iters, "inner_iters": self.inner_iters, "rel_residual": self.rel_residual}
 
 _lib = None
 
@@ -76,6 +85,8 @@ def lib():
         "bti_set_qoi_stride": ([vp, ip], st),
         "bti_apply_postcov": ([vp, vp, vp, i64], st),
         "bti_infer_map_prior": ([vp, vp, vp, vp, i64, ip], st),
+        "bti_set_shadow": ([vp, ip, ip], st),
+        "bti_solve_matfree": ([vp, vp, vp, vp, i64, ip, dp, ip, ip, dp, ctypes.POINTER(SolveInfo)], st),
         "bti_apply_Q": ([vp, vp, vp, i64], st),
         "bti_copy_Q": ([vp, vp, vp], st),
         "bti_apply_elliptic": ([vp, ip, ip, dp, dp, vp, vp, i64, ip], st),
@@ -277,6 +288,34 @@ class Handle:
             raise ValueError("batch sizes differ")
         self._check(fn(self._h, _ptr(v), _ptr(out), B))
         return out
+
+    def set_shadow(self, op, store):
+        """A lower-tier copy of F's or G's spectral blocks for the inner solve."""
+        self._check(lib().bti_set_shadow(self._h, int(op), int(store)))
+
+    def solve_matfree(self, d_obs, m_map, x=None, refine=1, tol=1e-12, max_outer=20, max_inner=500,
+                      inner_tol=1e-3):
+        """m_map = G^* K^{-1} d_obs by conjugate gradients without forming K: FP64 CG
+        (refine=0), FP64 iterative refinement around FP32 CG with the shadow operators
+        (refine=1), or that inner solve preconditioning flexible FP64 CG (refine=2).
+        Returns the solve statistics as a dict; raises BtiError (status
+        BTI_ERR_NO_CONVERGENCE) when tol is not reached."""
+        self._tensor(d_obs, (self.Nt, self.Nd), "d_obs")
+        self._tensor(m_map, (self.Nt, self.Nm), "m_map")
+        B = self._batch(d_obs, 2)
+        if self._batch(m_map, 2) != B:
+            raise ValueError("d_obs and m_map batch sizes differ")
+        if x is not None:
+            self._tensor(x, (self.Nt, self.Nd), "x")
+            if self._batch(x, 2) != B:
+                raise ValueError("d_obs and x batch sizes differ")
+        info = SolveInfo()
+        st = lib().bti_solve_matfree(self._h, _ptr(d_obs), _ptr(m_map), _ptr(x) if x is not None else None, B,
+                                     int(refine), float(tol), int(max_outer), int(max_inner),
+                                     float(inner_tol), ctypes.byref(info))
+        self.last_solve = info.as_dict()
+        self._check(st)
+        return self.last_solve
 
     def infer_map_prior(self, d_obs, m_prior, m_map, refine_iters=0):
         """m_map with a nonzero prior mean (Eq. (4.13) with Eq. (4.8))."""

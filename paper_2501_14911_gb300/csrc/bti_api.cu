@@ -42,6 +42,7 @@ struct bti_ctx {
   int64_t Nm = 0, Nd = 0, Nq = 0, Nt = 0, L = 0, nf = 0;
   FftPlan plan;
   OpStore op[3];
+  OpStore shadow[3];  // lower-tier copies for the inner iteration of bti_solve_matfree
   Tune tune[4];  // indexed by bti_prec
   bti_prec dense_prec = BTI_P_F64;  // arithmetic of K assembly, Cholesky and solves
   bool noise_set = false;
@@ -50,6 +51,7 @@ struct bti_ctx {
   bool prior_set = false;        // SE prior of bti_set_prior_se_grid (also applied to F_q)
   int prior_gx = 0, prior_gy = 0;
   double prior_ell = 0.0, prior_sigma = 0.0;
+  double* prior_axes = nullptr;  // C_x [gx][gx] then C_y [gy][gy]
   double* Q = nullptr;           // [N_q N_t][N_d N_t] d2q map
   double* covq = nullptr;        // [N_q N_t][N_q N_t] posterior covariance of the QoI
   bool Q_built = false, covq_built = false;
@@ -174,15 +176,22 @@ bti_status check_handle(bti_ctx* h) {
 bti_status make_spectral(bti_ctx* h, OpStore& o, const double* time_blocks) {
   const int64_t cols = o.R * h->Nm;
   if (o.prec == BTI_P_F16) {
-    // FP64 spectrum in a temporary, then per-row scaled FP16
+    // FP64 spectrum of a few rows at a time in a temporary (at most ~2 GB), then per-row
+    // scaled FP16
+    const int64_t row_bytes = h->nf * h->Nm * (int64_t)sizeof(double2);
+    int64_t ri = ((int64_t)2 << 30) / row_bytes;
+    ri = ri < 1 ? 1 : (ri > o.R ? o.R : ri);
     double2* tmp = nullptr;
-    bti_status st = dev_alloc(h, (void**)&tmp, sizeof(double2) * (size_t)h->nf * cols, "spectral temporary");
+    bti_status st = dev_alloc(h, (void**)&tmp, (size_t)(ri * row_bytes), "spectral temporary");
     if (st != BTI_OK) return st;
     st = dev_alloc(h, (void**)&o.scale, sizeof(float) * (size_t)h->nf * o.R, "row scales");
     if (st != BTI_OK) { dev_freep(tmp); return st; }
-    PROF(h, BTI_K_RFFT, (launch_rfft_cols<double, double, double>(h->plan, (int)h->Nt, time_blocks, cols, 0, tmp, 0,
-                                                                   cols, 1, h->stream)));
-    PROF(h, BTI_K_RFFT, launch_quantize_f16(tmp, o.hat, o.scale, h->nf * o.R, h->Nm, h->stream));
+    for (int64_t i0 = 0; i0 < o.R; i0 += ri) {
+      const int64_t rn = o.R - i0 < ri ? o.R - i0 : ri;
+      PROF(h, BTI_K_RFFT, (launch_rfft_cols<double, double, double>(h->plan, (int)h->Nt, time_blocks + i0 * h->Nm,
+                                                                     cols, 0, tmp, 0, rn * h->Nm, 1, h->stream)));
+      PROF(h, BTI_K_RFFT, launch_quantize_f16(tmp, o.hat, o.scale, h->nf, rn, o.R, i0, h->Nm, h->stream));
+    }
     cudaStreamSynchronize(h->stream);
     dev_freep(tmp);
     return launched(h, "spectral blocks");
@@ -198,6 +207,14 @@ bti_status make_spectral(bti_ctx* h, OpStore& o, const double* time_blocks) {
   return launched(h, "spectral blocks");
 }
 
+void drop_store(OpStore& o) {
+  dev_free(o.hat);
+  dev_freep(o.time);
+  dev_freep(o.scale);
+  o.hat = nullptr;
+  o.set = false;
+}
+
 void drop_online_graph_any(bti_ctx* h) {
   if (h->online_exec) cudaGraphExecDestroy(h->online_exec);
   h->online_exec = nullptr;
@@ -209,6 +226,7 @@ bti_status store_op(bti_ctx* h, bti_op opi, const double* blocks, bti_prec store
   OpStore& o = h->op[opi];
   const int64_t R = rows_of(h, opi);
   if (R <= 0) return fail(h, BTI_ERR_SHAPE, "operator has zero rows (N_q = 0?)");
+  drop_store(h->shadow[opi]);  // a shadow copy describes the blocks being replaced
   dev_free(o.hat);
   dev_freep(o.time);
   dev_freep(o.scale);
@@ -351,6 +369,14 @@ bti_status apply_adj_t(bti_ctx* h, const OpStore& o, const void* in, void* out, 
   return launched(h, "adjoint Toeplitz product");
 }
 
+// out = op(in) with an explicit store (an operator or its shadow copy); no argument checks
+bti_status apply_store(bti_ctx* h, const OpStore& o, bool adjoint, const void* in, void* out, int64_t B,
+                       bti_prec io) {
+  if (double_path(o.prec))  // FP64 and double-FP32 tiers: FFT spectra in FP64
+    return adjoint ? apply_adj_t<double>(h, o, in, out, B, io) : apply_fwd_t<double>(h, o, in, out, B, io);
+  return adjoint ? apply_adj_t<float>(h, o, in, out, B, io) : apply_fwd_t<float>(h, o, in, out, B, io);
+}
+
 bti_status apply_op(bti_ctx* h, bti_op opi, bool adjoint, const void* in, void* out, int64_t B,
                     bti_prec io, const char* name) {
   bti_status st = check_handle(h);
@@ -361,9 +387,22 @@ bti_status apply_op(bti_ctx* h, bti_op opi, bool adjoint, const void* in, void* 
   if (!o.set) return fail(h, BTI_ERR_STATE, std::string(name) + ": operator blocks not set");
   if (B == 0) return BTI_OK;
   if (!in || !out) return fail(h, BTI_ERR_ARG, std::string(name) + ": null pointer");
-  if (double_path(o.prec))  // FP64 and double-FP32 tiers: FFT spectra in FP64
-    return adjoint ? apply_adj_t<double>(h, o, in, out, B, io) : apply_fwd_t<double>(h, o, in, out, B, io);
-  return adjoint ? apply_adj_t<float>(h, o, in, out, B, io) : apply_fwd_t<float>(h, o, in, out, B, io);
+  return apply_store(h, o, adjoint, in, out, B, io);
+}
+
+// out = in C_s for `rows` grid-shaped rows (row r viewed as X_r [gx][gy]: C_x X_r C_y)
+// with the SE prior's axis matrices: Gamma_prior = I_t (x) C_s applied block by block.
+// U is a caller-provided temporary of rows * N_m doubles.  Stream-ordered, no sync.
+bti_status se_rows_into(bti_ctx* h, const double* in, double* out, int64_t rows, double* U) {
+  const int gx = h->prior_gx, gy = h->prior_gy;
+  const double* Cx = h->prior_axes;
+  const double* Cy = Cx + (size_t)gx * gx;
+  cudaStream_t s = h->stream;
+  int64_t nl = gemm_f64(false, rows * gx, gy, gy, 1.0, in, gy, 0, Cy, gy, 0, 0.0, U, gy, 0, 1, false, s);
+  nl += gemm_f64(false, gx, gy, gx, 1.0, Cx, gx, 0, U, gy, (int64_t)gx * gy, 0.0, out, gy, (int64_t)gx * gy, rows,
+                 false, s);
+  count_dense(h, nl);
+  return launched(h, "SE prior");
 }
 
 }  // namespace
@@ -449,11 +488,13 @@ bti_status bti_destroy(bti_handle h) {
   if (!h) return BTI_ERR_ARG;
   cudaSetDevice(h->device);
   cudaStreamSynchronize(h->stream);
-  for (auto& o : h->op) {
-    dev_free(o.hat);
-    dev_freep(o.time);
-    dev_freep(o.scale);
-  }
+  for (auto* set : {h->op, h->shadow})
+    for (int i = 0; i < 3; ++i) {
+      dev_free(set[i].hat);
+      dev_freep(set[i].time);
+      dev_freep(set[i].scale);
+    }
+  dev_freep(h->prior_axes);
   dev_freep(h->noise_diag);
   dev_freep(h->K);
   dev_freep(h->Q);
@@ -532,17 +573,23 @@ bti_status bti_set_prior_se_grid(bti_handle h, int gx, int gy, double ell, doubl
   OpStore& F = h->op[BTI_OP_F];
   if (!F.set || !F.time) return fail(h, BTI_ERR_STATE, "set_prior_se_grid: F blocks not set");
   const int64_t rows = h->Nt * h->Nd;
-  double* Cx = nullptr;
-  double* Cy = nullptr;
   double* U = nullptr;
   double* G = nullptr;
-  st = dev_alloc(h, (void**)&Cx, sizeof(double) * ((size_t)gx * gx + (size_t)gy * gy), "alloc prior axes");
+  drop_online_graph_any(h);
+  dev_freep(h->prior_axes);
+  h->prior_set = false;
+  // the previous G (and its shadow copy) goes first, so the peak holds one set of G blocks
+  drop_store(h->op[BTI_OP_G]);
+  drop_store(h->shadow[BTI_OP_G]);
+  h->K_built = h->K_factored = false;
+  h->Q_built = h->covq_built = false;
+  st = dev_alloc(h, (void**)&h->prior_axes, sizeof(double) * ((size_t)gx * gx + (size_t)gy * gy),
+                 "alloc prior axes");
   if (st != BTI_OK) return st;
-  Cy = Cx + (size_t)gx * gx;
   st = dev_alloc(h, (void**)&U, sizeof(double) * (size_t)rows * h->Nm, "alloc prior temp");
-  if (st != BTI_OK) { dev_freep(Cx); return st; }
+  if (st != BTI_OK) return st;
   st = dev_alloc(h, (void**)&G, sizeof(double) * (size_t)rows * h->Nm, "alloc G blocks");
-  if (st != BTI_OK) { dev_freep(Cx); dev_freep(U); return st; }
+  if (st != BTI_OK) { dev_freep(U); return st; }
   cudaStream_t s = h->stream;
   h->prior_set = true;
   h->prior_gx = gx;
@@ -550,20 +597,14 @@ bti_status bti_set_prior_se_grid(bti_handle h, int gx, int gy, double ell, doubl
   h->prior_ell = ell;
   h->prior_sigma = sigma;
   // C_s = C_x (x) C_y with sigma on each axis, node index ix * gy + iy
-  int64_t nl = se_axis_matrix(Cx, gx, ell, sigma, s);
-  nl += se_axis_matrix(Cy, gy, ell, sigma, s);
+  count_dense(h, se_axis_matrix(h->prior_axes, gx, ell, sigma, s) +
+                     se_axis_matrix(h->prior_axes + (size_t)gx * gx, gy, ell, sigma, s));
   // row r of the blocks viewed as X_r [gx][gy]: G_r = C_x X_r C_y
-  nl += gemm_f64(false, rows * gx, gy, gy, 1.0, F.time, gy, 0, Cy, gy, 0, 0.0, U, gy, 0, 1, false, s);
-  nl += gemm_f64(false, gx, gy, gx, 1.0, Cx, gx, 0, U, gy, (int64_t)gx * gy, 0.0, G, gy, (int64_t)gx * gy,
-                 rows, false, s);
-  count_dense(h, nl);
-  st = launched(h, "prior blocks");
+  st = se_rows_into(h, F.time, G, rows, U);
+  cudaStreamSynchronize(s);
+  dev_freep(U);  // before the spectral blocks are made
   if (st == BTI_OK) {
     OpStore& o = h->op[BTI_OP_G];
-    dev_free(o.hat);
-    dev_freep(o.time);
-    dev_freep(o.scale);
-    o.set = false;
     o.R = h->Nd;
     o.prec = store;
     o.time = G;
@@ -577,7 +618,6 @@ bti_status bti_set_prior_se_grid(bti_handle h, int gx, int gy, double ell, doubl
     }
   }
   cudaStreamSynchronize(s);
-  dev_freep(Cx);
   dev_freep(U);
   dev_freep(G);
   return st;
@@ -780,24 +820,11 @@ bti_status bti_infer_map(bti_handle h, const double* d_obs, double* m_map, int64
 // out = in C_s for `rows` grid-shaped rows (row r viewed as X_r [gx][gy]: C_x X_r C_y),
 // with the stored SE prior: the time-invariant Gamma_prior applied block by block.
 static bti_status apply_se_rows(bti_ctx* h, const double* in, double* out, int64_t rows) {
-  const int gx = h->prior_gx, gy = h->prior_gy;
-  double* Cx = nullptr;
   double* U = nullptr;
-  bti_status st = dev_alloc(h, (void**)&Cx, sizeof(double) * ((size_t)gx * gx + (size_t)gy * gy), "prior axes");
+  bti_status st = dev_alloc(h, (void**)&U, sizeof(double) * (size_t)rows * h->Nm, "prior temp");
   if (st != BTI_OK) return st;
-  double* Cy = Cx + (size_t)gx * gx;
-  st = dev_alloc(h, (void**)&U, sizeof(double) * (size_t)rows * h->Nm, "prior temp");
-  if (st != BTI_OK) { dev_freep(Cx); return st; }
-  cudaStream_t s = h->stream;
-  int64_t nl = se_axis_matrix(Cx, gx, h->prior_ell, h->prior_sigma, s);
-  nl += se_axis_matrix(Cy, gy, h->prior_ell, h->prior_sigma, s);
-  nl += gemm_f64(false, rows * gx, gy, gy, 1.0, in, gy, 0, Cy, gy, 0, 0.0, U, gy, 0, 1, false, s);
-  nl += gemm_f64(false, gx, gy, gx, 1.0, Cx, gx, 0, U, gy, (int64_t)gx * gy, 0.0, out, gy, (int64_t)gx * gy, rows,
-                 false, s);
-  count_dense(h, nl);
-  st = launched(h, "SE prior");
-  cudaStreamSynchronize(s);
-  dev_freep(Cx);
+  st = se_rows_into(h, in, out, rows, U);
+  cudaStreamSynchronize(h->stream);
   dev_freep(U);
   return st;
 }
@@ -911,6 +938,292 @@ bti_status bti_copy_Q(bti_handle h, double* Q_out, double* cov_out) {
   if (cov_out)
     st = cuda_check(h, cudaMemcpyAsync(cov_out, h->covq, sizeof(double) * nq * nq, cudaMemcpyDeviceToDevice,
                                        h->stream), "copy covariance");
+  return st;
+}
+
+bti_status bti_set_shadow(bti_handle h, bti_op op, bti_prec store) {
+  bti_status st = check_handle(h);
+  if (st != BTI_OK) return st;
+  if (op != BTI_OP_F && op != BTI_OP_G) return fail(h, BTI_ERR_ARG, "set_shadow: op must be F or G");
+  if (!prec_ok(store)) return fail(h, BTI_ERR_ARG, "set_shadow: bad precision");
+  const OpStore& o = h->op[op];
+  if (!o.set || !o.time) return fail(h, BTI_ERR_STATE, "set_shadow: operator blocks not set");
+  OpStore& sh = h->shadow[op];
+  drop_store(sh);
+  sh.R = o.R;
+  sh.prec = store;
+  st = dev_alloc(h, &sh.hat, (size_t)h->nf * sh.R * h->Nm * celem_size(store), "alloc shadow blocks");
+  if (st == BTI_OK) st = make_spectral(h, sh, o.time);
+  if (st == BTI_OK) st = cuda_check(h, cudaStreamSynchronize(h->stream), "set_shadow sync");
+  if (st != BTI_OK) {
+    drop_store(sh);
+    return st;
+  }
+  sh.set = true;
+  return BTI_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Buffers of one matrix-free solve for B right-hand sides (n = N_t N_d data, np = N_t N_m
+// parameters per vector).
+struct MatfreeWork {
+  double *x, *r, *y, *p, *q, *ro, *w1, *w2, *U;  // FP64 vectors and FP64 operator temporaries
+  float *dlt, *rt, *pt, *qt, *wf;                 // FP32 inner-iteration vectors
+  double *part, *dn2, *rn2, *rr, *rr2, *pq;       // dot workspace and per-vector scalars
+  double *rz, *zr, *zro, *num;                    // scalars of the flexible outer iteration
+};
+
+// y = K x = Gamma_noise x + F (G^* x) with FP64-accurate operators: the F store (FP64 or
+// double-FP32) and G^* from the G store when that is FP64-accurate, else Gamma_prior F^T.
+bti_status apply_K_accurate(bti_ctx* h, const double* x, double* y, int64_t B, MatfreeWork& w) {
+  const int64_t n = h->Nt * h->Nd;
+  bti_status st;
+  if (double_path(h->op[BTI_OP_G].prec)) {
+    st = apply_store(h, h->op[BTI_OP_G], true, x, w.w2, B, BTI_P_F64);
+  } else {
+    st = apply_store(h, h->op[BTI_OP_F], true, x, w.w1, B, BTI_P_F64);
+    if (st == BTI_OK) st = se_rows_into(h, w.w1, w.w2, B * h->Nt, w.U);
+  }
+  if (st == BTI_OK) st = apply_store(h, h->op[BTI_OP_F], false, w.w2, y, B, BTI_P_F64);
+  if (st != BTI_OK) return st;
+  count_dense(h, add_noise<double>(y, y, x, h->noise_diag, h->sigma2, n, B, h->stream));
+  return launched(h, "K x");
+}
+
+// m = G^* x with the FP64-accurate operators (as apply_K_accurate)
+bti_status apply_Gstar_accurate(bti_ctx* h, const double* x, double* m, int64_t B, MatfreeWork& w) {
+  if (double_path(h->op[BTI_OP_G].prec)) return apply_store(h, h->op[BTI_OP_G], true, x, m, B, BTI_P_F64);
+  bti_status st = apply_store(h, h->op[BTI_OP_F], true, x, w.w1, B, BTI_P_F64);
+  if (st == BTI_OK) st = se_rows_into(h, w.w1, m, B * h->Nt, w.U);
+  return st;
+}
+
+// q = K~ p with the inner (shadow where set) operators in FP32 vectors
+bti_status apply_K_inner(bti_ctx* h, const float* p, float* q, int64_t B, MatfreeWork& w) {
+  const OpStore& G = h->shadow[BTI_OP_G].set ? h->shadow[BTI_OP_G] : h->op[BTI_OP_G];
+  const OpStore& F = h->shadow[BTI_OP_F].set ? h->shadow[BTI_OP_F] : h->op[BTI_OP_F];
+  bti_status st = apply_store(h, G, true, p, w.wf, B, BTI_P_F32);
+  if (st == BTI_OK) st = apply_store(h, F, false, w.wf, q, B, BTI_P_F32);
+  if (st != BTI_OK) return st;
+  count_dense(h, add_noise<float>(q, q, p, h->noise_diag, h->sigma2, h->Nt * h->Nd, B, h->stream));
+  return launched(h, "inner K x");
+}
+
+// the per-vector scalars v[0..B) on the host (synchronises the stream)
+bti_status fetch(bti_ctx* h, const double* v, std::vector<double>& out, int64_t B) {
+  out.resize((size_t)B);
+  cudaError_t e = cudaMemcpyAsync(out.data(), v, sizeof(double) * B, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return cuda_check(h, e, "solver scalars");
+}
+
+// max over the batch of sqrt(a / b) (0 where b == 0); NaN propagates
+double max_ratio(const std::vector<double>& a, const std::vector<double>& b) {
+  double m = 0.0;
+  for (size_t i = 0; i < a.size(); ++i) {
+    const double v = b[i] > 0.0 ? std::sqrt(a[i] / b[i]) : (a[i] > 0.0 ? INFINITY : 0.0);
+    if (!(v <= m)) m = v;  // NaN wins
+  }
+  return m;
+}
+
+}  // namespace
+
+extern "C" {
+
+bti_status bti_solve_matfree(bti_handle h, const double* d_obs, double* m_map, double* x_out, int64_t B, int refine,
+                             double tol, int max_outer, int max_inner, double inner_tol, bti_solve_info* info) {
+  bti_status st = check_handle(h);
+  if (st != BTI_OK) return st;
+  if (info) *info = bti_solve_info{0, 0, 0.0};
+  if (B < 0 || refine < 0 || refine > 2 || !(tol > 0.0) || max_inner < 1 || max_outer < 0 ||
+      (refine != 0 && !(inner_tol > 0.0 && inner_tol < 1.0)))
+    return fail(h, BTI_ERR_ARG, "solve_matfree: bad B, refine, tolerance or iteration limit");
+  if (!h->op[BTI_OP_F].set || !double_path(h->op[BTI_OP_F].prec))
+    return fail(h, BTI_ERR_STATE, "solve_matfree: F must be stored in FP64 or double-FP32");
+  if (!h->prior_set || !h->op[BTI_OP_G].set) return fail(h, BTI_ERR_STATE, "solve_matfree: no SE prior set");
+  if (!h->noise_set) return fail(h, BTI_ERR_STATE, "solve_matfree: noise not set");
+  if (B == 0) return BTI_OK;
+  if (!d_obs || !m_map) return fail(h, BTI_ERR_ARG, "solve_matfree: null pointer");
+  const int64_t n = h->Nt * h->Nd, np = h->Nt * h->Nm;
+  const size_t Bn = (size_t)B * n, Bp = (size_t)B * np;
+  cudaStream_t s = h->stream;
+  // one allocation: 6 FP64 data vectors, 3 FP64 parameter temporaries, 4 FP32 data and
+  // 1 FP32 parameter vector, the dot workspace and 9 scalar rows
+  const size_t nd = 6 * Bn + 3 * Bp + dot_workspace_elems(B) + 9 * (size_t)B;
+  const size_t nfl = 4 * Bn + Bp;
+  void* buf = nullptr;
+  st = dev_alloc(h, &buf, sizeof(double) * nd + sizeof(float) * nfl, "solver workspace");
+  if (st != BTI_OK) return st;
+  MatfreeWork w;
+  double* dp = (double*)buf;
+  w.x = dp; dp += Bn;
+  w.r = dp; dp += Bn;
+  w.y = dp; dp += Bn;
+  w.p = dp; dp += Bn;
+  w.q = dp; dp += Bn;
+  w.ro = dp; dp += Bn;
+  w.w1 = dp; dp += Bp;
+  w.w2 = dp; dp += Bp;
+  w.U = dp; dp += Bp;
+  w.part = dp; dp += dot_workspace_elems(B);
+  w.dn2 = dp; dp += B;
+  w.rn2 = dp; dp += B;
+  w.rr = dp; dp += B;
+  w.rr2 = dp; dp += B;
+  w.pq = dp; dp += B;
+  w.rz = dp; dp += B;
+  w.zr = dp; dp += B;
+  w.zro = dp; dp += B;
+  w.num = dp; dp += B;
+  float* fp = (float*)dp;
+  w.dlt = fp; fp += Bn;
+  w.rt = fp; fp += Bn;
+  w.pt = fp; fp += Bn;
+  w.qt = fp; fp += Bn;
+  w.wf = fp;
+  std::vector<double> hd, hr;
+  int outer = 0, inner = 0;
+  double rel = 0.0;
+  bool converged = false;
+  auto dot = [&](auto* a, auto* b, double* out) { count_dense(h, dot_batched(a, b, n, B, w.part, out, s)); };
+  do {
+    st = cuda_check(h, cudaMemsetAsync(w.x, 0, sizeof(double) * Bn, s), "solver init");
+    if (st != BTI_OK) break;
+    st = cuda_check(h, cudaMemcpyAsync(w.r, d_obs, sizeof(double) * Bn, cudaMemcpyDeviceToDevice, s), "solver init");
+    if (st != BTI_OK) break;
+    dot(w.r, w.r, w.dn2);
+    st = fetch(h, w.dn2, hd, B);
+    if (st != BTI_OK) break;
+    if (refine == 0) {
+      // conjugate gradients on K with the FP64-accurate operators
+      cudaMemcpyAsync(w.p, w.r, sizeof(double) * Bn, cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(w.rr, w.dn2, sizeof(double) * B, cudaMemcpyDeviceToDevice, s);
+      for (int it = 0; it < max_inner; ++it) {
+        st = apply_K_accurate(h, w.p, w.q, B, w);
+        if (st != BTI_OK) break;
+        dot(w.p, w.q, w.pq);
+        count_dense(h, cg_update_xr(w.x, w.r, w.p, w.q, w.rr, w.pq, n, B, s));
+        dot(w.r, w.r, w.rr2);
+        ++inner;
+        st = fetch(h, w.rr2, hr, B);
+        if (st != BTI_OK) break;
+        rel = max_ratio(hr, hd);
+        if (rel <= tol) break;
+        count_dense(h, cg_update_p(w.p, w.r, w.rr2, w.rr, n, B, s));
+        std::swap(w.rr, w.rr2);
+      }
+    } else {
+      // z = ||r|| delta with K~ delta = r / ||r|| solved by FP32 conjugate gradients with the
+      // inner operators until the inner residual drops by inner_tol (rn2 = r . r on the device)
+      auto inner_solve = [&](const double* rv, const double* rn2, double* z) -> bti_status {
+        count_dense(h, normalize_to_f32(rv, rn2, w.rt, n, B, s));
+        cudaMemsetAsync(w.dlt, 0, sizeof(float) * Bn, s);
+        cudaMemcpyAsync(w.pt, w.rt, sizeof(float) * Bn, cudaMemcpyDeviceToDevice, s);
+        dot(w.rt, w.rt, w.rr);
+        std::vector<double> h0, hi;
+        bti_status si = fetch(h, w.rr, h0, B);
+        for (int it = 0; si == BTI_OK && it < max_inner; ++it) {
+          si = apply_K_inner(h, w.pt, w.qt, B, w);
+          if (si != BTI_OK) break;
+          dot(w.pt, w.qt, w.pq);
+          count_dense(h, cg_update_xr(w.dlt, w.rt, w.pt, w.qt, w.rr, w.pq, n, B, s));
+          dot(w.rt, w.rt, w.rr2);
+          ++inner;
+          si = fetch(h, w.rr2, hi, B);
+          if (si != BTI_OK) break;
+          const double ri = max_ratio(hi, h0);
+          if (ri <= inner_tol || !(ri == ri)) break;
+          count_dense(h, cg_update_p(w.pt, w.rt, w.rr2, w.rr, n, B, s));
+          std::swap(w.rr, w.rr2);
+        }
+        if (si != BTI_OK) return si;
+        cudaMemsetAsync(z, 0, sizeof(double) * Bn, s);
+        count_dense(h, add_scaled_f32(z, w.dlt, rn2, n, B, s));
+        return launched(h, "inner solve");
+      };
+      if (refine == 1) {
+        // FP64 iterative refinement: x += z with z from the inner solve of the residual
+        for (;;) {
+          dot(w.r, w.r, w.rn2);
+          st = fetch(h, w.rn2, hr, B);
+          if (st != BTI_OK) break;
+          rel = max_ratio(hr, hd);
+          if (rel <= tol || outer == max_outer || !(rel == rel)) break;
+          ++outer;
+          st = inner_solve(w.r, w.rn2, w.p);
+          if (st != BTI_OK) break;
+          count_dense(h, axpby_f64(w.x, w.p, 1.0, 1.0, (int64_t)Bn, s));
+          // r = d - K x with the FP64-accurate operators
+          st = apply_K_accurate(h, w.x, w.y, B, w);
+          if (st != BTI_OK) break;
+          cudaMemcpyAsync(w.r, d_obs, sizeof(double) * Bn, cudaMemcpyDeviceToDevice, s);
+          count_dense(h, axpby_f64(w.r, w.y, -1.0, 1.0, (int64_t)Bn, s));
+        }
+      } else {
+        // refinement accelerated by flexible conjugate gradients in FP64 (the CG analogue
+        // of GMRES-based refinement): the inner solve is a variable preconditioner, so
+        // beta takes the Polak-Ribiere form z_new . (r_new - r_old) / (z_old . r_old).
+        // y holds z; ro the previous residual.
+        dot(w.r, w.r, w.rn2);
+        st = inner_solve(w.r, w.rn2, w.y);
+        if (st != BTI_OK) break;
+        cudaMemcpyAsync(w.p, w.y, sizeof(double) * Bn, cudaMemcpyDeviceToDevice, s);
+        dot(w.r, w.y, w.rz);
+        for (;;) {
+          if (outer == max_outer) break;
+          ++outer;
+          st = apply_K_accurate(h, w.p, w.q, B, w);
+          if (st != BTI_OK) break;
+          dot(w.p, w.q, w.pq);
+          cudaMemcpyAsync(w.ro, w.r, sizeof(double) * Bn, cudaMemcpyDeviceToDevice, s);
+          count_dense(h, cg_update_xr(w.x, w.r, w.p, w.q, w.rz, w.pq, n, B, s));
+          dot(w.r, w.r, w.rn2);
+          st = fetch(h, w.rn2, hr, B);
+          if (st != BTI_OK) break;
+          rel = max_ratio(hr, hd);
+          if (rel <= tol || !(rel == rel)) break;
+          st = inner_solve(w.r, w.rn2, w.y);
+          if (st != BTI_OK) break;
+          dot(w.y, w.r, w.zr);    // z_new . r_new
+          dot(w.y, w.ro, w.zro);  // z_new . r_old
+          cudaMemcpyAsync(w.num, w.zr, sizeof(double) * B, cudaMemcpyDeviceToDevice, s);
+          count_dense(h, axpby_f64(w.num, w.zro, -1.0, 1.0, B, s));
+          count_dense(h, cg_update_p(w.p, w.y, w.num, w.rz, n, B, s));
+          std::swap(w.rz, w.zr);
+        }
+      }
+    }
+    if (st != BTI_OK) break;
+    if (refine != 1) {  // the recursive CG residual drifts: report the true one
+      st = apply_K_accurate(h, w.x, w.y, B, w);
+      if (st != BTI_OK) break;
+      cudaMemcpyAsync(w.r, d_obs, sizeof(double) * Bn, cudaMemcpyDeviceToDevice, s);
+      count_dense(h, axpby_f64(w.r, w.y, -1.0, 1.0, (int64_t)Bn, s));
+      dot(w.r, w.r, w.rn2);
+      st = fetch(h, w.rn2, hr, B);
+      if (st != BTI_OK) break;
+      rel = max_ratio(hr, hd);
+    }
+    converged = rel <= tol;
+    st = apply_Gstar_accurate(h, w.x, m_map, B, w);
+    if (st != BTI_OK) break;
+    if (x_out) cudaMemcpyAsync(x_out, w.x, sizeof(double) * Bn, cudaMemcpyDeviceToDevice, s);
+    st = launched(h, "solve_matfree");
+    if (st == BTI_OK) st = cuda_check(h, cudaStreamSynchronize(s), "solve_matfree sync");
+  } while (false);
+  cudaStreamSynchronize(s);
+  dev_free(buf);
+  if (info) *info = bti_solve_info{outer, inner, rel};
+  if (st == BTI_OK && !converged) {
+    char msg[160];
+    snprintf(msg, sizeof msg, "solve_matfree: relative residual %.3e above tol %.3e after %d outer, %d inner iterations",
+             rel, tol, outer, inner);
+    return fail(h, BTI_ERR_NO_CONVERGENCE, msg);
+  }
   return st;
 }
 

@@ -100,6 +100,13 @@ template <> __device__ __forceinline__ ffc cmul<ffloat>(ffc a, ffc b) {
 constexpr int kMaxPasses = 12;
 constexpr int kMaxL = 2048;  // longest transform (N_t <= 1024); also the per-CTA FFT size
 
+// Shared-memory slots per transform in the FFT kernels: element n sits at slot n + n / 8
+// (a padding slot after every 8 elements), and the count is 1 modulo 8 so that the
+// transforms of one CTA start in different banks.
+__host__ __device__ constexpr int fft_slots(int L) {
+  return (L + (L >> 3) + 1) + ((9 - ((L + (L >> 3) + 1) & 7)) & 7);
+}
+
 struct FftPlan {
   int L = 0;              // transform length (2 N_t)
   int npass = 0;
@@ -114,9 +121,10 @@ bool fft_plan_make(FftPlan& p, int L);   // host: factor L, choose P; false if u
 // The same factorisation without the twiddle tables (tw64 / tw32 left null for the caller to set).
 bool fft_plan_factor(FftPlan& p, int L);
 
-// Kernel launchers (fft.cu).  All act on "columns": element (t, c) of a real
-// column array sits at x[t * ld + c]; a spectrum element (w, c) at X[w * ld + c].
-// batch b offsets by x_bstride / X_bstride elements.
+// Kernel launchers (fft.cu).  All act on "columns".  Forward: element (t, c) of the
+// real input sits at x[t * ld + c] and spectrum element (w, c) is written to
+// X[w * ncols + c].  Inverse: spectrum element (w, c) at X[w * ld + c], output
+// element (t, c) at y[t * ld + c].  Batch b offsets by the b-strides.
 template <typename T, typename TI, typename TO>
 void launch_rfft_cols(const FftPlan& p, int Nt, const TI* x, int64_t ld, int64_t x_bstride,
                       C2<TO>* X, int64_t X_bstride, int64_t ncols, int64_t B, cudaStream_t s);
@@ -149,7 +157,9 @@ void launch_prod_fwd_df64(const float4* Fhat, const double2* mhat, double2* part
 void launch_prod_adj_df64(const float4* Fhat, const double2* dhat, double2* mhat, int64_t nf, int64_t R,
                           int64_t Nm, int64_t B, cudaStream_t s, int vpt = 0);
 // FP16 tier: spectral blocks as FP16 complex pairs with one FP32 power-of-two scale per row.
-void launch_quantize_f16(const double2* src, void* dst, float* scale, int64_t rows, int64_t Nm, cudaStream_t s);
+// src [nf][rn][Nm] FP64 spectrum of rows i0 .. i0 + rn -> rows (w, i0 + r) of dst [nf][R][Nm]
+void launch_quantize_f16(const double2* src, void* dst, float* scale, int64_t nf, int64_t rn, int64_t R,
+                         int64_t i0, int64_t Nm, cudaStream_t s);
 void launch_prod_fwd_f16(const void* Fhat, const float* scale, const float2* mhat, float2* partial, int64_t nf,
                          int64_t R, int64_t Nm, int64_t B, cudaStream_t s, int jc = 0);
 void launch_prod_adj_f16(const void* Fhat, const float* scale, const float2* dhat, float2* mhat, int64_t nf,
@@ -200,5 +210,26 @@ int select_time_blocks_sq(const double* in, double* out, int64_t Nt, int64_t R, 
 int block_diag_cumsum_all(double* X, int64_t Nt, int64_t R1, int64_t R2, cudaStream_t s);
 int noise_residual_f64(double* r, const double* x, const double* diag, int64_t n, int64_t B,
                        cudaStream_t s);
+
+// Krylov vector kernels (krylov.cu); vectors [B][n], per-vector scalars on the device.
+// out[b] = x[b] . y[b] in FP64 with a fixed reduction order; part holds
+// dot_workspace_elems(B) doubles.
+size_t dot_workspace_elems(int64_t B);
+template <typename T>
+int dot_batched(const T* x, const T* y, int64_t n, int64_t B, double* part, double* out, cudaStream_t s);
+// x += (rr / pq) p and r -= (rr / pq) q per vector (no step where pq <= 0 or rr <= 0)
+template <typename T>
+int cg_update_xr(T* x, T* r, const T* p, const T* q, const double* rr, const double* pq, int64_t n, int64_t B,
+                 cudaStream_t s);
+// p = r + (rr_new / rr_old) p per vector
+template <typename T>
+int cg_update_p(T* p, const T* r, const double* rr_new, const double* rr_old, int64_t n, int64_t B, cudaStream_t s);
+// q = y + Gamma_noise p (diag[i] per datum, else sigma2); q may alias y
+template <typename T>
+int add_noise(T* q, const T* y, const T* p, const double* diag, double sigma2, int64_t n, int64_t B, cudaStream_t s);
+// out = float(x / sqrt(nrm2)) and x += sqrt(nrm2) * d (the scaled hand-over between an FP64
+// refinement loop and an FP32 inner solve)
+int normalize_to_f32(const double* x, const double* nrm2, float* out, int64_t n, int64_t B, cudaStream_t s);
+int add_scaled_f32(double* x, const float* d, const double* nrm2, int64_t n, int64_t B, cudaStream_t s);
 
 }  // namespace bti

@@ -131,6 +131,11 @@ __device__ __forceinline__ C2<T> rot90(C2<T> a) {
   return INV ? mk<T>(-a.y, a.x) : mk<T>(a.y, -a.x);
 }
 
+// Shared-memory slot of element n of one transform: one padding slot after every 8
+// elements, so the stride-8 stores of a first radix-8 pass (and the column staging)
+// spread over all 32 banks instead of serialising on four of them.
+__device__ __forceinline__ int sp(int n) { return n + (n >> 3); }
+
 template <typename T, bool INV>
 __device__ __forceinline__ void dft4(C2<T>& a0, C2<T>& a1, C2<T>& a2, C2<T>& a3) {
   C2<T> t0 = cadd<T>(a0, a2), t1 = csub<T>(a0, a2);
@@ -141,13 +146,14 @@ __device__ __forceinline__ void dft4(C2<T>& a0, C2<T>& a1, C2<T>& a2, C2<T>& a3)
   a3 = csub<T>(t1, t3);
 }
 
-// One radix-R Stockham butterfly: inputs s[q*Lr], q < R; outputs d[m*Ns], m < R.
+// One radix-R Stockham butterfly: inputs element i0 + q Lr of src, q < R; outputs element
+// o0 + m Ns of dst, m < R (elements at their padded slots).
 template <int R, typename T, bool INV>
-__device__ __forceinline__ void butterfly(const C2<T>* s, int Lr, C2<T>* d, int Ns,
+__device__ __forceinline__ void butterfly(const C2<T>* src, int i0, int Lr, C2<T>* dst, int o0, int Ns,
                                           const C2<T>* __restrict__ tw, int twstep, int L) {
   C2<T> a[R];
 #pragma unroll
-  for (int q = 0; q < R; ++q) a[q] = s[q * Lr];
+  for (int q = 0; q < R; ++q) a[q] = src[sp(i0 + q * Lr)];
   if (twstep != 0) {
 #pragma unroll
     for (int q = 1; q < R; ++q) a[q] = cmul<T>(a[q], tw_get<T, INV>(tw, q * twstep));
@@ -197,38 +203,40 @@ __device__ __forceinline__ void butterfly(const C2<T>* s, int Lr, C2<T>* d, int 
     for (int m = 0; m < R; ++m) a[m] = b[m];
   }
 #pragma unroll
-  for (int m = 0; m < R; ++m) d[m * Ns] = a[m];
+  for (int m = 0; m < R; ++m) dst[sp(o0 + m * Ns)] = a[m];
 }
 
 // First radix-8 pass of a forward transform whose second half is zero padding
 // (L = 2 N_t, so inputs q = 4..7 of every first-pass butterfly vanish; the pass has
 // no twiddles since Ns = 1): the two radix-4 halves reduce to two additions each.
 template <typename T>
-__device__ __forceinline__ void butterfly8_half_zero(const C2<T>* s, int Lr, C2<T>* d) {
-  const C2<T> a0 = s[0], a1 = s[Lr], a2 = s[2 * Lr], a3 = s[3 * Lr];
+__device__ __forceinline__ void butterfly8_half_zero(const C2<T>* src, int i0, int Lr, C2<T>* dst, int o0) {
+  const C2<T> a0 = src[sp(i0)], a1 = src[sp(i0 + Lr)], a2 = src[sp(i0 + 2 * Lr)], a3 = src[sp(i0 + 3 * Lr)];
   // even half: DFT4(a0, a2, 0, 0); odd half: DFT4(a1, a3, 0, 0)
   const C2<T> r2 = rot90<T, false>(a2), r3 = rot90<T, false>(a3);
   C2<T> e0 = cadd<T>(a0, a2), e2 = csub<T>(a0, a2), e1 = cadd<T>(a0, r2), e3 = csub<T>(a0, r2);
-  C2<T> o0 = cadd<T>(a1, a3), o2 = csub<T>(a1, a3), o1 = cadd<T>(a1, r3), o3 = csub<T>(a1, r3);
+  C2<T> o0v = cadd<T>(a1, a3), o2 = csub<T>(a1, a3), o1 = cadd<T>(a1, r3), o3 = csub<T>(a1, r3);
   const T h = (T)0.70710678118654752440084436210485;  // sqrt(1/2)
   o1 = cmul<T>(o1, mk<T>(h, -h));
   o2 = rot90<T, false>(o2);
   o3 = cmul<T>(o3, mk<T>(-h, -h));
-  d[0] = cadd<T>(e0, o0);
-  d[4] = csub<T>(e0, o0);
-  d[1] = cadd<T>(e1, o1);
-  d[5] = csub<T>(e1, o1);
-  d[2] = cadd<T>(e2, o2);
-  d[6] = csub<T>(e2, o2);
-  d[3] = cadd<T>(e3, o3);
-  d[7] = csub<T>(e3, o3);
+  dst[sp(o0)] = cadd<T>(e0, o0v);
+  dst[sp(o0 + 4)] = csub<T>(e0, o0v);
+  dst[sp(o0 + 1)] = cadd<T>(e1, o1);
+  dst[sp(o0 + 5)] = csub<T>(e1, o1);
+  dst[sp(o0 + 2)] = cadd<T>(e2, o2);
+  dst[sp(o0 + 6)] = csub<T>(e2, o2);
+  dst[sp(o0 + 3)] = cadd<T>(e3, o3);
+  dst[sp(o0 + 7)] = csub<T>(e3, o3);
 }
 
-// All passes; data starts in buf0, result pointer returned (buf0 or buf1).  With
-// half_zero, the first pass is radix 8 and only the first half of each input is nonzero.
-template <typename T, bool INV>
+// All passes; data starts in buf0, result pointer returned (buf0 or buf1); transform p
+// of the CTA occupies LP slots from p LP.  With half_zero, the first pass is radix 8 and
+// only the first half of each input is nonzero.  POW2 compiles the radix 8, 4, 2
+// butterflies only (fewer registers for power-of-two lengths).
+template <typename T, bool INV, bool POW2>
 __device__ C2<T>* run_passes(const FftDesc& D, C2<T>* buf0, C2<T>* buf1, const C2<T>* __restrict__ tw,
-                             bool half_zero = false) {
+                             int LP, bool half_zero = false) {
   C2<T>* src = buf0;
   C2<T>* dst = buf1;
   const int L = D.L;
@@ -238,7 +246,7 @@ __device__ C2<T>* run_passes(const FftDesc& D, C2<T>* buf0, C2<T>* buf1, const C
     const int nbf = D.P * Lr;
     for (int bi = threadIdx.x; bi < nbf; bi += blockDim.x) {
       int p = bi / Lr, j = bi - p * Lr;
-      butterfly8_half_zero<T>(src + p * L + j, Lr, dst + p * L + j * 8);
+      butterfly8_half_zero<T>(src + p * LP, j, Lr, dst + p * LP, j * 8);
     }
     __syncthreads();
     C2<T>* tmp = src;
@@ -254,16 +262,23 @@ __device__ C2<T>* run_passes(const FftDesc& D, C2<T>* buf0, C2<T>* buf1, const C
       int p = bi / Lr;
       int j = bi - p * Lr;
       int k = j % Ns;
-      const C2<T>* s = src + p * L + j;
-      C2<T>* d = dst + p * L + (j - k) * r + k;
+      const C2<T>* s = src + p * LP;
+      C2<T>* d = dst + p * LP;
+      const int o0 = (j - k) * r + k;
       int twstep = k * (L / (Ns * r));
-      switch (r) {
-        case 8: butterfly<8, T, INV>(s, Lr, d, Ns, tw, twstep, L); break;
-        case 4: butterfly<4, T, INV>(s, Lr, d, Ns, tw, twstep, L); break;
-        case 2: butterfly<2, T, INV>(s, Lr, d, Ns, tw, twstep, L); break;
-        case 7: butterfly<7, T, INV>(s, Lr, d, Ns, tw, twstep, L); break;
-        case 5: butterfly<5, T, INV>(s, Lr, d, Ns, tw, twstep, L); break;
-        default: butterfly<3, T, INV>(s, Lr, d, Ns, tw, twstep, L); break;
+      if (POW2) {
+        if (r == 8) butterfly<8, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L);
+        else if (r == 4) butterfly<4, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L);
+        else butterfly<2, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L);
+      } else {
+        switch (r) {
+          case 8: butterfly<8, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L); break;
+          case 4: butterfly<4, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L); break;
+          case 2: butterfly<2, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L); break;
+          case 7: butterfly<7, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L); break;
+          case 5: butterfly<5, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L); break;
+          default: butterfly<3, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L); break;
+        }
       }
     }
     __syncthreads();
@@ -280,14 +295,14 @@ template <typename TO, typename T> __device__ __forceinline__ C2<TO> cvt2(C2<T> 
 }
 template <typename T> __device__ __forceinline__ C2<T> czero() { return mk<T>((T)0, (T)0); }
 
-template <typename T, typename TI, typename TO>
-__global__ void __launch_bounds__(256, 2)
+template <typename T, typename TI, typename TO, bool POW2>
+__global__ void __launch_bounds__(256, POW2 ? 3 : 2)  // power-of-two plans fit 3 CTAs per SM without spills
 rfft_cols_kernel(FftDesc D, int Nt, const TI* __restrict__ x, int64_t ld, int64_t xbs,
                  C2<TO>* __restrict__ X, int64_t Xbs, int64_t ncols, TwTabs tabs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int L = D.L, P = D.P, W2 = 2 * P;
+  const int L = D.L, P = D.P, W2 = 2 * P, LP = fft_slots(L);
   C2<T>* buf0 = reinterpret_cast<C2<T>*>(smem_raw);
-  C2<T>* buf1 = buf0 + P * L;
+  C2<T>* buf1 = buf0 + P * LP;
   const C2<T>* tw = twtab<T>(tabs);
   const int64_t col0 = (int64_t)blockIdx.x * W2;
   const TI* xb = x + (int64_t)blockIdx.y * xbs;
@@ -297,15 +312,15 @@ rfft_cols_kernel(FftDesc D, int Nt, const TI* __restrict__ x, int64_t ld, int64_
     int t = idx / W2, c = idx - t * W2;
     int64_t col = col0 + c;
     T v = (col < ncols) ? (T)xb[(int64_t)t * ld + col] : (T)0;
-    reinterpret_cast<T*>(&buf0[(c >> 1) * L + t])[c & 1] = v;
+    reinterpret_cast<T*>(&buf0[(c >> 1) * LP + sp(t)])[c & 1] = v;
   }
   const int pad = L - Nt;
   for (int idx = threadIdx.x; idx < P * pad; idx += blockDim.x) {
     int p = idx / pad, t = Nt + (idx - p * pad);
-    buf0[p * L + t] = czero<T>();
+    buf0[p * LP + sp(t)] = czero<T>();
   }
   __syncthreads();
-  C2<T>* Z = run_passes<T, false>(D, buf0, buf1, tw, 2 * Nt == L);
+  C2<T>* Z = run_passes<T, false, POW2>(D, buf0, buf1, tw, LP, 2 * Nt == L);
   // unpack the two real spectra of each pair and store bins 0..N_t
   const int nf = Nt + 1;
   for (int idx = threadIdx.x; idx < nf * W2; idx += blockDim.x) {
@@ -313,8 +328,8 @@ rfft_cols_kernel(FftDesc D, int Nt, const TI* __restrict__ x, int64_t ld, int64_
     int64_t col = col0 + c;
     if (col >= ncols) continue;
     int p = c >> 1;
-    C2<T> z = Z[p * L + k];
-    C2<T> zc = Z[p * L + (k == 0 ? 0 : L - k)];
+    C2<T> z = Z[p * LP + sp(k)];
+    C2<T> zc = Z[p * LP + sp(k == 0 ? 0 : L - k)];
     C2<T> out;
     const T half = (T)0.5;
     if ((c & 1) == 0) {
@@ -326,14 +341,14 @@ rfft_cols_kernel(FftDesc D, int Nt, const TI* __restrict__ x, int64_t ld, int64_
   }
 }
 
-template <typename T, typename TYI, typename TO>
-__global__ void __launch_bounds__(256, 2)
+template <typename T, typename TYI, typename TO, bool POW2>
+__global__ void __launch_bounds__(256, POW2 ? 3 : 2)
 irfft_cols_kernel(FftDesc D, int Nt, const C2<TYI>* __restrict__ Y, int64_t ld, int64_t Ybs,
                   TO* __restrict__ y, int64_t ybs, int64_t ncols, double scale_d, TwTabs tabs, int ostride) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int L = D.L, P = D.P, W2 = 2 * P;
+  const int L = D.L, P = D.P, W2 = 2 * P, LP = fft_slots(L);
   C2<T>* buf0 = reinterpret_cast<C2<T>*>(smem_raw);
-  C2<T>* buf1 = buf0 + P * L;
+  C2<T>* buf1 = buf0 + P * LP;
   const C2<T>* tw = twtab<T>(tabs);
   const T scale = (T)scale_d;
   const int64_t col0 = (int64_t)blockIdx.x * W2;
@@ -346,24 +361,24 @@ irfft_cols_kernel(FftDesc D, int Nt, const C2<TYI>* __restrict__ Y, int64_t ld, 
     int64_t col = col0 + c;
     C2<T> v = (col < ncols) ? cvt2<T, TYI>(Yb[(int64_t)k * ld + col]) : czero<T>();
     C2<T>* dst = (c & 1) ? buf1 : buf0;
-    dst[(c >> 1) * L + k] = v;
+    dst[(c >> 1) * LP + sp(k)] = v;
   }
   __syncthreads();
   // Z[k] = A[k] + i B[k] for k <= N_t and Z[L-k] = conj(A[k]) + i conj(B[k]);
   // bins 0 and N_t of a real signal's spectrum are real: their imaginary parts are dropped.
   for (int idx = threadIdx.x; idx < P * nf; idx += blockDim.x) {
     int p = idx / nf, k = idx - p * nf;
-    C2<T> a = buf0[p * L + k];
-    C2<T> b = buf1[p * L + k];
+    C2<T> a = buf0[p * LP + sp(k)];
+    C2<T> b = buf1[p * LP + sp(k)];
     if (k == 0 || k == Nt) {
-      buf0[p * L + k] = mk<T>(a.x, b.x);
+      buf0[p * LP + sp(k)] = mk<T>(a.x, b.x);
     } else {
-      buf0[p * L + k] = mk<T>(a.x - b.y, a.y + b.x);
-      buf0[p * L + (L - k)] = mk<T>(a.x + b.y, b.x - a.y);
+      buf0[p * LP + sp(k)] = mk<T>(a.x - b.y, a.y + b.x);
+      buf0[p * LP + sp(L - k)] = mk<T>(a.x + b.y, b.x - a.y);
     }
   }
   __syncthreads();
-  C2<T>* Z = run_passes<T, true>(D, buf0, buf1, tw);
+  C2<T>* Z = run_passes<T, true, POW2>(D, buf0, buf1, tw, LP);
   // rows t = ostride (k + 1) - 1 only (every row when ostride == 1), stored as row k
   const int nout = Nt / ostride;
   for (int idx = threadIdx.x; idx < nout * W2; idx += blockDim.x) {
@@ -371,7 +386,7 @@ irfft_cols_kernel(FftDesc D, int Nt, const C2<TYI>* __restrict__ Y, int64_t ld, 
     int64_t col = col0 + c;
     if (col >= ncols) continue;
     const int t = ostride * (k + 1) - 1;
-    C2<T> z = Z[(c >> 1) * L + t];
+    C2<T> z = Z[(c >> 1) * LP + sp(t)];
     T v = ((c & 1) ? z.y : z.x) * scale;
     yb[(int64_t)k * ld + col] = (TO)v;
   }
@@ -393,18 +408,26 @@ void launch_rfft_cols(const FftPlan& p, int Nt, const TI* x, int64_t ld, int64_t
                       C2<TO>* X, int64_t X_bstride, int64_t ncols, int64_t B, cudaStream_t s) {
   if (ncols <= 0 || B <= 0) return;
   FftDesc D = desc_of(p);
-  size_t smem = 2 * sizeof(C2<T>) * (size_t)p.P * p.L;
+  size_t smem = 2 * sizeof(C2<T>) * (size_t)p.P * fft_slots(p.L);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(rfft_cols_kernel<T, TI, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(rfft_cols_kernel<T, TI, TO, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+    cudaFuncSetAttribute(rfft_cols_kernel<T, TI, TO, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
     attr_set = true;
   }
+  const bool pow2 = (p.L & (p.L - 1)) == 0;
   int64_t gx = (ncols + 2 * p.P - 1) / (2 * p.P);
   for (int64_t b0 = 0; b0 < B; b0 += 65535) {
     int64_t nb = B - b0 < 65535 ? B - b0 : 65535;
     dim3 grid((unsigned)gx, (unsigned)nb);
-    rfft_cols_kernel<T, TI, TO><<<grid, 256, smem, s>>>(D, Nt, x + b0 * x_bstride, ld, x_bstride,
-                                                        X + b0 * X_bstride, X_bstride, ncols, tabs_of(p));
+    if (pow2)
+      rfft_cols_kernel<T, TI, TO, true><<<grid, 256, smem, s>>>(D, Nt, x + b0 * x_bstride, ld, x_bstride,
+                                                                X + b0 * X_bstride, X_bstride, ncols, tabs_of(p));
+    else
+      rfft_cols_kernel<T, TI, TO, false><<<grid, 256, smem, s>>>(D, Nt, x + b0 * x_bstride, ld, x_bstride,
+                                                                 X + b0 * X_bstride, X_bstride, ncols, tabs_of(p));
   }
 }
 
@@ -414,19 +437,29 @@ void launch_irfft_cols(const FftPlan& p, int Nt, const C2<TYI>* X, int64_t ld, i
                        int ostride) {
   if (ncols <= 0 || B <= 0) return;
   FftDesc D = desc_of(p);
-  size_t smem = 2 * sizeof(C2<T>) * (size_t)p.P * p.L;
+  size_t smem = 2 * sizeof(C2<T>) * (size_t)p.P * fft_slots(p.L);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(irfft_cols_kernel<T, TYI, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(irfft_cols_kernel<T, TYI, TO, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+    cudaFuncSetAttribute(irfft_cols_kernel<T, TYI, TO, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
     attr_set = true;
   }
+  const bool pow2 = (p.L & (p.L - 1)) == 0;
+  const int os = ostride < 1 ? 1 : ostride;
   int64_t gx = (ncols + 2 * p.P - 1) / (2 * p.P);
   for (int64_t b0 = 0; b0 < B; b0 += 65535) {
     int64_t nb = B - b0 < 65535 ? B - b0 : 65535;
     dim3 grid((unsigned)gx, (unsigned)nb);
-    irfft_cols_kernel<T, TYI, TO><<<grid, 256, smem, s>>>(D, Nt, X + b0 * X_bstride, ld, X_bstride,
-                                                          y + b0 * y_bstride, y_bstride, ncols, scale,
-                                                          tabs_of(p), ostride < 1 ? 1 : ostride);
+    if (pow2)
+      irfft_cols_kernel<T, TYI, TO, true><<<grid, 256, smem, s>>>(D, Nt, X + b0 * X_bstride, ld, X_bstride,
+                                                                  y + b0 * y_bstride, y_bstride, ncols, scale,
+                                                                  tabs_of(p), os);
+    else
+      irfft_cols_kernel<T, TYI, TO, false><<<grid, 256, smem, s>>>(D, Nt, X + b0 * X_bstride, ld, X_bstride,
+                                                                   y + b0 * y_bstride, y_bstride, ncols, scale,
+                                                                   tabs_of(p), os);
   }
 }
 

@@ -539,11 +539,14 @@ void launch_prod_adj_df64(const float4* Fhat, const double2* dhat, double2* mhat
 // element: the low-precision tier of mixed-precision solves, whose final accuracy
 // comes from refinement with the double-FP32 operators.
 
-// One CTA per row (w, i): max |re|, |im| over the row, then scale and round.
+// One CTA per source row (w, r) of a [nf][rn][Nm] chunk holding rows i0 .. i0 + rn of
+// [nf][R][Nm]: max |re|, |im| over the row, then scale and round into row (w, i0 + r).
 __global__ void quantize_f16_rows_kernel(const double2* __restrict__ src, __half2* __restrict__ dst,
-                                         float* __restrict__ scale, int64_t Nm) {
-  const int64_t row = blockIdx.x;
-  const double2* s = src + row * Nm;
+                                         float* __restrict__ scale, int64_t Nm, int64_t rn, int64_t R,
+                                         int64_t i0) {
+  const int64_t srow = blockIdx.x;
+  const int64_t row = (srow / rn) * R + i0 + srow % rn;  // destination row w R + i
+  const double2* s = src + srow * Nm;
   double mx = 0.0;
   for (int64_t j = threadIdx.x; j < Nm; j += blockDim.x) {
     double2 v = s[j];
@@ -575,8 +578,10 @@ __global__ void quantize_f16_rows_kernel(const double2* __restrict__ src, __half
   }
 }
 
-void launch_quantize_f16(const double2* src, void* dst, float* scale, int64_t rows, int64_t Nm, cudaStream_t s) {
-  if (rows > 0) quantize_f16_rows_kernel<<<(unsigned)rows, 256, 0, s>>>(src, (__half2*)dst, scale, Nm);
+void launch_quantize_f16(const double2* src, void* dst, float* scale, int64_t nf, int64_t rn, int64_t R,
+                         int64_t i0, int64_t Nm, cudaStream_t s) {
+  if (nf * rn > 0)
+    quantize_f16_rows_kernel<<<(unsigned)(nf * rn), 256, 0, s>>>(src, (__half2*)dst, scale, Nm, rn, R, i0);
 }
 
 // Forward product: grid (nchunk, nf, ceil(B / BG)); warp w handles rows w, w + 8, ...

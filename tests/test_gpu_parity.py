@@ -594,3 +594,57 @@ def test_coarse_qoi_grid(stride):
     with pytest.raises(bti.BtiError):
         h.set_qoi_stride(3)  # does not divide N_t = 64
     h.close()
+
+
+@pytest.mark.parametrize("form", ["plain_df64", "refined_f16", "refined_f32_f64store", "flexible_f16"])
+def test_matrix_free_solve_matches_dense_oracle(form):
+    """m_map = G^* K^{-1} d_obs by conjugate gradients without forming K, against the
+    oracle's dense Cholesky solve: FP64 CG with double-FP32 operators, and FP64
+    refinement around FP32 CG with FP16 (or FP32) shadow operators."""
+    p, F, Fq, G, d_obs = tiny_problem()
+    d = np.concatenate([d_obs, p.vectors_d(2)])
+    store = bti.F64 if form == "refined_f32_f64store" else bti.DF64
+    h = make_handle(F, None, store)
+    h.set_noise(p.sigma2)
+    if form == "plain_df64":
+        h.set_prior_se_grid(p.gx, p.gy, p.ell, p.sigma_p, bti.DF64)
+    else:
+        low = bti.F16 if form == "refined_f16" else bti.F32
+        h.set_prior_se_grid(p.gx, p.gy, p.ell, p.sigma_p, low)
+        h.set_shadow(bti.OP_F, low)
+    m = torch.empty((3, p.Nt, p.Nm), dtype=torch.float64, device="cuda")
+    x = torch.empty((3, p.Nt, p.Nd), dtype=torch.float64, device="cuda")
+    refine = {"plain_df64": 0, "flexible_f16": 2}.get(form, 1)
+    info = h.solve_matfree(cuda(d), m, x, refine=refine, tol=1e-12, max_outer=100, max_inner=2000,
+                           inner_tol=0.2 if refine == 2 else 1e-3)
+    h.close()
+    L = oracle.cholesky_lower(oracle.assemble_K(F, G, p.sigma2))
+    x_or = oracle.solve_K(L, d.reshape(3, -1)).reshape(x.shape)
+    assert relb(host(x), x_or) < 1e-10, info
+    assert relb(host(m), oracle.map_point(F, G, p.sigma2, d, L=L)) < 1e-10, info
+    assert info["rel_residual"] <= 1e-12
+    if refine == 1:  # each refinement step gains about -log10(kappa(K) ||K - K~|| / ||K||) digits
+        assert 1 <= info["outer_iters"] <= 30, info
+
+
+def test_matrix_free_solve_reports_no_convergence():
+    """An iteration limit too small for the tolerance returns BTI_ERR_NO_CONVERGENCE,
+    with the statistics of the iterations taken and the last iterate written."""
+    p, F, Fq, G, d_obs = tiny_problem()
+    h = make_handle(F, None, bti.DF64)
+    h.set_noise(p.sigma2)
+    h.set_prior_se_grid(p.gx, p.gy, p.ell, p.sigma_p, bti.DF64)
+    m = torch.full((1, p.Nt, p.Nm), float("nan"), dtype=torch.float64, device="cuda")
+    with pytest.raises(bti.BtiError) as e:
+        h.solve_matfree(cuda(d_obs), m, refine=False, tol=1e-14, max_inner=3)
+    assert e.value.status == 8
+    assert h.last_solve["inner_iters"] == 3 and h.last_solve["rel_residual"] > 1e-14
+    assert torch.isfinite(m).all()
+    with pytest.raises(bti.BtiError) as e:  # F in a low tier cannot give the FP64 residual
+        h2 = make_handle(F, None, bti.F32)
+        h2.set_noise(p.sigma2)
+        h2.set_prior_se_grid(p.gx, p.gy, p.ell, p.sigma_p, bti.F32)
+        h2.solve_matfree(cuda(d_obs), m)
+    assert e.value.status == 3
+    h2.close()
+    h.close()
