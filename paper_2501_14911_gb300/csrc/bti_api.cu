@@ -1090,6 +1090,22 @@ bti_status bti_solve_matfree(bti_handle h, const double* d_obs, double* m_map, d
   double rel = 0.0;
   bool converged = false;
   auto dot = [&](auto* a, auto* b, double* out) { count_dense(h, dot_batched(a, b, n, B, w.part, out, s)); };
+  // r = d - K x with the FP64-accurate operator, rn2 = r . r, and the max relative residual
+  auto true_residual = [&](double& out_rel) -> bti_status {
+    bti_status sr = apply_K_accurate(h, w.x, w.y, B, w);
+    if (sr != BTI_OK) return sr;
+    cudaMemcpyAsync(w.r, d_obs, sizeof(double) * Bn, cudaMemcpyDeviceToDevice, s);
+    count_dense(h, axpby_f64(w.r, w.y, -1.0, 1.0, (int64_t)Bn, s));
+    dot(w.r, w.r, w.rn2);
+    sr = fetch(h, w.rn2, hr, B);
+    if (sr == BTI_OK) out_rel = max_ratio(hr, hd);
+    return sr;
+  };
+  // The recursive residual of CG drifts from the true one by about the operator's rounding
+  // floor; when it meets tol, the true residual decides, and otherwise replaces it and the
+  // iteration restarts from there (at most kReplace times).
+  constexpr int kReplace = 4;
+  int replaced = 0;
   do {
     st = cuda_check(h, cudaMemsetAsync(w.x, 0, sizeof(double) * Bn, s), "solver init");
     if (st != BTI_OK) break;
@@ -1112,7 +1128,14 @@ bti_status bti_solve_matfree(bti_handle h, const double* d_obs, double* m_map, d
         st = fetch(h, w.rr2, hr, B);
         if (st != BTI_OK) break;
         rel = max_ratio(hr, hd);
-        if (rel <= tol) break;
+        if (rel <= tol) {
+          st = true_residual(rel);
+          if (st != BTI_OK || rel <= tol || !(rel == rel) || replaced == kReplace) break;
+          ++replaced;  // restart from the true residual
+          cudaMemcpyAsync(w.p, w.r, sizeof(double) * Bn, cudaMemcpyDeviceToDevice, s);
+          cudaMemcpyAsync(w.rr, w.rn2, sizeof(double) * B, cudaMemcpyDeviceToDevice, s);
+          continue;
+        }
         count_dense(h, cg_update_p(w.p, w.r, w.rr2, w.rr, n, B, s));
         std::swap(w.rr, w.rr2);
       }
@@ -1185,7 +1208,17 @@ bti_status bti_solve_matfree(bti_handle h, const double* d_obs, double* m_map, d
           st = fetch(h, w.rn2, hr, B);
           if (st != BTI_OK) break;
           rel = max_ratio(hr, hd);
-          if (rel <= tol || !(rel == rel)) break;
+          if (!(rel == rel)) break;
+          if (rel <= tol) {
+            st = true_residual(rel);
+            if (st != BTI_OK || rel <= tol || !(rel == rel) || replaced == kReplace) break;
+            ++replaced;  // restart the flexible iteration from the true residual
+            st = inner_solve(w.r, w.rn2, w.y);
+            if (st != BTI_OK) break;
+            cudaMemcpyAsync(w.p, w.y, sizeof(double) * Bn, cudaMemcpyDeviceToDevice, s);
+            dot(w.r, w.y, w.rz);
+            continue;
+          }
           st = inner_solve(w.r, w.rn2, w.y);
           if (st != BTI_OK) break;
           dot(w.y, w.r, w.zr);    // z_new . r_new
@@ -1199,14 +1232,8 @@ bti_status bti_solve_matfree(bti_handle h, const double* d_obs, double* m_map, d
     }
     if (st != BTI_OK) break;
     if (refine != 1) {  // the recursive CG residual drifts: report the true one
-      st = apply_K_accurate(h, w.x, w.y, B, w);
+      st = true_residual(rel);
       if (st != BTI_OK) break;
-      cudaMemcpyAsync(w.r, d_obs, sizeof(double) * Bn, cudaMemcpyDeviceToDevice, s);
-      count_dense(h, axpby_f64(w.r, w.y, -1.0, 1.0, (int64_t)Bn, s));
-      dot(w.r, w.r, w.rn2);
-      st = fetch(h, w.rn2, hr, B);
-      if (st != BTI_OK) break;
-      rel = max_ratio(hr, hd);
     }
     converged = rel <= tol;
     st = apply_Gstar_accurate(h, w.x, m_map, B, w);
