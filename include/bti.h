@@ -51,7 +51,7 @@ typedef enum {
   BTI_ERR_CUDA = 4,     /* a CUDA runtime call failed */
   BTI_ERR_OOM = 5,      /* device allocation failed */
   BTI_ERR_NOT_SPD = 6,  /* Cholesky met a non-positive or non-finite pivot */
-  BTI_ERR_TIMEOUT = 7,  /* reserved: a bounded device wait gave up */
+  BTI_ERR_TIMEOUT = 7,  /* a bounded device wait gave up (reported by bti_sync) */
   BTI_ERR_NO_CONVERGENCE = 8  /* an iterative solve missed its tolerance within its iteration limit */
 } bti_status;
 
@@ -220,6 +220,14 @@ bti_status bti_apply_postcov(bti_handle h, const double* v, double* out, int64_t
  * m_map not aliased).  refine_iters as bti_infer_map.  Synchronises. */
 bti_status bti_infer_map_prior(bti_handle h, const double* d_obs, const double* m_prior, double* m_map, int64_t B,
                                int refine_iters);
+
+/* Tensor-core products (on = 1, the default): with FP16 spectral blocks and B >= 8
+ * vectors per call (N_m a multiple of 4), the forward products F, F_q run as tcgen05
+ * FP16 GEMMs with FP32 accumulation; the vectors' spectra are rounded to FP16 with a
+ * power-of-two scale per vector and chunk (about 1e-3 relative in total, like the
+ * tier).  on = 0 keeps the CUDA-core FP16 kernels for every B.  A bounded wait that
+ * gives up inside the tensor-core kernel is reported by bti_sync as BTI_ERR_TIMEOUT. */
+bti_status bti_set_tensor_cores(bti_handle h, int on);
 
 /* ---------------------------------------------------------------- matrix-free solve
  * When K = Gamma_noise + F G^* is too large to form (N_d N_t = 252,000 makes it

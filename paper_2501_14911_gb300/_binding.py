@@ -86,6 +86,7 @@ def lib():
         "bti_apply_postcov": ([vp, vp, vp, i64], st),
         "bti_infer_map_prior": ([vp, vp, vp, vp, i64, ip], st),
         "bti_set_shadow": ([vp, ip, ip], st),
+        "bti_set_tensor_cores": ([vp, ip], st),
         "bti_solve_matfree": ([vp, vp, vp, vp, i64, ip, dp, ip, ip, dp, ctypes.POINTER(SolveInfo)], st),
         "bti_apply_Q": ([vp, vp, vp, i64], st),
         "bti_copy_Q": ([vp, vp, vp], st),
@@ -288,6 +289,10 @@ class Handle:
             raise ValueError("batch sizes differ")
         self._check(fn(self._h, _ptr(v), _ptr(out), B))
         return out
+
+    def set_tensor_cores(self, on=True):
+        """Tensor-core FP16 forward products for B >= 8 vectors (on by default)."""
+        self._check(lib().bti_set_tensor_cores(self._h, 1 if on else 0))
 
     def set_shadow(self, op, store):
         """A lower-tier copy of F's or G's spectral blocks for the inner solve."""

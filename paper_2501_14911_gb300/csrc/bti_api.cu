@@ -44,6 +44,7 @@ struct bti_ctx {
   OpStore op[3];
   OpStore shadow[3];  // lower-tier copies for the inner iteration of bti_solve_matfree
   Tune tune[4];  // indexed by bti_prec
+  bool tc_enabled = true;  // tensor-core FP16 products for B >= 8 (bti_set_tensor_cores)
   bti_prec dense_prec = BTI_P_F64;  // arithmetic of K assembly, Cholesky and solves
   bool noise_set = false;
   double sigma2 = 0.0;
@@ -318,7 +319,10 @@ template <typename T>
 bti_status apply_fwd_t(bti_ctx* h, const OpStore& o, const void* in, void* out, int64_t B, bti_prec io) {
   const int64_t nf = h->nf, Nm = h->Nm, R = o.R, Nt = h->Nt;
   size_t n_mhat = (size_t)B * nf * Nm;
+  // FP16 blocks with B >= 8 vectors: the tensor-core product (its own chunking)
+  const bool tc = o.prec == BTI_P_F16 && h->tc_enabled && tc_fwd_f16_supported(Nm, B);
   size_t n_part = prod_fwd_partial_elems(nf, R, Nm, B);
+  if (tc && tc_fwd_partial_elems(nf, R, Nm, B) > n_part) n_part = tc_fwd_partial_elems(nf, R, Nm, B);
   size_t n_dhat = (size_t)B * nf * R;
   bti_status st = ensure(h, &h->ws, &h->ws_bytes, sizeof(C2<T>) * (n_mhat + n_part + n_dhat), "workspace");
   if (st != BTI_OK) return st;
@@ -328,7 +332,17 @@ bti_status apply_fwd_t(bti_ctx* h, const OpStore& o, const void* in, void* out, 
   cudaStream_t s = h->stream;
   rfft_in<T>(h, o, in, Nm, Nt * Nm, mhat, nf * Nm, Nm, B, io);
   const int jc = h->tune[o.prec].jc[fwd_group(B) == 4];
-  if (o.prec == BTI_P_DF64)
+  if (tc) {
+    int nl = 0;
+    cudaError_t e;
+    {
+      ProfScope ps(h, BTI_K_PROD_FWD);  // the MMA kernel and its fixed-order chunk sum
+      e = launch_prod_fwd_f16_tc(o.hat, o.scale, (const float2*)mhat, (float2*)part, (float2*)dhat, nf, R, Nm, B,
+                                 h->status + 1, s, &nl);
+    }
+    h->prof_count[BTI_K_PROD_FWD] += nl - 1;
+    if (e != cudaSuccess) return cuda_check(h, e, "tensor-core forward product");
+  } else if (o.prec == BTI_P_DF64)
     PROF(h, BTI_K_PROD_FWD, launch_prod_fwd_df64((const float4*)o.hat, (const double2*)mhat, (double2*)part, nf,
                                                  R, Nm, B, s, jc));
   else if (o.prec == BTI_P_F16)
@@ -337,7 +351,7 @@ bti_status apply_fwd_t(bti_ctx* h, const OpStore& o, const void* in, void* out, 
   else
     PROF(h, BTI_K_PROD_FWD, (launch_prod_fwd<T, T>((const C2<T>*)o.hat, mhat, part, nf, R, Nm, B, s,
                                                    jc)));
-  PROF(h, BTI_K_REDUCE, (launch_reduce_chunks<T>(part, dhat, nf, R, Nm, B, s, jc)));
+  if (!tc) PROF(h, BTI_K_REDUCE, (launch_reduce_chunks<T>(part, dhat, nf, R, Nm, B, s, jc)));
   // the QoI map writes every qstride-th time step only (N_t / qstride rows per vector)
   const int os = (&o == &h->op[BTI_OP_FQ]) ? h->qstride : 1;
   irfft_out<T>(h, o, dhat, R, nf * R, out, (Nt / os) * R, R, B, io, os);
@@ -472,14 +486,15 @@ bti_status bti_create(int64_t Nm, int64_t Nd, int64_t Nq, int64_t Nt, int device
     delete h;
     return BTI_ERR_OOM;
   }
-  if (cudaMalloc(&h->status, sizeof(int)) != cudaSuccess) {
+  // status[0]: first bad Cholesky pivot; status[1]: a bounded device wait gave up
+  if (cudaMalloc(&h->status, 2 * sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(h->plan.tw64);
     cudaFree(h->plan.tw32);
     delete h;
     return BTI_ERR_OOM;
   }
-  cudaMemset(h->status, 0, sizeof(int));
+  cudaMemset(h->status, 0, 2 * sizeof(int));
   *out = h;
   return BTI_OK;
 }
@@ -939,6 +954,15 @@ bti_status bti_copy_Q(bti_handle h, double* Q_out, double* cov_out) {
     st = cuda_check(h, cudaMemcpyAsync(cov_out, h->covq, sizeof(double) * nq * nq, cudaMemcpyDeviceToDevice,
                                        h->stream), "copy covariance");
   return st;
+}
+
+bti_status bti_set_tensor_cores(bti_handle h, int on) {
+  bti_status st = check_handle(h);
+  if (st != BTI_OK) return st;
+  if (on != 0 && on != 1) return fail(h, BTI_ERR_ARG, "set_tensor_cores: on must be 0 or 1");
+  if (h->tc_enabled != (on == 1)) drop_online_graph_any(h);
+  h->tc_enabled = on == 1;
+  return BTI_OK;
 }
 
 bti_status bti_set_shadow(bti_handle h, bti_op op, bti_prec store) {
@@ -1533,14 +1557,19 @@ bti_status bti_autotune(bti_handle h, bti_op op, int64_t B, char* report, int64_
 bti_status bti_sync(bti_handle h) {
   bti_status st = check_handle(h);
   if (st != BTI_OK) return st;
-  int stat = 0;
-  st = cuda_check(h, cudaMemcpyAsync(&stat, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "status");
+  int stat[2] = {0, 0};
+  st = cuda_check(h, cudaMemcpyAsync(stat, h->status, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream),
+                  "status");
   if (st != BTI_OK) return st;
   st = cuda_check(h, cudaStreamSynchronize(h->stream), "sync");
   if (st != BTI_OK) return st;
   st = launched(h, "sync");
   if (st != BTI_OK) return st;
-  if (stat != 0) return fail(h, BTI_ERR_NOT_SPD, "device status: non-positive pivot " + std::to_string(stat));
+  if (stat[1] != 0) {
+    cudaMemsetAsync(h->status + 1, 0, sizeof(int), h->stream);  // reported once
+    return fail(h, BTI_ERR_TIMEOUT, "device status: a bounded wait in a tensor-core product gave up");
+  }
+  if (stat[0] != 0) return fail(h, BTI_ERR_NOT_SPD, "device status: non-positive pivot " + std::to_string(stat[0]));
   return BTI_OK;
 }
 

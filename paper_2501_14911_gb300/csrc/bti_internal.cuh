@@ -211,6 +211,16 @@ int block_diag_cumsum_all(double* X, int64_t Nt, int64_t R1, int64_t R2, cudaStr
 int noise_residual_f64(double* r, const double* x, const double* diag, int64_t n, int64_t B,
                        cudaStream_t s);
 
+// Tensor-core FP16-tier forward product (tc_f16.cu): for B >= 8 right-hand sides and N_m a
+// multiple of 4.  Writes per-chunk partials into `partial` (tc_fwd_partial_elems elements)
+// and their fixed-order sum into dhat [B][nf][R]; err is set when a bounded device wait
+// gave up.  *launches receives the number of kernels launched.
+bool tc_fwd_f16_supported(int64_t Nm, int64_t B);
+size_t tc_fwd_partial_elems(int64_t nf, int64_t R, int64_t Nm, int64_t B);
+cudaError_t launch_prod_fwd_f16_tc(const void* Fhat, const float* scale, const float2* mhat, float2* partial,
+                                   float2* dhat, int64_t nf, int64_t R, int64_t Nm, int64_t B, int* err,
+                                   cudaStream_t s, int* launches);
+
 // Krylov vector kernels (krylov.cu); vectors [B][n], per-vector scalars on the device.
 // out[b] = x[b] . y[b] in FP64 with a fixed reduction order; part holds
 // dot_workspace_elems(B) doubles.

@@ -1,0 +1,345 @@
+// FP16-tier forward product on the tensor cores (tcgen05) for batches of right-hand sides.
+//
+// For B >= 8 vectors the per-frequency product d-hat_w = F-hat_w m-hat_w (Sec. 4, the
+// block-diagonalised circulant) is a complex GEMM [R x N_m] x [N_m x B].  It runs as a
+// real GEMM whose K axis is the interleaved (real, imaginary) FP16 storage of F-hat
+// itself, K = 2 N_m, and whose N axis holds the real and imaginary outputs, N = 2 B_g:
+//   D[i][2b]   = sum_j F_r(i,j) m_r(b,j) - F_i(i,j) m_i(b,j)
+//   D[i][2b+1] = sum_j F_r(i,j) m_i(b,j) + F_i(i,j) m_r(b,j)
+// so row 2b of the B operand is (m_r, -m_i) and row 2b+1 is (m_i, m_r), interleaved
+// along K.  F-hat tiles [128 rows x 64 halves] stream in by TMA with the 128-byte
+// swizzle; the B tiles are built in shared memory by four warps from the FP32 m-hat
+// (scaled by a power of two per vector and chunk, then rounded to FP16); one thread
+// issues tcgen05.mma (M = 128, K = 16 per instruction) into an FP32 accumulator in
+// tensor memory; the four builder warps read it back (tcgen05.ld), apply the row scale
+// of F-hat and the inverse vector scale, and write per-chunk partial sums, which a
+// second kernel adds in a fixed order.  Every wait is bounded: on a timeout the kernel
+// sets the error word, stops issuing, drains what it issued and frees its tensor memory.
+#include "bti_internal.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_fp16.h>
+
+namespace bti {
+
+namespace {
+
+constexpr int kTcStages = 4;            // pipeline depth (A + B tiles per stage)
+constexpr int kTcRows = 128;            // MMA M: rows of F-hat per CTA
+constexpr int kTcKBox = 64;             // halves per TMA box row (128 bytes, the swizzle width)
+constexpr int kTcThreads = 192;         // warp 0 TMA, warp 1 MMA, warps 2-5 B tiles + epilogue
+constexpr uint32_t kTcATile = kTcRows * 128;  // bytes of one A stage
+constexpr long long kTcSpin = 1ll << 22;      // poll limit of every wait (about a second)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+               : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+  return done != 0;
+}
+// bounded wait; false on timeout or when another thread has flagged an abort
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  for (long long it = 0; it < kTcSpin; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 1023) == 1023 && *abort_flag) return false;
+  }
+  *abort_flag = 1;
+  return false;
+}
+
+template <int BG>
+__global__ void __launch_bounds__(kTcThreads, 1)
+prod_fwd_f16_tc_kernel(const __grid_constant__ CUtensorMap tmA, const float* __restrict__ scaleF,
+                       const float2* __restrict__ mhat, float2* __restrict__ partial, int nf, int R, int64_t Nm,
+                       int B, int Kc, int nchunk, int nrt, int* __restrict__ err) {
+  constexpr int N = 2 * BG;                      // MMA N: real and imaginary output columns
+  constexpr uint32_t kBTile = (uint32_t)N * 128;  // bytes of one B stage
+  constexpr uint32_t kTmemCols = N < 32 ? 32 : N;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  unsigned char* sA = smem;
+  unsigned char* sB = smem + kTcStages * kTcATile;
+  __shared__ uint64_t fullA[kTcStages], fullB[kTcStages], empty[kTcStages], accf;
+  __shared__ uint32_t tmem_holder;
+  __shared__ float inv_scale[BG];
+  __shared__ int abort_flag;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ch = blockIdx.x, w = blockIdx.y;
+  const int rt = blockIdx.z % nrt, grp = blockIdx.z / nrt;
+  const int b0 = grp * BG;
+  const int64_t K2 = 2 * Nm;                      // halves per F-hat row
+  const int64_t kc0 = (int64_t)ch * Kc;
+  const int64_t klen = (K2 - kc0) < Kc ? (K2 - kc0) : Kc;
+  const int nst = (int)((klen + kTcKBox - 1) / kTcKBox);
+
+  if (tid == 0) {
+    for (int s = 0; s < kTcStages; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&fullA[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(smem_u32(&fullB[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&accf)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    abort_flag = 0;
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_holder;
+  volatile int* abort_v = &abort_flag;
+
+  if (warp == 0) {
+    // ---- TMA producer: A stage s holds halves kc0 + 64 s .. + 63 of rows rt*128 .. + 127
+    if (lane == 0) {
+      int issued = 0;
+      for (int s = 0; s < nst; ++s) {
+        const int slot = s % kTcStages;
+        if (s >= kTcStages && !mbar_wait(smem_u32(&empty[slot]), ((s / kTcStages) - 1) & 1, abort_v)) break;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&fullA[slot])),
+                     "r"(kTcATile));
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+            ::"r"(smem_u32(sA + slot * kTcATile)), "l"(&tmA), "r"((int)(kc0 + (int64_t)s * kTcKBox)),
+            "r"(rt * kTcRows), "r"(w), "r"(smem_u32(&fullA[slot]))
+            : "memory");
+        ++issued;
+      }
+      // drain: every issued load lands before the CTA may exit
+      for (int s = (issued > kTcStages ? issued - kTcStages : 0); s < issued; ++s)
+        mbar_wait(smem_u32(&fullA[s % kTcStages]), (s / kTcStages) & 1, abort_v);
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
+      for (int s = 0; s < nst; ++s) {
+        const int slot = s % kTcStages;
+        const uint32_t par = (s / kTcStages) & 1;
+        if (!mbar_wait(smem_u32(&fullA[slot]), par, abort_v)) break;
+        if (!mbar_wait(smem_u32(&fullB[slot]), par, abort_v)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t a0 = smem_u32(sA + slot * kTcATile), bb0 = smem_u32(sB + slot * kBTile);
+#pragma unroll
+        for (int kk = 0; kk < kTcKBox / 16; ++kk) {
+          const uint32_t acc = (s > 0 || kk > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+              ::"r"(tmem), "l"(sdesc(a0 + kk * 32)), "l"(sdesc(bb0 + kk * 32)), "r"(idesc), "r"(acc));
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     ::"r"(smem_u32(&empty[slot])) : "memory");
+      }
+      // the accumulator is complete once every MMA issued above has finished
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                   ::"r"(smem_u32(&accf)) : "memory");
+    }
+  } else {
+    // ---- B-tile builders (128 threads): vector b = b0 + t / 8 (+16 per round), complex
+    // columns 4 (t % 8) .. + 3 of each 32-column stage
+    const int t = tid - 64;
+    const int g = t & 7;
+    constexpr int kRounds = BG / 16;
+    const float2* mw = mhat + (int64_t)w * Nm;
+    const int64_t jc0 = kc0 / 2;
+    const int64_t jlen = klen / 2;
+    // pass 1: max |m| per vector over this chunk -> a power-of-two scale into FP16's range
+#pragma unroll
+    for (int rd = 0; rd < kRounds; ++rd) {
+      const int bl = t / 8 + 16 * rd, b = b0 + bl;
+      float mx = 0.f;
+      if (b < B) {
+        const float2* mb = mw + (int64_t)b * nf * Nm + jc0;
+        for (int64_t j = 4 * g; j < jlen; j += 32) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (j + q < jlen) {
+              const float2 v = __ldg(mb + j + q);
+              mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+            }
+        }
+      }
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 4));
+      if (g == 0) {
+        int e = 0;
+        if (mx > 0.f) frexpf(mx, &e);  // mx = f 2^e, f in [0.5, 1): mx 2^(14-e) < 2^14
+        inv_scale[bl] = ldexpf(1.f, e - 14);
+      }
+    }
+    asm volatile("bar.sync 1, 128;");  // the four builder warps only
+    float sc[kRounds];
+#pragma unroll
+    for (int rd = 0; rd < kRounds; ++rd) sc[rd] = 1.f / inv_scale[t / 8 + 16 * rd];
+    // pass 2: B stages
+    for (int s = 0; s < nst; ++s) {
+      const int slot = s % kTcStages;
+      if (s >= kTcStages && !mbar_wait(smem_u32(&empty[slot]), ((s / kTcStages) - 1) & 1, abort_v)) break;
+      unsigned char* bt = sB + slot * kBTile;
+      const int64_t j = jc0 + (int64_t)s * 32 + 4 * g;  // first of this thread's 4 complex columns
+#pragma unroll
+      for (int rd = 0; rd < kRounds; ++rd) {
+        const int bl = t / 8 + 16 * rd, b = b0 + bl;
+        float2 v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          v[q] = make_float2(0.f, 0.f);
+          if (b < B && j + q < jc0 + jlen) {
+            v[q] = __ldg(mw + (int64_t)b * nf * Nm + j + q);
+            v[q].x *= sc[rd];
+            v[q].y *= sc[rd];
+          }
+        }
+        __half2 re[4], im[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          re[q] = __floats2half2_rn(v[q].x, -v[q].y);  // row 2b:   (m_r, -m_i)
+          im[q] = __floats2half2_rn(v[q].y, v[q].x);   // row 2b+1: (m_i,  m_r)
+        }
+        const int r0 = 2 * bl, r1 = 2 * bl + 1;
+        *reinterpret_cast<uint4*>(bt + r0 * 128 + ((g ^ (r0 & 7)) << 4)) = *reinterpret_cast<uint4*>(re);
+        *reinterpret_cast<uint4*>(bt + r1 * 128 + ((g ^ (r1 & 7)) << 4)) = *reinterpret_cast<uint4*>(im);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&fullB[slot])) : "memory");
+    }
+    // ---- epilogue: rows of this warp's lane quarter, all N accumulator columns
+    const bool ok = mbar_wait(smem_u32(&accf), 0, abort_v);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const int q4 = warp & 3;
+    const int i = rt * kTcRows + q4 * 32 + lane;
+    const float fs = (ok && i < R) ? scaleF[(int64_t)w * R + i] : 0.f;
+#pragma unroll
+    for (int c0 = 0; c0 < N; c0 += 8) {
+      uint32_t v[8];
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                   : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                   : "r"(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)c0));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (ok && i < R) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int bl = c0 / 2 + q, b = b0 + bl;
+          if (b < B) {
+            const float f = fs * inv_scale[bl];
+            partial[(((int64_t)b * nf + w) * nchunk + ch) * R + i] =
+                make_float2(__uint_as_float(v[2 * q]) * f, __uint_as_float(v[2 * q + 1]) * f);
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 1) {
+    // the MMAs have completed if accf fired; otherwise wait for them (bounded) before freeing
+    if (*abort_v) {
+      int dummy = 0;
+      mbar_wait(smem_u32(&accf), 0, &dummy);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+  }
+  if (tid == 0 && *abort_v) atomicExch(err, 1);
+}
+
+// dhat[b][w][i] = sum over the nchunk partials, fixed order
+__global__ void tc_reduce_kernel(const float2* __restrict__ partial, float2* __restrict__ dhat, int64_t total,
+                                 int64_t R, int nchunk) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const int64_t bw = idx / R, i = idx - bw * R;
+  const float2* p = partial + bw * nchunk * R + i;
+  float sr = 0.f, si = 0.f;
+  for (int c = 0; c < nchunk; ++c) {
+    const float2 v = p[(int64_t)c * R];
+    sr += v.x;
+    si += v.y;
+  }
+  dhat[idx] = make_float2(sr, si);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+}  // namespace
+
+bool tc_fwd_f16_supported(int64_t Nm, int64_t B) {
+  // rows of F-hat as FP16 halves must be 16-byte strided for TMA (N_m a multiple of 4)
+  return B >= 8 && Nm % 4 == 0 && 2 * Nm <= INT32_MAX && encode_fn() != nullptr;
+}
+
+size_t tc_fwd_partial_elems(int64_t nf, int64_t R, int64_t Nm, int64_t B) {
+  // at most ceil(2 N_m / 1024) chunks (chunks are at least 1024 halves)
+  return (size_t)(B * nf * ((2 * Nm + 1023) / 1024) * R);
+}
+
+cudaError_t launch_prod_fwd_f16_tc(const void* Fhat, const float* scale, const float2* mhat, float2* partial,
+                                   float2* dhat, int64_t nf, int64_t R, int64_t Nm, int64_t B, int* err,
+                                   cudaStream_t s, int* launches) {
+  *launches = 0;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  CUtensorMap tm;
+  const cuuint64_t dims[3] = {(cuuint64_t)(2 * Nm), (cuuint64_t)R, (cuuint64_t)nf};
+  const cuuint64_t strides[2] = {(cuuint64_t)(2 * Nm * 2), (cuuint64_t)(R * 2 * Nm * 2)};
+  const cuuint32_t box[3] = {(cuuint32_t)kTcKBox, (cuuint32_t)kTcRows, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<void*>(Fhat), dims, strides, box, es,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  const int BG = B > 16 ? 32 : 16;
+  const int64_t nrt = (R + kTcRows - 1) / kTcRows, ng = (B + BG - 1) / BG;
+  // enough chunks along K for about four CTAs per SM in total; chunks of >= 1024 halves
+  const int64_t tiles = nf * nrt * ng;
+  int64_t nchunk = (608 + tiles - 1) / tiles;
+  int64_t Kc = ((2 * Nm + nchunk - 1) / nchunk + kTcKBox - 1) / kTcKBox * kTcKBox;
+  if (Kc < 1024) Kc = 1024;
+  nchunk = (2 * Nm + Kc - 1) / Kc;
+  if (nf > 65535 || nrt * ng > 65535 || nchunk > INT32_MAX) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)nchunk, (unsigned)nf, (unsigned)(nrt * ng));
+  const size_t smem = 1024 + kTcStages * (kTcATile + (size_t)2 * BG * 128);
+  if (BG == 16) {
+    cudaFuncSetAttribute(prod_fwd_f16_tc_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    prod_fwd_f16_tc_kernel<16><<<grid, kTcThreads, smem, s>>>(tm, scale, mhat, partial, (int)nf, (int)R, Nm, (int)B,
+                                                              (int)Kc, (int)nchunk, (int)nrt, err);
+  } else {
+    cudaFuncSetAttribute(prod_fwd_f16_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    prod_fwd_f16_tc_kernel<32><<<grid, kTcThreads, smem, s>>>(tm, scale, mhat, partial, (int)nf, (int)R, Nm, (int)B,
+                                                              (int)Kc, (int)nchunk, (int)nrt, err);
+  }
+  const int64_t total = B * nf * R;
+  tc_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(partial, dhat, total, R, (int)nchunk);
+  *launches = 2;
+  return cudaGetLastError();
+}
+
+}  // namespace bti

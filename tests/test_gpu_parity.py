@@ -60,6 +60,10 @@ CASES = [
     ("Nt1_gemv", 257, 5, 3, 1, 2),
     ("scalar", 1, 1, 1, 16, 2),
     ("R1100_row_tiles", 600, 1100, 3, 20, 5),  # adjoint stages d-hat in 512-row tiles
+    # FP16 tier with B >= 8: tensor-core forward product (row tiles of 128, groups of 16/32)
+    ("tc_b16", 4096, 128, 4, 64, 16),
+    ("tc_b10_rows200_L90", 3000, 200, 5, 45, 10),
+    ("tc_b40_groups", 1024, 13, 3, 32, 40),
 ]
 
 
@@ -126,6 +130,30 @@ def test_tuned_launch_shapes_serve_every_batch_size(store):
         assert relb(host(od), oracle.p2o_apply(F, host(m_g))) < TOL[store], B
         assert relb(host(om), oracle.p2o_apply_adjoint(F, host(d_g))) < TOL[store], B
     h.close()
+
+
+@pytest.mark.parametrize("B", [8, 16, 33])
+def test_tensor_core_forward_matches_cuda_core_path(B):
+    """The tcgen05 FP16 forward product against the CUDA-core FP16 kernel and the oracle:
+    both within the FP16 tier's 1e-3, and within 1e-3 of each other (they differ by the
+    rounding of m-hat to FP16)."""
+    p = synthetic.small("tc_vs_cuda", 1, 2048, 130, 48, Nq=4)
+    F = p.blocks_F()
+    h = make_handle(F, None, bti.F16)
+    m = cuda(p.vectors_m(B), torch.float32)
+    d_tc = torch.empty((B, 48, 130), dtype=torch.float32, device="cuda")
+    d_cc = torch.empty_like(d_tc)
+    h.apply_F(m, d_tc)
+    h.sync()
+    h.set_tensor_cores(False)
+    h.apply_F(m, d_cc)
+    h.sync()
+    h.close()
+    ref = oracle.p2o_apply(F, host(m))
+    assert relb(host(d_tc), ref) < 1e-3
+    assert relb(host(d_cc), ref) < 1e-3
+    assert relb(host(d_tc), host(d_cc)) < 1e-3
+    assert relb(host(d_tc), host(d_cc)) > 0.0  # the tensor-core path really ran
 
 
 def test_impulse_response_and_causality():
