@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--case", choices=["sweep", "small"], default="sweep",
-                    help="small: the sweep shape with N_m = 4096 and 2 vectors (2.2 GB of FP64 spectral "
+                    help="small: the sweep shape with N_m = 4096 and 16 vectors (2.2 GB of FP64 spectral "
                          "blocks, still far above L2) for ncu captures; implies --no-online, "
                          "--no-mixed, --no-cpu-baseline and --no-e2e")
     a = ap.parse_args()
@@ -60,7 +60,7 @@ def workload(args):
 
     if args.case == "small":
         return synthetic.Problem("matvec_sweep_small_Nm4096_Nd128_Nt256", 6, 64, 64, 128, 256, 32, 64.0,
-                                 n_vectors=2)
+                                 n_vectors=16)
     return synthetic.SWEEP
 
 

@@ -370,7 +370,17 @@ bti_status apply_adj_t(bti_ctx* h, const OpStore& o, const void* in, void* out, 
   C2<T>* mhat = dhat + n_dhat;
   cudaStream_t s = h->stream;
   rfft_in<T>(h, o, in, R, Nt * R, dhat, nf * R, R, B, io);
-  if (o.prec == BTI_P_DF64)
+  if (o.prec == BTI_P_F16 && h->tc_enabled && tc_adj_f16_supported(Nm, R, B)) {
+    int nl = 0;
+    cudaError_t e;
+    {
+      ProfScope ps(h, BTI_K_PROD_ADJ);
+      e = launch_prod_adj_f16_tc(o.hat, o.scale, (const float2*)dhat, (float2*)mhat, nf, R, Nm, B, h->status + 1, s,
+                                 &nl);
+    }
+    h->prof_count[BTI_K_PROD_ADJ] += nl - 1;
+    if (e != cudaSuccess) return cuda_check(h, e, "tensor-core adjoint product");
+  } else if (o.prec == BTI_P_DF64)
     PROF(h, BTI_K_PROD_ADJ, launch_prod_adj_df64((const float4*)o.hat, (const double2*)dhat, (double2*)mhat, nf,
                                                  R, Nm, B, s, h->tune[o.prec].vpt));
   else if (o.prec == BTI_P_F16)

@@ -220,6 +220,12 @@ size_t tc_fwd_partial_elems(int64_t nf, int64_t R, int64_t Nm, int64_t B);
 cudaError_t launch_prod_fwd_f16_tc(const void* Fhat, const float* scale, const float2* mhat, float2* partial,
                                    float2* dhat, int64_t nf, int64_t R, int64_t Nm, int64_t B, int* err,
                                    cudaStream_t s, int* launches);
+// Adjoint: mhat [B][nf][N_m] = F-hat^H (scale-folded dhat) for B >= 8 and N_d up to 2048 (16
+// vectors per group) or 1024 (32 per group); no partials.
+bool tc_adj_f16_supported(int64_t Nm, int64_t R, int64_t B);
+cudaError_t launch_prod_adj_f16_tc(const void* Fhat, const float* scale, const float2* dhat, float2* mhat,
+                                   int64_t nf, int64_t R, int64_t Nm, int64_t B, int* err, cudaStream_t s,
+                                   int* launches);
 
 // Krylov vector kernels (krylov.cu); vectors [B][n], per-vector scalars on the device.
 // out[b] = x[b] . y[b] in FP64 with a fixed reduction order; part holds

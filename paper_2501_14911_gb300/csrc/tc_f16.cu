@@ -1,4 +1,4 @@
-// FP16-tier forward product on the tensor cores (tcgen05) for batches of right-hand sides.
+// FP16-tier spectral products on the tensor cores (tcgen05) for batches of right-hand sides.
 //
 // For B >= 8 vectors the per-frequency product d-hat_w = F-hat_w m-hat_w (Sec. 4, the
 // block-diagonalised circulant) is a complex GEMM [R x N_m] x [N_m x B].  It runs as a
@@ -258,6 +258,221 @@ prod_fwd_f16_tc_kernel(const __grid_constant__ CUtensorMap tmA, const float* __r
   if (tid == 0 && *abort_v) atomicExch(err, 1);
 }
 
+// Adjoint: m-hat_w[b][j] = sum_i conj(F-hat_w[i][j]) s_F(w, i) d-hat_w[b][i].  Read along
+// its interleaved (real, imaginary) axis m' = 2 j + c, the FP16 storage of F-hat is an
+// MN-major operand A'[m'][i] (m' contiguous for each row i), so with K = R and B rows
+// (d_r s_F, d_i s_F) the MMA gives D'[m'][n] = sum_i A'[m'][i] B[n][i], and
+//   Re m-hat(b, j) = D'[2j][2b] + D'[2j+1][2b+1],  Im m-hat(b, j) = D'[2j][2b+1] - D'[2j+1][2b]:
+// rows 2j and 2j+1 sit in neighbouring TMEM lanes and are combined with one shuffle.
+// A CTA covers one frequency, one vector group and a run of 128-row tiles of m'; the B
+// operand (all of K) is built once, and two TMEM accumulators let the epilogue of one
+// tile overlap the MMAs of the next.
+template <int BG>
+__global__ void __launch_bounds__(kTcThreads, 1)
+prod_adj_f16_tc_kernel(const __grid_constant__ CUtensorMap tmA, const float* __restrict__ scaleF,
+                       const float2* __restrict__ dhat, float2* __restrict__ mhat, int nf, int R, int64_t Nm,
+                       int B, int tpc, int ntiles, int* __restrict__ err) {
+  constexpr int N = 2 * BG;
+  constexpr uint32_t kBTile = (uint32_t)N * 128;  // one 64-row K block of the B operand
+  constexpr uint32_t kTmemCols = 2 * N;           // two accumulators
+  constexpr uint32_t kHalf = 64 * 128;            // one 64-wide half of an A stage: 64 rows of i x 128 B
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  unsigned char* sA = smem;
+  unsigned char* sB = smem + kTcStages * kTcATile;
+  __shared__ uint64_t fullA[kTcStages], empty[kTcStages], bfull, accf[2], acce[2], mdone;
+  __shared__ uint32_t tmem_holder;
+  __shared__ float inv_scale[BG];
+  __shared__ int abort_flag;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int w = blockIdx.y, grp = blockIdx.z, b0 = grp * BG;
+  const int t0 = blockIdx.x * tpc;
+  const int nt = (ntiles - t0) < tpc ? (ntiles - t0) : tpc;
+  const int nkb = (R + 63) / 64;
+  const int nq = nt * nkb;
+
+  if (tid == 0) {
+    for (int s = 0; s < kTcStages; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&fullA[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(smem_u32(&bfull)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mdone)));
+    for (int a = 0; a < 2; ++a) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&accf[a])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(smem_u32(&acce[a])));
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    abort_flag = 0;
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_holder;
+  volatile int* abort_v = &abort_flag;
+
+  if (warp == 0) {
+    // ---- TMA producer: stage q = (tile, K block); two boxes of 64 m' x 64 rows of i
+    if (lane == 0) {
+      int issued = 0;
+      for (int q = 0; q < nq; ++q) {
+        const int slot = q % kTcStages;
+        if (q >= kTcStages && !mbar_wait(smem_u32(&empty[slot]), ((q / kTcStages) - 1) & 1, abort_v)) break;
+        const int t = t0 + q / nkb, kb = q % nkb;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&fullA[slot])),
+                     "r"(kTcATile));
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh)
+          asm volatile(
+              "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+              ::"r"(smem_u32(sA + slot * kTcATile + hh * kHalf)), "l"(&tmA), "r"(kTcRows * t + 64 * hh), "r"(64 * kb),
+              "r"(w), "r"(smem_u32(&fullA[slot]))
+              : "memory");
+        ++issued;
+      }
+      for (int q = (issued > kTcStages ? issued - kTcStages : 0); q < issued; ++q)
+        mbar_wait(smem_u32(&fullA[q % kTcStages]), (q / kTcStages) & 1, abort_v);
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer: A MN-major (bit 15), B K-major
+    if (lane == 0) {
+      const uint32_t idesc =
+          (1u << 4) | (1u << 15) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
+      bool ok = mbar_wait(smem_u32(&bfull), 0, abort_v);
+      for (int tt = 0; ok && tt < nt; ++tt) {
+        const int acc = tt & 1;
+        if (tt >= 2 && !mbar_wait(smem_u32(&acce[acc]), ((tt >> 1) - 1) & 1, abort_v)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        for (int kb = 0; kb < nkb; ++kb) {
+          const int q = tt * nkb + kb, slot = q % kTcStages;
+          if (!mbar_wait(smem_u32(&fullA[slot]), (q / kTcStages) & 1, abort_v)) { ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t a0 = smem_u32(sA + slot * kTcATile), bb0 = smem_u32(sB + kb * kBTile);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            // A: 16 rows of i per step (2048 B); the two m' halves 8 KB apart (leading byte
+            // offset), 8-row groups 1024 B apart (stride byte offset)
+            const uint64_t ad = (uint64_t)(((a0 + kk * 2048) >> 4) & 0x3FFF) | ((uint64_t)(kHalf >> 4) << 16) |
+                                ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+            const uint32_t accum = (kb > 0 || kk > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                ::"r"(tmem + (uint32_t)(acc * N)), "l"(ad), "l"(sdesc(bb0 + kk * 32)), "r"(idesc), "r"(accum));
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                       ::"r"(smem_u32(&empty[slot])) : "memory");
+        }
+        if (!ok) break;
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     ::"r"(smem_u32(&accf[acc])) : "memory");
+      }
+      // completes once every MMA issued above has finished (the teardown waits on it)
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                   ::"r"(smem_u32(&mdone)) : "memory");
+    }
+  } else {
+    // ---- B operand builders: vector b = b0 + t / 8 (+16 per round); row chunk g of 8 rows of i
+    const int t = tid - 64, g = t & 7;
+    constexpr int kRounds = BG / 16;
+    const float* sf = scaleF + (int64_t)w * R;
+#pragma unroll
+    for (int rd = 0; rd < kRounds; ++rd) {
+      const int bl = t / 8 + 16 * rd, b = b0 + bl;
+      float mx = 0.f;
+      if (b < B) {
+        const float2* db = dhat + ((int64_t)b * nf + w) * R;
+        for (int i = g; i < R; i += 8) {
+          const float2 v = db[i];
+          const float f = sf[i];
+          mx = fmaxf(mx, fmaxf(fabsf(v.x * f), fabsf(v.y * f)));
+        }
+      }
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 4));
+      if (g == 0) {
+        int e = 0;
+        if (mx > 0.f) frexpf(mx, &e);
+        inv_scale[bl] = ldexpf(1.f, e - 14);
+      }
+    }
+    asm volatile("bar.sync 1, 128;");
+#pragma unroll
+    for (int rd = 0; rd < kRounds; ++rd) {
+      const int bl = t / 8 + 16 * rd, b = b0 + bl;
+      const float sc = 1.f / inv_scale[bl];
+      const float2* db = dhat + ((int64_t)b * nf + w) * R;
+      for (int kb = 0; kb < nkb; ++kb) {
+        __half re[8], im[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int i = 64 * kb + 8 * g + e;
+          float2 v = make_float2(0.f, 0.f);
+          if (b < B && i < R) {
+            v = db[i];
+            const float f = sf[i] * sc;
+            v.x *= f;
+            v.y *= f;
+          }
+          re[e] = __float2half_rn(v.x);  // row 2b:   d_r s_F
+          im[e] = __float2half_rn(v.y);  // row 2b+1: d_i s_F
+        }
+        unsigned char* bt = sB + kb * kBTile;
+        const int r0 = 2 * bl, r1 = 2 * bl + 1;
+        *reinterpret_cast<uint4*>(bt + r0 * 128 + ((g ^ (r0 & 7)) << 4)) = *reinterpret_cast<uint4*>(re);
+        *reinterpret_cast<uint4*>(bt + r1 * 128 + ((g ^ (r1 & 7)) << 4)) = *reinterpret_cast<uint4*>(im);
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bfull)) : "memory");
+    // ---- epilogue per tile
+    const int q4 = warp & 3;
+    for (int tt = 0; tt < nt; ++tt) {
+      const int acc = tt & 1;
+      const bool ok = mbar_wait(smem_u32(&accf[acc]), (tt >> 1) & 1, abort_v);
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const int64_t mrow = (int64_t)kTcRows * (t0 + tt) + q4 * 32 + lane;  // m' = 2 j + c
+      const int64_t j = mrow >> 1;
+#pragma unroll
+      for (int c0 = 0; c0 < N; c0 += 8) {
+        uint32_t v[8];
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                     : "r"(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(acc * N + c0)));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) {
+          const float x0 = __uint_as_float(v[2 * qq]), x1 = __uint_as_float(v[2 * qq + 1]);
+          const float u0 = __shfl_xor_sync(0xffffffffu, x0, 1), u1 = __shfl_xor_sync(0xffffffffu, x1, 1);
+          const int bl = c0 / 2 + qq, b = b0 + bl;
+          if (ok && (lane & 1) == 0 && b < B && j < Nm) {
+            const float f = inv_scale[bl];
+            mhat[((int64_t)b * nf + w) * Nm + j] = make_float2((x0 + u1) * f, (x1 - u0) * f);
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[acc])) : "memory");
+      if (!ok) break;
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 1) {
+    int dummy = 0;  // every MMA issued has finished before the columns are freed
+    mbar_wait(smem_u32(&mdone), 0, &dummy);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+  }
+  if (tid == 0 && *abort_v) atomicExch(err, 1);
+}
+
 // dhat[b][w][i] = sum over the nchunk partials, fixed order
 __global__ void tc_reduce_kernel(const float2* __restrict__ partial, float2* __restrict__ dhat, int64_t total,
                                  int64_t R, int nchunk) {
@@ -339,6 +554,51 @@ cudaError_t launch_prod_fwd_f16_tc(const void* Fhat, const float* scale, const f
   const int64_t total = B * nf * R;
   tc_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(partial, dhat, total, R, (int)nchunk);
   *launches = 2;
+  return cudaGetLastError();
+}
+
+bool tc_adj_f16_supported(int64_t Nm, int64_t R, int64_t B) {
+  const int64_t BG = B > 16 ? 32 : 16;
+  // the whole B operand (R rows of i in 64-row blocks) stays in shared memory
+  return B >= 8 && Nm % 4 == 0 && 2 * Nm <= INT32_MAX && ((R + 63) / 64) * 2 * BG * 128 <= 128 * 1024 &&
+         encode_fn() != nullptr;
+}
+
+cudaError_t launch_prod_adj_f16_tc(const void* Fhat, const float* scale, const float2* dhat, float2* mhat,
+                                   int64_t nf, int64_t R, int64_t Nm, int64_t B, int* err, cudaStream_t s,
+                                   int* launches) {
+  *launches = 0;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  CUtensorMap tm;
+  const cuuint64_t dims[3] = {(cuuint64_t)(2 * Nm), (cuuint64_t)R, (cuuint64_t)nf};
+  const cuuint64_t strides[2] = {(cuuint64_t)(2 * Nm * 2), (cuuint64_t)(R * 2 * Nm * 2)};
+  const cuuint32_t box[3] = {64, 64, 1};  // 64 m' (128 bytes) x 64 rows of i
+  const cuuint32_t es[3] = {1, 1, 1};
+  if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<void*>(Fhat), dims, strides, box, es,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  const int BG = B > 16 ? 32 : 16;
+  const int64_t ng = (B + BG - 1) / BG, ntiles = (2 * Nm + kTcRows - 1) / kTcRows;
+  // runs of tiles per CTA: about eight CTAs per SM in total
+  const int64_t work = ntiles * nf * ng;
+  int64_t tpc = (work + 1215) / 1216;
+  if (tpc < 1) tpc = 1;
+  const int64_t nblk = (ntiles + tpc - 1) / tpc;
+  if (nf > 65535 || ng > 65535 || nblk > INT32_MAX) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)nblk, (unsigned)nf, (unsigned)ng);
+  const size_t smem = 1024 + kTcStages * (size_t)kTcATile + (size_t)((R + 63) / 64) * 2 * BG * 128;
+  if (BG == 16) {
+    cudaFuncSetAttribute(prod_adj_f16_tc_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    prod_adj_f16_tc_kernel<16><<<grid, kTcThreads, smem, s>>>(tm, scale, dhat, mhat, (int)nf, (int)R, Nm, (int)B,
+                                                              (int)tpc, (int)ntiles, err);
+  } else {
+    cudaFuncSetAttribute(prod_adj_f16_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    prod_adj_f16_tc_kernel<32><<<grid, kTcThreads, smem, s>>>(tm, scale, dhat, mhat, (int)nf, (int)R, Nm, (int)B,
+                                                              (int)tpc, (int)ntiles, err);
+  }
+  *launches = 1;
   return cudaGetLastError();
 }
 

@@ -133,27 +133,32 @@ def test_tuned_launch_shapes_serve_every_batch_size(store):
 
 
 @pytest.mark.parametrize("B", [8, 16, 33])
-def test_tensor_core_forward_matches_cuda_core_path(B):
-    """The tcgen05 FP16 forward product against the CUDA-core FP16 kernel and the oracle:
-    both within the FP16 tier's 1e-3, and within 1e-3 of each other (they differ by the
-    rounding of m-hat to FP16)."""
+def test_tensor_core_products_match_cuda_core_path(B):
+    """The tcgen05 FP16 forward and adjoint products against the CUDA-core FP16 kernels and
+    the oracle: all within the FP16 tier's 1e-3, and the two paths within 1e-3 of each
+    other (they differ by the rounding of the vectors' spectra to FP16)."""
     p = synthetic.small("tc_vs_cuda", 1, 2048, 130, 48, Nq=4)
     F = p.blocks_F()
     h = make_handle(F, None, bti.F16)
     m = cuda(p.vectors_m(B), torch.float32)
-    d_tc = torch.empty((B, 48, 130), dtype=torch.float32, device="cuda")
-    d_cc = torch.empty_like(d_tc)
-    h.apply_F(m, d_tc)
-    h.sync()
-    h.set_tensor_cores(False)
-    h.apply_F(m, d_cc)
-    h.sync()
+    d = cuda(p.vectors_d(B), torch.float32)
+    out = {}
+    for tc in (True, False):
+        h.set_tensor_cores(tc)
+        od = torch.empty((B, 48, 130), dtype=torch.float32, device="cuda")
+        om = torch.empty((B, 48, 2048), dtype=torch.float32, device="cuda")
+        h.apply_F(m, od)
+        h.apply_FT(d, om)
+        h.sync()  # also reports a tensor-core wait that gave up
+        out[tc] = (host(od), host(om))
     h.close()
-    ref = oracle.p2o_apply(F, host(m))
-    assert relb(host(d_tc), ref) < 1e-3
-    assert relb(host(d_cc), ref) < 1e-3
-    assert relb(host(d_tc), host(d_cc)) < 1e-3
-    assert relb(host(d_tc), host(d_cc)) > 0.0  # the tensor-core path really ran
+    ref_d = oracle.p2o_apply(F, host(m))
+    ref_m = oracle.p2o_apply_adjoint(F, host(d))
+    for tc in (True, False):
+        assert relb(out[tc][0], ref_d) < 1e-3, tc
+        assert relb(out[tc][1], ref_m) < 1e-3, tc
+    for k in (0, 1):
+        assert 0.0 < relb(out[True][k], out[False][k]) < 1e-3  # the tensor-core path really ran
 
 
 def test_impulse_response_and_causality():
