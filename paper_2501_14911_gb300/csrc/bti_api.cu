@@ -1492,7 +1492,22 @@ bti_status bti_autotune(bti_handle h, bti_op op, int64_t B, char* report, int64_
   auto adj = [&]() { apply_op(h, op, true, vout, vin, B, BTI_P_F64, "autotune"); };
   std::string rep = "{\"op\": " + std::to_string((int)op) + ", \"tier\": " + std::to_string((int)o.prec) +
                     ", \"B\": " + std::to_string(B);
-  // 1. column pairs per FFT CTA (forward call: dominated by the FFT of the long vector)
+  // 1. column pairs per FFT CTA, timed on the transforms alone: the forward FFT of the
+  //    N_m-column input and the inverse FFT back to N_m columns (within a whole call the
+  //    products' time would drown the difference)
+  fwd();  // sizes the spectral workspace for B vectors
+  const int64_t nf = h->nf;
+  auto ffts = [&]() {
+    if (double_path(o.prec)) {
+      C2<double>* X = (C2<double>*)h->ws;
+      rfft_in<double>(h, o, vin, Nm, Nt * Nm, X, nf * Nm, Nm, B, BTI_P_F64);
+      irfft_out<double>(h, o, X, Nm, nf * Nm, vout, Nt * Nm, Nm, B, BTI_P_F64);
+    } else {
+      C2<float>* X = (C2<float>*)h->ws;
+      rfft_in<float>(h, o, vin, Nm, Nt * Nm, X, nf * Nm, Nm, B, BTI_P_F64);
+      irfft_out<float>(h, o, X, Nm, nf * Nm, vout, Nt * Nm, Nm, B, BTI_P_F64);
+    }
+  };
   {
     int best = 0;
     float best_ms = 1e30f;
@@ -1500,7 +1515,7 @@ bti_status bti_autotune(bti_handle h, bti_op op, int64_t B, char* report, int64_
     bool first = true;
     for (int p = h->plan.P; p >= 1; p /= 2) {
       t.fft_p = p;
-      float ms = time_ms(h, fwd, 3);
+      float ms = time_ms(h, ffts, 5);
       rep += std::string(first ? "" : ", ") + "\"" + std::to_string(p) + "\": " + std::to_string(ms);
       first = false;
       if (ms < best_ms) { best_ms = ms; best = p; }

@@ -157,20 +157,25 @@ prod_fwd_f16_tc_kernel(const __grid_constant__ CUtensorMap tmA, const float* __r
     const float2* mw = mhat + (int64_t)w * Nm;
     const int64_t jc0 = kc0 / 2;
     const int64_t jlen = klen / 2;
-    // pass 1: max |m| per vector over this chunk -> a power-of-two scale into FP16's range
+    // pass 1: max |m| per vector over this chunk -> a power-of-two scale into FP16's range.
+    // Four 32-byte loads per thread per trip keep enough requests in flight.
 #pragma unroll
     for (int rd = 0; rd < kRounds; ++rd) {
       const int bl = t / 8 + 16 * rd, b = b0 + bl;
       float mx = 0.f;
       if (b < B) {
         const float2* mb = mw + (int64_t)b * nf * Nm + jc0;
-        for (int64_t j = 4 * g; j < jlen; j += 32) {
+        for (int64_t j0 = 4 * g; j0 < jlen; j0 += 128) {
+          float2 v[16];
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
-            if (j + q < jlen) {
-              const float2 v = __ldg(mb + j + q);
-              mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int64_t j = j0 + 32 * u + q;
+              v[4 * u + q] = j < jlen ? __ldg(mb + j) : make_float2(0.f, 0.f);
             }
+#pragma unroll
+          for (int e = 0; e < 16; ++e) mx = fmaxf(mx, fmaxf(fabsf(v[e].x), fabsf(v[e].y)));
         }
       }
       mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
@@ -186,30 +191,35 @@ prod_fwd_f16_tc_kernel(const __grid_constant__ CUtensorMap tmA, const float* __r
     float sc[kRounds];
 #pragma unroll
     for (int rd = 0; rd < kRounds; ++rd) sc[rd] = 1.f / inv_scale[t / 8 + 16 * rd];
-    // pass 2: B stages
+    // pass 2: B stages.  The m-hat values of stage s + 1 are loaded before the wait for stage
+    // s's slot, so their latency overlaps the pipeline instead of adding to it.
+    auto load_stage = [&](int st, float2 (&v)[kRounds][4]) {
+      const int64_t j = jc0 + (int64_t)st * 32 + 4 * g;  // first of this thread's 4 complex columns
+#pragma unroll
+      for (int rd = 0; rd < kRounds; ++rd) {
+        const int b = b0 + t / 8 + 16 * rd;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          v[rd][q] = (st < nst && b < B && j + q < jc0 + jlen) ? __ldg(mw + (int64_t)b * nf * Nm + j + q)
+                                                               : make_float2(0.f, 0.f);
+      }
+    };
+    float2 cur[kRounds][4], nxt[kRounds][4];
+    load_stage(0, cur);
     for (int s = 0; s < nst; ++s) {
+      load_stage(s + 1, nxt);
       const int slot = s % kTcStages;
       if (s >= kTcStages && !mbar_wait(smem_u32(&empty[slot]), ((s / kTcStages) - 1) & 1, abort_v)) break;
       unsigned char* bt = sB + slot * kBTile;
-      const int64_t j = jc0 + (int64_t)s * 32 + 4 * g;  // first of this thread's 4 complex columns
 #pragma unroll
       for (int rd = 0; rd < kRounds; ++rd) {
-        const int bl = t / 8 + 16 * rd, b = b0 + bl;
-        float2 v[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          v[q] = make_float2(0.f, 0.f);
-          if (b < B && j + q < jc0 + jlen) {
-            v[q] = __ldg(mw + (int64_t)b * nf * Nm + j + q);
-            v[q].x *= sc[rd];
-            v[q].y *= sc[rd];
-          }
-        }
+        const int bl = t / 8 + 16 * rd;
         __half2 re[4], im[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          re[q] = __floats2half2_rn(v[q].x, -v[q].y);  // row 2b:   (m_r, -m_i)
-          im[q] = __floats2half2_rn(v[q].y, v[q].x);   // row 2b+1: (m_i,  m_r)
+          const float x = cur[rd][q].x * sc[rd], y = cur[rd][q].y * sc[rd];
+          re[q] = __floats2half2_rn(x, -y);  // row 2b:   (m_r, -m_i)
+          im[q] = __floats2half2_rn(y, x);   // row 2b+1: (m_i,  m_r)
         }
         const int r0 = 2 * bl, r1 = 2 * bl + 1;
         *reinterpret_cast<uint4*>(bt + r0 * 128 + ((g ^ (r0 & 7)) << 4)) = *reinterpret_cast<uint4*>(re);
@@ -217,6 +227,10 @@ prod_fwd_f16_tc_kernel(const __grid_constant__ CUtensorMap tmA, const float* __r
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&fullB[slot])) : "memory");
+#pragma unroll
+      for (int rd = 0; rd < kRounds; ++rd)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) cur[rd][q] = nxt[rd][q];
     }
     // ---- epilogue: rows of this warp's lane quarter, all N accumulator columns
     const bool ok = mbar_wait(smem_u32(&accf), 0, abort_v);
@@ -533,10 +547,13 @@ cudaError_t launch_prod_fwd_f16_tc(const void* Fhat, const float* scale, const f
     return cudaErrorInvalidValue;
   const int BG = B > 16 ? 32 : 16;
   const int64_t nrt = (R + kTcRows - 1) / kTcRows, ng = (B + BG - 1) / BG;
-  // enough chunks along K for about four CTAs per SM in total; chunks of >= 1024 halves
+  // Chunks along K: at least four CTAs per SM in total, and at most 4096 halves per chunk so
+  // that a CTA's m-hat chunk (B_g x 2048 complex, 256 KB at B_g = 16) is still in L2 when
+  // the B tiles are built right after the scale pass reads it; at least 1024 halves.
   const int64_t tiles = nf * nrt * ng;
   int64_t nchunk = (608 + tiles - 1) / tiles;
   int64_t Kc = ((2 * Nm + nchunk - 1) / nchunk + kTcKBox - 1) / kTcKBox * kTcKBox;
+  if (Kc > 4096) Kc = 4096;
   if (Kc < 1024) Kc = 1024;
   nchunk = (2 * Nm + Kc - 1) / Kc;
   if (nf > 65535 || nrt * ng > 65535 || nchunk > INT32_MAX) return cudaErrorInvalidValue;
