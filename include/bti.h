@@ -243,6 +243,16 @@ bti_status bti_set_tensor_cores(bti_handle h, int on);
  * copy.  Synchronises. */
 bti_status bti_set_shadow(bti_handle h, bti_op op, bti_prec store);
 
+/* Block-Jacobi preconditioner for bti_solve_matfree (kind = 1; 0 removes it): the inverses
+ * of K's N_t time-diagonal blocks K(t,t) = Gamma_noise(t) + sum_{k <= t} F_k G_k^T
+ * (N_d x N_d each, N_t N_d^2 doubles), from the time-domain blocks of F and G (Gram
+ * blocks in double-FP32 arithmetic, Cholesky and inverse per block).  Every CG
+ * iteration of the matrix-free solve (the FP64 one and the FP32 inner one) is then
+ * preconditioned.  Requires F, G (set_prior_se_grid) and set_noise; a later change of
+ * any of them drops it.  Returns BTI_ERR_NOT_SPD if a block fails to factor.
+ * Synchronises. */
+bti_status bti_set_matfree_precond(bti_handle h, int kind);
+
 typedef struct {
   int outer_iters;     /* refinement steps or flexible-CG iterations (0 for refine = 0) */
   int inner_iters;     /* conjugate-gradient iterations in total */

@@ -87,6 +87,7 @@ def lib():
         "bti_infer_map_prior": ([vp, vp, vp, vp, i64, ip], st),
         "bti_set_shadow": ([vp, ip, ip], st),
         "bti_set_tensor_cores": ([vp, ip], st),
+        "bti_set_matfree_precond": ([vp, ip], st),
         "bti_solve_matfree": ([vp, vp, vp, vp, i64, ip, dp, ip, ip, dp, ctypes.POINTER(SolveInfo)], st),
         "bti_apply_Q": ([vp, vp, vp, i64], st),
         "bti_copy_Q": ([vp, vp, vp], st),
@@ -293,6 +294,10 @@ class Handle:
     def set_tensor_cores(self, on=True):
         """Tensor-core FP16 forward products for B >= 8 vectors (on by default)."""
         self._check(lib().bti_set_tensor_cores(self._h, 1 if on else 0))
+
+    def set_matfree_precond(self, kind=1):
+        """Block-Jacobi preconditioner (time-diagonal blocks of K) for solve_matfree; 0 removes it."""
+        self._check(lib().bti_set_matfree_precond(self._h, int(kind)))
 
     def set_shadow(self, op, store):
         """A lower-tier copy of F's or G's spectral blocks for the inner solve."""

@@ -43,6 +43,7 @@ struct bti_ctx {
   FftPlan plan;
   OpStore op[3];
   OpStore shadow[3];  // lower-tier copies for the inner iteration of bti_solve_matfree
+  double* pinv = nullptr;  // block-Jacobi preconditioner: [N_t][N_d][N_d] inverses of K's diagonal blocks
   Tune tune[4];  // indexed by bti_prec
   bool tc_enabled = true;  // tensor-core FP16 products for B >= 8 (bti_set_tensor_cores)
   bti_prec dense_prec = BTI_P_F64;  // arithmetic of K assembly, Cholesky and solves
@@ -228,6 +229,7 @@ bti_status store_op(bti_ctx* h, bti_op opi, const double* blocks, bti_prec store
   const int64_t R = rows_of(h, opi);
   if (R <= 0) return fail(h, BTI_ERR_SHAPE, "operator has zero rows (N_q = 0?)");
   drop_store(h->shadow[opi]);  // a shadow copy describes the blocks being replaced
+  if (opi != BTI_OP_FQ) dev_freep(h->pinv);
   dev_free(o.hat);
   dev_freep(o.time);
   dev_freep(o.scale);
@@ -520,6 +522,7 @@ bti_status bti_destroy(bti_handle h) {
       dev_freep(set[i].scale);
     }
   dev_freep(h->prior_axes);
+  dev_freep(h->pinv);
   dev_freep(h->noise_diag);
   dev_freep(h->K);
   dev_freep(h->Q);
@@ -606,6 +609,7 @@ bti_status bti_set_prior_se_grid(bti_handle h, int gx, int gy, double ell, doubl
   // the previous G (and its shadow copy) goes first, so the peak holds one set of G blocks
   drop_store(h->op[BTI_OP_G]);
   drop_store(h->shadow[BTI_OP_G]);
+  dev_freep(h->pinv);
   h->K_built = h->K_factored = false;
   h->Q_built = h->covq_built = false;
   st = dev_alloc(h, (void**)&h->prior_axes, sizeof(double) * ((size_t)gx * gx + (size_t)gy * gy),
@@ -664,6 +668,7 @@ bti_status bti_set_noise(bti_handle h, double sigma2, const double* diag) {
   if (!diag && !(sigma2 > 0.0)) return fail(h, BTI_ERR_ARG, "set_noise: sigma2 must be > 0");
   drop_online_graph_any(h);
   dev_freep(h->noise_diag);
+  dev_freep(h->pinv);
   h->sigma2 = sigma2;
   if (diag) {
     size_t bytes = sizeof(double) * (size_t)h->Nt * h->Nd;
@@ -966,6 +971,58 @@ bti_status bti_copy_Q(bti_handle h, double* Q_out, double* cov_out) {
   return st;
 }
 
+bti_status bti_set_matfree_precond(bti_handle h, int kind) {
+  bti_status st = check_handle(h);
+  if (st != BTI_OK) return st;
+  if (kind != 0 && kind != 1) return fail(h, BTI_ERR_ARG, "set_matfree_precond: kind must be 0 or 1");
+  dev_freep(h->pinv);
+  if (kind == 0) return BTI_OK;
+  const OpStore& F = h->op[BTI_OP_F];
+  const OpStore& G = h->op[BTI_OP_G];
+  if (!F.set || !F.time || !G.set || !G.time) return fail(h, BTI_ERR_STATE, "set_matfree_precond: F or G not set");
+  if (!h->noise_set) return fail(h, BTI_ERR_STATE, "set_matfree_precond: noise not set");
+  const int64_t R = h->Nd, RR = R * R, Nt = h->Nt, Nm = h->Nm;
+  const int64_t nblk = (R + kCholNB - 1) / kCholNB;
+  const size_t nwork = std::max((size_t)R * kCholNB, trsm_work_elems(R, R));
+  double *W = nullptr, *P = nullptr, *Linv = nullptr, *work = nullptr;
+  st = dev_alloc(h, (void**)&W, sizeof(double) * (size_t)(Nt * RR), "preconditioner blocks");
+  if (st == BTI_OK) st = dev_alloc(h, (void**)&P, sizeof(double) * (size_t)(Nt * RR), "preconditioner");
+  if (st == BTI_OK) st = dev_alloc(h, (void**)&Linv, sizeof(double) * (size_t)(nblk * kCholNB * kCholNB), "Linv");
+  if (st == BTI_OK) st = dev_alloc(h, (void**)&work, sizeof(double) * nwork, "preconditioner work");
+  cudaStream_t s = h->stream;
+  if (st == BTI_OK) {
+    // K(t,t) = Gamma_noise(t) + sum_{k <= t} F_k G_k^T, the Gram blocks in double-FP32 arithmetic
+    int64_t nl = gemm_df64(true, R, R, Nm, 1.0, F.time, Nm, R * Nm, G.time, Nm, R * Nm, 0.0, W, R, RR, Nt, false, s);
+    nl += diag_block_cumsum(W, Nt, R, h->sigma2, h->noise_diag, s);
+    nl += identity_blocks(P, Nt, R, s);
+    cudaMemsetAsync(h->status, 0, sizeof(int), s);
+    for (int64_t t = 0; t < Nt; ++t) {  // P[t] = K(t,t)^{-1} from its Cholesky factor
+      nl += cholesky_f64(W + t * RR, R, Linv, work, h->status, s, true);
+      nl += trsm_lower_f64(W + t * RR, Linv, R, P + t * RR, R, work, h->status, s, true);
+    }
+    count_dense(h, nl);
+    st = launched(h, "block-Jacobi preconditioner");
+    int stat = 0;
+    if (st == BTI_OK)
+      st = cuda_check(h, cudaMemcpyAsync(&stat, h->status, sizeof(int), cudaMemcpyDeviceToHost, s), "status");
+    if (st == BTI_OK) st = cuda_check(h, cudaStreamSynchronize(s), "preconditioner sync");
+    if (st == BTI_OK && stat != 0) {
+      cudaMemsetAsync(h->status, 0, sizeof(int), s);
+      st = fail(h, BTI_ERR_NOT_SPD, "set_matfree_precond: a diagonal block of K is not SPD");
+    }
+  }
+  cudaStreamSynchronize(s);
+  dev_freep(W);
+  dev_freep(Linv);
+  dev_freep(work);
+  if (st != BTI_OK) {
+    dev_freep(P);
+    return st;
+  }
+  h->pinv = P;
+  return BTI_OK;
+}
+
 bti_status bti_set_tensor_cores(bti_handle h, int on) {
   bti_status st = check_handle(h);
   if (st != BTI_OK) return st;
@@ -1008,7 +1065,15 @@ struct MatfreeWork {
   float *dlt, *rt, *pt, *qt, *wf;                 // FP32 inner-iteration vectors
   double *part, *dn2, *rn2, *rr, *rr2, *pq;       // dot workspace and per-vector scalars
   double *rz, *zr, *zro, *num;                    // scalars of the flexible outer iteration
+  double* z;                                      // preconditioned residual
+  float* zt;                                      // preconditioned inner residual
 };
+
+// z = P^{-1} r with the block-Jacobi inverses: z_t = K(t,t)^{-1} r_t for every time block
+template <typename T>
+int apply_block_precond(bti_ctx* h, const T* r, T* z, int64_t B) {
+  return block_precond_apply<T>(h->pinv, r, z, h->Nt, h->Nd, B, h->stream);
+}
 
 // y = K x = Gamma_noise x + F (G^* x) with FP64-accurate operators: the F store (FP64 or
 // double-FP32) and G^* from the G store when that is FP64-accurate, else Gamma_prior F^T.
@@ -1085,10 +1150,10 @@ bti_status bti_solve_matfree(bti_handle h, const double* d_obs, double* m_map, d
   const int64_t n = h->Nt * h->Nd, np = h->Nt * h->Nm;
   const size_t Bn = (size_t)B * n, Bp = (size_t)B * np;
   cudaStream_t s = h->stream;
-  // one allocation: 6 FP64 data vectors, 3 FP64 parameter temporaries, 4 FP32 data and
+  // one allocation: 7 FP64 data vectors, 3 FP64 parameter temporaries, 5 FP32 data and
   // 1 FP32 parameter vector, the dot workspace and 9 scalar rows
-  const size_t nd = 6 * Bn + 3 * Bp + dot_workspace_elems(B) + 9 * (size_t)B;
-  const size_t nfl = 4 * Bn + Bp;
+  const size_t nd = 7 * Bn + 3 * Bp + dot_workspace_elems(B) + 9 * (size_t)B;
+  const size_t nfl = 5 * Bn + Bp;
   void* buf = nullptr;
   st = dev_alloc(h, &buf, sizeof(double) * nd + sizeof(float) * nfl, "solver workspace");
   if (st != BTI_OK) return st;
@@ -1100,6 +1165,7 @@ bti_status bti_solve_matfree(bti_handle h, const double* d_obs, double* m_map, d
   w.p = dp; dp += Bn;
   w.q = dp; dp += Bn;
   w.ro = dp; dp += Bn;
+  w.z = dp; dp += Bn;
   w.w1 = dp; dp += Bp;
   w.w2 = dp; dp += Bp;
   w.U = dp; dp += Bp;
@@ -1118,12 +1184,16 @@ bti_status bti_solve_matfree(bti_handle h, const double* d_obs, double* m_map, d
   w.rt = fp; fp += Bn;
   w.pt = fp; fp += Bn;
   w.qt = fp; fp += Bn;
+  w.zt = fp; fp += Bn;
   w.wf = fp;
   std::vector<double> hd, hr;
   int outer = 0, inner = 0;
   double rel = 0.0;
   bool converged = false;
   auto dot = [&](auto* a, auto* b, double* out) { count_dense(h, dot_batched(a, b, n, B, w.part, out, s)); };
+  const bool pc = h->pinv != nullptr;  // block-Jacobi preconditioning of every CG iteration
+  auto precond_d = [&](const double* r, double* z) { count_dense(h, apply_block_precond<double>(h, r, z, B)); };
+  auto precond_f = [&](const float* r, float* z) { count_dense(h, apply_block_precond<float>(h, r, z, B)); };
   // r = d - K x with the FP64-accurate operator, rn2 = r . r, and the max relative residual
   auto true_residual = [&](double& out_rel) -> bti_status {
     bti_status sr = apply_K_accurate(h, w.x, w.y, B, w);
@@ -1149,9 +1219,19 @@ bti_status bti_solve_matfree(bti_handle h, const double* d_obs, double* m_map, d
     st = fetch(h, w.dn2, hd, B);
     if (st != BTI_OK) break;
     if (refine == 0) {
-      // conjugate gradients on K with the FP64-accurate operators
-      cudaMemcpyAsync(w.p, w.r, sizeof(double) * Bn, cudaMemcpyDeviceToDevice, s);
-      cudaMemcpyAsync(w.rr, w.dn2, sizeof(double) * B, cudaMemcpyDeviceToDevice, s);
+      // conjugate gradients on K with the FP64-accurate operators (preconditioned when a
+      // block-Jacobi preconditioner is set: rr then holds r . z)
+      auto restart = [&]() {
+        if (pc) {
+          precond_d(w.r, w.z);
+          cudaMemcpyAsync(w.p, w.z, sizeof(double) * Bn, cudaMemcpyDeviceToDevice, s);
+          dot(w.r, w.z, w.rr);
+        } else {
+          cudaMemcpyAsync(w.p, w.r, sizeof(double) * Bn, cudaMemcpyDeviceToDevice, s);
+          dot(w.r, w.r, w.rr);
+        }
+      };
+      restart();
       for (int it = 0; it < max_inner; ++it) {
         st = apply_K_accurate(h, w.p, w.q, B, w);
         if (st != BTI_OK) break;
@@ -1166,12 +1246,18 @@ bti_status bti_solve_matfree(bti_handle h, const double* d_obs, double* m_map, d
           st = true_residual(rel);
           if (st != BTI_OK || rel <= tol || !(rel == rel) || replaced == kReplace) break;
           ++replaced;  // restart from the true residual
-          cudaMemcpyAsync(w.p, w.r, sizeof(double) * Bn, cudaMemcpyDeviceToDevice, s);
-          cudaMemcpyAsync(w.rr, w.rn2, sizeof(double) * B, cudaMemcpyDeviceToDevice, s);
+          restart();
           continue;
         }
-        count_dense(h, cg_update_p(w.p, w.r, w.rr2, w.rr, n, B, s));
-        std::swap(w.rr, w.rr2);
+        if (pc) {
+          precond_d(w.r, w.z);
+          dot(w.r, w.z, w.num);
+          count_dense(h, cg_update_p(w.p, w.z, w.num, w.rr, n, B, s));
+          std::swap(w.rr, w.num);
+        } else {
+          count_dense(h, cg_update_p(w.p, w.r, w.rr2, w.rr, n, B, s));
+          std::swap(w.rr, w.rr2);
+        }
       }
     } else {
       // z = ||r|| delta with K~ delta = r / ||r|| solved by FP32 conjugate gradients with the
@@ -1179,10 +1265,17 @@ bti_status bti_solve_matfree(bti_handle h, const double* d_obs, double* m_map, d
       auto inner_solve = [&](const double* rv, const double* rn2, double* z) -> bti_status {
         count_dense(h, normalize_to_f32(rv, rn2, w.rt, n, B, s));
         cudaMemsetAsync(w.dlt, 0, sizeof(float) * Bn, s);
-        cudaMemcpyAsync(w.pt, w.rt, sizeof(float) * Bn, cudaMemcpyDeviceToDevice, s);
-        dot(w.rt, w.rt, w.rr);
+        dot(w.rt, w.rt, w.rr2);
         std::vector<double> h0, hi;
-        bti_status si = fetch(h, w.rr, h0, B);
+        bti_status si = fetch(h, w.rr2, h0, B);
+        if (pc) {  // rr holds r . z for the preconditioned iteration
+          precond_f(w.rt, w.zt);
+          cudaMemcpyAsync(w.pt, w.zt, sizeof(float) * Bn, cudaMemcpyDeviceToDevice, s);
+          dot(w.rt, w.zt, w.rr);
+        } else {
+          cudaMemcpyAsync(w.pt, w.rt, sizeof(float) * Bn, cudaMemcpyDeviceToDevice, s);
+          cudaMemcpyAsync(w.rr, w.rr2, sizeof(double) * B, cudaMemcpyDeviceToDevice, s);
+        }
         for (int it = 0; si == BTI_OK && it < max_inner; ++it) {
           si = apply_K_inner(h, w.pt, w.qt, B, w);
           if (si != BTI_OK) break;
@@ -1194,8 +1287,15 @@ bti_status bti_solve_matfree(bti_handle h, const double* d_obs, double* m_map, d
           if (si != BTI_OK) break;
           const double ri = max_ratio(hi, h0);
           if (ri <= inner_tol || !(ri == ri)) break;
-          count_dense(h, cg_update_p(w.pt, w.rt, w.rr2, w.rr, n, B, s));
-          std::swap(w.rr, w.rr2);
+          if (pc) {
+            precond_f(w.rt, w.zt);
+            dot(w.rt, w.zt, w.num);
+            count_dense(h, cg_update_p(w.pt, w.zt, w.num, w.rr, n, B, s));
+            std::swap(w.rr, w.num);
+          } else {
+            count_dense(h, cg_update_p(w.pt, w.rt, w.rr2, w.rr, n, B, s));
+            std::swap(w.rr, w.rr2);
+          }
         }
         if (si != BTI_OK) return si;
         cudaMemsetAsync(z, 0, sizeof(double) * Bn, s);

@@ -247,5 +247,14 @@ int add_noise(T* q, const T* y, const T* p, const double* diag, double sigma2, i
 // refinement loop and an FP32 inner solve)
 int normalize_to_f32(const double* x, const double* nrm2, float* out, int64_t n, int64_t B, cudaStream_t s);
 int add_scaled_f32(double* x, const float* d, const double* nrm2, int64_t n, int64_t B, cudaStream_t s);
+// z [B][N_t][R] = blockdiag(P[t]) r with P [N_t][R][R] (FP64), r and z in T (float or double)
+template <typename T>
+int block_precond_apply(const double* P, const T* r, T* z, int64_t Nt, int64_t R, int64_t B, cudaStream_t s);
+int convert_f32_f64(const float* x, double* y, int64_t n, cudaStream_t s);
+int convert_f64_f32(const double* x, float* y, int64_t n, cudaStream_t s);
+// Time-diagonal blocks of K for the block-Jacobi preconditioner (dense.cu): W [Nt][R][R] holds
+// F_k G_k^T on entry and Gamma_noise(t) + sum_{k <= t} F_k G_k^T on exit; identity fill.
+int diag_block_cumsum(double* W, int64_t Nt, int64_t R, double sigma2, const double* diag, cudaStream_t s);
+int identity_blocks(double* X, int64_t nb, int64_t R, cudaStream_t s);
 
 }  // namespace bti

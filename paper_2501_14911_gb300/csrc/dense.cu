@@ -432,6 +432,41 @@ int k_diag_cumsum(double* WK, int64_t Nt, int64_t R, double sigma2, const double
   return 1;
 }
 
+// K(t,t) for the time-diagonal blocks only: W [Nt][R][R] holds F_k G_k^T; afterwards W[t] =
+// Gamma_noise(t) + sum_{k <= t} W[k] (the diagonal blocks of K, full R x R).
+__global__ void diag_block_cumsum_kernel(double* W, int64_t Nt, int64_t R, double sigma2,
+                                         const double* __restrict__ diag) {
+  const int64_t RR = R * R;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= RR) return;
+  const int64_t i = e / R, j = e - i * R;
+  double acc = 0.0;
+  for (int64_t t = 0; t < Nt; ++t) {
+    acc += W[t * RR + e];
+    W[t * RR + e] = acc + (i == j ? (diag ? diag[t * R + i] : sigma2) : 0.0);
+  }
+}
+int diag_block_cumsum(double* W, int64_t Nt, int64_t R, double sigma2, const double* diag, cudaStream_t s) {
+  const int64_t RR = R * R;
+  if (RR <= 0 || Nt <= 0) return 0;
+  diag_block_cumsum_kernel<<<(unsigned)((RR + 255) / 256), 256, 0, s>>>(W, Nt, R, sigma2, diag);
+  return 1;
+}
+
+// X [nb][R][R] = identity in every block
+__global__ void identity_blocks_kernel(double* X, int64_t total, int64_t R) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  const int64_t r = e % (R * R);
+  X[e] = (r / R == r % R) ? 1.0 : 0.0;
+}
+int identity_blocks(double* X, int64_t nb, int64_t R, cudaStream_t s) {
+  const int64_t total = nb * R * R;
+  if (total <= 0) return 0;
+  identity_blocks_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(X, total, R);
+  return 1;
+}
+
 // ------------------------------------------------------------------ Cholesky
 // Factor the kb x kb diagonal block in shared memory (right-looking, unblocked),
 // write L back, and write its inverse (lower, zeros above) to Linv (ld nb).

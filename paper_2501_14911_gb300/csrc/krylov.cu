@@ -117,9 +117,82 @@ __global__ void add_scaled_f32_kernel(double* __restrict__ x, const float* __res
     x[b * n + i] = fma(s, (double)d[b * n + i], x[b * n + i]);
 }
 
+template <typename TI, typename TO>
+__global__ void convert_kernel(const TI* __restrict__ x, TO* __restrict__ y, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (TO)x[i];
+}
+
+// z[b][t][i] = sum_j P[t][i][j] r[b][t][j]: the block-Jacobi preconditioner, one R x R block
+// per time step.  grid (N_t, ceil(R / 32)); each warp takes 4 rows, lanes stride the row
+// (coalesced), and the vectors' block r_t is staged in shared memory 8 vectors at a time.
+constexpr int kPcVec = 8;
+template <typename T>
+__global__ void __launch_bounds__(256) block_precond_kernel(const double* __restrict__ P, const T* __restrict__ r,
+                                                            T* __restrict__ z, int64_t Nt, int64_t R, int64_t B) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* rs = reinterpret_cast<double*>(smem_raw);  // [kPcVec][R]
+  const int64_t t = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t n = Nt * R;
+  const double* Pt = P + t * R * R;
+  for (int64_t b0 = 0; b0 < B; b0 += kPcVec) {
+    const int nb = (int)((B - b0) < kPcVec ? (B - b0) : kPcVec);
+    __syncthreads();
+    for (int64_t e = threadIdx.x; e < (int64_t)nb * R; e += blockDim.x) {
+      const int64_t bb = e / R, j = e - bb * R;
+      rs[bb * R + j] = (double)r[(b0 + bb) * n + t * R + j];
+    }
+    __syncthreads();
+    for (int q = 0; q < 4; ++q) {
+      const int64_t i = (int64_t)blockIdx.y * 32 + warp * 4 + q;
+      if (i >= R) break;
+      double acc[kPcVec];
+#pragma unroll
+      for (int bb = 0; bb < kPcVec; ++bb) acc[bb] = 0.0;
+      const double* row = Pt + i * R;
+      for (int64_t j = lane; j < R; j += 32) {
+        const double pv = __ldg(row + j);
+#pragma unroll
+        for (int bb = 0; bb < kPcVec; ++bb)
+          if (bb < nb) acc[bb] = fma(pv, rs[bb * R + j], acc[bb]);
+      }
+#pragma unroll
+      for (int bb = 0; bb < kPcVec; ++bb) {
+        double v = warp_sum(acc[bb]);
+        if (lane == 0 && bb < nb) z[(b0 + bb) * n + t * R + i] = (T)v;
+      }
+    }
+  }
+}
+
 }  // namespace
 
 size_t dot_workspace_elems(int64_t B) { return (size_t)B * kDotBlocks; }
+
+template <typename T>
+int block_precond_apply(const double* P, const T* r, T* z, int64_t Nt, int64_t R, int64_t B, cudaStream_t s) {
+  if (Nt <= 0 || R <= 0 || B <= 0) return 0;
+  const size_t smem = sizeof(double) * kPcVec * (size_t)R;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(block_precond_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  dim3 grid((unsigned)Nt, (unsigned)((R + 31) / 32));
+  block_precond_kernel<T><<<grid, 256, smem, s>>>(P, r, z, Nt, R, B);
+  return 1;
+}
+template int block_precond_apply<float>(const double*, const float*, float*, int64_t, int64_t, int64_t, cudaStream_t);
+template int block_precond_apply<double>(const double*, const double*, double*, int64_t, int64_t, int64_t,
+                                         cudaStream_t);
+
+int convert_f32_f64(const float* x, double* y, int64_t n, cudaStream_t s) {
+  if (n <= 0) return 0;
+  convert_kernel<float, double><<<vec_grid(n, 1), 256, 0, s>>>(x, y, n);
+  return 1;
+}
+int convert_f64_f32(const double* x, float* y, int64_t n, cudaStream_t s) {
+  if (n <= 0) return 0;
+  convert_kernel<double, float><<<vec_grid(n, 1), 256, 0, s>>>(x, y, n);
+  return 1;
+}
 
 template <typename T>
 int dot_batched(const T* x, const T* y, int64_t n, int64_t B, double* part, double* out, cudaStream_t s) {

@@ -629,7 +629,8 @@ def test_coarse_qoi_grid(stride):
     h.close()
 
 
-@pytest.mark.parametrize("form", ["plain_df64", "refined_f16", "refined_f32_f64store", "flexible_f16"])
+@pytest.mark.parametrize("form", ["plain_df64", "refined_f16", "refined_f32_f64store", "flexible_f16",
+                                  "plain_df64_pc", "flexible_f16_pc"])
 def test_matrix_free_solve_matches_dense_oracle(form):
     """m_map = G^* K^{-1} d_obs by conjugate gradients without forming K, against the
     oracle's dense Cholesky solve: FP64 CG with double-FP32 operators, and FP64
@@ -639,15 +640,17 @@ def test_matrix_free_solve_matches_dense_oracle(form):
     store = bti.F64 if form == "refined_f32_f64store" else bti.DF64
     h = make_handle(F, None, store)
     h.set_noise(p.sigma2)
-    if form == "plain_df64":
+    if form.startswith("plain_df64"):
         h.set_prior_se_grid(p.gx, p.gy, p.ell, p.sigma_p, bti.DF64)
     else:
-        low = bti.F16 if form == "refined_f16" else bti.F32
+        low = bti.F32 if form == "refined_f32_f64store" else bti.F16
         h.set_prior_se_grid(p.gx, p.gy, p.ell, p.sigma_p, low)
         h.set_shadow(bti.OP_F, low)
+    if form.endswith("_pc"):
+        h.set_matfree_precond(1)
     m = torch.empty((3, p.Nt, p.Nm), dtype=torch.float64, device="cuda")
     x = torch.empty((3, p.Nt, p.Nd), dtype=torch.float64, device="cuda")
-    refine = {"plain_df64": 0, "flexible_f16": 2}.get(form, 1)
+    refine = {"plain_df64": 0, "flexible_f16": 2, "plain_df64_pc": 0, "flexible_f16_pc": 2}.get(form, 1)
     info = h.solve_matfree(cuda(d), m, x, refine=refine, tol=1e-12, max_outer=100, max_inner=2000,
                            inner_tol=0.2 if refine == 2 else 1e-3)
     h.close()
@@ -658,6 +661,25 @@ def test_matrix_free_solve_matches_dense_oracle(form):
     assert info["rel_residual"] <= 1e-12
     if refine == 1:  # each refinement step gains about -log10(kappa(K) ||K - K~|| / ||K||) digits
         assert 1 <= info["outer_iters"] <= 30, info
+
+
+def test_block_jacobi_preconditioner_cuts_iterations():
+    """With the block-Jacobi preconditioner the FP64 CG of the matrix-free solve needs fewer
+    iterations for the same residual, and the answer is unchanged (against the oracle)."""
+    p, F, Fq, G, d_obs = tiny_problem()
+    h = make_handle(F, None, bti.DF64)
+    h.set_noise(p.sigma2)
+    h.set_prior_se_grid(p.gx, p.gy, p.ell, p.sigma_p, bti.DF64)
+    m = torch.empty((1, p.Nt, p.Nm), dtype=torch.float64, device="cuda")
+    plain = h.solve_matfree(cuda(d_obs), m, refine=0, tol=1e-12, max_inner=3000)
+    h.set_matfree_precond(1)
+    pcg = h.solve_matfree(cuda(d_obs), m, refine=0, tol=1e-12, max_inner=3000)
+    h.set_noise(p.sigma2)  # drops the preconditioner: the plain count again
+    again = h.solve_matfree(cuda(d_obs), m, refine=0, tol=1e-12, max_inner=3000)
+    h.close()
+    assert pcg["inner_iters"] < plain["inner_iters"], (pcg, plain)
+    assert again["inner_iters"] == plain["inner_iters"]
+    assert relb(host(m), oracle.map_point(F, G, p.sigma2, d_obs)) < 1e-10
 
 
 def test_matrix_free_solve_reports_no_convergence():
