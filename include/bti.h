@@ -229,6 +229,13 @@ bti_status bti_infer_map_prior(bti_handle h, const double* d_obs, const double* 
  * gives up inside the tensor-core kernel is reported by bti_sync as BTI_ERR_TIMEOUT. */
 bti_status bti_set_tensor_cores(bti_handle h, int on);
 
+/* Failure-handling test hook: while stage >= 0, the tensor-core forward product withholds
+ * the F-hat tile of that pipeline stage in every CTA, so its bounded waits (about a
+ * second) run out; the kernel then stops, drains what it issued, frees its tensor memory
+ * and sets the device status word that bti_sync reports as BTI_ERR_TIMEOUT.  The handle
+ * and the CUDA context stay usable.  -1 (the default) turns it off. */
+bti_status bti_test_withhold_tc_stage(bti_handle h, int stage);
+
 /* ---------------------------------------------------------------- matrix-free solve
  * When K = Gamma_noise + F G^* is too large to form (N_d N_t = 252,000 makes it
  * 508 GB in FP64), K x = d_obs is solved by conjugate gradients with K applied as

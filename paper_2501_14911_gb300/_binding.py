@@ -88,6 +88,7 @@ def lib():
         "bti_set_shadow": ([vp, ip, ip], st),
         "bti_set_tensor_cores": ([vp, ip], st),
         "bti_set_matfree_precond": ([vp, ip], st),
+        "bti_test_withhold_tc_stage": ([vp, ip], st),
         "bti_solve_matfree": ([vp, vp, vp, vp, i64, ip, dp, ip, ip, dp, ctypes.POINTER(SolveInfo)], st),
         "bti_apply_Q": ([vp, vp, vp, i64], st),
         "bti_copy_Q": ([vp, vp, vp], st),
@@ -294,6 +295,10 @@ class Handle:
     def set_tensor_cores(self, on=True):
         """Tensor-core FP16 forward products for B >= 8 vectors (on by default)."""
         self._check(lib().bti_set_tensor_cores(self._h, 1 if on else 0))
+
+    def test_withhold_tc_stage(self, stage):
+        """Failure-handling test hook: the tensor-core forward withholds one pipeline stage."""
+        self._check(lib().bti_test_withhold_tc_stage(self._h, int(stage)))
 
     def set_matfree_precond(self, kind=1):
         """Block-Jacobi preconditioner (time-diagonal blocks of K) for solve_matfree; 0 removes it."""

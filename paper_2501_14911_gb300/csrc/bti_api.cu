@@ -46,6 +46,7 @@ struct bti_ctx {
   double* pinv = nullptr;  // block-Jacobi preconditioner: [N_t][N_d][N_d] inverses of K's diagonal blocks
   Tune tune[4];  // indexed by bti_prec
   bool tc_enabled = true;  // tensor-core FP16 products for B >= 8 (bti_set_tensor_cores)
+  int tc_drop_stage = -1;  // failure-handling test hook (bti_test_withhold_tc_stage)
   bti_prec dense_prec = BTI_P_F64;  // arithmetic of K assembly, Cholesky and solves
   bool noise_set = false;
   double sigma2 = 0.0;
@@ -340,7 +341,7 @@ bti_status apply_fwd_t(bti_ctx* h, const OpStore& o, const void* in, void* out, 
     {
       ProfScope ps(h, BTI_K_PROD_FWD);  // the MMA kernel and its fixed-order chunk sum
       e = launch_prod_fwd_f16_tc(o.hat, o.scale, (const float2*)mhat, (float2*)part, (float2*)dhat, nf, R, Nm, B,
-                                 h->status + 1, s, &nl);
+                                 h->status + 1, s, &nl, h->tc_drop_stage);
     }
     h->prof_count[BTI_K_PROD_FWD] += nl - 1;
     if (e != cudaSuccess) return cuda_check(h, e, "tensor-core forward product");
@@ -1029,6 +1030,15 @@ bti_status bti_set_tensor_cores(bti_handle h, int on) {
   if (on != 0 && on != 1) return fail(h, BTI_ERR_ARG, "set_tensor_cores: on must be 0 or 1");
   if (h->tc_enabled != (on == 1)) drop_online_graph_any(h);
   h->tc_enabled = on == 1;
+  return BTI_OK;
+}
+
+bti_status bti_test_withhold_tc_stage(bti_handle h, int stage) {
+  bti_status st = check_handle(h);
+  if (st != BTI_OK) return st;
+  if (stage < -1) return fail(h, BTI_ERR_ARG, "test_withhold_tc_stage: stage must be >= -1");
+  drop_online_graph_any(h);
+  h->tc_drop_stage = stage;
   return BTI_OK;
 }
 

@@ -217,9 +217,11 @@ int noise_residual_f64(double* r, const double* x, const double* diag, int64_t n
 // gave up.  *launches receives the number of kernels launched.
 bool tc_fwd_f16_supported(int64_t Nm, int64_t B);
 size_t tc_fwd_partial_elems(int64_t nf, int64_t R, int64_t Nm, int64_t B);
+// drop_stage >= 0 (test hook): the producer withholds that stage's tile, so the kernel's bounded
+// waits run out and it reports through err.
 cudaError_t launch_prod_fwd_f16_tc(const void* Fhat, const float* scale, const float2* mhat, float2* partial,
                                    float2* dhat, int64_t nf, int64_t R, int64_t Nm, int64_t B, int* err,
-                                   cudaStream_t s, int* launches);
+                                   cudaStream_t s, int* launches, int drop_stage = -1);
 // Adjoint: mhat [B][nf][N_m] = F-hat^H (scale-folded dhat) for B >= 8 and N_d up to 2048 (16
 // vectors per group) or 1024 (32 per group); no partials.
 bool tc_adj_f16_supported(int64_t Nm, int64_t R, int64_t B);

@@ -60,7 +60,7 @@ template <int BG>
 __global__ void __launch_bounds__(kTcThreads, 1)
 prod_fwd_f16_tc_kernel(const __grid_constant__ CUtensorMap tmA, const float* __restrict__ scaleF,
                        const float2* __restrict__ mhat, float2* __restrict__ partial, int nf, int R, int64_t Nm,
-                       int B, int Kc, int nchunk, int nrt, int* __restrict__ err) {
+                       int B, int Kc, int nchunk, int nrt, int drop_stage, int* __restrict__ err) {
   constexpr int N = 2 * BG;                      // MMA N: real and imaginary output columns
   constexpr uint32_t kBTile = (uint32_t)N * 128;  // bytes of one B stage
   constexpr uint32_t kTmemCols = N < 32 ? 32 : N;
@@ -110,6 +110,7 @@ prod_fwd_f16_tc_kernel(const __grid_constant__ CUtensorMap tmA, const float* __r
       for (int s = 0; s < nst; ++s) {
         const int slot = s % kTcStages;
         if (s >= kTcStages && !mbar_wait(smem_u32(&empty[slot]), ((s / kTcStages) - 1) & 1, abort_v)) break;
+        if (s == drop_stage) break;  // test hook: this stage never arrives, so the waits run out
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&fullA[slot])),
                      "r"(kTcATile));
         asm volatile(
@@ -532,7 +533,7 @@ size_t tc_fwd_partial_elems(int64_t nf, int64_t R, int64_t Nm, int64_t B) {
 
 cudaError_t launch_prod_fwd_f16_tc(const void* Fhat, const float* scale, const float2* mhat, float2* partial,
                                    float2* dhat, int64_t nf, int64_t R, int64_t Nm, int64_t B, int* err,
-                                   cudaStream_t s, int* launches) {
+                                   cudaStream_t s, int* launches, int drop_stage) {
   *launches = 0;
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
@@ -562,11 +563,11 @@ cudaError_t launch_prod_fwd_f16_tc(const void* Fhat, const float* scale, const f
   if (BG == 16) {
     cudaFuncSetAttribute(prod_fwd_f16_tc_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     prod_fwd_f16_tc_kernel<16><<<grid, kTcThreads, smem, s>>>(tm, scale, mhat, partial, (int)nf, (int)R, Nm, (int)B,
-                                                              (int)Kc, (int)nchunk, (int)nrt, err);
+                                                              (int)Kc, (int)nchunk, (int)nrt, drop_stage, err);
   } else {
     cudaFuncSetAttribute(prod_fwd_f16_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     prod_fwd_f16_tc_kernel<32><<<grid, kTcThreads, smem, s>>>(tm, scale, mhat, partial, (int)nf, (int)R, Nm, (int)B,
-                                                              (int)Kc, (int)nchunk, (int)nrt, err);
+                                                              (int)Kc, (int)nchunk, (int)nrt, drop_stage, err);
   }
   const int64_t total = B * nf * R;
   tc_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(partial, dhat, total, R, (int)nchunk);

@@ -703,3 +703,25 @@ def test_matrix_free_solve_reports_no_convergence():
     assert e.value.status == 3
     h2.close()
     h.close()
+
+
+def test_tensor_core_wait_timeout_is_reported_and_recoverable():
+    """Failure handling without a fault: with one pipeline stage withheld (test hook), the
+    tensor-core forward's bounded waits run out; bti_sync reports BTI_ERR_TIMEOUT once, and
+    the same handle then computes correct products again."""
+    p = synthetic.small("tc_timeout", 1, 2048, 64, 32, Nq=4)
+    F = p.blocks_F()
+    h = make_handle(F, None, bti.F16)
+    m = cuda(p.vectors_m(16), torch.float32)
+    d = torch.empty((16, 32, 64), dtype=torch.float32, device="cuda")
+    h.test_withhold_tc_stage(2)
+    h.apply_F(m, d)
+    with pytest.raises(bti.BtiError) as e:
+        h.sync()
+    assert e.value.status == 7  # BTI_ERR_TIMEOUT
+    h.sync()  # reported once
+    h.test_withhold_tc_stage(-1)
+    h.apply_F(m, d)
+    h.sync()
+    h.close()
+    assert relb(host(d), oracle.p2o_apply(F, host(m))) < 1e-3
