@@ -308,11 +308,26 @@ rfft_cols_kernel(FftDesc D, int Nt, const TI* __restrict__ x, int64_t ld, int64_
   const TI* xb = x + (int64_t)blockIdx.y * xbs;
   C2<TO>* Xb = X + (int64_t)blockIdx.y * Xbs;
 
-  for (int idx = threadIdx.x; idx < Nt * W2; idx += blockDim.x) {
-    int t = idx / W2, c = idx - t * W2;
-    int64_t col = col0 + c;
-    T v = (col < ncols) ? (T)xb[(int64_t)t * ld + col] : (T)0;
-    reinterpret_cast<T*>(&buf0[(c >> 1) * LP + sp(t)])[c & 1] = v;
+  // stage the 2P columns (time along rows): eight loads per thread in flight before the
+  // shared-memory stores
+  const int total = Nt * W2;
+  for (int base = 0; base < total; base += 8 * blockDim.x) {
+    T v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * blockDim.x + threadIdx.x;
+      const int t = idx / W2, c = idx - t * W2;
+      const int64_t col = col0 + c;
+      v[u] = (idx < total && col < ncols) ? (T)xb[(int64_t)t * ld + col] : (T)0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * blockDim.x + threadIdx.x;
+      if (idx < total) {
+        const int t = idx / W2, c = idx - t * W2;
+        reinterpret_cast<T*>(&buf0[(c >> 1) * LP + sp(t)])[c & 1] = v[u];
+      }
+    }
   }
   const int pad = L - Nt;
   for (int idx = threadIdx.x; idx < P * pad; idx += blockDim.x) {
