@@ -64,6 +64,7 @@ CASES = [
     ("tc_b16", 4096, 128, 4, 64, 16),
     ("tc_b10_rows200_L90", 3000, 200, 5, 45, 10),
     ("tc_b40_groups", 1024, 13, 3, 32, 40),
+    ("L2048_max_length", 96, 5, 3, 1024, 9),  # the longest transform (N_t = 1024, one pair per CTA)
 ]
 
 
