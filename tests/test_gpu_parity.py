@@ -65,6 +65,8 @@ CASES = [
     ("tc_b10_rows200_L90", 3000, 200, 5, 45, 10),
     ("tc_b40_groups", 1024, 13, 3, 32, 40),
     ("L2048_max_length", 96, 5, 3, 1024, 9),  # the longest transform (N_t = 1024, one pair per CTA)
+    ("b9_Nm_not_mult4", 333, 7, 2, 20, 9),    # B >= 8 but N_m % 4 != 0: CUDA-core FP16 products
+    ("tc_R1100_b20", 512, 1100, 3, 12, 20),    # tensor-core forward over 9 row tiles; adjoint on CUDA cores
 ]
 
 
