@@ -370,21 +370,16 @@ irfft_cols_kernel(FftDesc D, int Nt, const C2<TYI>* __restrict__ Y, int64_t ld, 
   const C2<TYI>* Yb = Y + (int64_t)blockIdx.y * Ybs;
   TO* yb = y + (int64_t)blockIdx.y * ybs;
   const int nf = Nt + 1;
-  // stage spectrum a (even column) in buf0, spectrum b (odd column) in buf1
-  for (int idx = threadIdx.x; idx < nf * W2; idx += blockDim.x) {
-    int k = idx / W2, c = idx - k * W2;
-    int64_t col = col0 + c;
-    C2<T> v = (col < ncols) ? cvt2<T, TYI>(Yb[(int64_t)k * ld + col]) : czero<T>();
-    C2<T>* dst = (c & 1) ? buf1 : buf0;
-    dst[(c >> 1) * LP + sp(k)] = v;
-  }
-  __syncthreads();
-  // Z[k] = A[k] + i B[k] for k <= N_t and Z[L-k] = conj(A[k]) + i conj(B[k]);
-  // bins 0 and N_t of a real signal's spectrum are real: their imaginary parts are dropped.
-  for (int idx = threadIdx.x; idx < P * nf; idx += blockDim.x) {
-    int p = idx / nf, k = idx - p * nf;
-    C2<T> a = buf0[p * LP + sp(k)];
-    C2<T> b = buf1[p * LP + sp(k)];
+  // Stage the two spectra of each column pair straight into the complex input of one
+  // transform: Z[k] = A[k] + i B[k] for k <= N_t and Z[L-k] = conj(A[k]) + i conj(B[k]).
+  // Bins 0 and N_t of a real signal's spectrum are real: their imaginary parts are dropped.
+  // Each thread reads the pair's two neighbouring columns of one row.
+  for (int idx = threadIdx.x; idx < nf * P; idx += blockDim.x) {
+    const int k = idx / P, p = idx - k * P;
+    const int64_t c0 = col0 + 2 * p;
+    const C2<TYI>* row = Yb + (int64_t)k * ld;
+    const C2<T> a = (c0 < ncols) ? cvt2<T, TYI>(row[c0]) : czero<T>();
+    const C2<T> b = (c0 + 1 < ncols) ? cvt2<T, TYI>(row[c0 + 1]) : czero<T>();
     if (k == 0 || k == Nt) {
       buf0[p * LP + sp(k)] = mk<T>(a.x, b.x);
     } else {
