@@ -546,6 +546,7 @@ def online_block(args, dev, stream):
     e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     reps = 3
     forms = [("plain_f64", bti.F64, bti.F64, 0), ("dense_df64", bti.DF64, bti.F64, 1),
+             ("dense_df64_no_refinement", bti.DF64, bti.F64, 0),
              ("f32_assembly", bti.F64, bti.F32, 3), ("f32_assembly_dense_df64", bti.DF64, bti.F32, 3)]
     out = {"workload": p.name, "obs_vectors": B, "K_n": p.Nt * p.Nd}
     for name, dense, assembly, refine in forms:
@@ -598,8 +599,10 @@ def online_block(args, dev, stream):
             out[name]["Q_shape"] = [p.Nt * p.Nq, p.Nt * p.Nd]
     h.set_stream(stream)
     h.close()
-    out["accuracy"] = ("every form reaches FP64-level m_map and q_map: tests/test_gpu_parity.py (tiny, 1e-12) "
-                       "and tests/test_gpu_fullsize.py (batched full size, 1e-11) against the oracle")
+    out["accuracy"] = ("every form but dense_df64_no_refinement reaches FP64-level m_map and q_map: "
+                       "tests/test_gpu_parity.py (tiny, 1e-12) and tests/test_gpu_fullsize.py (batched full size, "
+                       "1e-11) against the oracle; dense_df64_no_refinement measures 1.2e-11 (48-bit arithmetic "
+                       "times kappa(K)), far inside the 1e-6 latency target")
     return out
 
 
