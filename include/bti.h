@@ -111,6 +111,17 @@ bti_status bti_set_blocks(bti_handle h, bti_op op, const double* blocks, bti_pre
 bti_status bti_set_prior_se_grid(bti_handle h, int gx, int gy, double ell, double sigma,
                                  bti_prec store);
 
+/* The elliptic prior of Eq. (5.1) instead: Gamma_prior = I_t (x) (alpha1 I - alpha2 Delta_h)^{-2}
+ * on the gx x gy grid (node index ix * gy + iy), Delta_h the 5-point Laplacian with
+ * Neumann boundaries in graph form (the paper's Robin coefficient is not given).  The
+ * operator is diagonalised by the orthonormal DCT-II on each axis, so the prior is applied
+ * exactly: X -> D_x^T [ (D_x X D_y^T) o W ] D_y with W = (alpha1 + alpha2 (lx + ly))^{-2} and
+ * lx_k = 2 - 2 cos(pi k / gx).  G = F Gamma_prior and its spectral blocks (tier `store`)
+ * replace any previous prior; everything that uses the prior (K, Q, Gamma_post, the
+ * matrix-free solve) then uses this one.  alpha1 > 0, alpha2 >= 0.  Synchronises. */
+bti_status bti_set_prior_elliptic_grid(bti_handle h, int gx, int gy, double alpha1, double alpha2,
+                                       bti_prec store);
+
 /* Arithmetic of the dense data-space work that follows (the Gram product of
  * bti_build_K, the panel and trailing updates of bti_factor_K, and the block
  * updates of the triangular solves): BTI_P_F64 (default; FP64 FMA) or BTI_P_DF64

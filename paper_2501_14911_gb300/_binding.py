@@ -67,6 +67,7 @@ def lib():
         "bti_set_stream": ([vp, vp], st),
         "bti_set_blocks": ([vp, ip, vp, ip], st),
         "bti_set_prior_se_grid": ([vp, ip, ip, dp, dp, ip], st),
+        "bti_set_prior_elliptic_grid": ([vp, ip, ip, dp, dp, ip], st),
         "bti_set_noise": ([vp, dp, vp], st),
         "bti_set_dense_precision": ([vp, ip], st),
         "bti_apply_F": ([vp, vp, vp, i64, ip], st),
@@ -206,6 +207,11 @@ class Handle:
 
     def set_prior_se_grid(self, gx, gy, ell, sigma, store=F64):
         self._check(lib().bti_set_prior_se_grid(self._h, gx, gy, float(ell), float(sigma), store))
+
+    def set_prior_elliptic_grid(self, gx, gy, alpha1=1.0, alpha2=1.0, store=F64):
+        """The elliptic prior (alpha1 I - alpha2 Delta_h)^{-2} of Eq. (5.1), applied exactly by DCT."""
+        self._check(lib().bti_set_prior_elliptic_grid(self._h, int(gx), int(gy), float(alpha1), float(alpha2),
+                                                      int(store)))
 
     def set_dense_precision(self, arith=F64):
         """Arithmetic of K assembly, Cholesky and solves: F64 (FP64 FMA) or DF64 (float pairs)."""

@@ -51,7 +51,8 @@ struct bti_ctx {
   bool noise_set = false;
   double sigma2 = 0.0;
   double* noise_diag = nullptr;  // [Nt][Nd] or null
-  bool prior_set = false;        // SE prior of bti_set_prior_se_grid (also applied to F_q)
+  bool prior_set = false;        // prior of bti_set_prior_se_grid / _elliptic_grid (also applied to F_q)
+  int prior_kind = 0;            // 0: squared exponential C_x (x) C_y; 1: elliptic (A_s^2)^{-1} by DCT
   int prior_gx = 0, prior_gy = 0;
   double prior_ell = 0.0, prior_sigma = 0.0;
   double* prior_axes = nullptr;  // C_x [gx][gx] then C_y [gy][gy]
@@ -417,19 +418,37 @@ bti_status apply_op(bti_ctx* h, bti_op opi, bool adjoint, const void* in, void* 
   return apply_store(h, o, adjoint, in, out, B, io);
 }
 
-// out = in C_s for `rows` grid-shaped rows (row r viewed as X_r [gx][gy]: C_x X_r C_y)
-// with the SE prior's axis matrices: Gamma_prior = I_t (x) C_s applied block by block.
-// U is a caller-provided temporary of rows * N_m doubles.  Stream-ordered, no sync.
+// out = Gamma_prior applied to `rows` grid-shaped rows (row r viewed as X_r [gx][gy]), the
+// time-invariant prior applied block by block.  U is a caller-provided temporary of
+// rows * N_m doubles; in and out must not alias.  Stream-ordered, no sync.
+//  - squared exponential: C_s = C_x (x) C_y, so X_r -> C_x X_r C_y (the axis matrices are
+//    symmetric);
+//  - elliptic, Eq. (5.1): Gamma_prior = (alpha1 I - alpha2 Delta_h)^{-2}.  The Neumann
+//    grid Laplacian is diagonalised by the orthonormal DCT-II on each axis (D_x, D_y), so
+//    X_r -> D_x^T [ (D_x X_r D_y^T) o W ] D_y with W[k][l] = (alpha1 + alpha2 (lx_k + ly_l))^{-2}.
 bti_status se_rows_into(bti_ctx* h, const double* in, double* out, int64_t rows, double* U) {
   const int gx = h->prior_gx, gy = h->prior_gy;
-  const double* Cx = h->prior_axes;
-  const double* Cy = Cx + (size_t)gx * gx;
+  const int64_t gg = (int64_t)gx * gy;
   cudaStream_t s = h->stream;
-  int64_t nl = gemm_f64(false, rows * gx, gy, gy, 1.0, in, gy, 0, Cy, gy, 0, 0.0, U, gy, 0, 1, false, s);
-  nl += gemm_f64(false, gx, gy, gx, 1.0, Cx, gx, 0, U, gy, (int64_t)gx * gy, 0.0, out, gy, (int64_t)gx * gy, rows,
-                 false, s);
+  int64_t nl = 0;
+  if (h->prior_kind == 0) {
+    const double* Cx = h->prior_axes;
+    const double* Cy = Cx + (size_t)gx * gx;
+    nl += gemm_f64(false, rows * gx, gy, gy, 1.0, in, gy, 0, Cy, gy, 0, 0.0, U, gy, 0, 1, false, s);
+    nl += gemm_f64(false, gx, gy, gx, 1.0, Cx, gx, 0, U, gy, gg, 0.0, out, gy, gg, rows, false, s);
+  } else {
+    const double* Dx = h->prior_axes;
+    const double* DxT = Dx + (size_t)gx * gx;
+    const double* Dy = DxT + (size_t)gx * gx;
+    const double* W = Dy + (size_t)gy * gy;
+    nl += gemm_f64(true, rows * gx, gy, gy, 1.0, in, gy, 0, Dy, gy, 0, 0.0, U, gy, 0, 1, false, s);     // X D_y^T
+    nl += gemm_f64(false, gx, gy, gx, 1.0, Dx, gx, 0, U, gy, gg, 0.0, out, gy, gg, rows, false, s);    // D_x (.)
+    nl += scale_blocks(out, W, gg, rows, s);                                                             // o W
+    nl += gemm_f64(false, rows * gx, gy, gy, 1.0, out, gy, 0, Dy, gy, 0, 0.0, U, gy, 0, 1, false, s);  // (.) D_y
+    nl += gemm_f64(false, gx, gy, gx, 1.0, DxT, gx, 0, U, gy, gg, 0.0, out, gy, gg, rows, false, s);   // D_x^T (.)
+  }
   count_dense(h, nl);
-  return launched(h, "SE prior");
+  return launched(h, "prior");
 }
 
 }  // namespace
@@ -593,14 +612,17 @@ bti_status bti_set_blocks(bti_handle h, bti_op op, const double* blocks, bti_pre
   return store_op(h, op, blocks, store, true);
 }
 
-bti_status bti_set_prior_se_grid(bti_handle h, int gx, int gy, double ell, double sigma, bti_prec store) {
-  bti_status st = check_handle(h);
-  if (st != BTI_OK) return st;
-  if (gx <= 0 || gy <= 0 || !(ell > 0.0) || !(sigma > 0.0) || !prec_ok(store))
-    return fail(h, BTI_ERR_ARG, "set_prior_se_grid: bad argument");
-  if ((int64_t)gx * gy != h->Nm) return fail(h, BTI_ERR_SHAPE, "set_prior_se_grid: gx * gy != N_m");
+}  // extern "C"
+
+namespace {
+
+// Shared part of the two prior set-ups: the axis tables (host, `tables` doubles) go to the
+// device, G_k = F_k Gamma_prior is formed from F's time-domain blocks, and its spectral
+// blocks are made in tier `store`.
+bti_status set_prior_common(bti_ctx* h, int gx, int gy, int kind, const std::vector<double>& tables,
+                            bti_prec store, const char* name) {
   OpStore& F = h->op[BTI_OP_F];
-  if (!F.set || !F.time) return fail(h, BTI_ERR_STATE, "set_prior_se_grid: F blocks not set");
+  if (!F.set || !F.time) return fail(h, BTI_ERR_STATE, std::string(name) + ": F blocks not set");
   const int64_t rows = h->Nt * h->Nd;
   double* U = nullptr;
   double* G = nullptr;
@@ -613,23 +635,22 @@ bti_status bti_set_prior_se_grid(bti_handle h, int gx, int gy, double ell, doubl
   dev_freep(h->pinv);
   h->K_built = h->K_factored = false;
   h->Q_built = h->covq_built = false;
-  st = dev_alloc(h, (void**)&h->prior_axes, sizeof(double) * ((size_t)gx * gx + (size_t)gy * gy),
-                 "alloc prior axes");
+  bti_status st = dev_alloc(h, (void**)&h->prior_axes, sizeof(double) * tables.size(), "alloc prior tables");
+  if (st != BTI_OK) return st;
+  cudaStream_t s = h->stream;
+  st = cuda_check(h, cudaMemcpyAsync(h->prior_axes, tables.data(), sizeof(double) * tables.size(),
+                                     cudaMemcpyHostToDevice, s), "prior tables");
+  if (st == BTI_OK) st = cuda_check(h, cudaStreamSynchronize(s), "prior tables");  // host vector goes away
   if (st != BTI_OK) return st;
   st = dev_alloc(h, (void**)&U, sizeof(double) * (size_t)rows * h->Nm, "alloc prior temp");
   if (st != BTI_OK) return st;
   st = dev_alloc(h, (void**)&G, sizeof(double) * (size_t)rows * h->Nm, "alloc G blocks");
   if (st != BTI_OK) { dev_freep(U); return st; }
-  cudaStream_t s = h->stream;
   h->prior_set = true;
+  h->prior_kind = kind;
   h->prior_gx = gx;
   h->prior_gy = gy;
-  h->prior_ell = ell;
-  h->prior_sigma = sigma;
-  // C_s = C_x (x) C_y with sigma on each axis, node index ix * gy + iy
-  count_dense(h, se_axis_matrix(h->prior_axes, gx, ell, sigma, s) +
-                     se_axis_matrix(h->prior_axes + (size_t)gx * gx, gy, ell, sigma, s));
-  // row r of the blocks viewed as X_r [gx][gy]: G_r = C_x X_r C_y
+  // row r of the blocks viewed as X_r [gx][gy]: G_r = Gamma_prior applied to X_r
   st = se_rows_into(h, F.time, G, rows, U);
   cudaStreamSynchronize(s);
   dev_freep(U);  // before the spectral blocks are made
@@ -648,9 +669,69 @@ bti_status bti_set_prior_se_grid(bti_handle h, int gx, int gy, double ell, doubl
     }
   }
   cudaStreamSynchronize(s);
-  dev_freep(U);
   dev_freep(G);
   return st;
+}
+
+// Squared-exponential axis matrix C[a][b] = scale exp(-(a - b)^2 / (2 ell^2)) (host copy of the
+// device table builder's definition)
+void se_axis_host(std::vector<double>& out, int n, double ell, double scale) {
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b) out.push_back(scale * std::exp(-0.5 * (double)(a - b) * (a - b) / (ell * ell)));
+}
+
+// Orthonormal DCT-II matrix D[k][j] = s_k cos(pi k (2 j + 1) / (2 n)): the eigenvectors of the
+// path-graph (Neumann) Laplacian, whose eigenvalues are 2 - 2 cos(pi k / n)
+void dct2_host(std::vector<double>& out, int n, bool transpose) {
+  const double pi = 3.14159265358979323846264338327950288;
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < n; ++c) {
+      const int k = transpose ? c : r, j = transpose ? r : c;
+      const double sk = k == 0 ? std::sqrt(1.0 / n) : std::sqrt(2.0 / n);
+      out.push_back(sk * std::cos(pi * k * (2.0 * j + 1.0) / (2.0 * n)));
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+bti_status bti_set_prior_se_grid(bti_handle h, int gx, int gy, double ell, double sigma, bti_prec store) {
+  bti_status st = check_handle(h);
+  if (st != BTI_OK) return st;
+  if (gx <= 0 || gy <= 0 || !(ell > 0.0) || !(sigma > 0.0) || !prec_ok(store))
+    return fail(h, BTI_ERR_ARG, "set_prior_se_grid: bad argument");
+  if ((int64_t)gx * gy != h->Nm) return fail(h, BTI_ERR_SHAPE, "set_prior_se_grid: gx * gy != N_m");
+  // C_s = C_x (x) C_y with sigma on each axis, node index ix * gy + iy
+  std::vector<double> tables;
+  tables.reserve((size_t)gx * gx + (size_t)gy * gy);
+  se_axis_host(tables, gx, ell, sigma);
+  se_axis_host(tables, gy, ell, sigma);
+  h->prior_ell = ell;
+  h->prior_sigma = sigma;
+  return set_prior_common(h, gx, gy, 0, tables, store, "set_prior_se_grid");
+}
+
+bti_status bti_set_prior_elliptic_grid(bti_handle h, int gx, int gy, double alpha1, double alpha2, bti_prec store) {
+  bti_status st = check_handle(h);
+  if (st != BTI_OK) return st;
+  if (gx <= 0 || gy <= 0 || !(alpha1 > 0.0) || !(alpha2 >= 0.0) || !prec_ok(store))
+    return fail(h, BTI_ERR_ARG, "set_prior_elliptic_grid: bad argument");
+  if ((int64_t)gx * gy != h->Nm) return fail(h, BTI_ERR_SHAPE, "set_prior_elliptic_grid: gx * gy != N_m");
+  // tables: D_x, D_x^T, D_y, then W[k][l] = (alpha1 + alpha2 (lx_k + ly_l))^{-2}
+  std::vector<double> tables;
+  tables.reserve(2 * (size_t)gx * gx + (size_t)gy * gy + (size_t)gx * gy);
+  dct2_host(tables, gx, false);
+  dct2_host(tables, gx, true);
+  dct2_host(tables, gy, false);
+  const double pi = 3.14159265358979323846264338327950288;
+  for (int k = 0; k < gx; ++k)
+    for (int l = 0; l < gy; ++l) {
+      const double lam = (2.0 - 2.0 * std::cos(pi * k / gx)) + (2.0 - 2.0 * std::cos(pi * l / gy));
+      const double mu = alpha1 + alpha2 * lam;
+      tables.push_back(1.0 / (mu * mu));
+    }
+  return set_prior_common(h, gx, gy, 1, tables, store, "set_prior_elliptic_grid");
 }
 
 bti_status bti_set_dense_precision(bti_handle h, bti_prec arith) {
@@ -1153,7 +1234,7 @@ bti_status bti_solve_matfree(bti_handle h, const double* d_obs, double* m_map, d
     return fail(h, BTI_ERR_ARG, "solve_matfree: bad B, refine, tolerance or iteration limit");
   if (!h->op[BTI_OP_F].set || !double_path(h->op[BTI_OP_F].prec))
     return fail(h, BTI_ERR_STATE, "solve_matfree: F must be stored in FP64 or double-FP32");
-  if (!h->prior_set || !h->op[BTI_OP_G].set) return fail(h, BTI_ERR_STATE, "solve_matfree: no SE prior set");
+  if (!h->prior_set || !h->op[BTI_OP_G].set) return fail(h, BTI_ERR_STATE, "solve_matfree: no prior set");
   if (!h->noise_set) return fail(h, BTI_ERR_STATE, "solve_matfree: noise not set");
   if (B == 0) return BTI_OK;
   if (!d_obs || !m_map) return fail(h, BTI_ERR_ARG, "solve_matfree: null pointer");
@@ -1414,7 +1495,7 @@ bti_status bti_apply_prior(bti_handle h, const double* v, double* out, int64_t B
   bti_status st = check_handle(h);
   if (st != BTI_OK) return st;
   if (B < 0) return fail(h, BTI_ERR_ARG, "apply_prior: B < 0");
-  if (!h->prior_set) return fail(h, BTI_ERR_STATE, "apply_prior: no SE prior set");
+  if (!h->prior_set) return fail(h, BTI_ERR_STATE, "apply_prior: no prior set");
   if (B == 0) return BTI_OK;
   if (!v || !out || v == out) return fail(h, BTI_ERR_ARG, "apply_prior: null or aliased pointers");
   return apply_se_rows(h, v, out, B * h->Nt);
@@ -1424,7 +1505,7 @@ bti_status bti_apply_postcov(bti_handle h, const double* v, double* out, int64_t
   bti_status st = check_handle(h);
   if (st != BTI_OK) return st;
   if (B < 0) return fail(h, BTI_ERR_ARG, "apply_postcov: B < 0");
-  if (!h->prior_set) return fail(h, BTI_ERR_STATE, "apply_postcov: no SE prior set");
+  if (!h->prior_set) return fail(h, BTI_ERR_STATE, "apply_postcov: no prior set");
   if (!h->K_factored || !h->op[BTI_OP_G].set) return fail(h, BTI_ERR_STATE, "apply_postcov: K not factored");
   if (B == 0) return BTI_OK;
   if (!v || !out || v == out) return fail(h, BTI_ERR_ARG, "apply_postcov: null or aliased pointers");

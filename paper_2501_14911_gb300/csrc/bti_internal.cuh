@@ -182,7 +182,8 @@ int gemm_f64(bool transB, int64_t M, int64_t N, int64_t K, double alpha, const d
 int gemm_df64(bool transB, int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda,
               int64_t sA, const double* Bm, int64_t ldb, int64_t sB, double beta, double* C, int64_t ldc,
               int64_t sC, int64_t batch, bool lower_only, cudaStream_t s);
-int se_axis_matrix(double* C, int n, double ell, double scale, cudaStream_t s);
+// X[r][e] *= W[e] for nrows rows of ne entries (the elliptic prior's spectral weights)
+int scale_blocks(double* X, const double* W, int64_t ne, int64_t nrows, cudaStream_t s);
 int k_diag_cumsum(double* WK, int64_t Nt, int64_t R, double sigma2, const double* diag,
                   cudaStream_t s);
 // Blocked Cholesky, lower, in place; Linv receives the inverses of the diagonal blocks

@@ -383,18 +383,16 @@ int gemm_f64(bool transB, int64_t M, int64_t N, int64_t K, double alpha, const d
   return 1;
 }
 
-// ------------------------------------------------------------------ SE prior, one axis
-// C[a][b] = scale * exp(-(a - b)^2 / (2 ell^2)); the 2-D SE covariance on a grid
-// with node index ix * gy + iy is C_x (x) C_y with scale = sigma on each axis.
-__global__ void se_axis_kernel(double* C, int n, double ell, double scale) {
-  int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= n * n) return;
-  int a = idx / n, b = idx - a * n;
-  double r = (double)(a - b);
-  C[idx] = scale * exp(-(r * r) / (2.0 * ell * ell));
+// ------------------------------------------------------------------ prior, spectral weights
+// X[r][e] *= W[e] for rows r < nrows of ne entries (the elliptic prior's DCT-domain weights)
+__global__ void scale_blocks_kernel(double* X, const double* __restrict__ W, int64_t ne, int64_t total) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < total) X[i] *= W[i % ne];
 }
-int se_axis_matrix(double* C, int n, double ell, double scale, cudaStream_t s) {
-  se_axis_kernel<<<(n * n + 255) / 256, 256, 0, s>>>(C, n, ell, scale);
+int scale_blocks(double* X, const double* W, int64_t ne, int64_t nrows, cudaStream_t s) {
+  const int64_t total = ne * nrows;
+  if (total <= 0) return 0;
+  scale_blocks_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(X, W, ne, total);
   return 1;
 }
 

@@ -728,3 +728,40 @@ def test_tensor_core_wait_timeout_is_reported_and_recoverable():
     h.sync()
     h.close()
     assert relb(host(d), oracle.p2o_apply(F, host(m))) < 1e-3
+
+
+@pytest.mark.parametrize("store", [bti.F64, bti.DF64], ids=["f64", "df64"])
+def test_elliptic_prior_full_inversion(store):
+    """The elliptic prior of Eq. (5.1), Gamma_prior = (alpha1 I - alpha2 Delta_h)^{-2},
+    applied by DCT on each axis: Gamma_prior v, K, m_map, q_map, Gamma_post(m) v and the
+    matrix-free solve against the oracle with the dense inverse of A_s^2."""
+    p = synthetic.small("elliptic_inv", 8, 12, 5, 24, Nq=3)
+    F, Fq = p.blocks_F(), p.blocks_Fq()
+    A = oracle.elliptic_operator(p.gx, p.gy, 1.3, 0.7).toarray()
+    Cs = np.linalg.inv(A @ A)
+    Cs = 0.5 * (Cs + Cs.T)
+    G = oracle.prior_blocks(F, Cs)
+    h = make_handle(F, Fq, store)
+    h.set_prior_elliptic_grid(p.gx, p.gy, 1.3, 0.7, store)
+    h.set_noise(p.sigma2)
+    v = p.vectors_m(2)
+    out = torch.empty((2, p.Nt, p.Nm), dtype=torch.float64, device="cuda")
+    h.apply_prior(cuda(v), out)
+    assert relb(host(out), oracle.prior_apply(Cs, v)) < 1e-12
+    d = p.vectors_d(2)
+    h.build_K()
+    h.factor_K()
+    m = torch.empty((2, p.Nt, p.Nm), dtype=torch.float64, device="cuda")
+    q = torch.empty((2, p.Nt, p.Nq), dtype=torch.float64, device="cuda")
+    h.infer_map(cuda(d), m)
+    h.predict_qoi(m, q)
+    L = oracle.cholesky_lower(oracle.assemble_K(F, G, p.sigma2))
+    m_or = oracle.map_point(F, G, p.sigma2, d, L=L)
+    assert relb(host(m), m_or) < 1e-11
+    assert relb(host(q), oracle.qoi_map(Fq, m_or)) < 1e-11
+    h.apply_postcov(cuda(v), out)
+    assert relb(host(out), oracle.posterior_cov_apply(F, G, Cs, p.sigma2, v, L=L)) < 1e-10
+    m.zero_()
+    h.solve_matfree(cuda(d), m, refine=0, tol=1e-12, max_inner=4000)
+    h.close()
+    assert relb(host(m), m_or) < 1e-10
