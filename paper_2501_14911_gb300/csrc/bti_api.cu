@@ -324,7 +324,7 @@ bti_status apply_fwd_t(bti_ctx* h, const OpStore& o, const void* in, void* out, 
   const int64_t nf = h->nf, Nm = h->Nm, R = o.R, Nt = h->Nt;
   size_t n_mhat = (size_t)B * nf * Nm;
   // FP16 blocks with B >= 8 vectors: the tensor-core product (its own chunking)
-  const bool tc = o.prec == BTI_P_F16 && h->tc_enabled && tc_fwd_f16_supported(Nm, B);
+  const bool tc = o.prec == BTI_P_F16 && h->tc_enabled && tc_fwd_f16_supported(Nm, R, B);
   size_t n_part = prod_fwd_partial_elems(nf, R, Nm, B);
   if (tc && tc_fwd_partial_elems(nf, R, Nm, B) > n_part) n_part = tc_fwd_partial_elems(nf, R, Nm, B);
   size_t n_dhat = (size_t)B * nf * R;

@@ -216,7 +216,7 @@ int noise_residual_f64(double* r, const double* x, const double* diag, int64_t n
 // multiple of 4.  Writes per-chunk partials into `partial` (tc_fwd_partial_elems elements)
 // and their fixed-order sum into dhat [B][nf][R]; err is set when a bounded device wait
 // gave up.  *launches receives the number of kernels launched.
-bool tc_fwd_f16_supported(int64_t Nm, int64_t B);
+bool tc_fwd_f16_supported(int64_t Nm, int64_t R, int64_t B);
 size_t tc_fwd_partial_elems(int64_t nf, int64_t R, int64_t Nm, int64_t B);
 // drop_stage >= 0 (test hook): the producer withholds that stage's tile, so the kernel's bounded
 // waits run out and it reports through err.

@@ -521,9 +521,12 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 }  // namespace
 
-bool tc_fwd_f16_supported(int64_t Nm, int64_t B) {
-  // rows of F-hat as FP16 halves must be 16-byte strided for TMA (N_m a multiple of 4)
-  return B >= 8 && Nm % 4 == 0 && 2 * Nm <= INT32_MAX && encode_fn() != nullptr;
+bool tc_fwd_f16_supported(int64_t Nm, int64_t R, int64_t B) {
+  // rows of F-hat as FP16 halves must be 16-byte strided for TMA (N_m a multiple of 4), and
+  // the row tiles times the vector groups must fit the grid's z extent
+  const int64_t BG = B > 16 ? 32 : 16;
+  const int64_t tiles = ((R + kTcRows - 1) / kTcRows) * ((B + BG - 1) / BG);
+  return B >= 8 && Nm % 4 == 0 && 2 * Nm <= INT32_MAX && tiles <= 65535 && encode_fn() != nullptr;
 }
 
 size_t tc_fwd_partial_elems(int64_t nf, int64_t R, int64_t Nm, int64_t B) {
@@ -579,7 +582,7 @@ bool tc_adj_f16_supported(int64_t Nm, int64_t R, int64_t B) {
   const int64_t BG = B > 16 ? 32 : 16;
   // the whole B operand (R rows of i in 64-row blocks) stays in shared memory
   return B >= 8 && Nm % 4 == 0 && 2 * Nm <= INT32_MAX && ((R + 63) / 64) * 2 * BG * 128 <= 128 * 1024 &&
-         encode_fn() != nullptr;
+         (B + BG - 1) / BG <= 65535 && encode_fn() != nullptr;
 }
 
 cudaError_t launch_prod_adj_f16_tc(const void* Fhat, const float* scale, const float2* dhat, float2* mhat,
