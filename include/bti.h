@@ -181,9 +181,23 @@ bti_status bti_factor_K(bti_handle h);
  * bti_factor_K; the strict upper triangle is undefined.  Requires build_K. */
 bti_status bti_copy_K(bti_handle h, double* dst);
 
+/* Explicit inverse of K for the online phase (Sec. 4, Phase 4: the triangular solves
+ * of Eq. (4.13) moved offline).  enable = 1, after bti_factor_K: forms K^{-1} by
+ * solving with the factor against the identity (double-FP32 GEMMs, 2 n^3 flops for
+ * n = N_t N_d) and keeps it on the device as float pairs (hi, lo), 8 n^2 bytes.
+ * bti_infer_map and bti_online then apply K^{-1} as one dense product, in double-FP32
+ * arithmetic (about 48 significant bits), instead of the n / 64 sequential blocked
+ * solves.  The inverse belongs to the factor it was formed from: after a new
+ * bti_factor_K the solves return to the factor until this is called again.
+ * enable = 0 releases the inverse.  Requires factor_K for enable = 1 (BTI_ERR_STATE);
+ * BTI_ERR_OOM if the 16 n^2-byte peak (inverse plus FP64 temporary) does not fit.
+ * Synchronises. */
+bti_status bti_invert_K(bti_handle h, int enable);
+
 /* m_map = G^* K^{-1} d_obs for B observation vectors (Eq. (4.13), zero prior
  * mean): d_obs [B][N_t][N_d] (double) -> m_map [B][N_t][N_m] (double).
- * K^{-1} is applied by the two triangular solves with the factor; with
+ * K^{-1} is applied by the two triangular solves with the factor (or, after
+ * bti_invert_K, by one product with the explicit inverse); with
  * refine_iters > 0 that many steps of iterative refinement x += K^{-1}(d - K x)
  * follow, the residual evaluated with the FP64 spectral operators.
  * Requires factor_K. */

@@ -77,6 +77,7 @@ def lib():
         "bti_build_K": ([vp, i64], st),
         "bti_build_K_prec": ([vp, i64, ip], st),
         "bti_factor_K": ([vp], st),
+        "bti_invert_K": ([vp, ip], st),
         "bti_copy_K": ([vp, vp], st),
         "bti_infer_map": ([vp, vp, vp, i64, ip], st),
         "bti_predict_qoi": ([vp, vp, vp, i64], st),
@@ -261,6 +262,10 @@ class Handle:
 
     def factor_K(self):
         self._check(lib().bti_factor_K(self._h))
+
+    def invert_K(self, enable=True):
+        """Form K^{-1} from the factor (or release it) so infer_map / online apply it as one product."""
+        self._check(lib().bti_invert_K(self._h, int(bool(enable))))
 
     def copy_K(self, out=None):
         import torch

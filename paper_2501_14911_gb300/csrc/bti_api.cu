@@ -63,6 +63,9 @@ struct bti_ctx {
   double* K = nullptr;           // [n][n], lower triangle: K, then L after factor_K
   double* Linv = nullptr;        // inverses of the factor's diagonal blocks
   bool K_built = false, K_factored = false;
+  int64_t factor_gen = 0;        // incremented by every successful factor_K
+  float2* Kinv = nullptr;        // explicit K^{-1} as float pairs [n][kinv_ld(n)] (bti_invert_K)
+  int64_t kinv_gen = -1;         // factor_gen it was formed from
   int* status = nullptr;  // device status word
   void* ws = nullptr;     // spectral workspace
   size_t ws_bytes = 0;
@@ -548,6 +551,7 @@ bti_status bti_destroy(bti_handle h) {
   dev_freep(h->Q);
   dev_freep(h->covq);
   dev_freep(h->Linv);
+  dev_freep(h->Kinv);
   dev_freep(h->status);
   dev_free(h->ws);
   dev_freep(h->wsolve);
@@ -867,6 +871,53 @@ bti_status bti_factor_K(bti_handle h) {
     return fail(h, BTI_ERR_NOT_SPD, buf);
   }
   h->K_factored = true;
+  ++h->factor_gen;
+  return BTI_OK;
+}
+
+static bool kinv_ready(const bti_ctx* h) { return h->Kinv && h->K_factored && h->kinv_gen == h->factor_gen; }
+
+bti_status bti_invert_K(bti_handle h, int enable) {
+  bti_status st = check_handle(h);
+  if (st != BTI_OK) return st;
+  drop_online_graph_any(h);
+  if (!enable) {
+    cudaStreamSynchronize(h->stream);
+    dev_freep(h->Kinv);
+    h->kinv_gen = -1;
+    return BTI_OK;
+  }
+  if (!h->K_factored) return fail(h, BTI_ERR_STATE, "invert_K: K not factored");
+  if (kinv_ready(h)) return BTI_OK;
+  const int64_t n = h->Nt * h->Nd;
+  const int64_t ldk = kinv_ld(n);
+  cudaStream_t s = h->stream;
+  if (!h->Kinv) {
+    st = dev_alloc(h, (void**)&h->Kinv, sizeof(float2) * (size_t)n * ldk, "alloc K inverse");
+    if (st != BTI_OK) return st;
+  }
+  st = ensure(h, (void**)&h->wsolve, &h->wsolve_bytes, sizeof(double) * trsm_work_elems(n, n), "solve workspace");
+  if (st != BTI_OK) return st;
+  double* X = nullptr;
+  st = dev_alloc(h, (void**)&X, sizeof(double) * (size_t)n * n, "K inverse temporary");
+  if (st != BTI_OK) {
+    dev_freep(h->Kinv);
+    return st;
+  }
+  // rows of X: K^{-1} e_b (= row b of the symmetric K^{-1})
+  int64_t nl = identity_blocks(X, 1, n, s);
+  nl += trsm_lower_f64(h->K, h->Linv, n, X, n, h->wsolve, h->status, s, true);
+  nl += split_to_pairs(X, h->Kinv, n, ldk, s);
+  count_dense(h, nl);
+  st = launched(h, "invert_K");
+  bti_status sy = cuda_check(h, cudaStreamSynchronize(s), "invert_K sync");
+  dev_freep(X);
+  if (st == BTI_OK) st = sy;
+  if (st != BTI_OK) {
+    dev_freep(h->Kinv);
+    return st;
+  }
+  h->kinv_gen = h->factor_gen;
   return BTI_OK;
 }
 
@@ -880,6 +931,18 @@ bti_status bti_copy_K(bti_handle h, double* dst) {
                                        h->stream), "copy_K");
 }
 
+// Dense-solve workspace of infer_map for B vectors: x and r ([B][n] each), then either the
+// blocked solves' work or the explicit inverse's correction [B][n] and partials; at least
+// the Cholesky panel work.
+static bti_status reserve_solve(bti_ctx* h, int64_t B) {
+  const int64_t n = h->Nt * h->Nd;
+  size_t tail = trsm_work_elems(n, B);
+  if (kinv_ready(h)) tail = std::max(tail, (size_t)B * n + kinv_apply_work_elems(n, B));
+  size_t need = sizeof(double) * ((size_t)2 * B * n + tail);
+  size_t chol = sizeof(double) * (size_t)n * kCholNB;
+  return ensure(h, (void**)&h->wsolve, &h->wsolve_bytes, need > chol ? need : chol, "solve workspace");
+}
+
 static bti_status infer_map_impl(bti_handle h, const double* d_obs, double* m_map, int64_t B, int refine_iters) {
   bti_status st = check_handle(h);
   if (st != BTI_OK) return st;
@@ -889,18 +952,22 @@ static bti_status infer_map_impl(bti_handle h, const double* d_obs, double* m_ma
   if (B == 0) return BTI_OK;
   if (!d_obs || !m_map) return fail(h, BTI_ERR_ARG, "infer_map: null pointer");
   const int64_t n = h->Nt * h->Nd;
-  // solve workspace: x [B][n], r [B][n], trsm work [B][nb], and Cholesky panel work
-  size_t need = sizeof(double) * ((size_t)2 * B * n + trsm_work_elems(n, B));
-  size_t chol = sizeof(double) * (size_t)n * kCholNB;
-  st = ensure(h, (void**)&h->wsolve, &h->wsolve_bytes, need > chol ? need : chol, "solve workspace");
+  st = reserve_solve(h, B);
   if (st != BTI_OK) return st;
+  // solve workspace: x [B][n], r [B][n], then the explicit-inverse correction [B][n] and
+  // its partials, or the blocked solves' work
   double* x = h->wsolve;
   double* r = x + (size_t)B * n;
   double* work = r + (size_t)B * n;
   cudaStream_t s = h->stream;
-  st = cuda_check(h, cudaMemcpyAsync(x, d_obs, sizeof(double) * B * n, cudaMemcpyDeviceToDevice, s), "copy d_obs");
-  if (st != BTI_OK) return st;
-  count_dense(h, trsm_lower_f64(h->K, h->Linv, n, x, B, work, h->status, s, h->dense_prec == BTI_P_DF64));
+  const bool inv = kinv_ready(h);
+  // x = K^{-1} v (v != x), by the explicit inverse or the blocked triangular solves
+  auto solve_into = [&](const double* v, double* xo) -> int64_t {
+    if (inv) return kinv_apply(h->Kinv, n, v, B, xo, work + (size_t)B * n, s);
+    if (v != xo) cudaMemcpyAsync(xo, v, sizeof(double) * B * n, cudaMemcpyDeviceToDevice, s);
+    return trsm_lower_f64(h->K, h->Linv, n, xo, B, work, h->status, s, h->dense_prec == BTI_P_DF64);
+  };
+  count_dense(h, solve_into(d_obs, x));
   st = launched(h, "triangular solves");
   if (st != BTI_OK) return st;
   for (int it = 0; it < refine_iters; ++it) {
@@ -916,8 +983,13 @@ static bti_status infer_map_impl(bti_handle h, const double* d_obs, double* m_ma
       nl += noise_residual_f64(r, x, h->noise_diag, n, B, s);
     else
       nl += axpby_f64(r, x, -h->sigma2, 1.0, B * n, s);
-    nl += trsm_lower_f64(h->K, h->Linv, n, r, B, work, h->status, s, h->dense_prec == BTI_P_DF64);
-    nl += axpby_f64(x, r, 1.0, 1.0, B * n, s);
+    if (inv) {
+      nl += solve_into(r, work);
+      nl += axpby_f64(x, work, 1.0, 1.0, B * n, s);
+    } else {
+      nl += solve_into(r, r);
+      nl += axpby_f64(x, r, 1.0, 1.0, B * n, s);
+    }
     count_dense(h, nl);
     st = launched(h, "refinement");
     if (st != BTI_OK) return st;
@@ -1589,10 +1661,7 @@ bti_status bti_predict_qoi(bti_handle h, const double* m_map, double* q_map, int
 
 // Workspace the online phase needs for B vectors, allocated before a capture.
 static bti_status reserve_online(bti_ctx* h, int64_t B) {
-  const int64_t n = h->Nt * h->Nd;
-  size_t need = sizeof(double) * ((size_t)2 * B * n + trsm_work_elems(n, B));
-  size_t chol = sizeof(double) * (size_t)n * kCholNB;
-  bti_status st = ensure(h, (void**)&h->wsolve, &h->wsolve_bytes, need > chol ? need : chol, "solve workspace");
+  bti_status st = reserve_solve(h, B);
   if (st != BTI_OK) return st;
   // spectral workspace: the larger of an adjoint (G*) and a forward (F, F_q) product
   const int64_t nf = h->nf, Nm = h->Nm;

@@ -196,6 +196,14 @@ constexpr int kCholNB = 64;
 int64_t trsm_lower_f64(const double* Lm, const double* Linv, int64_t n, double* X, int64_t B,
                        double* work, const int* status, cudaStream_t s, bool dd = false);
 size_t trsm_work_elems(int64_t n, int64_t B);
+// Explicit inverse for the online solve: Kinv [n][kinv_ld(n)] float pairs (hi, lo) of K^{-1}
+// (zero padding); X [B][n] = rows K^{-1} D[b] for D [B][n] (X != D); work of
+// kinv_apply_work_elems(n, B) doubles.  split_to_pairs: FP64 X [n][n] -> pairs Y [n][ldk].
+int64_t kinv_ld(int64_t n);
+size_t kinv_apply_work_elems(int64_t n, int64_t B);
+int64_t kinv_apply(const float2* Kinv, int64_t n, const double* D, int64_t B, double* X, double* work,
+                   cudaStream_t s);
+int split_to_pairs(const double* X, float2* Y, int64_t n, int64_t ldk, cudaStream_t s);
 int axpby_f64(double* y, const double* x, double a, double b, int64_t n, cudaStream_t s);
 // FP32 Gram product W = A B^T into an FP64 matrix (lower tiles) and the FP64 -> FP32 copy
 int sgemm_nt_lower_to_f64(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* Bm,

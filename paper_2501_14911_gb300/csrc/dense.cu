@@ -589,6 +589,216 @@ int64_t trsm_lower_f64(const double* Lm, const double* Linv, int64_t n, double* 
   return launches;
 }
 
+// ------------------------------------------------------------------ explicit inverse of K
+// The online solve x = K^{-1} d as one dense product with a precomputed K^{-1} (Eq. (4.13)
+// with the two triangular solves folded offline into the inverse): the blocked solves
+// above walk the factor's n / 64 diagonal blocks in sequence, each step a thin GEMM;
+// this product has no sequential dependence and keeps every SM busy.
+//
+// Kinv: [n][ldk] float pairs (hi, lo), ldk a multiple of 16 with zero padding, so every
+// 16-wide k-step reads whole 16-byte vectors.  D, X: FP64 [nb][n] (rows = right-hand
+// sides).  Products in double-FP32 arithmetic on the FP32 pipes (as gemm_df64).  Stream-K
+// partition: the (row tile, k-step) iterations are split evenly over a grid sized to the
+// resident CTAs, each CTA writes one FP64 partial tile per row tile it touches, and
+// kinv_reduce_kernel sums a tile's partials in CTA order (deterministic).
+constexpr int KIBM = 128, KIBK = 16;
+
+__global__ void split_pairs_kernel(const double* __restrict__ X, float2* __restrict__ Y, int64_t n, int64_t ldk) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * ldk) return;
+  const int64_t i = e / ldk, j = e - i * ldk;
+  float h = 0.f, l = 0.f;
+  if (j < n) dd_split(X[i * n + j], h, l);
+  Y[e] = make_float2(h, l);
+}
+int split_to_pairs(const double* X, float2* Y, int64_t n, int64_t ldk, cudaStream_t s) {
+  const int64_t total = n * ldk;
+  if (total <= 0) return 0;
+  split_pairs_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(X, Y, n, ldk);
+  return 1;
+}
+
+template <int BR, int TM, int TR>
+__global__ void __launch_bounds__(256)
+kinv_apply_kernel(const float2* __restrict__ Kinv, int64_t ldk, int64_t n, const double* __restrict__ D,
+                  int64_t ldd, int64_t nb, double* __restrict__ part, int64_t per, int64_t total, int64_t kpt,
+                  int span) {
+  constexpr int RG = BR / TR, YG = KIBM / TM;
+  static_assert(RG * YG == 256, "256 threads: rhs groups x row groups");
+  constexpr int NA = KIBM * KIBK / 2 / 256;        // float4 (two k) of K^{-1} per thread per k-step
+  constexpr int ND = (BR * KIBK + 255) / 256;      // FP64 elements of D per thread per k-step
+  extern __shared__ float2 kinv_smem[];  // As [2][KIBK][KIBM + 1], then Ds [2][KIBK][BR + 1]
+  float2(*As)[KIBK][KIBM + 1] = reinterpret_cast<float2(*)[KIBK][KIBM + 1]>(kinv_smem);
+  float2(*Ds)[KIBK][BR + 1] = reinterpret_cast<float2(*)[KIBK][BR + 1]>(kinv_smem + 2 * KIBK * (KIBM + 1));
+  const int tid = threadIdx.x;
+  const int tx = tid % RG, ty = tid / RG;
+  int64_t it = (int64_t)blockIdx.x * per;
+  const int64_t end = min(total, it + per);
+  const int64_t first_tile = it / kpt;
+  float4 ra[NA];
+  double rd[ND];
+  while (it < end) {
+    const int64_t t = it / kpt;
+    const int64_t kb = it - t * kpt;
+    const int64_t ke = min(kpt, kb + (end - it));
+    const int64_t m0 = t * KIBM;
+    auto load = [&](int64_t ks) {
+      const int64_t k0 = ks * KIBK;
+#pragma unroll
+      for (int e = 0; e < NA; ++e) {
+        const int idx = e * 256 + tid;
+        const int r = idx >> 3, q = idx & 7;
+        const int64_t row = m0 + r;
+        ra[e] = row < n ? __ldg(reinterpret_cast<const float4*>(Kinv + row * ldk + k0 + 2 * q))
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int e = 0; e < ND; ++e) {
+        const int idx = e * 256 + tid;
+        const int b = idx / KIBK, c = idx % KIBK;
+        const int64_t k = k0 + c;
+        rd[e] = (idx < BR * KIBK && b < nb && k < n) ? D[b * ldd + k] : 0.0;
+      }
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+      for (int e = 0; e < NA; ++e) {
+        const int idx = e * 256 + tid;
+        const int r = idx >> 3, q = idx & 7;
+        As[buf][2 * q][r] = make_float2(ra[e].x, ra[e].y);
+        As[buf][2 * q + 1][r] = make_float2(ra[e].z, ra[e].w);
+      }
+#pragma unroll
+      for (int e = 0; e < ND; ++e) {
+        const int idx = e * 256 + tid;
+        if (idx < BR * KIBK) {
+          float h, l;
+          dd_split(rd[e], h, l);
+          Ds[buf][idx % KIBK][idx / KIBK] = make_float2(h, l);
+        }
+      }
+    };
+    float sh[TM][TR], sl[TM][TR];
+#pragma unroll
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+      for (int b = 0; b < TR; ++b) sh[a][b] = sl[a][b] = 0.f;
+    load(kb);
+    store(0);
+    __syncthreads();
+    for (int64_t ks = kb; ks < ke; ++ks) {
+      const int buf = (int)((ks - kb) & 1);
+      const bool more = ks + 1 < ke;
+      if (more) load(ks + 1);
+#pragma unroll
+      for (int kk = 0; kk < KIBK; ++kk) {
+        float2 av[TM], bv[TR];
+#pragma unroll
+        for (int a = 0; a < TM; ++a) av[a] = As[buf][kk][ty + YG * a];
+#pragma unroll
+        for (int b = 0; b < TR; ++b) bv[b] = Ds[buf][kk][tx + RG * b];
+#pragma unroll
+        for (int a = 0; a < TM; ++a)
+#pragma unroll
+          for (int b = 0; b < TR; ++b) dd_mac(sh[a][b], sl[a][b], av[a].x, av[a].y, bv[b].x, bv[b].y);
+      }
+      if (more) store(buf ^ 1);
+      __syncthreads();
+    }
+    double* P = part + ((blockIdx.x * (int64_t)span + (t - first_tile)) * BR) * KIBM;
+#pragma unroll
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+      for (int b = 0; b < TR; ++b) P[(tx + RG * b) * KIBM + ty + YG * a] = (double)sh[a][b] + (double)sl[a][b];
+    it += ke - kb;
+  }
+}
+
+// X[q][row] = sum over the CTAs that covered row tile t of their partials (CTA order).
+__global__ void kinv_reduce_kernel(const double* __restrict__ part, double* __restrict__ X, int64_t ldx,
+                                   int64_t n, int64_t nb, int BR, int64_t per, int64_t kpt, int span) {
+  const int64_t t = blockIdx.x;
+  const int q = blockIdx.y;
+  const int64_t row = t * KIBM + threadIdx.x;
+  if (row >= n || q >= nb) return;
+  const int64_t c0 = (t * kpt) / per, c1 = ((t + 1) * kpt - 1) / per;
+  double sum = 0.0;
+  for (int64_t c = c0; c <= c1; ++c) {
+    const int64_t slot = t - (c * per) / kpt;
+    sum += part[((c * span + slot) * BR + q) * KIBM + threadIdx.x];
+  }
+  X[q * ldx + row] = sum;
+}
+
+namespace {
+struct KinvPlan {
+  int BR;
+  int64_t tiles, kpt, total, per, ctas;
+  int span;
+};
+constexpr size_t kinv_smem_bytes(int BR) { return sizeof(float2) * 2 * KIBK * ((KIBM + 1) + (BR + 1)); }
+// CTAs of kinv_apply_kernel<BR, TM, TR> resident per SM (first call also lifts the
+// kernel's dynamic shared-memory limit above 48 KB)
+template <int BR, int TM, int TR>
+int kinv_resident() {
+  static int occ = 0;
+  if (occ == 0) {
+    cudaFuncSetAttribute(kinv_apply_kernel<BR, TM, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kinv_smem_bytes(BR));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kinv_apply_kernel<BR, TM, TR>, 256, kinv_smem_bytes(BR));
+    if (occ <= 0) occ = 1;
+  }
+  return occ;
+}
+KinvPlan kinv_plan(int64_t n, int64_t ldk, int64_t nb) {
+  KinvPlan p;
+  p.BR = nb > 16 ? 64 : (nb > 4 ? 16 : 4);
+  const int occ = p.BR == 64 ? kinv_resident<64, 8, 4>() : (p.BR == 16 ? kinv_resident<16, 8, 1>()
+                                                                       : kinv_resident<4, 2, 1>());
+  p.tiles = (n + KIBM - 1) / KIBM;
+  p.kpt = ldk / KIBK;
+  p.total = p.tiles * p.kpt;
+  const int64_t slots = (int64_t)num_sms() * occ;
+  p.per = (p.total + slots - 1) / slots;
+  p.ctas = (p.total + p.per - 1) / p.per;
+  p.span = (int)((p.per + p.kpt - 1) / p.kpt + 1);
+  return p;
+}
+}  // namespace
+
+int64_t kinv_ld(int64_t n) { return (n + KIBK - 1) / KIBK * KIBK; }
+
+size_t kinv_apply_work_elems(int64_t n, int64_t B) {
+  if (n <= 0 || B <= 0) return 0;
+  KinvPlan p = kinv_plan(n, kinv_ld(n), B > 64 ? 64 : B);
+  return (size_t)p.ctas * p.span * p.BR * KIBM;
+}
+
+int64_t kinv_apply(const float2* Kinv, int64_t n, const double* D, int64_t B, double* X, double* work,
+                   cudaStream_t s) {
+  const int64_t ldk = kinv_ld(n);
+  int64_t launches = 0;
+  for (int64_t q0 = 0; q0 < B; q0 += 64) {
+    const int64_t nb = B - q0 < 64 ? B - q0 : 64;
+    const KinvPlan p = kinv_plan(n, ldk, nb);
+    const double* Dq = D + q0 * n;
+    double* Xq = X + q0 * n;
+    if (p.BR == 64)
+      kinv_apply_kernel<64, 8, 4><<<(unsigned)p.ctas, 256, kinv_smem_bytes(64), s>>>(Kinv, ldk, n, Dq, n, nb, work, p.per, p.total,
+                                                                  p.kpt, p.span);
+    else if (p.BR == 16)
+      kinv_apply_kernel<16, 8, 1><<<(unsigned)p.ctas, 256, kinv_smem_bytes(16), s>>>(Kinv, ldk, n, Dq, n, nb, work, p.per, p.total,
+                                                                  p.kpt, p.span);
+    else
+      kinv_apply_kernel<4, 2, 1><<<(unsigned)p.ctas, 256, kinv_smem_bytes(4), s>>>(Kinv, ldk, n, Dq, n, nb, work, p.per, p.total,
+                                                                 p.kpt, p.span);
+    kinv_reduce_kernel<<<dim3((unsigned)p.tiles, (unsigned)nb), KIBM, 0, s>>>(work, Xq, n, n, nb, p.BR, p.per,
+                                                                             p.kpt, p.span);
+    launches += 2;
+  }
+  return launches;
+}
+
 __global__ void axpby_kernel(double* y, const double* x, double a, double b, int64_t n) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] = fma(a, x[i], b * y[i]);

@@ -765,3 +765,86 @@ def test_elliptic_prior_full_inversion(store):
     h.solve_matfree(cuda(d), m, refine=0, tol=1e-12, max_inner=4000)
     h.close()
     assert relb(host(m), m_or) < 1e-10
+
+
+@pytest.mark.parametrize("B", [1, 5, 20, 70], ids=["b1", "b5", "b20", "b70"])
+def test_explicit_inverse_online_solve(B):
+    """bti_invert_K: x = K^{-1} d as one double-FP32 product with the explicit inverse
+    (float pairs; stream-K partials summed in CTA order; 4-, 16- and 64-wide right-hand-
+    side tiles and a second 64-chunk at B = 70).  m_map matches the oracle, refinement
+    brings it to the FP64 tolerance, a new factorisation returns to the triangular solves
+    until the inverse is formed again, and release works."""
+    p, F, Fq, G, _ = tiny_problem()
+    d = p.vectors_d(B)
+    m_or = oracle.map_point(F, G, p.sigma2, d)
+    h = make_handle(F, Fq, bti.DF64)
+    h.set_prior_se_grid(p.gx, p.gy, p.ell, p.sigma_p, bti.DF64)
+    h.set_noise(p.sigma2)
+    with pytest.raises(bti.BtiError) as e:
+        h.invert_K()
+    assert e.value.status == 3
+    h.build_K()
+    h.factor_K()
+    m = torch.empty((B, p.Nt, p.Nm), dtype=torch.float64, device="cuda")
+    h.profile_enable(True)
+    h.profile_read()
+    h.infer_map(cuda(d), m)
+    n_trsm = h.profile_read()[0]["dense"][1]
+    assert relb(host(m), m_or) < 1e-12
+    h.invert_K()
+    h.profile_read()  # drop the launches of forming the inverse
+    m.zero_()
+    h.infer_map(cuda(d), m)
+    n_inv = h.profile_read()[0]["dense"][1]
+    assert n_inv + 20 < n_trsm  # a product and a reduction per 64 vectors, not 2 n / 64 blocked steps
+    assert relb(host(m), m_or) < 1e-10
+    h.infer_map(cuda(d), m, refine_iters=1)
+    assert relb(host(m), m_or) < 1e-12
+    # the online graph applies the inverse too
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        h.set_stream(stream)
+        q = torch.empty((B, p.Nt, p.Nq), dtype=torch.float64, device="cuda")
+        m2 = torch.empty_like(m)
+        h.online(cuda(d), m2, q, refine_iters=1)
+        assert relb(host(m2), m_or) < 1e-12
+        assert relb(host(q), oracle.qoi_map(Fq, m_or)) < 1e-12
+    torch.cuda.synchronize()
+    h.set_stream(torch.cuda.current_stream())
+    # a new factor: the stale inverse is not used
+    h.set_noise(2.0 * p.sigma2)
+    h.build_K()
+    h.factor_K()
+    h.profile_read()
+    h.infer_map(cuda(d), m)
+    assert h.profile_read()[0]["dense"][1] == n_trsm
+    assert relb(host(m), oracle.map_point(F, G, 2.0 * p.sigma2, d)) < 1e-12
+    h.invert_K()
+    h.infer_map(cuda(d), m)
+    assert relb(host(m), oracle.map_point(F, G, 2.0 * p.sigma2, d)) < 1e-10
+    h.invert_K(False)
+    h.infer_map(cuda(d), m)
+    assert relb(host(m), oracle.map_point(F, G, 2.0 * p.sigma2, d)) < 1e-12
+    h.profile_enable(False)
+    h.close()
+
+
+def test_explicit_inverse_ragged_size():
+    """n = 150 (two 128-row tiles, the second ragged; rows padded to 160 columns) with a
+    diagonal noise covariance."""
+    p = synthetic.small("kinv_ragged", 6, 6, 5, 30, Nq=3)
+    F = p.blocks_F()
+    Cs = oracle.se_covariance(6, 6, 2.0, 1.0)
+    G = oracle.prior_blocks(F, Cs)
+    var = 1e-3 * (1.0 + np.arange(30 * 5).reshape(30, 5) % 7)
+    d_obs = p.vectors_d(7)
+    h = make_handle(F, p.blocks_Fq())
+    h.set_prior_se_grid(6, 6, 2.0, 1.0)
+    h.set_noise(0.0, cuda(var))
+    h.build_K(col_block=37)
+    h.factor_K()
+    h.invert_K()
+    m_map = torch.empty((7, 30, 36), dtype=torch.float64, device="cuda")
+    h.infer_map(cuda(d_obs), m_map, refine_iters=1)
+    assert relb(host(m_map), oracle.map_point(F, G, var, d_obs)) < 1e-11
+    h.close()
