@@ -601,47 +601,53 @@ int64_t trsm_lower_f64(const double* Lm, const double* Linv, int64_t n, double* 
 // partition: the (row tile, k-step) iterations are split evenly over a grid sized to the
 // resident CTAs, each CTA writes one FP64 partial tile per row tile it touches, and
 // kinv_reduce_kernel sums a tile's partials in CTA order (deterministic).
-constexpr int KIBM = 128, KIBK = 16;
+constexpr int KIBK = 16;
 
-__global__ void split_pairs_kernel(const double* __restrict__ X, float2* __restrict__ Y, int64_t n, int64_t ldk) {
+__global__ void split_pairs_kernel(const double* __restrict__ X, int64_t ldx, float2* __restrict__ Y, int64_t rows,
+                                   int64_t n, int64_t ldk) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n * ldk) return;
+  if (e >= rows * ldk) return;
   const int64_t i = e / ldk, j = e - i * ldk;
   float h = 0.f, l = 0.f;
-  if (j < n) dd_split(X[i * n + j], h, l);
+  if (j < n) dd_split(X[i * ldx + j], h, l);
   Y[e] = make_float2(h, l);
 }
-int split_to_pairs(const double* X, float2* Y, int64_t n, int64_t ldk, cudaStream_t s) {
-  const int64_t total = n * ldk;
+static int split_rows_to_pairs(const double* X, int64_t ldx, float2* Y, int64_t rows, int64_t n, int64_t ldk,
+                               cudaStream_t s) {
+  const int64_t total = rows * ldk;
   if (total <= 0) return 0;
-  split_pairs_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(X, Y, n, ldk);
+  split_pairs_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(X, ldx, Y, rows, n, ldk);
   return 1;
 }
+int split_to_pairs(const double* X, float2* Y, int64_t n, int64_t ldk, cudaStream_t s) {
+  return split_rows_to_pairs(X, n, Y, n, n, ldk, s);
+}
 
-template <int BR, int TM, int TR>
+// One CTA: BM rows of K^{-1} x BR right-hand sides; thread (tx, ty) owns rows ty + YG a
+// (a < TM) and right-hand sides tx + RG b (b < TR).  Dp: the right-hand sides as float
+// pairs [BR][ldk] (rows >= nb read as zeros).
+template <int BM, int BR, int TM, int TR>
 __global__ void __launch_bounds__(256)
-kinv_apply_kernel(const float2* __restrict__ Kinv, int64_t ldk, int64_t n, const double* __restrict__ D,
-                  int64_t ldd, int64_t nb, double* __restrict__ part, int64_t per, int64_t total, int64_t kpt,
-                  int span) {
-  constexpr int RG = BR / TR, YG = KIBM / TM;
+kinv_apply_kernel(const float2* __restrict__ Kinv, int64_t ldk, int64_t n, const float2* __restrict__ Dp,
+                  int64_t nb, double* __restrict__ part, int64_t per, int64_t total, int64_t kpt, int span) {
+  constexpr int RG = BR / TR, YG = BM / TM;
   static_assert(RG * YG == 256, "256 threads: rhs groups x row groups");
-  constexpr int NA = KIBM * KIBK / 2 / 256;        // float4 (two k) of K^{-1} per thread per k-step
-  constexpr int ND = (BR * KIBK + 255) / 256;      // FP64 elements of D per thread per k-step
-  extern __shared__ float2 kinv_smem[];  // As [2][KIBK][KIBM + 1], then Ds [2][KIBK][BR + 1]
-  float2(*As)[KIBK][KIBM + 1] = reinterpret_cast<float2(*)[KIBK][KIBM + 1]>(kinv_smem);
-  float2(*Ds)[KIBK][BR + 1] = reinterpret_cast<float2(*)[KIBK][BR + 1]>(kinv_smem + 2 * KIBK * (KIBM + 1));
+  constexpr int NA = BM * KIBK / 2 / 256;            // float4 (two k) of K^{-1} per thread per k-step
+  constexpr int ND = (BR * KIBK / 2 + 255) / 256;    // float4 of the right-hand sides per thread
+  extern __shared__ float2 kinv_smem[];  // As [2][KIBK][BM + 1], then Ds [2][KIBK][BR + 1]
+  float2(*As)[KIBK][BM + 1] = reinterpret_cast<float2(*)[KIBK][BM + 1]>(kinv_smem);
+  float2(*Ds)[KIBK][BR + 1] = reinterpret_cast<float2(*)[KIBK][BR + 1]>(kinv_smem + 2 * KIBK * (BM + 1));
   const int tid = threadIdx.x;
   const int tx = tid % RG, ty = tid / RG;
   int64_t it = (int64_t)blockIdx.x * per;
   const int64_t end = min(total, it + per);
   const int64_t first_tile = it / kpt;
-  float4 ra[NA];
-  double rd[ND];
+  float4 ra[NA], rd[ND];
   while (it < end) {
     const int64_t t = it / kpt;
     const int64_t kb = it - t * kpt;
     const int64_t ke = min(kpt, kb + (end - it));
-    const int64_t m0 = t * KIBM;
+    const int64_t m0 = t * BM;
     auto load = [&](int64_t ks) {
       const int64_t k0 = ks * KIBK;
 #pragma unroll
@@ -655,9 +661,10 @@ kinv_apply_kernel(const float2* __restrict__ Kinv, int64_t ldk, int64_t n, const
 #pragma unroll
       for (int e = 0; e < ND; ++e) {
         const int idx = e * 256 + tid;
-        const int b = idx / KIBK, c = idx % KIBK;
-        const int64_t k = k0 + c;
-        rd[e] = (idx < BR * KIBK && b < nb && k < n) ? D[b * ldd + k] : 0.0;
+        const int b = idx >> 3, q = idx & 7;
+        rd[e] = (idx < BR * KIBK / 2 && b < nb)
+                    ? __ldg(reinterpret_cast<const float4*>(Dp + b * ldk + k0 + 2 * q))
+                    : make_float4(0.f, 0.f, 0.f, 0.f);
       }
     };
     auto store = [&](int buf) {
@@ -671,10 +678,10 @@ kinv_apply_kernel(const float2* __restrict__ Kinv, int64_t ldk, int64_t n, const
 #pragma unroll
       for (int e = 0; e < ND; ++e) {
         const int idx = e * 256 + tid;
-        if (idx < BR * KIBK) {
-          float h, l;
-          dd_split(rd[e], h, l);
-          Ds[buf][idx % KIBK][idx / KIBK] = make_float2(h, l);
+        if (idx < BR * KIBK / 2) {
+          const int b = idx >> 3, q = idx & 7;
+          Ds[buf][2 * q][b] = make_float2(rd[e].x, rd[e].y);
+          Ds[buf][2 * q + 1][b] = make_float2(rd[e].z, rd[e].w);
         }
       }
     };
@@ -705,57 +712,70 @@ kinv_apply_kernel(const float2* __restrict__ Kinv, int64_t ldk, int64_t n, const
       if (more) store(buf ^ 1);
       __syncthreads();
     }
-    double* P = part + ((blockIdx.x * (int64_t)span + (t - first_tile)) * BR) * KIBM;
+    double* P = part + ((blockIdx.x * (int64_t)span + (t - first_tile)) * BR) * BM;
 #pragma unroll
     for (int a = 0; a < TM; ++a)
 #pragma unroll
-      for (int b = 0; b < TR; ++b) P[(tx + RG * b) * KIBM + ty + YG * a] = (double)sh[a][b] + (double)sl[a][b];
+      for (int b = 0; b < TR; ++b) P[(tx + RG * b) * BM + ty + YG * a] = (double)sh[a][b] + (double)sl[a][b];
     it += ke - kb;
   }
 }
 
 // X[q][row] = sum over the CTAs that covered row tile t of their partials (CTA order).
 __global__ void kinv_reduce_kernel(const double* __restrict__ part, double* __restrict__ X, int64_t ldx,
-                                   int64_t n, int64_t nb, int BR, int64_t per, int64_t kpt, int span) {
+                                   int64_t n, int64_t nb, int BM, int BR, int64_t per, int64_t kpt, int span) {
   const int64_t t = blockIdx.x;
   const int q = blockIdx.y;
-  const int64_t row = t * KIBM + threadIdx.x;
-  if (row >= n || q >= nb) return;
+  const int64_t row = t * BM + threadIdx.x;
+  if (threadIdx.x >= BM || row >= n || q >= nb) return;
   const int64_t c0 = (t * kpt) / per, c1 = ((t + 1) * kpt - 1) / per;
   double sum = 0.0;
   for (int64_t c = c0; c <= c1; ++c) {
     const int64_t slot = t - (c * per) / kpt;
-    sum += part[((c * span + slot) * BR + q) * KIBM + threadIdx.x];
+    sum += part[((c * span + slot) * BR + q) * BM + threadIdx.x];
   }
   X[q * ldx + row] = sum;
 }
 
 namespace {
-struct KinvPlan {
-  int BR;
-  int64_t tiles, kpt, total, per, ctas;
-  int span;
+// Tile shapes (rows x right-hand sides, per-thread rows x right-hand sides): 64 x 64 (4 x 4),
+// 128 x 16 (8 x 1) and 128 x 4 (2 x 1), chosen by the number of right-hand sides.
+struct KinvShape {
+  int BM, BR;
 };
-constexpr size_t kinv_smem_bytes(int BR) { return sizeof(float2) * 2 * KIBK * ((KIBM + 1) + (BR + 1)); }
-// CTAs of kinv_apply_kernel<BR, TM, TR> resident per SM (first call also lifts the
-// kernel's dynamic shared-memory limit above 48 KB)
-template <int BR, int TM, int TR>
+KinvShape kinv_shape(int64_t nb) {
+  if (nb > 16) return {64, 64};
+  if (nb > 4) return {128, 16};
+  return {128, 4};
+}
+constexpr size_t kinv_smem_bytes(int BM, int BR) { return sizeof(float2) * 2 * KIBK * ((BM + 1) + (BR + 1)); }
+// CTAs of kinv_apply_kernel<BM, BR, TM, TR> resident per SM (the first call also lifts the
+// kernel's dynamic shared-memory limit)
+template <int BM, int BR, int TM, int TR>
 int kinv_resident() {
   static int occ = 0;
   if (occ == 0) {
-    cudaFuncSetAttribute(kinv_apply_kernel<BR, TM, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)kinv_smem_bytes(BR));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kinv_apply_kernel<BR, TM, TR>, 256, kinv_smem_bytes(BR));
+    cudaFuncSetAttribute(kinv_apply_kernel<BM, BR, TM, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kinv_smem_bytes(BM, BR));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kinv_apply_kernel<BM, BR, TM, TR>, 256,
+                                                  kinv_smem_bytes(BM, BR));
     if (occ <= 0) occ = 1;
   }
   return occ;
 }
+struct KinvPlan {
+  int BM, BR;
+  int64_t tiles, kpt, total, per, ctas;
+  int span;
+};
 KinvPlan kinv_plan(int64_t n, int64_t ldk, int64_t nb) {
   KinvPlan p;
-  p.BR = nb > 16 ? 64 : (nb > 4 ? 16 : 4);
-  const int occ = p.BR == 64 ? kinv_resident<64, 8, 4>() : (p.BR == 16 ? kinv_resident<16, 8, 1>()
-                                                                       : kinv_resident<4, 2, 1>());
-  p.tiles = (n + KIBM - 1) / KIBM;
+  const KinvShape sh = kinv_shape(nb);
+  p.BM = sh.BM;
+  p.BR = sh.BR;
+  const int occ = p.BR == 64 ? kinv_resident<64, 64, 4, 4>()
+                             : (p.BR == 16 ? kinv_resident<128, 16, 8, 1>() : kinv_resident<128, 4, 2, 1>());
+  p.tiles = (n + p.BM - 1) / p.BM;
   p.kpt = ldk / KIBK;
   p.total = p.tiles * p.kpt;
   const int64_t slots = (int64_t)num_sms() * occ;
@@ -770,8 +790,16 @@ int64_t kinv_ld(int64_t n) { return (n + KIBK - 1) / KIBK * KIBK; }
 
 size_t kinv_apply_work_elems(int64_t n, int64_t B) {
   if (n <= 0 || B <= 0) return 0;
-  KinvPlan p = kinv_plan(n, kinv_ld(n), B > 64 ? 64 : B);
-  return (size_t)p.ctas * p.span * p.BR * KIBM;
+  const int64_t ldk = kinv_ld(n);
+  size_t most = 0;
+  for (int64_t nb : {B < 64 ? B : (int64_t)64, B % 64}) {
+    if (nb <= 0) continue;
+    const KinvPlan p = kinv_plan(n, ldk, nb);
+    // right-hand-side pairs (one float2 = one double of space), then the partials
+    size_t w = (size_t)nb * ldk + (size_t)p.ctas * p.span * p.BR * p.BM;
+    if (w > most) most = w;
+  }
+  return most;
 }
 
 int64_t kinv_apply(const float2* Kinv, int64_t n, const double* D, int64_t B, double* X, double* work,
@@ -781,19 +809,21 @@ int64_t kinv_apply(const float2* Kinv, int64_t n, const double* D, int64_t B, do
   for (int64_t q0 = 0; q0 < B; q0 += 64) {
     const int64_t nb = B - q0 < 64 ? B - q0 : 64;
     const KinvPlan p = kinv_plan(n, ldk, nb);
-    const double* Dq = D + q0 * n;
-    double* Xq = X + q0 * n;
+    float2* Dp = reinterpret_cast<float2*>(work);
+    double* part = work + nb * ldk;
+    launches += split_rows_to_pairs(D + q0 * n, n, Dp, nb, n, ldk, s);
+    const size_t sm = kinv_smem_bytes(p.BM, p.BR);
     if (p.BR == 64)
-      kinv_apply_kernel<64, 8, 4><<<(unsigned)p.ctas, 256, kinv_smem_bytes(64), s>>>(Kinv, ldk, n, Dq, n, nb, work, p.per, p.total,
-                                                                  p.kpt, p.span);
+      kinv_apply_kernel<64, 64, 4, 4><<<(unsigned)p.ctas, 256, sm, s>>>(Kinv, ldk, n, Dp, nb, part, p.per, p.total,
+                                                                      p.kpt, p.span);
     else if (p.BR == 16)
-      kinv_apply_kernel<16, 8, 1><<<(unsigned)p.ctas, 256, kinv_smem_bytes(16), s>>>(Kinv, ldk, n, Dq, n, nb, work, p.per, p.total,
-                                                                  p.kpt, p.span);
+      kinv_apply_kernel<128, 16, 8, 1><<<(unsigned)p.ctas, 256, sm, s>>>(Kinv, ldk, n, Dp, nb, part, p.per,
+                                                                       p.total, p.kpt, p.span);
     else
-      kinv_apply_kernel<4, 2, 1><<<(unsigned)p.ctas, 256, kinv_smem_bytes(4), s>>>(Kinv, ldk, n, Dq, n, nb, work, p.per, p.total,
-                                                                 p.kpt, p.span);
-    kinv_reduce_kernel<<<dim3((unsigned)p.tiles, (unsigned)nb), KIBM, 0, s>>>(work, Xq, n, n, nb, p.BR, p.per,
-                                                                             p.kpt, p.span);
+      kinv_apply_kernel<128, 4, 2, 1><<<(unsigned)p.ctas, 256, sm, s>>>(Kinv, ldk, n, Dp, nb, part, p.per,
+                                                                      p.total, p.kpt, p.span);
+    kinv_reduce_kernel<<<dim3((unsigned)p.tiles, (unsigned)nb), 128, 0, s>>>(part, X + q0 * n, n, n, nb, p.BM,
+                                                                            p.BR, p.per, p.kpt, p.span);
     launches += 2;
   }
   return launches;
