@@ -65,6 +65,8 @@ struct bti_ctx {
   bool K_built = false, K_factored = false;
   int64_t factor_gen = 0;        // incremented by every successful factor_K
   float2* Kinv = nullptr;        // explicit K^{-1} as float pairs [n][kinv_ld(n)] (bti_invert_K)
+  void* kinv_planes = nullptr;   // and as six FP16 digit planes for the tensor cores
+  int* kinv_ea = nullptr;        // their row exponents
   int64_t kinv_gen = -1;         // factor_gen it was formed from
   int* status = nullptr;  // device status word
   void* ws = nullptr;     // spectral workspace
@@ -552,6 +554,8 @@ bti_status bti_destroy(bti_handle h) {
   dev_freep(h->covq);
   dev_freep(h->Linv);
   dev_freep(h->Kinv);
+  dev_free(h->kinv_planes);
+  dev_freep(h->kinv_ea);
   dev_freep(h->status);
   dev_free(h->ws);
   dev_freep(h->wsolve);
@@ -881,10 +885,15 @@ bti_status bti_invert_K(bti_handle h, int enable) {
   bti_status st = check_handle(h);
   if (st != BTI_OK) return st;
   drop_online_graph_any(h);
+  auto release = [&]() {
+    dev_freep(h->Kinv);
+    dev_free(h->kinv_planes);
+    dev_freep(h->kinv_ea);
+    h->kinv_gen = -1;
+  };
   if (!enable) {
     cudaStreamSynchronize(h->stream);
-    dev_freep(h->Kinv);
-    h->kinv_gen = -1;
+    release();
     return BTI_OK;
   }
   if (!h->K_factored) return fail(h, BTI_ERR_STATE, "invert_K: K not factored");
@@ -892,29 +901,35 @@ bti_status bti_invert_K(bti_handle h, int enable) {
   const int64_t n = h->Nt * h->Nd;
   const int64_t ldk = kinv_ld(n);
   cudaStream_t s = h->stream;
-  if (!h->Kinv) {
-    st = dev_alloc(h, (void**)&h->Kinv, sizeof(float2) * (size_t)n * ldk, "alloc K inverse");
-    if (st != BTI_OK) return st;
-  }
-  st = ensure(h, (void**)&h->wsolve, &h->wsolve_bytes, sizeof(double) * trsm_work_elems(n, n), "solve workspace");
-  if (st != BTI_OK) return st;
+  const bool tc = kinv_tc_supported(n);
+  const int64_t ldt = kinv_tc_ld(n);
+  kinv_prepare();
+  if (tc) kinv_tc_prepare();
+  if (!h->Kinv) st = dev_alloc(h, (void**)&h->Kinv, sizeof(float2) * (size_t)n * ldk, "alloc K inverse");
+  if (st == BTI_OK && tc && !h->kinv_planes)
+    st = dev_alloc(h, &h->kinv_planes, sizeof(uint16_t) * kinv_tc_plane_elems(n), "alloc K inverse planes");
+  if (st == BTI_OK && tc && !h->kinv_ea)
+    st = dev_alloc(h, (void**)&h->kinv_ea, sizeof(int) * (size_t)ldt, "alloc K inverse exponents");
+  if (st == BTI_OK)
+    st = ensure(h, (void**)&h->wsolve, &h->wsolve_bytes, sizeof(double) * trsm_work_elems(n, n), "solve workspace");
   double* X = nullptr;
-  st = dev_alloc(h, (void**)&X, sizeof(double) * (size_t)n * n, "K inverse temporary");
+  if (st == BTI_OK) st = dev_alloc(h, (void**)&X, sizeof(double) * (size_t)n * n, "K inverse temporary");
   if (st != BTI_OK) {
-    dev_freep(h->Kinv);
+    release();
     return st;
   }
   // rows of X: K^{-1} e_b (= row b of the symmetric K^{-1})
   int64_t nl = identity_blocks(X, 1, n, s);
   nl += trsm_lower_f64(h->K, h->Linv, n, X, n, h->wsolve, h->status, s, true);
   nl += split_to_pairs(X, h->Kinv, n, ldk, s);
+  if (tc) nl += kinv_tc_slice(X, n, n, n, h->kinv_ea, h->kinv_planes, ldt, s);
   count_dense(h, nl);
   st = launched(h, "invert_K");
   bti_status sy = cuda_check(h, cudaStreamSynchronize(s), "invert_K sync");
   dev_freep(X);
   if (st == BTI_OK) st = sy;
   if (st != BTI_OK) {
-    dev_freep(h->Kinv);
+    release();
     return st;
   }
   h->kinv_gen = h->factor_gen;
@@ -937,7 +952,9 @@ bti_status bti_copy_K(bti_handle h, double* dst) {
 static bti_status reserve_solve(bti_ctx* h, int64_t B) {
   const int64_t n = h->Nt * h->Nd;
   size_t tail = trsm_work_elems(n, B);
-  if (kinv_ready(h)) tail = std::max(tail, (size_t)B * n + kinv_apply_work_elems(n, B));
+  if (kinv_ready(h))
+    tail = std::max(tail, (size_t)B * n + std::max(kinv_apply_work_elems(n, B),
+                                                   h->kinv_planes ? kinv_tc_work_elems(n) : (size_t)0));
   size_t need = sizeof(double) * ((size_t)2 * B * n + tail);
   size_t chol = sizeof(double) * (size_t)n * kCholNB;
   return ensure(h, (void**)&h->wsolve, &h->wsolve_bytes, need > chol ? need : chol, "solve workspace");
@@ -962,12 +979,23 @@ static bti_status infer_map_impl(bti_handle h, const double* d_obs, double* m_ma
   cudaStream_t s = h->stream;
   const bool inv = kinv_ready(h);
   // x = K^{-1} v (v != x), by the explicit inverse or the blocked triangular solves
+  // tensor-core form of the explicit inverse when the planes exist and tensor cores are on
+  const bool inv_tc = inv && h->kinv_planes && h->tc_enabled;
+  cudaError_t tc_err = cudaSuccess;
   auto solve_into = [&](const double* v, double* xo) -> int64_t {
+    if (inv_tc) {
+      int64_t nl = 0;
+      cudaError_t e = kinv_apply_tc(h->kinv_planes, h->kinv_ea, n, v, B, xo, work + (size_t)B * n, h->status + 1, s,
+                                    &nl);
+      if (e != cudaSuccess) tc_err = e;
+      return nl;
+    }
     if (inv) return kinv_apply(h->Kinv, n, v, B, xo, work + (size_t)B * n, s);
     if (v != xo) cudaMemcpyAsync(xo, v, sizeof(double) * B * n, cudaMemcpyDeviceToDevice, s);
     return trsm_lower_f64(h->K, h->Linv, n, xo, B, work, h->status, s, h->dense_prec == BTI_P_DF64);
   };
   count_dense(h, solve_into(d_obs, x));
+  if (tc_err != cudaSuccess) return cuda_check(h, tc_err, "tensor-core inverse product");
   st = launched(h, "triangular solves");
   if (st != BTI_OK) return st;
   for (int it = 0; it < refine_iters; ++it) {
@@ -991,6 +1019,7 @@ static bti_status infer_map_impl(bti_handle h, const double* d_obs, double* m_ma
       nl += axpby_f64(x, r, 1.0, 1.0, B * n, s);
     }
     count_dense(h, nl);
+    if (tc_err != cudaSuccess) return cuda_check(h, tc_err, "tensor-core inverse product");
     st = launched(h, "refinement");
     if (st != BTI_OK) return st;
   }

@@ -204,6 +204,24 @@ size_t kinv_apply_work_elems(int64_t n, int64_t B);
 int64_t kinv_apply(const float2* Kinv, int64_t n, const double* D, int64_t B, double* X, double* work,
                    cudaStream_t s);
 int split_to_pairs(const double* X, float2* Y, int64_t n, int64_t ldk, cudaStream_t s);
+// the same sum with partial tiles of BM rows x BR right-hand sides (both kinv paths)
+int kinv_reduce(const double* part, double* X, int64_t ldx, int64_t n, int64_t nb, int BM, int BR, int64_t per,
+                int64_t kpt, int span, int64_t tiles, cudaStream_t s);
+// Tensor-core form (tc_kinv.cu): K^{-1} as six FP16 planes of base-256 digits
+// [6][kinv_tc_ld(n)]^2 with row exponents ex [kinv_tc_ld(n)] (kinv_tc_slice of the FP64 inverse),
+// applied exactly per 128-column chunk.  work: kinv_tc_work_elems(n) doubles; err: the
+// handle's wait-timeout word.
+// one-time kernel attributes and occupancy queries, kept out of graph captures
+void kinv_prepare();
+void kinv_tc_prepare();
+int64_t kinv_tc_ld(int64_t n);
+bool kinv_tc_supported(int64_t n);
+size_t kinv_tc_plane_elems(int64_t n);
+size_t kinv_tc_work_elems(int64_t n);
+int64_t kinv_tc_slice(const double* X, int64_t ldx, int64_t rows, int64_t n, int* ex, void* planes,
+                      int64_t rows_pad, cudaStream_t s);
+cudaError_t kinv_apply_tc(const void* planes, const int* ea, int64_t n, const double* D, int64_t B, double* X,
+                          double* work, int* err, cudaStream_t s, int64_t* launches);
 int axpby_f64(double* y, const double* x, double a, double b, int64_t n, cudaStream_t s);
 // FP32 Gram product W = A B^T into an FP64 matrix (lower tiles) and the FP64 -> FP32 copy
 int sgemm_nt_lower_to_f64(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* Bm,

@@ -737,6 +737,12 @@ __global__ void kinv_reduce_kernel(const double* __restrict__ part, double* __re
   X[q * ldx + row] = sum;
 }
 
+int kinv_reduce(const double* part, double* X, int64_t ldx, int64_t n, int64_t nb, int BM, int BR, int64_t per,
+                int64_t kpt, int span, int64_t tiles, cudaStream_t s) {
+  kinv_reduce_kernel<<<dim3((unsigned)tiles, (unsigned)nb), 128, 0, s>>>(part, X, ldx, n, nb, BM, BR, per, kpt, span);
+  return 1;
+}
+
 namespace {
 // Tile shapes (rows x right-hand sides, per-thread rows x right-hand sides): 64 x 64 (4 x 4),
 // 128 x 16 (8 x 1) and 128 x 4 (2 x 1), chosen by the number of right-hand sides.
@@ -788,6 +794,12 @@ KinvPlan kinv_plan(int64_t n, int64_t ldk, int64_t nb) {
 
 int64_t kinv_ld(int64_t n) { return (n + KIBK - 1) / KIBK * KIBK; }
 
+void kinv_prepare() {
+  kinv_resident<64, 64, 4, 4>();
+  kinv_resident<128, 16, 8, 1>();
+  kinv_resident<128, 4, 2, 1>();
+}
+
 size_t kinv_apply_work_elems(int64_t n, int64_t B) {
   if (n <= 0 || B <= 0) return 0;
   const int64_t ldk = kinv_ld(n);
@@ -822,9 +834,7 @@ int64_t kinv_apply(const float2* Kinv, int64_t n, const double* D, int64_t B, do
     else
       kinv_apply_kernel<128, 4, 2, 1><<<(unsigned)p.ctas, 256, sm, s>>>(Kinv, ldk, n, Dp, nb, part, p.per,
                                                                       p.total, p.kpt, p.span);
-    kinv_reduce_kernel<<<dim3((unsigned)p.tiles, (unsigned)nb), 128, 0, s>>>(part, X + q0 * n, n, n, nb, p.BM,
-                                                                            p.BR, p.per, p.kpt, p.span);
-    launches += 2;
+    launches += 1 + kinv_reduce(part, X + q0 * n, n, n, nb, p.BM, p.BR, p.per, p.kpt, p.span, p.tiles, s);
   }
   return launches;
 }

@@ -474,14 +474,28 @@ prod_adj_df64_kernel(const float4* __restrict__ Fhat, const double2* __restrict_
       sd[bb * RS + (i - i0)] = v;
     }
     __syncthreads();
+    // F-hat row ii of the tile; with several vectors per CTA the next row is loaded
+    // while this one is used (single vectors are HBM-bound and keep one row in flight)
+    constexpr bool kAhead = BG >= 4;
+    float4 f[VPT], fn[VPT];
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      const int64_t j = jbase + 256 * v;
+      f[v] = (kAhead && j < Nm) ? __ldg(base + i0 * Nm + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     for (int64_t ii = 0; ii < rn; ++ii) {
-      const int64_t i = i0 + ii;
-      const float4* row = base + i * Nm;
-      float4 f[VPT];
+      // kAhead: fetch row ii + 1 into fn; otherwise fetch row ii into f
+      const int64_t il_ = kAhead ? ii + 1 : ii;
+      const bool live = il_ < rn;
+      const float4* row = base + (i0 + il_) * Nm;
 #pragma unroll
       for (int v = 0; v < VPT; ++v) {
-        int64_t j = jbase + 256 * v;
-        f[v] = (j < Nm) ? __ldg(row + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int64_t j = jbase + 256 * v;
+        const float4 g = (live && j < Nm) ? __ldg(row + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (kAhead)
+          fn[v] = g;
+        else
+          f[v] = g;
       }
 #pragma unroll
       for (int bb = 0; bb < BG; ++bb) {
@@ -494,6 +508,10 @@ prod_adj_df64_kernel(const float4* __restrict__ Fhat, const double2* __restrict_
           ff_mac(ih[bb][v], il[bb][v], f[v].x, f[v].y, x.z, x.w);
           ff_mac(ih[bb][v], il[bb][v], -f[v].z, -f[v].w, x.x, x.y);
         }
+      }
+      if (kAhead) {
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) f[v] = fn[v];
       }
     }
   }
@@ -513,13 +531,21 @@ template <int BG, int VPT>
 static void adj_df64_launch(const float4* Fhat, const double2* dhat, double2* mhat, int64_t nf, int64_t R,
                             int64_t Nm, int64_t B, cudaStream_t s) {
   size_t smem = sizeof(float4) * (size_t)BG * (R < kAdjRows ? R : kAdjRows);
+  static bool attr = false;  // 8 vectors x 512 staged rows take 64 KB
+  if (!attr) {
+    cudaFuncSetAttribute(prod_adj_df64_kernel<BG, VPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(sizeof(float4) * BG * kAdjRows));
+    attr = true;
+  }
   dim3 grid((unsigned)((Nm + 256 * VPT - 1) / (256 * VPT)), (unsigned)nf, (unsigned)((B + BG - 1) / BG));
   prod_adj_df64_kernel<BG, VPT><<<grid, 256, smem, s>>>(Fhat, dhat, mhat, nf, R, Nm, B);
 }
 
 void launch_prod_adj_df64(const float4* Fhat, const double2* dhat, double2* mhat, int64_t nf, int64_t R,
                           int64_t Nm, int64_t B, cudaStream_t s, int vpt) {
-  if (B >= 4)
+  if (B >= 8)
+    adj_df64_launch<8, 1>(Fhat, dhat, mhat, nf, R, Nm, B, s);
+  else if (B >= 4)
     adj_df64_launch<4, 2>(Fhat, dhat, mhat, nf, R, Nm, B, s);
   else if (vpt == 2)
     adj_df64_launch<1, 2>(Fhat, dhat, mhat, nf, R, Nm, B, s);

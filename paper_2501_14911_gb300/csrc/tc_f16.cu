@@ -521,6 +521,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 }  // namespace
 
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() { return encode_fn(); }
+
 bool tc_fwd_f16_supported(int64_t Nm, int64_t R, int64_t B) {
   // rows of F-hat as FP16 halves must be 16-byte strided for TMA (N_m a multiple of 4), and
   // the row tiles times the vector groups must fit the grid's z extent

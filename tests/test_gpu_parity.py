@@ -769,11 +769,12 @@ def test_elliptic_prior_full_inversion(store):
 
 @pytest.mark.parametrize("B", [1, 5, 20, 70], ids=["b1", "b5", "b20", "b70"])
 def test_explicit_inverse_online_solve(B):
-    """bti_invert_K: x = K^{-1} d as one double-FP32 product with the explicit inverse
-    (float pairs; stream-K partials summed in CTA order; 4-, 16- and 64-wide right-hand-
-    side tiles and a second 64-chunk at B = 70).  m_map matches the oracle, refinement
-    brings it to the FP64 tolerance, a new factorisation returns to the triangular solves
-    until the inverse is formed again, and release works."""
+    """bti_invert_K: x = K^{-1} d as one product with the explicit inverse, on the tensor
+    cores (six FP16 digit planes, exact per 128-column chunk) and, with tensor cores off,
+    in double-FP32 on the CUDA cores (4-, 16- and 64-wide right-hand-side tiles); stream-K
+    partials summed in CTA order; a second 64-chunk at B = 70.  m_map matches the oracle,
+    refinement brings it to the FP64 tolerance, a new factorisation returns to the
+    triangular solves until the inverse is formed again, and release works."""
     p, F, Fq, G, _ = tiny_problem()
     d = p.vectors_d(B)
     m_or = oracle.map_point(F, G, p.sigma2, d)
@@ -796,8 +797,15 @@ def test_explicit_inverse_online_solve(B):
     m.zero_()
     h.infer_map(cuda(d), m)
     n_inv = h.profile_read()[0]["dense"][1]
-    assert n_inv + 20 < n_trsm  # a product and a reduction per 64 vectors, not 2 n / 64 blocked steps
+    assert n_inv + 20 < n_trsm  # a few launches per 64 vectors, not 2 n / 64 blocked steps
     assert relb(host(m), m_or) < 1e-10
+    # the same product in double-FP32 on the CUDA cores (tensor cores off)
+    h.set_tensor_cores(False)
+    m_dd = torch.empty_like(m)
+    h.infer_map(cuda(d), m_dd)
+    h.set_tensor_cores(True)
+    assert relb(host(m_dd), m_or) < 1e-10
+    assert relb(host(m), host(m_dd)) < 1e-10
     h.infer_map(cuda(d), m, refine_iters=1)
     assert relb(host(m), m_or) < 1e-12
     # the online graph applies the inverse too
