@@ -25,6 +25,8 @@ struct OpStore {
   void* hat = nullptr;     // [nf][R][Nm] complex, storage tier
   float* scale = nullptr;  // [nf][R] row scales of the FP16 tier
   double* time = nullptr;  // [Nt][R][Nm] FP64 time-domain copy (F and G only)
+  void* dig = nullptr;     // adjoint digit planes of the double-FP32 tier (bti_set_digit_planes)
+  int* dig_ex = nullptr;   // their exponents, one per (w, j)
 };
 
 }  // namespace
@@ -220,6 +222,8 @@ void drop_store(OpStore& o) {
   dev_free(o.hat);
   dev_freep(o.time);
   dev_freep(o.scale);
+  dev_free(o.dig);
+  dev_freep(o.dig_ex);
   o.hat = nullptr;
   o.set = false;
 }
@@ -373,7 +377,10 @@ bti_status apply_adj_t(bti_ctx* h, const OpStore& o, const void* in, void* out, 
   const int64_t nf = h->nf, Nm = h->Nm, R = o.R, Nt = h->Nt;
   size_t n_dhat = (size_t)B * nf * R;
   size_t n_mhat = (size_t)B * nf * Nm;
-  bti_status st = ensure(h, &h->ws, &h->ws_bytes, sizeof(C2<T>) * (n_mhat + n_dhat), "workspace");
+  // exact digit-plane product on the tensor cores: its per-call planes follow the spectra
+  const bool dig = o.prec == BTI_P_DF64 && o.dig && h->tc_enabled && adj_digits_supported(nf, R, Nm, B);
+  const size_t base = sizeof(C2<T>) * (n_mhat + n_dhat);
+  bti_status st = ensure(h, &h->ws, &h->ws_bytes, base + (dig ? adj_digits_work_bytes(nf, R, B) : 0), "workspace");
   if (st != BTI_OK) return st;
   C2<T>* dhat = (C2<T>*)h->ws;
   C2<T>* mhat = dhat + n_dhat;
@@ -389,6 +396,15 @@ bti_status apply_adj_t(bti_ctx* h, const OpStore& o, const void* in, void* out, 
     }
     h->prof_count[BTI_K_PROD_ADJ] += nl - 1;
     if (e != cudaSuccess) return cuda_check(h, e, "tensor-core adjoint product");
+  } else if (dig) {
+    int nl = 0;
+    cudaError_t e;
+    {
+      ProfScope ps(h, BTI_K_PROD_ADJ);
+      e = adj_digits_apply(o.dig, o.dig_ex, nf, R, Nm, dhat, mhat, B, (char*)h->ws + base, h->status + 1, s, &nl);
+    }
+    h->prof_count[BTI_K_PROD_ADJ] += nl - 1;
+    if (e != cudaSuccess) return cuda_check(h, e, "tensor-core adjoint product (digit planes)");
   } else if (o.prec == BTI_P_DF64)
     PROF(h, BTI_K_PROD_ADJ, launch_prod_adj_df64((const float4*)o.hat, (const double2*)dhat, (double2*)mhat, nf,
                                                  R, Nm, B, s, h->tune[o.prec].vpt));
@@ -1206,6 +1222,35 @@ bti_status bti_set_matfree_precond(bti_handle h, int kind) {
   return BTI_OK;
 }
 
+bti_status bti_set_digit_planes(bti_handle h, bti_op op, int enable) {
+  bti_status st = check_handle(h);
+  if (st != BTI_OK) return st;
+  if (op < BTI_OP_F || op > BTI_OP_FQ || (enable != 0 && enable != 1))
+    return fail(h, BTI_ERR_ARG, "set_digit_planes: bad op or enable");
+  OpStore& o = h->op[op];
+  drop_online_graph_any(h);
+  cudaStreamSynchronize(h->stream);
+  dev_free(o.dig);
+  dev_freep(o.dig_ex);
+  if (!enable) return BTI_OK;
+  if (!o.set || o.prec != BTI_P_DF64)
+    return fail(h, BTI_ERR_STATE, "set_digit_planes: the operator's blocks must be set in the BTI_P_DF64 tier");
+  const int64_t nf = h->nf, R = o.R, Nm = h->Nm;
+  st = dev_alloc(h, &o.dig, sizeof(uint16_t) * adj_digits_plane_elems(nf, R, Nm), "alloc digit planes");
+  if (st == BTI_OK) st = dev_alloc(h, (void**)&o.dig_ex, sizeof(int) * adj_digits_exp_elems(nf, Nm), "alloc exps");
+  if (st == BTI_OK) {
+    adj_digits_prepare();
+    count_dense(h, adj_digits_build(o.hat, nf, R, Nm, o.dig, o.dig_ex, h->stream));
+    st = launched(h, "set_digit_planes");
+    if (st == BTI_OK) st = cuda_check(h, cudaStreamSynchronize(h->stream), "set_digit_planes sync");
+  }
+  if (st != BTI_OK) {
+    dev_free(o.dig);
+    dev_freep(o.dig_ex);
+  }
+  return st;
+}
+
 bti_status bti_set_tensor_cores(bti_handle h, int on) {
   bti_status st = check_handle(h);
   if (st != BTI_OK) return st;
@@ -1695,6 +1740,7 @@ static bti_status reserve_online(bti_ctx* h, int64_t B) {
   // spectral workspace: the larger of an adjoint (G*) and a forward (F, F_q) product
   const int64_t nf = h->nf, Nm = h->Nm;
   size_t adj = 16 * ((size_t)B * nf * Nm + (size_t)B * nf * h->Nd);
+  if (h->op[BTI_OP_G].dig) adj += adj_digits_work_bytes(nf, h->Nd, B);
   size_t fwd = 0;
   for (int op = 0; op < 3; ++op) {
     if (op == BTI_OP_G || !h->op[op].set) continue;

@@ -207,7 +207,7 @@ int split_to_pairs(const double* X, float2* Y, int64_t n, int64_t ldk, cudaStrea
 // the same sum with partial tiles of BM rows x BR right-hand sides (both kinv paths)
 int kinv_reduce(const double* part, double* X, int64_t ldx, int64_t n, int64_t nb, int BM, int BR, int64_t per,
                 int64_t kpt, int span, int64_t tiles, cudaStream_t s);
-// Tensor-core form (tc_kinv.cu): K^{-1} as six FP16 planes of base-256 digits
+// Tensor-core form (tc_digits.cu): K^{-1} as six FP16 planes of base-256 digits
 // [6][kinv_tc_ld(n)]^2 with row exponents ex [kinv_tc_ld(n)] (kinv_tc_slice of the FP64 inverse),
 // applied exactly per 128-column chunk.  work: kinv_tc_work_elems(n) doubles; err: the
 // handle's wait-timeout word.
@@ -222,6 +222,18 @@ int64_t kinv_tc_slice(const double* X, int64_t ldx, int64_t rows, int64_t n, int
                       int64_t rows_pad, cudaStream_t s);
 cudaError_t kinv_apply_tc(const void* planes, const int* ea, int64_t n, const double* D, int64_t B, double* X,
                           double* work, int* err, cudaStream_t s, int64_t* launches);
+// Double-FP32 tier's adjoint product for B >= 16 on the tensor cores (tc_digits.cu): digit
+// planes of conj(F-hat)^T, K-major over (i, re/im), one exponent per (w, j); built once from
+// the float-quad blocks.  adj_digits_apply: dhat [B][nf][R], mhat [B][nf][N_m] complex FP64;
+// work of adj_digits_work_bytes bytes.
+size_t adj_digits_plane_elems(int64_t nf, int64_t R, int64_t Nm);
+size_t adj_digits_exp_elems(int64_t nf, int64_t Nm);
+bool adj_digits_supported(int64_t nf, int64_t R, int64_t Nm, int64_t B);
+void adj_digits_prepare();
+int64_t adj_digits_build(const void* hat, int64_t nf, int64_t R, int64_t Nm, void* planes, int* ex, cudaStream_t s);
+size_t adj_digits_work_bytes(int64_t nf, int64_t R, int64_t B);
+cudaError_t adj_digits_apply(const void* planes, const int* ea, int64_t nf, int64_t R, int64_t Nm, const void* dhat,
+                             void* mhat, int64_t B, void* work, int* err, cudaStream_t s, int* launches);
 int axpby_f64(double* y, const double* x, double a, double b, int64_t n, cudaStream_t s);
 // FP32 Gram product W = A B^T into an FP64 matrix (lower tiles) and the FP64 -> FP32 copy
 int sgemm_nt_lower_to_f64(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* Bm,

@@ -1,0 +1,901 @@
+// Explicit-inverse product of the online solve on the tensor cores (tcgen05), exact in
+// integer slices.
+//
+// X[b][i] = sum_j Kinv[i][j] D[b][j] (x = K^{-1} d, Eq. (4.13) with the solves moved
+// offline) needs about 48 significant bits, which no tensor-core input type holds.  Both
+// operands are therefore cut into S = 6 planes of balanced base-256 digits, each digit an
+// integer in [-128, 128] and so exact in FP16:
+//   Kinv[i][j] = 2^(ea_i - 7) sum_s P_s[i][j] 2^(-8 s),   D[b][j] = 2^(eb_b - 7) sum_t Q_t[b][j] 2^(-8 t)
+// with ea_i, eb_b the binary exponents of the row maxima (so the planes hold a 47-bit
+// fixed-point image of each row, the rest rounded away).  Then
+//   X[b][i] = 2^(ea_i + eb_b - 14) sum_g 2^(-8 g) G_g[i][b],  G_g = sum_{s + t = g} P_s Q_t^T,
+// keeping the 21 plane pairs with s + t <= 5 (the dropped ones lie below 2^-48 of the row
+// scale).  Every product of two digits is at most 2^14 and each group sums at most six
+// plane pairs, so over a chunk of 128 columns j a group's sum stays below 6 * 128 * 2^14
+// < 2^24: the FP32 accumulators in tensor memory hold it exactly.  After each chunk the
+// epilogue warps read the six groups, scale them by 2^(-8 g) (exact) and add them into
+// float-pair accumulators with a two-sum, as the double-FP32 kernels do.
+//
+// Layout: the K^{-1} planes [S][ldk / 64][rows_pad][64] FP16 (rows_pad and ldk multiples of
+// 128, zero padding; tiled so each TMA box is contiguous) are formed once with the inverse;
+// the right-hand-side planes [S][ldk / 64][64][64] per call.  A CTA (one per SM) walks a contiguous run of (row tile, chunk) units (stream-K,
+// as the double-FP32 kernel), so every SM gets the same number of chunks; partial tiles go
+// to an FP64 buffer that a second kernel sums in CTA order.  Warp 0 issues the TMA loads
+// (K^{-1} planes 128 rows x 64 columns per stage, the six right-hand-side planes per 64
+// columns), warp 1 issues tcgen05.mma (M = 128, N = 64, K = 16) into six TMEM groups of 64
+// columns, warps 2-9 drain the groups per chunk.  Every wait is bounded; on a timeout the
+// kernel sets the error word, stops issuing, lets what it issued land and frees its tensor
+// memory.
+#include "bti_internal.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_fp16.h>
+
+namespace bti {
+
+namespace {
+
+constexpr int kSl = 6;                 // digit planes per operand
+constexpr int kKiRows = 128;           // MMA M: rows of K^{-1} per tile
+constexpr int kKiN = 64;               // MMA N: right-hand sides per launch chunk
+constexpr int kKiBox = 64;             // FP16 columns per TMA box row (128 bytes, the swizzle width)
+constexpr int kKiChunk = 128;          // columns per exact accumulation chunk (two boxes)
+constexpr int kKiAStages = 6;          // K^{-1} plane stages (16 KB each): one box's six planes
+constexpr int kKiBStages = 2;          // right-hand-side stages (six planes, 48 KB each)
+constexpr int kKiThreads = 320;        // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
+constexpr uint32_t kKiATile = kKiRows * 128;
+constexpr uint32_t kKiBPlane = kKiN * 128;
+constexpr uint32_t kKiBTile = kSl * kKiBPlane;
+constexpr uint32_t kKiTmemCols = 512;  // six groups of 64 columns (384) rounded to a power of two
+constexpr long long kKiSpin = 1ll << 22;
+constexpr size_t kKiSmem = 1024 + kKiAStages * (size_t)kKiATile + kKiBStages * (size_t)kKiBTile;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// K-major operand, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+               : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  for (long long it = 0; it < kKiSpin; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 1023) == 1023 && *abort_flag) return false;
+  }
+  *abort_flag = 1;
+  return false;
+}
+
+__device__ __forceinline__ void two_sum_acc(float& Sh, float& Sl, float p) {
+  const float s = Sh + p;
+  const float bb = s - Sh;
+  Sl += (Sh - (s - bb)) + (p - bb);
+  Sh = s;
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t addr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(addr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Add one chunk's six exact group sums G_g (TMEM columns 64 g + col0 .. + 31 of this warp's
+// lanes) into the float-pair accumulators: sum_g 2^(-8 g) G_g.  Groups 5, 4, 3 are summed in
+// plain FP32 first: that partial sum is below 1.01 in units where G_0 reaches 2^24, so its
+// rounding stays under 2^-47 of the total; groups 2, 1, 0 and that sum enter by two-sum.
+__device__ __forceinline__ void add_groups(uint32_t taddr, float (&Sh)[32], float (&Sl)[32]) {
+  uint32_t v[32];
+  float low[32];
+  tmem_ld32(taddr + 5 * kKiN, v);
+#pragma unroll
+  for (int c = 0; c < 32; ++c) low[c] = __uint_as_float(v[c]) * 0x1p-40f;
+  tmem_ld32(taddr + 4 * kKiN, v);
+#pragma unroll
+  for (int c = 0; c < 32; ++c) low[c] = fmaf(__uint_as_float(v[c]), 0x1p-32f, low[c]);
+  tmem_ld32(taddr + 3 * kKiN, v);
+#pragma unroll
+  for (int c = 0; c < 32; ++c) {
+    low[c] = fmaf(__uint_as_float(v[c]), 0x1p-24f, low[c]);
+    two_sum_acc(Sh[c], Sl[c], low[c]);
+  }
+#pragma unroll
+  for (int g = 2; g >= 0; --g) {
+    tmem_ld32(taddr + g * kKiN, v);
+    const float sc = __int_as_float((127 - 8 * g) << 23);  // 2^(-8 g), exact
+#pragma unroll
+    for (int c = 0; c < 32; ++c) two_sum_acc(Sh[c], Sl[c], __uint_as_float(v[c]) * sc);
+  }
+}
+
+// Balanced base-256 digits of v (|v| <= 2^47), most significant first: v = sum_s d[s] 256^(5 - s),
+// d[s] in [-128, 128] (the lower five in [-128, 127]).
+__device__ __forceinline__ void digits6(long long v, int (&d)[kSl]) {
+#pragma unroll
+  for (int k = 0; k < kSl - 1; ++k) {
+    const int dk = (int)(((v & 255) ^ 128) - 128);
+    d[kSl - 1 - k] = dk;
+    v = (v - dk) >> 8;
+  }
+  d[0] = (int)v;  // |v| <= 128 here
+}
+
+// One A plane s of a 64-column box against the B planes t = 0 .. 5 - s (four K-steps of 16
+// each): group s + t accumulates at TMEM columns 64 (s + t).  The descriptors are built once
+// per plane and advanced by 32 bytes per K-step (2 in the encoded start address) and by one
+// B plane (8 KB) per t, so the issuing thread spends few instructions per MMA.  first: the
+// box opens an accumulation chunk, so K-step 0 of plane 0 overwrites the groups.
+__device__ __forceinline__ void issue_plane(uint32_t tmem, int s, uint32_t a0, uint32_t b0, uint32_t idesc,
+                                            bool first) {
+  const uint64_t ad = sdesc(a0), bd = sdesc(b0);
+#pragma unroll
+  for (int t = 0; t < kSl; ++t) {
+    if (t + s < kSl) {
+      const uint32_t d = tmem + (uint32_t)((s + t) * kKiN);
+      const uint64_t bt = bd + (uint64_t)t * (kKiBPlane >> 4);
+#pragma unroll
+      for (int kk = 0; kk < kKiBox / 16; ++kk) {
+        const uint32_t acc = (first && kk == 0) ? 0u : 1u;
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+            ::"r"(d), "l"(ad + 2 * kk), "l"(bt + 2 * kk), "r"(idesc), "r"(acc));
+      }
+    }
+  }
+}
+
+// (hi + lo) 2^e as an FP64 value with integer operations only (GB300 issues FP64 at 1/64 of
+// its FP32 rate, and the epilogue converts every output): the pair is renormalised by a
+// two-sum, so |lo| <= ulp(hi) / 2; lo's significand is aligned to hi's in a 64-bit integer
+// (together at most 53 bits, so exact up to lo's bits below 2^-29 ulp(hi)), the sum is
+// renormalised by one bit if needed, and e is added to the exponent.  0 when hi is 0 or
+// below FP32's normal range.
+__device__ __forceinline__ double pair_to_double_scaled(float hi, float lo, int e) {
+  const float sm = hi + lo;
+  const float bb = sm - hi;
+  lo = (hi - (sm - bb)) + (lo - bb);
+  hi = sm;
+  const uint32_t hb = __float_as_uint(hi);
+  const int Eh = (int)((hb >> 23) & 255u);
+  if (Eh == 0) return 0.0;
+  long long X = (long long)((hb & 0x7FFFFFu) | 0x800000u) << 29;  // hi's significand at bit 52
+  const uint32_t lb = __float_as_uint(lo);
+  const int El = (int)((lb >> 23) & 255u);
+  if (El != 0) {
+    long long ml = (long long)((lb & 0x7FFFFFu) | 0x800000u);
+    const int sh = El - Eh + 29;  // <= 5 since |lo| <= ulp(hi) / 2
+    ml = sh >= 0 ? (ml << sh) : (sh > -40 ? (ml >> -sh) : 0);
+    X = ((lb ^ hb) >> 31) ? X - ml : X + ml;
+  }
+  int E = Eh;
+  if (X >= (1ll << 53)) {
+    X >>= 1;
+    ++E;
+  } else if (X < (1ll << 52)) {
+    X <<= 1;
+    --E;
+  }
+  const long long bits = ((long long)(hb >> 31) << 63) | ((long long)(E - 127 + 1023 + e) << 52) |
+                         (X & ((1ll << 52) - 1));
+  return __longlong_as_double(bits);
+}
+
+// exp[r] = binary exponent of max_j |X[r][j]| (frexp convention: max = f 2^e, f in [0.5, 1);
+// 0 for an all-zero row).  One CTA per row.
+__global__ void row_exponent_kernel(const double* __restrict__ X, int64_t ldx, int64_t n, int* __restrict__ ex) {
+  const int64_t r = blockIdx.x;
+  double mx = 0.0;
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) mx = fmax(mx, fabs(X[r * ldx + j]));
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
+    int e = 0;
+    if (mx > 0.0) frexp(mx, &e);
+    ex[r] = e;
+  }
+}
+
+// Digit planes of rows 0 .. rows-1 (columns 0 .. n-1; columns n .. ldk-1 and rows rows ..
+// rows_pad-1 are written as zeros): round X[r][j] 2^(47 - e_r) to an integer v (|v| <= 2^47)
+// and split it into balanced base-256 digits, most significant in plane 0.  Each plane is
+// tiled by 64-column boxes, [ldk / 64][rows_pad][64], so that every 128-row TMA box is one
+// contiguous 16 KB block of memory.
+__global__ void slice_digits_kernel(const double* __restrict__ X, int64_t ldx, int64_t rows, int64_t n,
+                                    const int* __restrict__ ex, __half* __restrict__ planes, int64_t rows_pad,
+                                    int64_t ldk) {
+  const int64_t total = rows_pad * ldk;
+  const int64_t plane = rows_pad * ldk;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / ldk, j = e - r * ldk;
+    long long v = 0;
+    if (r < rows && j < n) v = __double2ll_rn(scalbn(X[r * ldx + j], 47 - ex[r]));
+    int d[kSl];
+    digits6(v, d);
+#pragma unroll
+    for (int s = 0; s < kSl; ++s) planes[s * plane + (j / kKiBox) * rows_pad * kKiBox + r * kKiBox + (j % kKiBox)] =
+        __int2half_rn(d[s]);
+  }
+}
+
+__global__ void __launch_bounds__(kKiThreads, 1)
+kinv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               const int* __restrict__ ea, const int* __restrict__ eb, int64_t n, int nb, double* __restrict__ part,
+               int64_t per, int64_t total, int64_t kpt, int span, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  unsigned char* sA = smem;
+  unsigned char* sB = smem + kKiAStages * kKiATile;
+  __shared__ uint64_t fullA[kKiAStages], emptyA[kKiAStages], fullB[kKiBStages], emptyB[kKiBStages], accf, tfree,
+      mdone;
+  __shared__ uint32_t tmem_holder;
+  __shared__ int abort_flag;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t u0 = (int64_t)blockIdx.x * per;
+  const int64_t u1 = min(total, u0 + per);
+  const int64_t first_tile = u0 / kpt;
+  const int nunits = (int)(u1 - u0);
+
+  if (tid == 0) {
+    for (int s = 0; s < kKiAStages; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&fullA[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&emptyA[s])));
+    }
+    for (int s = 0; s < kKiBStages; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&fullB[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&emptyB[s])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&accf)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(smem_u32(&tfree)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mdone)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    abort_flag = 0;
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
+                 "r"(kKiTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_holder;
+  volatile int* abort_v = &abort_flag;
+
+  if (warp == 0) {
+    // ---- TMA producer: per 64-column box, the six right-hand-side planes, then the six
+    // K^{-1} planes of the unit's row tile
+    if (lane == 0) {
+      int na = 0, nbx = 0;
+      bool ok = true;
+      for (int u = 0; u < nunits && ok; ++u) {
+        const int64_t unit = u0 + u, t = unit / kpt, c = unit - t * kpt;
+        for (int kb = 0; kb < kKiChunk / kKiBox && ok; ++kb, ++nbx) {
+          const int kbg = (int)(c * (kKiChunk / kKiBox) + kb);  // 64-column box index
+          const int bs = nbx % kKiBStages;
+          if (nbx >= kKiBStages && !mbar_wait(smem_u32(&emptyB[bs]), ((nbx / kKiBStages) - 1) & 1, abort_v)) {
+            ok = false;
+            break;
+          }
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&fullB[bs])),
+                       "r"(kKiBTile));
+          for (int q = 0; q < kSl; ++q)
+            asm volatile(
+                "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                ::"r"(smem_u32(sB + bs * kKiBTile + q * kKiBPlane)), "l"(&tmB), "r"(0), "r"(kbg * kKiN), "r"(q),
+                "r"(smem_u32(&fullB[bs]))
+                : "memory");
+          for (int s = 0; s < kSl; ++s, ++na) {
+            const int as = na % kKiAStages;
+            if (na >= kKiAStages && !mbar_wait(smem_u32(&emptyA[as]), ((na / kKiAStages) - 1) & 1, abort_v)) {
+              ok = false;
+              break;
+            }
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&fullA[as])),
+                         "r"(kKiATile));
+            asm volatile(
+                "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                ::"r"(smem_u32(sA + as * kKiATile)), "l"(&tmA), "r"(0),
+                "r"((int)((int64_t)kbg * kpt * kKiChunk + t * kKiRows)), "r"(s),
+                "r"(smem_u32(&fullA[as]))
+                : "memory");
+          }
+        }
+      }
+      // drain: every issued load lands before the CTA may exit (bounded, even after an abort)
+      int unused = 0;
+      for (int i = (na > kKiAStages ? na - kKiAStages : 0); i < na; ++i)
+        mbar_wait(smem_u32(&fullA[i % kKiAStages]), (i / kKiAStages) & 1, &unused);
+      for (int i = (nbx > kKiBStages ? nbx - kKiBStages : 0); i < nbx; ++i)
+        mbar_wait(smem_u32(&fullB[i % kKiBStages]), (i / kKiBStages) & 1, &unused);
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer: group g = s + t accumulates P_s Q_t^T at TMEM columns 64 g
+    if (lane == 0) {
+      const uint32_t idesc = (1u << 4) | ((uint32_t)(kKiN >> 3) << 17) | ((uint32_t)(kKiRows >> 4) << 24);
+      int na = 0, nbx = 0;
+      bool ok = true;
+      for (int u = 0; u < nunits && ok; ++u) {
+        // the epilogue has drained the previous chunk's groups
+        if (u > 0 && !mbar_wait(smem_u32(&tfree), (u - 1) & 1, abort_v)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        for (int kb = 0; kb < kKiChunk / kKiBox && ok; ++kb, ++nbx) {
+          const int bs = nbx % kKiBStages;
+          if (!mbar_wait(smem_u32(&fullB[bs]), (nbx / kKiBStages) & 1, abort_v)) {
+            ok = false;
+            break;
+          }
+          const uint32_t b0 = smem_u32(sB + bs * kKiBTile);
+          for (int s = 0; s < kSl; ++s, ++na) {
+            const int as = na % kKiAStages;
+            if (!mbar_wait(smem_u32(&fullA[as]), (na / kKiAStages) & 1, abort_v)) {
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            issue_plane(tmem, s, smem_u32(sA + as * kKiATile), b0, idesc, kb == 0 && s == 0);
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         ::"r"(smem_u32(&emptyA[as])) : "memory");
+          }
+          if (!ok) break;
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                       ::"r"(smem_u32(&emptyB[bs])) : "memory");
+        }
+        if (!ok) break;
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     ::"r"(smem_u32(&accf)) : "memory");
+      }
+      // completion of every MMA issued above (waited on before the tensor memory is freed)
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                   ::"r"(smem_u32(&mdone)) : "memory");
+    }
+  } else {
+    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows of the tile) and
+    // right-hand sides 32 h .. + 31, h = (w - 2) / 4
+    const int q4 = warp & 3, h = (warp - 2) >> 2;
+    const int r = q4 * 32 + lane;
+    float Sh[32], Sl[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) Sh[c] = Sl[c] = 0.f;
+    for (int u = 0; u < nunits; ++u) {
+      const int64_t unit = u0 + u, t = unit / kpt;
+      if (!mbar_wait(smem_u32(&accf), u & 1, abort_v)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      add_groups(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(h * 32), Sh, Sl);
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tfree)) : "memory");
+      // last unit of this row tile within the CTA's run: write the partial tile
+      if (u == nunits - 1 || (unit + 1) / kpt != t) {
+        const int64_t row = t * kKiRows + r;
+        const int er = row < n ? ea[row] : 0;
+        double* P = part + ((blockIdx.x * (int64_t)span + (t - first_tile)) * kKiN) * kKiRows;
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          const int b = h * 32 + c;
+          const double val = (b < nb) ? pair_to_double_scaled(Sh[c], Sl[c], er + eb[b] - 14) : 0.0;
+          P[b * kKiRows + r] = val;
+          Sh[c] = Sl[c] = 0.f;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 1) {
+    // every issued MMA has finished before the tensor memory is released (bounded wait)
+    int unused = 0;
+    if (lane == 0) mbar_wait(smem_u32(&mdone), 0, &unused);
+    __syncwarp();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kKiTmemCols));
+  }
+  if (tid == 0 && *abort_v) atomicExch(err, 1);
+}
+
+}  // namespace
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
+
+void kinv_tc_prepare() {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(kinv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kKiSmem);
+    attr = true;
+  }
+}
+
+int64_t kinv_tc_ld(int64_t n) { return (n + kKiChunk - 1) / kKiChunk * kKiChunk; }
+
+bool kinv_tc_supported(int64_t n) {
+  const int64_t ld = kinv_tc_ld(n);
+  return n > 0 && ld <= INT32_MAX && tensor_map_encoder() != nullptr;
+}
+
+size_t kinv_tc_plane_elems(int64_t n) { return (size_t)kSl * kinv_tc_ld(n) * kinv_tc_ld(n); }
+
+int64_t kinv_tc_slice(const double* X, int64_t ldx, int64_t rows, int64_t n, int* ex, void* planes_v,
+                      int64_t rows_pad, cudaStream_t s) {
+  __half* planes = static_cast<__half*>(planes_v);
+  if (rows > 0) row_exponent_kernel<<<(unsigned)rows, 256, 0, s>>>(X, ldx, n, ex);
+  const int64_t ldk = kinv_tc_ld(n);
+  const int64_t total = rows_pad * ldk;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 65535 * 8) blocks = 65535 * 8;
+  slice_digits_kernel<<<(unsigned)blocks, 256, 0, s>>>(X, ldx, rows, n, ex, planes, rows_pad, ldk);
+  return rows > 0 ? 2 : 1;
+}
+
+namespace {
+struct KiPlan {
+  int64_t tiles, kpt, total, per, ctas;
+  int span;
+};
+int num_sms_tc() {
+  static int v = 0;
+  if (v == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    if (v <= 0) v = 1;
+  }
+  return v;
+}
+KiPlan ki_plan(int64_t n) {
+  KiPlan p;
+  const int64_t ld = kinv_tc_ld(n);
+  p.tiles = ld / kKiRows;
+  p.kpt = ld / kKiChunk;
+  p.total = p.tiles * p.kpt;
+  const int64_t slots = num_sms_tc();
+  p.per = (p.total + slots - 1) / slots;
+  p.ctas = (p.total + p.per - 1) / p.per;
+  p.span = (int)((p.per + p.kpt - 1) / p.kpt + 1);
+  return p;
+}
+}  // namespace
+
+size_t kinv_tc_work_elems(int64_t n) {
+  const int64_t ld = kinv_tc_ld(n);
+  const KiPlan p = ki_plan(n);
+  // right-hand-side planes (FP16, counted in doubles) + exponents + partials
+  const size_t planes = ((size_t)kSl * kKiN * ld * 2 + 7) / 8;
+  return 32 + planes + kKiN + (size_t)p.ctas * p.span * kKiN * kKiRows;  // 32: alignment slack
+}
+
+int kinv_reduce(const double* part, double* X, int64_t ldx, int64_t n, int64_t nb, int BM, int BR, int64_t per,
+                int64_t kpt, int span, int64_t tiles, cudaStream_t s);
+
+cudaError_t kinv_apply_tc(const void* planes, const int* ea, int64_t n, const double* D, int64_t B, double* X,
+                          double* work, int* err, cudaStream_t s, int64_t* launches) {
+  work = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(work) + 255) & ~(uintptr_t)255);
+  *launches = 0;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return cudaErrorNotSupported;
+  const int64_t ld = kinv_tc_ld(n);
+  const KiPlan p = ki_plan(n);
+  __half* bpl = reinterpret_cast<__half*>(work);
+  int* eb = reinterpret_cast<int*>(work + ((size_t)kSl * kKiN * ld * 2 + 7) / 8);
+  double* part = work + ((size_t)kSl * kKiN * ld * 2 + 7) / 8 + kKiN;
+  CUtensorMap tA, tB;
+  {
+    // tiled planes: (64 columns, box-major rows kb * ld + i, plane)
+    const cuuint64_t dims[3] = {(cuuint64_t)kKiBox, (cuuint64_t)(ld / kKiBox * ld), (cuuint64_t)kSl};
+    const cuuint64_t strides[2] = {(cuuint64_t)(kKiBox * 2), (cuuint64_t)(ld * ld * 2)};
+    const cuuint32_t box[3] = {(cuuint32_t)kKiBox, (cuuint32_t)kKiRows, 1};
+    const cuuint32_t es[3] = {1, 1, 1};
+    if (enc(&tA, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<void*>(planes), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  {
+    const cuuint64_t dims[3] = {(cuuint64_t)kKiBox, (cuuint64_t)(ld / kKiBox * kKiN), (cuuint64_t)kSl};
+    const cuuint64_t strides[2] = {(cuuint64_t)(kKiBox * 2), (cuuint64_t)(kKiN * ld * 2)};
+    const cuuint32_t box[3] = {(cuuint32_t)kKiBox, (cuuint32_t)kKiN, 1};
+    const cuuint32_t es[3] = {1, 1, 1};
+    if (enc(&tB, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, bpl, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  kinv_tc_prepare();
+  for (int64_t q0 = 0; q0 < B; q0 += kKiN) {
+    const int64_t nb = B - q0 < kKiN ? B - q0 : kKiN;
+    *launches += kinv_tc_slice(D + q0 * n, n, nb, n, eb, bpl, kKiN, s);
+    kinv_tc_kernel<<<(unsigned)p.ctas, kKiThreads, kKiSmem, s>>>(tA, tB, ea, eb, n, (int)nb, part, p.per, p.total,
+                                                                 p.kpt, p.span, err);
+    *launches += 1;
+    *launches += kinv_reduce(part, X + q0 * n, n, n, nb, kKiRows, kKiN, p.per, p.kpt, p.span, p.tiles, s);
+  }
+  return cudaGetLastError();
+}
+
+
+// ------------------------------------------------------------------ batched adjoint products
+// The double-FP32 tier's adjoint product for batches, m-hat_w[b][j] = sum_i conj(F-hat_w[i][j])
+// d-hat_w[b][i] (Sec. 4, the block-diagonalised circulant), by the same exact digit planes.
+// Per frequency it is the real GEMM D[j][n] = sum_k A'_w[j][k] B_w[n][k] over k = 2 i + c:
+//   A'_w[j][2i] = Re F-hat_w[i][j],  A'_w[j][2i+1] = Im F-hat_w[i][j]           (formed once)
+//   B_w[2b][.] = (Re d, Im d),  B_w[2b+1][.] = (Im d, -Re d)  at (2i, 2i+1)      (per call)
+// so that D[j][2b] = Re m-hat_w[b][j] and D[j][2b+1] = Im m-hat_w[b][j].  A' has one exponent
+// per (w, j) over i and B one per (w, b), so each output's scale factors out of its sum.
+// Planes: A' [S][n_f][K_pad / 64][N_m,pad][64], B [S][n_f][K_pad / 64][NB_pad][64] FP16 (tiled
+// by 64-column boxes) with K_pad = 2R rounded up to 128, N_m,pad to 128 and NB_pad = 2B to 64.  A unit is (w, 128 rows j, 64 columns n)
+// over all of K (chunks of 128 as above); units are split evenly over one CTA per SM, the
+// column groups of a row tile back to back so its A' planes are read from HBM once.
+
+namespace {
+
+__global__ void adj_planes_kernel(const float4* __restrict__ hat, int64_t nf, int64_t R, int64_t Nm, int64_t Nmp,
+                                  int64_t Kp, __half* __restrict__ planes, int* __restrict__ ex) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // w Nmp + j
+  if (idx >= nf * Nmp) return;
+  const int64_t w = idx / Nmp, j = idx - w * Nmp;
+  const int64_t plane2 = nf * Nmp * Kp / 2;  // one plane in half2 units
+  const int64_t KB = Kp / kKiBox;
+  // tiled: [w][k / 64][j][64] within a plane
+  __half2* row = reinterpret_cast<__half2*>(planes) + (w * KB * Nmp + j) * (kKiBox / 2);
+  int e = 0;
+  if (j < Nm) {
+    double mx = 0.0;
+    for (int64_t i = 0; i < R; ++i) {
+      const float4 v = hat[(w * R + i) * Nm + j];
+      mx = fmax(mx, fmax(fabs((double)v.x + (double)v.y), fabs((double)v.z + (double)v.w)));
+    }
+    if (mx > 0.0) frexp(mx, &e);
+  }
+  ex[idx] = e;
+  for (int64_t i = 0; i < Kp / 2; ++i) {
+    long long vr = 0, vi = 0;
+    if (j < Nm && i < R) {
+      const float4 v = hat[(w * R + i) * Nm + j];
+      vr = __double2ll_rn(scalbn((double)v.x + (double)v.y, 47 - e));
+      vi = __double2ll_rn(scalbn((double)v.z + (double)v.w, 47 - e));
+    }
+    int dr[kSl], di[kSl];
+    digits6(vr, dr);
+    digits6(vi, di);
+#pragma unroll
+    for (int s = 0; s < kSl; ++s)
+      row[s * plane2 + (i / (kKiBox / 2)) * Nmp * (kKiBox / 2) + (i % (kKiBox / 2))] =
+          __halves2half2(__int2half_rn(dr[s]), __int2half_rn(di[s]));
+  }
+}
+
+// B planes of one call: one CTA per (w, b), b < NBp / 2 (rows past B are zeros).
+__global__ void adj_vec_planes_kernel(const double2* __restrict__ dhat, int64_t nf, int64_t R, int64_t B,
+                                      int64_t NBp, int64_t Kp, __half* __restrict__ planes, int* __restrict__ eb) {
+  const int64_t w = blockIdx.x, b = blockIdx.y;
+  const double2* src = dhat + (b * nf + w) * R;
+  double mx = 0.0;
+  if (b < B)
+    for (int64_t i = threadIdx.x; i < R; i += blockDim.x) mx = fmax(mx, fmax(fabs(src[i].x), fabs(src[i].y)));
+  __shared__ double red[32];
+  __shared__ int es;
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) mx = fmax(mx, red[k]);
+    int e = 0;
+    if (mx > 0.0) frexp(mx, &e);
+    es = e;
+    eb[w * NBp + 2 * b] = e;
+    eb[w * NBp + 2 * b + 1] = e;
+  }
+  __syncthreads();
+  const int e = es;
+  const int64_t plane2 = nf * NBp * Kp / 2;
+  const int64_t KB = Kp / kKiBox;
+  // tiled: [w][k / 64][n][64] within a plane
+  __half2* r0 = reinterpret_cast<__half2*>(planes) + (w * KB * NBp + 2 * b) * (kKiBox / 2);
+  __half2* r1 = r0 + kKiBox / 2;
+  for (int64_t i = threadIdx.x; i < Kp / 2; i += blockDim.x) {
+    long long vr = 0, vi = 0;
+    if (b < B && i < R) {
+      vr = __double2ll_rn(scalbn(src[i].x, 47 - e));
+      vi = __double2ll_rn(scalbn(src[i].y, 47 - e));
+    }
+    int dr[kSl], di[kSl];
+    digits6(vr, dr);
+    digits6(vi, di);
+#pragma unroll
+    for (int s = 0; s < kSl; ++s) {
+      const int64_t o = s * plane2 + (i / (kKiBox / 2)) * NBp * (kKiBox / 2) + (i % (kKiBox / 2));
+      r0[o] = __halves2half2(__int2half_rn(dr[s]), __int2half_rn(di[s]));
+      r1[o] = __halves2half2(__int2half_rn(di[s]), __int2half_rn(-dr[s]));
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kKiThreads, 1)
+adj_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              const int* __restrict__ ea, const int* __restrict__ eb, double2* __restrict__ mhat, int nf,
+              int64_t Nm, int64_t Nmp, int64_t NBp, int B, int nchunk, int JT, int NG, int64_t per, int64_t total,
+              int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  unsigned char* sA = smem;
+  unsigned char* sB = smem + kKiAStages * kKiATile;
+  __shared__ uint64_t fullA[kKiAStages], emptyA[kKiAStages], fullB[kKiBStages], emptyB[kKiBStages], accf, tfree,
+      mdone;
+  __shared__ uint32_t tmem_holder;
+  __shared__ int abort_flag;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t u0 = (int64_t)blockIdx.x * per;
+  const int64_t u1 = min(total, u0 + per);
+  const int nunits = (int)(u1 - u0);
+  constexpr int kBoxes = kKiChunk / kKiBox;
+
+  if (tid == 0) {
+    for (int s = 0; s < kKiAStages; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&fullA[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&emptyA[s])));
+    }
+    for (int s = 0; s < kKiBStages; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&fullB[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&emptyB[s])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&accf)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(smem_u32(&tfree)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mdone)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    abort_flag = 0;
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
+                 "r"(kKiTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_holder;
+  volatile int* abort_v = &abort_flag;
+
+  if (warp == 0) {
+    // ---- TMA producer
+    if (lane == 0) {
+      int na = 0, nbx = 0;
+      bool ok = true;
+      for (int u = 0; u < nunits && ok; ++u) {
+        const int64_t unit = u0 + u;
+        const int g = (int)(unit % NG);
+        const int jt = (int)((unit / NG) % JT);
+        const int w = (int)(unit / ((int64_t)NG * JT));
+        const int KB = nchunk * kBoxes;
+        for (int kb = 0; kb < nchunk * kBoxes && ok; ++kb, ++nbx) {
+          // tiled planes: box kb of frequency w starts at row (w KB + kb) * rows
+          const int arow = (int)(((int64_t)w * KB + kb) * Nmp + (int64_t)jt * kKiRows);
+          const int brow = (int)(((int64_t)w * KB + kb) * NBp + (int64_t)g * kKiN);
+          const int bs = nbx % kKiBStages;
+          if (nbx >= kKiBStages && !mbar_wait(smem_u32(&emptyB[bs]), ((nbx / kKiBStages) - 1) & 1, abort_v)) {
+            ok = false;
+            break;
+          }
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&fullB[bs])),
+                       "r"(kKiBTile));
+          for (int q = 0; q < kSl; ++q)
+            asm volatile(
+                "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                ::"r"(smem_u32(sB + bs * kKiBTile + q * kKiBPlane)), "l"(&tmB), "r"(0), "r"(brow), "r"(q),
+                "r"(smem_u32(&fullB[bs]))
+                : "memory");
+          for (int s = 0; s < kSl; ++s, ++na) {
+            const int as = na % kKiAStages;
+            if (na >= kKiAStages && !mbar_wait(smem_u32(&emptyA[as]), ((na / kKiAStages) - 1) & 1, abort_v)) {
+              ok = false;
+              break;
+            }
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&fullA[as])),
+                         "r"(kKiATile));
+            asm volatile(
+                "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                ::"r"(smem_u32(sA + as * kKiATile)), "l"(&tmA), "r"(0), "r"(arow), "r"(s), "r"(smem_u32(&fullA[as]))
+                : "memory");
+          }
+        }
+      }
+      int unused = 0;
+      for (int i = (na > kKiAStages ? na - kKiAStages : 0); i < na; ++i)
+        mbar_wait(smem_u32(&fullA[i % kKiAStages]), (i / kKiAStages) & 1, &unused);
+      for (int i = (nbx > kKiBStages ? nbx - kKiBStages : 0); i < nbx; ++i)
+        mbar_wait(smem_u32(&fullB[i % kKiBStages]), (i / kKiBStages) & 1, &unused);
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer; one accumulation chunk = kBoxes boxes, chunk counter cc across units
+    if (lane == 0) {
+      const uint32_t idesc = (1u << 4) | ((uint32_t)(kKiN >> 3) << 17) | ((uint32_t)(kKiRows >> 4) << 24);
+      int na = 0, nbx = 0, cc = 0;
+      bool ok = true;
+      for (int u = 0; u < nunits && ok; ++u) {
+        for (int c = 0; c < nchunk && ok; ++c, ++cc) {
+          if (cc > 0 && !mbar_wait(smem_u32(&tfree), (cc - 1) & 1, abort_v)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          for (int kb = 0; kb < kBoxes && ok; ++kb, ++nbx) {
+            const int bs = nbx % kKiBStages;
+            if (!mbar_wait(smem_u32(&fullB[bs]), (nbx / kKiBStages) & 1, abort_v)) {
+              ok = false;
+              break;
+            }
+            const uint32_t b0 = smem_u32(sB + bs * kKiBTile);
+            for (int s = 0; s < kSl; ++s, ++na) {
+              const int as = na % kKiAStages;
+              if (!mbar_wait(smem_u32(&fullA[as]), (na / kKiAStages) & 1, abort_v)) {
+                ok = false;
+                break;
+              }
+              asm volatile("tcgen05.fence::after_thread_sync;");
+              issue_plane(tmem, s, smem_u32(sA + as * kKiATile), b0, idesc, kb == 0 && s == 0);
+              asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                           ::"r"(smem_u32(&emptyA[as])) : "memory");
+            }
+            if (!ok) break;
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         ::"r"(smem_u32(&emptyB[bs])) : "memory");
+          }
+          if (!ok) break;
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                       ::"r"(smem_u32(&accf)) : "memory");
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                   ::"r"(smem_u32(&mdone)) : "memory");
+    }
+  } else {
+    // ---- epilogue: TMEM lanes 32 (w % 4) .. + 31 = rows j of the tile, columns 32 h .. + 31
+    // = vectors 16 h .. + 15 of the group (real, imaginary interleaved)
+    const int q4 = warp & 3, h = (warp - 2) >> 2;
+    const int r = q4 * 32 + lane;
+    float Sh[32], Sl[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) Sh[c] = Sl[c] = 0.f;
+    int cc = 0;
+    bool ok = true;
+    for (int u = 0; u < nunits && ok; ++u) {
+      const int64_t unit = u0 + u;
+      const int g = (int)(unit % NG);
+      const int jt = (int)((unit / NG) % JT);
+      const int w = (int)(unit / ((int64_t)NG * JT));
+      for (int c = 0; c < nchunk; ++c, ++cc) {
+        if (!mbar_wait(smem_u32(&accf), cc & 1, abort_v)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        add_groups(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(h * 32), Sh, Sl);
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tfree)) : "memory");
+      }
+      if (!ok) break;
+      const int64_t j = (int64_t)jt * kKiRows + r;
+      const int ej = ea[w * Nmp + j];
+#pragma unroll
+      for (int k = 0; k < 32; k += 2) {
+        const int n = g * kKiN + h * 32 + k;
+        const int b = n >> 1;
+        if (j < Nm && b < B) {
+          const int sh = ej + eb[w * NBp + n] - 14;
+          mhat[((int64_t)b * nf + w) * Nm + j] =
+              make_double2(pair_to_double_scaled(Sh[k], Sl[k], sh), pair_to_double_scaled(Sh[k + 1], Sl[k + 1], sh));
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 32; ++k) Sh[k] = Sl[k] = 0.f;
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 1) {
+    int unused = 0;
+    if (lane == 0) mbar_wait(smem_u32(&mdone), 0, &unused);
+    __syncwarp();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kKiTmemCols));
+  }
+  if (tid == 0 && *abort_v) atomicExch(err, 1);
+}
+
+int64_t rup(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+size_t adj_digits_plane_elems(int64_t nf, int64_t R, int64_t Nm) {
+  return (size_t)kSl * nf * rup(Nm, kKiRows) * rup(2 * R, kKiChunk);
+}
+size_t adj_digits_exp_elems(int64_t nf, int64_t Nm) { return (size_t)nf * rup(Nm, kKiRows); }
+
+bool adj_digits_supported(int64_t nf, int64_t R, int64_t Nm, int64_t B) {
+  const int64_t Kp = rup(2 * R, kKiChunk), Nmp = rup(Nm, kKiRows), NBp = rup(2 * B, kKiN);
+  return B >= 16 && nf * Nmp <= INT32_MAX && nf * NBp <= INT32_MAX && Kp <= INT32_MAX &&
+         tensor_map_encoder() != nullptr;
+}
+
+int64_t adj_digits_build(const void* hat, int64_t nf, int64_t R, int64_t Nm, void* planes, int* ex, cudaStream_t s) {
+  const int64_t Nmp = rup(Nm, kKiRows), Kp = rup(2 * R, kKiChunk);
+  const int64_t total = nf * Nmp;
+  adj_planes_kernel<<<(unsigned)((total + 127) / 128), 128, 0, s>>>(static_cast<const float4*>(hat), nf, R, Nm, Nmp,
+                                                                    Kp, static_cast<__half*>(planes), ex);
+  return 1;
+}
+
+size_t adj_digits_work_bytes(int64_t nf, int64_t R, int64_t B) {
+  const int64_t Kp = rup(2 * R, kKiChunk), NBp = rup(2 * B, kKiN);
+  return 256 + (size_t)kSl * nf * NBp * Kp * 2 + (size_t)nf * NBp * sizeof(int);
+}
+
+cudaError_t adj_digits_apply(const void* planes, const int* ea, int64_t nf, int64_t R, int64_t Nm, const void* dhat,
+                             void* mhat, int64_t B, void* work, int* err, cudaStream_t s, int* launches) {
+  *launches = 0;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return cudaErrorNotSupported;
+  const int64_t Kp = rup(2 * R, kKiChunk), Nmp = rup(Nm, kKiRows), NBp = rup(2 * B, kKiN);
+  unsigned char* wb = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(work) + 255) & ~(uintptr_t)255);
+  __half* bpl = reinterpret_cast<__half*>(wb);
+  int* eb = reinterpret_cast<int*>(wb + (size_t)kSl * nf * NBp * Kp * 2);
+  CUtensorMap tA, tB;
+  const cuuint32_t es[3] = {1, 1, 1};
+  {
+    const cuuint64_t dims[3] = {(cuuint64_t)kKiBox, (cuuint64_t)(nf * (Kp / kKiBox) * Nmp), (cuuint64_t)kSl};
+    const cuuint64_t strides[2] = {(cuuint64_t)(kKiBox * 2), (cuuint64_t)(nf * Nmp * Kp * 2)};
+    const cuuint32_t box[3] = {(cuuint32_t)kKiBox, (cuuint32_t)kKiRows, 1};
+    if (enc(&tA, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<void*>(planes), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  {
+    const cuuint64_t dims[3] = {(cuuint64_t)kKiBox, (cuuint64_t)(nf * (Kp / kKiBox) * NBp), (cuuint64_t)kSl};
+    const cuuint64_t strides[2] = {(cuuint64_t)(kKiBox * 2), (cuuint64_t)(nf * NBp * Kp * 2)};
+    const cuuint32_t box[3] = {(cuuint32_t)kKiBox, (cuuint32_t)kKiN, 1};
+    if (enc(&tB, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, bpl, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  adj_digits_prepare();
+  adj_vec_planes_kernel<<<dim3((unsigned)nf, (unsigned)(NBp / 2)), 128, 0, s>>>(
+      static_cast<const double2*>(dhat), nf, R, B, NBp, Kp, bpl, eb);
+  const int JT = (int)(Nmp / kKiRows), NG = (int)(NBp / kKiN);
+  const int64_t total = nf * JT * NG;
+  const int64_t slots = num_sms_tc();
+  const int64_t per = (total + slots - 1) / slots;
+  const int64_t ctas = (total + per - 1) / per;
+  adj_tc_kernel<<<(unsigned)ctas, kKiThreads, kKiSmem, s>>>(tA, tB, ea, eb, static_cast<double2*>(mhat), (int)nf, Nm,
+                                                            Nmp, NBp, (int)B, (int)(Kp / kKiChunk), JT, NG, per, total,
+                                                            err);
+  *launches = 2;
+  return cudaGetLastError();
+}
+
+void adj_digits_prepare() {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(adj_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kKiSmem);
+    attr = true;
+  }
+}
+
+}  // namespace bti

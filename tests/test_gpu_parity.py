@@ -808,7 +808,8 @@ def test_explicit_inverse_online_solve(B):
     assert relb(host(m), host(m_dd)) < 1e-10
     h.infer_map(cuda(d), m, refine_iters=1)
     assert relb(host(m), m_or) < 1e-12
-    # the online graph applies the inverse too
+    # the online graph applies the inverse too, and with G's digit planes its G^* (B >= 16)
+    # runs on the tensor cores as well
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         h.set_stream(stream)
@@ -817,6 +818,11 @@ def test_explicit_inverse_online_solve(B):
         h.online(cuda(d), m2, q, refine_iters=1)
         assert relb(host(m2), m_or) < 1e-12
         assert relb(host(q), oracle.qoi_map(Fq, m_or)) < 1e-12
+        h.set_digit_planes(bti.OP_G, True)
+        h.online(cuda(d), m2, q)
+        assert relb(host(m2), m_or) < 1e-10
+        assert relb(host(q), oracle.qoi_map(Fq, m_or)) < 1e-10
+        h.set_digit_planes(bti.OP_G, False)
     torch.cuda.synchronize()
     h.set_stream(torch.cuda.current_stream())
     # a new factor: the stale inverse is not used
@@ -855,4 +861,49 @@ def test_explicit_inverse_ragged_size():
     m_map = torch.empty((7, 30, 36), dtype=torch.float64, device="cuda")
     h.infer_map(cuda(d_obs), m_map, refine_iters=1)
     assert relb(host(m_map), oracle.map_point(F, G, var, d_obs)) < 1e-11
+    h.close()
+
+
+DIGIT_CASES = [
+    # (name, Nm, Nd, Nt, B): ragged row tiles (N_m % 128 != 0), one or two column groups,
+    # one or many 128-wide accumulation chunks (2 R up to 2,200), ragged vector groups
+    ("b16_R13_ragged", 1000, 13, 45, 16),
+    ("b40_two_groups", 700, 6, 64, 40),
+    ("b20_R1100_chunks", 300, 1100, 8, 20),
+    ("b64_Nm512", 512, 20, 30, 64),
+]
+
+
+@pytest.mark.parametrize("name,Nm,Nd,Nt,B", DIGIT_CASES, ids=[c[0] for c in DIGIT_CASES])
+def test_digit_plane_adjoint_matches_oracle(name, Nm, Nd, Nt, B):
+    """bti_set_digit_planes: the double-FP32 tier's adjoint for B >= 16 on the tensor cores,
+    exact in FP16 digit planes, matches the oracle at the FP64 tolerance and the CUDA-core
+    double-FP32 kernel closely; releasing the planes returns to the CUDA cores."""
+    p = synthetic.small(name, 1, Nm, Nd, Nt, Nq=2)
+    F = p.blocks_F()
+    d = p.vectors_d(B)
+    h = make_handle(F, None, bti.DF64)
+    h.set_digit_planes(bti.OP_F, True)
+    out = torch.empty((B, Nt, Nm), dtype=torch.float64, device="cuda")
+    h.profile_enable(True)
+    h.profile_read()
+    h.apply_FT(cuda(d), out)
+    assert h.profile_read()[0]["prod_adj"][1] == 2  # vector planes + the tensor-core kernel
+    ref = oracle.p2o_apply_adjoint(F, d)
+    assert relb(host(out), ref) < 1e-12
+    h.set_digit_planes(bti.OP_F, False)
+    out2 = torch.empty_like(out)
+    h.apply_FT(cuda(d), out2)
+    assert h.profile_read()[0]["prod_adj"][1] == 1
+    assert relb(host(out), host(out2)) < 1e-12
+    h.profile_enable(False)
+    h.close()
+
+
+def test_digit_planes_need_the_double_fp32_tier():
+    p = synthetic.small("dig_state", 1, 64, 3, 8)
+    h = make_handle(p.blocks_F(), None, bti.F64)
+    with pytest.raises(bti.BtiError) as e:
+        h.set_digit_planes(bti.OP_F, True)
+    assert e.value.status == 3
     h.close()
