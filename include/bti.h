@@ -246,15 +246,17 @@ bti_status bti_apply_postcov(bti_handle h, const double* v, double* out, int64_t
 bti_status bti_infer_map_prior(bti_handle h, const double* d_obs, const double* m_prior, double* m_map, int64_t B,
                                int refine_iters);
 
-/* Exact tensor-core adjoint products for the double-FP32 tier (enable = 1; 0 releases).
- * Forms, once, digit planes of op's spectral blocks: each F-hat_w[i][j] (re and im) as six
- * FP16 planes of balanced base-256 digits with one power-of-two scale per (w, j), a 47-bit
- * fixed-point image (12 n_f ceil(N_m/128)*128 ceil(2R/128)*128 bytes; 2.5 GB for the batched
- * workload's G).  Adjoint-type calls (bti_apply_FT / bti_apply_Gstar, and G^* inside
- * infer_map and online) with B >= 16 vectors and tensor cores on then run as tcgen05 FP16
- * MMAs whose FP32 sums are exact (Sec. 4's per-frequency products, FP64-level results).
- * Requires the operator set in BTI_P_DF64 (BTI_ERR_STATE); new blocks or a new prior drop
- * the planes.  Synchronises. */
+/* Exact tensor-core products for the double-FP32 tier (enable = 1; 0 releases).  Forms,
+ * once, digit planes of op's spectral blocks: each F-hat_w[i][j] (re and im) as six FP16
+ * planes of balanced base-256 digits with a power-of-two scale per (w, j) for the adjoint and
+ * per (w, i) for the forward product, a 47-bit fixed-point image (about 24 n_f N_m (2R
+ * rounded up to 128) bytes in all: 5 GB for the batched workload's G, 1.9 GB for its F_q).
+ * Calls with B >= 16 vectors and tensor cores on then run the per-frequency products of
+ * Sec. 4 as tcgen05 FP16 MMAs whose FP32 sums are exact: adjoint-type calls (bti_apply_FT,
+ * bti_apply_Gstar, G^* inside infer_map and online) and forward-type calls (bti_apply_F,
+ * bti_apply_Fq, predict_qoi, F_q inside online).  Results match the double-FP32 CUDA-core
+ * kernels to FP64 level.  Requires the operator set in BTI_P_DF64 (BTI_ERR_STATE); new
+ * blocks or a new prior drop the planes.  Synchronises. */
 bti_status bti_set_digit_planes(bti_handle h, bti_op op, int enable);
 
 /* Tensor-core products (on = 1, the default): with FP16 spectral blocks and B >= 8

@@ -27,6 +27,8 @@ struct OpStore {
   double* time = nullptr;  // [Nt][R][Nm] FP64 time-domain copy (F and G only)
   void* dig = nullptr;     // adjoint digit planes of the double-FP32 tier (bti_set_digit_planes)
   int* dig_ex = nullptr;   // their exponents, one per (w, j)
+  void* dig_f = nullptr;   // forward digit planes
+  int* dig_f_ex = nullptr; // their exponents, one per (w, i)
 };
 
 }  // namespace
@@ -224,6 +226,8 @@ void drop_store(OpStore& o) {
   dev_freep(o.scale);
   dev_free(o.dig);
   dev_freep(o.dig_ex);
+  dev_free(o.dig_f);
+  dev_freep(o.dig_f_ex);
   o.hat = nullptr;
   o.set = false;
 }
@@ -334,10 +338,13 @@ bti_status apply_fwd_t(bti_ctx* h, const OpStore& o, const void* in, void* out, 
   size_t n_mhat = (size_t)B * nf * Nm;
   // FP16 blocks with B >= 8 vectors: the tensor-core product (its own chunking)
   const bool tc = o.prec == BTI_P_F16 && h->tc_enabled && tc_fwd_f16_supported(Nm, R, B);
+  // double-FP32 blocks with digit planes and B >= 16: exact digit-plane product on the tensor cores
+  const bool dig = o.prec == BTI_P_DF64 && o.dig_f && h->tc_enabled && fwd_digits_supported(nf, R, Nm, B);
   size_t n_part = prod_fwd_partial_elems(nf, R, Nm, B);
   if (tc && tc_fwd_partial_elems(nf, R, Nm, B) > n_part) n_part = tc_fwd_partial_elems(nf, R, Nm, B);
   size_t n_dhat = (size_t)B * nf * R;
-  bti_status st = ensure(h, &h->ws, &h->ws_bytes, sizeof(C2<T>) * (n_mhat + n_part + n_dhat), "workspace");
+  const size_t base = sizeof(C2<T>) * (n_mhat + n_part + n_dhat);
+  bti_status st = ensure(h, &h->ws, &h->ws_bytes, base + (dig ? fwd_digits_work_bytes(nf, R, Nm) : 0), "workspace");
   if (st != BTI_OK) return st;
   C2<T>* mhat = (C2<T>*)h->ws;
   C2<T>* part = mhat + n_mhat;
@@ -355,6 +362,15 @@ bti_status apply_fwd_t(bti_ctx* h, const OpStore& o, const void* in, void* out, 
     }
     h->prof_count[BTI_K_PROD_FWD] += nl - 1;
     if (e != cudaSuccess) return cuda_check(h, e, "tensor-core forward product");
+  } else if (dig) {
+    int nl = 0;
+    cudaError_t e;
+    {
+      ProfScope ps(h, BTI_K_PROD_FWD);  // vector planes, the MMA kernel and its fixed-order sum
+      e = fwd_digits_apply(o.dig_f, o.dig_f_ex, nf, R, Nm, mhat, dhat, B, (char*)h->ws + base, h->status + 1, s, &nl);
+    }
+    h->prof_count[BTI_K_PROD_FWD] += nl - 1;
+    if (e != cudaSuccess) return cuda_check(h, e, "tensor-core forward product (digit planes)");
   } else if (o.prec == BTI_P_DF64)
     PROF(h, BTI_K_PROD_FWD, launch_prod_fwd_df64((const float4*)o.hat, (const double2*)mhat, (double2*)part, nf,
                                                  R, Nm, B, s, jc));
@@ -364,7 +380,7 @@ bti_status apply_fwd_t(bti_ctx* h, const OpStore& o, const void* in, void* out, 
   else
     PROF(h, BTI_K_PROD_FWD, (launch_prod_fwd<T, T>((const C2<T>*)o.hat, mhat, part, nf, R, Nm, B, s,
                                                    jc)));
-  if (!tc) PROF(h, BTI_K_REDUCE, (launch_reduce_chunks<T>(part, dhat, nf, R, Nm, B, s, jc)));
+  if (!tc && !dig) PROF(h, BTI_K_REDUCE, (launch_reduce_chunks<T>(part, dhat, nf, R, Nm, B, s, jc)));
   // the QoI map writes every qstride-th time step only (N_t / qstride rows per vector)
   const int os = (&o == &h->op[BTI_OP_FQ]) ? h->qstride : 1;
   irfft_out<T>(h, o, dhat, R, nf * R, out, (Nt / os) * R, R, B, io, os);
@@ -1230,24 +1246,31 @@ bti_status bti_set_digit_planes(bti_handle h, bti_op op, int enable) {
   OpStore& o = h->op[op];
   drop_online_graph_any(h);
   cudaStreamSynchronize(h->stream);
-  dev_free(o.dig);
-  dev_freep(o.dig_ex);
+  auto release = [&]() {
+    dev_free(o.dig);
+    dev_freep(o.dig_ex);
+    dev_free(o.dig_f);
+    dev_freep(o.dig_f_ex);
+  };
+  release();
   if (!enable) return BTI_OK;
   if (!o.set || o.prec != BTI_P_DF64)
     return fail(h, BTI_ERR_STATE, "set_digit_planes: the operator's blocks must be set in the BTI_P_DF64 tier");
   const int64_t nf = h->nf, R = o.R, Nm = h->Nm;
   st = dev_alloc(h, &o.dig, sizeof(uint16_t) * adj_digits_plane_elems(nf, R, Nm), "alloc digit planes");
   if (st == BTI_OK) st = dev_alloc(h, (void**)&o.dig_ex, sizeof(int) * adj_digits_exp_elems(nf, Nm), "alloc exps");
+  if (st == BTI_OK) st = dev_alloc(h, &o.dig_f, sizeof(uint16_t) * fwd_digits_plane_elems(nf, R, Nm), "alloc planes");
+  if (st == BTI_OK) st = dev_alloc(h, (void**)&o.dig_f_ex, sizeof(int) * fwd_digits_exp_elems(nf, R), "alloc exps");
   if (st == BTI_OK) {
     adj_digits_prepare();
-    count_dense(h, adj_digits_build(o.hat, nf, R, Nm, o.dig, o.dig_ex, h->stream));
+    kinv_tc_prepare();
+    int64_t nl = adj_digits_build(o.hat, nf, R, Nm, o.dig, o.dig_ex, h->stream);
+    nl += fwd_digits_build(o.hat, nf, R, Nm, o.dig_f, o.dig_f_ex, h->stream);
+    count_dense(h, nl);
     st = launched(h, "set_digit_planes");
     if (st == BTI_OK) st = cuda_check(h, cudaStreamSynchronize(h->stream), "set_digit_planes sync");
   }
-  if (st != BTI_OK) {
-    dev_free(o.dig);
-    dev_freep(o.dig_ex);
-  }
+  if (st != BTI_OK) release();
   return st;
 }
 
@@ -1746,6 +1769,7 @@ static bti_status reserve_online(bti_ctx* h, int64_t B) {
     if (op == BTI_OP_G || !h->op[op].set) continue;
     int64_t R = h->op[op].R;
     size_t f = 16 * ((size_t)B * nf * Nm + prod_fwd_partial_elems(nf, R, Nm, B) + (size_t)B * nf * R);
+    if (h->op[op].dig_f) f += fwd_digits_work_bytes(nf, R, Nm);
     if (f > fwd) fwd = f;
   }
   size_t ws = adj > fwd ? adj : fwd;

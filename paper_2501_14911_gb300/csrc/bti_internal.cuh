@@ -232,6 +232,15 @@ bool adj_digits_supported(int64_t nf, int64_t R, int64_t Nm, int64_t B);
 void adj_digits_prepare();
 int64_t adj_digits_build(const void* hat, int64_t nf, int64_t R, int64_t Nm, void* planes, int* ex, cudaStream_t s);
 size_t adj_digits_work_bytes(int64_t nf, int64_t R, int64_t B);
+// Forward products of the same tier for B >= 16 (tc_digits.cu): planes of F-hat K-major over
+// (j, re/im), one exponent per (w, i); mhat [B][nf][N_m] -> dhat [B][nf][R] complex FP64.
+size_t fwd_digits_plane_elems(int64_t nf, int64_t R, int64_t Nm);
+size_t fwd_digits_exp_elems(int64_t nf, int64_t R);
+bool fwd_digits_supported(int64_t nf, int64_t R, int64_t Nm, int64_t B);
+int64_t fwd_digits_build(const void* hat, int64_t nf, int64_t R, int64_t Nm, void* planes, int* ex, cudaStream_t s);
+size_t fwd_digits_work_bytes(int64_t nf, int64_t R, int64_t Nm);
+cudaError_t fwd_digits_apply(const void* planes, const int* ex, int64_t nf, int64_t R, int64_t Nm, const void* mhat,
+                             void* dhat, int64_t B, void* work, int* err, cudaStream_t s, int* launches);
 cudaError_t adj_digits_apply(const void* planes, const int* ea, int64_t nf, int64_t R, int64_t Nm, const void* dhat,
                              void* mhat, int64_t B, void* work, int* err, cudaStream_t s, int* launches);
 int axpby_f64(double* y, const double* x, double a, double b, int64_t n, cudaStream_t s);

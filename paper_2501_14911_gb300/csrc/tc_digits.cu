@@ -81,7 +81,7 @@ __device__ __forceinline__ void two_sum_acc(float& Sh, float& Sl, float p) {
   Sh = s;
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t addr, uint32_t (&v)[32]) {
+__device__ __forceinline__ void tmem_ld(uint32_t addr, uint32_t (&v)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
       "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -92,32 +92,41 @@ __device__ __forceinline__ void tmem_ld32(uint32_t addr, uint32_t (&v)[32]) {
       : "r"(addr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+__device__ __forceinline__ void tmem_ld(uint32_t addr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(addr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
 
-// Add one chunk's six exact group sums G_g (TMEM columns 64 g + col0 .. + 31 of this warp's
-// lanes) into the float-pair accumulators: sum_g 2^(-8 g) G_g.  Groups 5, 4, 3 are summed in
-// plain FP32 first: that partial sum is below 1.01 in units where G_0 reaches 2^24, so its
-// rounding stays under 2^-47 of the total; groups 2, 1, 0 and that sum enter by two-sum.
-__device__ __forceinline__ void add_groups(uint32_t taddr, float (&Sh)[32], float (&Sl)[32]) {
-  uint32_t v[32];
-  float low[32];
-  tmem_ld32(taddr + 5 * kKiN, v);
+// Add one chunk's six exact group sums G_g (TMEM columns NC g + the W columns at taddr, this
+// warp's lanes) into the float-pair accumulators: sum_g 2^(-8 g) G_g.  Groups 5, 4, 3 are
+// summed in plain FP32 first: that partial sum is below 1.01 in units where G_0 reaches 2^24,
+// so its rounding stays under 2^-47 of the total; groups 2, 1, 0 and that sum enter by two-sum.
+template <int NC, int W>
+__device__ __forceinline__ void add_groups(uint32_t taddr, float (&Sh)[W], float (&Sl)[W]) {
+  uint32_t v[W];
+  float low[W];
+  tmem_ld(taddr + 5 * NC, v);
 #pragma unroll
-  for (int c = 0; c < 32; ++c) low[c] = __uint_as_float(v[c]) * 0x1p-40f;
-  tmem_ld32(taddr + 4 * kKiN, v);
+  for (int c = 0; c < W; ++c) low[c] = __uint_as_float(v[c]) * 0x1p-40f;
+  tmem_ld(taddr + 4 * NC, v);
 #pragma unroll
-  for (int c = 0; c < 32; ++c) low[c] = fmaf(__uint_as_float(v[c]), 0x1p-32f, low[c]);
-  tmem_ld32(taddr + 3 * kKiN, v);
+  for (int c = 0; c < W; ++c) low[c] = fmaf(__uint_as_float(v[c]), 0x1p-32f, low[c]);
+  tmem_ld(taddr + 3 * NC, v);
 #pragma unroll
-  for (int c = 0; c < 32; ++c) {
+  for (int c = 0; c < W; ++c) {
     low[c] = fmaf(__uint_as_float(v[c]), 0x1p-24f, low[c]);
     two_sum_acc(Sh[c], Sl[c], low[c]);
   }
 #pragma unroll
   for (int g = 2; g >= 0; --g) {
-    tmem_ld32(taddr + g * kKiN, v);
+    tmem_ld(taddr + g * NC, v);
     const float sc = __int_as_float((127 - 8 * g) << 23);  // 2^(-8 g), exact
 #pragma unroll
-    for (int c = 0; c < 32; ++c) two_sum_acc(Sh[c], Sl[c], __uint_as_float(v[c]) * sc);
+    for (int c = 0; c < W; ++c) two_sum_acc(Sh[c], Sl[c], __uint_as_float(v[c]) * sc);
   }
 }
 
@@ -134,18 +143,19 @@ __device__ __forceinline__ void digits6(long long v, int (&d)[kSl]) {
 }
 
 // One A plane s of a 64-column box against the B planes t = 0 .. 5 - s (four K-steps of 16
-// each): group s + t accumulates at TMEM columns 64 (s + t).  The descriptors are built once
+// each): group s + t accumulates at TMEM columns NC (s + t).  The descriptors are built once
 // per plane and advanced by 32 bytes per K-step (2 in the encoded start address) and by one
-// B plane (8 KB) per t, so the issuing thread spends few instructions per MMA.  first: the
-// box opens an accumulation chunk, so K-step 0 of plane 0 overwrites the groups.
+// B plane (NC rows of 128 bytes) per t.  first: the box opens an accumulation chunk, so
+// K-step 0 of plane 0 overwrites the groups.
+template <int NC>
 __device__ __forceinline__ void issue_plane(uint32_t tmem, int s, uint32_t a0, uint32_t b0, uint32_t idesc,
                                             bool first) {
   const uint64_t ad = sdesc(a0), bd = sdesc(b0);
 #pragma unroll
   for (int t = 0; t < kSl; ++t) {
     if (t + s < kSl) {
-      const uint32_t d = tmem + (uint32_t)((s + t) * kKiN);
-      const uint64_t bt = bd + (uint64_t)t * (kKiBPlane >> 4);
+      const uint32_t d = tmem + (uint32_t)((s + t) * NC);
+      const uint64_t bt = bd + (uint64_t)t * (NC * 128 >> 4);
 #pragma unroll
       for (int kk = 0; kk < kKiBox / 16; ++kk) {
         const uint32_t acc = (first && kk == 0) ? 0u : 1u;
@@ -233,10 +243,25 @@ __global__ void slice_digits_kernel(const double* __restrict__ X, int64_t ldx, i
   }
 }
 
+// Shared-memory bytes and TMEM columns of the stream-K kernel with NC B rows per MMA.
+constexpr size_t sk_smem(int NC) { return 1024 + kKiAStages * (size_t)kKiATile + kKiBStages * (size_t)kSl * NC * 128; }
+constexpr uint32_t sk_tmem_cols(int NC) { return NC > 32 ? 512u : 256u; }
+
+// Stream-K digit-plane GEMM: D[m][c] = sum_k A[m][k] B[c][k] for tiles of 128 rows m x NC
+// columns c, the K axis in exact chunks of 128.  Tile T is (w, rg) = (T / NRG, T % NRG) (a
+// problem and a group within it); K-box kbg of tile T sits at TMA row (w KB + kbg) a_blk +
+// rg a_rg of the A planes and (w KB + kbg) b_blk + rg b_rg of the B planes (KB = 2 kpt).
+// Row m's exponent is ea[w ea_w + rg ea_rg + m], column c's eb[w eb_w + rg eb_rg + c]
+// (padding rows and columns hold 0).  A CTA covers units [blockIdx per, + per) of the
+// (tile, chunk) sequence and writes one FP64 partial tile [NC][128] per tile it touches.
+template <int NC>
 __global__ void __launch_bounds__(kKiThreads, 1)
-kinv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-               const int* __restrict__ ea, const int* __restrict__ eb, int64_t n, int nb, double* __restrict__ part,
-               int64_t per, int64_t total, int64_t kpt, int span, int* __restrict__ err) {
+sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+             const int* __restrict__ ea, const int* __restrict__ eb, double* __restrict__ part, int64_t per,
+             int64_t total, int64_t kpt, int span, int NRG, int64_t a_blk, int a_rg, int64_t b_blk, int b_rg,
+             int ea_w, int ea_rg, int eb_w, int eb_rg, int* __restrict__ err) {
+  constexpr uint32_t kBPlane = NC * 128, kBTile = kSl * kBPlane, kCols = sk_tmem_cols(NC);
+  constexpr int W = NC / 2;  // columns per epilogue thread
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   unsigned char* sA = smem;
@@ -251,6 +276,7 @@ kinv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   const int64_t u1 = min(total, u0 + per);
   const int64_t first_tile = u0 / kpt;
   const int nunits = (int)(u1 - u0);
+  const int KB = (int)(kpt * (kKiChunk / kKiBox));
 
   if (tid == 0) {
     for (int s = 0; s < kKiAStages; ++s) {
@@ -269,7 +295,7 @@ kinv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
-                 "r"(kKiTmemCols));
+                 "r"(kCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -279,26 +305,27 @@ kinv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   volatile int* abort_v = &abort_flag;
 
   if (warp == 0) {
-    // ---- TMA producer: per 64-column box, the six right-hand-side planes, then the six
-    // K^{-1} planes of the unit's row tile
+    // ---- TMA producer: per 64-column box, the six B planes, then the six A planes
     if (lane == 0) {
       int na = 0, nbx = 0;
       bool ok = true;
       for (int u = 0; u < nunits && ok; ++u) {
-        const int64_t unit = u0 + u, t = unit / kpt, c = unit - t * kpt;
+        const int64_t unit = u0 + u, T = unit / kpt, c = unit - T * kpt;
+        const int64_t w = T / NRG, rg = T - w * NRG;
         for (int kb = 0; kb < kKiChunk / kKiBox && ok; ++kb, ++nbx) {
-          const int kbg = (int)(c * (kKiChunk / kKiBox) + kb);  // 64-column box index
+          const int64_t blk = w * KB + c * (kKiChunk / kKiBox) + kb;  // (problem, 64-column box)
+          const int arow = (int)(blk * a_blk + rg * a_rg), brow = (int)(blk * b_blk + rg * b_rg);
           const int bs = nbx % kKiBStages;
           if (nbx >= kKiBStages && !mbar_wait(smem_u32(&emptyB[bs]), ((nbx / kKiBStages) - 1) & 1, abort_v)) {
             ok = false;
             break;
           }
           asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&fullB[bs])),
-                       "r"(kKiBTile));
+                       "r"(kBTile));
           for (int q = 0; q < kSl; ++q)
             asm volatile(
                 "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-                ::"r"(smem_u32(sB + bs * kKiBTile + q * kKiBPlane)), "l"(&tmB), "r"(0), "r"(kbg * kKiN), "r"(q),
+                ::"r"(smem_u32(sB + bs * kBTile + q * kBPlane)), "l"(&tmB), "r"(0), "r"(brow), "r"(q),
                 "r"(smem_u32(&fullB[bs]))
                 : "memory");
           for (int s = 0; s < kSl; ++s, ++na) {
@@ -311,9 +338,7 @@ kinv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                          "r"(kKiATile));
             asm volatile(
                 "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-                ::"r"(smem_u32(sA + as * kKiATile)), "l"(&tmA), "r"(0),
-                "r"((int)((int64_t)kbg * kpt * kKiChunk + t * kKiRows)), "r"(s),
-                "r"(smem_u32(&fullA[as]))
+                ::"r"(smem_u32(sA + as * kKiATile)), "l"(&tmA), "r"(0), "r"(arow), "r"(s), "r"(smem_u32(&fullA[as]))
                 : "memory");
           }
         }
@@ -326,9 +351,9 @@ kinv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         mbar_wait(smem_u32(&fullB[i % kKiBStages]), (i / kKiBStages) & 1, &unused);
     }
   } else if (warp == 1) {
-    // ---- MMA issuer: group g = s + t accumulates P_s Q_t^T at TMEM columns 64 g
+    // ---- MMA issuer: group g = s + t accumulates A_s B_t^T at TMEM columns NC g
     if (lane == 0) {
-      const uint32_t idesc = (1u << 4) | ((uint32_t)(kKiN >> 3) << 17) | ((uint32_t)(kKiRows >> 4) << 24);
+      const uint32_t idesc = (1u << 4) | ((uint32_t)(NC >> 3) << 17) | ((uint32_t)(kKiRows >> 4) << 24);
       int na = 0, nbx = 0;
       bool ok = true;
       for (int u = 0; u < nunits && ok; ++u) {
@@ -341,7 +366,7 @@ kinv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             ok = false;
             break;
           }
-          const uint32_t b0 = smem_u32(sB + bs * kKiBTile);
+          const uint32_t b0 = smem_u32(sB + bs * kBTile);
           for (int s = 0; s < kSl; ++s, ++na) {
             const int as = na % kKiAStages;
             if (!mbar_wait(smem_u32(&fullA[as]), (na / kKiAStages) & 1, abort_v)) {
@@ -349,7 +374,7 @@ kinv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
               break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            issue_plane(tmem, s, smem_u32(sA + as * kKiATile), b0, idesc, kb == 0 && s == 0);
+            issue_plane<NC>(tmem, s, smem_u32(sA + as * kKiATile), b0, idesc, kb == 0 && s == 0);
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                          ::"r"(smem_u32(&emptyA[as])) : "memory");
           }
@@ -366,31 +391,31 @@ kinv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                    ::"r"(smem_u32(&mdone)) : "memory");
     }
   } else {
-    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows of the tile) and
-    // right-hand sides 32 h .. + 31, h = (w - 2) / 4
+    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows m of the tile) and
+    // columns W h .. + W - 1, h = (w - 2) / 4
     const int q4 = warp & 3, h = (warp - 2) >> 2;
     const int r = q4 * 32 + lane;
-    float Sh[32], Sl[32];
+    float Sh[W], Sl[W];
 #pragma unroll
-    for (int c = 0; c < 32; ++c) Sh[c] = Sl[c] = 0.f;
+    for (int c = 0; c < W; ++c) Sh[c] = Sl[c] = 0.f;
     for (int u = 0; u < nunits; ++u) {
-      const int64_t unit = u0 + u, t = unit / kpt;
+      const int64_t unit = u0 + u, T = unit / kpt;
       if (!mbar_wait(smem_u32(&accf), u & 1, abort_v)) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
-      add_groups(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(h * 32), Sh, Sl);
+      add_groups<NC, W>(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(h * W), Sh, Sl);
       asm volatile("tcgen05.fence::before_thread_sync;");
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tfree)) : "memory");
-      // last unit of this row tile within the CTA's run: write the partial tile
-      if (u == nunits - 1 || (unit + 1) / kpt != t) {
-        const int64_t row = t * kKiRows + r;
-        const int er = row < n ? ea[row] : 0;
-        double* P = part + ((blockIdx.x * (int64_t)span + (t - first_tile)) * kKiN) * kKiRows;
+      // last unit of this tile within the CTA's run: write the partial tile
+      if (u == nunits - 1 || (unit + 1) / kpt != T) {
+        const int64_t w = T / NRG, rg = T - w * NRG;
+        const int er = ea[w * ea_w + rg * ea_rg + r];
+        const int* ebt = eb + w * eb_w + rg * eb_rg;
+        double* P = part + ((blockIdx.x * (int64_t)span + (T - first_tile)) * NC) * kKiRows;
 #pragma unroll
-        for (int c = 0; c < 32; ++c) {
-          const int b = h * 32 + c;
-          const double val = (b < nb) ? pair_to_double_scaled(Sh[c], Sl[c], er + eb[b] - 14) : 0.0;
-          P[b * kKiRows + r] = val;
+        for (int c = 0; c < W; ++c) {
+          const int col = h * W + c;
+          P[col * kKiRows + r] = pair_to_double_scaled(Sh[c], Sl[c], er + ebt[col] - 14);
           Sh[c] = Sl[c] = 0.f;
         }
       }
@@ -404,7 +429,7 @@ kinv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     if (lane == 0) mbar_wait(smem_u32(&mdone), 0, &unused);
     __syncwarp();
     asm volatile("tcgen05.fence::after_thread_sync;");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kKiTmemCols));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols));
   }
   if (tid == 0 && *abort_v) atomicExch(err, 1);
 }
@@ -416,7 +441,8 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 void kinv_tc_prepare() {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(kinv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kKiSmem);
+    cudaFuncSetAttribute(sk_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sk_smem(64));
+    cudaFuncSetAttribute(sk_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sk_smem(32));
     attr = true;
   }
 }
@@ -433,6 +459,7 @@ size_t kinv_tc_plane_elems(int64_t n) { return (size_t)kSl * kinv_tc_ld(n) * kin
 int64_t kinv_tc_slice(const double* X, int64_t ldx, int64_t rows, int64_t n, int* ex, void* planes_v,
                       int64_t rows_pad, cudaStream_t s) {
   __half* planes = static_cast<__half*>(planes_v);
+  cudaMemsetAsync(ex, 0, sizeof(int) * (size_t)rows_pad, s);  // padding rows: exponent 0
   if (rows > 0) row_exponent_kernel<<<(unsigned)rows, 256, 0, s>>>(X, ldx, n, ex);
   const int64_t ldk = kinv_tc_ld(n);
   const int64_t total = rows_pad * ldk;
@@ -519,8 +546,9 @@ cudaError_t kinv_apply_tc(const void* planes, const int* ea, int64_t n, const do
   for (int64_t q0 = 0; q0 < B; q0 += kKiN) {
     const int64_t nb = B - q0 < kKiN ? B - q0 : kKiN;
     *launches += kinv_tc_slice(D + q0 * n, n, nb, n, eb, bpl, kKiN, s);
-    kinv_tc_kernel<<<(unsigned)p.ctas, kKiThreads, kKiSmem, s>>>(tA, tB, ea, eb, n, (int)nb, part, p.per, p.total,
-                                                                 p.kpt, p.span, err);
+    // tiles: the 128-row tiles of K^{-1} (one problem); A rows kbg ld + 128 t, B rows 64 kbg
+    sk_tc_kernel<64><<<(unsigned)p.ctas, kKiThreads, sk_smem(64), s>>>(
+        tA, tB, ea, eb, part, p.per, p.total, p.kpt, p.span, (int)p.tiles, ld, kKiRows, kKiN, 0, 0, kKiRows, 0, 0, err);
     *launches += 1;
     *launches += kinv_reduce(part, X + q0 * n, n, n, nb, kKiRows, kKiN, p.per, p.kpt, p.span, p.tiles, s);
   }
@@ -747,7 +775,7 @@ adj_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 break;
               }
               asm volatile("tcgen05.fence::after_thread_sync;");
-              issue_plane(tmem, s, smem_u32(sA + as * kKiATile), b0, idesc, kb == 0 && s == 0);
+              issue_plane<kKiN>(tmem, s, smem_u32(sA + as * kKiATile), b0, idesc, kb == 0 && s == 0);
               asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                            ::"r"(smem_u32(&emptyA[as])) : "memory");
             }
@@ -784,7 +812,7 @@ adj_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
-        add_groups(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(h * 32), Sh, Sl);
+        add_groups<kKiN, 32>(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(h * 32), Sh, Sl);
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncwarp();
         if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tfree)) : "memory");
@@ -896,6 +924,231 @@ void adj_digits_prepare() {
     cudaFuncSetAttribute(adj_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kKiSmem);
     attr = true;
   }
+}
+
+
+// ------------------------------------------------------------------ batched forward products
+// The double-FP32 tier's forward product for batches, d-hat_w[b][i] = sum_j F-hat_w[i][j]
+// m-hat_w[b][j], by the same exact digit planes.  Per frequency it is the real GEMM
+// D[n][i] = sum_k V_w[n][k] A_w[i][k] over k = 2 j + c with
+//   A_w[i][2j] = Re F-hat_w[i][j],  A_w[i][2j+1] = Im F-hat_w[i][j]          (formed once)
+//   V_w[2b][.] = (Re m, -Im m),  V_w[2b+1][.] = (Im m, Re m)  at (2j, 2j+1)   (per call)
+// so D[2b][i] = Re d-hat_w[b][i] and D[2b+1][i] = Im d-hat_w[b][i]; one exponent per (w, i) for
+// A and per (w, b) for V.  The long K axis (2 N_m) runs through the stream-K kernel with tiles
+// (w, NC rows i), the 128 vector rows of 64 vectors as the MMA's M, NC = 32 for R <= 32 and
+// 64 otherwise.  Planes: A [S][n_f][K_pad / 64][R_pad][64], V [S][n_f][K_pad / 64][128][64].
+
+namespace {
+
+int fwd_nc(int64_t R) { return R <= 32 ? 32 : 64; }
+
+// A planes: one CTA per (w, i < R_pad)
+__global__ void fwd_planes_kernel(const float4* __restrict__ hat, int64_t nf, int64_t R, int64_t Nm, int64_t Rp,
+                                  int64_t Kp, __half* __restrict__ planes, int* __restrict__ ex) {
+  const int64_t w = blockIdx.x, i = blockIdx.y;
+  const int64_t KB = Kp / kKiBox;
+  const float4* row = hat + (w * R + i) * Nm;
+  double mx = 0.0;
+  if (i < R)
+    for (int64_t j = threadIdx.x; j < Nm; j += blockDim.x) {
+      const float4 v = row[j];
+      mx = fmax(mx, fmax(fabs((double)v.x + (double)v.y), fabs((double)v.z + (double)v.w)));
+    }
+  __shared__ double red[32];
+  __shared__ int es;
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) mx = fmax(mx, red[k]);
+    int e = 0;
+    if (mx > 0.0) frexp(mx, &e);
+    es = e;
+    ex[w * Rp + i] = e;
+  }
+  __syncthreads();
+  const int e = es;
+  const int64_t plane2 = nf * KB * Rp * (kKiBox / 2);
+  __half2* out = reinterpret_cast<__half2*>(planes);
+  for (int64_t j = threadIdx.x; j < Kp / 2; j += blockDim.x) {
+    long long vr = 0, vi = 0;
+    if (i < R && j < Nm) {
+      const float4 v = row[j];
+      vr = __double2ll_rn(scalbn((double)v.x + (double)v.y, 47 - e));
+      vi = __double2ll_rn(scalbn((double)v.z + (double)v.w, 47 - e));
+    }
+    int dr[kSl], di[kSl];
+    digits6(vr, dr);
+    digits6(vi, di);
+    const int64_t o = ((w * KB + j / (kKiBox / 2)) * Rp + i) * (kKiBox / 2) + j % (kKiBox / 2);
+#pragma unroll
+    for (int s = 0; s < kSl; ++s) out[s * plane2 + o] = __halves2half2(__int2half_rn(dr[s]), __int2half_rn(di[s]));
+  }
+}
+
+// V planes of one call (vectors b0 .. b0 + nb - 1): one CTA per (w, b < 64); rows past nb zero
+__global__ void fwd_vec_planes_kernel(const double2* __restrict__ mhat, int64_t nf, int64_t Nm, int64_t b0, int64_t nb,
+                                      int64_t Kp, __half* __restrict__ planes, int* __restrict__ ex) {
+  const int64_t w = blockIdx.x, b = blockIdx.y;
+  const int64_t KB = Kp / kKiBox;
+  const double2* src = mhat + ((b0 + b) * nf + w) * Nm;
+  double mx = 0.0;
+  if (b < nb)
+    for (int64_t j = threadIdx.x; j < Nm; j += blockDim.x) mx = fmax(mx, fmax(fabs(src[j].x), fabs(src[j].y)));
+  __shared__ double red[32];
+  __shared__ int es;
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) mx = fmax(mx, red[k]);
+    int e = 0;
+    if (mx > 0.0) frexp(mx, &e);
+    es = e;
+    ex[w * kKiRows + 2 * b] = e;
+    ex[w * kKiRows + 2 * b + 1] = e;
+  }
+  __syncthreads();
+  const int e = es;
+  const int64_t plane2 = nf * KB * kKiRows * (kKiBox / 2);
+  __half2* out = reinterpret_cast<__half2*>(planes);
+  for (int64_t j = threadIdx.x; j < Kp / 2; j += blockDim.x) {
+    long long vr = 0, vi = 0;
+    if (b < nb && j < Nm) {
+      vr = __double2ll_rn(scalbn(src[j].x, 47 - e));
+      vi = __double2ll_rn(scalbn(src[j].y, 47 - e));
+    }
+    int dr[kSl], di[kSl];
+    digits6(vr, dr);
+    digits6(vi, di);
+    const int64_t o = ((w * KB + j / (kKiBox / 2)) * kKiRows + 2 * b) * (kKiBox / 2) + j % (kKiBox / 2);
+#pragma unroll
+    for (int s = 0; s < kSl; ++s) {
+      out[s * plane2 + o] = __halves2half2(__int2half_rn(dr[s]), __int2half_rn(-di[s]));
+      out[s * plane2 + o + kKiBox / 2] = __halves2half2(__int2half_rn(di[s]), __int2half_rn(dr[s]));
+    }
+  }
+}
+
+// d-hat[b0 + b][w][i] = (D[2b][i], D[2b+1][i]) summed over the CTAs that covered tile (w, i / NC)
+__global__ void fwd_reduce_kernel(const double* __restrict__ part, double2* __restrict__ dhat, int64_t nf, int64_t R,
+                                  int64_t b0, int64_t nb, int NC, int NRG, int64_t per, int64_t kpt, int span) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nb * nf * R) return;
+  const int64_t b = idx / (nf * R), wi = idx - b * nf * R, w = wi / R, i = wi - w * R;
+  const int64_t T = w * NRG + i / NC;
+  const int col = (int)(i % NC);
+  const int64_t c0 = (T * kpt) / per, c1 = ((T + 1) * kpt - 1) / per;
+  double re = 0.0, im = 0.0;
+  for (int64_t c = c0; c <= c1; ++c) {
+    const int64_t slot = T - (c * per) / kpt;
+    const double* P = part + ((c * span + slot) * NC + col) * kKiRows;
+    re += P[2 * b];
+    im += P[2 * b + 1];
+  }
+  dhat[((b0 + b) * nf + w) * R + i] = make_double2(re, im);
+}
+
+struct FwdPlan {
+  int NC, NRG;
+  int64_t Rp, Kp, KB, kpt, total, per, ctas;
+  int span;
+};
+FwdPlan fwd_plan(int64_t nf, int64_t R, int64_t Nm) {
+  FwdPlan p;
+  p.NC = fwd_nc(R);
+  p.Rp = rup(R, p.NC);
+  p.NRG = (int)(p.Rp / p.NC);
+  p.Kp = rup(2 * Nm, kKiChunk);
+  p.KB = p.Kp / kKiBox;
+  p.kpt = p.Kp / kKiChunk;
+  p.total = nf * p.NRG * p.kpt;
+  const int64_t slots = num_sms_tc();
+  p.per = (p.total + slots - 1) / slots;
+  p.ctas = (p.total + p.per - 1) / p.per;
+  p.span = (int)((p.per + p.kpt - 1) / p.kpt + 1);
+  return p;
+}
+
+}  // namespace
+
+size_t fwd_digits_plane_elems(int64_t nf, int64_t R, int64_t Nm) {
+  const FwdPlan p = fwd_plan(nf, R, Nm);
+  return (size_t)kSl * nf * p.KB * p.Rp * kKiBox;
+}
+size_t fwd_digits_exp_elems(int64_t nf, int64_t R) { return (size_t)nf * rup(R, fwd_nc(R)); }
+
+bool fwd_digits_supported(int64_t nf, int64_t R, int64_t Nm, int64_t B) {
+  const int64_t KB = rup(2 * Nm, kKiChunk) / kKiBox;
+  const int64_t rows = nf * KB * (rup(R, fwd_nc(R)) > kKiRows ? rup(R, fwd_nc(R)) : kKiRows);
+  return B >= 16 && rows <= INT32_MAX && tensor_map_encoder() != nullptr;
+}
+
+int64_t fwd_digits_build(const void* hat, int64_t nf, int64_t R, int64_t Nm, void* planes, int* ex, cudaStream_t s) {
+  const FwdPlan p = fwd_plan(nf, R, Nm);
+  fwd_planes_kernel<<<dim3((unsigned)nf, (unsigned)p.Rp), 256, 0, s>>>(
+      static_cast<const float4*>(hat), nf, R, Nm, p.Rp, p.Kp, static_cast<__half*>(planes), ex);
+  return 1;
+}
+
+size_t fwd_digits_work_bytes(int64_t nf, int64_t R, int64_t Nm) {
+  const FwdPlan p = fwd_plan(nf, R, Nm);
+  return 512 + (size_t)kSl * nf * p.KB * kKiRows * kKiBox * 2 + (size_t)nf * kKiRows * sizeof(int) +
+         (size_t)p.ctas * p.span * p.NC * kKiRows * sizeof(double);
+}
+
+cudaError_t fwd_digits_apply(const void* planes, const int* ex, int64_t nf, int64_t R, int64_t Nm, const void* mhat,
+                             void* dhat, int64_t B, void* work, int* err, cudaStream_t s, int* launches) {
+  *launches = 0;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return cudaErrorNotSupported;
+  const FwdPlan p = fwd_plan(nf, R, Nm);
+  unsigned char* wb = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(work) + 255) & ~(uintptr_t)255);
+  __half* vpl = reinterpret_cast<__half*>(wb);
+  const size_t vbytes = (size_t)kSl * nf * p.KB * kKiRows * kKiBox * 2;
+  int* ev = reinterpret_cast<int*>(wb + vbytes);
+  double* part = reinterpret_cast<double*>(
+      (reinterpret_cast<uintptr_t>(wb + vbytes + (size_t)nf * kKiRows * sizeof(int)) + 255) & ~(uintptr_t)255);
+  CUtensorMap tA, tB;
+  const cuuint32_t es[3] = {1, 1, 1};
+  {
+    const cuuint64_t dims[3] = {(cuuint64_t)kKiBox, (cuuint64_t)(nf * p.KB * kKiRows), (cuuint64_t)kSl};
+    const cuuint64_t strides[2] = {(cuuint64_t)(kKiBox * 2), (cuuint64_t)(nf * p.KB * kKiRows * kKiBox * 2)};
+    const cuuint32_t box[3] = {(cuuint32_t)kKiBox, (cuuint32_t)kKiRows, 1};
+    if (enc(&tA, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, vpl, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  {
+    const cuuint64_t dims[3] = {(cuuint64_t)kKiBox, (cuuint64_t)(nf * p.KB * p.Rp), (cuuint64_t)kSl};
+    const cuuint64_t strides[2] = {(cuuint64_t)(kKiBox * 2), (cuuint64_t)(nf * p.KB * p.Rp * kKiBox * 2)};
+    const cuuint32_t box[3] = {(cuuint32_t)kKiBox, (cuuint32_t)p.NC, 1};
+    if (enc(&tB, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<void*>(planes), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  kinv_tc_prepare();
+  for (int64_t b0 = 0; b0 < B; b0 += 64) {
+    const int64_t nb = B - b0 < 64 ? B - b0 : 64;
+    fwd_vec_planes_kernel<<<dim3((unsigned)nf, 64), 256, 0, s>>>(static_cast<const double2*>(mhat), nf, Nm, b0, nb,
+                                                                  p.Kp, vpl, ev);
+    // tiles (w, rg): A rows (w KB + kb) 128, B rows (w KB + kb) R_pad + NC rg
+    if (p.NC == 32)
+      sk_tc_kernel<32><<<(unsigned)p.ctas, kKiThreads, sk_smem(32), s>>>(
+          tA, tB, ev, ex, part, p.per, p.total, p.kpt, p.span, p.NRG, kKiRows, 0, p.Rp, p.NC, kKiRows, 0, (int)p.Rp,
+          p.NC, err);
+    else
+      sk_tc_kernel<64><<<(unsigned)p.ctas, kKiThreads, sk_smem(64), s>>>(
+          tA, tB, ev, ex, part, p.per, p.total, p.kpt, p.span, p.NRG, kKiRows, 0, p.Rp, p.NC, kKiRows, 0, (int)p.Rp,
+          p.NC, err);
+    const int64_t tot = nb * nf * R;
+    fwd_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, static_cast<double2*>(dhat), nf, R, b0, nb,
+                                                                   p.NC, p.NRG, p.per, p.kpt, p.span);
+    *launches += 3;
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace bti

@@ -819,10 +819,12 @@ def test_explicit_inverse_online_solve(B):
         assert relb(host(m2), m_or) < 1e-12
         assert relb(host(q), oracle.qoi_map(Fq, m_or)) < 1e-12
         h.set_digit_planes(bti.OP_G, True)
+        h.set_digit_planes(bti.OP_FQ, True)
         h.online(cuda(d), m2, q)
         assert relb(host(m2), m_or) < 1e-10
         assert relb(host(q), oracle.qoi_map(Fq, m_or)) < 1e-10
         h.set_digit_planes(bti.OP_G, False)
+        h.set_digit_planes(bti.OP_FQ, False)
     torch.cuda.synchronize()
     h.set_stream(torch.cuda.current_stream())
     # a new factor: the stale inverse is not used
@@ -875,27 +877,45 @@ DIGIT_CASES = [
 
 
 @pytest.mark.parametrize("name,Nm,Nd,Nt,B", DIGIT_CASES, ids=[c[0] for c in DIGIT_CASES])
-def test_digit_plane_adjoint_matches_oracle(name, Nm, Nd, Nt, B):
-    """bti_set_digit_planes: the double-FP32 tier's adjoint for B >= 16 on the tensor cores,
-    exact in FP16 digit planes, matches the oracle at the FP64 tolerance and the CUDA-core
-    double-FP32 kernel closely; releasing the planes returns to the CUDA cores."""
+def test_digit_plane_products_match_oracle(name, Nm, Nd, Nt, B):
+    """bti_set_digit_planes: the double-FP32 tier's products for B >= 16 on the tensor cores,
+    exact in FP16 digit planes -- the adjoint (row tiles of N_m, K = 2 N_d) and the forward
+    products F and F_q (stream-K over K = 2 N_m; 32- or 64-row groups of F, 18 of them at
+    N_d = 1,100) -- match the oracle at the FP64 tolerance and the CUDA-core double-FP32
+    kernels closely; releasing the planes returns to the CUDA cores."""
     p = synthetic.small(name, 1, Nm, Nd, Nt, Nq=2)
     F = p.blocks_F()
+    Fq = p.blocks_Fq()
     d = p.vectors_d(B)
-    h = make_handle(F, None, bti.DF64)
+    m = p.vectors_m(B)
+    h = make_handle(F, Fq, bti.DF64)
     h.set_digit_planes(bti.OP_F, True)
-    out = torch.empty((B, Nt, Nm), dtype=torch.float64, device="cuda")
+    h.set_digit_planes(bti.OP_FQ, True)
+    out_m = torch.empty((B, Nt, Nm), dtype=torch.float64, device="cuda")
+    out_d = torch.empty((B, Nt, Nd), dtype=torch.float64, device="cuda")
+    out_q = torch.empty((B, Nt, 2), dtype=torch.float64, device="cuda")
     h.profile_enable(True)
     h.profile_read()
-    h.apply_FT(cuda(d), out)
-    assert h.profile_read()[0]["prod_adj"][1] == 2  # vector planes + the tensor-core kernel
-    ref = oracle.p2o_apply_adjoint(F, d)
-    assert relb(host(out), ref) < 1e-12
+    h.apply_FT(cuda(d), out_m)
+    h.apply_F(cuda(m), out_d)
+    h.apply_Fq(cuda(m), out_q)
+    prof = h.profile_read()[0]
+    ngroups = (B + 63) // 64
+    assert prof["prod_adj"][1] == 2  # vector planes + the tensor-core kernel
+    assert prof["prod_fwd"][1] == 2 * 3 * ngroups  # per 64 vectors: planes, stream-K kernel, sum
+    assert prof["reduce"][1] == 0
+    assert relb(host(out_m), oracle.p2o_apply_adjoint(F, d)) < 1e-12
+    assert relb(host(out_d), oracle.p2o_apply(F, m)) < 1e-12
+    assert relb(host(out_q), oracle.p2o_apply(Fq, m)) < 1e-12
     h.set_digit_planes(bti.OP_F, False)
-    out2 = torch.empty_like(out)
-    h.apply_FT(cuda(d), out2)
-    assert h.profile_read()[0]["prod_adj"][1] == 1
-    assert relb(host(out), host(out2)) < 1e-12
+    h.set_digit_planes(bti.OP_FQ, False)
+    out_m2, out_d2 = torch.empty_like(out_m), torch.empty_like(out_d)
+    h.apply_FT(cuda(d), out_m2)
+    h.apply_F(cuda(m), out_d2)
+    prof = h.profile_read()[0]
+    assert prof["prod_adj"][1] == 1 and prof["prod_fwd"][1] == 1
+    assert relb(host(out_m), host(out_m2)) < 1e-12
+    assert relb(host(out_d), host(out_d2)) < 1e-12
     h.profile_enable(False)
     h.close()
 
