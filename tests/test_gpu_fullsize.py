@@ -163,7 +163,8 @@ def test_batched_double_fp32_dense_without_refinement_full_size():
     target.  Its error is set by the 48-bit arithmetic times kappa(K) ~ 2e2 (1.2e-11
     measured); one refinement step (the dense_df64 form) brings it to the FP64 level.
     The same through the explicit inverse of bti_invert_K in the online graph, whose
-    formation error adds to that of the product (5.0e-11 measured)."""
+    formation error adds to that of the product (5.0e-11 measured), with the inverse, G^*
+    and F_q products on the tensor cores in exact digit planes."""
     p = synthetic.BATCHED
     F = p.blocks_F()
     Fq = p.blocks_Fq()
@@ -185,6 +186,8 @@ def test_batched_double_fp32_dense_without_refinement_full_size():
     # the explicit inverse (bti_invert_K): n = 20,000 gives 157 row tiles of 1,250 k-steps,
     # so stream-K CTAs span two or three row tiles; B = 64 and a 1-vector call
     h.invert_K()
+    h.set_digit_planes(bti.OP_G, True)
+    h.set_digit_planes(bti.OP_FQ, True)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         h.set_stream(stream)
@@ -192,6 +195,10 @@ def test_batched_double_fp32_dense_without_refinement_full_size():
         torch.cuda.synchronize()
         m_inv = m_map.cpu().numpy()
         q_inv = q_map.cpu().numpy()
+        h.online(torch.from_numpy(d_obs).cuda(), m_map, q_map, refine_iters=1)
+        torch.cuda.synchronize()
+        m_ref = m_map.cpu().numpy()
+        q_ref = q_map.cpu().numpy()
     h.set_stream(torch.cuda.current_stream())
     m1 = torch.empty((1, p.Nt, p.Nm), dtype=torch.float64, device="cuda")
     h.infer_map(torch.from_numpy(d_obs[5:6]).cuda(), m1, refine_iters=0)
@@ -207,6 +214,9 @@ def test_batched_double_fp32_dense_without_refinement_full_size():
     assert relb(m_inv, m_or) < 1e-10
     assert relb(q_inv, q_or) < 1e-10
     assert relb(m1, m_or[5:6]) < 1e-10
+    # one refinement step, residual from the digit-plane products: FP64 level
+    assert relb(m_ref, m_or) < 1e-11
+    assert relb(q_ref, q_or) < 1e-11
 
 
 @pytest.mark.parametrize("dense", ["f64", "df64"])
