@@ -613,6 +613,27 @@ def online_block(args, dev, stream):
                 torch.cuda.synchronize()
             out[name]["m_map_plus_q_map_refined_graph_ms"] = e[0].elapsed_time(e[1]) / reps
             out[name]["digit_planes_ms"] = t_planes
+            # q_map = Q d_obs (Eq. (4.14)) with Q in digit planes, in the same online graph
+            with torch.cuda.stream(gs):
+                e[0].record(gs)
+                h.build_Q(with_covariance=False)
+                h.set_online_qoi(True)
+                e[1].record(gs)
+                torch.cuda.synchronize()
+                t_q = e[0].elapsed_time(e[1])
+                for r_it in (0, 1):
+                    for _ in range(2):
+                        h.online(d_obs, m_map, q_map, refine_iters=r_it)
+                    torch.cuda.synchronize()
+                    e[0].record(gs)
+                    for _ in range(reps):
+                        h.online(d_obs, m_map, q_map, refine_iters=r_it)
+                    e[1].record(gs)
+                    torch.cuda.synchronize()
+                    key = "m_map_plus_q_map_via_Q_graph_ms" if r_it == 0 else "m_map_plus_q_map_via_Q_refined_graph_ms"
+                    out[name][key] = e[0].elapsed_time(e[1]) / reps
+                h.set_online_qoi(False)
+            out[name]["build_Q_and_planes_ms"] = t_q
         if inverse:
             h.invert_K(False)
         if tcores:

@@ -364,6 +364,16 @@ bti_status bti_apply_Q(bti_handle h, const double* d_obs, double* q_map, int64_t
  * buffers; either pointer may be NULL. */
 bti_status bti_copy_Q(bti_handle h, double* Q_out, double* cov_out);
 
+/* How bti_online gives q_map.  via_Q = 1: q_map = Q d_obs with the d2q map of bti_build_Q
+ * (Eq. (4.14), the paper's online QoI prediction; requires build_Q, BTI_ERR_STATE
+ * otherwise), and Q is also formed as six FP16 digit planes (12 (N_q N_t^q rounded up to
+ * 128)(N_t N_d rounded up to 128) bytes), so that bti_apply_Q and the online graph apply
+ * it on the tensor cores with FP64-level accuracy while tensor cores are on.  via_Q = 0
+ * (the default): q_map = F_q m_map (push-forward, as bti_predict_qoi); the planes are
+ * released.  A later bti_build_Q makes the planes stale: apply_Q falls back to the dense
+ * GEMM until this is called again.  Synchronises. */
+bti_status bti_set_online_qoi(bti_handle h, int via_Q);
+
 /* q_map = F_q m_map (Eq. (4.2)): m_map [B][N_t][N_m] -> q_map [B][N_t][N_q],
  * both double.  Requires FQ. */
 bti_status bti_predict_qoi(bti_handle h, const double* m_map, double* q_map, int64_t B);

@@ -78,6 +78,7 @@ def lib():
         "bti_build_K_prec": ([vp, i64, ip], st),
         "bti_factor_K": ([vp], st),
         "bti_invert_K": ([vp, ip], st),
+        "bti_set_online_qoi": ([vp, ip], st),
         "bti_set_digit_planes": ([vp, ip, ip], st),
         "bti_copy_K": ([vp, vp], st),
         "bti_infer_map": ([vp, vp, vp, i64, ip], st),
@@ -267,6 +268,10 @@ class Handle:
     def set_digit_planes(self, op, enable=True):
         """Exact tensor-core adjoint products (B >= 16) for a double-FP32 operator."""
         self._check(lib().bti_set_digit_planes(self._h, int(op), int(bool(enable))))
+
+    def set_online_qoi(self, via_Q=True):
+        """online() takes q_map = Q d_obs (needs build_Q; Q on the tensor cores) or F_q m_map."""
+        self._check(lib().bti_set_online_qoi(self._h, int(bool(via_Q))))
 
     def invert_K(self, enable=True):
         """Form K^{-1} from the factor (or release it) so infer_map / online apply it as one product."""

@@ -63,6 +63,11 @@ struct bti_ctx {
   double* Q = nullptr;           // [N_q N_t][N_d N_t] d2q map
   double* covq = nullptr;        // [N_q N_t][N_q N_t] posterior covariance of the QoI
   bool Q_built = false, covq_built = false;
+  int64_t Q_gen = 0;             // incremented by every successful build_Q
+  void* Q_planes = nullptr;      // Q as FP16 digit planes for the tensor cores (bti_set_online_qoi)
+  int* Q_ea = nullptr;           // their row exponents
+  int64_t Qp_gen = -1;           // Q_gen the planes were formed from
+  bool online_via_Q = false;     // bti_online takes q_map = Q d_obs (Eq. (4.14))
   int qstride = 1;               // QoI time grid: every qstride-th step (N_t^q = N_t / qstride)
   double* K = nullptr;           // [n][n], lower triangle: K, then L after factor_K
   double* Linv = nullptr;        // inverses of the factor's diagonal blocks
@@ -583,6 +588,8 @@ bti_status bti_destroy(bti_handle h) {
   dev_freep(h->noise_diag);
   dev_freep(h->K);
   dev_freep(h->Q);
+  dev_free(h->Q_planes);
+  dev_freep(h->Q_ea);
   dev_freep(h->covq);
   dev_freep(h->Linv);
   dev_freep(h->Kinv);
@@ -1150,7 +1157,72 @@ bti_status bti_build_Q(bti_handle h, int with_covariance) {
   st = launched(h, "build_Q");
   if (st != BTI_OK) return st;
   h->Q_built = true;
+  ++h->Q_gen;
   h->covq_built = with_covariance != 0;
+  return BTI_OK;
+}
+
+static bool Q_planes_ready(const bti_ctx* h) { return h->Q_planes && h->Q_built && h->Qp_gen == h->Q_gen; }
+
+// Workspace of apply_Q's tensor-core form (in the dense-solve workspace, after x and r of
+// infer_map so that the online graph can run both).
+static size_t apply_Q_work_elems(const bti_ctx* h, int64_t B) {
+  const int64_t n = h->Nt * h->Nd, nq = (h->Nt / h->qstride) * h->Nq;
+  return (size_t)2 * B * n + rowmat_tc_work_elems(nq, n);
+}
+
+// q[b] = Q d[b] (Eq. (4.14)): by the digit-plane product on the tensor cores when Q's planes
+// are current, else as one dense GEMM (double-FP32 for B > 8 with dense_prec DF64, else FP64)
+static bti_status apply_Q_impl(bti_ctx* h, const double* d_obs, double* q_map, int64_t B) {
+  const int64_t n = h->Nt * h->Nd, nq = (h->Nt / h->qstride) * h->Nq;
+  if (Q_planes_ready(h) && h->tc_enabled) {
+    bti_status st = ensure(h, (void**)&h->wsolve, &h->wsolve_bytes, sizeof(double) * apply_Q_work_elems(h, B),
+                           "solve workspace");
+    if (st != BTI_OK) return st;
+    int64_t nl = 0;
+    cudaError_t e = rowmat_apply_tc(h->Q_planes, h->Q_ea, nq, n, d_obs, B, q_map, nq, h->wsolve + (size_t)2 * B * n,
+                                    h->status + 1, h->stream, &nl);
+    count_dense(h, nl);
+    if (e != cudaSuccess) return cuda_check(h, e, "tensor-core Q product");
+    return launched(h, "apply_Q");
+  }
+  const bool dd = h->dense_prec == BTI_P_DF64 && B > 8;
+  count_dense(h, (dd ? gemm_df64 : gemm_f64)(true, B, nq, n, 1.0, d_obs, n, 0, h->Q, n, 0, 0.0, q_map, nq, 0, 1,
+                                             false, h->stream));
+  return launched(h, "apply_Q");
+}
+
+bti_status bti_set_online_qoi(bti_handle h, int via_Q) {
+  bti_status st = check_handle(h);
+  if (st != BTI_OK) return st;
+  if (via_Q != 0 && via_Q != 1) return fail(h, BTI_ERR_ARG, "set_online_qoi: via_Q must be 0 or 1");
+  drop_online_graph_any(h);
+  cudaStreamSynchronize(h->stream);
+  dev_free(h->Q_planes);
+  dev_freep(h->Q_ea);
+  h->Qp_gen = -1;
+  h->online_via_Q = false;
+  if (!via_Q) return BTI_OK;
+  if (!h->Q_built) return fail(h, BTI_ERR_STATE, "set_online_qoi: Q not built");
+  const int64_t n = h->Nt * h->Nd, nq = (h->Nt / h->qstride) * h->Nq;
+  if (kinv_tc_supported(n) && kinv_tc_supported(nq)) {
+    st = dev_alloc(h, &h->Q_planes, sizeof(uint16_t) * rowmat_tc_plane_elems(nq, n), "alloc Q planes");
+    if (st == BTI_OK) st = dev_alloc(h, (void**)&h->Q_ea, sizeof(int) * (size_t)kinv_tc_ld(nq), "alloc Q exponents");
+    if (st == BTI_OK) {
+      kinv_prepare();
+      kinv_tc_prepare();
+      count_dense(h, kinv_tc_slice(h->Q, n, nq, n, h->Q_ea, h->Q_planes, kinv_tc_ld(nq), h->stream));
+      st = launched(h, "set_online_qoi");
+      if (st == BTI_OK) st = cuda_check(h, cudaStreamSynchronize(h->stream), "set_online_qoi sync");
+    }
+    if (st != BTI_OK) {
+      dev_free(h->Q_planes);
+      dev_freep(h->Q_ea);
+      return st;
+    }
+    h->Qp_gen = h->Q_gen;
+  }
+  h->online_via_Q = true;
   return BTI_OK;
 }
 
@@ -1161,12 +1233,7 @@ bti_status bti_apply_Q(bti_handle h, const double* d_obs, double* q_map, int64_t
   if (!h->Q_built) return fail(h, BTI_ERR_STATE, "apply_Q: Q not built");
   if (B == 0) return BTI_OK;
   if (!d_obs || !q_map) return fail(h, BTI_ERR_ARG, "apply_Q: null pointer");
-  const int64_t n = h->Nt * h->Nd, nq = (h->Nt / h->qstride) * h->Nq;
-  // q[b] = Q d[b]: rows of d against rows of Q
-  const bool dd = h->dense_prec == BTI_P_DF64 && B > 8;
-  count_dense(h, (dd ? gemm_df64 : gemm_f64)(true, B, nq, n, 1.0, d_obs, n, 0, h->Q, n, 0, 0.0, q_map, nq, 0, 1,
-                                             false, h->stream));
-  return launched(h, "apply_Q");
+  return apply_Q_impl(h, d_obs, q_map, B);
 }
 
 bti_status bti_copy_Q(bti_handle h, double* Q_out, double* cov_out) {
@@ -1760,6 +1827,10 @@ bti_status bti_predict_qoi(bti_handle h, const double* m_map, double* q_map, int
 static bti_status reserve_online(bti_ctx* h, int64_t B) {
   bti_status st = reserve_solve(h, B);
   if (st != BTI_OK) return st;
+  if (h->online_via_Q && Q_planes_ready(h)) {
+    st = ensure(h, (void**)&h->wsolve, &h->wsolve_bytes, sizeof(double) * apply_Q_work_elems(h, B), "solve workspace");
+    if (st != BTI_OK) return st;
+  }
   // spectral workspace: the larger of an adjoint (G*) and a forward (F, F_q) product
   const int64_t nf = h->nf, Nm = h->Nm;
   size_t adj = 16 * ((size_t)B * nf * Nm + (size_t)B * nf * h->Nd);
@@ -1784,7 +1855,8 @@ bti_status bti_online(bti_handle h, const double* d_obs, double* m_map, double* 
   if (!d_obs || !m_map) return fail(h, BTI_ERR_ARG, "online: null pointer");
   if (!h->K_factored) return fail(h, BTI_ERR_STATE, "online: K not factored");
   if (!h->op[BTI_OP_G].set) return fail(h, BTI_ERR_STATE, "online: G blocks not set");
-  if (q_map && !h->op[BTI_OP_FQ].set) return fail(h, BTI_ERR_STATE, "online: F_q blocks not set");
+  if (q_map && !h->online_via_Q && !h->op[BTI_OP_FQ].set) return fail(h, BTI_ERR_STATE, "online: F_q blocks not set");
+  if (q_map && h->online_via_Q && !h->Q_built) return fail(h, BTI_ERR_STATE, "online: q_map via Q but Q not built");
   if (!h->stream) return fail(h, BTI_ERR_STATE, "online: graph capture needs a non-default stream");
   const bool same = h->online_exec && h->og_d == d_obs && h->og_m == m_map && h->og_q == q_map && h->og_B == B &&
                     h->og_refine == refine_iters && h->og_stream == h->stream;
@@ -1800,7 +1872,9 @@ bti_status bti_online(bti_handle h, const double* d_obs, double* m_map, double* 
       return st;
     }
     bti_status run = infer_map_impl(h, d_obs, m_map, B, refine_iters);
-    if (run == BTI_OK && q_map) run = apply_op(h, BTI_OP_FQ, false, m_map, q_map, B, BTI_P_F64, "online F_q");
+    if (run == BTI_OK && q_map)
+      run = h->online_via_Q ? apply_Q_impl(h, d_obs, q_map, B)
+                            : apply_op(h, BTI_OP_FQ, false, m_map, q_map, B, BTI_P_F64, "online F_q");
     cudaGraph_t graph = nullptr;
     cudaError_t ee = cudaStreamEndCapture(h->stream, &graph);
     h->prof_on = prof;

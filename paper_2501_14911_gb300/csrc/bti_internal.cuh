@@ -222,6 +222,12 @@ int64_t kinv_tc_slice(const double* X, int64_t ldx, int64_t rows, int64_t n, int
                       int64_t rows_pad, cudaStream_t s);
 cudaError_t kinv_apply_tc(const void* planes, const int* ea, int64_t n, const double* D, int64_t B, double* X,
                           double* work, int* err, cudaStream_t s, int64_t* launches);
+// The same for any row-major M x n matrix (planes of kinv_tc_slice with rows_pad =
+// kinv_tc_ld(M)): X [B][ldx] rows = matrix D[b] (the d2q map Q of Eq. (4.14)).
+size_t rowmat_tc_plane_elems(int64_t M, int64_t n);
+size_t rowmat_tc_work_elems(int64_t M, int64_t n);
+cudaError_t rowmat_apply_tc(const void* planes, const int* ea, int64_t M, int64_t n, const double* D, int64_t B,
+                            double* X, int64_t ldx, double* work, int* err, cudaStream_t s, int64_t* launches);
 // Double-FP32 tier's adjoint product for B >= 16 on the tensor cores (tc_digits.cu): digit
 // planes of conj(F-hat)^T, K-major over (i, re/im), one exponent per (w, j); built once from
 // the float-quad blocks.  adj_digits_apply: dhat [B][nf][R], mhat [B][nf][N_m] complex FP64;

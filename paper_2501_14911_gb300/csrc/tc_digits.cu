@@ -142,10 +142,29 @@ __device__ __forceinline__ void digits6(long long v, int (&d)[kSl]) {
   d[0] = (int)v;  // |v| <= 128 here
 }
 
+// tcgen05.mma / tcgen05.commit issued by one elected lane of a warp that runs the issuing
+// loop in step, so descriptors and addresses stay warp-uniform.
+__device__ __forceinline__ void mma_elect(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p, e;\nsetp.ne.b32 p, %4, 0;\nelect.sync _|e, 0xffffffff;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void commit_elect(uint32_t bar) {
+  asm volatile(
+      "{\n.reg .pred e;\nelect.sync _|e, 0xffffffff;\n"
+      "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n"
+      ::"r"(bar) : "memory");
+}
+// bounded wait taken by a whole warp: true only if every lane saw the phase complete
+__device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  return __all_sync(0xffffffffu, mbar_wait(bar, parity, abort_flag));
+}
+
 // One A plane s of a 64-column box against the B planes t = 0 .. 5 - s (four K-steps of 16
-// each): group s + t accumulates at TMEM columns NC (s + t).  The descriptors are built once
-// per plane and advanced by 32 bytes per K-step (2 in the encoded start address) and by one
-// B plane (NC rows of 128 bytes) per t.  first: the box opens an accumulation chunk, so
+// each): group s + t accumulates at TMEM columns NC (s + t).  Called by a whole warp; the
+// descriptors are built once per plane and advanced by 32 bytes per K-step (2 in the encoded
+// start address) and by one B plane (NC rows of 128 bytes) per t.  first: the box opens an accumulation chunk, so
 // K-step 0 of plane 0 overwrites the groups.
 template <int NC>
 __device__ __forceinline__ void issue_plane(uint32_t tmem, int s, uint32_t a0, uint32_t b0, uint32_t idesc,
@@ -158,10 +177,7 @@ __device__ __forceinline__ void issue_plane(uint32_t tmem, int s, uint32_t a0, u
       const uint64_t bt = bd + (uint64_t)t * (NC * 128 >> 4);
 #pragma unroll
       for (int kk = 0; kk < kKiBox / 16; ++kk) {
-        const uint32_t acc = (first && kk == 0) ? 0u : 1u;
-        asm volatile(
-            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-            ::"r"(d), "l"(ad + 2 * kk), "l"(bt + 2 * kk), "r"(idesc), "r"(acc));
+        mma_elect(d, ad + 2 * kk, bt + 2 * kk, idesc, (first && kk == 0) ? 0u : 1u);
       }
     }
   }
@@ -351,44 +367,41 @@ sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
         mbar_wait(smem_u32(&fullB[i % kKiBStages]), (i / kKiBStages) & 1, &unused);
     }
   } else if (warp == 1) {
-    // ---- MMA issuer: group g = s + t accumulates A_s B_t^T at TMEM columns NC g
-    if (lane == 0) {
+    // ---- MMA issuer (the whole warp, one elected lane issues): group g = s + t accumulates
+    // A_s B_t^T at TMEM columns NC g
+    {
       const uint32_t idesc = (1u << 4) | ((uint32_t)(NC >> 3) << 17) | ((uint32_t)(kKiRows >> 4) << 24);
       int na = 0, nbx = 0;
       bool ok = true;
       for (int u = 0; u < nunits && ok; ++u) {
         // the epilogue has drained the previous chunk's groups
-        if (u > 0 && !mbar_wait(smem_u32(&tfree), (u - 1) & 1, abort_v)) break;
+        if (u > 0 && !mbar_wait_warp(smem_u32(&tfree), (u - 1) & 1, abort_v)) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
         for (int kb = 0; kb < kKiChunk / kKiBox && ok; ++kb, ++nbx) {
           const int bs = nbx % kKiBStages;
-          if (!mbar_wait(smem_u32(&fullB[bs]), (nbx / kKiBStages) & 1, abort_v)) {
+          if (!mbar_wait_warp(smem_u32(&fullB[bs]), (nbx / kKiBStages) & 1, abort_v)) {
             ok = false;
             break;
           }
           const uint32_t b0 = smem_u32(sB + bs * kBTile);
           for (int s = 0; s < kSl; ++s, ++na) {
             const int as = na % kKiAStages;
-            if (!mbar_wait(smem_u32(&fullA[as]), (na / kKiAStages) & 1, abort_v)) {
+            if (!mbar_wait_warp(smem_u32(&fullA[as]), (na / kKiAStages) & 1, abort_v)) {
               ok = false;
               break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
             issue_plane<NC>(tmem, s, smem_u32(sA + as * kKiATile), b0, idesc, kb == 0 && s == 0);
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         ::"r"(smem_u32(&emptyA[as])) : "memory");
+            commit_elect(smem_u32(&emptyA[as]));
           }
           if (!ok) break;
-          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                       ::"r"(smem_u32(&emptyB[bs])) : "memory");
+          commit_elect(smem_u32(&emptyB[bs]));
         }
         if (!ok) break;
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                     ::"r"(smem_u32(&accf)) : "memory");
+        commit_elect(smem_u32(&accf));
       }
       // completion of every MMA issued above (waited on before the tensor memory is freed)
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                   ::"r"(smem_u32(&mdone)) : "memory");
+      commit_elect(smem_u32(&mdone));
     }
   } else {
     // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows m of the tile) and
@@ -484,11 +497,11 @@ int num_sms_tc() {
   }
   return v;
 }
-KiPlan ki_plan(int64_t n) {
+// M x n matrix (rows padded to Mp, columns to ld, both multiples of 128)
+KiPlan ki_plan(int64_t M, int64_t n) {
   KiPlan p;
-  const int64_t ld = kinv_tc_ld(n);
-  p.tiles = ld / kKiRows;
-  p.kpt = ld / kKiChunk;
+  p.tiles = kinv_tc_ld(M) / kKiRows;
+  p.kpt = kinv_tc_ld(n) / kKiChunk;
   p.total = p.tiles * p.kpt;
   const int64_t slots = num_sms_tc();
   p.per = (p.total + slots - 1) / slots;
@@ -498,33 +511,36 @@ KiPlan ki_plan(int64_t n) {
 }
 }  // namespace
 
-size_t kinv_tc_work_elems(int64_t n) {
+size_t rowmat_tc_plane_elems(int64_t M, int64_t n) { return (size_t)kSl * kinv_tc_ld(M) * kinv_tc_ld(n); }
+
+size_t rowmat_tc_work_elems(int64_t M, int64_t n) {
   const int64_t ld = kinv_tc_ld(n);
-  const KiPlan p = ki_plan(n);
+  const KiPlan p = ki_plan(M, n);
   // right-hand-side planes (FP16, counted in doubles) + exponents + partials
   const size_t planes = ((size_t)kSl * kKiN * ld * 2 + 7) / 8;
   return 32 + planes + kKiN + (size_t)p.ctas * p.span * kKiN * kKiRows;  // 32: alignment slack
 }
+size_t kinv_tc_work_elems(int64_t n) { return rowmat_tc_work_elems(n, n); }
 
 int kinv_reduce(const double* part, double* X, int64_t ldx, int64_t n, int64_t nb, int BM, int BR, int64_t per,
                 int64_t kpt, int span, int64_t tiles, cudaStream_t s);
 
-cudaError_t kinv_apply_tc(const void* planes, const int* ea, int64_t n, const double* D, int64_t B, double* X,
-                          double* work, int* err, cudaStream_t s, int64_t* launches) {
+cudaError_t rowmat_apply_tc(const void* planes, const int* ea, int64_t M, int64_t n, const double* D, int64_t B,
+                            double* X, int64_t ldx, double* work, int* err, cudaStream_t s, int64_t* launches) {
   work = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(work) + 255) & ~(uintptr_t)255);
   *launches = 0;
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return cudaErrorNotSupported;
-  const int64_t ld = kinv_tc_ld(n);
-  const KiPlan p = ki_plan(n);
+  const int64_t ld = kinv_tc_ld(n), Mp = kinv_tc_ld(M);
+  const KiPlan p = ki_plan(M, n);
   __half* bpl = reinterpret_cast<__half*>(work);
   int* eb = reinterpret_cast<int*>(work + ((size_t)kSl * kKiN * ld * 2 + 7) / 8);
   double* part = work + ((size_t)kSl * kKiN * ld * 2 + 7) / 8 + kKiN;
   CUtensorMap tA, tB;
   {
-    // tiled planes: (64 columns, box-major rows kb * ld + i, plane)
-    const cuuint64_t dims[3] = {(cuuint64_t)kKiBox, (cuuint64_t)(ld / kKiBox * ld), (cuuint64_t)kSl};
-    const cuuint64_t strides[2] = {(cuuint64_t)(kKiBox * 2), (cuuint64_t)(ld * ld * 2)};
+    // tiled planes: (64 columns, box-major rows kb * Mp + i, plane)
+    const cuuint64_t dims[3] = {(cuuint64_t)kKiBox, (cuuint64_t)(ld / kKiBox * Mp), (cuuint64_t)kSl};
+    const cuuint64_t strides[2] = {(cuuint64_t)(kKiBox * 2), (cuuint64_t)(Mp * ld * 2)};
     const cuuint32_t box[3] = {(cuuint32_t)kKiBox, (cuuint32_t)kKiRows, 1};
     const cuuint32_t es[3] = {1, 1, 1};
     if (enc(&tA, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<void*>(planes), dims, strides, box, es,
@@ -546,13 +562,18 @@ cudaError_t kinv_apply_tc(const void* planes, const int* ea, int64_t n, const do
   for (int64_t q0 = 0; q0 < B; q0 += kKiN) {
     const int64_t nb = B - q0 < kKiN ? B - q0 : kKiN;
     *launches += kinv_tc_slice(D + q0 * n, n, nb, n, eb, bpl, kKiN, s);
-    // tiles: the 128-row tiles of K^{-1} (one problem); A rows kbg ld + 128 t, B rows 64 kbg
+    // tiles: the 128-row tiles of the matrix (one problem); A rows kbg Mp + 128 t, B rows 64 kbg
     sk_tc_kernel<64><<<(unsigned)p.ctas, kKiThreads, sk_smem(64), s>>>(
-        tA, tB, ea, eb, part, p.per, p.total, p.kpt, p.span, (int)p.tiles, ld, kKiRows, kKiN, 0, 0, kKiRows, 0, 0, err);
+        tA, tB, ea, eb, part, p.per, p.total, p.kpt, p.span, (int)p.tiles, Mp, kKiRows, kKiN, 0, 0, kKiRows, 0, 0, err);
     *launches += 1;
-    *launches += kinv_reduce(part, X + q0 * n, n, n, nb, kKiRows, kKiN, p.per, p.kpt, p.span, p.tiles, s);
+    *launches += kinv_reduce(part, X + q0 * ldx, ldx, M, nb, kKiRows, kKiN, p.per, p.kpt, p.span, p.tiles, s);
   }
   return cudaGetLastError();
+}
+
+cudaError_t kinv_apply_tc(const void* planes, const int* ea, int64_t n, const double* D, int64_t B, double* X,
+                          double* work, int* err, cudaStream_t s, int64_t* launches) {
+  return rowmat_apply_tc(planes, ea, n, n, D, B, X, n, work, err, s, launches);
 }
 
 
@@ -749,47 +770,44 @@ adj_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         mbar_wait(smem_u32(&fullB[i % kKiBStages]), (i / kKiBStages) & 1, &unused);
     }
   } else if (warp == 1) {
-    // ---- MMA issuer; one accumulation chunk = kBoxes boxes, chunk counter cc across units
-    if (lane == 0) {
+    // ---- MMA issuer (the whole warp, one elected lane issues); one accumulation chunk = kBoxes
+    // boxes, chunk counter cc across units
+    {
       const uint32_t idesc = (1u << 4) | ((uint32_t)(kKiN >> 3) << 17) | ((uint32_t)(kKiRows >> 4) << 24);
       int na = 0, nbx = 0, cc = 0;
       bool ok = true;
       for (int u = 0; u < nunits && ok; ++u) {
         for (int c = 0; c < nchunk && ok; ++c, ++cc) {
-          if (cc > 0 && !mbar_wait(smem_u32(&tfree), (cc - 1) & 1, abort_v)) {
+          if (cc > 0 && !mbar_wait_warp(smem_u32(&tfree), (cc - 1) & 1, abort_v)) {
             ok = false;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;");
           for (int kb = 0; kb < kBoxes && ok; ++kb, ++nbx) {
             const int bs = nbx % kKiBStages;
-            if (!mbar_wait(smem_u32(&fullB[bs]), (nbx / kKiBStages) & 1, abort_v)) {
+            if (!mbar_wait_warp(smem_u32(&fullB[bs]), (nbx / kKiBStages) & 1, abort_v)) {
               ok = false;
               break;
             }
             const uint32_t b0 = smem_u32(sB + bs * kKiBTile);
             for (int s = 0; s < kSl; ++s, ++na) {
               const int as = na % kKiAStages;
-              if (!mbar_wait(smem_u32(&fullA[as]), (na / kKiAStages) & 1, abort_v)) {
+              if (!mbar_wait_warp(smem_u32(&fullA[as]), (na / kKiAStages) & 1, abort_v)) {
                 ok = false;
                 break;
               }
               asm volatile("tcgen05.fence::after_thread_sync;");
               issue_plane<kKiN>(tmem, s, smem_u32(sA + as * kKiATile), b0, idesc, kb == 0 && s == 0);
-              asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                           ::"r"(smem_u32(&emptyA[as])) : "memory");
+              commit_elect(smem_u32(&emptyA[as]));
             }
             if (!ok) break;
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         ::"r"(smem_u32(&emptyB[bs])) : "memory");
+            commit_elect(smem_u32(&emptyB[bs]));
           }
           if (!ok) break;
-          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                       ::"r"(smem_u32(&accf)) : "memory");
+          commit_elect(smem_u32(&accf));
         }
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                   ::"r"(smem_u32(&mdone)) : "memory");
+      commit_elect(smem_u32(&mdone));
     }
   } else {
     // ---- epilogue: TMEM lanes 32 (w % 4) .. + 31 = rows j of the tile, columns 32 h .. + 31

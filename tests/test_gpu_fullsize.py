@@ -101,6 +101,11 @@ def test_batched_inversion_full_size():
     q_d2q = torch.empty_like(q_map)
     h.apply_Q(torch.from_numpy(d_obs).cuda(), q_d2q)
     q_d2q = q_d2q.cpu().numpy()
+    # the same through Q's digit planes on the tensor cores (6,400 x 20,000)
+    h.set_online_qoi(True)
+    q_tc = torch.empty_like(q_map)
+    h.apply_Q(torch.from_numpy(d_obs).cuda(), q_tc)
+    q_tc = q_tc.cpu().numpy()
     h.close()
 
     Cs = oracle.se_covariance(p.gx, p.gy, p.ell, p.sigma_p)
@@ -128,6 +133,7 @@ def test_batched_inversion_full_size():
     q_or = oracle.qoi_map(Fq, m_or)
     assert relb(q_gpu, q_or) < 1e-11
     assert relb(q_d2q, q_or) < 1e-11
+    assert relb(q_tc, q_or) < 1e-10
 
 
 def test_diff_gradient_full_size():

@@ -540,6 +540,57 @@ def test_d2q_map_and_qoi_covariance(dense):
     h.close()
 
 
+@pytest.mark.parametrize("B", [3, 70], ids=["b3", "b70"])
+def test_online_qoi_via_d2q_map_on_tensor_cores(B):
+    """bti_set_online_qoi: q_map = Q d_obs (Eq. (4.14)) with Q in FP16 digit planes on the
+    tensor cores (the stream-K product of the explicit inverse, rectangular here: N_q N_t =
+    256 rows against N_d N_t = 512 columns), in bti_apply_Q and in the online graph; the
+    dense-GEMM form with tensor cores off; errors for a missing Q."""
+    p, F, Fq, G, _ = tiny_problem()
+    h = make_handle(F, Fq, bti.DF64)
+    h.set_prior_se_grid(p.gx, p.gy, p.ell, p.sigma_p, bti.DF64)
+    h.set_noise(p.sigma2)
+    h.set_dense_precision(bti.DF64)
+    h.build_K()
+    h.factor_K()
+    with pytest.raises(bti.BtiError) as e:
+        h.set_online_qoi(True)
+    assert e.value.status == 3
+    h.build_Q()
+    h.set_online_qoi(True)
+    d = p.vectors_d(B)
+    m_or = oracle.map_point(F, G, p.sigma2, d)
+    q_or = oracle.qoi_map(Fq, m_or)
+    q = torch.empty((B, p.Nt, p.Nq), dtype=torch.float64, device="cuda")
+    h.profile_enable(True)
+    h.profile_read()
+    h.apply_Q(cuda(d), q)
+    n_tc = h.profile_read()[0]["dense"][1]
+    assert n_tc == 4 * ((B + 63) // 64)  # per 64 vectors: their planes (2 kernels), MMAs, sum
+    assert relb(host(q), q_or) < 1e-10
+    h.set_tensor_cores(False)
+    q2 = torch.empty_like(q)
+    h.apply_Q(cuda(d), q2)
+    assert h.profile_read()[0]["dense"][1] == 1
+    h.set_tensor_cores(True)
+    assert relb(host(q), host(q2)) < 1e-10
+    h.profile_enable(False)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        h.set_stream(stream)
+        m = torch.empty((B, p.Nt, p.Nm), dtype=torch.float64, device="cuda")
+        q3 = torch.empty_like(q)
+        h.online(cuda(d), m, q3, refine_iters=1)
+        assert relb(host(m), m_or) < 1e-12
+        assert relb(host(q3), q_or) < 1e-10
+        h.set_online_qoi(False)
+        h.online(cuda(d), m, q3, refine_iters=1)  # back to the push-forward F_q m_map
+        assert relb(host(q3), q_or) < 1e-12
+    torch.cuda.synchronize()
+    h.set_stream(torch.cuda.current_stream())
+    h.close()
+
+
 def test_posterior_covariance_actions_and_prior_mean():
     """Gamma_prior v, Gamma_post(m) v (Eq. (4.7)), pointwise posterior variances from unit
     vectors, and m_map with a nonzero prior mean (Eq. (4.13) with Eq. (4.8))."""
