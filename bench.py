@@ -45,10 +45,12 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-workload matrix-free solve block")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--case", choices=["sweep", "small"], default="sweep",
+    ap.add_argument("--case", choices=["sweep", "small", "digits_small"], default="sweep",
                     help="small: the sweep shape with N_m = 4096 and 16 vectors (2.2 GB of FP64 spectral "
                          "blocks, still far above L2) for ncu captures; implies --no-online, "
-                         "--no-mixed, --no-cpu-baseline and --no-e2e")
+                         "--no-mixed, --no-cpu-baseline and --no-e2e.  digits_small: the batched "
+                         "workload's shapes at N_t = 50 with 64 vectors, timing the tensor-core digit-plane "
+                         "products (adjoint, forward, explicit inverse) once each, for ncu captures")
     a = ap.parse_args()
     if a.case == "small":
         a.no_online = a.no_mixed = a.no_cpu_baseline = a.no_e2e = True
@@ -740,10 +742,55 @@ def mixed_block(args, dev, stream):
     return out
 
 
+def digits_small(args):
+    """The digit-plane tensor-core products at a small size for ncu captures: the batched
+    workload's shapes (N_m = 4,096, N_d = 100) with N_t = 50 (n_f = 51, n = 5,000) and 64
+    vectors; operator planes of 0.6 GB each, above L2.  Prints one JSON line of times."""
+    import torch
+
+    import paper_2501_14911_gb300 as bti
+    from paper_2501_14911_gb300 import synthetic
+
+    dev = torch.device("cuda", 0)
+    p = synthetic.small("digits_small_Nm4096_Nd100_Nt50", 64, 64, 100, 50, Nq=32)
+    h = bti.Handle(p.Nm, p.Nd, p.Nq, p.Nt, device=dev)
+    h.set_blocks(bti.OP_F, torch.from_numpy(p.blocks_F()).to(dev), bti.DF64)
+    h.set_prior_se_grid(p.gx, p.gy, p.ell, p.sigma_p, bti.DF64)
+    h.set_noise(p.sigma2)
+    h.set_dense_precision(bti.DF64)
+    h.build_K(512)
+    h.factor_K()
+    h.invert_K()
+    h.set_digit_planes(bti.OP_F, True)
+    B = 64
+    g = torch.Generator(device="cpu").manual_seed(5)
+    d = torch.randn((B, p.Nt, p.Nd), generator=g, dtype=torch.float64).to(dev)
+    m = torch.randn((B, p.Nt, p.Nm), generator=g, dtype=torch.float64).to(dev)
+    x = torch.empty_like(d)
+    calls = {"adjoint_FT": lambda: h.apply_FT(d, m), "forward_F": lambda: h.apply_F(m, x),
+             "infer_map_explicit_inverse": lambda: h.infer_map(d, m)}
+    for fn in calls.values():
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"case": p.name, "vectors": B}
+    for name, fn in calls.items():
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        out[name + "_ms"] = e0.elapsed_time(e1)
+    h.close()
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.case == "digits_small":
+        return digits_small(args)
     return run_ours(args)
 
 
