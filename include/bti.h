@@ -267,11 +267,13 @@ bti_status bti_set_digit_planes(bti_handle h, bti_op op, int enable);
  * gives up inside the tensor-core kernel is reported by bti_sync as BTI_ERR_TIMEOUT. */
 bti_status bti_set_tensor_cores(bti_handle h, int on);
 
-/* Failure-handling test hook: while stage >= 0, the tensor-core forward product withholds
- * the F-hat tile of that pipeline stage in every CTA, so its bounded waits (about a
- * second) run out; the kernel then stops, drains what it issued, frees its tensor memory
- * and sets the device status word that bti_sync reports as BTI_ERR_TIMEOUT.  The handle
- * and the CUDA context stay usable.  -1 (the default) turns it off. */
+/* Failure-handling test hook: while stage >= 0, the tensor-core kernels that stream an
+ * operand by TMA (the FP16 tier's forward product, and the digit-plane products of
+ * bti_set_digit_planes, bti_invert_K and bti_set_online_qoi) withhold that pipeline stage's
+ * tile in every CTA, so their bounded waits (about a second) run out; the kernel then
+ * stops, drains what it issued, frees its tensor memory and sets the device status word
+ * that bti_sync reports as BTI_ERR_TIMEOUT.  The handle and the CUDA context stay usable.
+ * -1 (the default) turns it off. */
 bti_status bti_test_withhold_tc_stage(bti_handle h, int stage);
 
 /* ---------------------------------------------------------------- matrix-free solve

@@ -372,7 +372,8 @@ bti_status apply_fwd_t(bti_ctx* h, const OpStore& o, const void* in, void* out, 
     cudaError_t e;
     {
       ProfScope ps(h, BTI_K_PROD_FWD);  // vector planes, the MMA kernel and its fixed-order sum
-      e = fwd_digits_apply(o.dig_f, o.dig_f_ex, nf, R, Nm, mhat, dhat, B, (char*)h->ws + base, h->status + 1, s, &nl);
+      e = fwd_digits_apply(o.dig_f, o.dig_f_ex, nf, R, Nm, mhat, dhat, B, (char*)h->ws + base, h->status + 1, s, &nl,
+                           h->tc_drop_stage);
     }
     h->prof_count[BTI_K_PROD_FWD] += nl - 1;
     if (e != cudaSuccess) return cuda_check(h, e, "tensor-core forward product (digit planes)");
@@ -422,7 +423,8 @@ bti_status apply_adj_t(bti_ctx* h, const OpStore& o, const void* in, void* out, 
     cudaError_t e;
     {
       ProfScope ps(h, BTI_K_PROD_ADJ);
-      e = adj_digits_apply(o.dig, o.dig_ex, nf, R, Nm, dhat, mhat, B, (char*)h->ws + base, h->status + 1, s, &nl);
+      e = adj_digits_apply(o.dig, o.dig_ex, nf, R, Nm, dhat, mhat, B, (char*)h->ws + base, h->status + 1, s, &nl,
+                           h->tc_drop_stage);
     }
     h->prof_count[BTI_K_PROD_ADJ] += nl - 1;
     if (e != cudaSuccess) return cuda_check(h, e, "tensor-core adjoint product (digit planes)");
@@ -1025,7 +1027,7 @@ static bti_status infer_map_impl(bti_handle h, const double* d_obs, double* m_ma
     if (inv_tc) {
       int64_t nl = 0;
       cudaError_t e = kinv_apply_tc(h->kinv_planes, h->kinv_ea, n, v, B, xo, work + (size_t)B * n, h->status + 1, s,
-                                    &nl);
+                                    &nl, h->tc_drop_stage);
       if (e != cudaSuccess) tc_err = e;
       return nl;
     }
@@ -1181,7 +1183,7 @@ static bti_status apply_Q_impl(bti_ctx* h, const double* d_obs, double* q_map, i
     if (st != BTI_OK) return st;
     int64_t nl = 0;
     cudaError_t e = rowmat_apply_tc(h->Q_planes, h->Q_ea, nq, n, d_obs, B, q_map, nq, h->wsolve + (size_t)2 * B * n,
-                                    h->status + 1, h->stream, &nl);
+                                    h->status + 1, h->stream, &nl, h->tc_drop_stage);
     count_dense(h, nl);
     if (e != cudaSuccess) return cuda_check(h, e, "tensor-core Q product");
     return launched(h, "apply_Q");

@@ -221,13 +221,14 @@ size_t kinv_tc_work_elems(int64_t n);
 int64_t kinv_tc_slice(const double* X, int64_t ldx, int64_t rows, int64_t n, int* ex, void* planes,
                       int64_t rows_pad, cudaStream_t s);
 cudaError_t kinv_apply_tc(const void* planes, const int* ea, int64_t n, const double* D, int64_t B, double* X,
-                          double* work, int* err, cudaStream_t s, int64_t* launches);
+                          double* work, int* err, cudaStream_t s, int64_t* launches, int drop_stage = -1);
 // The same for any row-major M x n matrix (planes of kinv_tc_slice with rows_pad =
 // kinv_tc_ld(M)): X [B][ldx] rows = matrix D[b] (the d2q map Q of Eq. (4.14)).
 size_t rowmat_tc_plane_elems(int64_t M, int64_t n);
 size_t rowmat_tc_work_elems(int64_t M, int64_t n);
 cudaError_t rowmat_apply_tc(const void* planes, const int* ea, int64_t M, int64_t n, const double* D, int64_t B,
-                            double* X, int64_t ldx, double* work, int* err, cudaStream_t s, int64_t* launches);
+                            double* X, int64_t ldx, double* work, int* err, cudaStream_t s, int64_t* launches,
+                            int drop_stage = -1);
 // Double-FP32 tier's adjoint product for B >= 16 on the tensor cores (tc_digits.cu): digit
 // planes of conj(F-hat)^T, K-major over (i, re/im), one exponent per (w, j); built once from
 // the float-quad blocks.  adj_digits_apply: dhat [B][nf][R], mhat [B][nf][N_m] complex FP64;
@@ -246,9 +247,11 @@ bool fwd_digits_supported(int64_t nf, int64_t R, int64_t Nm, int64_t B);
 int64_t fwd_digits_build(const void* hat, int64_t nf, int64_t R, int64_t Nm, void* planes, int* ex, cudaStream_t s);
 size_t fwd_digits_work_bytes(int64_t nf, int64_t R, int64_t Nm);
 cudaError_t fwd_digits_apply(const void* planes, const int* ex, int64_t nf, int64_t R, int64_t Nm, const void* mhat,
-                             void* dhat, int64_t B, void* work, int* err, cudaStream_t s, int* launches);
+                             void* dhat, int64_t B, void* work, int* err, cudaStream_t s, int* launches,
+                             int drop_stage = -1);
 cudaError_t adj_digits_apply(const void* planes, const int* ea, int64_t nf, int64_t R, int64_t Nm, const void* dhat,
-                             void* mhat, int64_t B, void* work, int* err, cudaStream_t s, int* launches);
+                             void* mhat, int64_t B, void* work, int* err, cudaStream_t s, int* launches,
+                             int drop_stage = -1);
 int axpby_f64(double* y, const double* x, double a, double b, int64_t n, cudaStream_t s);
 // FP32 Gram product W = A B^T into an FP64 matrix (lower tiles) and the FP64 -> FP32 copy
 int sgemm_nt_lower_to_f64(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* Bm,

@@ -48,7 +48,8 @@ constexpr uint32_t kKiATile = kKiRows * 128;
 constexpr uint32_t kKiBPlane = kKiN * 128;
 constexpr uint32_t kKiBTile = kSl * kKiBPlane;
 constexpr uint32_t kKiTmemCols = 512;  // six groups of 64 columns (384) rounded to a power of two
-constexpr long long kKiSpin = 1ll << 22;
+constexpr long long kKiSpin = 1ll << 24;              // poll backstop of every wait
+constexpr uint64_t kKiWaitNs = 1000000000ull;          // wall-time limit of every wait: 1 s
 constexpr size_t kKiSmem = 1024 + kKiAStages * (size_t)kKiATile + kKiBStages * (size_t)kKiBTile;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -65,10 +66,23 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
                : "=r"(done) : "r"(bar), "r"(parity) : "memory");
   return done != 0;
 }
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait: gives up after kKiWaitNs of wall time (checked every 256 polls; a poll of
+// try_wait may suspend the thread for microseconds) or kKiSpin polls, whichever comes first,
+// or as soon as another thread has flagged an abort.  On giving up it flags the abort.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
-  for (long long it = 0; it < kKiSpin; ++it) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (long long it = 1; it < kKiSpin; ++it) {
     if (mbar_try(bar, parity)) return true;
-    if ((it & 1023) == 1023 && *abort_flag) return false;
+    if ((it & 255) == 0) {
+      if (*abort_flag) return false;
+      if (global_ns() - t0 > kKiWaitNs) break;
+    }
   }
   *abort_flag = 1;
   return false;
@@ -275,7 +289,7 @@ __global__ void __launch_bounds__(kKiThreads, 1)
 sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
              const int* __restrict__ ea, const int* __restrict__ eb, double* __restrict__ part, int64_t per,
              int64_t total, int64_t kpt, int span, int NRG, int64_t a_blk, int a_rg, int64_t b_blk, int b_rg,
-             int ea_w, int ea_rg, int eb_w, int eb_rg, int* __restrict__ err) {
+             int ea_w, int ea_rg, int eb_w, int eb_rg, int drop_stage, int* __restrict__ err) {
   constexpr uint32_t kBPlane = NC * 128, kBTile = kSl * kBPlane, kCols = sk_tmem_cols(NC);
   constexpr int W = NC / 2;  // columns per epilogue thread
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -347,6 +361,10 @@ sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
           for (int s = 0; s < kSl; ++s, ++na) {
             const int as = na % kKiAStages;
             if (na >= kKiAStages && !mbar_wait(smem_u32(&emptyA[as]), ((na / kKiAStages) - 1) & 1, abort_v)) {
+              ok = false;
+              break;
+            }
+            if (na == drop_stage) {  // test hook: this stage never arrives, so the waits run out
               ok = false;
               break;
             }
@@ -526,7 +544,8 @@ int kinv_reduce(const double* part, double* X, int64_t ldx, int64_t n, int64_t n
                 int64_t kpt, int span, int64_t tiles, cudaStream_t s);
 
 cudaError_t rowmat_apply_tc(const void* planes, const int* ea, int64_t M, int64_t n, const double* D, int64_t B,
-                            double* X, int64_t ldx, double* work, int* err, cudaStream_t s, int64_t* launches) {
+                            double* X, int64_t ldx, double* work, int* err, cudaStream_t s, int64_t* launches,
+                            int drop_stage) {
   work = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(work) + 255) & ~(uintptr_t)255);
   *launches = 0;
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
@@ -564,7 +583,8 @@ cudaError_t rowmat_apply_tc(const void* planes, const int* ea, int64_t M, int64_
     *launches += kinv_tc_slice(D + q0 * n, n, nb, n, eb, bpl, kKiN, s);
     // tiles: the 128-row tiles of the matrix (one problem); A rows kbg Mp + 128 t, B rows 64 kbg
     sk_tc_kernel<64><<<(unsigned)p.ctas, kKiThreads, sk_smem(64), s>>>(
-        tA, tB, ea, eb, part, p.per, p.total, p.kpt, p.span, (int)p.tiles, Mp, kKiRows, kKiN, 0, 0, kKiRows, 0, 0, err);
+        tA, tB, ea, eb, part, p.per, p.total, p.kpt, p.span, (int)p.tiles, Mp, kKiRows, kKiN, 0, 0, kKiRows, 0, 0,
+        drop_stage, err);
     *launches += 1;
     *launches += kinv_reduce(part, X + q0 * ldx, ldx, M, nb, kKiRows, kKiN, p.per, p.kpt, p.span, p.tiles, s);
   }
@@ -572,8 +592,8 @@ cudaError_t rowmat_apply_tc(const void* planes, const int* ea, int64_t M, int64_
 }
 
 cudaError_t kinv_apply_tc(const void* planes, const int* ea, int64_t n, const double* D, int64_t B, double* X,
-                          double* work, int* err, cudaStream_t s, int64_t* launches) {
-  return rowmat_apply_tc(planes, ea, n, n, D, B, X, n, work, err, s, launches);
+                          double* work, int* err, cudaStream_t s, int64_t* launches, int drop_stage) {
+  return rowmat_apply_tc(planes, ea, n, n, D, B, X, n, work, err, s, launches, drop_stage);
 }
 
 
@@ -678,7 +698,7 @@ __global__ void __launch_bounds__(kKiThreads, 1)
 adj_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const int* __restrict__ ea, const int* __restrict__ eb, double2* __restrict__ mhat, int nf,
               int64_t Nm, int64_t Nmp, int64_t NBp, int B, int nchunk, int JT, int NG, int64_t per, int64_t total,
-              int* __restrict__ err) {
+              int drop_stage, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   unsigned char* sA = smem;
@@ -751,6 +771,10 @@ adj_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
           for (int s = 0; s < kSl; ++s, ++na) {
             const int as = na % kKiAStages;
             if (na >= kKiAStages && !mbar_wait(smem_u32(&emptyA[as]), ((na / kKiAStages) - 1) & 1, abort_v)) {
+              ok = false;
+              break;
+            }
+            if (na == drop_stage) {  // test hook: this stage never arrives, so the waits run out
               ok = false;
               break;
             }
@@ -893,7 +917,8 @@ size_t adj_digits_work_bytes(int64_t nf, int64_t R, int64_t B) {
 }
 
 cudaError_t adj_digits_apply(const void* planes, const int* ea, int64_t nf, int64_t R, int64_t Nm, const void* dhat,
-                             void* mhat, int64_t B, void* work, int* err, cudaStream_t s, int* launches) {
+                             void* mhat, int64_t B, void* work, int* err, cudaStream_t s, int* launches,
+                             int drop_stage) {
   *launches = 0;
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return cudaErrorNotSupported;
@@ -931,7 +956,7 @@ cudaError_t adj_digits_apply(const void* planes, const int* ea, int64_t nf, int6
   const int64_t ctas = (total + per - 1) / per;
   adj_tc_kernel<<<(unsigned)ctas, kKiThreads, kKiSmem, s>>>(tA, tB, ea, eb, static_cast<double2*>(mhat), (int)nf, Nm,
                                                             Nmp, NBp, (int)B, (int)(Kp / kKiChunk), JT, NG, per, total,
-                                                            err);
+                                                            drop_stage, err);
   *launches = 2;
   return cudaGetLastError();
 }
@@ -1116,7 +1141,8 @@ size_t fwd_digits_work_bytes(int64_t nf, int64_t R, int64_t Nm) {
 }
 
 cudaError_t fwd_digits_apply(const void* planes, const int* ex, int64_t nf, int64_t R, int64_t Nm, const void* mhat,
-                             void* dhat, int64_t B, void* work, int* err, cudaStream_t s, int* launches) {
+                             void* dhat, int64_t B, void* work, int* err, cudaStream_t s, int* launches,
+                             int drop_stage) {
   *launches = 0;
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return cudaErrorNotSupported;
@@ -1156,11 +1182,11 @@ cudaError_t fwd_digits_apply(const void* planes, const int* ex, int64_t nf, int6
     if (p.NC == 32)
       sk_tc_kernel<32><<<(unsigned)p.ctas, kKiThreads, sk_smem(32), s>>>(
           tA, tB, ev, ex, part, p.per, p.total, p.kpt, p.span, p.NRG, kKiRows, 0, p.Rp, p.NC, kKiRows, 0, (int)p.Rp,
-          p.NC, err);
+          p.NC, drop_stage, err);
     else
       sk_tc_kernel<64><<<(unsigned)p.ctas, kKiThreads, sk_smem(64), s>>>(
           tA, tB, ev, ex, part, p.per, p.total, p.kpt, p.span, p.NRG, kKiRows, 0, p.Rp, p.NC, kKiRows, 0, (int)p.Rp,
-          p.NC, err);
+          p.NC, drop_stage, err);
     const int64_t tot = nb * nf * R;
     fwd_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, static_cast<double2*>(dhat), nf, R, b0, nb,
                                                                    p.NC, p.NRG, p.per, p.kpt, p.span);

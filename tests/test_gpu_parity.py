@@ -781,6 +781,38 @@ def test_tensor_core_wait_timeout_is_reported_and_recoverable():
     assert relb(host(d), oracle.p2o_apply(F, host(m))) < 1e-3
 
 
+@pytest.mark.parametrize("which", ["adjoint", "forward"])
+def test_digit_plane_wait_timeout_is_reported_and_recoverable(which):
+    """The same failure handling in the digit-plane kernels (adjoint: adj_tc_kernel; forward:
+    the stream-K kernel shared with the explicit inverse and Q): with one TMA stage withheld
+    the bounded waits run out, the whole MMA warp agrees on the abort, the kernel drains,
+    frees its tensor memory and sets the status word; bti_sync reports BTI_ERR_TIMEOUT once
+    and the handle computes correct products afterwards."""
+    p = synthetic.small("dig_timeout", 1, 512, 20, 16, Nq=2)
+    F = p.blocks_F()
+    h = make_handle(F, None, bti.DF64)
+    h.set_digit_planes(bti.OP_F, True)
+    if which == "adjoint":
+        x = cuda(p.vectors_d(16))
+        y = torch.empty((16, 16, 512), dtype=torch.float64, device="cuda")
+        run, ref = h.apply_FT, lambda: oracle.p2o_apply_adjoint(F, host(x))
+    else:
+        x = cuda(p.vectors_m(16))
+        y = torch.empty((16, 16, 20), dtype=torch.float64, device="cuda")
+        run, ref = h.apply_F, lambda: oracle.p2o_apply(F, host(x))
+    h.test_withhold_tc_stage(3)
+    run(x, y)
+    with pytest.raises(bti.BtiError) as e:
+        h.sync()
+    assert e.value.status == 7  # BTI_ERR_TIMEOUT
+    h.sync()  # reported once
+    h.test_withhold_tc_stage(-1)
+    run(x, y)
+    h.sync()
+    assert relb(host(y), ref()) < 1e-12
+    h.close()
+
+
 @pytest.mark.parametrize("store", [bti.F64, bti.DF64], ids=["f64", "df64"])
 def test_elliptic_prior_full_inversion(store):
     """The elliptic prior of Eq. (5.1), Gamma_prior = (alpha1 I - alpha2 Delta_h)^{-2},
