@@ -636,6 +636,7 @@ def online_block(args, dev, stream):
                     out[name][key] = e[0].elapsed_time(e[1]) / reps
                 h.set_online_qoi(False)
             out[name]["build_Q_and_planes_ms"] = t_q
+            out[name]["tensor_roofline"] = digit_tensor_roofline(h, p, dev, gs, B)
         if inverse:
             h.invert_K(False)
         if tcores:
@@ -670,6 +671,44 @@ def online_block(args, dev, stream):
                        "forms) there: 48-bit arithmetic times kappa(K), 1.2e-11 and 5.0e-11 measured, far inside "
                        "the 1e-6 latency target")
     return out
+
+
+def digit_tensor_roofline(h, p, dev, gs, B):
+    """Tensor-pipe roofline of the digit-plane adjoint (G^* on B vectors): FP16 MMA flops
+    it issues (21 plane pairs x 4 K-steps per 64-column box, M = 128, N = 64, K = 16) over
+    its time from the library's per-launch events, against the measured dense BF16 peak
+    (FP16 runs at the same rate)."""
+    import torch
+
+    import paper_2501_14911_gb300 as bti
+
+    def rup(x, m):
+        return (x + m - 1) // m * m
+
+    nf = p.Nt + 1
+    boxes = rup(2 * p.Nd, 128) // 64
+    mmas = nf * (rup(p.Nm, 128) // 128) * (rup(2 * B, 64) // 64) * boxes * 21 * 4
+    flops = mmas * 2 * 128 * 64 * 16
+    x = torch.ones((B, p.Nt, p.Nd), dtype=torch.float64, device=dev)
+    y = torch.empty((B, p.Nt, p.Nm), dtype=torch.float64, device=dev)
+    with torch.cuda.stream(gs):
+        for _ in range(2):
+            h.apply_Gstar(x, y)
+        torch.cuda.synchronize()
+        h.profile_enable(True)
+        h.profile_read()
+        reps = 3
+        for _ in range(reps):
+            h.apply_Gstar(x, y)
+        torch.cuda.synchronize()
+        prof, _ok = h.profile_read()
+        h.profile_enable(False)
+    ms = prof["prod_adj"][0] / reps
+    _, peak, src = load_peaks()
+    ach = flops / (ms * 1e-3) / 1e12
+    return {"bound": "tensor", "kernel": "adj_tc_kernel (G^*, digit planes) + its vector planes",
+            "mma_flops_per_call": flops, "ms_per_call": ms, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            "frac": ach / peak, "peak_source": "MEASURED_PEAKS.json bf16_tflops (" + src + "); FP16 at the same rate"}
 
 
 def mixed_block(args, dev, stream):

@@ -1,0 +1,143 @@
+"""CPU model of the arithmetic behind the tensor-core digit-plane products (tc_digits.cu).
+
+The kernels cut each FP64 operand row into six planes of balanced base-256 digits with a
+power-of-two row scale, multiply plane pairs on FP16 tensor cores with FP32 accumulation,
+and rely on three facts that this file checks in plain numpy, independent of the GPU:
+
+1. the digits are integers in [-128, 128] (so FP16 holds them exactly) and the planes
+   reconstruct each row to 2^-47 of its largest entry;
+2. the FP32 sums the tensor cores form are exact: a group g collects the g + 1 plane
+   pairs with s + t = g (at most six), each product at most 2^14, over a 128-column chunk,
+   so the largest possible sum 6 * 128 * 2^14 stays below 2^24 -- checked with worst-case
+   digits and summed in float32 in every order;
+3. the epilogue's integer conversion of a float pair (hi, lo) times 2^e to FP64 agrees with
+   the exact value up to the dropped bits of lo.
+
+Together they bound the product's error by the 47-bit truncation, which the GPU parity
+tests then confirm against the oracle (1e-12 and below)."""
+
+import numpy as np
+
+S = 6  # planes
+
+
+def digits(v):
+    """Balanced base-256 digits of integers |v| <= 2^47, most significant first."""
+    v = np.asarray(v, dtype=np.int64).copy()
+    out = [None] * S
+    for k in range(S - 1):
+        dk = ((v & 255) ^ 128) - 128
+        out[S - 1 - k] = dk
+        v = (v - dk) >> 8
+    out[0] = v
+    return np.stack(out)
+
+
+def slice_rows(X):
+    mx = np.abs(X).max(axis=1)
+    e = np.where(mx > 0, np.frexp(mx)[1], 0)
+    v = np.rint(np.ldexp(X, (47 - e)[:, None])).astype(np.int64)
+    return digits(v), e
+
+
+def test_digits_are_exact_fp16_integers_and_reconstruct_rows():
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((64, 300)) * np.exp(3 * rng.standard_normal((64, 1)))
+    X[5, :] = 0.0  # an all-zero row
+    X[7, 11] = -np.abs(X[7]).max() * 1.0  # a row whose maximum is negative
+    P, e = slice_rows(X)
+    assert P.min() >= -128 and P.max() <= 128
+    assert np.array_equal(P.astype(np.float16).astype(np.int64), P)  # exact in FP16
+    rec = sum(P[s].astype(np.float64) * 2.0 ** (-8 * s) for s in range(S)) * np.ldexp(1.0, e - 7)[:, None]
+    rowmax = np.maximum(np.abs(X).max(axis=1), 1e-300)
+    assert np.all(np.abs(rec - X).max(axis=1) <= 2.0 ** -47 * rowmax * 1.0001)
+    assert np.all(rec[5] == 0.0)
+
+
+def test_chunk_group_sums_are_exact_in_float32_at_the_worst_case():
+    # every digit at +-128 with signs that make all products +2^14: the largest sum a group
+    # can reach over a 128-column chunk
+    chunk = 128
+    for g in range(S):
+        pairs = g + 1
+        prod = np.full(pairs * chunk, 128.0 * 128.0, dtype=np.float32)
+        total = pairs * chunk * 128 * 128
+        assert total < 2 ** 24
+        # sequential, pairwise and reversed float32 sums all equal the exact integer
+        acc = np.float32(0)
+        for x in prod:
+            acc = np.float32(acc + x)
+        assert int(acc) == total
+        assert int(np.sum(prod, dtype=np.float32)) == total
+        assert int(np.sum(prod[::-1], dtype=np.float32)) == total
+    # one more column would already need 2^24 + ...: the chunk length is at its limit
+    assert 6 * 171 * 128 * 128 >= 2 ** 24
+
+
+def test_digit_plane_product_matches_fp64_to_the_truncation():
+    rng = np.random.default_rng(4)
+    n, B = 700, 5
+    A = rng.standard_normal((n, n)) * np.exp(rng.standard_normal((n, 1)))
+    D = rng.standard_normal((B, n))
+    P, ea = slice_rows(A)
+    Q, eb = slice_rows(D)
+    acc = np.zeros((n, B))
+    for c0 in range(0, n, 128):
+        sl = slice(c0, c0 + 128)
+        for g in range(S):
+            G = np.zeros((n, B), dtype=np.float32)
+            for s in range(g + 1):
+                # float32 accumulation, as in the tensor memory
+                G = (G + (P[s][:, sl].astype(np.float32) @ Q[g - s][:, sl].astype(np.float32).T)).astype(np.float32)
+            exact = sum(P[s][:, sl].astype(np.int64) @ Q[g - s][:, sl].astype(np.int64).T for s in range(g + 1))
+            assert np.array_equal(G.astype(np.int64), exact)
+            acc += G.astype(np.float64) * 2.0 ** (-8 * g)
+    X = acc * np.ldexp(1.0, ea[:, None] + eb[None, :] - 14)
+    ref = A @ D.T
+    assert np.linalg.norm(X - ref) / np.linalg.norm(ref) < 1e-12
+
+
+def pair_to_double_scaled(hi, lo, e):
+    """Python restatement of the epilogue's integer conversion (two-sum renormalisation,
+    64-bit significand alignment, exponent add)."""
+    hi, lo = np.float32(hi), np.float32(lo)
+    sm = np.float32(hi + lo)
+    bb = np.float32(sm - hi)
+    lo = np.float32(np.float32(hi - np.float32(sm - bb)) + np.float32(lo - bb))
+    hi = sm
+    hb = int(np.array(hi, dtype=np.float32).view(np.uint32))
+    Eh = (hb >> 23) & 255
+    if Eh == 0:
+        return 0.0
+    X = ((hb & 0x7FFFFF) | 0x800000) << 29
+    lb = int(np.array(lo, dtype=np.float32).view(np.uint32))
+    El = (lb >> 23) & 255
+    if El != 0:
+        ml = (lb & 0x7FFFFF) | 0x800000
+        sh = El - Eh + 29
+        ml = ml << sh if sh >= 0 else (ml >> -sh if sh > -40 else 0)
+        X = X - ml if (lb ^ hb) >> 31 else X + ml
+    E = Eh
+    if X >= 1 << 53:
+        X >>= 1
+        E += 1
+    elif X < 1 << 52:
+        X <<= 1
+        E -= 1
+    bits = ((hb >> 31) << 63) | ((E - 127 + 1023 + e) << 52) | (X & ((1 << 52) - 1))
+    return float(np.array(bits, dtype=np.uint64).view(np.float64))
+
+
+def test_pair_to_double_conversion():
+    rng = np.random.default_rng(5)
+    for _ in range(2000):
+        hi = np.float32(rng.standard_normal() * 10.0 ** rng.integers(-6, 6))
+        lo = np.float32(hi * rng.uniform(-2.0 ** -24, 2.0 ** -24))
+        e = int(rng.integers(-60, 60))
+        exact = (float(hi) + float(lo)) * 2.0 ** e
+        got = pair_to_double_scaled(hi, lo, e)
+        assert abs(got - exact) <= 2.0 ** -50 * abs(exact)
+    assert pair_to_double_scaled(0.0, 0.0, 5) == 0.0
+    assert pair_to_double_scaled(-1.5, 0.0, 3) == -12.0
+    # a pair whose low part flips the sign of the residual and crosses a power of two
+    assert pair_to_double_scaled(1.0, -2.0 ** -30, 0) == 1.0 - 2.0 ** -30
