@@ -959,9 +959,39 @@ bti_status bti_invert_K(bti_handle h, int enable) {
     release();
     return st;
   }
-  // rows of X: K^{-1} e_b (= row b of the symmetric K^{-1})
   int64_t nl = identity_blocks(X, 1, n, s);
-  nl += trsm_lower_f64(h->K, h->Linv, n, X, n, h->wsolve, h->status, s, true);
+  if (tc && h->tc_enabled) {
+    // W^T = (L^{-1})^T by forward solves (rows that can be nonzero only), then
+    // K^{-1} = W^T W on the tensor cores: rows of W^T are both the digit-plane matrix and the
+    // right-hand sides (K^{-1}[j][i] = sum_k W^T[i][k] W^T[j][k]); W^T's planes use the
+    // buffer K^{-1}'s planes take afterwards
+    double* Y = nullptr;
+    st = dev_alloc(h, (void**)&Y, sizeof(double) * (size_t)n * n, "K inverse temporary");
+    if (st == BTI_OK)
+      st = ensure(h, (void**)&h->wsolve, &h->wsolve_bytes,
+                  sizeof(double) * std::max(trsm_work_elems(n, n), rowmat_tc_work_elems(n, n)), "solve workspace");
+    if (st != BTI_OK) {
+      dev_freep(Y);
+      dev_freep(X);
+      release();
+      return st;
+    }
+    nl += lower_inverse_rows(h->K, h->Linv, n, X, h->wsolve, s, true);
+    nl += kinv_tc_slice(X, n, n, n, h->kinv_ea, h->kinv_planes, ldt, s);
+    int64_t tl = 0;
+    cudaError_t e = rowmat_apply_tc(h->kinv_planes, h->kinv_ea, n, n, X, n, Y, n, h->wsolve, h->status + 1, s, &tl);
+    nl += tl;
+    std::swap(X, Y);
+    dev_freep(Y);
+    if (e != cudaSuccess) {
+      dev_freep(X);
+      release();
+      return cuda_check(h, e, "invert_K (tensor-core W^T W)");
+    }
+  } else {
+    // rows of X: K^{-1} e_b (= row b of the symmetric K^{-1}), by both triangular solves
+    nl += trsm_lower_f64(h->K, h->Linv, n, X, n, h->wsolve, h->status, s, true);
+  }
   nl += split_to_pairs(X, h->Kinv, n, ldk, s);
   if (tc) nl += kinv_tc_slice(X, n, n, n, h->kinv_ea, h->kinv_planes, ldt, s);
   count_dense(h, nl);
@@ -1131,11 +1161,28 @@ bti_status bti_build_Q(bti_handle h, int with_covariance) {
     if (st != BTI_OK) return st;
     cudaMemcpyAsync(X, h->Q, sizeof(double) * (size_t)nq * n, cudaMemcpyDeviceToDevice, s);
   }
-  // Q = X K^{-1}: every row of X is a right-hand side of the two triangular solves
+  // Q = X K^{-1}: every row of X is a right-hand side of the two triangular solves, or of
+  // one product with the explicit inverse on the tensor cores when bti_invert_K formed it
+  const bool inv_tc = kinv_ready(h) && h->kinv_planes && h->tc_enabled;
   st = ensure(h, (void**)&h->wsolve, &h->wsolve_bytes,
-              sizeof(double) * std::max(trsm_work_elems(n, nq), (size_t)n * kCholNB), "solve workspace");
+              sizeof(double) * std::max(std::max(trsm_work_elems(n, nq), (size_t)n * kCholNB),
+                                        inv_tc ? kinv_tc_work_elems(n) : (size_t)0),
+              "solve workspace");
   if (st != BTI_OK) { dev_freep(X); return st; }
-  nl += trsm_lower_f64(h->K, h->Linv, n, h->Q, nq, h->wsolve, h->status, s, dd);
+  if (inv_tc) {
+    double* Qn = nullptr;
+    st = dev_alloc(h, (void**)&Qn, sizeof(double) * (size_t)nq * n, "alloc Q");
+    if (st != BTI_OK) { dev_freep(X); return st; }
+    int64_t tl = 0;
+    cudaError_t e = kinv_apply_tc(h->kinv_planes, h->kinv_ea, n, h->Q, nq, Qn, h->wsolve, h->status + 1, s, &tl);
+    nl += tl;
+    cudaStreamSynchronize(s);
+    dev_freep(h->Q);
+    h->Q = Qn;
+    if (e != cudaSuccess) { dev_freep(X); return cuda_check(h, e, "build_Q (tensor-core K^{-1})"); }
+  } else {
+    nl += trsm_lower_f64(h->K, h->Linv, n, h->Q, nq, h->wsolve, h->status, s, dd);
+  }
   if (with_covariance) {
     double* Gq = nullptr;
     double* Cf = nullptr;

@@ -196,6 +196,10 @@ constexpr int kCholNB = 64;
 int64_t trsm_lower_f64(const double* Lm, const double* Linv, int64_t n, double* X, int64_t B,
                        double* work, const int* status, cudaStream_t s, bool dd = false);
 size_t trsm_work_elems(int64_t n, int64_t B);
+// X (n x n, = I on entry) := (L^{-1})^T, the forward solves against the identity restricted to
+// the rows that can be nonzero; work of trsm_work_elems(n, n).
+int64_t lower_inverse_rows(const double* Lm, const double* Linv, int64_t n, double* X, double* work,
+                           cudaStream_t s, bool dd);
 // Explicit inverse for the online solve: Kinv [n][kinv_ld(n)] float pairs (hi, lo) of K^{-1}
 // (zero padding); X [B][n] = rows K^{-1} D[b] for D [B][n] (X != D); work of
 // kinv_apply_work_elems(n, B) doubles.  split_to_pairs: FP64 X [n][n] -> pairs Y [n][ldk].

@@ -839,6 +839,29 @@ int64_t kinv_apply(const float2* Kinv, int64_t n, const double* D, int64_t B, do
   return launches;
 }
 
+// X := W^T with W = L^{-1}, starting from X = I (row b of the result is L^{-1} e_b, column b
+// of W): the forward half of trsm_lower_f64 on the identity, where row b stays zero before
+// column b, so block step k only touches the k + kb rows that can be nonzero (about n^3 / 3
+// flop instead of n^3).
+int64_t lower_inverse_rows(const double* Lm, const double* Linv, int64_t n, double* X, double* work,
+                           cudaStream_t s, bool dd) {
+  const int nb = kCholNB;
+  int64_t launches = 0;
+  for (int64_t k = 0; k < n; k += nb) {
+    const int kb = (int)std::min<int64_t>(nb, n - k);
+    const int64_t rows = k + kb;  // rows k + kb .. n - 1 are still zero in columns < k + kb
+    const double* Lk = Linv + (k / nb) * nb * nb;
+    launches += gemm_sel(dd, true, rows, kb, kb, 1.0, X + k, n, Lk, nb, 0.0, work, kb, false, s);
+    cudaMemcpy2DAsync(X + k, n * sizeof(double), work, kb * sizeof(double), kb * sizeof(double), rows,
+                      cudaMemcpyDeviceToDevice, s);
+    const int64_t m = n - k - kb;
+    if (m > 0)
+      launches += gemm_sel(dd, true, rows, m, kb, -1.0, X + k, n, Lm + (k + kb) * n + k, n, 1.0, X + k + kb, n,
+                           false, s);
+  }
+  return launches;
+}
+
 __global__ void axpby_kernel(double* y, const double* x, double a, double b, int64_t n) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] = fma(a, x[i], b * y[i]);

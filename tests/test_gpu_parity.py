@@ -540,6 +540,28 @@ def test_d2q_map_and_qoi_covariance(dense):
     h.close()
 
 
+def test_d2q_map_through_the_explicit_inverse():
+    """With bti_invert_K first (K^{-1} = W^T W, W = L^{-1} from forward solves on the identity,
+    the product on the tensor cores), bti_build_Q applies K^{-1} on the tensor cores instead
+    of the two triangular solves: Q and Gamma_post(q) still match the oracle."""
+    p, F, Fq, G, _ = tiny_problem()
+    h = make_handle(F, Fq, bti.DF64)
+    h.set_prior_se_grid(p.gx, p.gy, p.ell, p.sigma_p, bti.DF64)
+    h.set_noise(p.sigma2)
+    h.set_dense_precision(bti.DF64)
+    h.build_K()
+    h.factor_K()
+    h.invert_K()
+    h.build_Q(with_covariance=True)
+    Q, C = h.copy_Q(covariance=True)
+    Cs = oracle.se_covariance(p.gx, p.gy, p.ell, p.sigma_p)
+    Q_or = oracle.d2q_map(Fq, F, G, p.sigma2)
+    C_or = oracle.qoi_posterior_covariance(Fq, oracle.prior_blocks(Fq, Cs), F, G, p.sigma2)
+    assert np.linalg.norm(host(Q) - Q_or) / np.linalg.norm(Q_or) < 1e-10
+    assert np.linalg.norm(host(C) - C_or) / np.linalg.norm(C_or) < 1e-9
+    h.close()
+
+
 @pytest.mark.parametrize("B", [3, 70], ids=["b3", "b70"])
 def test_online_qoi_via_d2q_map_on_tensor_cores(B):
     """bti_set_online_qoi: q_map = Q d_obs (Eq. (4.14)) with Q in FP16 digit planes on the
