@@ -230,11 +230,14 @@ __device__ __forceinline__ void butterfly8_half_zero(const C2<T>* src, int i0, i
   dst[sp(o0 + 7)] = csub<T>(e3, o3);
 }
 
+// Radix sets compiled into a kernel: fewer butterflies compiled in means fewer registers,
+// and the restricted sets fit 3 CTAs per SM instead of 2.
+enum { kRadixAll = 0, kRadixPow2 = 1, kRadix25 = 2 };  // (8, 4, 2, 7, 5, 3); (8, 4, 2); (8, 4, 2, 5)
+
 // All passes; data starts in buf0, result pointer returned (buf0 or buf1); transform p
 // of the CTA occupies LP slots from p LP.  With half_zero, the first pass is radix 8 and
-// only the first half of each input is nonzero.  POW2 compiles the radix 8, 4, 2
-// butterflies only (fewer registers for power-of-two lengths).
-template <typename T, bool INV, bool POW2>
+// only the first half of each input is nonzero.  RS selects the compiled radix set.
+template <typename T, bool INV, int RS>
 __device__ C2<T>* run_passes(const FftDesc& D, C2<T>* buf0, C2<T>* buf1, const C2<T>* __restrict__ tw,
                              int LP, bool half_zero = false) {
   C2<T>* src = buf0;
@@ -266,10 +269,15 @@ __device__ C2<T>* run_passes(const FftDesc& D, C2<T>* buf0, C2<T>* buf1, const C
       C2<T>* d = dst + p * LP;
       const int o0 = (j - k) * r + k;
       int twstep = k * (L / (Ns * r));
-      if (POW2) {
+      if (RS == kRadixPow2) {
         if (r == 8) butterfly<8, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L);
         else if (r == 4) butterfly<4, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L);
         else butterfly<2, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L);
+      } else if (RS == kRadix25) {
+        if (r == 8) butterfly<8, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L);
+        else if (r == 4) butterfly<4, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L);
+        else if (r == 2) butterfly<2, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L);
+        else butterfly<5, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L);
       } else {
         switch (r) {
           case 8: butterfly<8, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L); break;
@@ -295,8 +303,8 @@ template <typename TO, typename T> __device__ __forceinline__ C2<TO> cvt2(C2<T> 
 }
 template <typename T> __device__ __forceinline__ C2<T> czero() { return mk<T>((T)0, (T)0); }
 
-template <typename T, typename TI, typename TO, bool POW2>
-__global__ void __launch_bounds__(256, POW2 ? 3 : 2)  // power-of-two plans fit 3 CTAs per SM without spills
+template <typename T, typename TI, typename TO, int RS>
+__global__ void __launch_bounds__(256, RS == kRadixAll ? 2 : 3)  // restricted radix sets fit 3 CTAs per SM
 rfft_cols_kernel(FftDesc D, int Nt, const TI* __restrict__ x, int64_t ld, int64_t xbs,
                  C2<TO>* __restrict__ X, int64_t Xbs, int64_t ncols, TwTabs tabs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -335,7 +343,7 @@ rfft_cols_kernel(FftDesc D, int Nt, const TI* __restrict__ x, int64_t ld, int64_
     buf0[p * LP + sp(t)] = czero<T>();
   }
   __syncthreads();
-  C2<T>* Z = run_passes<T, false, POW2>(D, buf0, buf1, tw, LP, 2 * Nt == L);
+  C2<T>* Z = run_passes<T, false, RS>(D, buf0, buf1, tw, LP, 2 * Nt == L);
   // unpack the two real spectra of each pair and store bins 0..N_t
   const int nf = Nt + 1;
   for (int idx = threadIdx.x; idx < nf * W2; idx += blockDim.x) {
@@ -356,8 +364,8 @@ rfft_cols_kernel(FftDesc D, int Nt, const TI* __restrict__ x, int64_t ld, int64_
   }
 }
 
-template <typename T, typename TYI, typename TO, bool POW2>
-__global__ void __launch_bounds__(256, POW2 ? 3 : 2)
+template <typename T, typename TYI, typename TO, int RS>
+__global__ void __launch_bounds__(256, RS == kRadixAll ? 2 : 3)
 irfft_cols_kernel(FftDesc D, int Nt, const C2<TYI>* __restrict__ Y, int64_t ld, int64_t Ybs,
                   TO* __restrict__ y, int64_t ybs, int64_t ncols, double scale_d, TwTabs tabs, int ostride) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -388,7 +396,7 @@ irfft_cols_kernel(FftDesc D, int Nt, const C2<TYI>* __restrict__ Y, int64_t ld, 
     }
   }
   __syncthreads();
-  C2<T>* Z = run_passes<T, true, POW2>(D, buf0, buf1, tw, LP);
+  C2<T>* Z = run_passes<T, true, RS>(D, buf0, buf1, tw, LP);
   // rows t = ostride (k + 1) - 1 only (every row when ostride == 1), stored as row k
   const int nout = Nt / ostride;
   for (int idx = threadIdx.x; idx < nout * W2; idx += blockDim.x) {
@@ -413,6 +421,17 @@ static FftDesc desc_of(const FftPlan& p) {
 
 static TwTabs tabs_of(const FftPlan& p) { return TwTabs{p.tw64, p.tw32, p.twff}; }
 
+// the smallest compiled radix set that covers the plan's passes
+static int radix_set(const FftPlan& p) {
+  bool only2 = true, only25 = true;
+  for (int i = 0; i < p.npass; ++i) {
+    const int r = p.radix[i];
+    if (r != 8 && r != 4 && r != 2) only2 = false;
+    if (r != 8 && r != 4 && r != 2 && r != 5) only25 = false;
+  }
+  return only2 ? kRadixPow2 : (only25 ? kRadix25 : kRadixAll);
+}
+
 template <typename T, typename TI, typename TO>
 void launch_rfft_cols(const FftPlan& p, int Nt, const TI* x, int64_t ld, int64_t x_bstride,
                       C2<TO>* X, int64_t X_bstride, int64_t ncols, int64_t B, cudaStream_t s) {
@@ -421,23 +440,30 @@ void launch_rfft_cols(const FftPlan& p, int Nt, const TI* x, int64_t ld, int64_t
   size_t smem = 2 * sizeof(C2<T>) * (size_t)p.P * fft_slots(p.L);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(rfft_cols_kernel<T, TI, TO, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(rfft_cols_kernel<T, TI, TO, kRadixPow2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          200 * 1024);
-    cudaFuncSetAttribute(rfft_cols_kernel<T, TI, TO, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(rfft_cols_kernel<T, TI, TO, kRadix25>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+    cudaFuncSetAttribute(rfft_cols_kernel<T, TI, TO, kRadixAll>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          200 * 1024);
     attr_set = true;
   }
-  const bool pow2 = (p.L & (p.L - 1)) == 0;
+  const int rs = radix_set(p);
   int64_t gx = (ncols + 2 * p.P - 1) / (2 * p.P);
   for (int64_t b0 = 0; b0 < B; b0 += 65535) {
     int64_t nb = B - b0 < 65535 ? B - b0 : 65535;
     dim3 grid((unsigned)gx, (unsigned)nb);
-    if (pow2)
-      rfft_cols_kernel<T, TI, TO, true><<<grid, 256, smem, s>>>(D, Nt, x + b0 * x_bstride, ld, x_bstride,
-                                                                X + b0 * X_bstride, X_bstride, ncols, tabs_of(p));
+    const TI* xb = x + b0 * x_bstride;
+    C2<TO>* Xb = X + b0 * X_bstride;
+    if (rs == kRadixPow2)
+      rfft_cols_kernel<T, TI, TO, kRadixPow2><<<grid, 256, smem, s>>>(D, Nt, xb, ld, x_bstride, Xb, X_bstride, ncols,
+                                                                      tabs_of(p));
+    else if (rs == kRadix25)
+      rfft_cols_kernel<T, TI, TO, kRadix25><<<grid, 256, smem, s>>>(D, Nt, xb, ld, x_bstride, Xb, X_bstride, ncols,
+                                                                    tabs_of(p));
     else
-      rfft_cols_kernel<T, TI, TO, false><<<grid, 256, smem, s>>>(D, Nt, x + b0 * x_bstride, ld, x_bstride,
-                                                                 X + b0 * X_bstride, X_bstride, ncols, tabs_of(p));
+      rfft_cols_kernel<T, TI, TO, kRadixAll><<<grid, 256, smem, s>>>(D, Nt, xb, ld, x_bstride, Xb, X_bstride, ncols,
+                                                                     tabs_of(p));
   }
 }
 
@@ -450,26 +476,31 @@ void launch_irfft_cols(const FftPlan& p, int Nt, const C2<TYI>* X, int64_t ld, i
   size_t smem = 2 * sizeof(C2<T>) * (size_t)p.P * fft_slots(p.L);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(irfft_cols_kernel<T, TYI, TO, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(irfft_cols_kernel<T, TYI, TO, kRadixPow2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          200 * 1024);
-    cudaFuncSetAttribute(irfft_cols_kernel<T, TYI, TO, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(irfft_cols_kernel<T, TYI, TO, kRadix25>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+    cudaFuncSetAttribute(irfft_cols_kernel<T, TYI, TO, kRadixAll>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          200 * 1024);
     attr_set = true;
   }
-  const bool pow2 = (p.L & (p.L - 1)) == 0;
+  const int rs = radix_set(p);
   const int os = ostride < 1 ? 1 : ostride;
   int64_t gx = (ncols + 2 * p.P - 1) / (2 * p.P);
   for (int64_t b0 = 0; b0 < B; b0 += 65535) {
     int64_t nb = B - b0 < 65535 ? B - b0 : 65535;
     dim3 grid((unsigned)gx, (unsigned)nb);
-    if (pow2)
-      irfft_cols_kernel<T, TYI, TO, true><<<grid, 256, smem, s>>>(D, Nt, X + b0 * X_bstride, ld, X_bstride,
-                                                                  y + b0 * y_bstride, y_bstride, ncols, scale,
-                                                                  tabs_of(p), os);
+    const C2<TYI>* Xb = X + b0 * X_bstride;
+    TO* yb = y + b0 * y_bstride;
+    if (rs == kRadixPow2)
+      irfft_cols_kernel<T, TYI, TO, kRadixPow2><<<grid, 256, smem, s>>>(D, Nt, Xb, ld, X_bstride, yb, y_bstride,
+                                                                        ncols, scale, tabs_of(p), os);
+    else if (rs == kRadix25)
+      irfft_cols_kernel<T, TYI, TO, kRadix25><<<grid, 256, smem, s>>>(D, Nt, Xb, ld, X_bstride, yb, y_bstride,
+                                                                      ncols, scale, tabs_of(p), os);
     else
-      irfft_cols_kernel<T, TYI, TO, false><<<grid, 256, smem, s>>>(D, Nt, X + b0 * X_bstride, ld, X_bstride,
-                                                                   y + b0 * y_bstride, y_bstride, ncols, scale,
-                                                                   tabs_of(p), os);
+      irfft_cols_kernel<T, TYI, TO, kRadixAll><<<grid, 256, smem, s>>>(D, Nt, Xb, ld, X_bstride, yb, y_bstride,
+                                                                       ncols, scale, tabs_of(p), os);
   }
 }
 
