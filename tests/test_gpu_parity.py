@@ -67,6 +67,10 @@ CASES = [
     ("L2048_max_length", 96, 5, 3, 1024, 9),  # the longest transform (N_t = 1024, one pair per CTA)
     ("b9_Nm_not_mult4", 333, 7, 2, 20, 9),    # B >= 8 but N_m % 4 != 0: CUDA-core FP16 products
     ("tc_R1100_b20", 512, 1100, 3, 12, 20),    # tensor-core forward over 9 row tiles; adjoint on CUDA cores
+    # lengths 2^a 5^b: the (8, 4, 2, 5) radix-set FFT kernels
+    ("L250_radix_2_5", 700, 6, 3, 125, 2),     # plan 2, 5, 5, 5 (no radix-8 first pass)
+    ("L1000_radix_8_5", 96, 5, 3, 500, 3),     # plan 8, 5, 5, 5 (half-zero radix-8 first pass)
+    ("L100_radix_4_5_b16", 300, 7, 2, 50, 16), # plan 4, 5, 5; B = 16 (tensor cores in the FP16 tier)
 ]
 
 
