@@ -1134,6 +1134,7 @@ bti_status bti_build_Q(bti_handle h, int with_covariance) {
   const bool dd = h->dense_prec == BTI_P_DF64;
   auto gemm = dd ? gemm_df64 : gemm_f64;
   cudaStream_t s = h->stream;
+  drop_online_graph_any(h);  // a captured online graph may read Q (bti_set_online_qoi)
   dev_freep(h->Q);  // the QoI grid may have changed since the last build
   dev_freep(h->covq);
   st = dev_alloc(h, (void**)&h->Q, sizeof(double) * (size_t)nq * n, "alloc Q");

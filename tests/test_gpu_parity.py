@@ -609,6 +609,10 @@ def test_online_qoi_via_d2q_map_on_tensor_cores(B):
         h.online(cuda(d), m, q3, refine_iters=1)
         assert relb(host(m), m_or) < 1e-12
         assert relb(host(q3), q_or) < 1e-10
+        # a new Q (here the same map rebuilt, in a new buffer) is picked up by the online graph
+        h.build_Q()
+        h.online(cuda(d), m, q3, refine_iters=1)
+        assert relb(host(q3), q_or) < 1e-10
         h.set_online_qoi(False)
         h.online(cuda(d), m, q3, refine_iters=1)  # back to the push-forward F_q m_map
         assert relb(host(q3), q_or) < 1e-12
