@@ -185,9 +185,10 @@ bti_status bti_copy_K(bti_handle h, double* dst);
  * of Eq. (4.13) moved offline).  enable = 1, after bti_factor_K: forms K^{-1} by
  * solving with the factor against the identity (double-FP32 GEMMs, 2 n^3 flops for
  * n = N_t N_d) and keeps it on the device as float pairs (hi, lo), 8 n^2 bytes.
- * bti_infer_map and bti_online then apply K^{-1} as one dense product, in double-FP32
- * arithmetic (about 48 significant bits), instead of the n / 64 sequential blocked
- * solves.  The inverse belongs to the factor it was formed from: after a new
+ * bti_infer_map and bti_online then apply K^{-1} as one dense product instead of the n / 64
+ * sequential blocked solves: for B >= 16 vectors with tensor cores on, as exact FP16
+ * digit-plane MMAs on tcgen05 (K^{-1} formed as W^T W with W = L^{-1}, the product on the
+ * tensor cores too); otherwise in double-FP32 arithmetic (about 48 significant bits).  The inverse belongs to the factor it was formed from: after a new
  * bti_factor_K the solves return to the factor until this is called again.
  * enable = 0 releases the inverse.  Requires factor_K for enable = 1 (BTI_ERR_STATE);
  * BTI_ERR_OOM if the 16 n^2-byte peak (inverse plus FP64 temporary) does not fit.
@@ -370,7 +371,7 @@ bti_status bti_copy_Q(bti_handle h, double* Q_out, double* cov_out);
  * (Eq. (4.14), the paper's online QoI prediction; requires build_Q, BTI_ERR_STATE
  * otherwise), and Q is also formed as six FP16 digit planes (12 (N_q N_t^q rounded up to
  * 128)(N_t N_d rounded up to 128) bytes), so that bti_apply_Q and the online graph apply
- * it on the tensor cores with FP64-level accuracy while tensor cores are on.  via_Q = 0
+ * it on the tensor cores with FP64-level accuracy for B >= 16 while tensor cores are on.  via_Q = 0
  * (the default): q_map = F_q m_map (push-forward, as bti_predict_qoi); the planes are
  * released.  A later bti_build_Q makes the planes stale: apply_Q falls back to the dense
  * GEMM until this is called again.  Synchronises. */

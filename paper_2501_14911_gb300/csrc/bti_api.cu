@@ -1050,8 +1050,10 @@ static bti_status infer_map_impl(bti_handle h, const double* d_obs, double* m_ma
   cudaStream_t s = h->stream;
   const bool inv = kinv_ready(h);
   // x = K^{-1} v (v != x), by the explicit inverse or the blocked triangular solves
-  // tensor-core form of the explicit inverse when the planes exist and tensor cores are on
-  const bool inv_tc = inv && h->kinv_planes && h->tc_enabled;
+  // tensor-core form of the explicit inverse when the planes exist, tensor cores are on and
+  // the batch fills its 64-column tiles enough (B >= 16, as for the spectral products); fewer
+  // vectors take the memory-bound double-FP32 kernel
+  const bool inv_tc = inv && h->kinv_planes && h->tc_enabled && B >= 16;
   cudaError_t tc_err = cudaSuccess;
   auto solve_into = [&](const double* v, double* xo) -> int64_t {
     if (inv_tc) {
@@ -1222,10 +1224,11 @@ static size_t apply_Q_work_elems(const bti_ctx* h, int64_t B) {
 }
 
 // q[b] = Q d[b] (Eq. (4.14)): by the digit-plane product on the tensor cores when Q's planes
-// are current, else as one dense GEMM (double-FP32 for B > 8 with dense_prec DF64, else FP64)
+// are current and B >= 16, else as one dense GEMM (double-FP32 for B > 8 with dense_prec DF64,
+// else FP64)
 static bti_status apply_Q_impl(bti_ctx* h, const double* d_obs, double* q_map, int64_t B) {
   const int64_t n = h->Nt * h->Nd, nq = (h->Nt / h->qstride) * h->Nq;
-  if (Q_planes_ready(h) && h->tc_enabled) {
+  if (Q_planes_ready(h) && h->tc_enabled && B >= 16) {
     bti_status st = ensure(h, (void**)&h->wsolve, &h->wsolve_bytes, sizeof(double) * apply_Q_work_elems(h, B),
                            "solve workspace");
     if (st != BTI_OK) return st;
@@ -1877,7 +1880,7 @@ bti_status bti_predict_qoi(bti_handle h, const double* m_map, double* q_map, int
 static bti_status reserve_online(bti_ctx* h, int64_t B) {
   bti_status st = reserve_solve(h, B);
   if (st != BTI_OK) return st;
-  if (h->online_via_Q && Q_planes_ready(h)) {
+  if (h->online_via_Q && Q_planes_ready(h) && B >= 16) {
     st = ensure(h, (void**)&h->wsolve, &h->wsolve_bytes, sizeof(double) * apply_Q_work_elems(h, B), "solve workspace");
     if (st != BTI_OK) return st;
   }
