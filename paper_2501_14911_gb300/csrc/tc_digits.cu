@@ -1,11 +1,15 @@
-// Explicit-inverse product of the online solve on the tensor cores (tcgen05), exact in
-// integer slices.
+// FP64-level products on the FP16 tensor cores (tcgen05), exact in integer digit planes.
 //
-// X[b][i] = sum_j Kinv[i][j] D[b][j] (x = K^{-1} d, Eq. (4.13) with the solves moved
-// offline) needs about 48 significant bits, which no tensor-core input type holds.  Both
-// operands are therefore cut into S = 6 planes of balanced base-256 digits, each digit an
-// integer in [-128, 128] and so exact in FP16:
-//   Kinv[i][j] = 2^(ea_i - 7) sum_s P_s[i][j] 2^(-8 s),   D[b][j] = 2^(eb_b - 7) sum_t Q_t[b][j] 2^(-8 t)
+// Used for the batched online phase and its offline preparation: the explicit-inverse
+// product x = K^{-1} d (Eq. (4.13) with the solves moved offline), K^{-1} = W^T W itself, the
+// d2q product q = Q d (Eq. (4.14)), and the double-FP32 tier's per-frequency products
+// d-hat_w = F-hat_w m-hat_w and m-hat_w = F-hat_w^H d-hat_w for batches (Sec. 4).
+//
+// Take the real product X[b][i] = sum_j A[i][j] D[b][j] (A = K^{-1}, say).  It needs about 48
+// significant bits, which no tensor-core input type holds.  Both operands are therefore cut
+// into S = 6 planes of balanced base-256 digits, each an integer in [-128, 128] and so exact
+// in FP16:
+//   A[i][j] = 2^(ea_i - 7) sum_s P_s[i][j] 2^(-8 s),   D[b][j] = 2^(eb_b - 7) sum_t Q_t[b][j] 2^(-8 t)
 // with ea_i, eb_b the binary exponents of the row maxima (so the planes hold a 47-bit
 // fixed-point image of each row, the rest rounded away).  Then
 //   X[b][i] = 2^(ea_i + eb_b - 14) sum_g 2^(-8 g) G_g[i][b],  G_g = sum_{s + t = g} P_s Q_t^T,
@@ -14,18 +18,20 @@
 // plane pairs, so over a chunk of 128 columns j a group's sum stays below 6 * 128 * 2^14
 // < 2^24: the FP32 accumulators in tensor memory hold it exactly.  After each chunk the
 // epilogue warps read the six groups, scale them by 2^(-8 g) (exact) and add them into
-// float-pair accumulators with a two-sum, as the double-FP32 kernels do.
+// float-pair accumulators with a two-sum, as the double-FP32 kernels do, and convert the
+// result to FP64 with integer operations.  The complex spectral products are real GEMMs over
+// an interleaved (re, im) K axis, the vectors' rows carrying the complex product's signs.
 //
-// Layout: the K^{-1} planes [S][ldk / 64][rows_pad][64] FP16 (rows_pad and ldk multiples of
-// 128, zero padding; tiled so each TMA box is contiguous) are formed once with the inverse;
-// the right-hand-side planes [S][ldk / 64][64][64] per call.  A CTA (one per SM) walks a contiguous run of (row tile, chunk) units (stream-K,
-// as the double-FP32 kernel), so every SM gets the same number of chunks; partial tiles go
-// to an FP64 buffer that a second kernel sums in CTA order.  Warp 0 issues the TMA loads
-// (K^{-1} planes 128 rows x 64 columns per stage, the six right-hand-side planes per 64
-// columns), warp 1 issues tcgen05.mma (M = 128, N = 64, K = 16) into six TMEM groups of 64
-// columns, warps 2-9 drain the groups per chunk.  Every wait is bounded; on a timeout the
-// kernel sets the error word, stops issuing, lets what it issued land and frees its tensor
-// memory.
+// Layout: a matrix's planes [S][ldk / 64][rows_pad][64] FP16 (rows_pad and ldk multiples of
+// 128, zero padding; tiled so each TMA box is contiguous) are formed once; the right-hand-
+// side planes [S][ldk / 64][64][64] per call.  In the stream-K kernel a CTA (one per SM)
+// walks a contiguous run of (tile, chunk) units, so every SM gets the same number of chunks;
+// partial tiles go to an FP64 buffer that a second kernel sums in CTA order.  Warp 0 issues
+// the TMA loads (the matrix's planes 128 rows x 64 columns per stage, the six right-hand-side
+// planes per 64 columns), warp 1 runs the MMA loop with one elected lane issuing tcgen05.mma
+// (M = 128, N = 64 or 32, K = 16) into six TMEM groups, warps 2-9 drain the groups per chunk.
+// Every wait is bounded; on a timeout the kernel sets the error word, stops issuing, lets what
+// it issued land and frees its tensor memory.
 #include "bti_internal.cuh"
 
 #include <cuda.h>
