@@ -239,6 +239,15 @@ bti_status bti_apply_prior(bti_handle h, const double* v, double* out, int64_t B
  * prior and factor_K; synchronises. */
 bti_status bti_apply_postcov(bti_handle h, const double* v, double* out, int64_t B);
 
+/* Probe estimate of the pointwise posterior variances, diag(Gamma_post(m)) (Sec. 4, Phase 2):
+ * diag[e] = sum_s V[s][e] (Gamma_post(m) V[s])[e] / sum_s V[s][e]^2 over S caller-drawn probe
+ * vectors V [S][N_t][N_m] (device doubles; e.g. random signs), 0 where no probe touches an
+ * entry; diag [N_t][N_m] (device double, not aliased with V).  The actions run in batches of
+ * up to 64 probes (bti_apply_postcov, so the explicit inverse and digit planes apply when
+ * set).  Exact for the unit vectors and for Hadamard sign vectors.  Requires the prior and
+ * factor_K; synchronises. */
+bti_status bti_postcov_diag_probe(bti_handle h, const double* V, int64_t S, double* diag);
+
 /* m_map with a nonzero prior mean, Eq. (4.13) with the term of Eq. (4.8):
  * m_map = G^* K^{-1} d_obs + (I - G^* K^{-1} F) m_prior
  *       = m_prior + G^* K^{-1} (d_obs - F m_prior).

@@ -58,6 +58,7 @@ from .inversion import (
     qoi_posterior_covariance,
     prior_apply,
     posterior_cov_apply,
+    posterior_variance_probe,
     map_point_with_prior_mean,
     qoi_time_steps,
     qoi_rows,
@@ -72,6 +73,6 @@ __all__ = [
     "elliptic_operator",
     "assemble_K", "assemble_K_columns", "cholesky_lower", "solve_K",
     "map_point", "map_point_woodbury_form", "qoi_map", "qoi_data_gram", "d2q_map",
-    "qoi_posterior_covariance", "prior_apply", "posterior_cov_apply", "map_point_with_prior_mean",
+    "qoi_posterior_covariance", "prior_apply", "posterior_cov_apply", "posterior_variance_probe", "map_point_with_prior_mean",
     "qoi_time_steps", "qoi_rows", "loss", "loss_gradient",
 ]

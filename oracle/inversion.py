@@ -222,6 +222,19 @@ def posterior_cov_apply(F_blocks, G_blocks, Cs, noise, v, L=None):
     return w - p2o_apply_adjoint(G_blocks, x)
 
 
+def posterior_variance_probe(F_blocks, G_blocks, Cs, noise, V, L=None):
+    """Probe estimate of the pointwise posterior variances diag(Gamma_post(m)) (Sec. 4, Phase 2
+    names them among the quantities that follow from Gamma_post(m) actions): elementwise
+    sum_s v_s * (Gamma_post(m) v_s) / sum_s v_s * v_s over caller-drawn probes V [S, N_t, N_m],
+    0 where no probe touches an entry.  Exact for the unit vectors, and for sign vectors whose
+    products cancel off the diagonal (the rows of a Hadamard matrix)."""
+    V = np.asarray(V, dtype=np.float64)
+    U = posterior_cov_apply(F_blocks, G_blocks, Cs, noise, V, L=L)
+    num = (V * U).sum(axis=0)
+    den = (V * V).sum(axis=0)
+    return np.where(den > 0, num / np.where(den > 0, den, 1.0), 0.0)
+
+
 def map_point_with_prior_mean(F_blocks, G_blocks, noise, d_obs, m_prior, L=None):
     """m_map of Eq. (4.13) with the prior-mean term of Eq. (4.8).
 

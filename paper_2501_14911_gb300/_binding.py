@@ -88,6 +88,7 @@ def lib():
         "bti_apply_prior": ([vp, vp, vp, i64], st),
         "bti_set_qoi_stride": ([vp, ip], st),
         "bti_apply_postcov": ([vp, vp, vp, i64], st),
+        "bti_postcov_diag_probe": ([vp, vp, i64, vp], st),
         "bti_infer_map_prior": ([vp, vp, vp, vp, i64, ip], st),
         "bti_set_shadow": ([vp, ip, ip], st),
         "bti_set_tensor_cores": ([vp, ip], st),
@@ -303,6 +304,10 @@ class Handle:
     def apply_postcov(self, v, out):
         """out = Gamma_post(m) v (Eq. (4.7))."""
         return self._param_op(lib().bti_apply_postcov, v, out, "apply_postcov")
+
+    def postcov_diag_probe(self, V, out):
+        """Probe estimate of diag(Gamma_post(m)) from S probe vectors V [S][N_t][N_m] into out [N_t][N_m]."""
+        self._check(lib().bti_postcov_diag_probe(self._h, _ptr(V), int(V.shape[0]), _ptr(out)))
 
     def _param_op(self, fn, v, out, name):
         self._tensor(v, (self.Nt, self.Nm), name + " input")

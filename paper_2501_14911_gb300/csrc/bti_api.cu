@@ -1817,6 +1817,39 @@ bti_status bti_apply_postcov(bti_handle h, const double* v, double* out, int64_t
   return st;
 }
 
+bti_status bti_postcov_diag_probe(bti_handle h, const double* V, int64_t S, double* diag) {
+  bti_status st = check_handle(h);
+  if (st != BTI_OK) return st;
+  if (S <= 0) return fail(h, BTI_ERR_ARG, "postcov_diag_probe: S must be > 0");
+  if (!V || !diag) return fail(h, BTI_ERR_ARG, "postcov_diag_probe: null pointer");
+  if (!h->prior_set) return fail(h, BTI_ERR_STATE, "postcov_diag_probe: no prior set");
+  if (!h->K_factored || !h->op[BTI_OP_G].set) return fail(h, BTI_ERR_STATE, "postcov_diag_probe: K not factored");
+  const int64_t npar = h->Nt * h->Nm;
+  const int64_t Bp = S < 64 ? S : 64;  // probes per batch of Gamma_post(m) actions
+  double* U = nullptr;
+  st = dev_alloc(h, (void**)&U, sizeof(double) * ((size_t)Bp * npar + 2 * (size_t)npar), "probe temporaries");
+  if (st != BTI_OK) return st;
+  double* num = U + (size_t)Bp * npar;
+  double* den = num + npar;
+  cudaMemsetAsync(num, 0, sizeof(double) * 2 * (size_t)npar, h->stream);
+  for (int64_t s0 = 0; s0 < S && st == BTI_OK; s0 += Bp) {
+    const int64_t nb = S - s0 < Bp ? S - s0 : Bp;
+    const double* Vb = V + (size_t)s0 * npar;
+    st = bti_apply_postcov(h, Vb, U, nb);
+    if (st == BTI_OK) {
+      count_dense(h, probe_accumulate(Vb, U, nb, npar, num, den, h->stream));
+      st = launched(h, "postcov_diag_probe");
+    }
+  }
+  if (st == BTI_OK) {
+    count_dense(h, probe_finish(num, den, diag, npar, h->stream));
+    st = launched(h, "postcov_diag_probe");
+  }
+  cudaStreamSynchronize(h->stream);
+  dev_freep(U);
+  return st;
+}
+
 bti_status bti_infer_map_prior(bti_handle h, const double* d_obs, const double* m_prior, double* m_map, int64_t B,
                                int refine_iters) {
   bti_status st = check_handle(h);

@@ -290,6 +290,11 @@ cudaError_t launch_prod_adj_f16_tc(const void* Fhat, const float* scale, const f
                                    int64_t nf, int64_t R, int64_t Nm, int64_t B, int* err, cudaStream_t s,
                                    int* launches);
 
+// Probe estimate of pointwise variances (krylov.cu): num/den accumulate sum_k V[k] U[k] and
+// sum_k V[k]^2 elementwise over nb probes [nb][n]; out = num / den (0 where den = 0).
+int probe_accumulate(const double* V, const double* U, int64_t nb, int64_t n, double* num, double* den,
+                     cudaStream_t s);
+int probe_finish(const double* num, const double* den, double* out, int64_t n, cudaStream_t s);
 // Krylov vector kernels (krylov.cu); vectors [B][n], per-vector scalars on the device.
 // out[b] = x[b] . y[b] in FP64 with a fixed reduction order; part holds
 // dot_workspace_elems(B) doubles.

@@ -250,4 +250,38 @@ template int add_noise<float>(float*, const float*, const float*, const double*,
 template int add_noise<double>(double*, const double*, const double*, const double*, double, int64_t, int64_t,
                                cudaStream_t);
 
+// ------------------------------------------------------------------ variance probes
+// num[e] += sum_k V[k][e] U[k][e], den[e] += sum_k V[k][e]^2 over nb probes (fixed order k),
+// for the probe estimate of the pointwise posterior variances.
+__global__ void probe_accumulate_kernel(const double* __restrict__ V, const double* __restrict__ U, int64_t nb,
+                                        int64_t n, double* __restrict__ num, double* __restrict__ den) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  double a = num[e], b = den[e];
+  for (int64_t k = 0; k < nb; ++k) {
+    const double v = V[k * n + e];
+    a = fma(v, U[k * n + e], a);
+    b = fma(v, v, b);
+  }
+  num[e] = a;
+  den[e] = b;
+}
+__global__ void probe_finish_kernel(const double* __restrict__ num, const double* __restrict__ den,
+                                    double* __restrict__ out, int64_t n) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) out[e] = den[e] > 0.0 ? num[e] / den[e] : 0.0;
+}
+int probe_accumulate(const double* V, const double* U, int64_t nb, int64_t n, double* num, double* den,
+                     cudaStream_t s) {
+  if (n <= 0 || nb <= 0) return 0;
+  probe_accumulate_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(V, U, nb, n, num, den);
+  return 1;
+}
+int probe_finish(const double* num, const double* den, double* out, int64_t n, cudaStream_t s) {
+  if (n <= 0) return 0;
+  probe_finish_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(num, den, out, n);
+  return 1;
+}
+
+
 }  // namespace bti

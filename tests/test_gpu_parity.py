@@ -659,6 +659,35 @@ def test_posterior_covariance_actions_and_prior_mean():
     h.close()
 
 
+@pytest.mark.parametrize("probes", ["unit", "signs"])
+def test_posterior_variance_probe(probes):
+    """bti_postcov_diag_probe against the oracle's estimator on the same probes: all unit
+    vectors (the exact diagonal of Gamma_post(m), 128 probes in two batches) and 100 random
+    sign vectors (a batch of 64 and one of 36); every estimated variance lies in (0, sigma_p^2]."""
+    p = synthetic.small("var_probe", 4, 4, 3, 8, Nq=2)
+    F = p.blocks_F()
+    Cs = oracle.se_covariance(4, 4, 2.0, 1.0)
+    G = oracle.prior_blocks(F, Cs)
+    h = make_handle(F, None, bti.DF64)
+    h.set_prior_se_grid(4, 4, 2.0, 1.0, bti.DF64)
+    h.set_noise(1e-2)
+    h.build_K()
+    h.factor_K()
+    N = p.Nt * p.Nm
+    if probes == "unit":
+        V = np.eye(N).reshape(N, p.Nt, p.Nm)
+    else:
+        V = np.sign(np.random.default_rng(7).standard_normal((100, p.Nt, p.Nm)))
+    out = torch.empty((p.Nt, p.Nm), dtype=torch.float64, device="cuda")
+    h.postcov_diag_probe(cuda(V), out)
+    ref = oracle.posterior_variance_probe(F, G, Cs, 1e-2, V)
+    got = host(out)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-11
+    if probes == "unit":
+        assert np.all(got > 0.0) and np.all(got <= 1.0 + 1e-12)
+    h.close()
+
+
 @pytest.mark.parametrize("stride", [4, 16])
 def test_coarse_qoi_grid(stride):
     """QoIs on every stride-th time step (the Remark after Eq. (2.15); the Sec. 5 example

@@ -432,6 +432,30 @@ def test_posterior_covariance_action_is_inverse_hessian():
                                rtol=1e-13, atol=1e-14)
 
 
+def test_posterior_variance_probe_is_exact_for_unit_and_hadamard_probes():
+    """The probe estimate of diag(Gamma_post(m)) equals the diagonal of H^{-1} (Eq. (2.13),
+    invertible elliptic prior) for the unit vectors and for the rows of a Hadamard matrix
+    (sign vectors whose products cancel off the diagonal); a few random sign probes do not
+    give it exactly (the estimator is not the diagonal by construction)."""
+    import scipy.linalg as sla
+
+    F, G, Cs, A, s2, rng = _elliptic_problem(gx=2, gy=4, Nt=4)  # N = 4 * 8 = 32 parameters
+    Nt, Nd, Nm = F.shape
+    P = oracle.p2o_dense(F)
+    H = P.T @ P / s2 + np.kron(np.eye(Nt), A @ A)
+    diag = np.diag(np.linalg.inv(H)).reshape(Nt, Nm)
+    unit = np.eye(Nt * Nm).reshape(-1, Nt, Nm)
+    assert rel(oracle.posterior_variance_probe(F, G, Cs, s2, unit), diag) < 1e-10
+    had = sla.hadamard(Nt * Nm).astype(np.float64).reshape(-1, Nt, Nm)
+    assert rel(oracle.posterior_variance_probe(F, G, Cs, s2, had), diag) < 1e-10
+    few = np.sign(rng.standard_normal((3, Nt, Nm)))
+    assert rel(oracle.posterior_variance_probe(F, G, Cs, s2, few), diag) > 1e-3
+    # entries no probe touches read 0
+    part = unit[:5]
+    est = oracle.posterior_variance_probe(F, G, Cs, s2, part).reshape(-1)
+    assert np.all(est[5:] == 0.0) and rel(est[:5], diag.reshape(-1)[:5]) < 1e-10
+
+
 def test_map_point_with_prior_mean_is_closed_form():
     """Eq. (4.13) + Eq. (4.8) against the normal equations of Eq. (2.12) with m_prior != 0."""
     F, G, Cs, A, s2, rng = _elliptic_problem(seed=43)
