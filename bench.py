@@ -548,8 +548,9 @@ def online_block(args, dev, stream):
     e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     reps = 3
     # (name, dense arithmetic, K assembly, refinement steps, explicit inverse, tensor cores):
-    # with tensor cores the explicit inverse and the G^* and F_q products of the 64 vectors run
-    # as exact digit-plane MMAs (bti_set_digit_planes); without, in double-FP32 on the CUDA cores
+    # with tensor cores the Gram product of K (double-FP32 dense), the explicit inverse and the
+    # G^* and F_q products of the 64 vectors run as exact digit-plane MMAs; without, in
+    # double-FP32 on the CUDA cores
     forms = [("plain_f64", bti.F64, bti.F64, 0, False, False), ("dense_df64", bti.DF64, bti.F64, 1, False, False),
              ("dense_df64_no_refinement", bti.DF64, bti.F64, 0, False, False),
              ("explicit_inverse_cuda_cores", bti.DF64, bti.F64, 0, True, False),
@@ -561,6 +562,7 @@ def online_block(args, dev, stream):
         h.set_stream(gs)
         with torch.cuda.stream(gs):
             h.set_dense_precision(dense)
+            h.set_tensor_cores(tcores)  # the FP16-tier products and every digit-plane product
             torch.cuda.synchronize()
             e[0].record(gs)
             h.build_K_prec(p.col_block, assembly)
@@ -570,7 +572,6 @@ def online_block(args, dev, stream):
             torch.cuda.synchronize()
             t_build, t_factor = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
             t_inv = t_planes = 0.0
-            h.set_tensor_cores(tcores)
             if inverse:
                 e[0].record(gs)
                 h.invert_K()

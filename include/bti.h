@@ -161,6 +161,10 @@ bti_status bti_apply_Gstar(bti_handle h, const void* d, void* m, int64_t B, bti_
  * width of the assembly; 512 is the default when 0 is passed. */
 bti_status bti_build_K(bti_handle h, int64_t col_block);
 
+/* (With bti_set_dense_precision(BTI_P_DF64) and tensor cores on, the Gram product
+ * W = F_stack G_stack^T of bti_build_K runs on tcgen05 as an exact FP16 digit-plane product,
+ * about 47 significant bits, like the double-FP32 GEMM it replaces.) */
+
 /* As bti_build_K, with the Gram product that assembles K computed in `assembly`
  * precision: BTI_P_F64 (same as bti_build_K) or BTI_P_F32 (FP32 products and
  * accumulation over N_m, about 1e-6 relative; K itself, its block-diagonal

@@ -868,6 +868,34 @@ static bti_status build_K_impl(bti_handle h, int64_t col_block, bti_prec assembl
     count_dense(h, nl);
     cudaStreamSynchronize(s);
     dev_freep(Ff);
+  } else if (h->dense_prec == BTI_P_DF64 && h->tc_enabled && kinv_tc_supported(n) && kinv_tc_supported(h->Nm)) {
+    // W = F_stack G_stack^T on the tensor cores in exact digit planes: G_stack's rows are the
+    // planes' matrix and F_stack's rows the right-hand sides, so row b of the product is
+    // W[b][.] = sum_j F[b][j] G[.][j] (all of W; the upper triangle is not read)
+    const int64_t Nm = h->Nm, Mp = kinv_tc_ld(n);
+    void* planes = nullptr;
+    int* ex = nullptr;
+    st = dev_alloc(h, &planes, sizeof(uint16_t) * rowmat_tc_plane_elems(n, Nm), "Gram planes");
+    if (st == BTI_OK) st = dev_alloc(h, (void**)&ex, sizeof(int) * (size_t)Mp, "Gram exponents");
+    if (st == BTI_OK)
+      st = ensure(h, (void**)&h->wsolve, &h->wsolve_bytes, sizeof(double) * rowmat_tc_work_elems(n, Nm),
+                  "solve workspace");
+    if (st != BTI_OK) {
+      dev_free(planes);
+      dev_freep(ex);
+      return st;
+    }
+    kinv_prepare();
+    kinv_tc_prepare();
+    int64_t nl = kinv_tc_slice(G.time, Nm, n, Nm, ex, planes, Mp, s);
+    int64_t tl = 0;
+    cudaError_t e = rowmat_apply_tc(planes, ex, n, Nm, F.time, n, h->K, n, h->wsolve, h->status + 1, s, &tl,
+                                    h->tc_drop_stage);
+    count_dense(h, nl + tl);
+    cudaStreamSynchronize(s);
+    dev_free(planes);
+    dev_freep(ex);
+    if (e != cudaSuccess) return cuda_check(h, e, "build_K (tensor-core Gram)");
   } else {
     // W = F_stack G_stack^T (lower block triangle), by column panels
     const bool dd = h->dense_prec == BTI_P_DF64;
