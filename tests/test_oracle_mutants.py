@@ -1,0 +1,336 @@
+"""Mutation check of the oracle's pins.  CPU only; the CUDA path is not involved.
+
+Each case plants one plausible mistake in one oracle routine: a dropped term, a wrong sign,
+an index shifted by one, the Toeplitz structure taken in the wrong direction, a factor
+applied on the wrong side, a missing or extra power of a variance.  The case then runs every
+pin of test_oracle_pins.py against the mutated oracle and requires that at least one of them
+fails.  A mistake that no pin catches could reach the parity tests, which would then hold the
+CUDA path to a wrong answer.  The unmutated oracle must pass every pin (checked first).
+
+The patch replaces the routine wherever the oracle modules hold it, including the names the
+oracle's own modules import from each other, so a mutant reaches its callers too.
+"""
+
+import contextlib
+import importlib.util
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import oracle
+import oracle.inversion as inv
+import oracle.prior as pri
+import oracle.toeplitz as tz
+
+MODULES = (oracle, tz, inv, pri)
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _load_pins():
+    spec = importlib.util.spec_from_file_location("oracle_pins_under_mutation",
+                                                  os.path.join(HERE, "test_oracle_pins.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return [(n, getattr(mod, n)) for n in sorted(dir(mod)) if n.startswith("test_")]
+
+
+PINS = _load_pins()
+
+
+def _first_failing_pin():
+    for name, fn in PINS:
+        try:
+            with np.errstate(all="ignore"):
+                fn()
+        except Exception:  # an assertion, or the mutant breaking a shape or a factorisation
+            return name
+    return None
+
+
+@contextlib.contextmanager
+def _planted(name, make):
+    orig = next(getattr(m, name) for m in MODULES if hasattr(m, name))
+    mutant = make(orig)
+    holders = [m for m in MODULES if getattr(m, name, None) is orig]
+    for m in holders:
+        setattr(m, name, mutant)
+    try:
+        yield
+    finally:
+        for m in holders:
+            setattr(m, name, orig)
+
+
+# ---------------------------------------------------------------- mutant helpers
+
+def _zero_block(blocks, k):
+    b = np.array(blocks, dtype=np.float64)
+    b[k] = 0.0
+    return b
+
+
+def _p2o_anticausal(blocks, m):
+    """d[t] = sum_k F_k m[t+k]: the Toeplitz structure taken upper instead of lower."""
+    blocks = np.asarray(blocks, dtype=np.float64)
+    m = np.asarray(m, dtype=np.float64)
+    Nt, R, _ = blocks.shape
+    d = np.zeros(m.shape[:-2] + (Nt, R))
+    for k in range(Nt):
+        d[..., : Nt - k, :] += m[..., k:, :] @ blocks[k].T
+    return d
+
+
+def _adjoint_wrong_direction(blocks, d):
+    """m[s] = sum_k F_k^T d[s-k]: the adjoint shifted the way the forward map shifts."""
+    blocks = np.asarray(blocks, dtype=np.float64)
+    d = np.asarray(d, dtype=np.float64)
+    Nt, _, Nm = blocks.shape
+    m = np.zeros(d.shape[:-2] + (Nt, Nm))
+    for k in range(Nt):
+        m[..., k:, :] += d[..., : Nt - k, :] @ blocks[k]
+    return m
+
+
+def _late_by_one(f):
+    def g(blocks, m):
+        d = f(blocks, m)
+        out = np.zeros_like(d)
+        out[..., 1:, :] = d[..., :-1, :]
+        return out
+    return g
+
+
+def _dense_upper(blocks):
+    blocks = np.asarray(blocks, dtype=np.float64)
+    Nt, R, Nm = blocks.shape
+    P = np.zeros((Nt * R, Nt * Nm))
+    for t in range(Nt):
+        for s in range(t, Nt):
+            P[t * R:(t + 1) * R, s * Nm:(s + 1) * Nm] = blocks[s - t]
+    return P
+
+
+def _simulate_observe_before_step(A, B, C, m):
+    w = np.zeros(np.asarray(A).shape[0])
+    d = np.empty((len(m), np.asarray(B).shape[0]))
+    for k in range(len(m)):
+        d[k] = B @ w
+        w = A @ w + C @ m[k]
+    return d
+
+
+def _K_wrong_diagonal(F, G, noise):
+    """Block-diagonal accumulation run from the bottom-right instead of the top-left."""
+    F = np.asarray(F, dtype=np.float64)
+    G = np.asarray(G, dtype=np.float64)
+    Nt, R, Nm = F.shape
+    n = Nt * R
+    K = F.reshape(n, Nm) @ G.reshape(n, Nm).T
+    for t in range(1, Nt):
+        K[t * R:(t + 1) * R, : n - R] += K[(t - 1) * R:t * R, R:]
+    K[np.diag_indices(n)] += inv._noise_diag(noise, Nt, R)
+    return K
+
+
+def _solve_forward_only(L, d):
+    d = np.asarray(d, dtype=np.float64)
+    rhs = d.T if d.ndim == 2 else d
+    y = sla.solve_triangular(L, rhs, lower=True)
+    return y.T if d.ndim == 2 else y
+
+
+def _solve_swapped_order(L, d):
+    """L^{-1} L^{-T} d = (L^T L)^{-1} d instead of (L L^T)^{-1} d."""
+    d = np.asarray(d, dtype=np.float64)
+    rhs = d.T if d.ndim == 2 else d
+    y = sla.solve_triangular(L, rhs, lower=True, trans="T")
+    x = sla.solve_triangular(L, y, lower=True)
+    return x.T if d.ndim == 2 else x
+
+
+def _map_with_FT(F, G, noise, d, L=None):
+    """Applies F^T where G^* = Gamma_prior F^T belongs: the prior dropped after the solve."""
+    Nt, R, _ = np.shape(F)
+    if L is None:
+        L = inv.cholesky_lower(inv.assemble_K(F, G, noise))
+    d = np.asarray(d, dtype=np.float64)
+    x = inv.solve_K(L, d.reshape(-1, Nt * R)).reshape(d.shape)
+    return tz.p2o_apply_adjoint(F, x)
+
+
+def _map_without_solve(F, G, noise, d, L=None):
+    Nt, R, _ = np.shape(F)
+    var = inv._noise_diag(noise, Nt, R).reshape(Nt, R)
+    return tz.p2o_apply_adjoint(G, np.asarray(d, dtype=np.float64) / var)
+
+
+def _woodbury_plus(f):
+    def g(F, G, noise, d, L=None):
+        Nt, R, _ = np.shape(F)
+        var = inv._noise_diag(noise, Nt, R).reshape(Nt, R)
+        y = tz.p2o_apply_adjoint(G, np.asarray(d, dtype=np.float64) / var)
+        return 2.0 * y - f(F, G, noise, d, L)  # y + G^* K^{-1} F y instead of y - ...
+    return g
+
+
+def _gram_without_accumulation(Fq, G):
+    Fq = np.asarray(Fq, dtype=np.float64)
+    G = np.asarray(G, dtype=np.float64)
+    Nt, Rq, Nm = Fq.shape
+    return Fq.reshape(Nt * Rq, Nm) @ G.reshape(-1, Nm).T
+
+
+def _gram_lower_only(Fq, G):
+    """Accumulates only the block lower triangle, as if F_q G^* were symmetric like K."""
+    Fq = np.asarray(Fq, dtype=np.float64)
+    G = np.asarray(G, dtype=np.float64)
+    Nt, Rq, Nm = Fq.shape
+    R = G.shape[1]
+    X = Fq.reshape(Nt * Rq, Nm) @ G.reshape(Nt * R, Nm).T
+    for t in range(1, Nt):
+        for tp in range(1, t + 1):
+            X[t * Rq:(t + 1) * Rq, tp * R:(tp + 1) * R] += X[(t - 1) * Rq:t * Rq, (tp - 1) * R:tp * R]
+    return X
+
+
+def _d2q_without_solve(Fq, F, G, noise, L=None):
+    Nt, R, _ = np.shape(F)
+    return inv.qoi_data_gram(Fq, G) / inv._noise_diag(noise, Nt, R)[None, :]
+
+
+def _probe_divide_by_count(F, G, Cs, noise, V, L=None):
+    V = np.asarray(V, dtype=np.float64)
+    U = inv.posterior_cov_apply(F, G, Cs, noise, V, L=L)
+    return (V * U).sum(axis=0) / V.shape[0]
+
+
+def _probe_square_of_action(F, G, Cs, noise, V, L=None):
+    V = np.asarray(V, dtype=np.float64)
+    U = inv.posterior_cov_apply(F, G, Cs, noise, V, L=L)
+    den = (V * V).sum(axis=0)
+    return np.where(den > 0, (U * U).sum(axis=0) / np.where(den > 0, den, 1.0), 0.0)
+
+
+def _sample_with_covariance(z, gx, gy, ell, sigma):
+    z = np.asarray(z, dtype=np.float64)
+    Cx = pri.se_covariance_1d(gx, ell, sigma)
+    Cy = pri.se_covariance_1d(gy, ell, sigma)
+    Z = z.reshape(z.shape[:-1] + (gx, gy))
+    return (Cx @ Z @ Cy).reshape(z.shape)
+
+
+def _elliptic_interior_degree(f):
+    def g(gx, gy, a1, a2):
+        A = f(gx, gy, a1, a2).tolil()
+        for a in range(gx * gy):
+            A[a, a] = a1 + 4.0 * a2  # every node given four neighbours, boundary or not
+        return A.tocsr()
+    return g
+
+
+def _first_term_dropped(blocks, v, t):
+    return np.asarray(blocks[t], dtype=np.float64) @ np.asarray(v, dtype=np.float64)[0]
+
+
+MUTANTS = {
+    # Toeplitz maps, Eq. (2.3)-(2.5)
+    "p2o_anticausal": ("p2o_apply", lambda f: _p2o_anticausal),
+    "p2o_drops_F0": ("p2o_apply", lambda f: lambda b, m: f(_zero_block(b, 0), m)),
+    "p2o_drops_last_block": ("p2o_apply", lambda f: lambda b, m: f(_zero_block(b, -1), m)),
+    "p2o_late_by_one_step": ("p2o_apply", _late_by_one),
+    "adjoint_wrong_direction": ("p2o_apply_adjoint", lambda f: _adjoint_wrong_direction),
+    "adjoint_drops_F0": ("p2o_apply_adjoint", lambda f: lambda b, d: f(_zero_block(b, 0), d)),
+    "adjoint_sign": ("p2o_apply_adjoint", lambda f: lambda b, d: -f(b, d)),
+    "dense_upper_triangular": ("p2o_dense", lambda f: _dense_upper),
+    "lti_blocks_power_plus_one": ("lti_blocks", lambda f: lambda A, B, C, Nt: f(A, B, np.asarray(A) @ C, Nt)),
+    "lti_observe_before_step": ("lti_simulate", lambda f: _simulate_observe_before_step),
+    "block_output_drops_last_term": (
+        "p2o_apply_block",
+        lambda f: lambda b, m, t: f(b, m, t) - _first_term_dropped(b, m, t)),
+    "adjoint_block_drops_first_term": (
+        "p2o_apply_adjoint_block",
+        lambda f: lambda b, d, s: f(b, d, s) - np.asarray(d, dtype=np.float64)[s] @ np.asarray(b[0], dtype=np.float64)),
+    # prior, Sec. 5 and Eq. (5.1)
+    "se_missing_factor_two": ("se_covariance", lambda f: lambda gx, gy, ell, s: f(gx, gy, ell / np.sqrt(2.0), s)),
+    "se_sigma_not_squared": ("se_covariance", lambda f: lambda gx, gy, ell, s: f(gx, gy, ell, np.sqrt(s))),
+    "se_iy_major_ordering": ("se_covariance", lambda f: lambda gx, gy, ell, s: f(gy, gx, ell, s)),
+    "se_1d_sigma_squared": ("se_covariance_1d", lambda f: lambda n, ell, s: f(n, ell, s * s)),
+    "prior_blocks_drop_prior": ("prior_blocks", lambda f: lambda b, Cs: np.asarray(b, dtype=np.float64)),
+    "prior_sample_uses_covariance": ("prior_sample", lambda f: _sample_with_covariance),
+    "elliptic_laplacian_sign": ("elliptic_operator", lambda f: lambda gx, gy, a1, a2: f(gx, gy, a1, -a2)),
+    "elliptic_boundary_degree": ("elliptic_operator", _elliptic_interior_degree),
+    # K, Cholesky, solves, Sec. 4 Phase 2
+    "noise_as_std": ("_noise_diag", lambda f: lambda noise, Nt, R: f(noise, Nt, R) ** 2),
+    "noise_vector_averaged": ("_noise_diag", lambda f: lambda noise, Nt, R: np.full(Nt * R, float(np.mean(noise)))),
+    "K_drops_noise": ("assemble_K", lambda f: lambda F, G, noise: f(F, G, 0.0)),
+    "K_wrong_block_diagonal": ("assemble_K", lambda f: _K_wrong_diagonal),
+    "K_uses_F_for_Gstar": ("assemble_K", lambda f: lambda F, G, noise: f(F, F, noise)),
+    "K_columns_drop_noise": ("assemble_K_columns", lambda f: lambda F, G, noise: f(F, G, 0.0)),
+    "cholesky_returns_upper": ("cholesky_lower", lambda f: lambda K: f(K).T),
+    "solve_forward_only": ("solve_K", lambda f: _solve_forward_only),
+    "solve_swapped_order": ("solve_K", lambda f: _solve_swapped_order),
+    # m_map, q_map, Eq. (4.2), (4.13)
+    "map_uses_FT_not_Gstar": ("map_point", lambda f: _map_with_FT),
+    "map_without_solve": ("map_point", lambda f: _map_without_solve),
+    "woodbury_sign": ("map_point_woodbury_form", _woodbury_plus),
+    "qoi_map_drops_F0": ("qoi_map", lambda f: lambda Fq, m: f(_zero_block(Fq, 0), m)),
+    "qoi_map_anticausal": ("qoi_map", lambda f: lambda Fq, m: _p2o_anticausal(Fq, m)),
+    # loss and gradient, Eq. (2.9), (5.1)
+    "loss_without_noise_weight": ("loss", lambda f: lambda F, m, d, noise, A_s=None: f(F, m, d, 1.0, A_s)),
+    "loss_prior_term_doubled": (
+        "loss",
+        lambda f: lambda F, m, d, noise, A_s=None: 2.0 * f(F, m, d, noise, A_s) - f(F, m, d, noise, None)),
+    "gradient_sign": ("loss_gradient", lambda f: lambda F, m, d, noise, A_s=None: -f(F, m, d, noise, A_s)),
+    "gradient_drops_prior": ("loss_gradient", lambda f: lambda F, m, d, noise, A_s=None: f(F, m, d, noise, None)),
+    "gradient_noise_std": (
+        "loss_gradient",
+        lambda f: lambda F, m, d, noise, A_s=None: f(F, m, d, np.sqrt(np.asarray(noise, dtype=np.float64)), A_s)),
+    # d2q map and Gamma_post(q), Eq. (4.10)-(4.11)
+    "gram_without_accumulation": ("qoi_data_gram", lambda f: _gram_without_accumulation),
+    "gram_lower_only": ("qoi_data_gram", lambda f: _gram_lower_only),
+    "d2q_without_solve": ("d2q_map", lambda f: _d2q_without_solve),
+    "postcov_q_sign": (
+        "qoi_posterior_covariance",
+        lambda f: lambda Fq, Gq, F, G, noise, L=None: 2.0 * inv.qoi_data_gram(Fq, Gq) - f(Fq, Gq, F, G, noise, L)),
+    "postcov_q_drops_prior_part": (
+        "qoi_posterior_covariance",
+        lambda f: lambda Fq, Gq, F, G, noise, L=None: f(Fq, Gq, F, G, noise, L) - inv.qoi_data_gram(Fq, Gq)),
+    # Gamma_post(m) actions and probes, Eq. (4.7)
+    "prior_apply_identity": ("prior_apply", lambda f: lambda Cs, v: np.asarray(v, dtype=np.float64)),
+    "prior_apply_squared": ("prior_apply", lambda f: lambda Cs, v: f(Cs, f(Cs, v))),
+    "postcov_sign": (
+        "posterior_cov_apply",
+        lambda f: lambda F, G, Cs, noise, v, L=None: 2.0 * inv.prior_apply(Cs, v) - f(F, G, Cs, noise, v, L)),
+    "postcov_without_prior": (
+        "posterior_cov_apply",
+        lambda f: lambda F, G, Cs, noise, v, L=None: f(F, G, np.eye(np.shape(Cs)[0]), noise, v, L)),
+    "probe_divides_by_count": ("posterior_variance_probe", lambda f: _probe_divide_by_count),
+    "probe_squares_action": ("posterior_variance_probe", lambda f: _probe_square_of_action),
+    # prior mean, Eq. (4.8)
+    "prior_mean_residual_dropped": (
+        "map_point_with_prior_mean",
+        lambda f: lambda F, G, noise, d, mp, L=None: inv.map_point(F, G, noise, d, L) + mp),
+    "prior_mean_not_added": (
+        "map_point_with_prior_mean",
+        lambda f: lambda F, G, noise, d, mp, L=None: f(F, G, noise, d, mp, L) - mp),
+    # QoI time grid (Remark after Eq. (2.15), Sec. 5)
+    "qoi_steps_at_interval_start": ("qoi_time_steps", lambda f: lambda Nt, stride: np.arange(0, Nt, stride)),
+    "qoi_rows_time_minor": (
+        "qoi_rows",
+        lambda f: lambda Nt, Nq, stride: (np.arange(Nq)[:, None] * Nt
+                                          + inv.qoi_time_steps(Nt, stride)[None, :]).reshape(-1)),
+}
+
+
+def test_unmutated_oracle_passes_every_pin():
+    assert _first_failing_pin() is None
+
+
+@pytest.mark.parametrize("case", sorted(MUTANTS))
+def test_a_pin_catches_the_planted_mistake(case):
+    name, make = MUTANTS[case]
+    with _planted(name, make):
+        caught_by = _first_failing_pin()
+    assert caught_by is not None, f"no pin fails when {name} carries the mistake '{case}'"
