@@ -565,8 +565,7 @@ bti_status bti_create(int64_t Nm, int64_t Nd, int64_t Nq, int64_t Nt, int device
   // status[0]: first bad Cholesky pivot; status[1]: a bounded device wait gave up
   if (cudaMalloc(&h->status, 2 * sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
-    cudaFree(h->plan.tw64);
-    cudaFree(h->plan.tw32);
+    fft_plan_free(h->plan);
     delete h;
     return BTI_ERR_OOM;
   }
@@ -580,11 +579,7 @@ bti_status bti_destroy(bti_handle h) {
   cudaSetDevice(h->device);
   cudaStreamSynchronize(h->stream);
   for (auto* set : {h->op, h->shadow})
-    for (int i = 0; i < 3; ++i) {
-      dev_free(set[i].hat);
-      dev_freep(set[i].time);
-      dev_freep(set[i].scale);
-    }
+    for (int i = 0; i < 3; ++i) drop_store(set[i]);  // spectral blocks, time copies, scales, digit planes
   dev_freep(h->prior_axes);
   dev_freep(h->pinv);
   dev_freep(h->noise_diag);
@@ -601,9 +596,7 @@ bti_status bti_destroy(bti_handle h) {
   dev_free(h->ws);
   dev_freep(h->wsolve);
   drop_online_graph_any(h);
-  dev_freep(h->plan.tw64);
-  dev_freep(h->plan.tw32);
-  dev_freep(h->plan.twff);
+  fft_plan_free(h->plan);
   for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
   delete h;
   return BTI_OK;

@@ -118,6 +118,7 @@ struct FftPlan {
 };
 
 bool fft_plan_make(FftPlan& p, int L);   // host: factor L, choose P; false if unsupported
+void fft_plan_free(FftPlan& p);          // host: release the twiddle tables (null entries are skipped)
 // The same factorisation without the twiddle tables (tw64 / tw32 left null for the caller to set).
 bool fft_plan_factor(FftPlan& p, int L);
 

@@ -31,6 +31,15 @@ struct FftDesc {
   int radix[kMaxPasses];
 };
 
+void fft_plan_free(FftPlan& p) {
+  cudaFree(p.tw64);
+  cudaFree(p.tw32);
+  cudaFree(p.twff);
+  p.tw64 = nullptr;
+  p.tw32 = nullptr;
+  p.twff = nullptr;
+}
+
 bool fft_plan_make(FftPlan& p, int L) {
   if (L < 2 || L > kMaxL) return false;
   int n = L, np = 0;
@@ -63,9 +72,11 @@ bool fft_plan_make(FftPlan& p, int L) {
     tff[k].x = ffloat(t64[k].x);
     tff[k].y = ffloat(t64[k].y);
   }
-  if (cudaMalloc(&p.tw64, sizeof(double2) * L) != cudaSuccess) return false;
-  if (cudaMalloc(&p.tw32, sizeof(float2) * L) != cudaSuccess) return false;
-  if (cudaMalloc(&p.twff, sizeof(ffc) * L) != cudaSuccess) return false;
+  if (cudaMalloc(&p.tw64, sizeof(double2) * L) != cudaSuccess || cudaMalloc(&p.tw32, sizeof(float2) * L) != cudaSuccess ||
+      cudaMalloc(&p.twff, sizeof(ffc) * L) != cudaSuccess) {
+    fft_plan_free(p);  // no table outlives a failed plan
+    return false;
+  }
   cudaMemcpy(p.tw64, t64.data(), sizeof(double2) * L, cudaMemcpyHostToDevice);
   cudaMemcpy(p.tw32, t32.data(), sizeof(float2) * L, cudaMemcpyHostToDevice);
   cudaMemcpy(p.twff, tff.data(), sizeof(ffc) * L, cudaMemcpyHostToDevice);
