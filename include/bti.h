@@ -99,7 +99,11 @@ bti_status bti_set_stream(bti_handle h, void* cuda_stream);
  * FQ; block k is F_k.  The spectral blocks hat_F_w = sum_k F_k e^{-2 pi i k w / L}
  * (w = 0..N_t) are kept in `store` precision, layout [N_t+1][R][N_m] complex.
  * The caller's buffer is read during the call's stream work only.  Calling
- * again replaces the operator (and invalidates K for OP_F / OP_G). */
+ * again replaces the operator and releases its digit planes (bti_set_digit_planes).
+ * It invalidates Q and Gamma_post(q) (rebuild with bti_build_Q), and for OP_F / OP_G
+ * also K with its factor and inverse.  Replacing OP_F also releases a G that
+ * bti_set_prior_* formed from the old F; calls that need G return BTI_ERR_STATE
+ * until the prior is set again. */
 bti_status bti_set_blocks(bti_handle h, bti_op op, const double* blocks, bti_prec store);
 
 /* Build the G operator from the stored F time-domain blocks and a squared-
@@ -132,7 +136,7 @@ bti_status bti_set_prior_elliptic_grid(bti_handle h, int gx, int gy, double alph
 bti_status bti_set_dense_precision(bti_handle h, bti_prec arith);
 
 /* Gamma_noise: sigma2 * I if `diag` is NULL, otherwise diag (device, FP64,
- * [N_t][N_d] variances, all > 0).  Invalidates K. */
+ * [N_t][N_d] variances, all > 0).  Invalidates K, Q and Gamma_post(q). */
 bti_status bti_set_noise(bti_handle h, double sigma2, const double* diag);
 
 /* d = F m for B vectors: m [B][N_t][N_m] -> d [B][N_t][N_d] (Eq. (2.6)),

@@ -56,6 +56,7 @@ struct bti_ctx {
   double sigma2 = 0.0;
   double* noise_diag = nullptr;  // [Nt][Nd] or null
   bool prior_set = false;        // prior of bti_set_prior_se_grid / _elliptic_grid (also applied to F_q)
+  bool g_from_prior = false;     // the G blocks were formed from F's by that prior (not bti_set_blocks)
   int prior_kind = 0;            // 0: squared exponential C_x (x) C_y; 1: elliptic (A_s^2)^{-1} by DCT
   int prior_gx = 0, prior_gy = 0;
   double prior_ell = 0.0, prior_sigma = 0.0;
@@ -250,10 +251,13 @@ bti_status store_op(bti_ctx* h, bti_op opi, const double* blocks, bti_prec store
   if (R <= 0) return fail(h, BTI_ERR_SHAPE, "operator has zero rows (N_q = 0?)");
   drop_store(h->shadow[opi]);  // a shadow copy describes the blocks being replaced
   if (opi != BTI_OP_FQ) dev_freep(h->pinv);
-  dev_free(o.hat);
-  dev_freep(o.time);
-  dev_freep(o.scale);
-  o.set = false;
+  drop_store(o);  // the old blocks' spectra, time copy, scales and digit planes
+  if (opi == BTI_OP_F && h->g_from_prior) {  // G = F Gamma_prior was formed from the old F
+    drop_store(h->op[BTI_OP_G]);
+    drop_store(h->shadow[BTI_OP_G]);
+  }
+  if (opi != BTI_OP_FQ) h->g_from_prior = false;
+  h->Q_built = h->covq_built = false;  // Q = F_q G^* K^{-1} involves every operator
   o.R = R;
   o.prec = store;
   size_t hat_bytes = (size_t)h->nf * R * h->Nm * celem_size(store);
@@ -671,6 +675,7 @@ bti_status set_prior_common(bti_ctx* h, int gx, int gy, int kind, const std::vec
   drop_online_graph_any(h);
   dev_freep(h->prior_axes);
   h->prior_set = false;
+  h->g_from_prior = false;
   // the previous G (and its shadow copy) goes first, so the peak holds one set of G blocks
   drop_store(h->op[BTI_OP_G]);
   drop_store(h->shadow[BTI_OP_G]);
@@ -706,6 +711,7 @@ bti_status set_prior_common(bti_ctx* h, int gx, int gy, int kind, const std::vec
     if (st == BTI_OK) st = make_spectral(h, o, o.time);
     if (st == BTI_OK) {
       o.set = true;
+      h->g_from_prior = true;
       h->K_built = false;
       h->K_factored = false;
     }
@@ -805,6 +811,7 @@ bti_status bti_set_noise(bti_handle h, double sigma2, const double* diag) {
   h->noise_set = true;
   h->K_built = false;
   h->K_factored = false;
+  h->Q_built = h->covq_built = false;
   return BTI_OK;
 }
 

@@ -624,6 +624,72 @@ def test_online_qoi_via_d2q_map_on_tensor_cores(B):
     h.close()
 
 
+def test_replacing_blocks_drops_what_was_derived_from_them():
+    """bti_set_blocks on an operator that is already set must take effect everywhere:
+    - the old blocks' digit planes go, so B >= 16 products use the new blocks;
+    - Q goes when any operator or the noise changes;
+    - a G that a prior formed from the old F goes;
+    - calls that need what was dropped return BTI_ERR_STATE until it is rebuilt."""
+    p, F, Fq, G, _ = tiny_problem()
+    B = 16
+    rng = np.random.default_rng(5)
+    F2 = F * (1.0 + 0.5 * rng.standard_normal(F.shape))
+    Fq2 = Fq * (1.0 + 0.5 * rng.standard_normal(Fq.shape))
+    m = p.vectors_m(B)
+    d = p.vectors_d(B)
+    h = make_handle(F, Fq, bti.DF64)
+    h.set_prior_se_grid(p.gx, p.gy, p.ell, p.sigma_p, bti.DF64)
+    h.set_noise(p.sigma2)
+    h.set_dense_precision(bti.DF64)
+    for op in (bti.OP_F, bti.OP_G, bti.OP_FQ):
+        h.set_digit_planes(op, True)
+    h.build_K()
+    h.factor_K()
+    h.build_Q()
+    out_d = torch.empty((B, p.Nt, p.Nd), dtype=torch.float64, device="cuda")
+    out_q = torch.empty((B, p.Nt, p.Nq), dtype=torch.float64, device="cuda")
+    h.apply_F(cuda(m), out_d)
+    assert relb(host(out_d), oracle.p2o_apply(F, m)) < 1e-12
+
+    def state_error(fn, *args):
+        with pytest.raises(bti.BtiError) as e:
+            fn(*args)
+        assert e.value.status == 3
+
+    h.set_blocks(bti.OP_F, cuda(F2), bti.DF64)
+    h.apply_F(cuda(m), out_d)
+    assert relb(host(out_d), oracle.p2o_apply(F2, m)) < 1e-12
+    state_error(h.apply_Q, cuda(d), out_q)
+    state_error(h.build_K)  # G was formed from the old F
+    state_error(h.apply_Gstar, cuda(d), torch.empty((B, p.Nt, p.Nm), dtype=torch.float64, device="cuda"))
+    h.set_prior_se_grid(p.gx, p.gy, p.ell, p.sigma_p, bti.DF64)
+    h.set_digit_planes(bti.OP_F, True)
+    h.set_digit_planes(bti.OP_G, True)
+    h.profile_enable(True)
+    h.profile_read()
+    h.apply_F(cuda(m), out_d)
+    assert h.profile_read()[0]["prod_fwd"][1] == 3  # the digit-plane path again, on the new planes
+    h.profile_enable(False)
+    assert relb(host(out_d), oracle.p2o_apply(F2, m)) < 1e-12
+    Cs = oracle.se_covariance(p.gx, p.gy, p.ell, p.sigma_p)
+    G2 = oracle.prior_blocks(F2, Cs)
+    h.build_K()
+    h.factor_K()
+    h.build_Q()
+    h.apply_Q(cuda(d), out_q)
+    q_or = (d.reshape(B, -1) @ oracle.d2q_map(Fq, F2, G2, p.sigma2).T).reshape(B, p.Nt, p.Nq)
+    assert relb(host(out_q), q_or) < 1e-10
+
+    h.set_blocks(bti.OP_FQ, cuda(Fq2), bti.DF64)
+    state_error(h.apply_Q, cuda(d), out_q)
+    h.apply_Fq(cuda(m), out_q)
+    assert relb(host(out_q), oracle.p2o_apply(Fq2, m)) < 1e-12
+    h.build_Q()
+    h.set_noise(2.0 * p.sigma2)
+    state_error(h.apply_Q, cuda(d), out_q)
+    h.close()
+
+
 def test_posterior_covariance_actions_and_prior_mean():
     """Gamma_prior v, Gamma_post(m) v (Eq. (4.7)), pointwise posterior variances from unit
     vectors, and m_map with a nonzero prior mean (Eq. (4.13) with Eq. (4.8))."""
