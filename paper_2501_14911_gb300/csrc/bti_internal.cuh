@@ -2,12 +2,28 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdint>
 #include <string>
 
 #include "../../include/bti.h"
 
 namespace bti {
+
+// Runs a set-up step once for each CUDA device of the process.  Kernel attributes such as the
+// dynamic shared-memory limit belong to the device the module is loaded on, so a step done
+// once per process would leave the other devices of a multi-device process without them.
+struct PerDeviceOnce {
+  std::atomic<unsigned long long> done{0};
+  template <typename Fn> void operator()(Fn fn) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done.load(std::memory_order_acquire) & bit) return;
+    fn();
+    done.fetch_or(bit, std::memory_order_acq_rel);
+  }
+};
 
 // ----------------------------------------------------------------- complex helpers
 template <typename T> struct cplx;

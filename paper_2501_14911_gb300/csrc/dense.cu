@@ -759,15 +759,16 @@ constexpr size_t kinv_smem_bytes(int BM, int BR) { return sizeof(float2) * 2 * K
 // kernel's dynamic shared-memory limit)
 template <int BM, int BR, int TM, int TR>
 int kinv_resident() {
-  static int occ = 0;
-  if (occ == 0) {
+  static PerDeviceOnce attr;
+  static std::atomic<int> occ{1};
+  attr([] {
     cudaFuncSetAttribute(kinv_apply_kernel<BM, BR, TM, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kinv_smem_bytes(BM, BR));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kinv_apply_kernel<BM, BR, TM, TR>, 256,
-                                                  kinv_smem_bytes(BM, BR));
-    if (occ <= 0) occ = 1;
-  }
-  return occ;
+    int o = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kinv_apply_kernel<BM, BR, TM, TR>, 256, kinv_smem_bytes(BM, BR));
+    occ.store(o > 0 ? o : 1);
+  });
+  return occ.load();
 }
 struct KinvPlan {
   int BM, BR;

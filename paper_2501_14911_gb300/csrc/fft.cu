@@ -449,16 +449,15 @@ void launch_rfft_cols(const FftPlan& p, int Nt, const TI* x, int64_t ld, int64_t
   if (ncols <= 0 || B <= 0) return;
   FftDesc D = desc_of(p);
   size_t smem = 2 * sizeof(C2<T>) * (size_t)p.P * fft_slots(p.L);
-  static bool attr_set = false;
-  if (!attr_set) {
+  static PerDeviceOnce attr;
+  attr([] {
     cudaFuncSetAttribute(rfft_cols_kernel<T, TI, TO, kRadixPow2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          200 * 1024);
     cudaFuncSetAttribute(rfft_cols_kernel<T, TI, TO, kRadix25>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          200 * 1024);
     cudaFuncSetAttribute(rfft_cols_kernel<T, TI, TO, kRadixAll>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          200 * 1024);
-    attr_set = true;
-  }
+  });
   const int rs = radix_set(p);
   int64_t gx = (ncols + 2 * p.P - 1) / (2 * p.P);
   for (int64_t b0 = 0; b0 < B; b0 += 65535) {
@@ -485,16 +484,15 @@ void launch_irfft_cols(const FftPlan& p, int Nt, const C2<TYI>* X, int64_t ld, i
   if (ncols <= 0 || B <= 0) return;
   FftDesc D = desc_of(p);
   size_t smem = 2 * sizeof(C2<T>) * (size_t)p.P * fft_slots(p.L);
-  static bool attr_set = false;
-  if (!attr_set) {
+  static PerDeviceOnce attr;
+  attr([] {
     cudaFuncSetAttribute(irfft_cols_kernel<T, TYI, TO, kRadixPow2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          200 * 1024);
     cudaFuncSetAttribute(irfft_cols_kernel<T, TYI, TO, kRadix25>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          200 * 1024);
     cudaFuncSetAttribute(irfft_cols_kernel<T, TYI, TO, kRadixAll>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          200 * 1024);
-    attr_set = true;
-  }
+  });
   const int rs = radix_set(p);
   const int os = ostride < 1 ? 1 : ostride;
   int64_t gx = (ncols + 2 * p.P - 1) / (2 * p.P);

@@ -159,12 +159,11 @@ void launch_prod_fwd(const C2<TS>* Fhat, const C2<T>* mhat, C2<T>* partial,
   size_t smem = sizeof(C2<T>) * (size_t)bg * JC;
   dim3 grid((unsigned)nchunk, (unsigned)nf, (unsigned)((B + bg - 1) / bg));
   constexpr int U1 = sizeof(C2<TS>) >= 16 ? 8 : 16;  // 128 bytes of loads per lane per step
-  static bool attr = false;
-  if (!attr) {
+  static PerDeviceOnce attr;
+  attr([] {
     cudaFuncSetAttribute(prod_fwd_kernel<T, TS, 4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmemMax);
     cudaFuncSetAttribute(prod_fwd_kernel<T, TS, 1, U1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmemMax);
-    attr = true;
-  }
+  });
   if (bg == 4)
     prod_fwd_kernel<T, TS, 4, 4><<<grid, 256, smem, s>>>(Fhat, mhat, partial, nf, R, Nm, B, JC, nchunk);
   else
@@ -430,12 +429,11 @@ void launch_prod_fwd_df64(const float4* Fhat, const double2* mhat, double2* part
   int nchunk = fwd_nchunk<double>(Nm, B, &JC, jc);
   size_t smem = sizeof(float4) * (size_t)bg * JC;
   dim3 grid((unsigned)nchunk, (unsigned)nf, (unsigned)((B + bg - 1) / bg));
-  static bool attr = false;
-  if (!attr) {
+  static PerDeviceOnce attr;
+  attr([] {
     cudaFuncSetAttribute(prod_fwd_df64_kernel<4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmemMax);
     cudaFuncSetAttribute(prod_fwd_df64_kernel<1, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmemMax);
-    attr = true;
-  }
+  });
   if (bg == 4)
     prod_fwd_df64_kernel<4, 4><<<grid, 256, smem, s>>>(Fhat, mhat, partial, nf, R, Nm, B, JC, nchunk);
   else
@@ -531,12 +529,11 @@ template <int BG, int VPT>
 static void adj_df64_launch(const float4* Fhat, const double2* dhat, double2* mhat, int64_t nf, int64_t R,
                             int64_t Nm, int64_t B, cudaStream_t s) {
   size_t smem = sizeof(float4) * (size_t)BG * (R < kAdjRows ? R : kAdjRows);
-  static bool attr = false;  // 8 vectors x 512 staged rows take 64 KB
-  if (!attr) {
+  static PerDeviceOnce attr;  // 8 vectors x 512 staged rows take 64 KB
+  attr([] {
     cudaFuncSetAttribute(prod_adj_df64_kernel<BG, VPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(sizeof(float4) * BG * kAdjRows));
-    attr = true;
-  }
+  });
   dim3 grid((unsigned)((Nm + 256 * VPT - 1) / (256 * VPT)), (unsigned)nf, (unsigned)((B + BG - 1) / BG));
   prod_adj_df64_kernel<BG, VPT><<<grid, 256, smem, s>>>(Fhat, dhat, mhat, nf, R, Nm, B);
 }
@@ -688,12 +685,11 @@ void launch_prod_fwd_f16(const void* Fhat, const float* scale, const float2* mha
   int nchunk = fwd_nchunk<float>(Nm, B, &JC, jc);
   size_t smem = sizeof(float2) * (size_t)bg * JC;
   dim3 grid((unsigned)nchunk, (unsigned)nf, (unsigned)((B + bg - 1) / bg));
-  static bool attr = false;
-  if (!attr) {
+  static PerDeviceOnce attr;
+  attr([] {
     cudaFuncSetAttribute(prod_fwd_f16_kernel<4, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmemMax);
     cudaFuncSetAttribute(prod_fwd_f16_kernel<1, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmemMax);
-    attr = true;
-  }
+  });
   if (bg == 4)
     prod_fwd_f16_kernel<4, 8><<<grid, 256, smem, s>>>((const __half2*)Fhat, scale, mhat, partial, nf, R, Nm, B,
                                                       JC, nchunk);

@@ -476,12 +476,11 @@ sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 
 void kinv_tc_prepare() {
-  static bool attr = false;
-  if (!attr) {
+  static PerDeviceOnce attr;
+  attr([] {
     cudaFuncSetAttribute(sk_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sk_smem(64));
     cudaFuncSetAttribute(sk_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sk_smem(32));
-    attr = true;
-  }
+  });
 }
 
 int64_t kinv_tc_ld(int64_t n) { return (n + kKiChunk - 1) / kKiChunk * kKiChunk; }
@@ -968,11 +967,8 @@ cudaError_t adj_digits_apply(const void* planes, const int* ea, int64_t nf, int6
 }
 
 void adj_digits_prepare() {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(adj_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kKiSmem);
-    attr = true;
-  }
+  static PerDeviceOnce attr;
+  attr([] { cudaFuncSetAttribute(adj_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kKiSmem); });
 }
 
 
