@@ -141,3 +141,75 @@ def test_pair_to_double_conversion():
     assert pair_to_double_scaled(-1.5, 0.0, 3) == -12.0
     # a pair whose low part flips the sign of the residual and crosses a power of two
     assert pair_to_double_scaled(1.0, -2.0 ** -30, 0) == 1.0 - 2.0 ** -30
+
+
+def _complex_case(seed, R=7, Nm=9, B=3):
+    rng = np.random.default_rng(seed)
+    F = rng.standard_normal((R, Nm)) + 1j * rng.standard_normal((R, Nm))
+    m = rng.standard_normal((B, Nm)) + 1j * rng.standard_normal((B, Nm))
+    d = rng.standard_normal((B, R)) + 1j * rng.standard_normal((B, R))
+    return F, m, d
+
+
+def test_forward_complex_product_as_interleaved_real_gemm():
+    """d-hat[b][i] = sum_j F[i][j] m-hat[b][j] as D[n][i] = sum_k V[n][k] A[i][k], k = 2 j + c, with
+    A[i][2j] = Re F, A[i][2j+1] = Im F, V[2b] = (Re m, -Im m), V[2b+1] = (Im m, Re m)."""
+    F, m, _ = _complex_case(6)
+    R, Nm = F.shape
+    B = m.shape[0]
+    A = np.empty((R, 2 * Nm))
+    A[:, 0::2], A[:, 1::2] = F.real, F.imag
+    V = np.empty((2 * B, 2 * Nm))
+    V[0::2, 0::2], V[0::2, 1::2] = m.real, -m.imag
+    V[1::2, 0::2], V[1::2, 1::2] = m.imag, m.real
+    D = V @ A.T
+    ref = m @ F.T
+    np.testing.assert_allclose(D[0::2], ref.real, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(D[1::2], ref.imag, rtol=0, atol=1e-13)
+
+
+def test_adjoint_complex_product_as_interleaved_real_gemm():
+    """m-hat[b][j] = sum_i conj(F[i][j]) d-hat[b][i] as D[j][n] = sum_k A'[j][k] B[n][k], k = 2 i + c,
+    with A'[j][2i] = Re F, A'[j][2i+1] = Im F, B[2b] = (Re d, Im d), B[2b+1] = (Im d, -Re d)."""
+    F, _, d = _complex_case(7)
+    R, Nm = F.shape
+    B = d.shape[0]
+    Ap = np.empty((Nm, 2 * R))
+    Ap[:, 0::2], Ap[:, 1::2] = F.real.T, F.imag.T
+    Bv = np.empty((2 * B, 2 * R))
+    Bv[0::2, 0::2], Bv[0::2, 1::2] = d.real, d.imag
+    Bv[1::2, 0::2], Bv[1::2, 1::2] = d.imag, -d.real
+    D = Ap @ Bv.T
+    ref = d @ F.conj()
+    np.testing.assert_allclose(D[:, 0::2].T, ref.real, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(D[:, 1::2].T, ref.imag, rtol=0, atol=1e-13)
+
+
+def test_adjoint_digit_product_with_per_column_and_per_vector_scales():
+    """The whole adjoint pipeline in exact integer arithmetic: A' sliced with one exponent per
+    row j (a column of F-hat, over the contraction i), B with one per vector pair (2b, 2b+1);
+    the group sums are exact integers and the result matches the complex FP64 product to the
+    47-bit truncation."""
+    F, _, d = _complex_case(8, R=40, Nm=50, B=4)
+    F = F * np.exp(np.random.default_rng(9).standard_normal((1, F.shape[1])))  # columns of very different size
+    R, Nm = F.shape
+    B = d.shape[0]
+    Ap = np.empty((Nm, 2 * R))
+    Ap[:, 0::2], Ap[:, 1::2] = F.real.T, F.imag.T
+    Bv = np.empty((2 * B, 2 * R))
+    Bv[0::2, 0::2], Bv[0::2, 1::2] = d.real, d.imag
+    Bv[1::2, 0::2], Bv[1::2, 1::2] = d.imag, -d.real
+    P, ea = slice_rows(Ap)
+    # one exponent per vector: both rows of a pair share the larger row maximum
+    mx = np.maximum(np.abs(Bv[0::2]).max(axis=1), np.abs(Bv[1::2]).max(axis=1))
+    eb = np.repeat(np.frexp(mx)[1], 2)
+    Q = digits(np.rint(np.ldexp(Bv, (47 - eb)[:, None])).astype(np.int64))
+    acc = np.zeros((Nm, 2 * B))
+    for g in range(S):
+        G = sum(P[s].astype(np.int64) @ Q[g - s].astype(np.int64).T for s in range(g + 1))
+        assert np.abs(G).max() < 2 ** 24  # one 128-wide chunk: the FP32 sums are exact
+        acc += G.astype(np.float64) * 2.0 ** (-8 * g)
+    D = acc * np.ldexp(1.0, ea[:, None] + eb[None, :] - 14)
+    ref = d @ F.conj()
+    got = D[:, 0::2].T + 1j * D[:, 1::2].T
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-12
