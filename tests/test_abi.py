@@ -1,9 +1,11 @@
-"""The C ABI library builds, loads and exports every symbol the header declares.
+"""The C ABI library builds, loads and exports every symbol the header declares, and the
+binding's ctypes signatures match the header's prototypes.
 CPU only: no call here touches a GPU (only argument checks that fail before
 any CUDA call)."""
 
 import ctypes
 import os
+import re
 
 import pytest
 
@@ -58,3 +60,34 @@ def test_no_cpu_fallback_in_binding():
     src = open(os.path.join(ROOT, "paper_2501_14911_gb300", "_binding.py")).read()
     for forbidden in ("numpy", "torch.fft", "oracle", "@ ", "matmul", "einsum"):
         assert forbidden not in src, forbidden
+
+
+def _c_kind(param):
+    """Argument class of one C parameter: pointer, 64- or 32-bit integer, or double."""
+    p = " ".join(param.split())
+    if "*" in p or p.startswith("bti_handle"):
+        return "ptr"
+    return {"int64_t": "i64", "int": "i32", "double": "f64", "bti_op": "i32", "bti_prec": "i32"}[p.rsplit(" ", 1)[0]]
+
+
+def _py_kind(t):
+    if t in (ctypes.c_void_p, ctypes.c_char_p) or issubclass(t, ctypes._Pointer):
+        return "ptr"
+    if t is ctypes.c_double:
+        return "f64"
+    return {8: "i64", 4: "i32"}[ctypes.sizeof(t)]
+
+
+def test_binding_argtypes_match_the_header_prototypes(L):
+    """A ctypes signature that disagrees with the C prototype (an int where the C side takes
+    int64_t, a scalar where it takes a pointer) would corrupt arguments without an error."""
+    with open(os.path.join(ROOT, "include", "bti.h")) as f:
+        text = re.sub(r"/\*.*?\*/", "", f.read(), flags=re.S)
+    protos = re.findall(r"^\s*(bti_status|const char\s*\*)\s+(bti_\w+)\s*\(([^)]*)\)\s*;", text, re.M)
+    assert {name for _, name, _ in protos} == set(bti.header_symbols())
+    for ret, name, params in protos:
+        params = [q for q in (x.strip() for x in params.split(",")) if q and q != "void"]
+        fn = getattr(L, name)
+        assert fn.argtypes is not None, f"{name}: the binding sets no argtypes"
+        assert [_c_kind(q) for q in params] == [_py_kind(t) for t in fn.argtypes], name
+        assert fn.restype is (ctypes.c_int if ret == "bti_status" else ctypes.c_char_p), name
