@@ -91,3 +91,24 @@ def test_binding_argtypes_match_the_header_prototypes(L):
         assert fn.argtypes is not None, f"{name}: the binding sets no argtypes"
         assert [_c_kind(q) for q in params] == [_py_kind(t) for t in fn.argtypes], name
         assert fn.restype is (ctypes.c_int if ret == "bti_status" else ctypes.c_char_p), name
+
+
+def test_binding_constants_and_struct_match_the_header():
+    """The enum values, the kernel classes of the profile hook and bti_solve_info's layout as
+    the binding mirrors them."""
+    from paper_2501_14911_gb300 import _binding as b
+
+    with open(os.path.join(ROOT, "include", "bti.h")) as f:
+        text = re.sub(r"/\*.*?\*/", "", f.read(), flags=re.S)
+    enum = {k: int(v) for k, v in re.findall(r"\b(BTI_\w+)\s*=\s*(\d+)", text)}
+    assert (b.OP_F, b.OP_G, b.OP_FQ) == (enum["BTI_OP_F"], enum["BTI_OP_G"], enum["BTI_OP_FQ"])
+    assert (b.F64, b.F32, b.DF64, b.F16) == tuple(enum["BTI_P_" + t] for t in ("F64", "F32", "DF64", "F16"))
+    assert b.STATUS == {v: k for k, v in enum.items() if k == "BTI_OK" or k.startswith("BTI_ERR_")}
+    kcls = ["RFFT", "PROD_FWD", "REDUCE", "IRFFT", "PROD_ADJ", "DENSE"]
+    assert len(b.KCLASSES) == enum["BTI_K_NCLASS"]
+    assert [enum["BTI_K_" + k] for k in kcls] == list(range(len(kcls)))
+    assert list(b.KCLASSES) == [k.lower() for k in kcls]
+    body = re.search(r"typedef struct \{([^}]*)\} bti_solve_info;", text).group(1)
+    fields = [tuple(x.split()) for x in body.replace("\n", " ").split(";") if x.strip()]
+    ct = {"int": ctypes.c_int, "double": ctypes.c_double}
+    assert [(n, ct[t]) for t, n in fields] == list(b.SolveInfo._fields_)
