@@ -168,7 +168,10 @@ void launch_reduce_chunks(const C2<T>* partial, C2<T>* dhat, int64_t nf, int64_t
                           int64_t B, cudaStream_t s, int jc = 0);
 size_t prod_fwd_partial_elems(int64_t nf, int64_t R, int64_t Nm, int64_t B);
 // Double-FP32 tier: spectral blocks as (re_hi, re_lo, im_hi, im_lo) float quads.
-void launch_split_df64(void* hat, int64_t n, cudaStream_t s);  // in place, from complex FP64
+// in place, from complex FP64 scaled by 2^-pexp
+void launch_split_df64(void* hat, int64_t n, int pexp, cudaStream_t s);
+// *out = bit pattern of max |x[i]| (a non-negative double; a NaN input reads as a NaN)
+void launch_max_abs(const double* x, int64_t n, unsigned long long* out, cudaStream_t s);
 void launch_prod_fwd_df64(const float4* Fhat, const double2* mhat, double2* partial, int64_t nf,
                           int64_t R, int64_t Nm, int64_t B, cudaStream_t s, int jc = 0);
 void launch_prod_adj_df64(const float4* Fhat, const double2* dhat, double2* mhat, int64_t nf, int64_t R,
@@ -225,6 +228,22 @@ size_t kinv_apply_work_elems(int64_t n, int64_t B);
 int64_t kinv_apply(const float2* Kinv, int64_t n, const double* D, int64_t B, double* X, double* work,
                    cudaStream_t s);
 int split_to_pairs(const double* X, float2* Y, int64_t n, int64_t ldk, cudaStream_t s);
+// rows x n FP64 (row stride ldx) -> float pairs [rows][ldk], zeros in columns n .. ldk-1
+int split_rows_to_pairs_ld(const double* X, int64_t ldx, float2* Y, int64_t rows, int64_t n, int64_t ldk,
+                           cudaStream_t s);
+// Few right-hand sides (gemv.cu), float-pair arithmetic, HBM-bound:
+// symv_lower_pairs: X [1][n] = A D for the symmetric n x n float-pair matrix A (row stride lda,
+// a multiple of 16, zeros past column n) reading its lower triangle only (B = 1; returns 0
+// launches otherwise); work of symv_pairs_work_elems(n, 1) doubles.  gemv_pairs: Y [B][ldy] =
+// A D[b] for a rows x cols float-pair matrix (row stride lda, a multiple of 4, zeros past column
+// cols), B = 1 or 2 (0 launches otherwise); work of gemv_pairs_work_elems(cols, B) doubles.
+int64_t symv_pairs_ldx(int64_t n);
+size_t symv_pairs_work_elems(int64_t n, int64_t B);
+int64_t symv_lower_pairs(const float2* A, int64_t lda, int64_t n, const double* D, int64_t B, double* X,
+                         double* work, cudaStream_t s);
+size_t gemv_pairs_work_elems(int64_t cols, int64_t B);
+int64_t gemv_pairs(const float2* A, int64_t lda, int64_t rows, int64_t cols, const double* D, int64_t B, double* Y,
+                   int64_t ldy, double* work, cudaStream_t s);
 // the same sum with partial tiles of BM rows x BR right-hand sides (both kinv paths)
 int kinv_reduce(const double* part, double* X, int64_t ldx, int64_t n, int64_t nb, int BM, int BR, int64_t per,
                 int64_t kpt, int span, int64_t tiles, cudaStream_t s);

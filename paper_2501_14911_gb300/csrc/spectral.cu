@@ -318,17 +318,53 @@ __device__ __forceinline__ double ff_to_d(float h, float l) { return (double)h +
 
 }  // namespace
 
-// In place: a complex FP64 array becomes (re_hi, re_lo, im_hi, im_lo) float quads.
-__global__ void split_df64_kernel(double2* a, int64_t n) {
+// In place: a complex FP64 array times 2^-pexp (exact) becomes (re_hi, re_lo, im_hi, im_lo)
+// float quads.  The power of two brings the largest entry near 1, so that the pairs keep their
+// 48 bits whatever the operator's units (FP32's exponent range is far narrower than FP64's).
+__global__ void split_df64_kernel(double2* a, int64_t n, int pexp) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double2 v = a[i];
-  ff re = split_d(v.x), im = split_d(v.y);
+  ff re = split_d(scalbn(v.x, -pexp)), im = split_d(scalbn(v.y, -pexp));
   reinterpret_cast<float4*>(a)[i] = make_float4(re.h, re.l, im.h, im.l);
 }
 
-void launch_split_df64(void* hat, int64_t n, cudaStream_t s) {
-  if (n > 0) split_df64_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((double2*)hat, n);
+void launch_split_df64(void* hat, int64_t n, int pexp, cudaStream_t s) {
+  if (n > 0) split_df64_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((double2*)hat, n, pexp);
+}
+
+// out = max |x[i]| over n doubles, as the bit pattern of a non-negative double (which orders
+// like an unsigned integer, so atomicMax reduces it); a NaN reads above every finite value.
+// *out must be 0 before the launch.
+__global__ void max_abs_kernel(const double* __restrict__ x, int64_t n, unsigned long long* out) {
+  double m = 0.0;
+  unsigned long long nan = 0ull;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = fabs(x[i]);
+    if (v != v) nan = 0x7FF8000000000000ull;
+    m = fmax(m, v);
+  }
+  unsigned long long b = (unsigned long long)__double_as_longlong(m);
+  if (nan) b = nan;
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long c = __shfl_xor_sync(0xffffffffu, b, o);
+    b = c > b ? c : b;
+  }
+  __shared__ unsigned long long red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = b;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) b = red[w] > b ? red[w] : b;
+    atomicMax(out, b);
+  }
+}
+
+void launch_max_abs(const double* x, int64_t n, unsigned long long* out, cudaStream_t s) {
+  cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
+  if (n <= 0) return;
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  max_abs_kernel<<<(unsigned)blocks, 256, 0, s>>>(x, n, out);
 }
 
 // Forward product, double-FP32 arithmetic.  Same decomposition as prod_fwd_kernel:
