@@ -63,13 +63,23 @@ typedef enum { BTI_OP_F = 0, BTI_OP_G = 1, BTI_OP_FQ = 2 } bti_op;
 
 /* Storage / arithmetic tier of the spectral blocks, and (F64, F32 only) vector precision.
  * BTI_P_F64 : spectral blocks complex FP64, FFTs and products FP64.
- * BTI_P_F32 : spectral blocks complex FP32, FFTs and products FP32.
+ * BTI_P_F32 : spectral blocks complex FP32, FFTs and products FP32 (so blocks
+ *             and vectors within FP32's range, about 1e-30 .. 1e30 in magnitude).
  * BTI_P_DF64: spectral blocks as pairs of FP32 (hi + lo, about 48 significant
  *             bits; 16 bytes per complex like FP64), products in double-FP32
- *             arithmetic on the FP32 pipes with error-free accumulation; FFTs
- *             and vectors FP64.  FP64-level accuracy (well inside 1e-12) at
- *             the HBM rate, where GB300's FP64 pipe would bind first.
- *             Valid as a storage tier only, not as an io type.
+ *             arithmetic on the FP32 pipes with error-free accumulation; the
+ *             FFTs in float pairs as well; input and output vectors FP64.
+ *             FP64-level accuracy (well inside 1e-12) at the HBM rate, where
+ *             GB300's FP64 pipe would bind first.  Valid as a storage tier
+ *             only, not as an io type.  Range: float pairs have FP32's exponent
+ *             range, so the spectral blocks are stored divided by the power of
+ *             two that puts their largest entry in [1/2, 1), and every output
+ *             is multiplied back (both exact): operators in any units within
+ *             FP64's range keep the FP64-level accuracy.  Input vectors must
+ *             have their entries within about 2^-90 .. 2^90 (1e-27 .. 1e27) of
+ *             one: below that their low parts underflow, above it the float-pair
+ *             sums can overflow.  set_blocks returns BTI_ERR_ARG for blocks
+ *             holding a non-finite value.
  * BTI_P_F16 : spectral blocks as FP16 complex pairs (4 bytes per complex) with one
  *             power-of-two FP32 scale per frequency row; products with FP32
  *             accumulation, FFTs and vectors FP32.  About 1e-3 relative: the
@@ -158,16 +168,17 @@ bti_status bti_apply_Fq(bti_handle h, const void* m, void* q, int64_t B, bti_pre
  * d [B][N_t][N_d] -> m [B][N_t][N_m]. */
 bti_status bti_apply_Gstar(bti_handle h, const void* d, void* m, int64_t B, bti_prec io);
 
-/* Assemble K = Gamma_noise + F G^* in FP64 on the device (Sec. 4, Phase 2),
- * lower triangle only (the strict upper triangle is left undefined).
+/* Assemble K = Gamma_noise + F G^* on the device (Sec. 4, Phase 2), lower
+ * triangle only (the strict upper triangle is left undefined), stored in FP64.
+ * The Gram product W = F_stack G_stack^T that holds the work runs in the dense
+ * arithmetic of bti_set_dense_precision: FP64 FMA by default; under BTI_P_DF64
+ * float pairs (about 48 significant bits), or, with tensor cores also on, exact
+ * FP16 digit planes on tcgen05 (a 47-bit image of each row); the block-diagonal
+ * prefix sums and the noise are FP64 either way.
  * Requires F and G (either tier; the FP64 time-domain blocks kept by
  * set_blocks are used) and set_noise.  col_block (> 0) is the column-panel
  * width of the assembly; 512 is the default when 0 is passed. */
 bti_status bti_build_K(bti_handle h, int64_t col_block);
-
-/* (With bti_set_dense_precision(BTI_P_DF64) and tensor cores on, the Gram product
- * W = F_stack G_stack^T of bti_build_K runs on tcgen05 as an exact FP16 digit-plane product,
- * about 47 significant bits, like the double-FP32 GEMM it replaces.) */
 
 /* As bti_build_K, with the Gram product that assembles K computed in `assembly`
  * precision: BTI_P_F64 (same as bti_build_K) or BTI_P_F32 (FP32 products and
@@ -179,7 +190,10 @@ bti_status bti_build_K(bti_handle h, int64_t col_block);
  * below one. */
 bti_status bti_build_K_prec(bti_handle h, int64_t col_block, bti_prec assembly);
 
-/* Cholesky-factor K = L L^T in place (FP64, lower).  Synchronises; returns
+/* Cholesky-factor K = L L^T in place (lower triangle, stored in FP64).  The
+ * 64 x 64 diagonal-block factorisations are FP64; the panel and trailing updates
+ * run in the arithmetic of bti_set_dense_precision (FP64 FMA by default, float
+ * pairs with about 48 significant bits under BTI_P_DF64).  Synchronises; returns
  * BTI_ERR_NOT_SPD (message names the 1-based pivot) if a pivot is <= 0 or
  * not finite. */
 bti_status bti_factor_K(bti_handle h);
@@ -196,7 +210,8 @@ bti_status bti_copy_K(bti_handle h, double* dst);
  * bti_infer_map and bti_online then apply K^{-1} as one dense product instead of the n / 64
  * sequential blocked solves: for B >= 16 vectors with tensor cores on, as exact FP16
  * digit-plane MMAs on tcgen05 (K^{-1} formed as W^T W with W = L^{-1}, the product on the
- * tensor cores too); otherwise in double-FP32 arithmetic (about 48 significant bits).  The inverse belongs to the factor it was formed from: after a new
+ * tensor cores too); otherwise in double-FP32 arithmetic (about 48 significant bits), for a
+ * single vector by a symmetric product that reads K^{-1}'s lower triangle only.  The inverse belongs to the factor it was formed from: after a new
  * bti_factor_K the solves return to the factor until this is called again.
  * enable = 0 releases the inverse.  Requires factor_K for enable = 1 (BTI_ERR_STATE);
  * BTI_ERR_OOM if the 16 n^2-byte peak (inverse plus FP64 temporary) does not fit.
@@ -287,8 +302,9 @@ bti_status bti_set_tensor_cores(bti_handle h, int on);
 
 /* Failure-handling test hook: while stage >= 0, the tensor-core kernels that stream an
  * operand by TMA (the FP16 tier's forward product, and the digit-plane products of
- * bti_set_digit_planes, bti_invert_K and bti_set_online_qoi) withhold that pipeline stage's
- * tile in every CTA, so their bounded waits (about a second) run out; the kernel then
+ * bti_set_digit_planes, bti_invert_K and bti_set_online_qoi) withhold the stage-th tile load
+ * (counting from 0; a 32-column box of all digit planes in the digit-plane kernels) in every
+ * CTA that issues that many, so their bounded waits (about a second) run out; the kernel then
  * stops, drains what it issued, frees its tensor memory and sets the device status word
  * that bti_sync reports as BTI_ERR_TIMEOUT.  The handle and the CUDA context stay usable.
  * -1 (the default) turns it off. */
@@ -390,8 +406,11 @@ bti_status bti_copy_Q(bti_handle h, double* Q_out, double* cov_out);
  * 128)(N_t N_d rounded up to 128) bytes), so that bti_apply_Q and the online graph apply
  * it on the tensor cores with FP64-level accuracy for B >= 16 while tensor cores are on.  via_Q = 0
  * (the default): q_map = F_q m_map (push-forward, as bti_predict_qoi); the planes are
- * released.  A later bti_build_Q makes the planes stale: apply_Q falls back to the dense
- * GEMM until this is called again.  Synchronises. */
+ * released.  via_Q = 1 also keeps Q as float pairs (8 (N_q N_t^q) (N_t N_d) bytes), which
+ * bti_apply_Q and the online graph read for one or two vectors per call (a matrix-vector
+ * product at the HBM rate, double-FP32 arithmetic).  A later bti_build_Q makes the planes
+ * and pairs stale: apply_Q falls back to the dense GEMM until this is called again.
+ * Synchronises. */
 bti_status bti_set_online_qoi(bti_handle h, int via_Q);
 
 /* q_map = F_q m_map (Eq. (4.2)): m_map [B][N_t][N_m] -> q_map [B][N_t][N_q],
@@ -457,7 +476,10 @@ const char* bti_last_error(bti_handle h);
  * (about 16 (N_t+1) N_m (N_d + B) bytes plus small terms) returns
  * BTI_ERR_SHAPE before anything is launched.  The first call on a device
  * resolves that array's device address (cudaGetSymbolAddress, with the device
- * current); make that first call before any stream capture.  Every call on a
+ * current) and keeps it with the current context; a later call in another
+ * context on that device (after cudaDeviceReset, or under a caller's own
+ * context) resolves it again, since each context holds its own copy of the
+ * array.  Make the first call in each context before any stream capture.  Every call on a
  * device shares the array, so calls that overlap on the GPU (other streams or
  * host threads) race and must be serialised by the caller.  Returns BTI_ERR_ARG
  * for null pointers, sizes <= 0 or an unsupported L = 2 N_t, BTI_ERR_CUDA if a

@@ -29,6 +29,7 @@ struct OpStore {
   int* dig_ex = nullptr;   // their exponents, one per (w, j)
   void* dig_f = nullptr;   // forward digit planes
   int* dig_f_ex = nullptr; // their exponents, one per (w, i)
+  int pexp = 0;            // double-FP32 tier: hat holds F-hat 2^-pexp; outputs are scaled back
 };
 
 }  // namespace
@@ -68,6 +69,8 @@ struct bti_ctx {
   void* Q_planes = nullptr;      // Q as FP16 digit planes for the tensor cores (bti_set_online_qoi)
   int* Q_ea = nullptr;           // their row exponents
   int64_t Qp_gen = -1;           // Q_gen the planes were formed from
+  float2* Q_pairs = nullptr;     // Q as float pairs [nq][kQpairLd(n)] for one or two vectors per call
+  int64_t Qpr_gen = -1;          // Q_gen the pairs were formed from
   bool online_via_Q = false;     // bti_online takes q_map = Q d_obs (Eq. (4.14))
   int qstride = 1;               // QoI time grid: every qstride-th step (N_t^q = N_t / qstride)
   double* K = nullptr;           // [n][n], lower triangle: K, then L after factor_K
@@ -221,8 +224,27 @@ bti_status make_spectral(bti_ctx* h, OpStore& o, const double* time_blocks) {
   else
     PROF(h, BTI_K_RFFT, (launch_rfft_cols<double, double, float>(h->plan, (int)h->Nt, time_blocks, cols, 0,
                                                                   (float2*)o.hat, 0, cols, 1, h->stream)));
-  if (o.prec == BTI_P_DF64)  // each FP64 complex becomes a (hi, lo) float pair per part, in place
-    PROF(h, BTI_K_RFFT, launch_split_df64(o.hat, h->nf * cols, h->stream));
+  o.pexp = 0;
+  if (o.prec == BTI_P_DF64) {
+    // each FP64 complex becomes a (hi, lo) float pair per part, in place, after an exact
+    // power-of-two scaling that puts the largest entry in [1/2, 1): float pairs have FP32's
+    // exponent range, and operators in physical units may sit far outside it
+    unsigned long long* mx = nullptr;
+    bti_status st = dev_alloc(h, (void**)&mx, sizeof(unsigned long long), "alloc max word");
+    if (st != BTI_OK) return st;
+    PROF(h, BTI_K_RFFT, launch_max_abs((const double*)o.hat, 2 * h->nf * cols, mx, h->stream));
+    unsigned long long bits = 0;
+    st = cuda_check(h, cudaMemcpyAsync(&bits, mx, sizeof bits, cudaMemcpyDeviceToHost, h->stream),
+                    "read block maximum");
+    if (st == BTI_OK) st = cuda_check(h, cudaStreamSynchronize(h->stream), "read block maximum");
+    dev_freep(mx);
+    if (st != BTI_OK) return st;
+    double m;
+    std::memcpy(&m, &bits, sizeof m);
+    if (!std::isfinite(m)) return fail(h, BTI_ERR_ARG, "set_blocks: the blocks hold a non-finite value");
+    if (m > 0.0) std::frexp(m, &o.pexp);
+    PROF(h, BTI_K_RFFT, launch_split_df64(o.hat, h->nf * cols, o.pexp, h->stream));
+  }
   return launched(h, "spectral blocks");
 }
 
@@ -235,6 +257,7 @@ void drop_store(OpStore& o) {
   dev_free(o.dig_f);
   dev_freep(o.dig_f_ex);
   o.hat = nullptr;
+  o.pexp = 0;
   o.set = false;
 }
 
@@ -323,7 +346,8 @@ void irfft_out(bti_ctx* h, const OpStore& o, const C2<T>* Y, int64_t ld, int64_t
   const int Nt = (int)h->Nt;
   cudaStream_t s = h->stream;
   const FftPlan plan = tuned_plan(h, o);
-  const double scale = 1.0 / (double)h->L;
+  // 1/L, times the power of two the stored double-FP32 blocks were divided by (exact)
+  const double scale = std::ldexp(1.0 / (double)h->L, o.pexp);
   if (o.prec == BTI_P_DF64) {
     if (io == BTI_P_F64)
       PROF(h, BTI_K_IRFFT, (launch_irfft_cols<ffloat, double, double>(plan, Nt, (const double2*)Y, ld, Ybstride,
@@ -591,6 +615,7 @@ bti_status bti_destroy(bti_handle h) {
   dev_freep(h->Q);
   dev_free(h->Q_planes);
   dev_freep(h->Q_ea);
+  dev_freep(h->Q_pairs);
   dev_freep(h->covq);
   dev_freep(h->Linv);
   dev_freep(h->Kinv);
@@ -796,22 +821,30 @@ bti_status bti_set_noise(bti_handle h, double sigma2, const double* diag) {
   bti_status st = check_handle(h);
   if (st != BTI_OK) return st;
   if (!diag && !(sigma2 > 0.0)) return fail(h, BTI_ERR_ARG, "set_noise: sigma2 must be > 0");
+  // everything derived from the old noise goes first, so that a failure below leaves no K,
+  // factor, Q or preconditioner built with a noise the handle no longer holds
   drop_online_graph_any(h);
-  dev_freep(h->noise_diag);
-  dev_freep(h->pinv);
-  h->sigma2 = sigma2;
-  if (diag) {
-    size_t bytes = sizeof(double) * (size_t)h->Nt * h->Nd;
-    st = dev_alloc(h, (void**)&h->noise_diag, bytes, "alloc noise");
-    if (st != BTI_OK) return st;
-    st = cuda_check(h, cudaMemcpyAsync(h->noise_diag, diag, bytes, cudaMemcpyDeviceToDevice, h->stream),
-                    "copy noise");
-    if (st != BTI_OK) return st;
-  }
-  h->noise_set = true;
+  h->noise_set = false;
   h->K_built = false;
   h->K_factored = false;
   h->Q_built = h->covq_built = false;
+  dev_freep(h->pinv);
+  double* nd = nullptr;
+  if (diag) {
+    size_t bytes = sizeof(double) * (size_t)h->Nt * h->Nd;
+    st = dev_alloc(h, (void**)&nd, bytes, "alloc noise");
+    if (st == BTI_OK)
+      st = cuda_check(h, cudaMemcpyAsync(nd, diag, bytes, cudaMemcpyDeviceToDevice, h->stream), "copy noise");
+    if (st != BTI_OK) {
+      dev_freep(nd);
+      return st;
+    }
+  }
+  // the new noise replaces the old one only once it is complete
+  dev_freep(h->noise_diag);
+  h->noise_diag = nd;
+  h->sigma2 = sigma2;
+  h->noise_set = true;
   return BTI_OK;
 }
 
@@ -1052,7 +1085,7 @@ static bti_status reserve_solve(bti_ctx* h, int64_t B) {
   const int64_t n = h->Nt * h->Nd;
   size_t tail = trsm_work_elems(n, B);
   if (kinv_ready(h))
-    tail = std::max(tail, (size_t)B * n + std::max(kinv_apply_work_elems(n, B),
+    tail = std::max(tail, (size_t)B * n + std::max(std::max(kinv_apply_work_elems(n, B), symv_pairs_work_elems(n, B)),
                                                    h->kinv_planes ? kinv_tc_work_elems(n) : (size_t)0));
   size_t need = sizeof(double) * ((size_t)2 * B * n + tail);
   size_t chol = sizeof(double) * (size_t)n * kCholNB;
@@ -1091,6 +1124,8 @@ static bti_status infer_map_impl(bti_handle h, const double* d_obs, double* m_ma
       if (e != cudaSuccess) tc_err = e;
       return nl;
     }
+    // one vector: the symmetric product reads K^{-1}'s lower triangle only
+    if (inv && B == 1) return symv_lower_pairs(h->Kinv, kinv_ld(n), n, v, 1, xo, work + (size_t)B * n, s);
     if (inv) return kinv_apply(h->Kinv, n, v, B, xo, work + (size_t)B * n, s);
     if (v != xo) cudaMemcpyAsync(xo, v, sizeof(double) * B * n, cudaMemcpyDeviceToDevice, s);
     return trsm_lower_f64(h->K, h->Linv, n, xo, B, work, h->status, s, h->dense_prec == BTI_P_DF64);
@@ -1243,6 +1278,9 @@ bti_status bti_build_Q(bti_handle h, int with_covariance) {
 }
 
 static bool Q_planes_ready(const bti_ctx* h) { return h->Q_planes && h->Q_built && h->Qp_gen == h->Q_gen; }
+static bool Q_pairs_ready(const bti_ctx* h) { return h->Q_pairs && h->Q_built && h->Qpr_gen == h->Q_gen; }
+// row stride of Q's float pairs (16-byte rows for the vector loads)
+static int64_t qpair_ld(int64_t n) { return (n + 3) / 4 * 4; }
 
 // Workspace of apply_Q's tensor-core form (in the dense-solve workspace, after x and r of
 // infer_map so that the online graph can run both).
@@ -1267,6 +1305,15 @@ static bti_status apply_Q_impl(bti_ctx* h, const double* d_obs, double* q_map, i
     if (e != cudaSuccess) return cuda_check(h, e, "tensor-core Q product");
     return launched(h, "apply_Q");
   }
+  if (Q_pairs_ready(h) && B <= 2) {
+    // one or two vectors: a matrix-vector product over Q's float pairs, HBM-bound
+    bti_status st = ensure(h, (void**)&h->wsolve, &h->wsolve_bytes,
+                           sizeof(double) * ((size_t)2 * B * n + gemv_pairs_work_elems(n, B)), "solve workspace");
+    if (st != BTI_OK) return st;
+    count_dense(h, gemv_pairs(h->Q_pairs, qpair_ld(n), nq, n, d_obs, B, q_map, nq, h->wsolve + (size_t)2 * B * n,
+                              h->stream));
+    return launched(h, "apply_Q");
+  }
   const bool dd = h->dense_prec == BTI_P_DF64 && B > 8;
   count_dense(h, (dd ? gemm_df64 : gemm_f64)(true, B, nq, n, 1.0, d_obs, n, 0, h->Q, n, 0, 0.0, q_map, nq, 0, 1,
                                              false, h->stream));
@@ -1281,11 +1328,17 @@ bti_status bti_set_online_qoi(bti_handle h, int via_Q) {
   cudaStreamSynchronize(h->stream);
   dev_free(h->Q_planes);
   dev_freep(h->Q_ea);
-  h->Qp_gen = -1;
+  dev_freep(h->Q_pairs);
+  h->Qp_gen = h->Qpr_gen = -1;
   h->online_via_Q = false;
   if (!via_Q) return BTI_OK;
   if (!h->Q_built) return fail(h, BTI_ERR_STATE, "set_online_qoi: Q not built");
   const int64_t n = h->Nt * h->Nd, nq = (h->Nt / h->qstride) * h->Nq;
+  // Q as float pairs: the one- and two-vector products read it at the HBM rate
+  st = dev_alloc(h, (void**)&h->Q_pairs, sizeof(float2) * (size_t)nq * qpair_ld(n), "alloc Q pairs");
+  if (st != BTI_OK) return st;
+  count_dense(h, split_rows_to_pairs_ld(h->Q, n, h->Q_pairs, nq, n, qpair_ld(n), h->stream));
+  h->Qpr_gen = h->Q_gen;
   if (kinv_tc_supported(n) && kinv_tc_supported(nq)) {
     st = dev_alloc(h, &h->Q_planes, sizeof(uint16_t) * rowmat_tc_plane_elems(nq, n), "alloc Q planes");
     if (st == BTI_OK) st = dev_alloc(h, (void**)&h->Q_ea, sizeof(int) * (size_t)kinv_tc_ld(nq), "alloc Q exponents");
@@ -1943,6 +1996,12 @@ static bti_status reserve_online(bti_ctx* h, int64_t B) {
   if (st != BTI_OK) return st;
   if (h->online_via_Q && Q_planes_ready(h) && B >= 16) {
     st = ensure(h, (void**)&h->wsolve, &h->wsolve_bytes, sizeof(double) * apply_Q_work_elems(h, B), "solve workspace");
+    if (st != BTI_OK) return st;
+  }
+  if (h->online_via_Q && Q_pairs_ready(h) && B <= 2) {
+    const int64_t n = h->Nt * h->Nd;
+    st = ensure(h, (void**)&h->wsolve, &h->wsolve_bytes,
+                sizeof(double) * ((size_t)2 * B * n + gemv_pairs_work_elems(n, B)), "solve workspace");
     if (st != BTI_OK) return st;
   }
   // spectral workspace: the larger of an adjoint (G*) and a forward (F, F_q) product

@@ -619,6 +619,10 @@ static int split_rows_to_pairs(const double* X, int64_t ldx, float2* Y, int64_t 
   split_pairs_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(X, ldx, Y, rows, n, ldk);
   return 1;
 }
+int split_rows_to_pairs_ld(const double* X, int64_t ldx, float2* Y, int64_t rows, int64_t n, int64_t ldk,
+                           cudaStream_t s) {
+  return split_rows_to_pairs(X, ldx, Y, rows, n, ldk, s);
+}
 int split_to_pairs(const double* X, float2* Y, int64_t n, int64_t ldk, cudaStream_t s) {
   return split_rows_to_pairs(X, n, Y, n, n, ldk, s);
 }
