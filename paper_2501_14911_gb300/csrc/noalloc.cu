@@ -10,6 +10,9 @@
 // file-scope device array of fixed size that is part of the loaded library.
 #include "bti_internal.cuh"
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <mutex>
 
 namespace {
@@ -22,21 +25,51 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[BTI_NOALLOC_SCR
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
+// per device: the context the address was resolved in, and the address
+void* g_ctx[kMaxDevices] = {nullptr};
 void* g_ptr[kMaxDevices] = {nullptr};
 
-// Device address of the scratch array for the current device; resolved once
-// per device (with that device current) and cached.
+// The driver's current context (null if none is current yet), through the runtime's
+// entry-point query, so the library needs no link to the driver library.
+cudaError_t current_context(void** ctx) {
+  static PFN_cuCtxGetCurrent_v4000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !p) return cudaErrorNotSupported;
+    fn = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(p);
+  }
+  CUcontext c = nullptr;
+  if (fn(&c) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+  *ctx = c;
+  return cudaSuccess;
+}
+
+// Device address of the scratch array in the current context.  Set-up, once per device and
+// context: with that device current, cudaGetSymbolAddress resolves the address (initialising
+// the device's primary context if no context is current yet), and the address is kept with
+// the context it belongs to.  A different current context on the same device (after
+// cudaDeviceReset, or a caller's own context) holds its own copy of the module, so the address
+// is resolved again there rather than reused.
 cudaError_t scratch_address(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  void* ctx = nullptr;
+  e = current_context(&ctx);
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_ptr[dev]) {
+  if (!ctx || !g_ptr[dev] || g_ctx[dev] != ctx) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
+    e = current_context(&ctx);
+    if (e != cudaSuccess) return e;
     g_ptr[dev] = p;
+    g_ctx[dev] = ctx;
   }
   *out = g_ptr[dev];
   return cudaSuccess;
