@@ -30,7 +30,8 @@ constexpr int kTcRows = 128;            // MMA M: rows of F-hat per CTA
 constexpr int kTcKBox = 64;             // halves per TMA box row (128 bytes, the swizzle width)
 constexpr int kTcThreads = 192;         // warp 0 TMA, warp 1 MMA, warps 2-5 B tiles + epilogue
 constexpr uint32_t kTcATile = kTcRows * 128;  // bytes of one A stage
-constexpr long long kTcSpin = 1ll << 22;      // poll limit of every wait (about a second)
+constexpr long long kTcSpin = 1ll << 24;      // poll backstop of every wait
+constexpr uint64_t kTcWaitNs = 1000000000ull;  // wall-time limit of every wait: 1 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -46,11 +47,23 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
                : "=r"(done) : "r"(bar), "r"(parity) : "memory");
   return done != 0;
 }
-// bounded wait; false on timeout or when another thread has flagged an abort
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait: false after kTcWaitNs of wall time (checked every 256 polls, since a poll of
+// try_wait may suspend the thread for microseconds) or kTcSpin polls, whichever comes first,
+// or as soon as another thread has flagged an abort.  On giving up it flags the abort.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
-  for (long long it = 0; it < kTcSpin; ++it) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (long long it = 1; it < kTcSpin; ++it) {
     if (mbar_try(bar, parity)) return true;
-    if ((it & 1023) == 1023 && *abort_flag) return false;
+    if ((it & 255) == 0) {
+      if (*abort_flag) return false;
+      if (global_ns() - t0 > kTcWaitNs) break;
+    }
   }
   *abort_flag = 1;
   return false;
@@ -120,9 +133,10 @@ prod_fwd_f16_tc_kernel(const __grid_constant__ CUtensorMap tmA, const float* __r
             : "memory");
         ++issued;
       }
-      // drain: every issued load lands before the CTA may exit
+      // drain: every issued load lands before the CTA may exit (bounded, even after an abort)
+      int unused = 0;
       for (int s = (issued > kTcStages ? issued - kTcStages : 0); s < issued; ++s)
-        mbar_wait(smem_u32(&fullA[s % kTcStages]), (s / kTcStages) & 1, abort_v);
+        mbar_wait(smem_u32(&fullA[s % kTcStages]), (s / kTcStages) & 1, &unused);
     }
   } else if (warp == 1) {
     // ---- MMA issuer
@@ -351,8 +365,10 @@ prod_adj_f16_tc_kernel(const __grid_constant__ CUtensorMap tmA, const float* __r
               : "memory");
         ++issued;
       }
+      // drain: every issued load lands before the CTA may exit (bounded, even after an abort)
+      int unused = 0;
       for (int q = (issued > kTcStages ? issued - kTcStages : 0); q < issued; ++q)
-        mbar_wait(smem_u32(&fullA[q % kTcStages]), (q / kTcStages) & 1, abort_v);
+        mbar_wait(smem_u32(&fullA[q % kTcStages]), (q / kTcStages) & 1, &unused);
     }
   } else if (warp == 1) {
     // ---- MMA issuer: A MN-major (bit 15), B K-major
