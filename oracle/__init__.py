@@ -42,6 +42,7 @@ from .prior import (
     se_covariance_1d,
     se_covariance,
     prior_blocks,
+    prior_blocks_separable,
     prior_sample,
     elliptic_operator,
 )
@@ -69,7 +70,7 @@ from .inversion import (
 __all__ = [
     "p2o_apply", "p2o_apply_adjoint", "p2o_dense", "p2o_apply_block",
     "p2o_apply_adjoint_block", "lti_blocks", "lti_simulate",
-    "se_covariance_1d", "se_covariance", "prior_blocks", "prior_sample",
+    "se_covariance_1d", "se_covariance", "prior_blocks", "prior_blocks_separable", "prior_sample",
     "elliptic_operator",
     "assemble_K", "assemble_K_columns", "cholesky_lower", "solve_K",
     "map_point", "map_point_woodbury_form", "qoi_map", "qoi_data_gram", "d2q_map",

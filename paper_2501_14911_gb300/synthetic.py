@@ -135,6 +135,11 @@ MIXED = Problem("mixed_precision_Nm16384_Nd600_Nt420", 3, 128, 128, 600, 420, 32
 BATCHED = Problem("batched_online_Nm4096_Nd100_Nt200", 4, 64, 64, 100, 200, 32, 50.0, n_vectors=64)
 DIFF = Problem("diff_qoi_Nm8192_Nd64_Nt256_Nq32", 5, 64, 128, 64, 256, 32, 64.0, n_vectors=1)
 
+# The mixed-precision workload truncated to its first 42 time steps (K 25,200^2, which the
+# oracle can still factor densely): the same workload number and decay, so its blocks are the
+# first 42 blocks of MIXED; 16 observation vectors.
+MIXED_NT42 = Problem("mixed_precision_Nm16384_Nd600_Nt42", 3, 128, 128, 600, 42, 32, 105.0, n_vectors=16)
+
 WORKLOADS = {p.name: p for p in (TINY, SWEEP, MIXED, BATCHED, DIFF)}
 
 

@@ -121,6 +121,21 @@ def _simulate_observe_before_step(A, B, C, m):
     return d
 
 
+def _separable_axes_swapped(blocks, gx, gy, ell, sigma):
+    """The 1-D kernels applied to the wrong axes (iy-major reading of the node index)."""
+    blocks = np.asarray(blocks, dtype=np.float64)
+    X = blocks.reshape(blocks.shape[:-1] + (gy, gx))
+    out = pri.se_covariance_1d(gy, ell, sigma) @ X @ pri.se_covariance_1d(gx, ell, sigma)
+    return out.reshape(blocks.shape)
+
+
+def _separable_one_axis(blocks, gx, gy, ell, sigma):
+    """Only the y-axis kernel applied, carrying sigma^2."""
+    blocks = np.asarray(blocks, dtype=np.float64)
+    X = blocks.reshape(blocks.shape[:-1] + (gx, gy))
+    return (sigma * (X @ pri.se_covariance_1d(gy, ell, sigma))).reshape(blocks.shape)
+
+
 def _K_wrong_diagonal(F, G, noise):
     """Block-diagonal accumulation run from the bottom-right instead of the top-left."""
     F = np.asarray(F, dtype=np.float64)
@@ -258,6 +273,10 @@ MUTANTS = {
     "se_iy_major_ordering": ("se_covariance", lambda f: lambda gx, gy, ell, s: f(gy, gx, ell, s)),
     "se_1d_sigma_squared": ("se_covariance_1d", lambda f: lambda n, ell, s: f(n, ell, s * s)),
     "prior_blocks_drop_prior": ("prior_blocks", lambda f: lambda b, Cs: np.asarray(b, dtype=np.float64)),
+    "separable_prior_axes_swapped": (
+        "prior_blocks_separable", lambda f: lambda b, gx, gy, ell, s: _separable_axes_swapped(b, gx, gy, ell, s)),
+    "separable_prior_one_axis": (
+        "prior_blocks_separable", lambda f: lambda b, gx, gy, ell, s: _separable_one_axis(b, gx, gy, ell, s)),
     "prior_sample_uses_covariance": ("prior_sample", lambda f: _sample_with_covariance),
     "elliptic_laplacian_sign": ("elliptic_operator", lambda f: lambda gx, gy, a1, a2: f(gx, gy, a1, -a2)),
     "elliptic_boundary_degree": ("elliptic_operator", _elliptic_interior_degree),

@@ -157,6 +157,17 @@ def test_se_covariance_is_kronecker_of_axes():
     np.testing.assert_allclose(C[0, gy + 1], sig * sig * np.exp(-2 / (2 * ell * ell)), rtol=1e-15)
 
 
+def test_separable_prior_blocks_equal_the_dense_product():
+    """prior_blocks_separable against prior_blocks with the dense SE covariance, on a
+    non-square grid (the axes cannot be swapped unnoticed) and with several blocks and rows."""
+    gx, gy, ell, sig = 5, 7, 1.6, 1.4
+    rng = np.random.default_rng(11)
+    blocks = rng.standard_normal((3, 4, gx * gy))
+    dense = oracle.prior_blocks(blocks, oracle.se_covariance(gx, gy, ell, sig))
+    np.testing.assert_allclose(oracle.prior_blocks_separable(blocks, gx, gy, ell, sig), dense, rtol=1e-13,
+                               atol=1e-13 * np.abs(dense).max())
+
+
 def test_prior_sample_root():
     gx, gy, ell, sig = 5, 3, 2.0, 0.8
     n = gx * gy
