@@ -43,27 +43,29 @@ namespace bti {
 namespace {
 
 constexpr int kSl = 6;                 // digit planes per operand
-constexpr int kKiRows = 128;           // MMA M: rows of K^{-1} per tile
-constexpr int kKiN = 64;               // MMA N: right-hand sides per launch chunk
-constexpr int kKiBox = 64;             // FP16 columns per TMA box row (128 bytes, the swizzle width)
-constexpr int kKiChunk = 128;          // columns per exact accumulation chunk (two boxes)
-constexpr int kKiAStages = 6;          // K^{-1} plane stages (16 KB each): one box's six planes
-constexpr int kKiBStages = 2;          // right-hand-side stages (six planes, 48 KB each)
+constexpr int kKiRows = 128;           // MMA M: rows of the matrix per tile
+constexpr int kKiN = 64;               // MMA N: right-hand-side columns per launch chunk
+constexpr int kKiBox = 64;             // FP16 columns per tile of the planes in memory (128 bytes)
+constexpr int kKiChunk = 128;          // columns per exact accumulation chunk
+constexpr int kBx = 32;                // FP16 columns per TMA box in the pipeline (64 bytes, the swizzle width)
+constexpr int kBoxesPerChunk = kKiChunk / kBx;
+constexpr int kStages = 3;             // pipeline stages: one 32-column box of all six planes of both operands
 constexpr int kKiThreads = 320;        // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
-constexpr uint32_t kKiATile = kKiRows * 128;
-constexpr uint32_t kKiBPlane = kKiN * 128;
-constexpr uint32_t kKiBTile = kSl * kKiBPlane;
-constexpr uint32_t kKiTmemCols = 512;  // six groups of 64 columns (384) rounded to a power of two
+constexpr uint32_t kAPlane = kKiRows * kBx * 2;  // bytes of one A plane in a stage (128 rows x 64 B)
+constexpr uint32_t kAStage = kSl * kAPlane;       // 48 KB
+constexpr uint32_t kTmemCols = 512;    // six accumulator groups (6 N columns) and two A buffers (2 x 48)
 constexpr long long kKiSpin = 1ll << 24;              // poll backstop of every wait
 constexpr uint64_t kKiWaitNs = 1000000000ull;          // wall-time limit of every wait: 1 s
-constexpr size_t kKiSmem = 1024 + kKiAStages * (size_t)kKiATile + kKiBStages * (size_t)kKiBTile;
+// shared memory of a kernel whose B operand has NC rows: 1 KB alignment slack and kStages stages
+constexpr size_t dig_smem(int NC) { return 1024 + kStages * ((size_t)kAStage + (size_t)kSl * NC * kBx * 2); }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// K-major operand, 128-byte swizzle, 8-row groups 1024 B apart
+// K-major operand, 64-byte swizzle, 8-row groups 512 B apart (the layout TMA writes with
+// CU_TENSOR_MAP_SWIZZLE_64B for 64-byte rows); a K-step of 16 halves advances the start by 32 B
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
 }
 
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
@@ -162,13 +164,22 @@ __device__ __forceinline__ void digits6(long long v, int (&d)[kSl]) {
   d[0] = (int)v;  // |v| <= 128 here
 }
 
-// tcgen05.mma / tcgen05.commit issued by one elected lane of a warp that runs the issuing
-// loop in step, so descriptors and addresses stay warp-uniform.
-__device__ __forceinline__ void mma_elect(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+// tcgen05.cp / tcgen05.mma / tcgen05.commit issued by one elected lane of a warp that runs the
+// issuing loop in step, so descriptors and addresses stay warp-uniform.
+// A operand from tensor memory: D (+)= A[tmem] B[smem]
+__device__ __forceinline__ void mma_ts_elect(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n.reg .pred p, e;\nsetp.ne.b32 p, %4, 0;\nelect.sync _|e, 0xffffffff;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-      ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+      "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n"
+      ::"r"(d), "r"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+// 128 rows x 32 bytes (one K-step of 16 halves) from shared memory into tensor memory lanes 0-127,
+// eight 32-bit columns from taddr
+__device__ __forceinline__ void cp_elect(uint32_t taddr, uint64_t sd) {
+  asm volatile(
+      "{\n.reg .pred e;\nelect.sync _|e, 0xffffffff;\n"
+      "@e tcgen05.cp.cta_group::1.128x256b [%0], %1;\n}\n"
+      ::"r"(taddr), "l"(sd));
 }
 __device__ __forceinline__ void commit_elect(uint32_t bar) {
   asm volatile(
@@ -181,24 +192,26 @@ __device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, vo
   return __all_sync(0xffffffffu, mbar_wait(bar, parity, abort_flag));
 }
 
-// One A plane s of a 64-column box against the B planes t = 0 .. 5 - s (four K-steps of 16
-// each): group s + t accumulates at TMEM columns NC (s + t).  Called by a whole warp; the
-// descriptors are built once per plane and advanced by 32 bytes per K-step (2 in the encoded
-// start address) and by one B plane (NC rows of 128 bytes) per t.  first: the box opens an accumulation chunk, so
-// K-step 0 of plane 0 overwrites the groups.
+// One K-step (16 columns) of a stage: the six A plane slices are copied into tensor memory
+// (columns abuf + 8 s), then the 21 plane pairs s + t <= 5 run with A from tensor memory, so each
+// A slice is read from shared memory once instead of once per pair; group s + t accumulates at
+// TMEM columns NC (s + t).  a0, b0: the stage's plane 0 of A and of B; kk: the K-step within the
+// 32-column box (32 bytes, 2 in the encoded start address).  first: the K-step opens an
+// accumulation chunk, so the pairs (0, t), issued first, overwrite the groups.  Called by a
+// whole warp.
 template <int NC>
-__device__ __forceinline__ void issue_plane(uint32_t tmem, int s, uint32_t a0, uint32_t b0, uint32_t idesc,
-                                            bool first) {
-  const uint64_t ad = sdesc(a0), bd = sdesc(b0);
+__device__ __forceinline__ void issue_kstep(uint32_t tmem, uint32_t abuf, uint32_t a0, uint32_t b0, int kk,
+                                            uint32_t idesc, bool first) {
 #pragma unroll
-  for (int t = 0; t < kSl; ++t) {
-    if (t + s < kSl) {
-      const uint32_t d = tmem + (uint32_t)((s + t) * NC);
-      const uint64_t bt = bd + (uint64_t)t * (NC * 128 >> 4);
+  for (int s = 0; s < kSl; ++s) cp_elect(abuf + 8u * (uint32_t)s, sdesc(a0 + (uint32_t)s * kAPlane) + 2 * kk);
+  const uint64_t bd = sdesc(b0) + 2 * kk;
 #pragma unroll
-      for (int kk = 0; kk < kKiBox / 16; ++kk) {
-        mma_elect(d, ad + 2 * kk, bt + 2 * kk, idesc, (first && kk == 0) ? 0u : 1u);
-      }
+  for (int s = 0; s < kSl; ++s) {
+#pragma unroll
+    for (int t = 0; t < kSl; ++t) {
+      if (t + s < kSl)
+        mma_ts_elect(tmem + (uint32_t)((s + t) * NC), abuf + 8u * (uint32_t)s,
+                     bd + (uint64_t)t * ((uint32_t)(NC * kBx * 2) >> 4), idesc, (first && s == 0) ? 0u : 1u);
     }
   }
 }
@@ -279,14 +292,12 @@ __global__ void slice_digits_kernel(const double* __restrict__ X, int64_t ldx, i
   }
 }
 
-// Shared-memory bytes and TMEM columns of the stream-K kernel with NC B rows per MMA.
-constexpr size_t sk_smem(int NC) { return 1024 + kKiAStages * (size_t)kKiATile + kKiBStages * (size_t)kSl * NC * 128; }
-constexpr uint32_t sk_tmem_cols(int NC) { return NC > 32 ? 512u : 256u; }
-
 // Stream-K digit-plane GEMM: D[m][c] = sum_k A[m][k] B[c][k] for tiles of 128 rows m x NC
 // columns c, the K axis in exact chunks of 128.  Tile T is (w, rg) = (T / NRG, T % NRG) (a
-// problem and a group within it); K-box kbg of tile T sits at TMA row (w KB + kbg) a_blk +
-// rg a_rg of the A planes and (w KB + kbg) b_blk + rg b_rg of the B planes (KB = 2 kpt).
+// problem and a group within it); the 64-column memory tile kbg of tile T sits at TMA row
+// (w KB + kbg) a_blk + rg a_rg of the A planes and (w KB + kbg) b_blk + rg b_rg of the B planes
+// (KB = 2 kpt); the pipeline loads it as two 32-column boxes.  Only the first ksteps 16-column
+// K-steps hold data (the rest of the last chunk is padding, neither loaded nor multiplied).
 // Row m's exponent is ea[w ea_w + rg ea_rg + m], column c's eb[w eb_w + rg eb_rg + c]
 // (padding rows and columns hold 0).  A CTA covers units [blockIdx per, + per) of the
 // (tile, chunk) sequence and writes one FP64 partial tile [NC][128] per tile it touches.
@@ -295,15 +306,15 @@ __global__ void __launch_bounds__(kKiThreads, 1)
 sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
              const int* __restrict__ ea, const int* __restrict__ eb, double* __restrict__ part, int64_t per,
              int64_t total, int64_t kpt, int span, int NRG, int64_t a_blk, int a_rg, int64_t b_blk, int b_rg,
-             int ea_w, int ea_rg, int eb_w, int eb_rg, int drop_stage, int* __restrict__ err) {
-  constexpr uint32_t kBPlane = NC * 128, kBTile = kSl * kBPlane, kCols = sk_tmem_cols(NC);
-  constexpr int W = NC / 2;  // columns per epilogue thread
+             int ea_w, int ea_rg, int eb_w, int eb_rg, int64_t ksteps, int drop_stage, int* __restrict__ err) {
+  constexpr uint32_t kBPlane = NC * kBx * 2, kBStage = kSl * kBPlane;
+  constexpr uint32_t kACol = kSl * NC;  // TMEM column of the two A buffers (48 columns each)
+  constexpr int W = NC / 2;             // columns per epilogue thread
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   unsigned char* sA = smem;
-  unsigned char* sB = smem + kKiAStages * kKiATile;
-  __shared__ uint64_t fullA[kKiAStages], emptyA[kKiAStages], fullB[kKiBStages], emptyB[kKiBStages], accf, tfree,
-      mdone;
+  unsigned char* sB = smem + kStages * kAStage;
+  __shared__ uint64_t full[kStages], empty[kStages], abar[2], accf, tfree, mdone;
   __shared__ uint32_t tmem_holder;
   __shared__ int abort_flag;
 
@@ -313,16 +324,15 @@ sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
   const int64_t first_tile = u0 / kpt;
   const int nunits = (int)(u1 - u0);
   const int KB = (int)(kpt * (kKiChunk / kKiBox));
+  // K-steps and 32-column boxes of chunk c (the last chunk may be partly padding)
+  auto chunk_ksteps = [&](int64_t c) { return (int)min((int64_t)(kKiChunk / 16), ksteps - c * (kKiChunk / 16)); };
 
   if (tid == 0) {
-    for (int s = 0; s < kKiAStages; ++s) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&fullA[s])));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&emptyA[s])));
+    for (int q = 0; q < kStages; ++q) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[q])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[q])));
     }
-    for (int s = 0; s < kKiBStages; ++s) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&fullB[s])));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&emptyB[s])));
-    }
+    for (int q = 0; q < 2; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&abar[q])));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&accf)));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(smem_u32(&tfree)));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mdone)));
@@ -331,7 +341,7 @@ sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
-                 "r"(kCols));
+                 "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -341,85 +351,82 @@ sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
   volatile int* abort_v = &abort_flag;
 
   if (warp == 0) {
-    // ---- TMA producer: per 64-column box, the six B planes, then the six A planes
+    // ---- TMA producer: per 32-column box, the six A planes and the six B planes in one stage
     if (lane == 0) {
-      int na = 0, nbx = 0;
+      int nbx = 0;
       bool ok = true;
       for (int u = 0; u < nunits && ok; ++u) {
         const int64_t unit = u0 + u, T = unit / kpt, c = unit - T * kpt;
         const int64_t w = T / NRG, rg = T - w * NRG;
-        for (int kb = 0; kb < kKiChunk / kKiBox && ok; ++kb, ++nbx) {
-          const int64_t blk = w * KB + c * (kKiChunk / kKiBox) + kb;  // (problem, 64-column box)
+        const int nbox = (chunk_ksteps(c) + 1) / 2;
+        for (int kb = 0; kb < nbox; ++kb, ++nbx) {
+          const int64_t gb = c * kBoxesPerChunk + kb;       // 32-column box along K
+          const int64_t blk = w * KB + (gb >> 1);            // (problem, 64-column memory tile)
+          const int x = (int)(gb & 1) * kBx;
           const int arow = (int)(blk * a_blk + rg * a_rg), brow = (int)(blk * b_blk + rg * b_rg);
-          const int bs = nbx % kKiBStages;
-          if (nbx >= kKiBStages && !mbar_wait(smem_u32(&emptyB[bs]), ((nbx / kKiBStages) - 1) & 1, abort_v)) {
+          const int st = nbx % kStages;
+          if (nbx >= kStages && !mbar_wait(smem_u32(&empty[st]), ((nbx / kStages) - 1) & 1, abort_v)) {
             ok = false;
             break;
           }
-          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&fullB[bs])),
-                       "r"(kBTile));
-          for (int q = 0; q < kSl; ++q)
+          if (nbx == drop_stage) {  // test hook: this stage never arrives, so the waits run out
+            ok = false;
+            break;
+          }
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&full[st])),
+                       "r"(kAStage + kBStage));
+          for (int q = 0; q < kSl; ++q) {
             asm volatile(
                 "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-                ::"r"(smem_u32(sB + bs * kBTile + q * kBPlane)), "l"(&tmB), "r"(0), "r"(brow), "r"(q),
-                "r"(smem_u32(&fullB[bs]))
+                ::"r"(smem_u32(sA + st * kAStage + q * kAPlane)), "l"(&tmA), "r"(x), "r"(arow), "r"(q),
+                "r"(smem_u32(&full[st]))
                 : "memory");
-          for (int s = 0; s < kSl; ++s, ++na) {
-            const int as = na % kKiAStages;
-            if (na >= kKiAStages && !mbar_wait(smem_u32(&emptyA[as]), ((na / kKiAStages) - 1) & 1, abort_v)) {
-              ok = false;
-              break;
-            }
-            if (na == drop_stage) {  // test hook: this stage never arrives, so the waits run out
-              ok = false;
-              break;
-            }
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&fullA[as])),
-                         "r"(kKiATile));
             asm volatile(
                 "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-                ::"r"(smem_u32(sA + as * kKiATile)), "l"(&tmA), "r"(0), "r"(arow), "r"(s), "r"(smem_u32(&fullA[as]))
+                ::"r"(smem_u32(sB + st * kBStage + q * kBPlane)), "l"(&tmB), "r"(x), "r"(brow), "r"(q),
+                "r"(smem_u32(&full[st]))
                 : "memory");
           }
         }
       }
       // drain: every issued load lands before the CTA may exit (bounded, even after an abort)
       int unused = 0;
-      for (int i = (na > kKiAStages ? na - kKiAStages : 0); i < na; ++i)
-        mbar_wait(smem_u32(&fullA[i % kKiAStages]), (i / kKiAStages) & 1, &unused);
-      for (int i = (nbx > kKiBStages ? nbx - kKiBStages : 0); i < nbx; ++i)
-        mbar_wait(smem_u32(&fullB[i % kKiBStages]), (i / kKiBStages) & 1, &unused);
+      for (int i = (nbx > kStages ? nbx - kStages : 0); i < nbx; ++i)
+        mbar_wait(smem_u32(&full[i % kStages]), (i / kStages) & 1, &unused);
     }
   } else if (warp == 1) {
-    // ---- MMA issuer (the whole warp, one elected lane issues): group g = s + t accumulates
-    // A_s B_t^T at TMEM columns NC g
+    // ---- MMA issuer (the whole warp, one elected lane issues): per K-step the A slices go to
+    // one of two tensor-memory buffers, which the K-step two earlier must have finished reading
     {
       const uint32_t idesc = (1u << 4) | ((uint32_t)(NC >> 3) << 17) | ((uint32_t)(kKiRows >> 4) << 24);
-      int na = 0, nbx = 0;
+      int nbx = 0, ks = 0;
       bool ok = true;
       for (int u = 0; u < nunits && ok; ++u) {
+        const int64_t unit = u0 + u, T = unit / kpt, c = unit - T * kpt;
+        const int nks = chunk_ksteps(c);
         // the epilogue has drained the previous chunk's groups
         if (u > 0 && !mbar_wait_warp(smem_u32(&tfree), (u - 1) & 1, abort_v)) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
-        for (int kb = 0; kb < kKiChunk / kKiBox && ok; ++kb, ++nbx) {
-          const int bs = nbx % kKiBStages;
-          if (!mbar_wait_warp(smem_u32(&fullB[bs]), (nbx / kKiBStages) & 1, abort_v)) {
+        for (int kb = 0; kb < (nks + 1) / 2 && ok; ++kb, ++nbx) {
+          const int st = nbx % kStages;
+          if (!mbar_wait_warp(smem_u32(&full[st]), (nbx / kStages) & 1, abort_v)) {
             ok = false;
             break;
           }
-          const uint32_t b0 = smem_u32(sB + bs * kBTile);
-          for (int s = 0; s < kSl; ++s, ++na) {
-            const int as = na % kKiAStages;
-            if (!mbar_wait_warp(smem_u32(&fullA[as]), (na / kKiAStages) & 1, abort_v)) {
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          for (int kk = 0; kk < 2 && 2 * kb + kk < nks; ++kk, ++ks) {
+            const int ab = ks & 1;
+            if (ks >= 2 && !mbar_wait_warp(smem_u32(&abar[ab]), ((ks >> 1) - 1) & 1, abort_v)) {
               ok = false;
               break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            issue_plane<NC>(tmem, s, smem_u32(sA + as * kKiATile), b0, idesc, kb == 0 && s == 0);
-            commit_elect(smem_u32(&emptyA[as]));
+            issue_kstep<NC>(tmem, tmem + kACol + 48u * (uint32_t)ab, smem_u32(sA + st * kAStage),
+                            smem_u32(sB + st * kBStage), kk, idesc, kb == 0 && kk == 0);
+            commit_elect(smem_u32(&abar[ab]));
           }
           if (!ok) break;
-          commit_elect(smem_u32(&emptyB[bs]));
+          commit_elect(smem_u32(&empty[st]));
         }
         if (!ok) break;
         commit_elect(smem_u32(&accf));
@@ -466,7 +473,7 @@ sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     if (lane == 0) mbar_wait(smem_u32(&mdone), 0, &unused);
     __syncwarp();
     asm volatile("tcgen05.fence::after_thread_sync;");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
   }
   if (tid == 0 && *abort_v) atomicExch(err, 1);
 }
@@ -475,11 +482,27 @@ sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 
+namespace {
+// Tensor map of six FP16 digit planes tiled by 64-column memory tiles: dims (64 columns, rows
+// tile-major, plane), one plane every plane_elems halves; the pipeline loads boxes of 32 columns
+// x box_rows rows with the 64-byte swizzle (x = 0 or 32 within a tile, 64 bytes, 16-byte aligned).
+bool encode_planes(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap* tm, const void* planes, int64_t rows,
+                   int64_t plane_elems, int box_rows) {
+  const cuuint64_t dims[3] = {(cuuint64_t)kKiBox, (cuuint64_t)rows, (cuuint64_t)kSl};
+  const cuuint64_t strides[2] = {(cuuint64_t)(kKiBox * 2), (cuuint64_t)(plane_elems * 2)};
+  const cuuint32_t box[3] = {(cuuint32_t)kBx, (cuuint32_t)box_rows, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  return enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<void*>(planes), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+}  // namespace
+
 void kinv_tc_prepare() {
   static PerDeviceOnce attr;
   attr([] {
-    cudaFuncSetAttribute(sk_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sk_smem(64));
-    cudaFuncSetAttribute(sk_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sk_smem(32));
+    cudaFuncSetAttribute(sk_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dig_smem(64));
+    cudaFuncSetAttribute(sk_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dig_smem(32));
   });
 }
 
@@ -560,36 +583,19 @@ cudaError_t rowmat_apply_tc(const void* planes, const int* ea, int64_t M, int64_
   __half* bpl = reinterpret_cast<__half*>(work);
   int* eb = reinterpret_cast<int*>(work + ((size_t)kSl * kKiN * ld * 2 + 7) / 8);
   double* part = work + ((size_t)kSl * kKiN * ld * 2 + 7) / 8 + kKiN;
+  // tiled planes: (64 columns, tile-major rows kb * Mp + i, plane)
   CUtensorMap tA, tB;
-  {
-    // tiled planes: (64 columns, box-major rows kb * Mp + i, plane)
-    const cuuint64_t dims[3] = {(cuuint64_t)kKiBox, (cuuint64_t)(ld / kKiBox * Mp), (cuuint64_t)kSl};
-    const cuuint64_t strides[2] = {(cuuint64_t)(kKiBox * 2), (cuuint64_t)(Mp * ld * 2)};
-    const cuuint32_t box[3] = {(cuuint32_t)kKiBox, (cuuint32_t)kKiRows, 1};
-    const cuuint32_t es[3] = {1, 1, 1};
-    if (enc(&tA, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<void*>(planes), dims, strides, box, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-      return cudaErrorInvalidValue;
-  }
-  {
-    const cuuint64_t dims[3] = {(cuuint64_t)kKiBox, (cuuint64_t)(ld / kKiBox * kKiN), (cuuint64_t)kSl};
-    const cuuint64_t strides[2] = {(cuuint64_t)(kKiBox * 2), (cuuint64_t)(kKiN * ld * 2)};
-    const cuuint32_t box[3] = {(cuuint32_t)kKiBox, (cuuint32_t)kKiN, 1};
-    const cuuint32_t es[3] = {1, 1, 1};
-    if (enc(&tB, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, bpl, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-      return cudaErrorInvalidValue;
-  }
+  if (!encode_planes(enc, &tA, planes, ld / kKiBox * Mp, Mp * ld, kKiRows) ||
+      !encode_planes(enc, &tB, bpl, ld / kKiBox * kKiN, kKiN * ld, kKiN))
+    return cudaErrorInvalidValue;
   kinv_tc_prepare();
   for (int64_t q0 = 0; q0 < B; q0 += kKiN) {
     const int64_t nb = B - q0 < kKiN ? B - q0 : kKiN;
     *launches += kinv_tc_slice(D + q0 * n, n, nb, n, eb, bpl, kKiN, s);
     // tiles: the 128-row tiles of the matrix (one problem); A rows kbg Mp + 128 t, B rows 64 kbg
-    sk_tc_kernel<64><<<(unsigned)p.ctas, kKiThreads, sk_smem(64), s>>>(
+    sk_tc_kernel<64><<<(unsigned)p.ctas, kKiThreads, dig_smem(64), s>>>(
         tA, tB, ea, eb, part, p.per, p.total, p.kpt, p.span, (int)p.tiles, Mp, kKiRows, kKiN, 0, 0, kKiRows, 0, 0,
-        drop_stage, err);
+        (n + 15) / 16, drop_stage, err);
     *launches += 1;
     *launches += kinv_reduce(part, X + q0 * ldx, ldx, M, nb, kKiRows, kKiN, p.per, p.kpt, p.span, p.tiles, s);
   }
@@ -703,13 +709,14 @@ __global__ void __launch_bounds__(kKiThreads, 1)
 adj_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const int* __restrict__ ea, const int* __restrict__ eb, double2* __restrict__ mhat, int nf,
               int64_t Nm, int64_t Nmp, int64_t NBp, int B, int nchunk, int JT, int NG, int64_t per, int64_t total,
-              int drop_stage, int* __restrict__ err) {
+              int ksteps, int drop_stage, int* __restrict__ err) {
+  constexpr uint32_t kBPlane = kKiN * kBx * 2, kBStage = kSl * kBPlane;
+  constexpr uint32_t kACol = kSl * kKiN;  // TMEM column of the two A buffers
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   unsigned char* sA = smem;
-  unsigned char* sB = smem + kKiAStages * kKiATile;
-  __shared__ uint64_t fullA[kKiAStages], emptyA[kKiAStages], fullB[kKiBStages], emptyB[kKiBStages], accf, tfree,
-      mdone;
+  unsigned char* sB = smem + kStages * kAStage;
+  __shared__ uint64_t full[kStages], empty[kStages], abar[2], accf, tfree, mdone;
   __shared__ uint32_t tmem_holder;
   __shared__ int abort_flag;
 
@@ -717,17 +724,15 @@ adj_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
   const int64_t u0 = (int64_t)blockIdx.x * per;
   const int64_t u1 = min(total, u0 + per);
   const int nunits = (int)(u1 - u0);
-  constexpr int kBoxes = kKiChunk / kKiBox;
+  // K-steps of chunk c (the last chunk may be partly padding, neither loaded nor multiplied)
+  auto chunk_ksteps = [&](int c) { return min(kKiChunk / 16, ksteps - c * (kKiChunk / 16)); };
 
   if (tid == 0) {
-    for (int s = 0; s < kKiAStages; ++s) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&fullA[s])));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&emptyA[s])));
+    for (int q = 0; q < kStages; ++q) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[q])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[q])));
     }
-    for (int s = 0; s < kKiBStages; ++s) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&fullB[s])));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&emptyB[s])));
-    }
+    for (int q = 0; q < 2; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&abar[q])));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&accf)));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(smem_u32(&tfree)));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mdone)));
@@ -736,7 +741,7 @@ adj_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
-                 "r"(kKiTmemCols));
+                 "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -746,91 +751,90 @@ adj_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
   volatile int* abort_v = &abort_flag;
 
   if (warp == 0) {
-    // ---- TMA producer
+    // ---- TMA producer: per 32-column box, the six A' planes and the six B planes in one stage
     if (lane == 0) {
-      int na = 0, nbx = 0;
+      int nbx = 0;
       bool ok = true;
       for (int u = 0; u < nunits && ok; ++u) {
         const int64_t unit = u0 + u;
         const int g = (int)(unit % NG);
         const int jt = (int)((unit / NG) % JT);
         const int w = (int)(unit / ((int64_t)NG * JT));
-        const int KB = nchunk * kBoxes;
-        for (int kb = 0; kb < nchunk * kBoxes && ok; ++kb, ++nbx) {
-          // tiled planes: box kb of frequency w starts at row (w KB + kb) * rows
-          const int arow = (int)(((int64_t)w * KB + kb) * Nmp + (int64_t)jt * kKiRows);
-          const int brow = (int)(((int64_t)w * KB + kb) * NBp + (int64_t)g * kKiN);
-          const int bs = nbx % kKiBStages;
-          if (nbx >= kKiBStages && !mbar_wait(smem_u32(&emptyB[bs]), ((nbx / kKiBStages) - 1) & 1, abort_v)) {
-            ok = false;
-            break;
-          }
-          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&fullB[bs])),
-                       "r"(kKiBTile));
-          for (int q = 0; q < kSl; ++q)
-            asm volatile(
-                "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-                ::"r"(smem_u32(sB + bs * kKiBTile + q * kKiBPlane)), "l"(&tmB), "r"(0), "r"(brow), "r"(q),
-                "r"(smem_u32(&fullB[bs]))
-                : "memory");
-          for (int s = 0; s < kSl; ++s, ++na) {
-            const int as = na % kKiAStages;
-            if (na >= kKiAStages && !mbar_wait(smem_u32(&emptyA[as]), ((na / kKiAStages) - 1) & 1, abort_v)) {
+        const int KB = nchunk * (kKiChunk / kKiBox);
+        for (int c = 0; c < nchunk && ok; ++c) {
+          const int nbox = (chunk_ksteps(c) + 1) / 2;
+          for (int kb = 0; kb < nbox; ++kb, ++nbx) {
+            const int gb = c * kBoxesPerChunk + kb;  // 32-column box along K
+            // tiled planes: memory tile gb / 2 of frequency w starts at row (w KB + gb / 2) * rows
+            const int64_t tile = (int64_t)w * KB + (gb >> 1);
+            const int arow = (int)(tile * Nmp + (int64_t)jt * kKiRows);
+            const int brow = (int)(tile * NBp + (int64_t)g * kKiN);
+            const int x = (gb & 1) * kBx;
+            const int st = nbx % kStages;
+            if (nbx >= kStages && !mbar_wait(smem_u32(&empty[st]), ((nbx / kStages) - 1) & 1, abort_v)) {
               ok = false;
               break;
             }
-            if (na == drop_stage) {  // test hook: this stage never arrives, so the waits run out
+            if (nbx == drop_stage) {  // test hook: this stage never arrives, so the waits run out
               ok = false;
               break;
             }
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&fullA[as])),
-                         "r"(kKiATile));
-            asm volatile(
-                "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-                ::"r"(smem_u32(sA + as * kKiATile)), "l"(&tmA), "r"(0), "r"(arow), "r"(s), "r"(smem_u32(&fullA[as]))
-                : "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&full[st])),
+                         "r"(kAStage + kBStage));
+            for (int q = 0; q < kSl; ++q) {
+              asm volatile(
+                  "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                  ::"r"(smem_u32(sA + st * kAStage + q * kAPlane)), "l"(&tmA), "r"(x), "r"(arow), "r"(q),
+                  "r"(smem_u32(&full[st]))
+                  : "memory");
+              asm volatile(
+                  "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                  ::"r"(smem_u32(sB + st * kBStage + q * kBPlane)), "l"(&tmB), "r"(x), "r"(brow), "r"(q),
+                  "r"(smem_u32(&full[st]))
+                  : "memory");
+            }
           }
         }
       }
       int unused = 0;
-      for (int i = (na > kKiAStages ? na - kKiAStages : 0); i < na; ++i)
-        mbar_wait(smem_u32(&fullA[i % kKiAStages]), (i / kKiAStages) & 1, &unused);
-      for (int i = (nbx > kKiBStages ? nbx - kKiBStages : 0); i < nbx; ++i)
-        mbar_wait(smem_u32(&fullB[i % kKiBStages]), (i / kKiBStages) & 1, &unused);
+      for (int i = (nbx > kStages ? nbx - kStages : 0); i < nbx; ++i)
+        mbar_wait(smem_u32(&full[i % kStages]), (i / kStages) & 1, &unused);
     }
   } else if (warp == 1) {
-    // ---- MMA issuer (the whole warp, one elected lane issues); one accumulation chunk = kBoxes
-    // boxes, chunk counter cc across units
+    // ---- MMA issuer (the whole warp, one elected lane issues); chunk counter cc across units,
+    // K-step counter ks for the two tensor-memory A buffers
     {
       const uint32_t idesc = (1u << 4) | ((uint32_t)(kKiN >> 3) << 17) | ((uint32_t)(kKiRows >> 4) << 24);
-      int na = 0, nbx = 0, cc = 0;
+      int nbx = 0, cc = 0, ks = 0;
       bool ok = true;
       for (int u = 0; u < nunits && ok; ++u) {
         for (int c = 0; c < nchunk && ok; ++c, ++cc) {
+          const int nks = chunk_ksteps(c);
           if (cc > 0 && !mbar_wait_warp(smem_u32(&tfree), (cc - 1) & 1, abort_v)) {
             ok = false;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;");
-          for (int kb = 0; kb < kBoxes && ok; ++kb, ++nbx) {
-            const int bs = nbx % kKiBStages;
-            if (!mbar_wait_warp(smem_u32(&fullB[bs]), (nbx / kKiBStages) & 1, abort_v)) {
+          for (int kb = 0; kb < (nks + 1) / 2 && ok; ++kb, ++nbx) {
+            const int st = nbx % kStages;
+            if (!mbar_wait_warp(smem_u32(&full[st]), (nbx / kStages) & 1, abort_v)) {
               ok = false;
               break;
             }
-            const uint32_t b0 = smem_u32(sB + bs * kKiBTile);
-            for (int s = 0; s < kSl; ++s, ++na) {
-              const int as = na % kKiAStages;
-              if (!mbar_wait_warp(smem_u32(&fullA[as]), (na / kKiAStages) & 1, abort_v)) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            for (int kk = 0; kk < 2 && 2 * kb + kk < nks; ++kk, ++ks) {
+              const int ab = ks & 1;
+              if (ks >= 2 && !mbar_wait_warp(smem_u32(&abar[ab]), ((ks >> 1) - 1) & 1, abort_v)) {
                 ok = false;
                 break;
               }
               asm volatile("tcgen05.fence::after_thread_sync;");
-              issue_plane<kKiN>(tmem, s, smem_u32(sA + as * kKiATile), b0, idesc, kb == 0 && s == 0);
-              commit_elect(smem_u32(&emptyA[as]));
+              issue_kstep<kKiN>(tmem, tmem + kACol + 48u * (uint32_t)ab, smem_u32(sA + st * kAStage),
+                                smem_u32(sB + st * kBStage), kk, idesc, kb == 0 && kk == 0);
+              commit_elect(smem_u32(&abar[ab]));
             }
             if (!ok) break;
-            commit_elect(smem_u32(&emptyB[bs]));
+            commit_elect(smem_u32(&empty[st]));
           }
           if (!ok) break;
           commit_elect(smem_u32(&accf));
@@ -888,7 +892,7 @@ adj_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     if (lane == 0) mbar_wait(smem_u32(&mdone), 0, &unused);
     __syncwarp();
     asm volatile("tcgen05.fence::after_thread_sync;");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kKiTmemCols));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
   }
   if (tid == 0 && *abort_v) atomicExch(err, 1);
 }
@@ -932,25 +936,9 @@ cudaError_t adj_digits_apply(const void* planes, const int* ea, int64_t nf, int6
   __half* bpl = reinterpret_cast<__half*>(wb);
   int* eb = reinterpret_cast<int*>(wb + (size_t)kSl * nf * NBp * Kp * 2);
   CUtensorMap tA, tB;
-  const cuuint32_t es[3] = {1, 1, 1};
-  {
-    const cuuint64_t dims[3] = {(cuuint64_t)kKiBox, (cuuint64_t)(nf * (Kp / kKiBox) * Nmp), (cuuint64_t)kSl};
-    const cuuint64_t strides[2] = {(cuuint64_t)(kKiBox * 2), (cuuint64_t)(nf * Nmp * Kp * 2)};
-    const cuuint32_t box[3] = {(cuuint32_t)kKiBox, (cuuint32_t)kKiRows, 1};
-    if (enc(&tA, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<void*>(planes), dims, strides, box, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-      return cudaErrorInvalidValue;
-  }
-  {
-    const cuuint64_t dims[3] = {(cuuint64_t)kKiBox, (cuuint64_t)(nf * (Kp / kKiBox) * NBp), (cuuint64_t)kSl};
-    const cuuint64_t strides[2] = {(cuuint64_t)(kKiBox * 2), (cuuint64_t)(nf * NBp * Kp * 2)};
-    const cuuint32_t box[3] = {(cuuint32_t)kKiBox, (cuuint32_t)kKiN, 1};
-    if (enc(&tB, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, bpl, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-      return cudaErrorInvalidValue;
-  }
+  if (!encode_planes(enc, &tA, planes, nf * (Kp / kKiBox) * Nmp, nf * Nmp * Kp, kKiRows) ||
+      !encode_planes(enc, &tB, bpl, nf * (Kp / kKiBox) * NBp, nf * NBp * Kp, kKiN))
+    return cudaErrorInvalidValue;
   adj_digits_prepare();
   adj_vec_planes_kernel<<<dim3((unsigned)nf, (unsigned)(NBp / 2)), 128, 0, s>>>(
       static_cast<const double2*>(dhat), nf, R, B, NBp, Kp, bpl, eb);
@@ -959,16 +947,16 @@ cudaError_t adj_digits_apply(const void* planes, const int* ea, int64_t nf, int6
   const int64_t slots = num_sms_tc();
   const int64_t per = (total + slots - 1) / slots;
   const int64_t ctas = (total + per - 1) / per;
-  adj_tc_kernel<<<(unsigned)ctas, kKiThreads, kKiSmem, s>>>(tA, tB, ea, eb, static_cast<double2*>(mhat), (int)nf, Nm,
-                                                            Nmp, NBp, (int)B, (int)(Kp / kKiChunk), JT, NG, per, total,
-                                                            drop_stage, err);
+  adj_tc_kernel<<<(unsigned)ctas, kKiThreads, dig_smem(kKiN), s>>>(
+      tA, tB, ea, eb, static_cast<double2*>(mhat), (int)nf, Nm, Nmp, NBp, (int)B, (int)(Kp / kKiChunk), JT, NG, per,
+      total, (int)((2 * R + 15) / 16), drop_stage, err);
   *launches = 2;
   return cudaGetLastError();
 }
 
 void adj_digits_prepare() {
   static PerDeviceOnce attr;
-  attr([] { cudaFuncSetAttribute(adj_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kKiSmem); });
+  attr([] { cudaFuncSetAttribute(adj_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dig_smem(kKiN)); });
 }
 
 
@@ -1156,39 +1144,24 @@ cudaError_t fwd_digits_apply(const void* planes, const int* ex, int64_t nf, int6
   double* part = reinterpret_cast<double*>(
       (reinterpret_cast<uintptr_t>(wb + vbytes + (size_t)nf * kKiRows * sizeof(int)) + 255) & ~(uintptr_t)255);
   CUtensorMap tA, tB;
-  const cuuint32_t es[3] = {1, 1, 1};
-  {
-    const cuuint64_t dims[3] = {(cuuint64_t)kKiBox, (cuuint64_t)(nf * p.KB * kKiRows), (cuuint64_t)kSl};
-    const cuuint64_t strides[2] = {(cuuint64_t)(kKiBox * 2), (cuuint64_t)(nf * p.KB * kKiRows * kKiBox * 2)};
-    const cuuint32_t box[3] = {(cuuint32_t)kKiBox, (cuuint32_t)kKiRows, 1};
-    if (enc(&tA, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, vpl, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-      return cudaErrorInvalidValue;
-  }
-  {
-    const cuuint64_t dims[3] = {(cuuint64_t)kKiBox, (cuuint64_t)(nf * p.KB * p.Rp), (cuuint64_t)kSl};
-    const cuuint64_t strides[2] = {(cuuint64_t)(kKiBox * 2), (cuuint64_t)(nf * p.KB * p.Rp * kKiBox * 2)};
-    const cuuint32_t box[3] = {(cuuint32_t)kKiBox, (cuuint32_t)p.NC, 1};
-    if (enc(&tB, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<void*>(planes), dims, strides, box, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-      return cudaErrorInvalidValue;
-  }
+  if (!encode_planes(enc, &tA, vpl, nf * p.KB * kKiRows, nf * p.KB * kKiRows * kKiBox, kKiRows) ||
+      !encode_planes(enc, &tB, planes, nf * p.KB * p.Rp, nf * p.KB * p.Rp * kKiBox, p.NC))
+    return cudaErrorInvalidValue;
   kinv_tc_prepare();
   for (int64_t b0 = 0; b0 < B; b0 += 64) {
     const int64_t nb = B - b0 < 64 ? B - b0 : 64;
     fwd_vec_planes_kernel<<<dim3((unsigned)nf, 64), 256, 0, s>>>(static_cast<const double2*>(mhat), nf, Nm, b0, nb,
                                                                   p.Kp, vpl, ev);
     // tiles (w, rg): A rows (w KB + kb) 128, B rows (w KB + kb) R_pad + NC rg
+    const int64_t ksteps = (2 * Nm + 15) / 16;
     if (p.NC == 32)
-      sk_tc_kernel<32><<<(unsigned)p.ctas, kKiThreads, sk_smem(32), s>>>(
+      sk_tc_kernel<32><<<(unsigned)p.ctas, kKiThreads, dig_smem(32), s>>>(
           tA, tB, ev, ex, part, p.per, p.total, p.kpt, p.span, p.NRG, kKiRows, 0, p.Rp, p.NC, kKiRows, 0, (int)p.Rp,
-          p.NC, drop_stage, err);
+          p.NC, ksteps, drop_stage, err);
     else
-      sk_tc_kernel<64><<<(unsigned)p.ctas, kKiThreads, sk_smem(64), s>>>(
+      sk_tc_kernel<64><<<(unsigned)p.ctas, kKiThreads, dig_smem(64), s>>>(
           tA, tB, ev, ex, part, p.per, p.total, p.kpt, p.span, p.NRG, kKiRows, 0, p.Rp, p.NC, kKiRows, 0, (int)p.Rp,
-          p.NC, drop_stage, err);
+          p.NC, ksteps, drop_stage, err);
     const int64_t tot = nb * nf * R;
     fwd_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, static_cast<double2*>(dhat), nf, R, b0, nb,
                                                                    p.NC, p.NRG, p.per, p.kpt, p.span);
