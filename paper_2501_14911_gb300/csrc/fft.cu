@@ -195,8 +195,27 @@ __device__ __forceinline__ void butterfly(const C2<T>* src, int i0, int Lr, C2<T
     a[6] = csub<T>(e2, o2);
     a[3] = cadd<T>(e3, o3);
     a[7] = csub<T>(e3, o3);
+  } else if (R == 5) {
+    // radix 5 with constant twiddles: with t1 = a1 + a4, t2 = a2 + a3, t3 = a1 - a4,
+    // t4 = a2 - a3, c_k = cos(2 pi k / 5) and s_k = sin(2 pi k / 5) (k = 1, 2), the outputs are
+    // b0 = a0 + t1 + t2, b1,4 = u1 -+ i v1, b2,3 = u2 -+ i v2 (signs of i flipped for the
+    // inverse) with u1 = a0 + c1 t1 + c2 t2, u2 = a0 + c2 t1 + c1 t2, v1 = s1 t3 + s2 t4 and
+    // v2 = s2 t3 - s1 t4, since w^4 = conj(w) and w^3 = conj(w^2) for w = e^{-2 pi i / 5}
+    const T c1 = (T)0.30901699437494742410229341718282, c2 = (T)-0.80901699437494742410229341718282;
+    const T s1 = (T)0.95105651629515357211643933337938, s2 = (T)0.58778525229247312916870595463907;
+    const C2<T> t1 = cadd<T>(a[1], a[4]), t2 = cadd<T>(a[2], a[3]);
+    const C2<T> t3 = csub<T>(a[1], a[4]), t4 = csub<T>(a[2], a[3]);
+    const C2<T> u1 = cadd<T>(a[0], cadd<T>(mk<T>(c1 * t1.x, c1 * t1.y), mk<T>(c2 * t2.x, c2 * t2.y)));
+    const C2<T> u2 = cadd<T>(a[0], cadd<T>(mk<T>(c2 * t1.x, c2 * t1.y), mk<T>(c1 * t2.x, c1 * t2.y)));
+    const C2<T> v1 = rot90<T, INV>(cadd<T>(mk<T>(s1 * t3.x, s1 * t3.y), mk<T>(s2 * t4.x, s2 * t4.y)));
+    const C2<T> v2 = rot90<T, INV>(csub<T>(mk<T>(s2 * t3.x, s2 * t3.y), mk<T>(s1 * t4.x, s1 * t4.y)));
+    a[0] = cadd<T>(a[0], cadd<T>(t1, t2));
+    a[1] = cadd<T>(u1, v1);
+    a[4] = csub<T>(u1, v1);
+    a[2] = cadd<T>(u2, v2);
+    a[3] = csub<T>(u2, v2);
   } else {
-    // generic small DFT (R = 3, 5, 7): b_m = sum_q a_q w_R^{q m}, w_R^n = tw[(n mod R) L / R]
+    // generic small DFT (R = 3, 7): b_m = sum_q a_q w_R^{q m}, w_R^n = tw[(n mod R) L / R]
     C2<T> b[R];
     const int LR = L / R;
 #pragma unroll
