@@ -190,13 +190,23 @@ bti_status bti_build_K(bti_handle h, int64_t col_block);
  * below one. */
 bti_status bti_build_K_prec(bti_handle h, int64_t col_block, bti_prec assembly);
 
-/* Cholesky-factor K = L L^T in place (lower triangle, stored in FP64).  The
- * 64 x 64 diagonal-block factorisations are FP64; the panel and trailing updates
- * run in the arithmetic of bti_set_dense_precision (FP64 FMA by default, float
- * pairs with about 48 significant bits under BTI_P_DF64).  Synchronises; returns
- * BTI_ERR_NOT_SPD (message names the 1-based pivot) if a pivot is <= 0 or
- * not finite. */
+/* Cholesky-factor K = L L^T in place (lower triangle, stored in FP64; Sec. 4,
+ * Phase 2).  The 64 x 64 diagonal-block factorisations are FP64; the panel and
+ * trailing updates run in the arithmetic of bti_set_dense_precision: FP64 FMA by
+ * default; float pairs (about 48 significant bits) under BTI_P_DF64; under
+ * BTI_P_DF64 with tensor cores on (bti_set_tensor_cores) and N_d N_t above the
+ * panel width of bti_set_factor_panel, blocked by panels of that width whose
+ * trailing updates A22 -= L21 L21^T run on tcgen05 in exact FP16 digit planes of
+ * L21's rows (a 47-bit image of each row), the rest in float pairs.  Synchronises;
+ * returns BTI_ERR_NOT_SPD (message names the 1-based pivot) if a pivot is <= 0 or
+ * not finite, and BTI_ERR_TIMEOUT if a bounded wait of the tensor-core update gave
+ * up (K is then no longer valid: build it again). */
 bti_status bti_factor_K(bti_handle h);
+
+/* Panel width of the tensor-core form of bti_factor_K: a multiple of 64 in [64, 8192],
+ * or 0 for the default (512).  Wider panels put a larger share of the n^3 / 3 flop on
+ * the tensor cores and leave more to the float-pair panel steps (about n^2 P / 2 flop). */
+bti_status bti_set_factor_panel(bti_handle h, int64_t width);
 
 /* Copy the (N_t N_d) x (N_t N_d) row-major K buffer to dst (device, double):
  * its lower triangle holds K after bti_build_K and the Cholesky factor L after

@@ -92,6 +92,7 @@ def lib():
         "bti_infer_map_prior": ([vp, vp, vp, vp, i64, ip], st),
         "bti_set_shadow": ([vp, ip, ip], st),
         "bti_set_tensor_cores": ([vp, ip], st),
+        "bti_set_factor_panel": ([vp, i64], st),
         "bti_set_matfree_precond": ([vp, ip], st),
         "bti_test_withhold_tc_stage": ([vp, ip], st),
         "bti_solve_matfree": ([vp, vp, vp, vp, i64, ip, dp, ip, ip, dp, ctypes.POINTER(SolveInfo)], st),
@@ -321,6 +322,10 @@ class Handle:
     def set_tensor_cores(self, on=True):
         """Tensor-core FP16 forward products for B >= 8 vectors (on by default)."""
         self._check(lib().bti_set_tensor_cores(self._h, 1 if on else 0))
+
+    def set_factor_panel(self, width=0):
+        """Panel width of the tensor-core Cholesky (a multiple of 64; 0: the default, 512)."""
+        self._check(lib().bti_set_factor_panel(self._h, int(width)))
 
     def test_withhold_tc_stage(self, stage):
         """Failure-handling test hook: the tensor-core forward withholds one pipeline stage."""

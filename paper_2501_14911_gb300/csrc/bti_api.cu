@@ -53,6 +53,7 @@ struct bti_ctx {
   bool tc_enabled = true;  // tensor-core FP16 products for B >= 8 (bti_set_tensor_cores)
   int tc_drop_stage = -1;  // failure-handling test hook (bti_test_withhold_tc_stage)
   bti_prec dense_prec = BTI_P_F64;  // arithmetic of K assembly, Cholesky and solves
+  int64_t factor_panel = 512;       // panel width of the tensor-core Cholesky (bti_set_factor_panel)
   bool noise_set = false;
   double sigma2 = 0.0;
   double* noise_diag = nullptr;  // [Nt][Nd] or null
@@ -961,15 +962,48 @@ bti_status bti_factor_K(bti_handle h) {
   }
   st = ensure(h, (void**)&h->wsolve, &h->wsolve_bytes, sizeof(double) * (size_t)n * kCholNB, "solve workspace");
   if (st != BTI_OK) return st;
-  cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
-  count_dense(h, cholesky_f64(h->K, n, h->Linv, h->wsolve, h->status, h->stream, h->dense_prec == BTI_P_DF64));
+  cudaMemsetAsync(h->status, 0, 2 * sizeof(int), h->stream);
+  const int64_t P = h->factor_panel;
+  const bool tc = h->dense_prec == BTI_P_DF64 && h->tc_enabled && n > P && kinv_tc_supported(n);
+  if (tc) {
+    // wide panels, trailing updates on the tensor cores in digit planes
+    void* planes = nullptr;
+    int* ex = nullptr;
+    st = dev_alloc(h, &planes, sizeof(uint16_t) * cholesky_tc_plane_elems(n, P), "Cholesky planes");
+    if (st == BTI_OK) st = dev_alloc(h, (void**)&ex, sizeof(int) * (size_t)kinv_tc_ld(n), "Cholesky exponents");
+    if (st != BTI_OK) {
+      dev_free(planes);
+      return st;
+    }
+    kinv_tc_prepare();
+    cudaError_t ce = cudaSuccess;
+    count_dense(h, cholesky_tc(h->K, n, P, h->Linv, h->wsolve, planes, ex, h->status, h->status + 1, h->stream, &ce,
+                               h->tc_drop_stage));
+    cudaStreamSynchronize(h->stream);
+    dev_free(planes);
+    dev_freep(ex);
+    if (ce != cudaSuccess) {
+      h->K_built = false;
+      return cuda_check(h, ce, "factor_K (tensor-core trailing update)");
+    }
+  } else {
+    count_dense(h, cholesky_f64(h->K, n, h->Linv, h->wsolve, h->status, h->stream, h->dense_prec == BTI_P_DF64));
+  }
   st = launched(h, "factor_K");
   if (st != BTI_OK) return st;
-  int stat = 0;
-  st = cuda_check(h, cudaMemcpyAsync(&stat, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "status");
+  int stat2[2] = {0, 0};
+  st = cuda_check(h, cudaMemcpyAsync(stat2, h->status, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream),
+                  "status");
   if (st != BTI_OK) return st;
   st = cuda_check(h, cudaStreamSynchronize(h->stream), "factor_K sync");
   if (st != BTI_OK) return st;
+  const int stat = stat2[0];
+  if (stat2[1] != 0) {
+    h->K_built = false;  // K was partly overwritten
+    cudaMemsetAsync(h->status, 0, 2 * sizeof(int), h->stream);
+    cudaStreamSynchronize(h->stream);
+    return fail(h, BTI_ERR_TIMEOUT, "factor_K: a bounded wait in the tensor-core trailing update gave up");
+  }
   if (stat != 0) {
     h->K_built = false;  // K was overwritten
     char buf[128];
@@ -1481,6 +1515,16 @@ bti_status bti_set_tensor_cores(bti_handle h, int on) {
   if (on != 0 && on != 1) return fail(h, BTI_ERR_ARG, "set_tensor_cores: on must be 0 or 1");
   if (h->tc_enabled != (on == 1)) drop_online_graph_any(h);
   h->tc_enabled = on == 1;
+  return BTI_OK;
+}
+
+bti_status bti_set_factor_panel(bti_handle h, int64_t width) {
+  bti_status st = check_handle(h);
+  if (st != BTI_OK) return st;
+  if (width == 0) width = 512;
+  if (width < kCholNB || width % kCholNB != 0 || width > 8192)
+    return fail(h, BTI_ERR_ARG, "set_factor_panel: width must be 0 or a multiple of 64 in [64, 8192]");
+  h->factor_panel = width;
   return BTI_OK;
 }
 

@@ -552,6 +552,54 @@ int64_t cholesky_f64(double* A, int64_t n, double* Linv, double* work, int* stat
   return launches;
 }
 
+// The same factorisation with wide panels, so that most of its work (the trailing updates,
+// n^3 / 3 of the n^3 / 3 + O(n^2 P) flop) runs on the tensor cores.  Panel K0 .. K0 + P - 1 is
+// factored by the 64-column steps above, each step's update restricted to the panel's own
+// columns (all rows below); then the trailing matrix takes the whole panel's update
+// A22 -= L21 L21^T at once, in exact digit planes of L21's rows (a 47-bit image of each row).
+size_t cholesky_tc_plane_elems(int64_t n, int64_t P) {
+  const int64_t m = n > P ? n - P : 1;
+  return (size_t)6 * kinv_tc_ld(m) * kinv_tc_ld(P);
+}
+
+int64_t cholesky_tc(double* A, int64_t n, int64_t P, double* Linv, double* work, void* planes, int* ex,
+                    int* status, int* err, cudaStream_t s, cudaError_t* cerr, int drop_stage) {
+  const int nb = kCholNB;
+  int64_t launches = 0;
+  *cerr = cudaSuccess;
+  for (int64_t K0 = 0; K0 < n; K0 += P) {
+    const int64_t pend = std::min<int64_t>(K0 + P, n);
+    for (int64_t k = K0; k < pend; k += nb) {
+      const int kb = (int)std::min<int64_t>(nb, pend - k);
+      double* Lk = Linv + (k / nb) * nb * nb;
+      potrf_diag_kernel<<<1, 256, 0, s>>>(A + k * n + k, n, kb, Lk, status, k);
+      launches += 1;
+      const int64_t m = n - k - kb;
+      if (m <= 0) continue;
+      // panel rows below the diagonal block: P = A[k+kb:, k:k+kb] L_kk^{-T}
+      launches += gemm_sel(true, true, m, kb, kb, 1.0, A + (k + kb) * n + k, n, Lk, nb, 0.0, work, kb, false, s);
+      cudaMemcpy2DAsync(A + (k + kb) * n + k, n * sizeof(double), work, kb * sizeof(double),
+                        kb * sizeof(double), m, cudaMemcpyDeviceToDevice, s);
+      // the rest of this panel's columns: A[k+kb:, k+kb:pend] -= P P[0:w]^T (lower part)
+      const int64_t w = pend - k - kb;
+      if (w > 0)
+        launches += gemm_sel(true, true, m, w, kb, -1.0, work, kb, work, kb, 1.0, A + (k + kb) * n + (k + kb), n,
+                             true, s);
+    }
+    const int64_t m2 = n - pend;
+    if (m2 <= 0) continue;
+    launches += kinv_tc_slice(A + pend * n + K0, n, m2, pend - K0, ex, planes, kinv_tc_ld(m2), s);
+    int64_t tl = 0;
+    const cudaError_t e = syrk_lower_tc(planes, ex, m2, pend - K0, A + pend * n + pend, n, err, s, &tl, drop_stage);
+    launches += tl;
+    if (e != cudaSuccess) {
+      *cerr = e;
+      return launches;
+    }
+  }
+  return launches;
+}
+
 // ------------------------------------------------------------------ triangular solves
 size_t trsm_work_elems(int64_t n, int64_t B) { return (size_t)B * kCholNB; }
 

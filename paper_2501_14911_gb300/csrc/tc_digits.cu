@@ -292,6 +292,16 @@ __global__ void slice_digits_kernel(const double* __restrict__ X, int64_t ldx, i
   }
 }
 
+// Lower tile (I, J) of the triangular enumeration T = I (I + 1) + J, J in [0, 2 I + 1]: the
+// 128-row tile I against the 64-column tiles that reach its diagonal.
+__device__ __forceinline__ void tri_tile(int64_t T, int64_t& I, int64_t& J) {
+  int64_t i = (int64_t)((sqrt(4.0 * (double)T + 1.0) - 1.0) * 0.5);
+  while ((i + 1) * (i + 2) <= T) ++i;
+  while (i > 0 && i * (i + 1) > T) --i;
+  I = i;
+  J = T - i * (i + 1);
+}
+
 // Stream-K digit-plane GEMM: D[m][c] = sum_k A[m][k] B[c][k] for tiles of 128 rows m x NC
 // columns c, the K axis in exact chunks of 128.  Tile T is (w, rg) = (T / NRG, T % NRG) (a
 // problem and a group within it); the 64-column memory tile kbg of tile T sits at TMA row
@@ -301,12 +311,19 @@ __global__ void slice_digits_kernel(const double* __restrict__ X, int64_t ldx, i
 // Row m's exponent is ea[w ea_w + rg ea_rg + m], column c's eb[w eb_w + rg eb_rg + c]
 // (padding rows and columns hold 0).  A CTA covers units [blockIdx per, + per) of the
 // (tile, chunk) sequence and writes one FP64 partial tile [NC][128] per tile it touches.
-template <int NC>
+//
+// SYRK form (the Cholesky's trailing update): A and B are the same planes of a matrix X
+// (rows 0 .. mvalid - 1), tile T is the lower tile (I, J) of tri_tile (A rows 128 I, B rows
+// NC J, a_blk = b_blk = the planes' padded row count), each CTA's run holds whole tiles (per is
+// a multiple of kpt), and the epilogue subtracts the tile from part = C (row stride ldc) on and
+// below the diagonal: C[i][j] -= sum_k X[i][k] X[j][k], j <= i < mvalid.
+template <int NC, bool SYRK = false>
 __global__ void __launch_bounds__(kKiThreads, 1)
 sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
              const int* __restrict__ ea, const int* __restrict__ eb, double* __restrict__ part, int64_t per,
              int64_t total, int64_t kpt, int span, int NRG, int64_t a_blk, int a_rg, int64_t b_blk, int b_rg,
-             int ea_w, int ea_rg, int eb_w, int eb_rg, int64_t ksteps, int drop_stage, int* __restrict__ err) {
+             int ea_w, int ea_rg, int eb_w, int eb_rg, int64_t ksteps, int drop_stage, int* __restrict__ err,
+             int64_t ldc, int64_t mvalid) {
   constexpr uint32_t kBPlane = NC * kBx * 2, kBStage = kSl * kBPlane;
   constexpr uint32_t kACol = kSl * NC;  // TMEM column of the two A buffers (48 columns each)
   constexpr int W = NC / 2;             // columns per epilogue thread
@@ -319,6 +336,14 @@ sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
   __shared__ int abort_flag;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if constexpr (SYRK) {
+    // a bounded wait of an earlier update in the same factorisation gave up: the matrix is no
+    // longer meaningful, so skip the work (read once, so the whole CTA agrees)
+    __shared__ int skip;
+    if (tid == 0) skip = *(volatile int*)err;
+    __syncthreads();
+    if (skip) return;
+  }
   const int64_t u0 = (int64_t)blockIdx.x * per;
   const int64_t u1 = min(total, u0 + per);
   const int64_t first_tile = u0 / kpt;
@@ -357,13 +382,25 @@ sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
       bool ok = true;
       for (int u = 0; u < nunits && ok; ++u) {
         const int64_t unit = u0 + u, T = unit / kpt, c = unit - T * kpt;
-        const int64_t w = T / NRG, rg = T - w * NRG;
+        int64_t w, ta, tb;  // problem, and the tile's row offsets in A and in B
+        if constexpr (SYRK) {
+          int64_t I, J;
+          tri_tile(T, I, J);
+          w = 0;
+          ta = I * kKiRows;
+          tb = J * NC;
+        } else {
+          w = T / NRG;
+          const int64_t rg = T - w * NRG;
+          ta = rg * a_rg;
+          tb = rg * b_rg;
+        }
         const int nbox = (chunk_ksteps(c) + 1) / 2;
         for (int kb = 0; kb < nbox; ++kb, ++nbx) {
           const int64_t gb = c * kBoxesPerChunk + kb;       // 32-column box along K
           const int64_t blk = w * KB + (gb >> 1);            // (problem, 64-column memory tile)
           const int x = (int)(gb & 1) * kBx;
-          const int arow = (int)(blk * a_blk + rg * a_rg), brow = (int)(blk * b_blk + rg * b_rg);
+          const int arow = (int)(blk * a_blk + ta), brow = (int)(blk * b_blk + tb);
           const int st = nbx % kStages;
           if (nbx >= kStages && !mbar_wait(smem_u32(&empty[st]), ((nbx / kStages) - 1) & 1, abort_v)) {
             ok = false;
@@ -452,6 +489,23 @@ sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tfree)) : "memory");
       // last unit of this tile within the CTA's run: write the partial tile
       if (u == nunits - 1 || (unit + 1) / kpt != T) {
+        if constexpr (SYRK) {
+          int64_t I, J;
+          tri_tile(T, I, J);
+          const int64_t row = I * kKiRows + r;
+          if (row < mvalid) {
+            const int er = ea[row];
+            double* Crow = part + row * ldc;
+#pragma unroll
+            for (int c = 0; c < W; ++c) {
+              const int64_t col = J * NC + h * W + c;
+              if (col <= row) Crow[col] -= pair_to_double_scaled(Sh[c], Sl[c], er + eb[col] - 14);
+            }
+          }
+#pragma unroll
+          for (int c = 0; c < W; ++c) Sh[c] = Sl[c] = 0.f;
+          continue;
+        }
         const int64_t w = T / NRG, rg = T - w * NRG;
         const int er = ea[w * ea_w + rg * ea_rg + r];
         const int* ebt = eb + w * eb_w + rg * eb_rg;
@@ -503,6 +557,7 @@ void kinv_tc_prepare() {
   attr([] {
     cudaFuncSetAttribute(sk_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dig_smem(64));
     cudaFuncSetAttribute(sk_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dig_smem(32));
+    cudaFuncSetAttribute(sk_tc_kernel<64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dig_smem(64));
   });
 }
 
@@ -595,7 +650,7 @@ cudaError_t rowmat_apply_tc(const void* planes, const int* ea, int64_t M, int64_
     // tiles: the 128-row tiles of the matrix (one problem); A rows kbg Mp + 128 t, B rows 64 kbg
     sk_tc_kernel<64><<<(unsigned)p.ctas, kKiThreads, dig_smem(64), s>>>(
         tA, tB, ea, eb, part, p.per, p.total, p.kpt, p.span, (int)p.tiles, Mp, kKiRows, kKiN, 0, 0, kKiRows, 0, 0,
-        (n + 15) / 16, drop_stage, err);
+        (n + 15) / 16, drop_stage, err, 0, 0);
     *launches += 1;
     *launches += kinv_reduce(part, X + q0 * ldx, ldx, M, nb, kKiRows, kKiN, p.per, p.kpt, p.span, p.tiles, s);
   }
@@ -605,6 +660,35 @@ cudaError_t rowmat_apply_tc(const void* planes, const int* ea, int64_t M, int64_
 cudaError_t kinv_apply_tc(const void* planes, const int* ea, int64_t n, const double* D, int64_t B, double* X,
                           double* work, int* err, cudaStream_t s, int64_t* launches, int drop_stage) {
   return rowmat_apply_tc(planes, ea, n, n, D, B, X, n, work, err, s, launches, drop_stage);
+}
+
+// The Cholesky's trailing update C -= X X^T on and below the diagonal (Sec. 4, Phase 2), X the
+// m x kdim panel whose planes kinv_tc_slice formed with rows_pad = kinv_tc_ld(m).  The lower
+// tiles (128 rows x 64 columns, K = kdim in exact chunks) are dealt out in runs of whole tiles,
+// one run per SM, so no partial tiles and no reduction: the epilogue subtracts in place.
+cudaError_t syrk_lower_tc(const void* planes, const int* ex, int64_t m, int64_t kdim, double* C, int64_t ldc,
+                          int* err, cudaStream_t s, int64_t* launches, int drop_stage) {
+  *launches = 0;
+  if (m <= 0 || kdim <= 0) return cudaSuccess;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return cudaErrorNotSupported;
+  const int64_t Mp = kinv_tc_ld(m), ld = kinv_tc_ld(kdim);
+  const int64_t RT = Mp / kKiRows;
+  const int64_t tiles = RT * (RT + 1);
+  const int64_t kpt = ld / kKiChunk;
+  const int64_t slots = num_sms_tc();
+  const int64_t tpc = (tiles + slots - 1) / slots;
+  const int64_t ctas = (tiles + tpc - 1) / tpc;
+  CUtensorMap tA, tB;
+  if (!encode_planes(enc, &tA, planes, ld / kKiBox * Mp, Mp * ld, kKiRows) ||
+      !encode_planes(enc, &tB, planes, ld / kKiBox * Mp, Mp * ld, kKiN))
+    return cudaErrorInvalidValue;
+  kinv_tc_prepare();
+  sk_tc_kernel<64, true><<<(unsigned)ctas, kKiThreads, dig_smem(64), s>>>(
+      tA, tB, ex, ex, C, tpc * kpt, tiles * kpt, kpt, 1, 1, Mp, 0, Mp, 0, 0, 0, 0, 0, (kdim + 15) / 16, drop_stage,
+      err, ldc, m);
+  *launches = 1;
+  return cudaGetLastError();
 }
 
 
@@ -1157,11 +1241,11 @@ cudaError_t fwd_digits_apply(const void* planes, const int* ex, int64_t nf, int6
     if (p.NC == 32)
       sk_tc_kernel<32><<<(unsigned)p.ctas, kKiThreads, dig_smem(32), s>>>(
           tA, tB, ev, ex, part, p.per, p.total, p.kpt, p.span, p.NRG, kKiRows, 0, p.Rp, p.NC, kKiRows, 0, (int)p.Rp,
-          p.NC, ksteps, drop_stage, err);
+          p.NC, ksteps, drop_stage, err, 0, 0);
     else
       sk_tc_kernel<64><<<(unsigned)p.ctas, kKiThreads, dig_smem(64), s>>>(
           tA, tB, ev, ex, part, p.per, p.total, p.kpt, p.span, p.NRG, kKiRows, 0, p.Rp, p.NC, kKiRows, 0, (int)p.Rp,
-          p.NC, ksteps, drop_stage, err);
+          p.NC, ksteps, drop_stage, err, 0, 0);
     const int64_t tot = nb * nf * R;
     fwd_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, static_cast<double2*>(dhat), nf, R, b0, nb,
                                                                    p.NC, p.NRG, p.per, p.kpt, p.span);

@@ -190,9 +190,11 @@ def test_diff_gradient_full_size():
 
 
 def test_batched_double_fp32_dense_without_refinement_full_size(batched):
-    """The batched workload with K's Gram product, Cholesky and triangular solves in
-    double-FP32 arithmetic and no refinement step: the online form for the 1e-6 latency
-    target, held to the solve bound 10 kappa(K) 2^-48.  The same through the explicit inverse
+    """The batched workload with K's Gram product and the Cholesky's trailing updates in
+    exact digit planes on the tensor cores (panels of 512), the panel steps and triangular
+    solves in double-FP32 arithmetic, and no refinement step: the online form for the 1e-6
+    latency target.  L and the solves are held to the solve bound 10 kappa(K) 2^-47 of the
+    digit planes.  The same through the explicit inverse
     of bti_invert_K (K^{-1} = W^T W, W = L^{-1}) in the online graph, with the inverse, G^* and
     F_q products on the tensor cores in exact digit planes: the inverse adds its formation
     error to every product, so it is held to 10 kappa(K) rho 2^-47; one refinement step, its
@@ -203,6 +205,10 @@ def test_batched_double_fp32_dense_without_refinement_full_size(batched):
     h.set_dense_precision(bti.DF64)
     h.build_K(p.col_block)
     h.factor_K()
+    L_gpu = h.copy_K().cpu().numpy()
+    low = np.tril_indices(p.Nt * p.Nd)
+    err_L = rel(L_gpu[low], o.L[low])
+    del L_gpu, low
     m_map = torch.empty((p.n_vectors, p.Nt, p.Nm), dtype=torch.float64, device="cuda")
     q_map = torch.empty((p.n_vectors, p.Nt, p.Nq), dtype=torch.float64, device="cuda")
     h.infer_map(torch.from_numpy(o.d_obs).cuda(), m_map, refine_iters=0)
@@ -231,7 +237,8 @@ def test_batched_double_fp32_dense_without_refinement_full_size(batched):
     m1 = m1.cpu().numpy()
     h.close()
     kinfo = f"kappa(K) = {o.kappa:.0f}, rho = {o.rho:.1f}"
-    tol = parity.tol_solve(o.kappa, parity.U_DF64)
+    tol = parity.tol_solve(o.kappa, parity.U_DIGITS)
+    check(err_L, tol, "L, tensor-core trailing updates " + kinfo)
     check(relb(m_gpu, o.m), tol, "m_map, double-FP32 solves " + kinfo)
     check(relb(q_gpu, o.q), tol, "q_map, double-FP32 solves " + kinfo)
     tol = parity.tol_inverse(o.kappa, parity.U_DIGITS, o.rho)

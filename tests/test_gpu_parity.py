@@ -1327,3 +1327,81 @@ def test_double_fp32_tier_refuses_non_finite_blocks():
     assert e.value.status == 1 and "non-finite" in e.value.message
     h.set_blocks(bti.OP_F, cuda(p.blocks_F()), bti.DF64)  # the handle stays usable
     h.close()
+
+
+FACTOR_CASES = [
+    # (name, gx, gy, Nd, Nt, panel): n = N_d N_t over several panels; ragged last panels and
+    # trailing matrices ragged against the 128-row tiles, or exact multiples of them
+    ("n770_panel128", 6, 6, 11, 70, 128),    # 6 panels + 2 columns; trailing 642, 514, ..., 2
+    ("n720_panel64", 6, 6, 24, 30, 64),      # 11 panels + 16 columns; K = 64: half a digit chunk
+    ("n640_panel128_exact", 8, 8, 10, 64, 128),  # trailing 512, 384, 256, 128 rows: whole tiles
+    ("n1200_panel512", 8, 8, 12, 100, 512),  # the default width: two panels and a ragged third
+]
+
+
+@pytest.mark.parametrize("name,gx,gy,Nd,Nt,panel", FACTOR_CASES, ids=[c[0] for c in FACTOR_CASES])
+def test_tensor_core_cholesky_matches_oracle(name, gx, gy, Nd, Nt, panel):
+    """bti_factor_K under BTI_P_DF64 with tensor cores on: panels of `panel` columns whose
+    trailing updates A22 -= L21 L21^T run in exact digit planes on tcgen05 (lower tiles only,
+    subtracted in place).  L against the oracle's factor, and m_map through the blocked solves
+    that use its diagonal-block inverses, at the solve bound 10 kappa(K) 2^-47 (reading R20;
+    noise variance 1 gives kappa(K) of a few thousand, as in the batched workload)."""
+    p = synthetic.small(name, gx, gy, Nd, Nt, Nq=3, sigma2=1.0)
+    F, Fq = p.blocks_F(), p.blocks_Fq()
+    G = oracle.prior_blocks(F, oracle.se_covariance(gx, gy, 2.0, 1.0))
+    h = make_handle(F, Fq, bti.DF64)
+    h.set_prior_se_grid(gx, gy, 2.0, 1.0, bti.DF64)
+    h.set_noise(p.sigma2)
+    h.set_dense_precision(bti.DF64)
+    h.set_factor_panel(panel)
+    h.build_K()
+    h.factor_K()
+    L_gpu = host(h.copy_K())
+    d = p.vectors_d(3)
+    m = torch.empty((3, Nt, gx * gy), dtype=torch.float64, device="cuda")
+    h.infer_map(cuda(d), m, refine_iters=0)
+    h.close()
+    c = oracle_K(name, F, G, p.sigma2, Fq)
+    low = np.tril_indices(Nd * Nt)
+    tol = parity.tol_solve(c.kappa, parity.U_DIGITS)
+    check(rel(L_gpu[low], c.L[low]), tol, f"L, panel {panel}; kappa(K) = {c.kappa:.0f}")
+    b = solve_bounds(c, d, parity.U_DIGITS)
+    check(relb(host(m), b.m), b.tol_m, "m_map, blocked solves; " + b.info)
+
+
+def test_tensor_core_cholesky_reports_pivot_and_timeout():
+    """Failure handling of the tensor-core factorisation, injected on the host: a negative noise
+    variance past the first panel gives BTI_ERR_NOT_SPD with its pivot; a withheld TMA stage
+    (test hook) makes the trailing update's bounded waits run out, factor_K returns
+    BTI_ERR_TIMEOUT, and the same handle then builds and factors K correctly."""
+    name, gx, gy, Nd, Nt = "chol_tc_fail", 6, 6, 10, 40
+    p = synthetic.small(name, gx, gy, Nd, Nt, Nq=3, sigma2=1.0)
+    F = p.blocks_F()
+    G = oracle.prior_blocks(F, oracle.se_covariance(gx, gy, 2.0, 1.0))
+    var = np.full((Nt, Nd), 1.0)
+    var[30, 3] = -1e4  # data index 303 (third panel of 128) -> pivot 304 (1-based)
+    h = make_handle(F, None, bti.DF64)
+    h.set_prior_se_grid(gx, gy, 2.0, 1.0, bti.DF64)
+    h.set_dense_precision(bti.DF64)
+    h.set_factor_panel(128)
+    h.set_noise(0.0, cuda(var))
+    h.build_K()
+    with pytest.raises(bti.BtiError) as e:
+        h.factor_K()
+    assert e.value.status == 6
+    assert "pivot 304" in e.value.message, e.value.message
+    h.set_noise(p.sigma2)
+    h.build_K()
+    h.test_withhold_tc_stage(1)
+    with pytest.raises(bti.BtiError) as e:
+        h.factor_K()
+    assert e.value.status == 7  # BTI_ERR_TIMEOUT
+    h.test_withhold_tc_stage(-1)
+    h.build_K()
+    h.factor_K()
+    L_gpu = host(h.copy_K())
+    h.close()
+    c = oracle_K(name, F, G, p.sigma2)
+    low = np.tril_indices(Nd * Nt)
+    check(rel(L_gpu[low], c.L[low]), parity.tol_solve(c.kappa, parity.U_DIGITS),
+          f"L after a timeout; kappa(K) = {c.kappa:.0f}")
