@@ -193,19 +193,24 @@ bti_status bti_build_K_prec(bti_handle h, int64_t col_block, bti_prec assembly);
 /* Cholesky-factor K = L L^T in place (lower triangle, stored in FP64; Sec. 4,
  * Phase 2).  The 64 x 64 diagonal-block factorisations are FP64; the panel and
  * trailing updates run in the arithmetic of bti_set_dense_precision: FP64 FMA by
- * default; float pairs (about 48 significant bits) under BTI_P_DF64; under
- * BTI_P_DF64 with tensor cores on (bti_set_tensor_cores) and N_d N_t above the
- * panel width of bti_set_factor_panel, blocked by panels of that width whose
- * trailing updates A22 -= L21 L21^T run on tcgen05 in exact FP16 digit planes of
- * L21's rows (a 47-bit image of each row), the rest in float pairs.  Synchronises;
+ * default; float pairs (about 48 significant bits) under BTI_P_DF64 with tensor
+ * cores off; under BTI_P_DF64 with tensor cores on (bti_set_tensor_cores, the
+ * default) and N_d N_t > 64, blocked by panels of the width of
+ * bti_set_factor_panel, each factored recursively by halves, with every update
+ * A22 -= L21 L21^T (within the panels and of the trailing matrix) on tcgen05 in
+ * exact FP16 digit planes of L21's rows (a 47-bit image of each row); the solves
+ * of the 64-row panels below each diagonal block stay in float pairs.  Synchronises;
  * returns BTI_ERR_NOT_SPD (message names the 1-based pivot) if a pivot is <= 0 or
  * not finite, and BTI_ERR_TIMEOUT if a bounded wait of the tensor-core update gave
  * up (K is then no longer valid: build it again). */
 bti_status bti_factor_K(bti_handle h);
 
-/* Panel width of the tensor-core form of bti_factor_K: a multiple of 64 in [64, 8192],
- * or 0 for the default (512).  Wider panels put a larger share of the n^3 / 3 flop on
- * the tensor cores and leave more to the float-pair panel steps (about n^2 P / 2 flop). */
+/* Panel width of the tensor-core form of bti_factor_K: a positive multiple of 64 (at
+ * most 2^30), or 0 for the default (512).  It sets the contraction length of the
+ * trailing updates and the depth of the recursion inside each panel (a width of at
+ * least N_d N_t factors K by recursive halves alone); the flop count does not depend
+ * on it.  The planes take 12 ceil128(N_d N_t) ceil128(min(width, N_d N_t)) bytes
+ * during the call. */
 bti_status bti_set_factor_panel(bti_handle h, int64_t width);
 
 /* Copy the (N_t N_d) x (N_t N_d) row-major K buffer to dst (device, double):

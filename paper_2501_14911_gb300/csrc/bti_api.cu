@@ -964,7 +964,7 @@ bti_status bti_factor_K(bti_handle h) {
   if (st != BTI_OK) return st;
   cudaMemsetAsync(h->status, 0, 2 * sizeof(int), h->stream);
   const int64_t P = h->factor_panel;
-  const bool tc = h->dense_prec == BTI_P_DF64 && h->tc_enabled && n > P && kinv_tc_supported(n);
+  const bool tc = h->dense_prec == BTI_P_DF64 && h->tc_enabled && n > kCholNB && kinv_tc_supported(n);
   if (tc) {
     // wide panels, trailing updates on the tensor cores in digit planes
     void* planes = nullptr;
@@ -1522,8 +1522,8 @@ bti_status bti_set_factor_panel(bti_handle h, int64_t width) {
   bti_status st = check_handle(h);
   if (st != BTI_OK) return st;
   if (width == 0) width = 512;
-  if (width < kCholNB || width % kCholNB != 0 || width > 8192)
-    return fail(h, BTI_ERR_ARG, "set_factor_panel: width must be 0 or a multiple of 64 in [64, 8192]");
+  if (width < kCholNB || width % kCholNB != 0 || width > (int64_t)1 << 30)
+    return fail(h, BTI_ERR_ARG, "set_factor_panel: width must be 0 or a positive multiple of 64");
   h->factor_panel = width;
   return BTI_OK;
 }

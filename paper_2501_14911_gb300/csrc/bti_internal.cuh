@@ -269,16 +269,18 @@ size_t rowmat_tc_work_elems(int64_t M, int64_t n);
 cudaError_t rowmat_apply_tc(const void* planes, const int* ea, int64_t M, int64_t n, const double* D, int64_t B,
                             double* X, int64_t ldx, double* work, int* err, cudaStream_t s, int64_t* launches,
                             int drop_stage = -1);
-// C -= X X^T on and below the diagonal (C row stride ldc), X m x kdim given by its planes
-// (kinv_tc_slice, rows_pad = kinv_tc_ld(m)) and row exponents ex: the tensor-core trailing
-// update of cholesky_tc.
-cudaError_t syrk_lower_tc(const void* planes, const int* ex, int64_t m, int64_t kdim, double* C, int64_t ldc,
-                          int* err, cudaStream_t s, int64_t* launches, int drop_stage = -1);
-// Blocked Cholesky with panels of P columns (a multiple of 64): inside a panel the 64-column
-// steps of cholesky_f64 in double-FP32 arithmetic, restricted to the panel's columns; the
-// trailing update of each panel on the tensor cores (syrk_lower_tc).  Same outputs as
-// cholesky_f64 (L in place, Linv of the 64 x 64 diagonal blocks, status).  work: n x 64
-// doubles; planes / ex: cholesky_tc_plane_elems(n, P) halves and kinv_tc_ld(n) ints.
+// C -= X X[0:w]^T on and below the diagonal (C row stride ldc, the first w <= m columns), X
+// m x kdim given by its planes (kinv_tc_slice, rows_pad = kinv_tc_ld(m)) and row exponents ex:
+// the tensor-core updates of cholesky_tc.
+cudaError_t syrk_lower_tc(const void* planes, const int* ex, int64_t m, int64_t w, int64_t kdim, double* C,
+                          int64_t ldc, int* err, cudaStream_t s, int64_t* launches, int drop_stage = -1);
+// Blocked Cholesky with panels of P columns (a multiple of 64), each panel factored
+// recursively: its left half, then the update of its right half on the tensor cores, then the
+// right half; 64-column leaves take the FP64 diagonal block and the double-FP32 solve of the
+// rows below it.  The trailing update of each panel runs on the tensor cores too
+// (syrk_lower_tc).  Same outputs as cholesky_f64 (L in place, Linv of the 64 x 64 diagonal
+// blocks, status).  work: n x 64 doubles; planes / ex: cholesky_tc_plane_elems(n, P) halves
+// and kinv_tc_ld(n) ints.
 size_t cholesky_tc_plane_elems(int64_t n, int64_t P);
 int64_t cholesky_tc(double* A, int64_t n, int64_t P, double* Linv, double* work, void* planes, int* ex,
                     int* status, int* err, cudaStream_t s, cudaError_t* cerr, int drop_stage = -1);

@@ -466,58 +466,81 @@ int identity_blocks(double* X, int64_t nb, int64_t R, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------ Cholesky
-// Factor the kb x kb diagonal block in shared memory (right-looking, unblocked),
-// write L back, and write its inverse (lower, zeros above) to Linv (ld nb).
+// Factor the kb x kb diagonal block (kb <= 64) in shared memory, write L back, and write its
+// inverse (lower, zeros elsewhere) to Linv (ld 64).  All in FP64; GB300 runs FP64 at about
+// two FMAs per clock per SM, so the kernel keeps every step in shared memory and every thread
+// busy: 64 groups of 4 threads, group g owning row g in the factorisation and column g in the
+// inversion.
+//
+// Factorisation, right-looking, two barriers per column j: (a) column j of L goes to the
+// upper triangle, S[j][i] = S[i][j] / sqrt(d_j) (i > j), where the trailing update reads it
+// row-wise; (b) row i's group updates S[i][c] -= L[i][j] L[c][j] for j < c <= i, and the lane
+// that updates the next diagonal entry takes its pivot d_{j+1}: sqrt into the diagonal, the
+// reciprocal into rinv.  Inversion, X = L^{-1} by columns (no barriers: column c of X depends
+// only on itself): X[c][c] = 1 / L[c][c], X[r][c] = -(sum_{l=c}^{r-1} L[r][l] X[l][c]) / L[r][r],
+// the four lanes of a group splitting the sum; X overwrites the lower triangle.
 __global__ void __launch_bounds__(256)
 potrf_diag_kernel(double* A, int64_t lda, int kb, double* Linv, int* status, int64_t k0) {
   __shared__ double S[kCholNB][kCholNB + 1];
+  __shared__ double rinv[kCholNB];
   __shared__ int failed;
   if (*status != 0) return;  // an earlier block already failed
-  if (threadIdx.x == 0) failed = 0;
-  for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
-    int r = idx / kb, c = idx - r * kb;
-    S[r][c] = (c <= r) ? A[r * lda + c] : 0.0;
+  const int tid = threadIdx.x, g = tid >> 2, q = tid & 3;
+  if (tid == 0) failed = 0;
+  for (int idx = tid; idx < kb * kb; idx += blockDim.x) {
+    const int r = idx / kb, c = idx - r * kb;
+    if (c <= r) S[r][c] = A[r * lda + c];
   }
   __syncthreads();
+  auto pivot = [&](int i) {
+    const double d = S[i][i];
+    if (!(d > 0.0) || !isfinite(d)) {
+      failed = 1;
+      atomicCAS(status, 0, (int)(k0 + i + 1));
+    } else {
+      const double sq = sqrt(d);
+      S[i][i] = sq;
+      rinv[i] = 1.0 / sq;
+    }
+  };
+  if (tid == 0 && kb > 0) pivot(0);
+  __syncthreads();
   for (int j = 0; j < kb; ++j) {
-    if (threadIdx.x == 0) {
-      double d = S[j][j];
-      if (!(d > 0.0) || !isfinite(d)) {
-        failed = 1;
-        atomicCAS(status, 0, (int)(k0 + j + 1));
-      } else {
-        S[j][j] = sqrt(d);
-      }
-    }
+    if (failed) return;  // set before the last barrier: uniform
+    const double rj = rinv[j];
+    for (int i = j + 1 + tid; i < kb; i += blockDim.x) S[j][i] = S[i][j] * rj;
     __syncthreads();
-    if (failed) return;
-    double piv = S[j][j];
-    for (int i = j + 1 + threadIdx.x; i < kb; i += blockDim.x) S[i][j] /= piv;
-    __syncthreads();
-    int w = kb - j - 1;
-    for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
-      int r = j + 1 + idx / w, c = j + 1 + idx % w;
-      if (c <= r) S[r][c] = fma(-S[r][j], S[c][j], S[r][c]);
+    if (g > j && g < kb) {
+      const double li = S[j][g];
+      for (int c = j + 1 + q; c <= g; c += 4) S[g][c] = fma(-li, S[j][c], S[g][c]);
+      if (q == 0 && g == j + 1) pivot(g);  // this lane just updated S[g][g] (c = j + 1)
     }
     __syncthreads();
   }
-  for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
-    int r = idx / kb, c = idx - r * kb;
-    if (c <= r) A[r * lda + c] = S[r][c];
+  // L back to memory: the diagonal, and the columns from the upper triangle
+  for (int idx = tid; idx < kb * kb; idx += blockDim.x) {
+    const int r = idx / kb, c = idx - r * kb;
+    if (c <= r) A[r * lda + c] = (c == r) ? S[r][r] : S[c][r];
   }
-  // inverse of the lower-triangular block, written to Linv (ld kCholNB, zeros
-  // elsewhere): thread c solves L x = e_c by forward substitution.
-  if (threadIdx.x < kCholNB) {
-    const int c = threadIdx.x;
-    for (int r = 0; r < kCholNB; ++r) {
-      double v = 0.0;
-      if (c < kb && r < kb && r >= c) {
-        v = (r == c) ? 1.0 : 0.0;
-        for (int l = c; l < r; ++l) v = fma(-S[r][l], Linv[l * kCholNB + c], v);
-        v = v / S[r][r];
-      }
-      Linv[r * kCholNB + c] = v;
+  __syncthreads();
+  if (g < kb) {
+    const unsigned mask = 0xFu << (threadIdx.x & 28);  // the group's four lanes
+    const int c = g;
+    if (q == 0) S[c][c] = rinv[c];
+    __syncwarp(mask);
+    for (int r = c + 1; r < kb; ++r) {
+      double part = 0.0;
+      for (int l = c + q; l < r; l += 4) part = fma(S[l][r], S[l][c], part);
+      part += __shfl_xor_sync(mask, part, 1);
+      part += __shfl_xor_sync(mask, part, 2);
+      if (q == 0) S[r][c] = -rinv[r] * part;
+      __syncwarp(mask);
     }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < kCholNB * kCholNB; idx += blockDim.x) {
+    const int r = idx / kCholNB, c = idx - r * kCholNB;
+    Linv[idx] = (c <= r && r < kb) ? S[r][c] : 0.0;
   }
 }
 
@@ -552,52 +575,79 @@ int64_t cholesky_f64(double* A, int64_t n, double* Linv, double* work, int* stat
   return launches;
 }
 
-// The same factorisation with wide panels, so that most of its work (the trailing updates,
-// n^3 / 3 of the n^3 / 3 + O(n^2 P) flop) runs on the tensor cores.  Panel K0 .. K0 + P - 1 is
-// factored by the 64-column steps above, each step's update restricted to the panel's own
-// columns (all rows below); then the trailing matrix takes the whole panel's update
-// A22 -= L21 L21^T at once, in exact digit planes of L21's rows (a 47-bit image of each row).
+// The same factorisation with wide panels, so that nearly all of its n^3 / 3 flop runs on the
+// tensor cores.  Panel K0 .. K0 + P - 1 (all rows below K0) is factored recursively: its left
+// half, then the update of its right half by the left half's columns, then its right half.  The
+// 64-column leaves are the steps above (the FP64 diagonal block, the double-FP32 solve of the
+// rows below it); every update is a digit-plane product on the tensor cores, lower trapezoid
+// only, subtracted in place (syrk_lower_tc): within a panel, then the trailing matrix's
+// A22 -= L21 L21^T once per panel.  The planes are 47-bit images of the rows of L.
+namespace {
+struct CholTc {
+  double* A;
+  int64_t n;
+  double* Linv;
+  double* work;
+  void* planes;
+  int* ex;
+  int* status;
+  int* err;
+  cudaStream_t s;
+  int drop_stage;
+  int64_t launches = 0;
+  cudaError_t cerr = cudaSuccess;
+};
+
+// C = A[r0:n, r0:r0 + w] -= X X[0:w]^T (lower), X = A[r0:n, c0:r0] (m = n - r0 rows)
+void chol_update_tc(CholTc& c, int64_t c0, int64_t r0, int64_t w) {
+  const int64_t m = c.n - r0, kdim = r0 - c0;
+  if (m <= 0 || w <= 0 || c.cerr != cudaSuccess) return;
+  c.launches += kinv_tc_slice(c.A + r0 * c.n + c0, c.n, m, kdim, c.ex, c.planes, kinv_tc_ld(m), c.s);
+  int64_t tl = 0;
+  c.cerr = syrk_lower_tc(c.planes, c.ex, m, w, kdim, c.A + r0 * c.n + r0, c.n, c.err, c.s, &tl, c.drop_stage);
+  c.launches += tl;
+}
+
+// columns c0 .. c0 + width - 1 for rows c0 .. n - 1, those columns up to date
+void chol_panel_tc(CholTc& c, int64_t c0, int64_t width) {
+  if (c.cerr != cudaSuccess) return;
+  const int nb = kCholNB;
+  if (width <= nb) {
+    const int kb = (int)width;
+    double* Lk = c.Linv + (c0 / nb) * nb * nb;
+    potrf_diag_kernel<<<1, 256, 0, c.s>>>(c.A + c0 * c.n + c0, c.n, kb, Lk, c.status, c0);
+    c.launches += 1;
+    const int64_t m = c.n - c0 - kb;
+    if (m <= 0) return;
+    // rows below the diagonal block: A[c0+kb:, c0:c0+kb] L_kk^{-T}
+    c.launches += gemm_sel(true, true, m, kb, kb, 1.0, c.A + (c0 + kb) * c.n + c0, c.n, Lk, nb, 0.0, c.work, kb,
+                           false, c.s);
+    cudaMemcpy2DAsync(c.A + (c0 + kb) * c.n + c0, c.n * sizeof(double), c.work, kb * sizeof(double),
+                      kb * sizeof(double), m, cudaMemcpyDeviceToDevice, c.s);
+    return;
+  }
+  const int64_t h = (width / 2 + nb - 1) / nb * nb;  // a multiple of 64 below width
+  chol_panel_tc(c, c0, h);
+  chol_update_tc(c, c0, c0 + h, width - h);
+  chol_panel_tc(c, c0 + h, width - h);
+}
+}  // namespace
+
 size_t cholesky_tc_plane_elems(int64_t n, int64_t P) {
-  const int64_t m = n > P ? n - P : 1;
-  return (size_t)6 * kinv_tc_ld(m) * kinv_tc_ld(P);
+  const int64_t w = P < n ? P : n;
+  return (size_t)6 * kinv_tc_ld(n) * kinv_tc_ld(w);
 }
 
 int64_t cholesky_tc(double* A, int64_t n, int64_t P, double* Linv, double* work, void* planes, int* ex,
                     int* status, int* err, cudaStream_t s, cudaError_t* cerr, int drop_stage) {
-  const int nb = kCholNB;
-  int64_t launches = 0;
-  *cerr = cudaSuccess;
-  for (int64_t K0 = 0; K0 < n; K0 += P) {
+  CholTc c{A, n, Linv, work, planes, ex, status, err, s, drop_stage};
+  for (int64_t K0 = 0; K0 < n && c.cerr == cudaSuccess; K0 += P) {
     const int64_t pend = std::min<int64_t>(K0 + P, n);
-    for (int64_t k = K0; k < pend; k += nb) {
-      const int kb = (int)std::min<int64_t>(nb, pend - k);
-      double* Lk = Linv + (k / nb) * nb * nb;
-      potrf_diag_kernel<<<1, 256, 0, s>>>(A + k * n + k, n, kb, Lk, status, k);
-      launches += 1;
-      const int64_t m = n - k - kb;
-      if (m <= 0) continue;
-      // panel rows below the diagonal block: P = A[k+kb:, k:k+kb] L_kk^{-T}
-      launches += gemm_sel(true, true, m, kb, kb, 1.0, A + (k + kb) * n + k, n, Lk, nb, 0.0, work, kb, false, s);
-      cudaMemcpy2DAsync(A + (k + kb) * n + k, n * sizeof(double), work, kb * sizeof(double),
-                        kb * sizeof(double), m, cudaMemcpyDeviceToDevice, s);
-      // the rest of this panel's columns: A[k+kb:, k+kb:pend] -= P P[0:w]^T (lower part)
-      const int64_t w = pend - k - kb;
-      if (w > 0)
-        launches += gemm_sel(true, true, m, w, kb, -1.0, work, kb, work, kb, 1.0, A + (k + kb) * n + (k + kb), n,
-                             true, s);
-    }
-    const int64_t m2 = n - pend;
-    if (m2 <= 0) continue;
-    launches += kinv_tc_slice(A + pend * n + K0, n, m2, pend - K0, ex, planes, kinv_tc_ld(m2), s);
-    int64_t tl = 0;
-    const cudaError_t e = syrk_lower_tc(planes, ex, m2, pend - K0, A + pend * n + pend, n, err, s, &tl, drop_stage);
-    launches += tl;
-    if (e != cudaSuccess) {
-      *cerr = e;
-      return launches;
-    }
+    chol_panel_tc(c, K0, pend - K0);
+    chol_update_tc(c, K0, pend, n - pend);  // the trailing matrix, whole lower triangle
   }
-  return launches;
+  *cerr = c.cerr;
+  return c.launches;
 }
 
 // ------------------------------------------------------------------ triangular solves

@@ -292,9 +292,16 @@ __global__ void slice_digits_kernel(const double* __restrict__ X, int64_t ldx, i
   }
 }
 
-// Lower tile (I, J) of the triangular enumeration T = I (I + 1) + J, J in [0, 2 I + 1]: the
-// 128-row tile I against the 64-column tiles that reach its diagonal.
-__device__ __forceinline__ void tri_tile(int64_t T, int64_t& I, int64_t& J) {
+// Tile T of the lower trapezoid of 128-row tiles I and 64-column tiles J < JW with J <= 2 I + 1
+// (the column tiles that reach row tile I's diagonal): rows I < I0 = JW / 2 hold 2 I + 2 tiles
+// (T = I (I + 1) + J), the rows after them JW tiles each.
+__device__ __forceinline__ void trap_tile(int64_t T, int64_t JW, int64_t& I, int64_t& J) {
+  const int64_t I0 = JW / 2, T0 = I0 * (I0 + 1);
+  if (T >= T0) {
+    I = I0 + (T - T0) / JW;
+    J = (T - T0) % JW;
+    return;
+  }
   int64_t i = (int64_t)((sqrt(4.0 * (double)T + 1.0) - 1.0) * 0.5);
   while ((i + 1) * (i + 2) <= T) ++i;
   while (i > 0 && i * (i + 1) > T) --i;
@@ -312,18 +319,19 @@ __device__ __forceinline__ void tri_tile(int64_t T, int64_t& I, int64_t& J) {
 // (padding rows and columns hold 0).  A CTA covers units [blockIdx per, + per) of the
 // (tile, chunk) sequence and writes one FP64 partial tile [NC][128] per tile it touches.
 //
-// SYRK form (the Cholesky's trailing update): A and B are the same planes of a matrix X
-// (rows 0 .. mvalid - 1), tile T is the lower tile (I, J) of tri_tile (A rows 128 I, B rows
-// NC J, a_blk = b_blk = the planes' padded row count), each CTA's run holds whole tiles (per is
-// a multiple of kpt), and the epilogue subtracts the tile from part = C (row stride ldc) on and
-// below the diagonal: C[i][j] -= sum_k X[i][k] X[j][k], j <= i < mvalid.
+// SYRK form (the Cholesky's updates): A and B are the same planes of a matrix X (rows 0 ..
+// mvalid - 1), tile T is the lower-trapezoid tile (I, J) of trap_tile with JW = NRG (A rows
+// 128 I, B rows NC J, a_blk = b_blk = the planes' padded row count), each CTA's run holds whole
+// tiles (per is a multiple of kpt), and the epilogue subtracts the tile from part = C (row
+// stride ldc) on and below the diagonal: C[i][j] -= sum_k X[i][k] X[j][k], j <= i < mvalid,
+// j < wvalid.
 template <int NC, bool SYRK = false>
 __global__ void __launch_bounds__(kKiThreads, 1)
 sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
              const int* __restrict__ ea, const int* __restrict__ eb, double* __restrict__ part, int64_t per,
              int64_t total, int64_t kpt, int span, int NRG, int64_t a_blk, int a_rg, int64_t b_blk, int b_rg,
              int ea_w, int ea_rg, int eb_w, int eb_rg, int64_t ksteps, int drop_stage, int* __restrict__ err,
-             int64_t ldc, int64_t mvalid) {
+             int64_t ldc, int64_t mvalid, int64_t wvalid) {
   constexpr uint32_t kBPlane = NC * kBx * 2, kBStage = kSl * kBPlane;
   constexpr uint32_t kACol = kSl * NC;  // TMEM column of the two A buffers (48 columns each)
   constexpr int W = NC / 2;             // columns per epilogue thread
@@ -385,7 +393,7 @@ sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
         int64_t w, ta, tb;  // problem, and the tile's row offsets in A and in B
         if constexpr (SYRK) {
           int64_t I, J;
-          tri_tile(T, I, J);
+          trap_tile(T, NRG, I, J);
           w = 0;
           ta = I * kKiRows;
           tb = J * NC;
@@ -491,7 +499,7 @@ sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
       if (u == nunits - 1 || (unit + 1) / kpt != T) {
         if constexpr (SYRK) {
           int64_t I, J;
-          tri_tile(T, I, J);
+          trap_tile(T, NRG, I, J);
           const int64_t row = I * kKiRows + r;
           if (row < mvalid) {
             const int er = ea[row];
@@ -499,7 +507,7 @@ sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
 #pragma unroll
             for (int c = 0; c < W; ++c) {
               const int64_t col = J * NC + h * W + c;
-              if (col <= row) Crow[col] -= pair_to_double_scaled(Sh[c], Sl[c], er + eb[col] - 14);
+              if (col <= row && col < wvalid) Crow[col] -= pair_to_double_scaled(Sh[c], Sl[c], er + eb[col] - 14);
             }
           }
 #pragma unroll
@@ -650,7 +658,7 @@ cudaError_t rowmat_apply_tc(const void* planes, const int* ea, int64_t M, int64_
     // tiles: the 128-row tiles of the matrix (one problem); A rows kbg Mp + 128 t, B rows 64 kbg
     sk_tc_kernel<64><<<(unsigned)p.ctas, kKiThreads, dig_smem(64), s>>>(
         tA, tB, ea, eb, part, p.per, p.total, p.kpt, p.span, (int)p.tiles, Mp, kKiRows, kKiN, 0, 0, kKiRows, 0, 0,
-        (n + 15) / 16, drop_stage, err, 0, 0);
+        (n + 15) / 16, drop_stage, err, 0, 0, 0);
     *launches += 1;
     *launches += kinv_reduce(part, X + q0 * ldx, ldx, M, nb, kKiRows, kKiN, p.per, p.kpt, p.span, p.tiles, s);
   }
@@ -662,19 +670,21 @@ cudaError_t kinv_apply_tc(const void* planes, const int* ea, int64_t n, const do
   return rowmat_apply_tc(planes, ea, n, n, D, B, X, n, work, err, s, launches, drop_stage);
 }
 
-// The Cholesky's trailing update C -= X X^T on and below the diagonal (Sec. 4, Phase 2), X the
-// m x kdim panel whose planes kinv_tc_slice formed with rows_pad = kinv_tc_ld(m).  The lower
-// tiles (128 rows x 64 columns, K = kdim in exact chunks) are dealt out in runs of whole tiles,
-// one run per SM, so no partial tiles and no reduction: the epilogue subtracts in place.
-cudaError_t syrk_lower_tc(const void* planes, const int* ex, int64_t m, int64_t kdim, double* C, int64_t ldc,
-                          int* err, cudaStream_t s, int64_t* launches, int drop_stage) {
+// The Cholesky's updates C -= X X[0:w]^T on and below the diagonal (Sec. 4, Phase 2), X the
+// m x kdim block whose planes kinv_tc_slice formed with rows_pad = kinv_tc_ld(m), w <= m (w = m:
+// the whole lower triangle).  The lower-trapezoid tiles (128 rows x 64 columns, K = kdim in
+// exact chunks) are dealt out in runs of whole tiles, one run per SM, so no partial tiles and no
+// reduction: the epilogue subtracts in place.
+cudaError_t syrk_lower_tc(const void* planes, const int* ex, int64_t m, int64_t w, int64_t kdim, double* C,
+                          int64_t ldc, int* err, cudaStream_t s, int64_t* launches, int drop_stage) {
   *launches = 0;
-  if (m <= 0 || kdim <= 0) return cudaSuccess;
+  if (m <= 0 || w <= 0 || kdim <= 0) return cudaSuccess;
+  if (w > m) return cudaErrorInvalidValue;
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return cudaErrorNotSupported;
   const int64_t Mp = kinv_tc_ld(m), ld = kinv_tc_ld(kdim);
-  const int64_t RT = Mp / kKiRows;
-  const int64_t tiles = RT * (RT + 1);
+  const int64_t RT = Mp / kKiRows, JW = (w + kKiN - 1) / kKiN, I0 = JW / 2;
+  const int64_t tiles = I0 * (I0 + 1) + (RT - I0) * JW;
   const int64_t kpt = ld / kKiChunk;
   const int64_t slots = num_sms_tc();
   const int64_t tpc = (tiles + slots - 1) / slots;
@@ -685,12 +695,11 @@ cudaError_t syrk_lower_tc(const void* planes, const int* ex, int64_t m, int64_t 
     return cudaErrorInvalidValue;
   kinv_tc_prepare();
   sk_tc_kernel<64, true><<<(unsigned)ctas, kKiThreads, dig_smem(64), s>>>(
-      tA, tB, ex, ex, C, tpc * kpt, tiles * kpt, kpt, 1, 1, Mp, 0, Mp, 0, 0, 0, 0, 0, (kdim + 15) / 16, drop_stage,
-      err, ldc, m);
+      tA, tB, ex, ex, C, tpc * kpt, tiles * kpt, kpt, 1, (int)JW, Mp, 0, Mp, 0, 0, 0, 0, 0, (kdim + 15) / 16,
+      drop_stage, err, ldc, m, w);
   *launches = 1;
   return cudaGetLastError();
 }
-
 
 // ------------------------------------------------------------------ batched adjoint products
 // The double-FP32 tier's adjoint product for batches, m-hat_w[b][j] = sum_i conj(F-hat_w[i][j])
@@ -1241,11 +1250,11 @@ cudaError_t fwd_digits_apply(const void* planes, const int* ex, int64_t nf, int6
     if (p.NC == 32)
       sk_tc_kernel<32><<<(unsigned)p.ctas, kKiThreads, dig_smem(32), s>>>(
           tA, tB, ev, ex, part, p.per, p.total, p.kpt, p.span, p.NRG, kKiRows, 0, p.Rp, p.NC, kKiRows, 0, (int)p.Rp,
-          p.NC, ksteps, drop_stage, err, 0, 0);
+          p.NC, ksteps, drop_stage, err, 0, 0, 0);
     else
       sk_tc_kernel<64><<<(unsigned)p.ctas, kKiThreads, dig_smem(64), s>>>(
           tA, tB, ev, ex, part, p.per, p.total, p.kpt, p.span, p.NRG, kKiRows, 0, p.Rp, p.NC, kKiRows, 0, (int)p.Rp,
-          p.NC, ksteps, drop_stage, err, 0, 0);
+          p.NC, ksteps, drop_stage, err, 0, 0, 0);
     const int64_t tot = nb * nf * R;
     fwd_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, static_cast<double2*>(dhat), nf, R, b0, nb,
                                                                    p.NC, p.NRG, p.per, p.kpt, p.span);

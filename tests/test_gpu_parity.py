@@ -538,8 +538,9 @@ def test_dense_double_fp32_path():
     h.factor_K()
     L_gpu = host(h.copy_K())
     c = oracle_K("tiny", F, G, p.sigma2, Fq)
-    check(rel(L_gpu[low], c.L[low]), parity.tol_solve(c.kappa, parity.U_DF64),
-          f"double-FP32 factor; kappa(K) = {c.kappa:.0f}")
+    # the factor's updates run in digit planes on the tensor cores (the default)
+    check(rel(L_gpu[low], c.L[low]), parity.tol_solve(c.kappa, parity.U_DIGITS),
+          f"double-FP32 and digit-plane factor; kappa(K) = {c.kappa:.0f}")
     m = torch.empty((1, p.Nt, p.Nm), dtype=torch.float64, device="cuda")
     q = torch.empty((1, p.Nt, p.Nq), dtype=torch.float64, device="cuda")
     h.infer_map(cuda(d_obs), m, refine_iters=1)
@@ -620,7 +621,7 @@ def test_d2q_map_and_qoi_covariance(dense):
     h.close()
     # rows of Q are solves with K; Gamma_post(q) = X_qq - Q X^T cancels, q = Q d amplifies
     t = d2q_bounds(oracle_K("tiny", F, G, p.sigma2, Fq), Fq, G, Q_or, C_or, host(d),
-                   parity.U_F64 if dense == "f64" else parity.U_DF64)
+                   parity.U_F64 if dense == "f64" else parity.U_DIGITS)
     check(rel(host(Q), Q_or), t.tol_Q, t.info)
     check(rel(host(C), C_or), t.tol_C, t.info)
     check(relb(host(q), q_or), t.tol_q, t.info)
@@ -671,10 +672,10 @@ def test_online_qoi_via_d2q_map_on_tensor_cores(B):
     d = p.vectors_d(B)
     m_or = oracle.map_point(F, G, p.sigma2, d)
     q_or = oracle.qoi_map(Fq, m_or)
-    # Q from double-FP32 solves (reading R20); the digit-plane and GEMM products of the same Q
-    # differ by the products' rounding only
+    # Q from double-FP32 solves with the digit-plane factor (reading R20); the digit-plane and
+    # GEMM products of the same Q differ by the products' rounding only
     Q_or = oracle.d2q_map(Fq, F, G, p.sigma2)
-    t = d2q_bounds(oracle_K("tiny", F, G, p.sigma2, Fq), Fq, G, Q_or, Q_or, d, parity.U_DF64)
+    t = d2q_bounds(oracle_K("tiny", F, G, p.sigma2, Fq), Fq, G, Q_or, Q_or, d, parity.U_DIGITS)
     tol_prod = max(parity.FLOOR, parity.C_BOUND * parity.U_DIGITS * t.alpha)
     q = torch.empty((B, p.Nt, p.Nq), dtype=torch.float64, device="cuda")
     h.profile_enable(True)
@@ -1336,13 +1337,15 @@ FACTOR_CASES = [
     ("n720_panel64", 6, 6, 24, 30, 64),      # 11 panels + 16 columns; K = 64: half a digit chunk
     ("n640_panel128_exact", 8, 8, 10, 64, 128),  # trailing 512, 384, 256, 128 rows: whole tiles
     ("n1200_panel512", 8, 8, 12, 100, 512),  # the default width: two panels and a ragged third
+    ("n1200_recursive", 8, 8, 12, 100, 1 << 20),  # one panel: the whole factor by recursive halves
 ]
 
 
 @pytest.mark.parametrize("name,gx,gy,Nd,Nt,panel", FACTOR_CASES, ids=[c[0] for c in FACTOR_CASES])
 def test_tensor_core_cholesky_matches_oracle(name, gx, gy, Nd, Nt, panel):
-    """bti_factor_K under BTI_P_DF64 with tensor cores on: panels of `panel` columns whose
-    trailing updates A22 -= L21 L21^T run in exact digit planes on tcgen05 (lower tiles only,
+    """bti_factor_K under BTI_P_DF64 with tensor cores on: panels of `panel` columns, each
+    factored by recursive halves, whose updates A22 -= L21 L21^T (inside the panel and of the
+    trailing matrix) run in exact digit planes on tcgen05 (lower-trapezoid tiles only,
     subtracted in place).  L against the oracle's factor, and m_map through the blocked solves
     that use its diagonal-block inverses, at the solve bound 10 kappa(K) 2^-47 (reading R20;
     noise variance 1 gives kappa(K) of a few thousand, as in the batched workload)."""
