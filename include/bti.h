@@ -206,7 +206,7 @@ bti_status bti_build_K_prec(bti_handle h, int64_t col_block, bti_prec assembly);
 bti_status bti_factor_K(bti_handle h);
 
 /* Panel width of the tensor-core form of bti_factor_K: a positive multiple of 64 (at
- * most 2^30), or 0 for the default (512).  It sets the contraction length of the
+ * most 2^30), or 0 for the default (4096).  It sets the contraction length of the
  * trailing updates and the depth of the recursion inside each panel (a width of at
  * least N_d N_t factors K by recursive halves alone); the flop count does not depend
  * on it.  The planes take 12 ceil128(N_d N_t) ceil128(min(width, N_d N_t)) bytes

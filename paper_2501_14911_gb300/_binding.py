@@ -324,7 +324,7 @@ class Handle:
         self._check(lib().bti_set_tensor_cores(self._h, 1 if on else 0))
 
     def set_factor_panel(self, width=0):
-        """Panel width of the tensor-core Cholesky (a multiple of 64; 0: the default, 512)."""
+        """Panel width of the tensor-core Cholesky (a multiple of 64; 0: the default, 4096)."""
         self._check(lib().bti_set_factor_panel(self._h, int(width)))
 
     def test_withhold_tc_stage(self, stage):

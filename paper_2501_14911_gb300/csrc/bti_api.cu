@@ -53,7 +53,7 @@ struct bti_ctx {
   bool tc_enabled = true;  // tensor-core FP16 products for B >= 8 (bti_set_tensor_cores)
   int tc_drop_stage = -1;  // failure-handling test hook (bti_test_withhold_tc_stage)
   bti_prec dense_prec = BTI_P_F64;  // arithmetic of K assembly, Cholesky and solves
-  int64_t factor_panel = 512;       // panel width of the tensor-core Cholesky (bti_set_factor_panel)
+  int64_t factor_panel = 4096;      // panel width of the tensor-core Cholesky (bti_set_factor_panel)
   bool noise_set = false;
   double sigma2 = 0.0;
   double* noise_diag = nullptr;  // [Nt][Nd] or null
@@ -1521,7 +1521,7 @@ bti_status bti_set_tensor_cores(bti_handle h, int on) {
 bti_status bti_set_factor_panel(bti_handle h, int64_t width) {
   bti_status st = check_handle(h);
   if (st != BTI_OK) return st;
-  if (width == 0) width = 512;
+  if (width == 0) width = 4096;
   if (width < kCholNB || width % kCholNB != 0 || width > (int64_t)1 << 30)
     return fail(h, BTI_ERR_ARG, "set_factor_panel: width must be 0 or a positive multiple of 64");
   h->factor_panel = width;

@@ -492,15 +492,29 @@ potrf_diag_kernel(double* A, int64_t lda, int kb, double* Linv, int* status, int
     if (c <= r) S[r][c] = A[r * lda + c];
   }
   __syncthreads();
+  // The pivot d_i's square root and its reciprocal are on the critical path of every column,
+  // and GB300's FP64 square root and division take long chains of FP64 instructions.  Instead:
+  // d = f 4^k with f in [0.5, 2) (exact exponent arithmetic), y = 1 / sqrt(f) by the Newton-
+  // Raphson iteration for the reciprocal square root, y <- y + y (1 - f y^2) / 2, seeded with
+  // FP32 rsqrtf (about 23 bits) and taken twice in FP64 (the error squares each time: about
+  // 2^-46, then below FP64 rounding); then 1 / sqrt(d) = y 2^-k and sqrt(d) = f y 2^k.
   auto pivot = [&](int i) {
     const double d = S[i][i];
     if (!(d > 0.0) || !isfinite(d)) {
       failed = 1;
       atomicCAS(status, 0, (int)(k0 + i + 1));
     } else {
-      const double sq = sqrt(d);
-      S[i][i] = sq;
-      rinv[i] = 1.0 / sq;
+      int e = 0;
+      double f = frexp(d, &e);  // d = f 2^e, f in [0.5, 1)
+      if (e & 1) {
+        f *= 2.0;
+        e -= 1;
+      }
+      double y = (double)rsqrtf((float)f);
+      y = fma(0.5 * y, fma(-f * y, y, 1.0), y);
+      y = fma(0.5 * y, fma(-f * y, y, 1.0), y);
+      S[i][i] = ldexp(f * y, e / 2);
+      rinv[i] = ldexp(y, -e / 2);
     }
   };
   if (tid == 0 && kb > 0) pivot(0);

@@ -252,43 +252,37 @@ __device__ __forceinline__ double pair_to_double_scaled(float hi, float lo, int 
   return __longlong_as_double(bits);
 }
 
-// exp[r] = binary exponent of max_j |X[r][j]| (frexp convention: max = f 2^e, f in [0.5, 1);
-// 0 for an all-zero row).  One CTA per row.
-__global__ void row_exponent_kernel(const double* __restrict__ X, int64_t ldx, int64_t n, int* __restrict__ ex) {
-  const int64_t r = blockIdx.x;
-  double mx = 0.0;
-  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) mx = fmax(mx, fabs(X[r * ldx + j]));
-  __shared__ double red[32];
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
+// Digit planes of rows 0 .. rows-1 (columns 0 .. n-1; columns n .. ldk-1 and rows rows ..
+// rows_pad-1 are written as zeros), one warp per row: ex[r] = the binary exponent of
+// max_j |X[r][j]| (frexp convention, max = f 2^e with f in [0.5, 1); 0 for a zero or padding
+// row), then X[r][j] 2^(47 - e) rounded to an integer v (|v| <= 2^47) and split into balanced
+// base-256 digits, most significant in plane 0.  Each plane is tiled by 64-column boxes,
+// [ldk / 64][rows_pad][64], so that every 128-row TMA box is one contiguous 16 KB block.
+__global__ void __launch_bounds__(256)
+slice_rows_kernel(const double* __restrict__ X, int64_t ldx, int64_t rows, int64_t n, int* __restrict__ ex,
+                  __half* __restrict__ planes, int64_t rows_pad, int64_t ldk) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t plane = rows_pad * ldk;
+  for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < rows_pad; r += warps) {
+    const double* x = X + r * ldx;
+    double mx = 0.0;
+    if (r < rows)
+      for (int64_t j = lane; j < n; j += 32) mx = fmax(mx, fabs(x[j]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     int e = 0;
     if (mx > 0.0) frexp(mx, &e);
-    ex[r] = e;
-  }
-}
-
-// Digit planes of rows 0 .. rows-1 (columns 0 .. n-1; columns n .. ldk-1 and rows rows ..
-// rows_pad-1 are written as zeros): round X[r][j] 2^(47 - e_r) to an integer v (|v| <= 2^47)
-// and split it into balanced base-256 digits, most significant in plane 0.  Each plane is
-// tiled by 64-column boxes, [ldk / 64][rows_pad][64], so that every 128-row TMA box is one
-// contiguous 16 KB block of memory.
-__global__ void slice_digits_kernel(const double* __restrict__ X, int64_t ldx, int64_t rows, int64_t n,
-                                    const int* __restrict__ ex, __half* __restrict__ planes, int64_t rows_pad,
-                                    int64_t ldk) {
-  const int64_t total = rows_pad * ldk;
-  const int64_t plane = rows_pad * ldk;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = e / ldk, j = e - r * ldk;
-    long long v = 0;
-    if (r < rows && j < n) v = __double2ll_rn(scalbn(X[r * ldx + j], 47 - ex[r]));
-    int d[kSl];
-    digits6(v, d);
+    if (lane == 0) ex[r] = e;
+    __half* out = planes + r * kKiBox;
+    for (int64_t j = lane; j < ldk; j += 32) {
+      long long v = 0;
+      if (r < rows && j < n) v = __double2ll_rn(scalbn(x[j], 47 - e));
+      int d[kSl];
+      digits6(v, d);
+      const int64_t o = (j / kKiBox) * rows_pad * kKiBox + (j % kKiBox);
 #pragma unroll
-    for (int s = 0; s < kSl; ++s) planes[s * plane + (j / kKiBox) * rows_pad * kKiBox + r * kKiBox + (j % kKiBox)] =
-        __int2half_rn(d[s]);
+      for (int sl = 0; sl < kSl; ++sl) out[sl * plane + o] = __int2half_rn(d[sl]);
+    }
   }
 }
 
@@ -580,15 +574,12 @@ size_t kinv_tc_plane_elems(int64_t n) { return (size_t)kSl * kinv_tc_ld(n) * kin
 
 int64_t kinv_tc_slice(const double* X, int64_t ldx, int64_t rows, int64_t n, int* ex, void* planes_v,
                       int64_t rows_pad, cudaStream_t s) {
-  __half* planes = static_cast<__half*>(planes_v);
-  cudaMemsetAsync(ex, 0, sizeof(int) * (size_t)rows_pad, s);  // padding rows: exponent 0
-  if (rows > 0) row_exponent_kernel<<<(unsigned)rows, 256, 0, s>>>(X, ldx, n, ex);
-  const int64_t ldk = kinv_tc_ld(n);
-  const int64_t total = rows_pad * ldk;
-  int64_t blocks = (total + 255) / 256;
+  if (rows_pad <= 0) return 0;
+  int64_t blocks = (rows_pad + 7) / 8;  // eight warps (rows) per CTA
   if (blocks > 65535 * 8) blocks = 65535 * 8;
-  slice_digits_kernel<<<(unsigned)blocks, 256, 0, s>>>(X, ldx, rows, n, ex, planes, rows_pad, ldk);
-  return rows > 0 ? 2 : 1;
+  slice_rows_kernel<<<(unsigned)blocks, 256, 0, s>>>(X, ldx, rows, n, ex, static_cast<__half*>(planes_v), rows_pad,
+                                                    kinv_tc_ld(n));
+  return 1;
 }
 
 namespace {

@@ -191,7 +191,7 @@ def test_diff_gradient_full_size():
 
 def test_batched_double_fp32_dense_without_refinement_full_size(batched):
     """The batched workload with K's Gram product and the Cholesky's trailing updates in
-    exact digit planes on the tensor cores (panels of 512), the panel steps and triangular
+    exact digit planes on the tensor cores (panels of 4,096, each by recursive halves), the panel steps and triangular
     solves in double-FP32 arithmetic, and no refinement step: the online form for the 1e-6
     latency target.  L and the solves are held to the solve bound 10 kappa(K) 2^-47 of the
     digit planes.  The same through the explicit inverse

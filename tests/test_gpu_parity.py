@@ -683,7 +683,7 @@ def test_online_qoi_via_d2q_map_on_tensor_cores(B):
     h.apply_Q(cuda(d), q)
     n_tc = h.profile_read()[0]["dense"][1]
     if B >= 16:
-        assert n_tc == 4 * ((B + 63) // 64)  # per 64 vectors: their planes (2 kernels), MMAs, sum
+        assert n_tc == 3 * ((B + 63) // 64)  # per 64 vectors: their planes, MMAs, sum
     elif B <= 2:
         assert n_tc == 2  # the vectors as float pairs, then the matrix-vector product
     else:
@@ -1336,7 +1336,7 @@ FACTOR_CASES = [
     ("n770_panel128", 6, 6, 11, 70, 128),    # 6 panels + 2 columns; trailing 642, 514, ..., 2
     ("n720_panel64", 6, 6, 24, 30, 64),      # 11 panels + 16 columns; K = 64: half a digit chunk
     ("n640_panel128_exact", 8, 8, 10, 64, 128),  # trailing 512, 384, 256, 128 rows: whole tiles
-    ("n1200_panel512", 8, 8, 12, 100, 512),  # the default width: two panels and a ragged third
+    ("n1200_panel512", 8, 8, 12, 100, 512),  # two panels and a ragged third
     ("n1200_recursive", 8, 8, 12, 100, 1 << 20),  # one panel: the whole factor by recursive halves
 ]
 
