@@ -1054,46 +1054,84 @@ bti_status bti_invert_K(bti_handle h, int enable) {
     release();
     return st;
   }
-  int64_t nl = identity_blocks(X, 1, n, s);
+  int64_t nl = 0;
   if (tc && h->tc_enabled) {
-    // W^T = (L^{-1})^T by forward solves (rows that can be nonzero only), then
-    // K^{-1} = W^T W on the tensor cores: rows of W^T are both the digit-plane matrix and the
-    // right-hand sides (K^{-1}[j][i] = sum_k W^T[i][k] W^T[j][k]); W^T's planes use the
-    // buffer K^{-1}'s planes take afterwards
-    double* Y = nullptr;
-    st = dev_alloc(h, (void**)&Y, sizeof(double) * (size_t)n * n, "K inverse temporary");
+    // W = L^{-1} on the tensor cores by recursive halves, then K^{-1} = W^T W: the rows of W^T
+    // (the columns of W, zero before the diagonal, so row tile I starts at chunk I) are both
+    // operands of one lower-triangle digit-plane product, mirrored into the upper triangle.
+    // W^T's planes use the buffer that K^{-1}'s planes take afterwards.
+    const int64_t hh = lower_inverse_tc_half(n), ldh = kinv_tc_ld(hh);
+    double* W = nullptr;
+    double* T = nullptr;
+    void* pa = nullptr;
+    void* pb = nullptr;
+    int* eab = nullptr;
+    unsigned long long* colmax = nullptr;
+    st = dev_alloc(h, (void**)&W, sizeof(double) * (size_t)n * n, "inverse factor");
+    if (st == BTI_OK) st = dev_alloc(h, (void**)&T, sizeof(double) * (size_t)hh * hh, "inverse temporary");
+    if (st == BTI_OK) st = dev_alloc(h, &pa, sizeof(uint16_t) * lower_inverse_tc_plane_elems(n), "inverse planes");
+    if (st == BTI_OK) st = dev_alloc(h, &pb, sizeof(uint16_t) * lower_inverse_tc_plane_elems(n), "inverse planes");
+    if (st == BTI_OK) st = dev_alloc(h, (void**)&eab, sizeof(int) * (size_t)(2 * ldh), "inverse exponents");
     if (st == BTI_OK)
-      st = ensure(h, (void**)&h->wsolve, &h->wsolve_bytes,
-                  sizeof(double) * std::max(trsm_work_elems(n, n), rowmat_tc_work_elems(n, n)), "solve workspace");
+      st = dev_alloc(h, (void**)&colmax, sizeof(unsigned long long) * (size_t)(ldt > ldh ? ldt : ldh),
+                     "column maxima");
+    cudaError_t e = cudaSuccess;
+    if (st == BTI_OK) {
+      kinv_tc_prepare();
+      nl += lower_inverse_tc(h->K, h->Linv, n, W, T, pa, eab, pb, eab + ldh, colmax, h->status + 1, s, &e,
+                             h->tc_drop_stage);
+    }
+    if (st == BTI_OK && e == cudaSuccess) {
+      nl += kinv_tc_slice_t(W, n, n, n, h->kinv_ea, h->kinv_planes, ldt, colmax, s);
+      DigitGemm g{};
+      g.C = X;
+      g.ldc = n;
+      g.M = n;
+      g.N = n;
+      g.K = n;
+      g.lower = true;
+      g.op = 0;
+      g.kfirst = 1;
+      g.skip_on_err = true;
+      int64_t tl = 0;
+      e = digit_gemm_tc(h->kinv_planes, h->kinv_ea, h->kinv_planes, h->kinv_ea, g, h->status + 1, s, &tl,
+                        h->tc_drop_stage);
+      nl += tl;
+      nl += symmetrize_lower(X, n, s);
+    }
+    cudaStreamSynchronize(s);
+    dev_freep(W);
+    dev_freep(T);
+    dev_free(pa);
+    dev_free(pb);
+    dev_freep(eab);
+    dev_freep(colmax);
+    if (st == BTI_OK && e != cudaSuccess) st = cuda_check(h, e, "invert_K (tensor-core inverse)");
     if (st != BTI_OK) {
-      dev_freep(Y);
       dev_freep(X);
       release();
       return st;
     }
-    nl += lower_inverse_rows(h->K, h->Linv, n, X, h->wsolve, s, true);
-    nl += kinv_tc_slice(X, n, n, n, h->kinv_ea, h->kinv_planes, ldt, s);
-    int64_t tl = 0;
-    cudaError_t e = rowmat_apply_tc(h->kinv_planes, h->kinv_ea, n, n, X, n, Y, n, h->wsolve, h->status + 1, s, &tl);
-    nl += tl;
-    std::swap(X, Y);
-    dev_freep(Y);
-    if (e != cudaSuccess) {
-      dev_freep(X);
-      release();
-      return cuda_check(h, e, "invert_K (tensor-core W^T W)");
-    }
   } else {
     // rows of X: K^{-1} e_b (= row b of the symmetric K^{-1}), by both triangular solves
+    nl += identity_blocks(X, 1, n, s);
     nl += trsm_lower_f64(h->K, h->Linv, n, X, n, h->wsolve, h->status, s, true);
   }
   nl += split_to_pairs(X, h->Kinv, n, ldk, s);
   if (tc) nl += kinv_tc_slice(X, n, n, n, h->kinv_ea, h->kinv_planes, ldt, s);
   count_dense(h, nl);
   st = launched(h, "invert_K");
-  bti_status sy = cuda_check(h, cudaStreamSynchronize(s), "invert_K sync");
+  int stat2[2] = {0, 0};
+  bti_status sy = cuda_check(h, cudaMemcpyAsync(stat2, h->status, 2 * sizeof(int), cudaMemcpyDeviceToHost, s),
+                             "status");
+  if (sy == BTI_OK) sy = cuda_check(h, cudaStreamSynchronize(s), "invert_K sync");
   dev_freep(X);
   if (st == BTI_OK) st = sy;
+  if (st == BTI_OK && stat2[1] != 0) {
+    cudaMemsetAsync(h->status + 1, 0, sizeof(int), s);
+    cudaStreamSynchronize(s);
+    st = fail(h, BTI_ERR_TIMEOUT, "invert_K: a bounded wait in a tensor-core product gave up");
+  }
   if (st != BTI_OK) {
     release();
     return st;

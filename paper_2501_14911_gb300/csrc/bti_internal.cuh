@@ -216,10 +216,6 @@ constexpr int kCholNB = 64;
 int64_t trsm_lower_f64(const double* Lm, const double* Linv, int64_t n, double* X, int64_t B,
                        double* work, const int* status, cudaStream_t s, bool dd = false);
 size_t trsm_work_elems(int64_t n, int64_t B);
-// X (n x n, = I on entry) := (L^{-1})^T, the forward solves against the identity restricted to
-// the rows that can be nonzero; work of trsm_work_elems(n, n).
-int64_t lower_inverse_rows(const double* Lm, const double* Linv, int64_t n, double* X, double* work,
-                           cudaStream_t s, bool dd);
 // Explicit inverse for the online solve: Kinv [n][kinv_ld(n)] float pairs (hi, lo) of K^{-1}
 // (zero padding); X [B][n] = rows K^{-1} D[b] for D [B][n] (X != D); work of
 // kinv_apply_work_elems(n, B) doubles.  split_to_pairs: FP64 X [n][n] -> pairs Y [n][ldk].
@@ -274,6 +270,40 @@ cudaError_t rowmat_apply_tc(const void* planes, const int* ea, int64_t M, int64_
 // the tensor-core updates of cholesky_tc.
 cudaError_t syrk_lower_tc(const void* planes, const int* ex, int64_t m, int64_t w, int64_t kdim, double* C,
                           int64_t ldc, int* err, cudaStream_t s, int64_t* launches, int drop_stage = -1);
+// Digit planes of the transpose of a rows x cols block of X (row stride ldx): planes row c = column
+// c of X, K = rows; rows_pad >= kinv_tc_ld(cols); colmax: cols scratch words.  Three launches.
+int64_t kinv_tc_slice_t(const double* X, int64_t ldx, int64_t rows, int64_t cols, int* ex, void* planes,
+                        int64_t rows_pad, unsigned long long* colmax, cudaStream_t s);
+// C (op)= A B^T for A (M x K) and B (N x K) given by digit planes and row exponents, over tiles
+// of 128 rows x 64 columns; lower: only the tiles and entries on and below the diagonal (N <= M).
+// op: 0 C = v, 1 C -= v, 2 C = -v.  kfirst / klast skip chunks of 128 along K that triangular
+// operands make zero: kfirst 1 starts row tile I at chunk I (A K-major upper triangular, row i
+// zero for k < i), 2 starts column tile J at chunk floor(64 J / 128) (B K-major upper
+// triangular); klast 1 ends row tile I at chunk I (A lower triangular, row i zero for k > i).
+// skip_on_err: do nothing if *err is already set (a chain of products after a timeout).  Npad:
+// B's padded row count if its planes were formed for more rows than N (0: kinv_tc_ld(N)).
+struct DigitGemm {
+  double* C;
+  int64_t ldc, M, N, K;
+  int64_t Npad;
+  bool lower;
+  int op, kfirst, klast;
+  bool skip_on_err;
+};
+cudaError_t digit_gemm_tc(const void* pa, const int* ea, const void* pb, const int* eb, const DigitGemm& g, int* err,
+                          cudaStream_t s, int64_t* launches, int drop_stage = -1);
+// W = L^{-1} for the n x n lower-triangular factor L (row stride n; the inverses of its 64 x 64
+// diagonal blocks in Linv), on the tensor cores by recursive halves (cholesky_tc's planes).
+// W: n x n, zero above the diagonal.  Work: T (h x h doubles), planes pa / pb (each
+// lower_inverse_tc_plane_elems(n) halves), exponents ea / eb and colmax (kinv_tc_ld(h) each),
+// h = lower_inverse_tc_half(n).
+int64_t lower_inverse_tc_half(int64_t n);
+size_t lower_inverse_tc_plane_elems(int64_t n);
+int64_t lower_inverse_tc(const double* L, const double* Linv, int64_t n, double* W, double* T, void* pa, int* ea,
+                         void* pb, int* eb, unsigned long long* colmax, int* err, cudaStream_t s, cudaError_t* cerr,
+                         int drop_stage = -1);
+// Mirror the lower triangle of the n x n matrix X (row stride n) into its upper triangle.
+int symmetrize_lower(double* X, int64_t n, cudaStream_t s);
 // Blocked Cholesky with panels of P columns (a multiple of 64), each panel factored
 // recursively: its left half, then the update of its right half on the tensor cores, then the
 // right half; 64-column leaves take the FP64 diagonal block and the double-FP32 solve of the

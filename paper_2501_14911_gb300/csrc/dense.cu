@@ -664,6 +664,129 @@ int64_t cholesky_tc(double* A, int64_t n, int64_t P, double* Linv, double* work,
   return c.launches;
 }
 
+// ------------------------------------------------------------------ inverse of the factor
+// W = L^{-1} on the tensor cores, for the explicit inverse K^{-1} = W^T W of the online phase
+// (Eq. (4.13) with both triangular solves moved offline).  Recursively by halves: with
+// L = [L11 0; L21 L22] and W11 = L11^{-1}, W22 = L22^{-1} known, W21 = -W22 (L21 W11).  Both
+// products are digit-plane GEMMs (digit_gemm_tc) of K-major operands: T = L21 W11 takes L21's
+// rows and W11's columns (the rows of W11^T, zero before the diagonal, so column tile J starts at
+// chunk J / 2); W21 = -W22 T takes W22's rows (zero past the diagonal: row tile I ends at chunk
+// I) and T's columns.  The 64 x 64 diagonal blocks are the factorisation's FP64 inverses.
+namespace {
+// W's diagonal 64 x 64 blocks from Linv ([nblk][64][64]); the rest of W is zero beforehand
+__global__ void diag_blocks_kernel(const double* __restrict__ Linv, int64_t n, double* __restrict__ W) {
+  const int64_t b = blockIdx.x;
+  for (int i = threadIdx.x; i < kCholNB * kCholNB; i += blockDim.x) {
+    const int r = i / kCholNB, c = i - r * kCholNB;
+    const int64_t gr = b * kCholNB + r, gc = b * kCholNB + c;
+    if (gr < n && gc < n) W[gr * n + gc] = Linv[b * kCholNB * kCholNB + i];
+  }
+}
+
+// X[c][r] = X[r][c] for r > c, by 32 x 32 tiles through shared memory (tile (R, C), C < R, is
+// read by rows and written transposed into tile (C, R); diagonal tiles mirror in place)
+__global__ void __launch_bounds__(256) symmetrize_kernel(double* X, int64_t n) {
+  __shared__ double t[32][33];
+  const int64_t R = blockIdx.y, C = blockIdx.x;
+  if (C > R) return;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int j = ty; j < 32; j += 8) {
+    const int64_t r = R * 32 + j, c = C * 32 + tx;
+    t[j][tx] = (r < n && c < n) ? X[r * n + c] : 0.0;
+  }
+  __syncthreads();
+  for (int j = ty; j < 32; j += 8) {
+    const int64_t r = C * 32 + j, c = R * 32 + tx;  // upper entry (r, c) = lower entry (c, r)
+    if (r < n && c < n && c > r) X[r * n + c] = t[tx][j];
+  }
+}
+
+struct InvTc {
+  const double* L;
+  int64_t n;
+  double* W;
+  double* T;
+  void* pa;
+  int* ea;
+  void* pb;
+  int* eb;
+  unsigned long long* colmax;
+  int* err;
+  cudaStream_t s;
+  int drop_stage;
+  int64_t launches = 0;
+  cudaError_t cerr = cudaSuccess;
+};
+
+void inv_gemm(InvTc& v, const DigitGemm& g) {
+  if (v.cerr != cudaSuccess) return;
+  int64_t tl = 0;
+  v.cerr = digit_gemm_tc(v.pa, v.ea, v.pb, v.eb, g, v.err, v.s, &tl, v.drop_stage);
+  v.launches += tl;
+}
+
+// W[c0:c0+w, c0:c0+w] = L[c0:c0+w, c0:c0+w]^{-1}
+void inv_rec(InvTc& v, int64_t c0, int64_t w) {
+  if (w <= kCholNB || v.cerr != cudaSuccess) return;
+  const int64_t h = (w / 2 + kCholNB - 1) / kCholNB * kCholNB, m2 = w - h, n = v.n;
+  inv_rec(v, c0, h);
+  inv_rec(v, c0 + h, m2);
+  // T = L21 W11 (m2 x h, row stride h)
+  v.launches += kinv_tc_slice(v.L + (c0 + h) * n + c0, n, m2, h, v.ea, v.pa, kinv_tc_ld(m2), v.s);
+  v.launches += kinv_tc_slice_t(v.W + c0 * n + c0, n, h, h, v.eb, v.pb, kinv_tc_ld(h), v.colmax, v.s);
+  DigitGemm g{};
+  g.C = v.T;
+  g.ldc = h;
+  g.M = m2;
+  g.N = h;
+  g.K = h;
+  g.op = 0;
+  g.kfirst = 2;
+  g.skip_on_err = true;
+  inv_gemm(v, g);
+  // W21 = -W22 T (m2 x h, into W)
+  v.launches += kinv_tc_slice(v.W + (c0 + h) * n + (c0 + h), n, m2, m2, v.ea, v.pa, kinv_tc_ld(m2), v.s);
+  v.launches += kinv_tc_slice_t(v.T, h, m2, h, v.eb, v.pb, kinv_tc_ld(h), v.colmax, v.s);
+  g = DigitGemm{};
+  g.C = v.W + (c0 + h) * n + c0;
+  g.ldc = n;
+  g.M = m2;
+  g.N = h;
+  g.K = m2;
+  g.op = 2;
+  g.klast = 1;
+  g.skip_on_err = true;
+  inv_gemm(v, g);
+}
+}  // namespace
+
+int64_t lower_inverse_tc_half(int64_t n) { return (n / 2 + kCholNB - 1) / kCholNB * kCholNB; }
+
+size_t lower_inverse_tc_plane_elems(int64_t n) {
+  const int64_t h = kinv_tc_ld(lower_inverse_tc_half(n));
+  return (size_t)6 * h * h;
+}
+
+int64_t lower_inverse_tc(const double* L, const double* Linv, int64_t n, double* W, double* T, void* pa, int* ea,
+                         void* pb, int* eb, unsigned long long* colmax, int* err, cudaStream_t s, cudaError_t* cerr,
+                         int drop_stage) {
+  InvTc v{L, n, W, T, pa, ea, pb, eb, colmax, err, s, drop_stage};
+  cudaMemsetAsync(W, 0, sizeof(double) * (size_t)n * n, s);
+  const int64_t nblk = (n + kCholNB - 1) / kCholNB;
+  diag_blocks_kernel<<<(unsigned)nblk, 256, 0, s>>>(Linv, n, W);
+  v.launches = 1;
+  inv_rec(v, 0, n);
+  *cerr = v.cerr;
+  return v.launches;
+}
+
+int symmetrize_lower(double* X, int64_t n, cudaStream_t s) {
+  if (n <= 0) return 0;
+  const unsigned t = (unsigned)((n + 31) / 32);
+  symmetrize_kernel<<<dim3(t, t), 256, 0, s>>>(X, n);
+  return 1;
+}
+
 // ------------------------------------------------------------------ triangular solves
 size_t trsm_work_elems(int64_t n, int64_t B) { return (size_t)B * kCholNB; }
 
@@ -952,29 +1075,6 @@ int64_t kinv_apply(const float2* Kinv, int64_t n, const double* D, int64_t B, do
       kinv_apply_kernel<128, 4, 2, 1><<<(unsigned)p.ctas, 256, sm, s>>>(Kinv, ldk, n, Dp, nb, part, p.per,
                                                                       p.total, p.kpt, p.span);
     launches += 1 + kinv_reduce(part, X + q0 * n, n, n, nb, p.BM, p.BR, p.per, p.kpt, p.span, p.tiles, s);
-  }
-  return launches;
-}
-
-// X := W^T with W = L^{-1}, starting from X = I (row b of the result is L^{-1} e_b, column b
-// of W): the forward half of trsm_lower_f64 on the identity, where row b stays zero before
-// column b, so block step k only touches the k + kb rows that can be nonzero (about n^3 / 3
-// flop instead of n^3).
-int64_t lower_inverse_rows(const double* Lm, const double* Linv, int64_t n, double* X, double* work,
-                           cudaStream_t s, bool dd) {
-  const int nb = kCholNB;
-  int64_t launches = 0;
-  for (int64_t k = 0; k < n; k += nb) {
-    const int kb = (int)std::min<int64_t>(nb, n - k);
-    const int64_t rows = k + kb;  // rows k + kb .. n - 1 are still zero in columns < k + kb
-    const double* Lk = Linv + (k / nb) * nb * nb;
-    launches += gemm_sel(dd, true, rows, kb, kb, 1.0, X + k, n, Lk, nb, 0.0, work, kb, false, s);
-    cudaMemcpy2DAsync(X + k, n * sizeof(double), work, kb * sizeof(double), kb * sizeof(double), rows,
-                      cudaMemcpyDeviceToDevice, s);
-    const int64_t m = n - k - kb;
-    if (m > 0)
-      launches += gemm_sel(dd, true, rows, m, kb, -1.0, X + k, n, Lm + (k + kb) * n + k, n, 1.0, X + k + kb, n,
-                           false, s);
   }
   return launches;
 }

@@ -286,6 +286,64 @@ slice_rows_kernel(const double* __restrict__ X, int64_t ldx, int64_t rows, int64
   }
 }
 
+// Column maxima of a rows x cols block of X (row stride ldx) as FP64 bit patterns (|x| >= 0 orders
+// like its bits): CTA (column block of 64, row block of 256), four threads per column.
+__global__ void __launch_bounds__(256)
+col_max_kernel(const double* __restrict__ X, int64_t ldx, int64_t rows, int64_t cols,
+               unsigned long long* __restrict__ colmax) {
+  __shared__ double red[4][64];
+  const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
+  const int64_t c = (int64_t)blockIdx.x * 64 + tx;
+  const int64_t r0 = (int64_t)blockIdx.y * 256;
+  double mx = 0.0;
+  if (c < cols)
+    for (int64_t r = r0 + ty; r < rows && r < r0 + 256; r += 4) mx = fmax(mx, fabs(X[r * ldx + c]));
+  red[ty][tx] = mx;
+  __syncthreads();
+  if (ty == 0 && c < cols) {
+    mx = fmax(fmax(red[0][tx], red[1][tx]), fmax(red[2][tx], red[3][tx]));
+    atomicMax(&colmax[c], (unsigned long long)__double_as_longlong(mx));
+  }
+}
+
+// Digit planes of the transpose of a rows x cols block of X: row c of X^T (column c of X) is
+// planes row c with K index k = row of X, exponent from colmax[c]; the same layout and padding
+// as slice_rows_kernel ([6][ldk / 64][rows_pad][64], rows_pad >= cols, ldk >= rows, zeros past
+// them).  CTA = (64-value K tile, 64 output rows): the 64 x 64 block of X through shared memory,
+// so both its reads (rows of X) and its writes (64 K values of an output row) are contiguous.
+__global__ void __launch_bounds__(256)
+slice_cols_kernel(const double* __restrict__ X, int64_t ldx, int64_t rows, int64_t cols,
+                  const unsigned long long* __restrict__ colmax, int* __restrict__ ex, __half* __restrict__ planes,
+                  int64_t rows_pad, int64_t ldk) {
+  __shared__ double t[64][65];
+  const int64_t k0 = (int64_t)blockIdx.x * 64, c0 = (int64_t)blockIdx.y * 64;
+  for (int i = threadIdx.x; i < 64 * 64; i += 256) {
+    const int kr = i >> 6, cc = i & 63;
+    const int64_t k = k0 + kr, c = c0 + cc;
+    t[kr][cc] = (k < rows && c < cols) ? X[k * ldx + c] : 0.0;
+  }
+  __syncthreads();
+  const int cc = threadIdx.x >> 2, kq = (threadIdx.x & 3) * 16;
+  const int64_t c = c0 + cc;
+  int e = 0;
+  if (c < cols) {
+    const double mx = __longlong_as_double((long long)colmax[c]);
+    if (mx > 0.0) frexp(mx, &e);
+  }
+  if (blockIdx.x == 0 && (threadIdx.x & 3) == 0 && c < rows_pad) ex[c] = e;
+  const int64_t plane = rows_pad * ldk;
+  __half* out = planes + (k0 / kKiBox) * rows_pad * kKiBox + c * kKiBox + kq;
+#pragma unroll 4
+  for (int j = 0; j < 16; ++j) {
+    long long v = 0;
+    if (c < cols) v = __double2ll_rn(scalbn(t[kq + j][cc], 47 - e));
+    int d[kSl];
+    digits6(v, d);
+#pragma unroll
+    for (int sl = 0; sl < kSl; ++sl) out[sl * plane + j] = __int2half_rn(d[sl]);
+  }
+}
+
 // Tile T of the lower trapezoid of 128-row tiles I and 64-column tiles J < JW with J <= 2 I + 1
 // (the column tiles that reach row tile I's diagonal): rows I < I0 = JW / 2 hold 2 I + 2 tiles
 // (T = I (I + 1) + J), the rows after them JW tiles each.
@@ -303,29 +361,99 @@ __device__ __forceinline__ void trap_tile(int64_t T, int64_t JW, int64_t& I, int
   J = T - i * (i + 1);
 }
 
-// Stream-K digit-plane GEMM: D[m][c] = sum_k A[m][k] B[c][k] for tiles of 128 rows m x NC
-// columns c, the K axis in exact chunks of 128.  Tile T is (w, rg) = (T / NRG, T % NRG) (a
-// problem and a group within it); the 64-column memory tile kbg of tile T sits at TMA row
-// (w KB + kbg) a_blk + rg a_rg of the A planes and (w KB + kbg) b_blk + rg b_rg of the B planes
-// (KB = 2 kpt); the pipeline loads it as two 32-column boxes.  Only the first ksteps 16-column
+// Which (tile, chunk) work items a CTA takes, in order, and where each tile's result goes.
+// Stream-K (tiles == false): units [blockIdx per, + per) of the (tile, chunk) sequence, one FP64
+// partial tile per tile touched.  Tile mode (tiles == true): tiles blockIdx, blockIdx + grid, ...
+// of a rectangle (T = I JW + J) or of the lower trapezoid (trap_tile), each over its chunk range
+// [c0, c1) whole, the result combined into C by op.  The chunk range skips chunks whose A rows
+// (row tile I of a lower-triangular A: k < 128 (I + 1)) or B rows (column tile J of the transpose
+// of a lower-triangular matrix, or of a triangular inverse: k >= NC J; K-major rows of an upper-
+// triangular matrix: k >= 128 I) are known to be zero.
+struct TileJob {
+  double* C;
+  int64_t ldc, mvalid, wvalid;  // C row stride; rows and columns of C written
+  int64_t JW, tiles;            // column tiles; tiles in the enumeration
+  int trap;                     // 1: lower trapezoid, 0: rectangle
+  int lower;                    // 1: write only on and below the diagonal (j <= i)
+  int op;                       // 0: C = v, 1: C -= v, 2: C = -v
+  int kfirst;                   // first chunk: 0; 1: I; 2: floor(NC J / 128)
+  int klast;                    // chunk range end: 0: kpt; 1: I + 1
+  int skip_on_err;              // 1: return at once if *err is already set
+};
+
+template <bool TILES, int NC>
+struct WorkIter {
+  int64_t T, c, c1, I, J, u, u1, kpt;
+  bool valid;
+  __device__ __forceinline__ void tile_range(const TileJob& tj) {
+    if (tj.trap) {
+      trap_tile(T, tj.JW, I, J);
+    } else {
+      I = T / tj.JW;
+      J = T - I * tj.JW;
+    }
+    c = tj.kfirst == 1 ? I : (tj.kfirst == 2 ? (J * NC) / kKiChunk : 0);
+    c1 = tj.klast == 1 ? I + 1 : kpt;
+    if (c1 > kpt) c1 = kpt;
+  }
+  __device__ __forceinline__ void seek(const TileJob& tj) {  // first nonempty tile from T on
+    for (; T < tj.tiles; T += gridDim.x) {
+      tile_range(tj);
+      if (c < c1) return;
+    }
+    valid = false;
+  }
+  __device__ __forceinline__ void init(const TileJob& tj, int64_t per, int64_t total, int64_t kpt_) {
+    kpt = kpt_;
+    valid = true;
+    if constexpr (TILES) {
+      T = blockIdx.x;
+      seek(tj);
+    } else {
+      u = (int64_t)blockIdx.x * per;
+      u1 = min(total, u + per);
+      valid = u < u1;
+      T = u / kpt;
+      c = u - T * kpt;
+    }
+  }
+  __device__ __forceinline__ bool last() const {
+    if constexpr (TILES) return c + 1 == c1;
+    return u + 1 == u1 || (u + 1) / kpt != T;
+  }
+  __device__ __forceinline__ void next(const TileJob& tj) {
+    if constexpr (TILES) {
+      if (++c < c1) return;
+      T += gridDim.x;
+      seek(tj);
+    } else {
+      ++u;
+      valid = u < u1;
+      T = u / kpt;
+      c = u - T * kpt;
+    }
+  }
+};
+
+// Digit-plane GEMM: D[m][c] = sum_k A[m][k] B[c][k] for tiles of 128 rows m x NC columns c, the
+// K axis in exact chunks of 128.  Stream-K form (TILES = false): tile T is (w, rg) = (T / NRG,
+// T % NRG) (a problem and a group within it); the 64-column memory tile kbg of tile T sits at
+// TMA row (w KB + kbg) a_blk + rg a_rg of the A planes and (w KB + kbg) b_blk + rg b_rg of the B
+// planes (KB = 2 kpt); row m's exponent is ea[w ea_w + rg ea_rg + m], column c's
+// eb[w eb_w + rg eb_rg + c] (padding rows and columns hold 0); a CTA covers units
+// [blockIdx per, + per) and writes one FP64 partial tile [NC][128] per tile it touches.  Tile
+// form (TILES = true, the Cholesky's updates and the triangular products of the inverse): tile
+// (I, J) of tj reads A rows 128 I and B rows NC J (a_blk, b_blk: the planes' padded row counts),
+// exponents ea[128 I + m] and eb[NC J + c], and combines its result into tj.C.  Either way the
+// pipeline loads each memory tile as two 32-column boxes, and only the first ksteps 16-column
 // K-steps hold data (the rest of the last chunk is padding, neither loaded nor multiplied).
-// Row m's exponent is ea[w ea_w + rg ea_rg + m], column c's eb[w eb_w + rg eb_rg + c]
-// (padding rows and columns hold 0).  A CTA covers units [blockIdx per, + per) of the
-// (tile, chunk) sequence and writes one FP64 partial tile [NC][128] per tile it touches.
-//
-// SYRK form (the Cholesky's updates): A and B are the same planes of a matrix X (rows 0 ..
-// mvalid - 1), tile T is the lower-trapezoid tile (I, J) of trap_tile with JW = NRG (A rows
-// 128 I, B rows NC J, a_blk = b_blk = the planes' padded row count), each CTA's run holds whole
-// tiles (per is a multiple of kpt), and the epilogue subtracts the tile from part = C (row
-// stride ldc) on and below the diagonal: C[i][j] -= sum_k X[i][k] X[j][k], j <= i < mvalid,
-// j < wvalid.
-template <int NC, bool SYRK = false>
+template <int NC, bool TILES = false>
 __global__ void __launch_bounds__(kKiThreads, 1)
 sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
              const int* __restrict__ ea, const int* __restrict__ eb, double* __restrict__ part, int64_t per,
              int64_t total, int64_t kpt, int span, int NRG, int64_t a_blk, int a_rg, int64_t b_blk, int b_rg,
              int ea_w, int ea_rg, int eb_w, int eb_rg, int64_t ksteps, int drop_stage, int* __restrict__ err,
-             int64_t ldc, int64_t mvalid, int64_t wvalid) {
+             const TileJob tj) {
   constexpr uint32_t kBPlane = NC * kBx * 2, kBStage = kSl * kBPlane;
   constexpr uint32_t kACol = kSl * NC;  // TMEM column of the two A buffers (48 columns each)
   constexpr int W = NC / 2;             // columns per epilogue thread
@@ -338,18 +466,17 @@ sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
   __shared__ int abort_flag;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if constexpr (SYRK) {
-    // a bounded wait of an earlier update in the same factorisation gave up: the matrix is no
-    // longer meaningful, so skip the work (read once, so the whole CTA agrees)
-    __shared__ int skip;
-    if (tid == 0) skip = *(volatile int*)err;
-    __syncthreads();
-    if (skip) return;
+  if constexpr (TILES) {
+    if (tj.skip_on_err) {
+      // a bounded wait of an earlier product of the same chain gave up: its result is no
+      // longer meaningful, so skip the work (read once, so the whole CTA agrees)
+      __shared__ int skip;
+      if (tid == 0) skip = *(volatile int*)err;
+      __syncthreads();
+      if (skip) return;
+    }
   }
-  const int64_t u0 = (int64_t)blockIdx.x * per;
-  const int64_t u1 = min(total, u0 + per);
-  const int64_t first_tile = u0 / kpt;
-  const int nunits = (int)(u1 - u0);
+  const int64_t first_tile = ((int64_t)blockIdx.x * per) / kpt;  // stream-K: first tile of the run
   const int KB = (int)(kpt * (kKiChunk / kKiBox));
   // K-steps and 32-column boxes of chunk c (the last chunk may be partly padding)
   auto chunk_ksteps = [&](int64_t c) { return (int)min((int64_t)(kKiChunk / 16), ksteps - c * (kKiChunk / 16)); };
@@ -382,15 +509,14 @@ sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     if (lane == 0) {
       int nbx = 0;
       bool ok = true;
-      for (int u = 0; u < nunits && ok; ++u) {
-        const int64_t unit = u0 + u, T = unit / kpt, c = unit - T * kpt;
+      WorkIter<TILES, NC> it;
+      for (it.init(tj, per, total, kpt); it.valid && ok; it.next(tj)) {
+        const int64_t T = it.T, c = it.c;
         int64_t w, ta, tb;  // problem, and the tile's row offsets in A and in B
-        if constexpr (SYRK) {
-          int64_t I, J;
-          trap_tile(T, NRG, I, J);
+        if constexpr (TILES) {
           w = 0;
-          ta = I * kKiRows;
-          tb = J * NC;
+          ta = it.I * kKiRows;
+          tb = it.J * NC;
         } else {
           w = T / NRG;
           const int64_t rg = T - w * NRG;
@@ -438,13 +564,13 @@ sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     // one of two tensor-memory buffers, which the K-step two earlier must have finished reading
     {
       const uint32_t idesc = (1u << 4) | ((uint32_t)(NC >> 3) << 17) | ((uint32_t)(kKiRows >> 4) << 24);
-      int nbx = 0, ks = 0;
+      int nbx = 0, ks = 0, cc = 0;
       bool ok = true;
-      for (int u = 0; u < nunits && ok; ++u) {
-        const int64_t unit = u0 + u, T = unit / kpt, c = unit - T * kpt;
-        const int nks = chunk_ksteps(c);
+      WorkIter<TILES, NC> it;
+      for (it.init(tj, per, total, kpt); it.valid && ok; it.next(tj), ++cc) {
+        const int nks = chunk_ksteps(it.c);
         // the epilogue has drained the previous chunk's groups
-        if (u > 0 && !mbar_wait_warp(smem_u32(&tfree), (u - 1) & 1, abort_v)) break;
+        if (cc > 0 && !mbar_wait_warp(smem_u32(&tfree), (cc - 1) & 1, abort_v)) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
         for (int kb = 0; kb < (nks + 1) / 2 && ok; ++kb, ++nbx) {
           const int st = nbx % kStages;
@@ -481,33 +607,35 @@ sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     float Sh[W], Sl[W];
 #pragma unroll
     for (int c = 0; c < W; ++c) Sh[c] = Sl[c] = 0.f;
-    for (int u = 0; u < nunits; ++u) {
-      const int64_t unit = u0 + u, T = unit / kpt;
-      if (!mbar_wait(smem_u32(&accf), u & 1, abort_v)) break;
+    int cc = 0;
+    WorkIter<TILES, NC> it;
+    for (it.init(tj, per, total, kpt); it.valid; it.next(tj), ++cc) {
+      const int64_t T = it.T;
+      if (!mbar_wait(smem_u32(&accf), cc & 1, abort_v)) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
       add_groups<NC, W>(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(h * W), Sh, Sl);
       asm volatile("tcgen05.fence::before_thread_sync;");
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tfree)) : "memory");
-      // last unit of this tile within the CTA's run: write the partial tile
-      if (u == nunits - 1 || (unit + 1) / kpt != T) {
-        if constexpr (SYRK) {
-          int64_t I, J;
-          trap_tile(T, NRG, I, J);
-          const int64_t row = I * kKiRows + r;
-          if (row < mvalid) {
-            const int er = ea[row];
-            double* Crow = part + row * ldc;
+      if (!it.last()) continue;
+      // the tile's last chunk in this CTA's share: write the result
+      if constexpr (TILES) {
+        const int64_t row = it.I * kKiRows + r;
+        if (row < tj.mvalid) {
+          const int er = ea[row];
+          double* Crow = tj.C + row * tj.ldc;
 #pragma unroll
-            for (int c = 0; c < W; ++c) {
-              const int64_t col = J * NC + h * W + c;
-              if (col <= row && col < wvalid) Crow[col] -= pair_to_double_scaled(Sh[c], Sl[c], er + eb[col] - 14);
+          for (int c = 0; c < W; ++c) {
+            const int64_t col = it.J * NC + h * W + c;
+            if (col < tj.wvalid && (!tj.lower || col <= row)) {
+              const double v = pair_to_double_scaled(Sh[c], Sl[c], er + eb[col] - 14);
+              Crow[col] = tj.op == 0 ? v : (tj.op == 1 ? Crow[col] - v : -v);
             }
           }
-#pragma unroll
-          for (int c = 0; c < W; ++c) Sh[c] = Sl[c] = 0.f;
-          continue;
         }
+#pragma unroll
+        for (int c = 0; c < W; ++c) Sh[c] = Sl[c] = 0.f;
+      } else {
         const int64_t w = T / NRG, rg = T - w * NRG;
         const int er = ea[w * ea_w + rg * ea_rg + r];
         const int* ebt = eb + w * eb_w + rg * eb_rg;
@@ -649,7 +777,7 @@ cudaError_t rowmat_apply_tc(const void* planes, const int* ea, int64_t M, int64_
     // tiles: the 128-row tiles of the matrix (one problem); A rows kbg Mp + 128 t, B rows 64 kbg
     sk_tc_kernel<64><<<(unsigned)p.ctas, kKiThreads, dig_smem(64), s>>>(
         tA, tB, ea, eb, part, p.per, p.total, p.kpt, p.span, (int)p.tiles, Mp, kKiRows, kKiN, 0, 0, kKiRows, 0, 0,
-        (n + 15) / 16, drop_stage, err, 0, 0, 0);
+        (n + 15) / 16, drop_stage, err, TileJob{});
     *launches += 1;
     *launches += kinv_reduce(part, X + q0 * ldx, ldx, M, nb, kKiRows, kKiN, p.per, p.kpt, p.span, p.tiles, s);
   }
@@ -661,35 +789,77 @@ cudaError_t kinv_apply_tc(const void* planes, const int* ea, int64_t n, const do
   return rowmat_apply_tc(planes, ea, n, n, D, B, X, n, work, err, s, launches, drop_stage);
 }
 
-// The Cholesky's updates C -= X X[0:w]^T on and below the diagonal (Sec. 4, Phase 2), X the
-// m x kdim block whose planes kinv_tc_slice formed with rows_pad = kinv_tc_ld(m), w <= m (w = m:
-// the whole lower triangle).  The lower-trapezoid tiles (128 rows x 64 columns, K = kdim in
-// exact chunks) are dealt out in runs of whole tiles, one run per SM, so no partial tiles and no
-// reduction: the epilogue subtracts in place.
-cudaError_t syrk_lower_tc(const void* planes, const int* ex, int64_t m, int64_t w, int64_t kdim, double* C,
-                          int64_t ldc, int* err, cudaStream_t s, int64_t* launches, int drop_stage) {
+int64_t kinv_tc_slice_t(const double* X, int64_t ldx, int64_t rows, int64_t cols, int* ex, void* planes,
+                        int64_t rows_pad, unsigned long long* colmax, cudaStream_t s) {
+  if (rows_pad <= 0) return 0;
+  const int64_t ldk = kinv_tc_ld(rows);
+  cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * (size_t)(cols > 0 ? cols : 1), s);
+  int64_t nl = 0;
+  if (rows > 0 && cols > 0) {
+    col_max_kernel<<<dim3((unsigned)((cols + 63) / 64), (unsigned)((rows + 255) / 256)), 256, 0, s>>>(X, ldx, rows,
+                                                                                                  cols, colmax);
+    ++nl;
+  }
+  slice_cols_kernel<<<dim3((unsigned)(ldk / 64), (unsigned)(rows_pad / 64)), 256, 0, s>>>(
+      X, ldx, rows, cols, colmax, ex, static_cast<__half*>(planes), rows_pad, ldk);
+  return nl + 1;
+}
+
+// C (op)= A B^T over 128 x 64 tiles (Sec. 4, Phase 2: the Cholesky's updates and the inverse of its
+// factor), A and B given by digit planes (rows padded to kinv_tc_ld(M), kinv_tc_ld(N); K columns)
+// and row exponents; A and B may be the same planes.  Lower: the lower trapezoid of tiles only,
+// written on and below the diagonal (N <= M).  Tiles are dealt round-robin to one CTA per SM.
+cudaError_t digit_gemm_tc(const void* pa, const int* ea, const void* pb, const int* eb, const DigitGemm& g, int* err,
+                          cudaStream_t s, int64_t* launches, int drop_stage) {
   *launches = 0;
-  if (m <= 0 || w <= 0 || kdim <= 0) return cudaSuccess;
-  if (w > m) return cudaErrorInvalidValue;
+  if (g.M <= 0 || g.N <= 0 || g.K <= 0) return cudaSuccess;
+  if (g.lower && g.N > g.M) return cudaErrorInvalidValue;
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return cudaErrorNotSupported;
-  const int64_t Mp = kinv_tc_ld(m), ld = kinv_tc_ld(kdim);
-  const int64_t RT = Mp / kKiRows, JW = (w + kKiN - 1) / kKiN, I0 = JW / 2;
-  const int64_t tiles = I0 * (I0 + 1) + (RT - I0) * JW;
-  const int64_t kpt = ld / kKiChunk;
-  const int64_t slots = num_sms_tc();
-  const int64_t tpc = (tiles + slots - 1) / slots;
-  const int64_t ctas = (tiles + tpc - 1) / tpc;
+  const int64_t Mp = kinv_tc_ld(g.M), Np = g.Npad > 0 ? g.Npad : kinv_tc_ld(g.N), ld = kinv_tc_ld(g.K);
+  const int64_t RT = Mp / kKiRows, JW = (g.N + kKiN - 1) / kKiN, I0 = JW / 2;
+  TileJob tj{};
+  tj.C = g.C;
+  tj.ldc = g.ldc;
+  tj.mvalid = g.M;
+  tj.wvalid = g.N;
+  tj.JW = JW;
+  tj.trap = g.lower ? 1 : 0;
+  tj.tiles = g.lower ? I0 * (I0 + 1) + (RT - I0) * JW : RT * JW;
+  tj.lower = g.lower ? 1 : 0;
+  tj.op = g.op;
+  tj.kfirst = g.kfirst;
+  tj.klast = g.klast;
+  tj.skip_on_err = g.skip_on_err ? 1 : 0;
+  const int64_t ctas = tj.tiles < num_sms_tc() ? tj.tiles : num_sms_tc();
   CUtensorMap tA, tB;
-  if (!encode_planes(enc, &tA, planes, ld / kKiBox * Mp, Mp * ld, kKiRows) ||
-      !encode_planes(enc, &tB, planes, ld / kKiBox * Mp, Mp * ld, kKiN))
+  if (!encode_planes(enc, &tA, pa, ld / kKiBox * Mp, Mp * ld, kKiRows) ||
+      !encode_planes(enc, &tB, pb, ld / kKiBox * Np, Np * ld, kKiN))
     return cudaErrorInvalidValue;
   kinv_tc_prepare();
   sk_tc_kernel<64, true><<<(unsigned)ctas, kKiThreads, dig_smem(64), s>>>(
-      tA, tB, ex, ex, C, tpc * kpt, tiles * kpt, kpt, 1, (int)JW, Mp, 0, Mp, 0, 0, 0, 0, 0, (kdim + 15) / 16,
-      drop_stage, err, ldc, m, w);
+      tA, tB, ea, eb, nullptr, 0, 0, ld / kKiChunk, 1, 1, Mp, 0, Np, 0, 0, 0, 0, 0, (g.K + 15) / 16, drop_stage, err,
+      tj);
   *launches = 1;
   return cudaGetLastError();
+}
+
+// The Cholesky's updates C -= X X[0:w]^T on and below the diagonal, X the m x kdim block whose
+// planes kinv_tc_slice formed (rows_pad = kinv_tc_ld(m)), w <= m (w = m: the whole lower
+// triangle); B's rows are the first w rows of the same planes.  The epilogue subtracts in place.
+cudaError_t syrk_lower_tc(const void* planes, const int* ex, int64_t m, int64_t w, int64_t kdim, double* C,
+                          int64_t ldc, int* err, cudaStream_t s, int64_t* launches, int drop_stage) {
+  DigitGemm g{};
+  g.C = C;
+  g.ldc = ldc;
+  g.M = m;
+  g.N = w;
+  g.K = kdim;
+  g.Npad = kinv_tc_ld(m);
+  g.lower = true;
+  g.op = 1;
+  g.skip_on_err = true;
+  return digit_gemm_tc(planes, ex, planes, ex, g, err, s, launches, drop_stage);
 }
 
 // ------------------------------------------------------------------ batched adjoint products
@@ -1241,11 +1411,11 @@ cudaError_t fwd_digits_apply(const void* planes, const int* ex, int64_t nf, int6
     if (p.NC == 32)
       sk_tc_kernel<32><<<(unsigned)p.ctas, kKiThreads, dig_smem(32), s>>>(
           tA, tB, ev, ex, part, p.per, p.total, p.kpt, p.span, p.NRG, kKiRows, 0, p.Rp, p.NC, kKiRows, 0, (int)p.Rp,
-          p.NC, ksteps, drop_stage, err, 0, 0, 0);
+          p.NC, ksteps, drop_stage, err, TileJob{});
     else
       sk_tc_kernel<64><<<(unsigned)p.ctas, kKiThreads, dig_smem(64), s>>>(
           tA, tB, ev, ex, part, p.per, p.total, p.kpt, p.span, p.NRG, kKiRows, 0, p.Rp, p.NC, kKiRows, 0, (int)p.Rp,
-          p.NC, ksteps, drop_stage, err, 0, 0, 0);
+          p.NC, ksteps, drop_stage, err, TileJob{});
     const int64_t tot = nb * nf * R;
     fwd_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, static_cast<double2*>(dhat), nf, R, b0, nb,
                                                                    p.NC, p.NRG, p.per, p.kpt, p.span);
