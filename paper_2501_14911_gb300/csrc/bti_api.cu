@@ -903,28 +903,33 @@ static bti_status build_K_impl(bti_handle h, int64_t col_block, bti_prec assembl
     cudaStreamSynchronize(s);
     dev_freep(Ff);
   } else if (h->dense_prec == BTI_P_DF64 && h->tc_enabled && kinv_tc_supported(n) && kinv_tc_supported(h->Nm)) {
-    // W = F_stack G_stack^T on the tensor cores in exact digit planes: G_stack's rows are the
-    // planes' matrix and F_stack's rows the right-hand sides, so row b of the product is
-    // W[b][.] = sum_j F[b][j] G[.][j] (all of W; the upper triangle is not read)
+    // W = F_stack G_stack^T on the tensor cores in exact digit planes, lower triangle only (the
+    // block-diagonal prefix sums read nothing else): one tile product with F_stack's rows as A
+    // and G_stack's rows as B, W[b][i] = sum_j F[b][j] G[i][j] for i <= b
     const int64_t Nm = h->Nm, Mp = kinv_tc_ld(n);
     void* planes = nullptr;
     int* ex = nullptr;
-    st = dev_alloc(h, &planes, sizeof(uint16_t) * rowmat_tc_plane_elems(n, Nm), "Gram planes");
-    if (st == BTI_OK) st = dev_alloc(h, (void**)&ex, sizeof(int) * (size_t)Mp, "Gram exponents");
-    if (st == BTI_OK)
-      st = ensure(h, (void**)&h->wsolve, &h->wsolve_bytes, sizeof(double) * rowmat_tc_work_elems(n, Nm),
-                  "solve workspace");
+    st = dev_alloc(h, &planes, sizeof(uint16_t) * 2 * rowmat_tc_plane_elems(n, Nm), "Gram planes");
+    if (st == BTI_OK) st = dev_alloc(h, (void**)&ex, sizeof(int) * (size_t)(2 * Mp), "Gram exponents");
     if (st != BTI_OK) {
       dev_free(planes);
       dev_freep(ex);
       return st;
     }
-    kinv_prepare();
+    void* gplanes = static_cast<uint16_t*>(planes) + rowmat_tc_plane_elems(n, Nm);
     kinv_tc_prepare();
-    int64_t nl = kinv_tc_slice(G.time, Nm, n, Nm, ex, planes, Mp, s);
+    int64_t nl = kinv_tc_slice(F.time, Nm, n, Nm, ex, planes, Mp, s);
+    nl += kinv_tc_slice(G.time, Nm, n, Nm, ex + Mp, gplanes, Mp, s);
+    DigitGemm g{};
+    g.C = h->K;
+    g.ldc = n;
+    g.M = n;
+    g.N = n;
+    g.K = Nm;
+    g.lower = true;
+    g.op = 0;
     int64_t tl = 0;
-    cudaError_t e = rowmat_apply_tc(planes, ex, n, Nm, F.time, n, h->K, n, h->wsolve, h->status + 1, s, &tl,
-                                    h->tc_drop_stage);
+    cudaError_t e = digit_gemm_tc(planes, ex, gplanes, ex + Mp, g, h->status + 1, s, &tl, h->tc_drop_stage);
     count_dense(h, nl + tl);
     cudaStreamSynchronize(s);
     dev_free(planes);

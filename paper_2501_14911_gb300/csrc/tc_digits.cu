@@ -286,6 +286,40 @@ slice_rows_kernel(const double* __restrict__ X, int64_t ldx, int64_t rows, int64
   }
 }
 
+// The same planes for few, long rows (the right-hand sides of a product): CTA (row r, 512-column
+// slice), each CTA taking the whole row's maximum itself (the row is read from L2 again by the
+// row's other slices) so that a handful of rows still spreads over every SM.
+__global__ void __launch_bounds__(256)
+slice_rows_wide_kernel(const double* __restrict__ X, int64_t ldx, int64_t rows, int64_t n, int* __restrict__ ex,
+                       __half* __restrict__ planes, int64_t rows_pad, int64_t ldk) {
+  __shared__ double red[8];
+  const int64_t r = blockIdx.x;
+  const double* x = X + r * ldx;
+  double mx = 0.0;
+  if (r < rows)
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) mx = fmax(mx, fabs(x[j]));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  mx = red[0];
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
+  int e = 0;
+  if (mx > 0.0) frexp(mx, &e);
+  if (blockIdx.y == 0 && threadIdx.x == 0) ex[r] = e;
+  const int64_t plane = rows_pad * ldk;
+  __half* out = planes + r * kKiBox;
+  const int64_t j1 = min(ldk, (int64_t)(blockIdx.y + 1) * 512);
+  for (int64_t j = (int64_t)blockIdx.y * 512 + threadIdx.x; j < j1; j += blockDim.x) {
+    long long v = 0;
+    if (r < rows && j < n) v = __double2ll_rn(scalbn(x[j], 47 - e));
+    int d[kSl];
+    digits6(v, d);
+    const int64_t o = (j / kKiBox) * rows_pad * kKiBox + (j % kKiBox);
+#pragma unroll
+    for (int sl = 0; sl < kSl; ++sl) out[sl * plane + o] = __int2half_rn(d[sl]);
+  }
+}
+
 // Column maxima of a rows x cols block of X (row stride ldx) as FP64 bit patterns (|x| >= 0 orders
 // like its bits): CTA (column block of 64, row block of 256), four threads per column.
 __global__ void __launch_bounds__(256)
@@ -700,21 +734,7 @@ bool kinv_tc_supported(int64_t n) {
 
 size_t kinv_tc_plane_elems(int64_t n) { return (size_t)kSl * kinv_tc_ld(n) * kinv_tc_ld(n); }
 
-int64_t kinv_tc_slice(const double* X, int64_t ldx, int64_t rows, int64_t n, int* ex, void* planes_v,
-                      int64_t rows_pad, cudaStream_t s) {
-  if (rows_pad <= 0) return 0;
-  int64_t blocks = (rows_pad + 7) / 8;  // eight warps (rows) per CTA
-  if (blocks > 65535 * 8) blocks = 65535 * 8;
-  slice_rows_kernel<<<(unsigned)blocks, 256, 0, s>>>(X, ldx, rows, n, ex, static_cast<__half*>(planes_v), rows_pad,
-                                                    kinv_tc_ld(n));
-  return 1;
-}
-
 namespace {
-struct KiPlan {
-  int64_t tiles, kpt, total, per, ctas;
-  int span;
-};
 int num_sms_tc() {
   static int v = 0;
   if (v == 0) {
@@ -725,6 +745,29 @@ int num_sms_tc() {
   }
   return v;
 }
+}  // namespace
+
+int64_t kinv_tc_slice(const double* X, int64_t ldx, int64_t rows, int64_t n, int* ex, void* planes_v,
+                      int64_t rows_pad, cudaStream_t s) {
+  if (rows_pad <= 0) return 0;
+  const int64_t ldk = kinv_tc_ld(n);
+  if (rows_pad < 8 * (int64_t)num_sms_tc()) {  // few rows: split each row over CTAs too
+    slice_rows_wide_kernel<<<dim3((unsigned)rows_pad, (unsigned)((ldk + 511) / 512)), 256, 0, s>>>(
+        X, ldx, rows, n, ex, static_cast<__half*>(planes_v), rows_pad, ldk);
+    return 1;
+  }
+  int64_t blocks = (rows_pad + 7) / 8;  // eight warps (rows) per CTA
+  if (blocks > 65535 * 8) blocks = 65535 * 8;
+  slice_rows_kernel<<<(unsigned)blocks, 256, 0, s>>>(X, ldx, rows, n, ex, static_cast<__half*>(planes_v), rows_pad,
+                                                    ldk);
+  return 1;
+}
+
+namespace {
+struct KiPlan {
+  int64_t tiles, kpt, total, per, ctas;
+  int span;
+};
 // M x n matrix (rows padded to Mp, columns to ld, both multiples of 128)
 KiPlan ki_plan(int64_t M, int64_t n) {
   KiPlan p;

@@ -1373,10 +1373,11 @@ def test_tensor_core_cholesky_matches_oracle(name, gx, gy, Nd, Nt, panel):
 
 
 def test_tensor_core_cholesky_reports_pivot_and_timeout():
-    """Failure handling of the tensor-core factorisation, injected on the host: a negative noise
-    variance past the first panel gives BTI_ERR_NOT_SPD with its pivot; a withheld TMA stage
-    (test hook) makes the trailing update's bounded waits run out, factor_K returns
-    BTI_ERR_TIMEOUT, and the same handle then builds and factors K correctly."""
+    """Failure handling of the tensor-core factorisation and inverse, injected on the host: a
+    negative noise variance past the first panel gives BTI_ERR_NOT_SPD with its pivot; a
+    withheld TMA stage (test hook) makes the digit-plane products' bounded waits run out, and
+    factor_K, then invert_K, return BTI_ERR_TIMEOUT; the same handle then builds, factors and
+    inverts K correctly."""
     name, gx, gy, Nd, Nt = "chol_tc_fail", 6, 6, 10, 40
     p = synthetic.small(name, gx, gy, Nd, Nt, Nq=3, sigma2=1.0)
     F = p.blocks_F()
@@ -1403,8 +1404,19 @@ def test_tensor_core_cholesky_reports_pivot_and_timeout():
     h.build_K()
     h.factor_K()
     L_gpu = host(h.copy_K())
+    h.test_withhold_tc_stage(1)
+    with pytest.raises(bti.BtiError) as e:
+        h.invert_K()
+    assert e.value.status == 7
+    h.test_withhold_tc_stage(-1)
+    h.invert_K()
+    d = p.vectors_d(2)
+    m = torch.empty((2, Nt, gx * gy), dtype=torch.float64, device="cuda")
+    h.infer_map(cuda(d), m)
     h.close()
     c = oracle_K(name, F, G, p.sigma2)
     low = np.tril_indices(Nd * Nt)
     check(rel(L_gpu[low], c.L[low]), parity.tol_solve(c.kappa, parity.U_DIGITS),
           f"L after a timeout; kappa(K) = {c.kappa:.0f}")
+    b = solve_bounds(c, d, parity.U_DIGITS, kind="inverse")
+    check(relb(host(m), b.m), b.tol_m, "m_map, explicit inverse after a timeout; " + b.info)
