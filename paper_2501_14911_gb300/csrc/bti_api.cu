@@ -1260,6 +1260,41 @@ static bti_status prior_apply_fq(bti_ctx* h, double* out) {
   return apply_se_rows(h, h->op[BTI_OP_FQ].time, out, h->Nt * h->Nq);
 }
 
+// Digit planes (and row exponents) of a rows x cols FP64 matrix, allocated here: for the
+// tensor-core tile products of bti_build_Q.  rows_pad = kinv_tc_ld(rows).
+struct Planes {
+  void* p = nullptr;
+  int* ex = nullptr;
+};
+static bti_status make_planes(bti_ctx* h, const double* X, int64_t ldx, int64_t rows, int64_t cols, Planes& out,
+                              int64_t* nl, const char* what) {
+  const int64_t rp = kinv_tc_ld(rows);
+  bti_status st = dev_alloc(h, &out.p, sizeof(uint16_t) * (size_t)6 * rp * kinv_tc_ld(cols), what);
+  if (st == BTI_OK) st = dev_alloc(h, (void**)&out.ex, sizeof(int) * (size_t)rp, what);
+  if (st != BTI_OK) return st;
+  *nl += kinv_tc_slice(X, ldx, rows, cols, out.ex, out.p, rp, h->stream);
+  return BTI_OK;
+}
+static void free_planes(Planes& q) {
+  dev_free(q.p);
+  dev_freep(q.ex);
+}
+// C (op)= A B^T on the tensor cores for planes A (M x K) and B (N x K)
+static cudaError_t tile_product(bti_ctx* h, const Planes& A, const Planes& B, double* C, int64_t ldc, int64_t M,
+                                int64_t N, int64_t K, int op, int64_t* nl) {
+  DigitGemm g{};
+  g.C = C;
+  g.ldc = ldc;
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.op = op;
+  int64_t tl = 0;
+  const cudaError_t e = digit_gemm_tc(A.p, A.ex, B.p, B.ex, g, h->status + 1, h->stream, &tl, h->tc_drop_stage);
+  *nl += tl;
+  return e;
+}
+
 bti_status bti_build_Q(bti_handle h, int with_covariance) {
   bti_status st = check_handle(h);
   if (st != BTI_OK) return st;
@@ -1274,6 +1309,8 @@ bti_status bti_build_Q(bti_handle h, int with_covariance) {
   const int qs = h->qstride;
   const int64_t nq = (h->Nt / qs) * h->Nq;  // rows of Q on the QoI time grid
   const bool dd = h->dense_prec == BTI_P_DF64;
+  // dense products on the tensor cores in digit planes under double-FP32 dense arithmetic
+  const bool tcg = dd && h->tc_enabled && kinv_tc_supported(n) && kinv_tc_supported(Nm) && kinv_tc_supported(nqf);
   auto gemm = dd ? gemm_df64 : gemm_f64;
   cudaStream_t s = h->stream;
   drop_online_graph_any(h);  // a captured online graph may read Q (bti_set_online_qoi)
@@ -1282,6 +1319,15 @@ bti_status bti_build_Q(bti_handle h, int with_covariance) {
   st = dev_alloc(h, (void**)&h->Q, sizeof(double) * (size_t)nq * n, "alloc Q");
   if (st != BTI_OK) return st;
   h->Q_built = h->covq_built = false;
+  Planes pFq, pG, pX;
+  auto done = [&](bti_status r) {
+    cudaStreamSynchronize(s);
+    free_planes(pFq);
+    free_planes(pG);
+    free_planes(pX);
+    return r;
+  };
+  cudaError_t e = cudaSuccess;
   // X = F_q G^*: Gram of the stacked blocks, then block-diagonal prefix sums (fine time grid);
   // the rows at QoI times t = qs (k + 1) - 1 form Q's right-hand sides
   double* Xf = h->Q;
@@ -1289,7 +1335,21 @@ bti_status bti_build_Q(bti_handle h, int with_covariance) {
     st = dev_alloc(h, (void**)&Xf, sizeof(double) * (size_t)nqf * n, "F_q G* (fine)");
     if (st != BTI_OK) return st;
   }
-  int64_t nl = gemm(true, nqf, n, Nm, 1.0, Fq.time, Nm, 0, G.time, Nm, 0, 0.0, Xf, n, 0, 1, false, s);
+  int64_t nl = 0;
+  if (tcg) {
+    kinv_tc_prepare();
+    st = make_planes(h, Fq.time, Nm, nqf, Nm, pFq, &nl, "F_q planes");
+    if (st == BTI_OK) st = make_planes(h, G.time, Nm, n, Nm, pG, &nl, "G planes");
+    if (st == BTI_OK) e = tile_product(h, pFq, pG, Xf, n, nqf, n, Nm, 0, &nl);
+    if (st == BTI_OK && e != cudaSuccess) st = cuda_check(h, e, "build_Q (tensor-core Gram)");
+    free_planes(pG);
+    if (st != BTI_OK) {
+      if (qs > 1) dev_freep(Xf);
+      return done(st);
+    }
+  } else {
+    nl += gemm(true, nqf, n, Nm, 1.0, Fq.time, Nm, 0, G.time, Nm, 0, 0.0, Xf, n, 0, 1, false, s);
+  }
   nl += block_diag_cumsum_all(Xf, h->Nt, h->Nq, h->Nd, s);
   if (qs > 1) {
     const size_t blk = sizeof(double) * (size_t)h->Nq * n;  // one time block of rows
@@ -1298,32 +1358,39 @@ bti_status bti_build_Q(bti_handle h, int with_covariance) {
     cudaStreamSynchronize(s);
     dev_freep(Xf);
   }
-  double* X = nullptr;
-  if (with_covariance) {
+  // Q = X K^{-1}: every row of X is a right-hand side of the two triangular solves, or the rows of
+  // X against the explicit inverse's planes in one tile product on the tensor cores when
+  // bti_invert_K formed it (K^{-1} is symmetric: its rows are its columns)
+  const bool inv_tc = kinv_ready(h) && h->kinv_planes && h->tc_enabled;
+  double* X = nullptr;  // X on the QoI grid (the covariance subtracts Q X^T)
+  if (with_covariance && !tcg) {
     st = dev_alloc(h, (void**)&X, sizeof(double) * (size_t)nq * n, "F_q G* copy");
-    if (st != BTI_OK) return st;
+    if (st != BTI_OK) return done(st);
     cudaMemcpyAsync(X, h->Q, sizeof(double) * (size_t)nq * n, cudaMemcpyDeviceToDevice, s);
   }
-  // Q = X K^{-1}: every row of X is a right-hand side of the two triangular solves, or of
-  // one product with the explicit inverse on the tensor cores when bti_invert_K formed it
-  const bool inv_tc = kinv_ready(h) && h->kinv_planes && h->tc_enabled;
-  st = ensure(h, (void**)&h->wsolve, &h->wsolve_bytes,
-              sizeof(double) * std::max(std::max(trsm_work_elems(n, nq), (size_t)n * kCholNB),
-                                        inv_tc ? kinv_tc_work_elems(n) : (size_t)0),
-              "solve workspace");
-  if (st != BTI_OK) { dev_freep(X); return st; }
+  if (inv_tc || (with_covariance && tcg)) {
+    st = make_planes(h, h->Q, n, nq, n, pX, &nl, "X planes");
+    if (st != BTI_OK) return done(st);
+  }
   if (inv_tc) {
     double* Qn = nullptr;
     st = dev_alloc(h, (void**)&Qn, sizeof(double) * (size_t)nq * n, "alloc Q");
-    if (st != BTI_OK) { dev_freep(X); return st; }
-    int64_t tl = 0;
-    cudaError_t e = kinv_apply_tc(h->kinv_planes, h->kinv_ea, n, h->Q, nq, Qn, h->wsolve, h->status + 1, s, &tl);
-    nl += tl;
+    if (st != BTI_OK) return done(st);
+    Planes pK;
+    pK.p = h->kinv_planes;
+    pK.ex = h->kinv_ea;
+    e = tile_product(h, pX, pK, Qn, n, nq, n, n, 0, &nl);
     cudaStreamSynchronize(s);
     dev_freep(h->Q);
     h->Q = Qn;
-    if (e != cudaSuccess) { dev_freep(X); return cuda_check(h, e, "build_Q (tensor-core K^{-1})"); }
+    if (e != cudaSuccess) return done(cuda_check(h, e, "build_Q (tensor-core K^{-1})"));
   } else {
+    st = ensure(h, (void**)&h->wsolve, &h->wsolve_bytes,
+                sizeof(double) * std::max(trsm_work_elems(n, nq), (size_t)n * kCholNB), "solve workspace");
+    if (st != BTI_OK) {
+      dev_freep(X);
+      return done(st);
+    }
     nl += trsm_lower_f64(h->K, h->Linv, n, h->Q, nq, h->wsolve, h->status, s, dd);
   }
   if (with_covariance) {
@@ -1333,21 +1400,47 @@ bti_status bti_build_Q(bti_handle h, int with_covariance) {
     if (st == BTI_OK) st = prior_apply_fq(h, Gq);
     if (st == BTI_OK) st = dev_alloc(h, (void**)&h->covq, sizeof(double) * (size_t)nq * nq, "alloc cov");
     if (st == BTI_OK && qs > 1) st = dev_alloc(h, (void**)&Cf, sizeof(double) * (size_t)nqf * nqf, "cov (fine)");
-    if (st != BTI_OK) { dev_freep(X); dev_freep(Gq); dev_freep(Cf); return st; }
+    if (st != BTI_OK) {
+      dev_freep(X);
+      dev_freep(Gq);
+      dev_freep(Cf);
+      return done(st);
+    }
     // Gamma_post(q) = F_q Gamma_prior F_q^T - Q X^T  (Eq. (4.10) with F G_q^* = X^T), on the QoI grid
     double* C0 = qs > 1 ? Cf : h->covq;
-    nl += gemm(true, nqf, nqf, Nm, 1.0, Fq.time, Nm, 0, Gq, Nm, 0, 0.0, C0, nqf, 0, 1, false, s);
-    nl += block_diag_cumsum_all(C0, h->Nt, h->Nq, h->Nq, s);
-    if (qs > 1) nl += select_time_blocks_sq(Cf, h->covq, h->Nt, h->Nq, qs, s);
-    nl += gemm(true, nq, nq, n, -1.0, h->Q, n, 0, X, n, 0, 1.0, h->covq, nq, 0, 1, false, s);
+    if (tcg) {
+      Planes pGq, pQ;
+      st = make_planes(h, Gq, Nm, nqf, Nm, pGq, &nl, "G_q planes");
+      if (st == BTI_OK) e = tile_product(h, pFq, pGq, C0, nqf, nqf, nqf, Nm, 0, &nl);
+      if (st == BTI_OK && e == cudaSuccess) {
+        nl += block_diag_cumsum_all(C0, h->Nt, h->Nq, h->Nq, s);
+        if (qs > 1) nl += select_time_blocks_sq(Cf, h->covq, h->Nt, h->Nq, qs, s);
+        st = make_planes(h, h->Q, n, nq, n, pQ, &nl, "Q planes");
+        if (st == BTI_OK) e = tile_product(h, pQ, pX, h->covq, nq, nq, nq, n, 1, &nl);
+      }
+      cudaStreamSynchronize(s);
+      free_planes(pGq);
+      free_planes(pQ);
+      if (st == BTI_OK && e != cudaSuccess) st = cuda_check(h, e, "build_Q (tensor-core covariance)");
+    } else {
+      nl += gemm(true, nqf, nqf, Nm, 1.0, Fq.time, Nm, 0, Gq, Nm, 0, 0.0, C0, nqf, 0, 1, false, s);
+      nl += block_diag_cumsum_all(C0, h->Nt, h->Nq, h->Nq, s);
+      if (qs > 1) nl += select_time_blocks_sq(Cf, h->covq, h->Nt, h->Nq, qs, s);
+      nl += gemm(true, nq, nq, n, -1.0, h->Q, n, 0, X, n, 0, 1.0, h->covq, nq, 0, 1, false, s);
+    }
     cudaStreamSynchronize(s);
     dev_freep(Gq);
     dev_freep(Cf);
-    dev_freep(X);
+    if (st != BTI_OK) {
+      dev_freep(X);
+      return done(st);
+    }
   }
+  dev_freep(X);
   count_dense(h, nl);
   st = launched(h, "build_Q");
-  if (st != BTI_OK) return st;
+  if (st != BTI_OK) return done(st);
+  done(BTI_OK);
   h->Q_built = true;
   ++h->Q_gen;
   h->covq_built = with_covariance != 0;

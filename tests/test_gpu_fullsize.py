@@ -235,6 +235,17 @@ def test_batched_double_fp32_dense_without_refinement_full_size(batched):
     m1 = torch.empty((1, p.Nt, p.Nm), dtype=torch.float64, device="cuda")
     h.infer_map(torch.from_numpy(o.d_obs[5:6]).cuda(), m1, refine_iters=0)
     m1 = m1.cpu().numpy()
+    # q_map = Q d_obs (Eq. (4.14)) with Q = X K^{-1} formed by the tile products (the Gram X =
+    # F_q G^* and the product with the explicit inverse, both in digit planes) and applied in
+    # digit planes in the online graph
+    h.build_Q()
+    h.set_online_qoi(True)
+    with torch.cuda.stream(stream):
+        h.set_stream(stream)
+        h.online(torch.from_numpy(o.d_obs).cuda(), m_map, q_map, refine_iters=0)
+        torch.cuda.synchronize()
+        q_Q = q_map.cpu().numpy()
+    h.set_stream(torch.cuda.current_stream())
     h.close()
     kinfo = f"kappa(K) = {o.kappa:.0f}, rho = {o.rho:.1f}"
     tol = parity.tol_solve(o.kappa, parity.U_DIGITS)
@@ -245,6 +256,7 @@ def test_batched_double_fp32_dense_without_refinement_full_size(batched):
     check(relb(m_inv, o.m), tol, "m_map, explicit inverse " + kinfo)
     check(relb(q_inv, o.q), tol, "q_map, explicit inverse " + kinfo)
     check(relb(m1, o.m[5:6]), tol, "m_map, explicit inverse, one vector " + kinfo)
+    check(relb(q_Q, o.q), tol, "q_map = Q d_obs, Q from the explicit inverse " + kinfo)
     tol = parity.tol_solve(o.kappa, parity.U_DIGITS)
     check(relb(m_ref, o.m), tol, "m_map, inverse + one refinement step " + kinfo)
     check(relb(q_ref, o.q), tol, "q_map, inverse + one refinement step " + kinfo)
