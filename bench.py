@@ -45,12 +45,14 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-workload matrix-free solve block")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--case", choices=["sweep", "small", "digits_small"], default="sweep",
+    ap.add_argument("--case", choices=["sweep", "small", "digits_small", "factor_small"], default="sweep",
                     help="small: the sweep shape with N_m = 4096 and 16 vectors (2.2 GB of FP64 spectral "
                          "blocks, still far above L2) for ncu captures; implies --no-online, "
                          "--no-mixed, --no-cpu-baseline and --no-e2e.  digits_small: the batched "
                          "workload's shapes at N_t = 50 with 64 vectors, timing the tensor-core digit-plane "
-                         "products (adjoint, forward, explicit inverse) once each, for ncu captures")
+                         "products (adjoint, forward, explicit inverse) once each, for ncu captures.  "
+                         "factor_small: K of 8,192^2 factored by recursive halves and inverted on the tensor "
+                         "cores once each, for ncu captures")
     a = ap.parse_args()
     if a.case == "small":
         a.no_online = a.no_mixed = a.no_cpu_baseline = a.no_e2e = True
@@ -980,12 +982,46 @@ def digits_small(args):
     return 0
 
 
+def factor_small(args):
+    """The tensor-core Cholesky and inverse at a small size for ncu captures: K of 8,192^2
+    (N_m = 1,024, N_d = 64, N_t = 128, noise variance 1), factored as one panel by recursive
+    halves (its largest update, the 64th digit-plane tile product, has K = 4,096) and inverted;
+    0.5 GB for K and 0.8 GB of planes.  Prints one JSON line of times."""
+    import torch
+
+    import paper_2501_14911_gb300 as bti
+    from paper_2501_14911_gb300 import synthetic
+
+    dev = torch.device("cuda", 0)
+    p = synthetic.small("factor_small_Nm1024_Nd64_Nt128", 32, 32, 64, 128, Nq=4, sigma2=1.0)
+    h = bti.Handle(p.Nm, p.Nd, p.Nq, p.Nt, device=dev)
+    h.set_blocks(bti.OP_F, torch.from_numpy(p.blocks_F()).to(dev), bti.DF64)
+    h.set_prior_se_grid(p.gx, p.gy, 2.0, 1.0, bti.DF64)
+    h.set_noise(p.sigma2)
+    h.set_dense_precision(bti.DF64)
+    h.set_factor_panel(1 << 20)
+    h.build_K()
+    torch.cuda.synchronize()
+    out = {"case": p.name, "n": p.Nt * p.Nd}
+    t0 = time.perf_counter()
+    h.factor_K()
+    out["factor_K_ms"] = 1e3 * (time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    h.invert_K()
+    out["invert_K_ms"] = 1e3 * (time.perf_counter() - t0)
+    h.close()
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.case == "digits_small":
         return digits_small(args)
+    if args.case == "factor_small":
+        return factor_small(args)
     return run_ours(args)
 
 

@@ -34,6 +34,8 @@
 // it issued land and frees its tensor memory.
 #include "bti_internal.cuh"
 
+#include <algorithm>
+
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
@@ -286,12 +288,12 @@ slice_rows_kernel(const double* __restrict__ X, int64_t ldx, int64_t rows, int64
   }
 }
 
-// The same planes for few, long rows (the right-hand sides of a product): CTA (row r, 512-column
-// slice), each CTA taking the whole row's maximum itself (the row is read from L2 again by the
-// row's other slices) so that a handful of rows still spreads over every SM.
+// The same planes for few, long rows (the right-hand sides of a product): CTA (row r, column
+// slice of cw), each CTA taking the whole row's maximum itself (the row is read from L2 again by
+// the row's other slices) so that a handful of rows still spreads over every SM.
 __global__ void __launch_bounds__(256)
 slice_rows_wide_kernel(const double* __restrict__ X, int64_t ldx, int64_t rows, int64_t n, int* __restrict__ ex,
-                       __half* __restrict__ planes, int64_t rows_pad, int64_t ldk) {
+                       __half* __restrict__ planes, int64_t rows_pad, int64_t ldk, int64_t cw) {
   __shared__ double red[8];
   const int64_t r = blockIdx.x;
   const double* x = X + r * ldx;
@@ -308,8 +310,8 @@ slice_rows_wide_kernel(const double* __restrict__ X, int64_t ldx, int64_t rows, 
   if (blockIdx.y == 0 && threadIdx.x == 0) ex[r] = e;
   const int64_t plane = rows_pad * ldk;
   __half* out = planes + r * kKiBox;
-  const int64_t j1 = min(ldk, (int64_t)(blockIdx.y + 1) * 512);
-  for (int64_t j = (int64_t)blockIdx.y * 512 + threadIdx.x; j < j1; j += blockDim.x) {
+  const int64_t j1 = min(ldk, (int64_t)(blockIdx.y + 1) * cw);
+  for (int64_t j = (int64_t)blockIdx.y * cw + threadIdx.x; j < j1; j += blockDim.x) {
     long long v = 0;
     if (r < rows && j < n) v = __double2ll_rn(scalbn(x[j], 47 - e));
     int d[kSl];
@@ -752,8 +754,10 @@ int64_t kinv_tc_slice(const double* X, int64_t ldx, int64_t rows, int64_t n, int
   if (rows_pad <= 0) return 0;
   const int64_t ldk = kinv_tc_ld(n);
   if (rows_pad < 8 * (int64_t)num_sms_tc()) {  // few rows: split each row over CTAs too
-    slice_rows_wide_kernel<<<dim3((unsigned)rows_pad, (unsigned)((ldk + 511) / 512)), 256, 0, s>>>(
-        X, ldx, rows, n, ex, static_cast<__half*>(planes_v), rows_pad, ldk);
+    // at most eight slices per row (each reads the whole row for its maximum), at least 512 wide
+    const int64_t cw = std::max<int64_t>(512, (ldk / 8 + 511) / 512 * 512);
+    slice_rows_wide_kernel<<<dim3((unsigned)rows_pad, (unsigned)((ldk + cw - 1) / cw)), 256, 0, s>>>(
+        X, ldx, rows, n, ex, static_cast<__half*>(planes_v), rows_pad, ldk, cw);
     return 1;
   }
   int64_t blocks = (rows_pad + 7) / 8;  // eight warps (rows) per CTA
