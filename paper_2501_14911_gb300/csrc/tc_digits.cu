@@ -166,23 +166,7 @@ __device__ __forceinline__ void digits6(long long v, int (&d)[kSl]) {
   d[0] = (int)v;  // |v| <= 128 here
 }
 
-// tcgen05.cp / tcgen05.mma / tcgen05.commit issued by one elected lane of a warp that runs the
-// issuing loop in step, so descriptors and addresses stay warp-uniform.
-// A operand from tensor memory: D (+)= A[tmem] B[smem]
-__device__ __forceinline__ void mma_ts_elect(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n.reg .pred p, e;\nsetp.ne.b32 p, %4, 0;\nelect.sync _|e, 0xffffffff;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n"
-      ::"r"(d), "r"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-// 128 rows x 32 bytes (one K-step of 16 halves) from shared memory into tensor memory lanes 0-127,
-// eight 32-bit columns from taddr
-__device__ __forceinline__ void cp_elect(uint32_t taddr, uint64_t sd) {
-  asm volatile(
-      "{\n.reg .pred e;\nelect.sync _|e, 0xffffffff;\n"
-      "@e tcgen05.cp.cta_group::1.128x256b [%0], %1;\n}\n"
-      ::"r"(taddr), "l"(sd));
-}
+// tcgen05.commit issued by one elected lane of a warp that runs the issuing loop in step.
 __device__ __forceinline__ void commit_elect(uint32_t bar) {
   asm volatile(
       "{\n.reg .pred e;\nelect.sync _|e, 0xffffffff;\n"
@@ -194,28 +178,81 @@ __device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, vo
   return __all_sync(0xffffffffu, mbar_wait(bar, parity, abort_flag));
 }
 
-// One K-step (16 columns) of a stage: the six A plane slices are copied into tensor memory
-// (columns abuf + 8 s), then the 21 plane pairs s + t <= 5 run with A from tensor memory, so each
-// A slice is read from shared memory once instead of once per pair; group s + t accumulates at
-// TMEM columns NC (s + t).  a0, b0: the stage's plane 0 of A and of B; kk: the K-step within the
-// 32-column box (32 bytes, 2 in the encoded start address).  first: the K-step opens an
-// accumulation chunk, so the pairs (0, t), issued first, overwrite the groups.  Called by a
-// whole warp.
+// One K-step (16 columns) of a stage, as one instruction block under a single elect.sync: the
+// six A plane slices are copied into tensor memory (columns abuf + 8 s), then the 21 plane pairs
+// s + t <= 5 run with A from tensor memory, group s + t accumulating at TMEM columns NC (s + t).
+// a0, b0: the stage's plane 0 of A and of B; kk: the K-step within the 32-column box (32 bytes, 2
+// in the encoded start address).  first: the K-step opens an accumulation chunk, so the pairs
+// (0, t), issued first, overwrite the groups.  Consecutive planes of a stage are kAPlane bytes
+// apart (512 in the descriptor's 16-byte units) for A and NC kBx 2 bytes for B; the shared-
+// memory addresses stay below 2^18, so the offsets add to the descriptors' address field
+// without carrying out of it.  Called by a whole warp.
 template <int NC>
 __device__ __forceinline__ void issue_kstep(uint32_t tmem, uint32_t abuf, uint32_t a0, uint32_t b0, int kk,
                                             uint32_t idesc, bool first) {
-#pragma unroll
-  for (int s = 0; s < kSl; ++s) cp_elect(abuf + 8u * (uint32_t)s, sdesc(a0 + (uint32_t)s * kAPlane) + 2 * kk);
+  static_assert(kAPlane == 512 * 16, "A plane stride in descriptor units");
+  constexpr uint64_t bs = (uint64_t)((NC * kBx * 2) >> 4);
+  const uint64_t ad = sdesc(a0) + 2 * kk;
   const uint64_t bd = sdesc(b0) + 2 * kk;
-#pragma unroll
-  for (int s = 0; s < kSl; ++s) {
-#pragma unroll
-    for (int t = 0; t < kSl; ++t) {
-      if (t + s < kSl)
-        mma_ts_elect(tmem + (uint32_t)((s + t) * NC), abuf + 8u * (uint32_t)s,
-                     bd + (uint64_t)t * ((uint32_t)(NC * kBx * 2) >> 4), idesc, (first && s == 0) ? 0u : 1u);
-    }
-  }
+  asm volatile(
+      "{\n"
+      ".reg .pred e, pa, pt;\n"
+      ".reg .b64 a1, a2, a3, a4, a5, b1, b2, b3, b4, b5;\n"
+      ".reg .b32 c1, c2, c3, c4, c5, d1, d2, d3, d4, d5;\n"
+      "elect.sync _|e, 0xffffffff;\n"
+      "setp.eq.u32 pa, %5, 0;\n"
+      "setp.eq.u32 pt, %5, %5;\n"
+      "add.u64 a1, %2, 512;\n"
+      "add.u64 b1, %3, %6;\n"
+      "add.u32 c1, %1, 8;\n"
+      "add.u32 d1, %0, %11;\n"
+      "add.u64 a2, %2, 1024;\n"
+      "add.u64 b2, %3, %7;\n"
+      "add.u32 c2, %1, 16;\n"
+      "add.u32 d2, %0, %12;\n"
+      "add.u64 a3, %2, 1536;\n"
+      "add.u64 b3, %3, %8;\n"
+      "add.u32 c3, %1, 24;\n"
+      "add.u32 d3, %0, %13;\n"
+      "add.u64 a4, %2, 2048;\n"
+      "add.u64 b4, %3, %9;\n"
+      "add.u32 c4, %1, 32;\n"
+      "add.u32 d4, %0, %14;\n"
+      "add.u64 a5, %2, 2560;\n"
+      "add.u64 b5, %3, %10;\n"
+      "add.u32 c5, %1, 40;\n"
+      "add.u32 d5, %0, %15;\n"
+      "@e tcgen05.cp.cta_group::1.128x256b [%1], %2;\n"
+      "@e tcgen05.cp.cta_group::1.128x256b [c1], a1;\n"
+      "@e tcgen05.cp.cta_group::1.128x256b [c2], a2;\n"
+      "@e tcgen05.cp.cta_group::1.128x256b [c3], a3;\n"
+      "@e tcgen05.cp.cta_group::1.128x256b [c4], a4;\n"
+      "@e tcgen05.cp.cta_group::1.128x256b [c5], a5;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %3, %4, pa;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [d1], [%1], b1, %4, pa;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [d2], [%1], b2, %4, pa;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [d3], [%1], b3, %4, pa;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [d4], [%1], b4, %4, pa;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [d5], [%1], b5, %4, pa;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [d1], [c1], %3, %4, pt;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [d2], [c1], b1, %4, pt;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [d3], [c1], b2, %4, pt;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [d4], [c1], b3, %4, pt;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [d5], [c1], b4, %4, pt;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [d2], [c2], %3, %4, pt;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [d3], [c2], b1, %4, pt;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [d4], [c2], b2, %4, pt;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [d5], [c2], b3, %4, pt;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [d3], [c3], %3, %4, pt;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [d4], [c3], b1, %4, pt;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [d5], [c3], b2, %4, pt;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [d4], [c4], %3, %4, pt;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [d5], [c4], b1, %4, pt;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [d5], [c5], %3, %4, pt;\n"
+      "}\n"
+      ::"r"(tmem), "r"(abuf), "l"(ad), "l"(bd), "r"(idesc), "r"(first ? 1u : 0u), "n"(bs), "n"(2 * bs), "n"(3 * bs),
+        "n"(4 * bs), "n"(5 * bs), "n"(NC), "n"(2 * NC), "n"(3 * NC), "n"(4 * NC), "n"(5 * NC)
+      : "memory");
 }
 
 // (hi + lo) 2^e as an FP64 value with integer operations only (GB300 issues FP64 at 1/64 of
