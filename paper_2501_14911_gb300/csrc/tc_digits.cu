@@ -154,6 +154,42 @@ __device__ __forceinline__ void add_groups(uint32_t taddr, float (&Sh)[W], float
   }
 }
 
+// Integer-only helpers of the slicing kernels (GB300 runs FP64 instructions, conversions and
+// scaling included, at a small fraction of its integer rate).  abs_bits: |x| as bits, which order
+// like the values for |x| >= 0.  exp_of_bits: the frexp exponent of |x| from those bits (|x| =
+// f 2^e, f in [0.5, 1); 0 for zero).  round_scaled: x 2^k rounded to the nearest integer, ties to
+// even (as llrint), for |x 2^k| < 2^62: x = m 2^(max(E, 1) - 1075) from its biased exponent E and
+// significand m, so x 2^k = m 2^s is a shift of m with the bits shifted out deciding the rounding.
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+__device__ __forceinline__ int exp_of_bits(unsigned long long mb) {
+  if (mb == 0) return 0;
+  const int E = (int)(mb >> 52);
+  if (E != 0) return E - 1022;
+  return 64 - __clzll((long long)mb) - 1074;  // subnormal: m 2^-1074 with its top bit at 63 - clz
+}
+__device__ __forceinline__ long long round_scaled(double x, int k) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7FF);
+  unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  if (E != 0) m |= 1ull << 52;
+  const int sft = (E != 0 ? E : 1) - 1075 + k;
+  long long v;
+  if (sft >= 0) {
+    v = sft < 63 ? (long long)(m << sft) : 0;  // a subnormal x with a large k (m 2^sft < 2^62)
+  } else {
+    const int r = -sft;
+    if (r > 63) {
+      v = 0;
+    } else {
+      const unsigned long long q = m >> r, rem = m & ((1ull << r) - 1), half = 1ull << (r - 1);
+      v = (long long)(q + ((rem > half || (rem == half && (q & 1))) ? 1ull : 0ull));
+    }
+  }
+  return (b >> 63) ? -v : v;
+}
+
 // Balanced base-256 digits of v (|v| <= 2^47), most significant first: v = sum_s d[s] 256^(5 - s),
 // d[s] in [-128, 128] (the lower five in [-128, 127]).
 __device__ __forceinline__ void digits6(long long v, int (&d)[kSl]) {
@@ -305,17 +341,16 @@ slice_rows_kernel(const double* __restrict__ X, int64_t ldx, int64_t rows, int64
   const int64_t plane = rows_pad * ldk;
   for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < rows_pad; r += warps) {
     const double* x = X + r * ldx;
-    double mx = 0.0;
+    unsigned long long mb = 0;
     if (r < rows)
-      for (int64_t j = lane; j < n; j += 32) mx = fmax(mx, fabs(x[j]));
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    int e = 0;
-    if (mx > 0.0) frexp(mx, &e);
+      for (int64_t j = lane; j < n; j += 32) mb = max(mb, abs_bits(x[j]));
+    for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+    const int e = exp_of_bits(mb);
     if (lane == 0) ex[r] = e;
     __half* out = planes + r * kKiBox;
     for (int64_t j = lane; j < ldk; j += 32) {
       long long v = 0;
-      if (r < rows && j < n) v = __double2ll_rn(scalbn(x[j], 47 - e));
+      if (r < rows && j < n) v = round_scaled(x[j], 47 - e);
       int d[kSl];
       digits6(v, d);
       const int64_t o = (j / kKiBox) * rows_pad * kKiBox + (j % kKiBox);
@@ -331,26 +366,25 @@ slice_rows_kernel(const double* __restrict__ X, int64_t ldx, int64_t rows, int64
 __global__ void __launch_bounds__(256)
 slice_rows_wide_kernel(const double* __restrict__ X, int64_t ldx, int64_t rows, int64_t n, int* __restrict__ ex,
                        __half* __restrict__ planes, int64_t rows_pad, int64_t ldk, int64_t cw) {
-  __shared__ double red[8];
+  __shared__ unsigned long long red[8];
   const int64_t r = blockIdx.x;
   const double* x = X + r * ldx;
-  double mx = 0.0;
+  unsigned long long mb = 0;
   if (r < rows)
-    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) mx = fmax(mx, fabs(x[j]));
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) mb = max(mb, abs_bits(x[j]));
+  for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mb;
   __syncthreads();
-  mx = red[0];
-  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
-  int e = 0;
-  if (mx > 0.0) frexp(mx, &e);
+  mb = red[0];
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mb = max(mb, red[w]);
+  const int e = exp_of_bits(mb);
   if (blockIdx.y == 0 && threadIdx.x == 0) ex[r] = e;
   const int64_t plane = rows_pad * ldk;
   __half* out = planes + r * kKiBox;
   const int64_t j1 = min(ldk, (int64_t)(blockIdx.y + 1) * cw);
   for (int64_t j = (int64_t)blockIdx.y * cw + threadIdx.x; j < j1; j += blockDim.x) {
     long long v = 0;
-    if (r < rows && j < n) v = __double2ll_rn(scalbn(x[j], 47 - e));
+    if (r < rows && j < n) v = round_scaled(x[j], 47 - e);
     int d[kSl];
     digits6(v, d);
     const int64_t o = (j / kKiBox) * rows_pad * kKiBox + (j % kKiBox);
@@ -364,18 +398,18 @@ slice_rows_wide_kernel(const double* __restrict__ X, int64_t ldx, int64_t rows, 
 __global__ void __launch_bounds__(256)
 col_max_kernel(const double* __restrict__ X, int64_t ldx, int64_t rows, int64_t cols,
                unsigned long long* __restrict__ colmax) {
-  __shared__ double red[4][64];
+  __shared__ unsigned long long red[4][64];
   const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
   const int64_t c = (int64_t)blockIdx.x * 64 + tx;
   const int64_t r0 = (int64_t)blockIdx.y * 256;
-  double mx = 0.0;
+  unsigned long long mb = 0;
   if (c < cols)
-    for (int64_t r = r0 + ty; r < rows && r < r0 + 256; r += 4) mx = fmax(mx, fabs(X[r * ldx + c]));
-  red[ty][tx] = mx;
+    for (int64_t r = r0 + ty; r < rows && r < r0 + 256; r += 4) mb = max(mb, abs_bits(X[r * ldx + c]));
+  red[ty][tx] = mb;
   __syncthreads();
   if (ty == 0 && c < cols) {
-    mx = fmax(fmax(red[0][tx], red[1][tx]), fmax(red[2][tx], red[3][tx]));
-    atomicMax(&colmax[c], (unsigned long long)__double_as_longlong(mx));
+    mb = max(max(red[0][tx], red[1][tx]), max(red[2][tx], red[3][tx]));
+    atomicMax(&colmax[c], mb);
   }
 }
 
@@ -398,18 +432,14 @@ slice_cols_kernel(const double* __restrict__ X, int64_t ldx, int64_t rows, int64
   __syncthreads();
   const int cc = threadIdx.x >> 2, kq = (threadIdx.x & 3) * 16;
   const int64_t c = c0 + cc;
-  int e = 0;
-  if (c < cols) {
-    const double mx = __longlong_as_double((long long)colmax[c]);
-    if (mx > 0.0) frexp(mx, &e);
-  }
+  const int e = c < cols ? exp_of_bits(colmax[c]) : 0;
   if (blockIdx.x == 0 && (threadIdx.x & 3) == 0 && c < rows_pad) ex[c] = e;
   const int64_t plane = rows_pad * ldk;
   __half* out = planes + (k0 / kKiBox) * rows_pad * kKiBox + c * kKiBox + kq;
 #pragma unroll 4
   for (int j = 0; j < 16; ++j) {
     long long v = 0;
-    if (c < cols) v = __double2ll_rn(scalbn(t[kq + j][cc], 47 - e));
+    if (c < cols) v = round_scaled(t[kq + j][cc], 47 - e);
     int d[kSl];
     digits6(v, d);
 #pragma unroll
@@ -1002,18 +1032,17 @@ __global__ void adj_vec_planes_kernel(const double2* __restrict__ dhat, int64_t 
                                       int64_t NBp, int64_t Kp, __half* __restrict__ planes, int* __restrict__ eb) {
   const int64_t w = blockIdx.x, b = blockIdx.y;
   const double2* src = dhat + (b * nf + w) * R;
-  double mx = 0.0;
+  unsigned long long mb = 0;
   if (b < B)
-    for (int64_t i = threadIdx.x; i < R; i += blockDim.x) mx = fmax(mx, fmax(fabs(src[i].x), fabs(src[i].y)));
-  __shared__ double red[32];
+    for (int64_t i = threadIdx.x; i < R; i += blockDim.x) mb = max(mb, max(abs_bits(src[i].x), abs_bits(src[i].y)));
+  __shared__ unsigned long long red[32];
   __shared__ int es;
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mb;
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) mx = fmax(mx, red[k]);
-    int e = 0;
-    if (mx > 0.0) frexp(mx, &e);
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) mb = max(mb, red[k]);
+    const int e = exp_of_bits(mb);
     es = e;
     eb[w * NBp + 2 * b] = e;
     eb[w * NBp + 2 * b + 1] = e;
@@ -1028,8 +1057,8 @@ __global__ void adj_vec_planes_kernel(const double2* __restrict__ dhat, int64_t 
   for (int64_t i = threadIdx.x; i < Kp / 2; i += blockDim.x) {
     long long vr = 0, vi = 0;
     if (b < B && i < R) {
-      vr = __double2ll_rn(scalbn(src[i].x, 47 - e));
-      vi = __double2ll_rn(scalbn(src[i].y, 47 - e));
+      vr = round_scaled(src[i].x, 47 - e);
+      vi = round_scaled(src[i].y, 47 - e);
     }
     int dr[kSl], di[kSl];
     digits6(vr, dr);
@@ -1363,18 +1392,17 @@ __global__ void fwd_vec_planes_kernel(const double2* __restrict__ mhat, int64_t 
   const int64_t w = blockIdx.x, b = blockIdx.y;
   const int64_t KB = Kp / kKiBox;
   const double2* src = mhat + ((b0 + b) * nf + w) * Nm;
-  double mx = 0.0;
+  unsigned long long mb = 0;
   if (b < nb)
-    for (int64_t j = threadIdx.x; j < Nm; j += blockDim.x) mx = fmax(mx, fmax(fabs(src[j].x), fabs(src[j].y)));
-  __shared__ double red[32];
+    for (int64_t j = threadIdx.x; j < Nm; j += blockDim.x) mb = max(mb, max(abs_bits(src[j].x), abs_bits(src[j].y)));
+  __shared__ unsigned long long red[32];
   __shared__ int es;
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mb;
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) mx = fmax(mx, red[k]);
-    int e = 0;
-    if (mx > 0.0) frexp(mx, &e);
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) mb = max(mb, red[k]);
+    const int e = exp_of_bits(mb);
     es = e;
     ex[w * kKiRows + 2 * b] = e;
     ex[w * kKiRows + 2 * b + 1] = e;
@@ -1386,8 +1414,8 @@ __global__ void fwd_vec_planes_kernel(const double2* __restrict__ mhat, int64_t 
   for (int64_t j = threadIdx.x; j < Kp / 2; j += blockDim.x) {
     long long vr = 0, vi = 0;
     if (b < nb && j < Nm) {
-      vr = __double2ll_rn(scalbn(src[j].x, 47 - e));
-      vi = __double2ll_rn(scalbn(src[j].y, 47 - e));
+      vr = round_scaled(src[j].x, 47 - e);
+      vi = round_scaled(src[j].y, 47 - e);
     }
     int dr[kSl], di[kSl];
     digits6(vr, dr);
