@@ -14,12 +14,14 @@
 // fixed-point image of each row, the rest rounded away).  Then
 //   X[b][i] = 2^(ea_i + eb_b - 14) sum_g 2^(-8 g) G_g[i][b],  G_g = sum_{s + t = g} P_s Q_t^T,
 // keeping the 21 plane pairs with s + t <= 5 (the dropped ones lie below 2^-48 of the row
-// scale).  Every product of two digits is at most 2^14 and each group sums at most six
-// plane pairs, so over a chunk of 128 columns j a group's sum stays below 6 * 128 * 2^14
-// < 2^24: the FP32 accumulators in tensor memory hold it exactly.  After each chunk the
-// epilogue warps read the six groups, scale them by 2^(-8 g) (exact) and add them into
-// float-pair accumulators with a two-sum, as the double-FP32 kernels do, and convert the
-// result to FP64 with integer operations.  The complex spectral products are real GEMMs over
+// scale).  Every product of two digits is at most 2^14 and group g sums g + 1 plane pairs, so
+// over an accumulation period of 192 columns j group g's sum stays below (g + 1) 192 2^14: up
+// to group 4 that is below 2^24, and the FP32 accumulators in tensor memory hold it exactly;
+// group 5 (6 pairs, 2^-40 of group 0's weight) may exceed 2^24 by a fraction, and its rounding
+// stays below 2^-54 of the period's scale.  After each period the epilogue warps read the six
+// groups, scale them by 2^(-8 g) (exact) and add them into float-pair accumulators with a
+// two-sum, as the double-FP32 kernels do, and convert the result to FP64 with integer
+// operations.  The complex spectral products are real GEMMs over
 // an interleaved (re, im) K axis, the vectors' rows carrying the complex product's signs.
 //
 // Layout: a matrix's planes [S][ldk / 64][rows_pad][64] FP16 (rows_pad and ldk multiples of
@@ -29,7 +31,9 @@
 // partial tiles go to an FP64 buffer that a second kernel sums in CTA order.  Warp 0 issues
 // the TMA loads (the matrix's planes 128 rows x 64 columns per stage, the six right-hand-side
 // planes per 64 columns), warp 1 runs the MMA loop with one elected lane issuing tcgen05.mma
-// (M = 128, N = 64 or 32, K = 16) into six TMEM groups, warps 2-9 drain the groups per chunk.
+// (M = 128, N = 64 or 32, K = 16) into six TMEM groups, A reused from the tensor core's
+// collector across the MMAs of each A plane, and warps 2-9 drain the groups per period (and at
+// the end of each tile in the CTA's share).
 // Every wait is bounded; on a timeout the kernel sets the error word, stops issuing, lets what
 // it issued land and frees its tensor memory.
 #include "bti_internal.cuh"
@@ -48,14 +52,16 @@ constexpr int kSl = 6;                 // digit planes per operand
 constexpr int kKiRows = 128;           // MMA M: rows of the matrix per tile
 constexpr int kKiN = 64;               // MMA N: right-hand-side columns per launch chunk
 constexpr int kKiBox = 64;             // FP16 columns per tile of the planes in memory (128 bytes)
-constexpr int kKiChunk = 128;          // columns per exact accumulation chunk
+constexpr int kKiChunk = 128;          // columns per work chunk (the unit of stream-K and of tile skipping)
+constexpr int kDrainK = 12;            // K-steps (16 columns each) per accumulation period: 192 columns
+constexpr int kPeriodCols = 204;       // most data columns a period may hold (5 204 2^14 < 2^24)
 constexpr int kBx = 32;                // FP16 columns per TMA box in the pipeline (64 bytes, the swizzle width)
 constexpr int kBoxesPerChunk = kKiChunk / kBx;
 constexpr int kStages = 3;             // pipeline stages: one 32-column box of all six planes of both operands
 constexpr int kKiThreads = 320;        // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
 constexpr uint32_t kAPlane = kKiRows * kBx * 2;  // bytes of one A plane in a stage (128 rows x 64 B)
 constexpr uint32_t kAStage = kSl * kAPlane;       // 48 KB
-constexpr uint32_t kTmemCols = 512;    // six accumulator groups (6 N columns) and two A buffers (2 x 48)
+constexpr uint32_t kTmemCols = 512;    // six accumulator groups (6 N columns, N <= 64)
 constexpr long long kKiSpin = 1ll << 24;              // poll backstop of every wait
 constexpr uint64_t kKiWaitNs = 1000000000ull;          // wall-time limit of every wait: 1 s
 // shared memory of a kernel whose B operand has NC rows: 1 KB alignment slack and kStages stages
@@ -125,10 +131,11 @@ __device__ __forceinline__ void tmem_ld(uint32_t addr, uint32_t (&v)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Add one chunk's six exact group sums G_g (TMEM columns NC g + the W columns at taddr, this
-// warp's lanes) into the float-pair accumulators: sum_g 2^(-8 g) G_g.  Groups 5, 4, 3 are
-// summed in plain FP32 first: that partial sum is below 1.01 in units where G_0 reaches 2^24,
-// so its rounding stays under 2^-47 of the total; groups 2, 1, 0 and that sum enter by two-sum.
+// Add one accumulation period's six group sums G_g (TMEM columns NC g + the W columns at taddr,
+// this warp's lanes) into the float-pair accumulators: sum_g 2^(-8 g) G_g.  Groups 5, 4, 3 are
+// summed in plain FP32 first: in group 0's units that partial sum is below 0.76 (|G_3| <
+// 4 192 2^14), so its rounding, at most 2^-25, stays under 2^-46 of the period's bound
+// 192 2^14 on |G_0|; groups 2, 1, 0 and that sum enter by two-sum.
 template <int NC, int W>
 __device__ __forceinline__ void add_groups(uint32_t taddr, float (&Sh)[W], float (&Sl)[W]) {
   uint32_t v[W];
@@ -209,23 +216,35 @@ __device__ __forceinline__ void commit_elect(uint32_t bar) {
       "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n"
       ::"r"(bar) : "memory");
 }
+// Whether the accumulation period closes after K-step k (0-based along a K axis of ksteps
+// K-steps): at the end of the CTA's share of a tile, and after every kDrainK K-steps, except
+// that the axis's last K-step joins the period before it when that period then holds at most
+// kPeriodCols data columns (tail_cols: the data columns of the last K-step).
+__device__ __forceinline__ bool period_closes(int64_t k, int64_t ksteps, int tail_cols, bool share_last) {
+  if (share_last) return true;
+  if ((k + 1) % kDrainK != 0) return false;
+  return !(k + 2 == ksteps && kDrainK * 16 + tail_cols <= kPeriodCols);
+}
+
 // bounded wait taken by a whole warp: true only if every lane saw the phase complete
 __device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
   return __all_sync(0xffffffffu, mbar_wait(bar, parity, abort_flag));
 }
 
-// One K-step (16 columns) of a stage, as one instruction block under a single elect.sync: the
-// six A plane slices are copied into tensor memory (columns abuf + 8 s), then the 21 plane pairs
-// s + t <= 5 run with A from tensor memory, group s + t accumulating at TMEM columns NC (s + t).
-// a0, b0: the stage's plane 0 of A and of B; kk: the K-step within the 32-column box (32 bytes, 2
-// in the encoded start address).  first: the K-step opens an accumulation chunk, so the pairs
-// (0, t), issued first, overwrite the groups.  Consecutive planes of a stage are kAPlane bytes
-// apart (512 in the descriptor's 16-byte units) for A and NC kBx 2 bytes for B; the shared-
-// memory addresses stay below 2^18, so the offsets add to the descriptors' address field
-// without carrying out of it.  Called by a whole warp.
+// One K-step (16 columns) of a stage, as one instruction block under a single elect.sync: the 21
+// plane pairs s + t <= 5, group s + t accumulating at TMEM columns NC (s + t), both operands read
+// from shared memory.  The pairs are issued plane by plane of A, and each A plane slice is read
+// once: the first MMA of plane s fills the tensor core's A collector, the next ones reuse it and
+// the last releases it (plane 5 has one MMA, which reads A directly).  a0, b0: the stage's plane 0
+// of A and of B; kk: the K-step within the 32-column box (32 bytes, 2 in the encoded start
+// address).  first: the K-step opens an accumulation period, so the pairs (0, t), issued first,
+// overwrite the groups.  Consecutive planes of a stage are kAPlane bytes apart (512 in the
+// descriptor's 16-byte units) for A and NC kBx 2 bytes for B; the shared-memory addresses stay
+// below 2^18, so the offsets add to the descriptors' address field without carrying out of it.
+// Called by a whole warp.
 template <int NC>
-__device__ __forceinline__ void issue_kstep(uint32_t tmem, uint32_t abuf, uint32_t a0, uint32_t b0, int kk,
-                                            uint32_t idesc, bool first) {
+__device__ __forceinline__ void issue_kstep(uint32_t tmem, uint32_t a0, uint32_t b0, int kk, uint32_t idesc,
+                                            bool first) {
   static_assert(kAPlane == 512 * 16, "A plane stride in descriptor units");
   constexpr uint64_t bs = (uint64_t)((NC * kBx * 2) >> 4);
   const uint64_t ad = sdesc(a0) + 2 * kk;
@@ -234,60 +253,49 @@ __device__ __forceinline__ void issue_kstep(uint32_t tmem, uint32_t abuf, uint32
       "{\n"
       ".reg .pred e, pa, pt;\n"
       ".reg .b64 a1, a2, a3, a4, a5, b1, b2, b3, b4, b5;\n"
-      ".reg .b32 c1, c2, c3, c4, c5, d1, d2, d3, d4, d5;\n"
+      ".reg .b32 d1, d2, d3, d4, d5;\n"
       "elect.sync _|e, 0xffffffff;\n"
-      "setp.eq.u32 pa, %5, 0;\n"
-      "setp.eq.u32 pt, %5, %5;\n"
-      "add.u64 a1, %2, 512;\n"
-      "add.u64 b1, %3, %6;\n"
-      "add.u32 c1, %1, 8;\n"
-      "add.u32 d1, %0, %11;\n"
-      "add.u64 a2, %2, 1024;\n"
-      "add.u64 b2, %3, %7;\n"
-      "add.u32 c2, %1, 16;\n"
-      "add.u32 d2, %0, %12;\n"
-      "add.u64 a3, %2, 1536;\n"
-      "add.u64 b3, %3, %8;\n"
-      "add.u32 c3, %1, 24;\n"
-      "add.u32 d3, %0, %13;\n"
-      "add.u64 a4, %2, 2048;\n"
-      "add.u64 b4, %3, %9;\n"
-      "add.u32 c4, %1, 32;\n"
-      "add.u32 d4, %0, %14;\n"
-      "add.u64 a5, %2, 2560;\n"
-      "add.u64 b5, %3, %10;\n"
-      "add.u32 c5, %1, 40;\n"
-      "add.u32 d5, %0, %15;\n"
-      "@e tcgen05.cp.cta_group::1.128x256b [%1], %2;\n"
-      "@e tcgen05.cp.cta_group::1.128x256b [c1], a1;\n"
-      "@e tcgen05.cp.cta_group::1.128x256b [c2], a2;\n"
-      "@e tcgen05.cp.cta_group::1.128x256b [c3], a3;\n"
-      "@e tcgen05.cp.cta_group::1.128x256b [c4], a4;\n"
-      "@e tcgen05.cp.cta_group::1.128x256b [c5], a5;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %3, %4, pa;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16 [d1], [%1], b1, %4, pa;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16 [d2], [%1], b2, %4, pa;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16 [d3], [%1], b3, %4, pa;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16 [d4], [%1], b4, %4, pa;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16 [d5], [%1], b5, %4, pa;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16 [d1], [c1], %3, %4, pt;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16 [d2], [c1], b1, %4, pt;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16 [d3], [c1], b2, %4, pt;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16 [d4], [c1], b3, %4, pt;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16 [d5], [c1], b4, %4, pt;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16 [d2], [c2], %3, %4, pt;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16 [d3], [c2], b1, %4, pt;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16 [d4], [c2], b2, %4, pt;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16 [d5], [c2], b3, %4, pt;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16 [d3], [c3], %3, %4, pt;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16 [d4], [c3], b1, %4, pt;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16 [d5], [c3], b2, %4, pt;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16 [d4], [c4], %3, %4, pt;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16 [d5], [c4], b1, %4, pt;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16 [d5], [c5], %3, %4, pt;\n"
+      "setp.eq.u32 pa, %4, 0;\n"
+      "setp.eq.u32 pt, %4, %4;\n"
+      "add.u64 a1, %1, 512;\n"
+      "add.u64 b1, %2, %5;\n"
+      "add.u32 d1, %0, %10;\n"
+      "add.u64 a2, %1, 1024;\n"
+      "add.u64 b2, %2, %6;\n"
+      "add.u32 d2, %0, %11;\n"
+      "add.u64 a3, %1, 1536;\n"
+      "add.u64 b3, %2, %7;\n"
+      "add.u32 d3, %0, %12;\n"
+      "add.u64 a4, %1, 2048;\n"
+      "add.u64 b4, %2, %8;\n"
+      "add.u32 d4, %0, %13;\n"
+      "add.u64 a5, %1, 2560;\n"
+      "add.u64 b5, %2, %9;\n"
+      "add.u32 d5, %0, %14;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, %3, pa;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::use [d1], %1, b1, %3, pa;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::use [d2], %1, b2, %3, pa;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::use [d3], %1, b3, %3, pa;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::use [d4], %1, b4, %3, pa;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [d5], %1, b5, %3, pa;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [d1], a1, %2, %3, pt;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::use [d2], a1, b1, %3, pt;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::use [d3], a1, b2, %3, pt;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::use [d4], a1, b3, %3, pt;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [d5], a1, b4, %3, pt;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [d2], a2, %2, %3, pt;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::use [d3], a2, b1, %3, pt;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::use [d4], a2, b2, %3, pt;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [d5], a2, b3, %3, pt;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [d3], a3, %2, %3, pt;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::use [d4], a3, b1, %3, pt;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [d5], a3, b2, %3, pt;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [d4], a4, %2, %3, pt;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [d5], a4, b1, %3, pt;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [d5], a5, %2, %3, pt;\n"
       "}\n"
-      ::"r"(tmem), "r"(abuf), "l"(ad), "l"(bd), "r"(idesc), "r"(first ? 1u : 0u), "n"(bs), "n"(2 * bs), "n"(3 * bs),
-        "n"(4 * bs), "n"(5 * bs), "n"(NC), "n"(2 * NC), "n"(3 * NC), "n"(4 * NC), "n"(5 * NC)
+      ::"r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(first ? 1u : 0u), "n"(bs), "n"(2 * bs), "n"(3 * bs), "n"(4 * bs),
+        "n"(5 * bs), "n"(NC), "n"(2 * NC), "n"(3 * NC), "n"(4 * NC), "n"(5 * NC)
       : "memory");
 }
 
@@ -555,16 +563,15 @@ __global__ void __launch_bounds__(kKiThreads, 1)
 sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
              const int* __restrict__ ea, const int* __restrict__ eb, double* __restrict__ part, int64_t per,
              int64_t total, int64_t kpt, int span, int NRG, int64_t a_blk, int a_rg, int64_t b_blk, int b_rg,
-             int ea_w, int ea_rg, int eb_w, int eb_rg, int64_t ksteps, int drop_stage, int* __restrict__ err,
-             const TileJob tj) {
+             int ea_w, int ea_rg, int eb_w, int eb_rg, int64_t ksteps, int tail_cols, int drop_stage,
+             int* __restrict__ err, const TileJob tj) {
   constexpr uint32_t kBPlane = NC * kBx * 2, kBStage = kSl * kBPlane;
-  constexpr uint32_t kACol = kSl * NC;  // TMEM column of the two A buffers (48 columns each)
   constexpr int W = NC / 2;             // columns per epilogue thread
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   unsigned char* sA = smem;
   unsigned char* sB = smem + kStages * kAStage;
-  __shared__ uint64_t full[kStages], empty[kStages], abar[2], accf, tfree, mdone;
+  __shared__ uint64_t full[kStages], empty[kStages], accf, tfree, mdone;
   __shared__ uint32_t tmem_holder;
   __shared__ int abort_flag;
 
@@ -589,7 +596,6 @@ sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[q])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[q])));
     }
-    for (int q = 0; q < 2; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&abar[q])));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&accf)));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(smem_u32(&tfree)));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mdone)));
@@ -663,18 +669,17 @@ sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
         mbar_wait(smem_u32(&full[i % kStages]), (i / kStages) & 1, &unused);
     }
   } else if (warp == 1) {
-    // ---- MMA issuer (the whole warp, one elected lane issues): per K-step the A slices go to
-    // one of two tensor-memory buffers, which the K-step two earlier must have finished reading
+    // ---- MMA issuer (the whole warp, one elected lane issues).  An accumulation period ends
+    // after kDrainK K-steps or with the last K-step of the tile's chunks in this CTA's share;
+    // the next period starts once the epilogue has drained the groups.
     {
       const uint32_t idesc = (1u << 4) | ((uint32_t)(NC >> 3) << 17) | ((uint32_t)(kKiRows >> 4) << 24);
-      int nbx = 0, ks = 0, cc = 0;
+      int nbx = 0, kp = 0, dc = 0;  // boxes consumed, K-steps in the open period, periods closed
       bool ok = true;
       WorkIter<TILES, NC> it;
-      for (it.init(tj, per, total, kpt); it.valid && ok; it.next(tj), ++cc) {
+      for (it.init(tj, per, total, kpt); it.valid && ok; it.next(tj)) {
         const int nks = chunk_ksteps(it.c);
-        // the epilogue has drained the previous chunk's groups
-        if (cc > 0 && !mbar_wait_warp(smem_u32(&tfree), (cc - 1) & 1, abort_v)) break;
-        asm volatile("tcgen05.fence::after_thread_sync;");
+        const bool tile_end = it.last();
         for (int kb = 0; kb < (nks + 1) / 2 && ok; ++kb, ++nbx) {
           const int st = nbx % kStages;
           if (!mbar_wait_warp(smem_u32(&full[st]), (nbx / kStages) & 1, abort_v)) {
@@ -682,22 +687,27 @@ sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;");
-          for (int kk = 0; kk < 2 && 2 * kb + kk < nks; ++kk, ++ks) {
-            const int ab = ks & 1;
-            if (ks >= 2 && !mbar_wait_warp(smem_u32(&abar[ab]), ((ks >> 1) - 1) & 1, abort_v)) {
-              ok = false;
-              break;
+          for (int kk = 0; kk < 2 && 2 * kb + kk < nks; ++kk) {
+            if (kp == 0 && dc > 0) {
+              // the epilogue has drained the previous period's groups
+              if (!mbar_wait_warp(smem_u32(&tfree), (dc - 1) & 1, abort_v)) {
+                ok = false;
+                break;
+              }
+              asm volatile("tcgen05.fence::after_thread_sync;");
             }
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            issue_kstep<NC>(tmem, tmem + kACol + 48u * (uint32_t)ab, smem_u32(sA + st * kAStage),
-                            smem_u32(sB + st * kBStage), kk, idesc, kb == 0 && kk == 0);
-            commit_elect(smem_u32(&abar[ab]));
+            issue_kstep<NC>(tmem, smem_u32(sA + st * kAStage), smem_u32(sB + st * kBStage), kk, idesc, kp == 0);
+            ++kp;
+            if (period_closes(it.c * (kKiChunk / 16) + 2 * kb + kk, ksteps, tail_cols,
+                              tile_end && 2 * kb + kk + 1 == nks)) {
+              commit_elect(smem_u32(&accf));
+              ++dc;
+              kp = 0;
+            }
           }
           if (!ok) break;
           commit_elect(smem_u32(&empty[st]));
         }
-        if (!ok) break;
-        commit_elect(smem_u32(&accf));
       }
       // completion of every MMA issued above (waited on before the tensor memory is freed)
       commit_elect(smem_u32(&mdone));
@@ -710,17 +720,29 @@ sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     float Sh[W], Sl[W];
 #pragma unroll
     for (int c = 0; c < W; ++c) Sh[c] = Sl[c] = 0.f;
-    int cc = 0;
+    int dc = 0;  // periods drained
+    bool ok = true;
     WorkIter<TILES, NC> it;
-    for (it.init(tj, per, total, kpt); it.valid; it.next(tj), ++cc) {
+    for (it.init(tj, per, total, kpt); it.valid && ok; it.next(tj)) {
       const int64_t T = it.T;
-      if (!mbar_wait(smem_u32(&accf), cc & 1, abort_v)) break;
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      add_groups<NC, W>(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(h * W), Sh, Sl);
-      asm volatile("tcgen05.fence::before_thread_sync;");
-      __syncwarp();
-      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tfree)) : "memory");
-      if (!it.last()) continue;
+      const bool tile_end = it.last();
+      // periods that close within this chunk (the MMA warp's schedule)
+      const int nks = chunk_ksteps(it.c);
+      int nd = 0;
+      for (int k = 0; k < nks; ++k)
+        nd += period_closes(it.c * (kKiChunk / 16) + k, ksteps, tail_cols, tile_end && k + 1 == nks);
+      for (int q = 0; q < nd; ++q, ++dc) {
+        if (!mbar_wait(smem_u32(&accf), dc & 1, abort_v)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        add_groups<NC, W>(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(h * W), Sh, Sl);
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tfree)) : "memory");
+      }
+      if (!ok || !tile_end) continue;
       // the tile's last chunk in this CTA's share: write the result
       if constexpr (TILES) {
         const int64_t row = it.I * kKiRows + r;
@@ -804,6 +826,9 @@ bool kinv_tc_supported(int64_t n) {
 size_t kinv_tc_plane_elems(int64_t n) { return (size_t)kSl * kinv_tc_ld(n) * kinv_tc_ld(n); }
 
 namespace {
+// data columns of the last 16-column K-step of a K axis of K columns (K > 0)
+int tail_cols(int64_t K) { return (int)(K - 16 * ((K + 15) / 16 - 1)); }
+
 int num_sms_tc() {
   static int v = 0;
   if (v == 0) {
@@ -891,7 +916,7 @@ cudaError_t rowmat_apply_tc(const void* planes, const int* ea, int64_t M, int64_
     // tiles: the 128-row tiles of the matrix (one problem); A rows kbg Mp + 128 t, B rows 64 kbg
     sk_tc_kernel<64><<<(unsigned)p.ctas, kKiThreads, dig_smem(64), s>>>(
         tA, tB, ea, eb, part, p.per, p.total, p.kpt, p.span, (int)p.tiles, Mp, kKiRows, kKiN, 0, 0, kKiRows, 0, 0,
-        (n + 15) / 16, drop_stage, err, TileJob{});
+        (n + 15) / 16, tail_cols(n), drop_stage, err, TileJob{});
     *launches += 1;
     *launches += kinv_reduce(part, X + q0 * ldx, ldx, M, nb, kKiRows, kKiN, p.per, p.kpt, p.span, p.tiles, s);
   }
@@ -952,8 +977,8 @@ cudaError_t digit_gemm_tc(const void* pa, const int* ea, const void* pb, const i
     return cudaErrorInvalidValue;
   kinv_tc_prepare();
   sk_tc_kernel<64, true><<<(unsigned)ctas, kKiThreads, dig_smem(64), s>>>(
-      tA, tB, ea, eb, nullptr, 0, 0, ld / kKiChunk, 1, 1, Mp, 0, Np, 0, 0, 0, 0, 0, (g.K + 15) / 16, drop_stage, err,
-      tj);
+      tA, tB, ea, eb, nullptr, 0, 0, ld / kKiChunk, 1, 1, Mp, 0, Np, 0, 0, 0, 0, 0, (g.K + 15) / 16, tail_cols(g.K),
+      drop_stage, err, tj);
   *launches = 1;
   return cudaGetLastError();
 }
@@ -1076,14 +1101,13 @@ __global__ void __launch_bounds__(kKiThreads, 1)
 adj_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const int* __restrict__ ea, const int* __restrict__ eb, double2* __restrict__ mhat, int nf,
               int64_t Nm, int64_t Nmp, int64_t NBp, int B, int nchunk, int JT, int NG, int64_t per, int64_t total,
-              int ksteps, int drop_stage, int* __restrict__ err) {
+              int ksteps, int tail_cols, int drop_stage, int* __restrict__ err) {
   constexpr uint32_t kBPlane = kKiN * kBx * 2, kBStage = kSl * kBPlane;
-  constexpr uint32_t kACol = kSl * kKiN;  // TMEM column of the two A buffers
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   unsigned char* sA = smem;
   unsigned char* sB = smem + kStages * kAStage;
-  __shared__ uint64_t full[kStages], empty[kStages], abar[2], accf, tfree, mdone;
+  __shared__ uint64_t full[kStages], empty[kStages], accf, tfree, mdone;
   __shared__ uint32_t tmem_holder;
   __shared__ int abort_flag;
 
@@ -1099,7 +1123,6 @@ adj_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[q])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[q])));
     }
-    for (int q = 0; q < 2; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&abar[q])));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&accf)));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(smem_u32(&tfree)));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mdone)));
@@ -1168,20 +1191,15 @@ adj_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         mbar_wait(smem_u32(&full[i % kStages]), (i / kStages) & 1, &unused);
     }
   } else if (warp == 1) {
-    // ---- MMA issuer (the whole warp, one elected lane issues); chunk counter cc across units,
-    // K-step counter ks for the two tensor-memory A buffers
+    // ---- MMA issuer (the whole warp, one elected lane issues); accumulation periods of kDrainK
+    // K-steps, the last one of each unit closed by the unit's end
     {
       const uint32_t idesc = (1u << 4) | ((uint32_t)(kKiN >> 3) << 17) | ((uint32_t)(kKiRows >> 4) << 24);
-      int nbx = 0, cc = 0, ks = 0;
+      int nbx = 0, kp = 0, dc = 0;  // boxes consumed, K-steps in the open period, periods closed
       bool ok = true;
       for (int u = 0; u < nunits && ok; ++u) {
-        for (int c = 0; c < nchunk && ok; ++c, ++cc) {
+        for (int c = 0; c < nchunk && ok; ++c) {
           const int nks = chunk_ksteps(c);
-          if (cc > 0 && !mbar_wait_warp(smem_u32(&tfree), (cc - 1) & 1, abort_v)) {
-            ok = false;
-            break;
-          }
-          asm volatile("tcgen05.fence::after_thread_sync;");
           for (int kb = 0; kb < (nks + 1) / 2 && ok; ++kb, ++nbx) {
             const int st = nbx % kStages;
             if (!mbar_wait_warp(smem_u32(&full[st]), (nbx / kStages) & 1, abort_v)) {
@@ -1189,22 +1207,26 @@ adj_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
               break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            for (int kk = 0; kk < 2 && 2 * kb + kk < nks; ++kk, ++ks) {
-              const int ab = ks & 1;
-              if (ks >= 2 && !mbar_wait_warp(smem_u32(&abar[ab]), ((ks >> 1) - 1) & 1, abort_v)) {
-                ok = false;
-                break;
+            for (int kk = 0; kk < 2 && 2 * kb + kk < nks; ++kk) {
+              if (kp == 0 && dc > 0) {
+                if (!mbar_wait_warp(smem_u32(&tfree), (dc - 1) & 1, abort_v)) {
+                  ok = false;
+                  break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
               }
-              asm volatile("tcgen05.fence::after_thread_sync;");
-              issue_kstep<kKiN>(tmem, tmem + kACol + 48u * (uint32_t)ab, smem_u32(sA + st * kAStage),
-                                smem_u32(sB + st * kBStage), kk, idesc, kb == 0 && kk == 0);
-              commit_elect(smem_u32(&abar[ab]));
+              issue_kstep<kKiN>(tmem, smem_u32(sA + st * kAStage), smem_u32(sB + st * kBStage), kk, idesc, kp == 0);
+              ++kp;
+              if (period_closes(c * (kKiChunk / 16) + 2 * kb + kk, ksteps, tail_cols,
+                                c == nchunk - 1 && 2 * kb + kk + 1 == nks)) {
+                commit_elect(smem_u32(&accf));
+                ++dc;
+                kp = 0;
+              }
             }
             if (!ok) break;
             commit_elect(smem_u32(&empty[st]));
           }
-          if (!ok) break;
-          commit_elect(smem_u32(&accf));
         }
       }
       commit_elect(smem_u32(&mdone));
@@ -1217,15 +1239,18 @@ adj_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     float Sh[32], Sl[32];
 #pragma unroll
     for (int c = 0; c < 32; ++c) Sh[c] = Sl[c] = 0.f;
-    int cc = 0;
+    // periods per unit: the MMA warp's schedule over the unit's ksteps K-steps
+    int nper = 0;
+    for (int k = 0; k < ksteps; ++k) nper += period_closes(k, ksteps, tail_cols, k + 1 == ksteps);
+    int dc = 0;
     bool ok = true;
     for (int u = 0; u < nunits && ok; ++u) {
       const int64_t unit = u0 + u;
       const int g = (int)(unit % NG);
       const int jt = (int)((unit / NG) % JT);
       const int w = (int)(unit / ((int64_t)NG * JT));
-      for (int c = 0; c < nchunk; ++c, ++cc) {
-        if (!mbar_wait(smem_u32(&accf), cc & 1, abort_v)) {
+      for (int q = 0; q < nper; ++q, ++dc) {
+        if (!mbar_wait(smem_u32(&accf), dc & 1, abort_v)) {
           ok = false;
           break;
         }
@@ -1316,7 +1341,7 @@ cudaError_t adj_digits_apply(const void* planes, const int* ea, int64_t nf, int6
   const int64_t ctas = (total + per - 1) / per;
   adj_tc_kernel<<<(unsigned)ctas, kKiThreads, dig_smem(kKiN), s>>>(
       tA, tB, ea, eb, static_cast<double2*>(mhat), (int)nf, Nm, Nmp, NBp, (int)B, (int)(Kp / kKiChunk), JT, NG, per,
-      total, (int)((2 * R + 15) / 16), drop_stage, err);
+      total, (int)((2 * R + 15) / 16), tail_cols(2 * R), drop_stage, err);
   *launches = 2;
   return cudaGetLastError();
 }
@@ -1523,11 +1548,11 @@ cudaError_t fwd_digits_apply(const void* planes, const int* ex, int64_t nf, int6
     if (p.NC == 32)
       sk_tc_kernel<32><<<(unsigned)p.ctas, kKiThreads, dig_smem(32), s>>>(
           tA, tB, ev, ex, part, p.per, p.total, p.kpt, p.span, p.NRG, kKiRows, 0, p.Rp, p.NC, kKiRows, 0, (int)p.Rp,
-          p.NC, ksteps, drop_stage, err, TileJob{});
+          p.NC, ksteps, tail_cols(2 * Nm), drop_stage, err, TileJob{});
     else
       sk_tc_kernel<64><<<(unsigned)p.ctas, kKiThreads, dig_smem(64), s>>>(
           tA, tB, ev, ex, part, p.per, p.total, p.kpt, p.span, p.NRG, kKiRows, 0, p.Rp, p.NC, kKiRows, 0, (int)p.Rp,
-          p.NC, ksteps, drop_stage, err, TileJob{});
+          p.NC, ksteps, tail_cols(2 * Nm), drop_stage, err, TileJob{});
     const int64_t tot = nb * nf * R;
     fwd_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, static_cast<double2*>(dhat), nf, R, b0, nb,
                                                                    p.NC, p.NRG, p.per, p.kpt, p.span);
