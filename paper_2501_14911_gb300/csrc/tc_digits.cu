@@ -494,7 +494,8 @@ struct TileJob {
 
 template <bool TILES, int NC>
 struct WorkIter {
-  int64_t T, c, c1, I, J, u, u1, kpt;
+  int64_t T, c, c1, I, J, u, u1, kpt, wt;
+  int side, rg;  // stream-K: NRG CTAs side by side (side = NRG), this CTA's row group; else side = 0
   bool valid;
   __device__ __forceinline__ void tile_range(const TileJob& tj) {
     if (tj.trap) {
@@ -514,23 +515,29 @@ struct WorkIter {
     }
     valid = false;
   }
-  __device__ __forceinline__ void init(const TileJob& tj, int64_t per, int64_t total, int64_t kpt_) {
+  __device__ __forceinline__ void locate() {  // stream-K: tile and chunk of unit u
+    wt = u / kpt;
+    c = u - wt * kpt;
+    T = side ? wt * side + rg : wt;
+  }
+  __device__ __forceinline__ void init(const TileJob& tj, int64_t per, int64_t total, int64_t kpt_, int side_ = 0) {
     kpt = kpt_;
     valid = true;
     if constexpr (TILES) {
       T = blockIdx.x;
       seek(tj);
     } else {
-      u = (int64_t)blockIdx.x * per;
+      side = side_;
+      rg = side ? (int)(blockIdx.x % side) : 0;
+      u = (int64_t)(side ? blockIdx.x / side : blockIdx.x) * per;
       u1 = min(total, u + per);
       valid = u < u1;
-      T = u / kpt;
-      c = u - T * kpt;
+      locate();
     }
   }
   __device__ __forceinline__ bool last() const {
     if constexpr (TILES) return c + 1 == c1;
-    return u + 1 == u1 || (u + 1) / kpt != T;
+    return u + 1 == u1 || (u + 1) / kpt != wt;
   }
   __device__ __forceinline__ void next(const TileJob& tj) {
     if constexpr (TILES) {
@@ -540,8 +547,7 @@ struct WorkIter {
     } else {
       ++u;
       valid = u < u1;
-      T = u / kpt;
-      c = u - T * kpt;
+      locate();
     }
   }
 };
@@ -552,7 +558,9 @@ struct WorkIter {
 // TMA row (w KB + kbg) a_blk + rg a_rg of the A planes and (w KB + kbg) b_blk + rg b_rg of the B
 // planes (KB = 2 kpt); row m's exponent is ea[w ea_w + rg ea_rg + m], column c's
 // eb[w eb_w + rg eb_rg + c] (padding rows and columns hold 0); a CTA covers units
-// [blockIdx per, + per) and writes one FP64 partial tile [NC][128] per tile it touches.  Tile
+// [blockIdx per, + per) and writes one FP64 partial tile [NC][128] per tile it touches.  With
+// side = NRG the units are (w, chunk) instead, and CTA b takes row group b % side of units
+// [(b / side) per, + per): the NRG CTAs of a group stream the same A planes side by side.  Tile
 // form (TILES = true, the Cholesky's updates and the triangular products of the inverse): tile
 // (I, J) of tj reads A rows 128 I and B rows NC J (a_blk, b_blk: the planes' padded row counts),
 // exponents ea[128 I + m] and eb[NC J + c], and combines its result into tj.C.  Either way the
@@ -563,7 +571,7 @@ __global__ void __launch_bounds__(kKiThreads, 1)
 sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
              const int* __restrict__ ea, const int* __restrict__ eb, double* __restrict__ part, int64_t per,
              int64_t total, int64_t kpt, int span, int NRG, int64_t a_blk, int a_rg, int64_t b_blk, int b_rg,
-             int ea_w, int ea_rg, int eb_w, int eb_rg, int64_t ksteps, int tail_cols, int drop_stage,
+             int ea_w, int ea_rg, int eb_w, int eb_rg, int64_t ksteps, int tail_cols, int side, int drop_stage,
              int* __restrict__ err, const TileJob tj) {
   constexpr uint32_t kBPlane = NC * kBx * 2, kBStage = kSl * kBPlane;
   constexpr int W = NC / 2;             // columns per epilogue thread
@@ -586,7 +594,8 @@ sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
       if (skip) return;
     }
   }
-  const int64_t first_tile = ((int64_t)blockIdx.x * per) / kpt;  // stream-K: first tile of the run
+  // stream-K: first tile of the CTA's run, counted in its own sequence of tiles
+  const int64_t first_tile = ((int64_t)(side ? blockIdx.x / side : blockIdx.x) * per) / kpt;
   const int KB = (int)(kpt * (kKiChunk / kKiBox));
   // K-steps and 32-column boxes of chunk c (the last chunk may be partly padding)
   auto chunk_ksteps = [&](int64_t c) { return (int)min((int64_t)(kKiChunk / 16), ksteps - c * (kKiChunk / 16)); };
@@ -619,7 +628,7 @@ sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
       int nbx = 0;
       bool ok = true;
       WorkIter<TILES, NC> it;
-      for (it.init(tj, per, total, kpt); it.valid && ok; it.next(tj)) {
+      for (it.init(tj, per, total, kpt, side); it.valid && ok; it.next(tj)) {
         const int64_t T = it.T, c = it.c;
         int64_t w, ta, tb;  // problem, and the tile's row offsets in A and in B
         if constexpr (TILES) {
@@ -677,7 +686,7 @@ sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
       int nbx = 0, kp = 0, dc = 0;  // boxes consumed, K-steps in the open period, periods closed
       bool ok = true;
       WorkIter<TILES, NC> it;
-      for (it.init(tj, per, total, kpt); it.valid && ok; it.next(tj)) {
+      for (it.init(tj, per, total, kpt, side); it.valid && ok; it.next(tj)) {
         const int nks = chunk_ksteps(it.c);
         const bool tile_end = it.last();
         for (int kb = 0; kb < (nks + 1) / 2 && ok; ++kb, ++nbx) {
@@ -723,7 +732,7 @@ sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     int dc = 0;  // periods drained
     bool ok = true;
     WorkIter<TILES, NC> it;
-    for (it.init(tj, per, total, kpt); it.valid && ok; it.next(tj)) {
+    for (it.init(tj, per, total, kpt, side); it.valid && ok; it.next(tj)) {
       const int64_t T = it.T;
       const bool tile_end = it.last();
       // periods that close within this chunk (the MMA warp's schedule)
@@ -764,7 +773,7 @@ sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
         const int64_t w = T / NRG, rg = T - w * NRG;
         const int er = ea[w * ea_w + rg * ea_rg + r];
         const int* ebt = eb + w * eb_w + rg * eb_rg;
-        double* P = part + ((blockIdx.x * (int64_t)span + (T - first_tile)) * NC) * kKiRows;
+        double* P = part + ((blockIdx.x * (int64_t)span + (it.wt - first_tile)) * NC) * kKiRows;
 #pragma unroll
         for (int c = 0; c < W; ++c) {
           const int col = h * W + c;
@@ -916,7 +925,7 @@ cudaError_t rowmat_apply_tc(const void* planes, const int* ea, int64_t M, int64_
     // tiles: the 128-row tiles of the matrix (one problem); A rows kbg Mp + 128 t, B rows 64 kbg
     sk_tc_kernel<64><<<(unsigned)p.ctas, kKiThreads, dig_smem(64), s>>>(
         tA, tB, ea, eb, part, p.per, p.total, p.kpt, p.span, (int)p.tiles, Mp, kKiRows, kKiN, 0, 0, kKiRows, 0, 0,
-        (n + 15) / 16, tail_cols(n), drop_stage, err, TileJob{});
+        (n + 15) / 16, tail_cols(n), 0, drop_stage, err, TileJob{});
     *launches += 1;
     *launches += kinv_reduce(part, X + q0 * ldx, ldx, M, nb, kKiRows, kKiN, p.per, p.kpt, p.span, p.tiles, s);
   }
@@ -977,7 +986,7 @@ cudaError_t digit_gemm_tc(const void* pa, const int* ea, const void* pb, const i
     return cudaErrorInvalidValue;
   kinv_tc_prepare();
   sk_tc_kernel<64, true><<<(unsigned)ctas, kKiThreads, dig_smem(64), s>>>(
-      tA, tB, ea, eb, nullptr, 0, 0, ld / kKiChunk, 1, 1, Mp, 0, Np, 0, 0, 0, 0, 0, (g.K + 15) / 16, tail_cols(g.K),
+      tA, tB, ea, eb, nullptr, 0, 0, ld / kKiChunk, 1, 1, Mp, 0, Np, 0, 0, 0, 0, 0, (g.K + 15) / 16, tail_cols(g.K), 0,
       drop_stage, err, tj);
   *launches = 1;
   return cudaGetLastError();
@@ -1011,8 +1020,9 @@ cudaError_t syrk_lower_tc(const void* planes, const int* ex, int64_t m, int64_t 
 // per (w, j) over i and B one per (w, b), so each output's scale factors out of its sum.
 // Planes: A' [S][n_f][K_pad / 64][N_m,pad][64], B [S][n_f][K_pad / 64][NB_pad][64] FP16 (tiled
 // by 64-column boxes) with K_pad = 2R rounded up to 128, N_m,pad to 128 and NB_pad = 2B to 64.  A unit is (w, 128 rows j, 64 columns n)
-// over all of K (chunks of 128 as above); units are split evenly over one CTA per SM, the
-// column groups of a row tile back to back so its A' planes are read from HBM once.
+// over all of K (chunks of 128 as above); the (w, row tile) units are split evenly over groups of
+// NG CTAs (one CTA per SM), the CTAs of a group taking the same units for the NG column groups
+// side by side, so a row tile's A' planes come from HBM once and from L2 for the other groups.
 
 namespace {
 
@@ -1112,7 +1122,11 @@ adj_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
   __shared__ int abort_flag;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t u0 = (int64_t)blockIdx.x * per;
+  // CTA b takes column group g = b % NG of the (w, row tile) units [q per, (q + 1) per), q = b / NG:
+  // the NG CTAs of a row tile stream its planes at about the same time, so all but the first
+  // read them from L2
+  const int g = (int)(blockIdx.x % NG);
+  const int64_t u0 = (int64_t)(blockIdx.x / NG) * per;
   const int64_t u1 = min(total, u0 + per);
   const int nunits = (int)(u1 - u0);
   // K-steps of chunk c (the last chunk may be partly padding, neither loaded nor multiplied)
@@ -1147,9 +1161,8 @@ adj_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
       bool ok = true;
       for (int u = 0; u < nunits && ok; ++u) {
         const int64_t unit = u0 + u;
-        const int g = (int)(unit % NG);
-        const int jt = (int)((unit / NG) % JT);
-        const int w = (int)(unit / ((int64_t)NG * JT));
+        const int jt = (int)(unit % JT);
+        const int w = (int)(unit / JT);
         const int KB = nchunk * (kKiChunk / kKiBox);
         for (int c = 0; c < nchunk && ok; ++c) {
           const int nbox = (chunk_ksteps(c) + 1) / 2;
@@ -1246,9 +1259,8 @@ adj_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     bool ok = true;
     for (int u = 0; u < nunits && ok; ++u) {
       const int64_t unit = u0 + u;
-      const int g = (int)(unit % NG);
-      const int jt = (int)((unit / NG) % JT);
-      const int w = (int)(unit / ((int64_t)NG * JT));
+      const int jt = (int)(unit % JT);
+      const int w = (int)(unit / JT);
       for (int q = 0; q < nper; ++q, ++dc) {
         if (!mbar_wait(smem_u32(&accf), dc & 1, abort_v)) {
           ok = false;
@@ -1335,10 +1347,11 @@ cudaError_t adj_digits_apply(const void* planes, const int* ea, int64_t nf, int6
   adj_vec_planes_kernel<<<dim3((unsigned)nf, (unsigned)(NBp / 2)), 128, 0, s>>>(
       static_cast<const double2*>(dhat), nf, R, B, NBp, Kp, bpl, eb);
   const int JT = (int)(Nmp / kKiRows), NG = (int)(NBp / kKiN);
-  const int64_t total = nf * JT * NG;
-  const int64_t slots = num_sms_tc();
-  const int64_t per = (total + slots - 1) / slots;
-  const int64_t ctas = (total + per - 1) / per;
+  // units (w, row tile), each taken by NG CTAs side by side (one per 64-column group of B)
+  const int64_t total = nf * JT;
+  const int64_t groups = std::max<int64_t>(1, num_sms_tc() / NG);
+  const int64_t per = (total + groups - 1) / groups;
+  const int64_t ctas = (total + per - 1) / per * NG;
   adj_tc_kernel<<<(unsigned)ctas, kKiThreads, dig_smem(kKiN), s>>>(
       tA, tB, ea, eb, static_cast<double2*>(mhat), (int)nf, Nm, Nmp, NBp, (int)B, (int)(Kp / kKiChunk), JT, NG, per,
       total, (int)((2 * R + 15) / 16), tail_cols(2 * R), drop_stage, err);
@@ -1361,7 +1374,8 @@ void adj_digits_prepare() {
 // so D[2b][i] = Re d-hat_w[b][i] and D[2b+1][i] = Im d-hat_w[b][i]; one exponent per (w, i) for
 // A and per (w, b) for V.  The long K axis (2 N_m) runs through the stream-K kernel with tiles
 // (w, NC rows i), the 128 vector rows of 64 vectors as the MMA's M, NC = 32 for R <= 32 and
-// 64 otherwise.  Planes: A [S][n_f][K_pad / 64][R_pad][64], V [S][n_f][K_pad / 64][128][64].
+// 64 otherwise; the row groups of a frequency run side by side on neighbouring CTAs.
+// Planes: A [S][n_f][K_pad / 64][R_pad][64], V [S][n_f][K_pad / 64][128][64].
 
 namespace {
 
@@ -1460,13 +1474,14 @@ __global__ void fwd_reduce_kernel(const double* __restrict__ part, double2* __re
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= nb * nf * R) return;
   const int64_t b = idx / (nf * R), wi = idx - b * nf * R, w = wi / R, i = wi - w * R;
-  const int64_t T = w * NRG + i / NC;
+  const int64_t rg = i / NC;
   const int col = (int)(i % NC);
-  const int64_t c0 = (T * kpt) / per, c1 = ((T + 1) * kpt - 1) / per;
+  // the CTA groups whose runs of (w, chunk) units cover frequency w, each through its CTA rg
+  const int64_t q0 = (w * kpt) / per, q1 = ((w + 1) * kpt - 1) / per;
   double re = 0.0, im = 0.0;
-  for (int64_t c = c0; c <= c1; ++c) {
-    const int64_t slot = T - (c * per) / kpt;
-    const double* P = part + ((c * span + slot) * NC + col) * kKiRows;
+  for (int64_t q = q0; q <= q1; ++q) {
+    const int64_t slot = w - (q * per) / kpt;
+    const double* P = part + (((q * NRG + rg) * span + slot) * NC + col) * kKiRows;
     re += P[2 * b];
     im += P[2 * b + 1];
   }
@@ -1486,10 +1501,12 @@ FwdPlan fwd_plan(int64_t nf, int64_t R, int64_t Nm) {
   p.Kp = rup(2 * Nm, kKiChunk);
   p.KB = p.Kp / kKiBox;
   p.kpt = p.Kp / kKiChunk;
-  p.total = nf * p.NRG * p.kpt;
-  const int64_t slots = num_sms_tc();
-  p.per = (p.total + slots - 1) / slots;
-  p.ctas = (p.total + p.per - 1) / p.per;
+  // units (w, chunk), each taken by NRG CTAs side by side (one per row group of F), so that a
+  // frequency's vector planes come from HBM once and from L2 for the other row groups
+  p.total = nf * p.kpt;
+  const int64_t groups = std::max<int64_t>(1, num_sms_tc() / p.NRG);
+  p.per = (p.total + groups - 1) / groups;
+  p.ctas = (p.total + p.per - 1) / p.per * p.NRG;
   p.span = (int)((p.per + p.kpt - 1) / p.kpt + 1);
   return p;
 }
@@ -1548,11 +1565,11 @@ cudaError_t fwd_digits_apply(const void* planes, const int* ex, int64_t nf, int6
     if (p.NC == 32)
       sk_tc_kernel<32><<<(unsigned)p.ctas, kKiThreads, dig_smem(32), s>>>(
           tA, tB, ev, ex, part, p.per, p.total, p.kpt, p.span, p.NRG, kKiRows, 0, p.Rp, p.NC, kKiRows, 0, (int)p.Rp,
-          p.NC, ksteps, tail_cols(2 * Nm), drop_stage, err, TileJob{});
+          p.NC, ksteps, tail_cols(2 * Nm), p.NRG, drop_stage, err, TileJob{});
     else
       sk_tc_kernel<64><<<(unsigned)p.ctas, kKiThreads, dig_smem(64), s>>>(
           tA, tB, ev, ex, part, p.per, p.total, p.kpt, p.span, p.NRG, kKiRows, 0, p.Rp, p.NC, kKiRows, 0, (int)p.Rp,
-          p.NC, ksteps, tail_cols(2 * Nm), drop_stage, err, TileJob{});
+          p.NC, ksteps, tail_cols(2 * Nm), p.NRG, drop_stage, err, TileJob{});
     const int64_t tot = nb * nf * R;
     fwd_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, static_cast<double2*>(dhat), nf, R, b0, nb,
                                                                    p.NC, p.NRG, p.per, p.kpt, p.span);
