@@ -415,6 +415,19 @@ bti_status bti_apply_Q(bti_handle h, const double* d_obs, double* q_map, int64_t
  * buffers; either pointer may be NULL. */
 bti_status bti_copy_Q(bti_handle h, double* Q_out, double* cov_out);
 
+/* Precision of the online phase that bti_online captures (Sec. 4, Phase 4), for latency
+ * targets looser than FP64.  BTI_P_DF64 (the default): FP64-level m_map and q_map, the same
+ * arithmetic as bti_infer_map and bti_predict_qoi / bti_apply_Q.  BTI_P_F32: for B >= 16
+ * vectors with tensor cores on, the digit-plane products (bti_invert_K, bti_set_digit_planes,
+ * bti_set_online_qoi) use only the most significant of the six planes of each operand: five
+ * for K^{-1} (a 39-bit image, error about kappa(K) 2^-38 relative to ||K^{-1} d||) and four
+ * for G^*, F_q and Q (31 bits, about 2^-30 of each output's row scale); the transforms keep
+ * FP64 level.  m_map and q_map then stay within about 1e-8 of the FP64 result (relative,
+ * 2-norm) for kappa(K) up to about 1e4; fewer vectors, and the other entry points, keep FP64
+ * level.  refine_iters must be 0 under BTI_P_F32 (BTI_ERR_ARG from bti_online).  Any other
+ * prec: BTI_ERR_ARG.  A change drops the captured online graph. */
+bti_status bti_set_online_precision(bti_handle h, bti_prec prec);
+
 /* How bti_online gives q_map.  via_Q = 1: q_map = Q d_obs with the d2q map of bti_build_Q
  * (Eq. (4.14), the paper's online QoI prediction; requires build_Q, BTI_ERR_STATE
  * otherwise), and Q is also formed as six FP16 digit planes (12 (N_q N_t^q rounded up to

@@ -79,6 +79,7 @@ def lib():
         "bti_factor_K": ([vp], st),
         "bti_invert_K": ([vp, ip], st),
         "bti_set_online_qoi": ([vp, ip], st),
+        "bti_set_online_precision": ([vp, ip], st),
         "bti_set_digit_planes": ([vp, ip, ip], st),
         "bti_copy_K": ([vp, vp], st),
         "bti_infer_map": ([vp, vp, vp, i64, ip], st),
@@ -270,6 +271,11 @@ class Handle:
     def set_digit_planes(self, op, enable=True):
         """Exact tensor-core adjoint products (B >= 16) for a double-FP32 operator."""
         self._check(lib().bti_set_digit_planes(self._h, int(op), int(bool(enable))))
+
+    def set_online_precision(self, prec):
+        """online() at FP64 level (DF64, the default) or at FP32 level (F32: the tensor-core
+        products on their most significant digit planes only, about 1e-8 relative)."""
+        self._check(lib().bti_set_online_precision(self._h, int(prec)))
 
     def set_online_qoi(self, via_Q=True):
         """online() takes q_map = Q d_obs (needs build_Q; Q on the tensor cores) or F_q m_map."""

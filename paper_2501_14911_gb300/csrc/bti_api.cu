@@ -73,6 +73,10 @@ struct bti_ctx {
   float2* Q_pairs = nullptr;     // Q as float pairs [nq][kQpairLd(n)] for one or two vectors per call
   int64_t Qpr_gen = -1;          // Q_gen the pairs were formed from
   bool online_via_Q = false;     // bti_online takes q_map = Q d_obs (Eq. (4.14))
+  int online_prec = BTI_P_DF64;  // bti_set_online_precision: BTI_P_DF64 or BTI_P_F32
+  // digit planes the tensor-core products use (6: all); fewer only while bti_online captures the
+  // graph of the FP32-level online form
+  int planes_kinv = 6, planes_op = 6;
   int qstride = 1;               // QoI time grid: every qstride-th step (N_t^q = N_t / qstride)
   double* K = nullptr;           // [n][n], lower triangle: K, then L after factor_K
   double* Linv = nullptr;        // inverses of the factor's diagonal blocks
@@ -94,6 +98,7 @@ struct bti_ctx {
   void* og_q = nullptr;
   int64_t og_B = -1;
   int og_refine = -1;
+  int og_prec = -1;
   cudaStream_t og_stream = nullptr;
   // measurement hook (bti_profile_enable / bti_profile_read)
   bool prof_on = false;
@@ -402,7 +407,7 @@ bti_status apply_fwd_t(bti_ctx* h, const OpStore& o, const void* in, void* out, 
     {
       ProfScope ps(h, BTI_K_PROD_FWD);  // vector planes, the MMA kernel and its fixed-order sum
       e = fwd_digits_apply(o.dig_f, o.dig_f_ex, nf, R, Nm, mhat, dhat, B, (char*)h->ws + base, h->status + 1, s, &nl,
-                           h->tc_drop_stage);
+                           h->tc_drop_stage, h->planes_op);
     }
     h->prof_count[BTI_K_PROD_FWD] += nl - 1;
     if (e != cudaSuccess) return cuda_check(h, e, "tensor-core forward product (digit planes)");
@@ -453,7 +458,7 @@ bti_status apply_adj_t(bti_ctx* h, const OpStore& o, const void* in, void* out, 
     {
       ProfScope ps(h, BTI_K_PROD_ADJ);
       e = adj_digits_apply(o.dig, o.dig_ex, nf, R, Nm, dhat, mhat, B, (char*)h->ws + base, h->status + 1, s, &nl,
-                           h->tc_drop_stage);
+                           h->tc_drop_stage, h->planes_op);
     }
     h->prof_count[BTI_K_PROD_ADJ] += nl - 1;
     if (e != cudaSuccess) return cuda_check(h, e, "tensor-core adjoint product (digit planes)");
@@ -1197,7 +1202,7 @@ static bti_status infer_map_impl(bti_handle h, const double* d_obs, double* m_ma
     if (inv_tc) {
       int64_t nl = 0;
       cudaError_t e = kinv_apply_tc(h->kinv_planes, h->kinv_ea, n, v, B, xo, work + (size_t)B * n, h->status + 1, s,
-                                    &nl, h->tc_drop_stage);
+                                    &nl, h->tc_drop_stage, h->planes_kinv);
       if (e != cudaSuccess) tc_err = e;
       return nl;
     }
@@ -1470,7 +1475,7 @@ static bti_status apply_Q_impl(bti_ctx* h, const double* d_obs, double* q_map, i
     if (st != BTI_OK) return st;
     int64_t nl = 0;
     cudaError_t e = rowmat_apply_tc(h->Q_planes, h->Q_ea, nq, n, d_obs, B, q_map, nq, h->wsolve + (size_t)2 * B * n,
-                                    h->status + 1, h->stream, &nl, h->tc_drop_stage);
+                                    h->status + 1, h->stream, &nl, h->tc_drop_stage, h->planes_op);
     count_dense(h, nl);
     if (e != cudaSuccess) return cuda_check(h, e, "tensor-core Q product");
     return launched(h, "apply_Q");
@@ -1488,6 +1493,16 @@ static bti_status apply_Q_impl(bti_ctx* h, const double* d_obs, double* q_map, i
   count_dense(h, (dd ? gemm_df64 : gemm_f64)(true, B, nq, n, 1.0, d_obs, n, 0, h->Q, n, 0, 0.0, q_map, nq, 0, 1,
                                              false, h->stream));
   return launched(h, "apply_Q");
+}
+
+bti_status bti_set_online_precision(bti_handle h, bti_prec prec) {
+  bti_status st = check_handle(h);
+  if (st != BTI_OK) return st;
+  if (prec != BTI_P_DF64 && prec != BTI_P_F32)
+    return fail(h, BTI_ERR_ARG, "set_online_precision: BTI_P_DF64 or BTI_P_F32");
+  if (prec != h->online_prec) drop_online_graph_any(h);
+  h->online_prec = prec;
+  return BTI_OK;
 }
 
 bti_status bti_set_online_qoi(bti_handle h, int via_Q) {
@@ -2205,6 +2220,9 @@ bti_status bti_online(bti_handle h, const double* d_obs, double* m_map, double* 
   bti_status st = check_handle(h);
   if (st != BTI_OK) return st;
   if (B <= 0 || refine_iters < 0) return fail(h, BTI_ERR_ARG, "online: B must be > 0 and refine_iters >= 0");
+  const bool f32 = h->online_prec == BTI_P_F32;
+  if (f32 && refine_iters > 0)
+    return fail(h, BTI_ERR_ARG, "online: refinement needs the FP64-level form (bti_set_online_precision)");
   if (!d_obs || !m_map) return fail(h, BTI_ERR_ARG, "online: null pointer");
   if (!h->K_factored) return fail(h, BTI_ERR_STATE, "online: K not factored");
   if (!h->op[BTI_OP_G].set) return fail(h, BTI_ERR_STATE, "online: G blocks not set");
@@ -2212,7 +2230,7 @@ bti_status bti_online(bti_handle h, const double* d_obs, double* m_map, double* 
   if (q_map && h->online_via_Q && !h->Q_built) return fail(h, BTI_ERR_STATE, "online: q_map via Q but Q not built");
   if (!h->stream) return fail(h, BTI_ERR_STATE, "online: graph capture needs a non-default stream");
   const bool same = h->online_exec && h->og_d == d_obs && h->og_m == m_map && h->og_q == q_map && h->og_B == B &&
-                    h->og_refine == refine_iters && h->og_stream == h->stream;
+                    h->og_refine == refine_iters && h->og_prec == h->online_prec && h->og_stream == h->stream;
   if (!same) {
     drop_online_graph_any(h);
     st = reserve_online(h, B);
@@ -2224,10 +2242,17 @@ bti_status bti_online(bti_handle h, const double* d_obs, double* m_map, double* 
       h->prof_on = prof;
       return st;
     }
+    if (f32) {
+      // FP32-level form: the top five digit planes for K^{-1} (its error grows with kappa(K)),
+      // four for G^*, F_q and Q
+      h->planes_kinv = 5;
+      h->planes_op = 4;
+    }
     bti_status run = infer_map_impl(h, d_obs, m_map, B, refine_iters);
     if (run == BTI_OK && q_map)
       run = h->online_via_Q ? apply_Q_impl(h, d_obs, q_map, B)
                             : apply_op(h, BTI_OP_FQ, false, m_map, q_map, B, BTI_P_F64, "online F_q");
+    h->planes_kinv = h->planes_op = 6;
     cudaGraph_t graph = nullptr;
     cudaError_t ee = cudaStreamEndCapture(h->stream, &graph);
     h->prof_on = prof;
@@ -2249,6 +2274,7 @@ bti_status bti_online(bti_handle h, const double* d_obs, double* m_map, double* 
     h->og_q = q_map;
     h->og_B = B;
     h->og_refine = refine_iters;
+    h->og_prec = h->online_prec;
     h->og_stream = h->stream;
   }
   return cuda_check(h, cudaGraphLaunch(h->online_exec, h->stream), "launch online graph");

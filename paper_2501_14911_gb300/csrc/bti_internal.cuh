@@ -256,15 +256,18 @@ size_t kinv_tc_plane_elems(int64_t n);
 size_t kinv_tc_work_elems(int64_t n);
 int64_t kinv_tc_slice(const double* X, int64_t ldx, int64_t rows, int64_t n, int* ex, void* planes,
                       int64_t rows_pad, cudaStream_t s);
+// planes (4 to 6, every product here): how many of the six digit planes of each operand the
+// product uses, most significant first (8 planes - 1 bits); 6 keeps the 47-bit image.
 cudaError_t kinv_apply_tc(const void* planes, const int* ea, int64_t n, const double* D, int64_t B, double* X,
-                          double* work, int* err, cudaStream_t s, int64_t* launches, int drop_stage = -1);
+                          double* work, int* err, cudaStream_t s, int64_t* launches, int drop_stage = -1,
+                          int nplanes = 6);
 // The same for any row-major M x n matrix (planes of kinv_tc_slice with rows_pad =
 // kinv_tc_ld(M)): X [B][ldx] rows = matrix D[b] (the d2q map Q of Eq. (4.14)).
 size_t rowmat_tc_plane_elems(int64_t M, int64_t n);
 size_t rowmat_tc_work_elems(int64_t M, int64_t n);
 cudaError_t rowmat_apply_tc(const void* planes, const int* ea, int64_t M, int64_t n, const double* D, int64_t B,
                             double* X, int64_t ldx, double* work, int* err, cudaStream_t s, int64_t* launches,
-                            int drop_stage = -1);
+                            int drop_stage = -1, int nplanes = 6);
 // C -= X X[0:w]^T on and below the diagonal (C row stride ldc, the first w <= m columns), X
 // m x kdim given by its planes (kinv_tc_slice, rows_pad = kinv_tc_ld(m)) and row exponents ex:
 // the tensor-core updates of cholesky_tc.
@@ -333,10 +336,10 @@ int64_t fwd_digits_build(const void* hat, int64_t nf, int64_t R, int64_t Nm, voi
 size_t fwd_digits_work_bytes(int64_t nf, int64_t R, int64_t Nm);
 cudaError_t fwd_digits_apply(const void* planes, const int* ex, int64_t nf, int64_t R, int64_t Nm, const void* mhat,
                              void* dhat, int64_t B, void* work, int* err, cudaStream_t s, int* launches,
-                             int drop_stage = -1);
+                             int drop_stage = -1, int nplanes = 6);
 cudaError_t adj_digits_apply(const void* planes, const int* ea, int64_t nf, int64_t R, int64_t Nm, const void* dhat,
                              void* mhat, int64_t B, void* work, int* err, cudaStream_t s, int* launches,
-                             int drop_stage = -1);
+                             int drop_stage = -1, int nplanes = 6);
 int axpby_f64(double* y, const double* x, double a, double b, int64_t n, cudaStream_t s);
 // FP32 Gram product W = A B^T into an FP64 matrix (lower tiles) and the FP64 -> FP32 copy
 int sgemm_nt_lower_to_f64(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* Bm,

@@ -131,27 +131,31 @@ __device__ __forceinline__ void tmem_ld(uint32_t addr, uint32_t (&v)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Add one accumulation period's six group sums G_g (TMEM columns NC g + the W columns at taddr,
-// this warp's lanes) into the float-pair accumulators: sum_g 2^(-8 g) G_g.  Groups 5, 4, 3 are
+// Add one accumulation period's S group sums G_g (TMEM columns NC g + the W columns at taddr,
+// this warp's lanes) into the float-pair accumulators: sum_g 2^(-8 g) G_g.  Groups S - 1 .. 3 are
 // summed in plain FP32 first: in group 0's units that partial sum is below 0.76 (|G_3| <
 // 4 192 2^14), so its rounding, at most 2^-25, stays under 2^-46 of the period's bound
 // 192 2^14 on |G_0|; groups 2, 1, 0 and that sum enter by two-sum.
-template <int NC, int W>
+template <int NC, int W, int S>
 __device__ __forceinline__ void add_groups(uint32_t taddr, float (&Sh)[W], float (&Sl)[W]) {
+  static_assert(S >= 4 && S <= 6, "four to six digit planes");
   uint32_t v[W];
   float low[W];
-  tmem_ld(taddr + 5 * NC, v);
+  tmem_ld(taddr + (S - 1) * NC, v);
+  {
+    const float sc = __int_as_float((127 - 8 * (S - 1)) << 23);  // 2^(-8 (S - 1)), exact
 #pragma unroll
-  for (int c = 0; c < W; ++c) low[c] = __uint_as_float(v[c]) * 0x1p-40f;
-  tmem_ld(taddr + 4 * NC, v);
-#pragma unroll
-  for (int c = 0; c < W; ++c) low[c] = fmaf(__uint_as_float(v[c]), 0x1p-32f, low[c]);
-  tmem_ld(taddr + 3 * NC, v);
-#pragma unroll
-  for (int c = 0; c < W; ++c) {
-    low[c] = fmaf(__uint_as_float(v[c]), 0x1p-24f, low[c]);
-    two_sum_acc(Sh[c], Sl[c], low[c]);
+    for (int c = 0; c < W; ++c) low[c] = __uint_as_float(v[c]) * sc;
   }
+#pragma unroll
+  for (int g = S - 2; g >= 3; --g) {
+    tmem_ld(taddr + g * NC, v);
+    const float sc = __int_as_float((127 - 8 * g) << 23);
+#pragma unroll
+    for (int c = 0; c < W; ++c) low[c] = fmaf(__uint_as_float(v[c]), sc, low[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < W; ++c) two_sum_acc(Sh[c], Sl[c], low[c]);
 #pragma unroll
   for (int g = 2; g >= 0; --g) {
     tmem_ld(taddr + g * NC, v);
@@ -231,72 +235,161 @@ __device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, vo
   return __all_sync(0xffffffffu, mbar_wait(bar, parity, abort_flag));
 }
 
-// One K-step (16 columns) of a stage, as one instruction block under a single elect.sync: the 21
-// plane pairs s + t <= 5, group s + t accumulating at TMEM columns NC (s + t), both operands read
-// from shared memory.  The pairs are issued plane by plane of A, and each A plane slice is read
-// once: the first MMA of plane s fills the tensor core's A collector, the next ones reuse it and
-// the last releases it (plane 5 has one MMA, which reads A directly).  a0, b0: the stage's plane 0
-// of A and of B; kk: the K-step within the 32-column box (32 bytes, 2 in the encoded start
-// address).  first: the K-step opens an accumulation period, so the pairs (0, t), issued first,
-// overwrite the groups.  Consecutive planes of a stage are kAPlane bytes apart (512 in the
-// descriptor's 16-byte units) for A and NC kBx 2 bytes for B; the shared-memory addresses stay
-// below 2^18, so the offsets add to the descriptors' address field without carrying out of it.
-// Called by a whole warp.
-template <int NC>
+// One K-step (16 columns) of a stage, as one instruction block under a single elect.sync: the
+// S (S + 1) / 2 plane pairs s + t <= S - 1 of the first S planes of each operand (S = 6: all 21),
+// group s + t accumulating at TMEM columns NC (s + t), both operands read from shared memory.
+// The pairs are issued plane by plane of A, and each A plane slice is read once: the first MMA
+// of plane s fills the tensor core's A collector, the next ones reuse it and the last releases
+// it (plane S - 1 has one MMA, which reads A directly).  ad, bd: the descriptors of the stage's
+// plane 0 of A and of B at this K-step.  first: the K-step opens an accumulation period, so the
+// pairs (0, t), issued first, overwrite the groups.  Consecutive planes of a stage are kAPlane
+// bytes apart (512 in the descriptor's 16-byte units) for A and NC kBx 2 bytes for B; the
+// shared-memory addresses stay below 2^18, so the offsets add to the descriptors' address field
+// without carrying out of it.  Called by a whole warp.
+static_assert(kAPlane == 512 * 16, "A plane stride in descriptor units");
+template <int S> struct KStep;
+template <> struct KStep<4> {
+  template <int NC>
+  static __device__ __forceinline__ void issue(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, bool first) {
+    constexpr uint64_t bs = (uint64_t)((NC * kBx * 2) >> 4);
+    asm volatile(
+        "{\n"
+        ".reg .pred e, pa, pt;\n"
+        ".reg .b64 a1, a2, a3, b1, b2, b3;\n"
+        ".reg .b32 d1, d2, d3;\n"
+        "elect.sync _|e, 0xffffffff;\n"
+        "setp.eq.u32 pa, %4, 0;\n"
+        "setp.eq.u32 pt, %4, %4;\n"
+        "add.u64 a1, %1, 512;\n"
+        "add.u64 b1, %2, %5;\n"
+        "add.u32 d1, %0, %8;\n"
+        "add.u64 a2, %1, 1024;\n"
+        "add.u64 b2, %2, %6;\n"
+        "add.u32 d2, %0, %9;\n"
+        "add.u64 a3, %1, 1536;\n"
+        "add.u64 b3, %2, %7;\n"
+        "add.u32 d3, %0, %10;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, %3, pa;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::use [d1], %1, b1, %3, pa;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::use [d2], %1, b2, %3, pa;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [d3], %1, b3, %3, pa;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [d1], a1, %2, %3, pt;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::use [d2], a1, b1, %3, pt;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [d3], a1, b2, %3, pt;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [d2], a2, %2, %3, pt;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [d3], a2, b1, %3, pt;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [d3], a3, %2, %3, pt;\n"
+        "}\n"
+        ::"r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(first ? 1u : 0u), "n"(1 * bs), "n"(2 * bs), "n"(3 * bs),
+          "n"(1 * NC), "n"(2 * NC), "n"(3 * NC)
+        : "memory");
+  }
+};
+template <> struct KStep<5> {
+  template <int NC>
+  static __device__ __forceinline__ void issue(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, bool first) {
+    constexpr uint64_t bs = (uint64_t)((NC * kBx * 2) >> 4);
+    asm volatile(
+        "{\n"
+        ".reg .pred e, pa, pt;\n"
+        ".reg .b64 a1, a2, a3, a4, b1, b2, b3, b4;\n"
+        ".reg .b32 d1, d2, d3, d4;\n"
+        "elect.sync _|e, 0xffffffff;\n"
+        "setp.eq.u32 pa, %4, 0;\n"
+        "setp.eq.u32 pt, %4, %4;\n"
+        "add.u64 a1, %1, 512;\n"
+        "add.u64 b1, %2, %5;\n"
+        "add.u32 d1, %0, %9;\n"
+        "add.u64 a2, %1, 1024;\n"
+        "add.u64 b2, %2, %6;\n"
+        "add.u32 d2, %0, %10;\n"
+        "add.u64 a3, %1, 1536;\n"
+        "add.u64 b3, %2, %7;\n"
+        "add.u32 d3, %0, %11;\n"
+        "add.u64 a4, %1, 2048;\n"
+        "add.u64 b4, %2, %8;\n"
+        "add.u32 d4, %0, %12;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, %3, pa;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::use [d1], %1, b1, %3, pa;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::use [d2], %1, b2, %3, pa;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::use [d3], %1, b3, %3, pa;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [d4], %1, b4, %3, pa;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [d1], a1, %2, %3, pt;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::use [d2], a1, b1, %3, pt;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::use [d3], a1, b2, %3, pt;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [d4], a1, b3, %3, pt;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [d2], a2, %2, %3, pt;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::use [d3], a2, b1, %3, pt;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [d4], a2, b2, %3, pt;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [d3], a3, %2, %3, pt;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [d4], a3, b1, %3, pt;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [d4], a4, %2, %3, pt;\n"
+        "}\n"
+        ::"r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(first ? 1u : 0u), "n"(1 * bs), "n"(2 * bs), "n"(3 * bs),
+          "n"(4 * bs), "n"(1 * NC), "n"(2 * NC), "n"(3 * NC), "n"(4 * NC)
+        : "memory");
+  }
+};
+template <> struct KStep<6> {
+  template <int NC>
+  static __device__ __forceinline__ void issue(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, bool first) {
+    constexpr uint64_t bs = (uint64_t)((NC * kBx * 2) >> 4);
+    asm volatile(
+        "{\n"
+        ".reg .pred e, pa, pt;\n"
+        ".reg .b64 a1, a2, a3, a4, a5, b1, b2, b3, b4, b5;\n"
+        ".reg .b32 d1, d2, d3, d4, d5;\n"
+        "elect.sync _|e, 0xffffffff;\n"
+        "setp.eq.u32 pa, %4, 0;\n"
+        "setp.eq.u32 pt, %4, %4;\n"
+        "add.u64 a1, %1, 512;\n"
+        "add.u64 b1, %2, %5;\n"
+        "add.u32 d1, %0, %10;\n"
+        "add.u64 a2, %1, 1024;\n"
+        "add.u64 b2, %2, %6;\n"
+        "add.u32 d2, %0, %11;\n"
+        "add.u64 a3, %1, 1536;\n"
+        "add.u64 b3, %2, %7;\n"
+        "add.u32 d3, %0, %12;\n"
+        "add.u64 a4, %1, 2048;\n"
+        "add.u64 b4, %2, %8;\n"
+        "add.u32 d4, %0, %13;\n"
+        "add.u64 a5, %1, 2560;\n"
+        "add.u64 b5, %2, %9;\n"
+        "add.u32 d5, %0, %14;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, %3, pa;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::use [d1], %1, b1, %3, pa;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::use [d2], %1, b2, %3, pa;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::use [d3], %1, b3, %3, pa;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::use [d4], %1, b4, %3, pa;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [d5], %1, b5, %3, pa;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [d1], a1, %2, %3, pt;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::use [d2], a1, b1, %3, pt;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::use [d3], a1, b2, %3, pt;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::use [d4], a1, b3, %3, pt;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [d5], a1, b4, %3, pt;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [d2], a2, %2, %3, pt;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::use [d3], a2, b1, %3, pt;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::use [d4], a2, b2, %3, pt;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [d5], a2, b3, %3, pt;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [d3], a3, %2, %3, pt;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::use [d4], a3, b1, %3, pt;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [d5], a3, b2, %3, pt;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [d4], a4, %2, %3, pt;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [d5], a4, b1, %3, pt;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [d5], a5, %2, %3, pt;\n"
+        "}\n"
+        ::"r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(first ? 1u : 0u), "n"(1 * bs), "n"(2 * bs), "n"(3 * bs),
+          "n"(4 * bs), "n"(5 * bs), "n"(1 * NC), "n"(2 * NC), "n"(3 * NC), "n"(4 * NC), "n"(5 * NC)
+        : "memory");
+  }
+};
+
+// The K-step kk (0 or 1) of a stage whose plane 0 of A and of B sit at a0 and b0.
+template <int NC, int S>
 __device__ __forceinline__ void issue_kstep(uint32_t tmem, uint32_t a0, uint32_t b0, int kk, uint32_t idesc,
                                             bool first) {
-  static_assert(kAPlane == 512 * 16, "A plane stride in descriptor units");
-  constexpr uint64_t bs = (uint64_t)((NC * kBx * 2) >> 4);
-  const uint64_t ad = sdesc(a0) + 2 * kk;
-  const uint64_t bd = sdesc(b0) + 2 * kk;
-  asm volatile(
-      "{\n"
-      ".reg .pred e, pa, pt;\n"
-      ".reg .b64 a1, a2, a3, a4, a5, b1, b2, b3, b4, b5;\n"
-      ".reg .b32 d1, d2, d3, d4, d5;\n"
-      "elect.sync _|e, 0xffffffff;\n"
-      "setp.eq.u32 pa, %4, 0;\n"
-      "setp.eq.u32 pt, %4, %4;\n"
-      "add.u64 a1, %1, 512;\n"
-      "add.u64 b1, %2, %5;\n"
-      "add.u32 d1, %0, %10;\n"
-      "add.u64 a2, %1, 1024;\n"
-      "add.u64 b2, %2, %6;\n"
-      "add.u32 d2, %0, %11;\n"
-      "add.u64 a3, %1, 1536;\n"
-      "add.u64 b3, %2, %7;\n"
-      "add.u32 d3, %0, %12;\n"
-      "add.u64 a4, %1, 2048;\n"
-      "add.u64 b4, %2, %8;\n"
-      "add.u32 d4, %0, %13;\n"
-      "add.u64 a5, %1, 2560;\n"
-      "add.u64 b5, %2, %9;\n"
-      "add.u32 d5, %0, %14;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, %3, pa;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::use [d1], %1, b1, %3, pa;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::use [d2], %1, b2, %3, pa;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::use [d3], %1, b3, %3, pa;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::use [d4], %1, b4, %3, pa;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [d5], %1, b5, %3, pa;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [d1], a1, %2, %3, pt;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::use [d2], a1, b1, %3, pt;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::use [d3], a1, b2, %3, pt;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::use [d4], a1, b3, %3, pt;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [d5], a1, b4, %3, pt;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [d2], a2, %2, %3, pt;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::use [d3], a2, b1, %3, pt;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::use [d4], a2, b2, %3, pt;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [d5], a2, b3, %3, pt;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [d3], a3, %2, %3, pt;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::use [d4], a3, b1, %3, pt;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [d5], a3, b2, %3, pt;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [d4], a4, %2, %3, pt;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [d5], a4, b1, %3, pt;\n"
-      "@e tcgen05.mma.cta_group::1.kind::f16 [d5], a5, %2, %3, pt;\n"
-      "}\n"
-      ::"r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(first ? 1u : 0u), "n"(bs), "n"(2 * bs), "n"(3 * bs), "n"(4 * bs),
-        "n"(5 * bs), "n"(NC), "n"(2 * NC), "n"(3 * NC), "n"(4 * NC), "n"(5 * NC)
-      : "memory");
+  KStep<S>::template issue<NC>(tmem, sdesc(a0) + 2 * kk, sdesc(b0) + 2 * kk, idesc, first);
 }
 
 // (hi + lo) 2^e as an FP64 value with integer operations only (GB300 issues FP64 at 1/64 of
@@ -566,7 +659,7 @@ struct WorkIter {
 // exponents ea[128 I + m] and eb[NC J + c], and combines its result into tj.C.  Either way the
 // pipeline loads each memory tile as two 32-column boxes, and only the first ksteps 16-column
 // K-steps hold data (the rest of the last chunk is padding, neither loaded nor multiplied).
-template <int NC, bool TILES = false>
+template <int NC, bool TILES = false, int S = kSl>
 __global__ void __launch_bounds__(kKiThreads, 1)
 sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
              const int* __restrict__ ea, const int* __restrict__ eb, double* __restrict__ part, int64_t per,
@@ -657,8 +750,8 @@ sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
             break;
           }
           asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&full[st])),
-                       "r"(kAStage + kBStage));
-          for (int q = 0; q < kSl; ++q) {
+                       "r"((uint32_t)S * (kAPlane + kBPlane)));
+          for (int q = 0; q < S; ++q) {
             asm volatile(
                 "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
                 ::"r"(smem_u32(sA + st * kAStage + q * kAPlane)), "l"(&tmA), "r"(x), "r"(arow), "r"(q),
@@ -705,7 +798,7 @@ sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
               }
               asm volatile("tcgen05.fence::after_thread_sync;");
             }
-            issue_kstep<NC>(tmem, smem_u32(sA + st * kAStage), smem_u32(sB + st * kBStage), kk, idesc, kp == 0);
+            issue_kstep<NC, S>(tmem, smem_u32(sA + st * kAStage), smem_u32(sB + st * kBStage), kk, idesc, kp == 0);
             ++kp;
             if (period_closes(it.c * (kKiChunk / 16) + 2 * kb + kk, ksteps, tail_cols,
                               tile_end && 2 * kb + kk + 1 == nks)) {
@@ -746,7 +839,7 @@ sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
-        add_groups<NC, W>(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(h * W), Sh, Sl);
+        add_groups<NC, W, S>(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(h * W), Sh, Sl);
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncwarp();
         if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tfree)) : "memory");
@@ -819,11 +912,24 @@ bool encode_planes(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap* tm, const
 void kinv_tc_prepare() {
   static PerDeviceOnce attr;
   attr([] {
-    cudaFuncSetAttribute(sk_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dig_smem(64));
-    cudaFuncSetAttribute(sk_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dig_smem(32));
-    cudaFuncSetAttribute(sk_tc_kernel<64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dig_smem(64));
+    const int s64 = (int)dig_smem(64), s32 = (int)dig_smem(32);
+    cudaFuncSetAttribute(sk_tc_kernel<64, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, s64);
+    cudaFuncSetAttribute(sk_tc_kernel<64, false, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, s64);
+    cudaFuncSetAttribute(sk_tc_kernel<64, false, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, s64);
+    cudaFuncSetAttribute(sk_tc_kernel<32, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, s32);
+    cudaFuncSetAttribute(sk_tc_kernel<32, false, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, s32);
+    cudaFuncSetAttribute(sk_tc_kernel<32, false, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, s32);
+    cudaFuncSetAttribute(sk_tc_kernel<64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s64);
   });
 }
+
+namespace {
+// The stream-K kernel for NC columns and nplanes digit planes (4, 5 or 6; 6 otherwise).
+template <int NC>
+decltype(&sk_tc_kernel<NC, false, 6>) sk_stream_kernel(int nplanes) {
+  return nplanes == 4 ? sk_tc_kernel<NC, false, 4> : (nplanes == 5 ? sk_tc_kernel<NC, false, 5> : sk_tc_kernel<NC, false, 6>);
+}
+}  // namespace
 
 int64_t kinv_tc_ld(int64_t n) { return (n + kKiChunk - 1) / kKiChunk * kKiChunk; }
 
@@ -903,7 +1009,7 @@ int kinv_reduce(const double* part, double* X, int64_t ldx, int64_t n, int64_t n
 
 cudaError_t rowmat_apply_tc(const void* planes, const int* ea, int64_t M, int64_t n, const double* D, int64_t B,
                             double* X, int64_t ldx, double* work, int* err, cudaStream_t s, int64_t* launches,
-                            int drop_stage) {
+                            int drop_stage, int nplanes) {
   work = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(work) + 255) & ~(uintptr_t)255);
   *launches = 0;
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
@@ -923,7 +1029,7 @@ cudaError_t rowmat_apply_tc(const void* planes, const int* ea, int64_t M, int64_
     const int64_t nb = B - q0 < kKiN ? B - q0 : kKiN;
     *launches += kinv_tc_slice(D + q0 * n, n, nb, n, eb, bpl, kKiN, s);
     // tiles: the 128-row tiles of the matrix (one problem); A rows kbg Mp + 128 t, B rows 64 kbg
-    sk_tc_kernel<64><<<(unsigned)p.ctas, kKiThreads, dig_smem(64), s>>>(
+    sk_stream_kernel<64>(nplanes)<<<(unsigned)p.ctas, kKiThreads, dig_smem(64), s>>>(
         tA, tB, ea, eb, part, p.per, p.total, p.kpt, p.span, (int)p.tiles, Mp, kKiRows, kKiN, 0, 0, kKiRows, 0, 0,
         (n + 15) / 16, tail_cols(n), 0, drop_stage, err, TileJob{});
     *launches += 1;
@@ -933,8 +1039,8 @@ cudaError_t rowmat_apply_tc(const void* planes, const int* ea, int64_t M, int64_
 }
 
 cudaError_t kinv_apply_tc(const void* planes, const int* ea, int64_t n, const double* D, int64_t B, double* X,
-                          double* work, int* err, cudaStream_t s, int64_t* launches, int drop_stage) {
-  return rowmat_apply_tc(planes, ea, n, n, D, B, X, n, work, err, s, launches, drop_stage);
+                          double* work, int* err, cudaStream_t s, int64_t* launches, int drop_stage, int nplanes) {
+  return rowmat_apply_tc(planes, ea, n, n, D, B, X, n, work, err, s, launches, drop_stage, nplanes);
 }
 
 int64_t kinv_tc_slice_t(const double* X, int64_t ldx, int64_t rows, int64_t cols, int* ex, void* planes,
@@ -1107,6 +1213,7 @@ __global__ void adj_vec_planes_kernel(const double2* __restrict__ dhat, int64_t 
   }
 }
 
+template <int S>
 __global__ void __launch_bounds__(kKiThreads, 1)
 adj_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const int* __restrict__ ea, const int* __restrict__ eb, double2* __restrict__ mhat, int nf,
@@ -1183,8 +1290,8 @@ adj_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
               break;
             }
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&full[st])),
-                         "r"(kAStage + kBStage));
-            for (int q = 0; q < kSl; ++q) {
+                         "r"((uint32_t)S * (kAPlane + kBPlane)));
+            for (int q = 0; q < S; ++q) {
               asm volatile(
                   "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
                   ::"r"(smem_u32(sA + st * kAStage + q * kAPlane)), "l"(&tmA), "r"(x), "r"(arow), "r"(q),
@@ -1228,7 +1335,7 @@ adj_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
               }
-              issue_kstep<kKiN>(tmem, smem_u32(sA + st * kAStage), smem_u32(sB + st * kBStage), kk, idesc, kp == 0);
+              issue_kstep<kKiN, S>(tmem, smem_u32(sA + st * kAStage), smem_u32(sB + st * kBStage), kk, idesc, kp == 0);
               ++kp;
               if (period_closes(c * (kKiChunk / 16) + 2 * kb + kk, ksteps, tail_cols,
                                 c == nchunk - 1 && 2 * kb + kk + 1 == nks)) {
@@ -1267,7 +1374,7 @@ adj_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
-        add_groups<kKiN, 32>(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(h * 32), Sh, Sl);
+        add_groups<kKiN, 32, S>(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(h * 32), Sh, Sl);
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncwarp();
         if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tfree)) : "memory");
@@ -1331,7 +1438,7 @@ size_t adj_digits_work_bytes(int64_t nf, int64_t R, int64_t B) {
 
 cudaError_t adj_digits_apply(const void* planes, const int* ea, int64_t nf, int64_t R, int64_t Nm, const void* dhat,
                              void* mhat, int64_t B, void* work, int* err, cudaStream_t s, int* launches,
-                             int drop_stage) {
+                             int drop_stage, int nplanes) {
   *launches = 0;
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return cudaErrorNotSupported;
@@ -1352,7 +1459,8 @@ cudaError_t adj_digits_apply(const void* planes, const int* ea, int64_t nf, int6
   const int64_t groups = std::max<int64_t>(1, num_sms_tc() / NG);
   const int64_t per = (total + groups - 1) / groups;
   const int64_t ctas = (total + per - 1) / per * NG;
-  adj_tc_kernel<<<(unsigned)ctas, kKiThreads, dig_smem(kKiN), s>>>(
+  auto kern = nplanes == 4 ? adj_tc_kernel<4> : (nplanes == 5 ? adj_tc_kernel<5> : adj_tc_kernel<6>);
+  kern<<<(unsigned)ctas, kKiThreads, dig_smem(kKiN), s>>>(
       tA, tB, ea, eb, static_cast<double2*>(mhat), (int)nf, Nm, Nmp, NBp, (int)B, (int)(Kp / kKiChunk), JT, NG, per,
       total, (int)((2 * R + 15) / 16), tail_cols(2 * R), drop_stage, err);
   *launches = 2;
@@ -1361,7 +1469,12 @@ cudaError_t adj_digits_apply(const void* planes, const int* ea, int64_t nf, int6
 
 void adj_digits_prepare() {
   static PerDeviceOnce attr;
-  attr([] { cudaFuncSetAttribute(adj_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dig_smem(kKiN)); });
+  attr([] {
+    const int sm = (int)dig_smem(kKiN);
+    cudaFuncSetAttribute(adj_tc_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(adj_tc_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(adj_tc_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  });
 }
 
 
@@ -1540,7 +1653,7 @@ size_t fwd_digits_work_bytes(int64_t nf, int64_t R, int64_t Nm) {
 
 cudaError_t fwd_digits_apply(const void* planes, const int* ex, int64_t nf, int64_t R, int64_t Nm, const void* mhat,
                              void* dhat, int64_t B, void* work, int* err, cudaStream_t s, int* launches,
-                             int drop_stage) {
+                             int drop_stage, int nplanes) {
   *launches = 0;
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return cudaErrorNotSupported;
@@ -1563,11 +1676,11 @@ cudaError_t fwd_digits_apply(const void* planes, const int* ex, int64_t nf, int6
     // tiles (w, rg): A rows (w KB + kb) 128, B rows (w KB + kb) R_pad + NC rg
     const int64_t ksteps = (2 * Nm + 15) / 16;
     if (p.NC == 32)
-      sk_tc_kernel<32><<<(unsigned)p.ctas, kKiThreads, dig_smem(32), s>>>(
+      sk_stream_kernel<32>(nplanes)<<<(unsigned)p.ctas, kKiThreads, dig_smem(32), s>>>(
           tA, tB, ev, ex, part, p.per, p.total, p.kpt, p.span, p.NRG, kKiRows, 0, p.Rp, p.NC, kKiRows, 0, (int)p.Rp,
           p.NC, ksteps, tail_cols(2 * Nm), p.NRG, drop_stage, err, TileJob{});
     else
-      sk_tc_kernel<64><<<(unsigned)p.ctas, kKiThreads, dig_smem(64), s>>>(
+      sk_stream_kernel<64>(nplanes)<<<(unsigned)p.ctas, kKiThreads, dig_smem(64), s>>>(
           tA, tB, ev, ex, part, p.per, p.total, p.kpt, p.span, p.NRG, kKiRows, 0, p.Rp, p.NC, kKiRows, 0, (int)p.Rp,
           p.NC, ksteps, tail_cols(2 * Nm), p.NRG, drop_stage, err, TileJob{});
     const int64_t tot = nb * nf * R;

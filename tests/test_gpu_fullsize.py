@@ -245,6 +245,18 @@ def test_batched_double_fp32_dense_without_refinement_full_size(batched):
         h.online(torch.from_numpy(o.d_obs).cuda(), m_map, q_map, refine_iters=0)
         torch.cuda.synchronize()
         q_Q = q_map.cpu().numpy()
+        # the FP32-level online form (bti_set_online_precision): five digit planes for K^{-1},
+        # four for G^* and Q; 64 vectors, and one (which takes the FP64-level kernels)
+        h.set_online_precision(bti.F32)
+        h.online(torch.from_numpy(o.d_obs).cuda(), m_map, q_map, refine_iters=0)
+        torch.cuda.synchronize()
+        m_32, q_32 = m_map.cpu().numpy(), q_map.cpu().numpy()
+        m_1 = torch.empty((1, p.Nt, p.Nm), dtype=torch.float64, device="cuda")
+        q_1 = torch.empty((1, p.Nt, p.Nq), dtype=torch.float64, device="cuda")
+        h.online(torch.from_numpy(o.d_obs[5:6].copy()).cuda(), m_1, q_1, refine_iters=0)
+        torch.cuda.synchronize()
+        m_32_1, q_32_1 = m_1.cpu().numpy(), q_1.cpu().numpy()
+        h.set_online_precision(bti.DF64)
     h.set_stream(torch.cuda.current_stream())
     h.close()
     kinfo = f"kappa(K) = {o.kappa:.0f}, rho = {o.rho:.1f}"
@@ -257,6 +269,11 @@ def test_batched_double_fp32_dense_without_refinement_full_size(batched):
     check(relb(q_inv, o.q), tol, "q_map, explicit inverse " + kinfo)
     check(relb(m1, o.m[5:6]), tol, "m_map, explicit inverse, one vector " + kinfo)
     check(relb(q_Q, o.q), tol, "q_map = Q d_obs, Q from the explicit inverse " + kinfo)
+    # the FP32-level form, against the online latency metric's 1e-6
+    check(relb(m_32, o.m), 1e-6, "m_map, FP32-level online form " + kinfo)
+    check(relb(q_32, o.q), 1e-6, "q_map, FP32-level online form " + kinfo)
+    check(relb(m_32_1, o.m[5:6]), 1e-6, "m_map, FP32-level online form, one vector " + kinfo)
+    check(relb(q_32_1, o.q[5:6]), 1e-6, "q_map, FP32-level online form, one vector " + kinfo)
     tol = parity.tol_solve(o.kappa, parity.U_DIGITS)
     check(relb(m_ref, o.m), tol, "m_map, inverse + one refinement step " + kinfo)
     check(relb(q_ref, o.q), tol, "q_map, inverse + one refinement step " + kinfo)

@@ -716,6 +716,61 @@ def test_online_qoi_via_d2q_map_on_tensor_cores(B):
     h.close()
 
 
+ONLINE_LATENCY_TOL = 1e-6  # the online latency metric's relative error
+
+
+@pytest.mark.parametrize("via_Q", [True, False], ids=["via_Q", "push_forward"])
+def test_online_fp32_level_form(via_Q):
+    """bti_set_online_precision(BTI_P_F32): the online graph with its digit-plane products cut
+    to their most significant planes (five for K^{-1}, four for G^*, F_q and Q).  B = 20
+    vectors on the tensor cores; m_map and q_map against the oracle within the online latency
+    metric's 1e-6; the truncation takes effect (the result differs from the FP64-level form's);
+    refinement is refused; switching back restores the FP64-level graph."""
+    p, F, Fq, G, _ = tiny_problem()
+    B = 20
+    d = p.vectors_d(B)
+    m_or = oracle.map_point(F, G, p.sigma2, d)
+    q_or = oracle.qoi_map(Fq, m_or)
+    h = make_handle(F, Fq, bti.DF64)
+    h.set_prior_se_grid(p.gx, p.gy, p.ell, p.sigma_p, bti.DF64)
+    h.set_noise(p.sigma2)
+    h.set_dense_precision(bti.DF64)
+    h.build_K()
+    h.factor_K()
+    h.invert_K()
+    h.set_digit_planes(bti.OP_G, True)
+    h.set_digit_planes(bti.OP_FQ, True)
+    if via_Q:
+        h.build_Q()
+        h.set_online_qoi(True)
+    with pytest.raises(bti.BtiError) as e:
+        h.set_online_precision(bti.F16)
+    assert e.value.status == 1
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        h.set_stream(stream)
+        m = torch.empty((B, p.Nt, p.Nm), dtype=torch.float64, device="cuda")
+        q = torch.empty((B, p.Nt, p.Nq), dtype=torch.float64, device="cuda")
+        h.online(cuda(d), m, q)
+        m64, q64 = host(m), host(q)
+        h.set_online_precision(bti.F32)
+        with pytest.raises(bti.BtiError) as e:
+            h.online(cuda(d), m, q, refine_iters=1)
+        assert e.value.status == 1
+        h.online(cuda(d), m, q)
+        m32, q32 = host(m), host(q)
+        h.set_online_precision(bti.DF64)
+        h.online(cuda(d), m, q)
+        m64b = host(m)
+    torch.cuda.synchronize()
+    h.set_stream(torch.cuda.current_stream())
+    h.close()
+    check(relb(m32, m_or), ONLINE_LATENCY_TOL, "m_map, FP32-level online form")
+    check(relb(q32, q_or), ONLINE_LATENCY_TOL, "q_map, FP32-level online form")
+    assert relb(m32, m64) > 1e-12  # the truncated planes took effect
+    assert np.array_equal(m64b, m64)  # the FP64-level graph is back, bit for bit
+
+
 def test_replacing_blocks_drops_what_was_derived_from_them():
     """bti_set_blocks on an operator that is already set must take effect everywhere:
     - the old blocks' digit planes go, so B >= 16 products use the new blocks;
