@@ -20,6 +20,7 @@
 #include "bti_internal.cuh"
 
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 namespace bti {
@@ -260,70 +261,129 @@ __device__ __forceinline__ void butterfly8_half_zero(const C2<T>* src, int i0, i
   dst[sp(o0 + 7)] = csub<T>(e3, o3);
 }
 
+// The radix sequence of a length L in fft_plan_make's order (8, 4, 2, 7, 5, 3), at compile time
+// for the kernels specialised on L.
+__host__ __device__ constexpr int ct_radix(int L, int i) {
+  const int order[6] = {8, 4, 2, 7, 5, 3};
+  int n = L, k = 0;
+  for (int oi = 0; oi < 6; ++oi)
+    while (n % order[oi] == 0) {
+      if (k == i) return order[oi];
+      n /= order[oi];
+      ++k;
+    }
+  return 1;
+}
+__host__ __device__ constexpr int ct_npass(int L) {
+  int k = 0;
+  while (ct_radix(L, k) != 1) ++k;
+  return k;
+}
+
 // Radix sets compiled into a kernel: fewer butterflies compiled in means fewer registers,
 // and the restricted sets fit 3 CTAs per SM instead of 2.
 enum { kRadixAll = 0, kRadixPow2 = 1, kRadix25 = 2 };  // (8, 4, 2, 7, 5, 3); (8, 4, 2); (8, 4, 2, 5)
 
+// One Stockham pass of radix r over the CTA's P transforms (src -> dst, padded slots).
+template <typename T, bool INV, int RS>
+__device__ __forceinline__ void one_pass(const C2<T>* src, C2<T>* dst, const C2<T>* __restrict__ tw, int r, int L,
+                                         int Ns, int P, int LP) {
+  const int Lr = L / r;
+  const int nbf = P * Lr;
+  for (int bi = threadIdx.x; bi < nbf; bi += blockDim.x) {
+    int p = bi / Lr;
+    int j = bi - p * Lr;
+    int k = j % Ns;
+    const C2<T>* s = src + p * LP;
+    C2<T>* d = dst + p * LP;
+    const int o0 = (j - k) * r + k;
+    int twstep = k * (L / (Ns * r));
+    if (RS == kRadixPow2) {
+      if (r == 8) butterfly<8, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L);
+      else if (r == 4) butterfly<4, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L);
+      else butterfly<2, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L);
+    } else if (RS == kRadix25) {
+      if (r == 8) butterfly<8, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L);
+      else if (r == 4) butterfly<4, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L);
+      else if (r == 2) butterfly<2, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L);
+      else butterfly<5, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L);
+    } else {
+      switch (r) {
+        case 8: butterfly<8, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L); break;
+        case 4: butterfly<4, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L); break;
+        case 2: butterfly<2, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L); break;
+        case 7: butterfly<7, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L); break;
+        case 5: butterfly<5, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L); break;
+        default: butterfly<3, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L); break;
+      }
+    }
+  }
+}
+
+// The first radix-8 pass of a forward transform whose second half is zero padding.
+template <typename T>
+__device__ __forceinline__ void first_pass_half_zero(const C2<T>* src, C2<T>* dst, int L, int P, int LP) {
+  const int Lr = L / 8;
+  const int nbf = P * Lr;
+  for (int bi = threadIdx.x; bi < nbf; bi += blockDim.x) {
+    int p = bi / Lr, j = bi - p * Lr;
+    butterfly8_half_zero<T>(src + p * LP, j, Lr, dst + p * LP, j * 8);
+  }
+}
+
 // All passes; data starts in buf0, result pointer returned (buf0 or buf1); transform p
 // of the CTA occupies LP slots from p LP.  With half_zero, the first pass is radix 8 and
-// only the first half of each input is nonzero.  RS selects the compiled radix set.
-template <typename T, bool INV, int RS>
+// only the first half of each input is nonzero.  RS selects the compiled radix set.  CL > 0:
+// the length is CL at compile time (D.L must equal it): the radix sequence, every index
+// divisor and twiddle stride are constants and the pass loop is unrolled; for a forward
+// transform half_zero must then hold (L = 2 N_t).
+template <typename T, bool INV, int RS, int CL = 0>
 __device__ C2<T>* run_passes(const FftDesc& D, C2<T>* buf0, C2<T>* buf1, const C2<T>* __restrict__ tw,
                              int LP, bool half_zero = false) {
   C2<T>* src = buf0;
   C2<T>* dst = buf1;
-  const int L = D.L;
-  int Ns = 1;
-  if (!INV && half_zero && D.npass > 0 && D.radix[0] == 8) {
-    const int Lr = L / 8;
-    const int nbf = D.P * Lr;
-    for (int bi = threadIdx.x; bi < nbf; bi += blockDim.x) {
-      int p = bi / Lr, j = bi - p * Lr;
-      butterfly8_half_zero<T>(src + p * LP, j, Lr, dst + p * LP, j * 8);
+  if constexpr (CL > 0) {
+    constexpr bool hz = !INV && ct_radix(CL, 0) == 8;  // the zero-padded first pass (forward)
+    if constexpr (hz) {
+      first_pass_half_zero<T>(src, dst, CL, D.P, LP);
+      __syncthreads();
+      C2<T>* tmp = src;
+      src = dst;
+      dst = tmp;
     }
-    __syncthreads();
-    C2<T>* tmp = src;
-    src = dst;
-    dst = tmp;
-    Ns = 8;
-  }
-  for (int ps = (Ns == 8 ? 1 : 0); ps < D.npass; ++ps) {
-    const int r = D.radix[ps];
-    const int Lr = L / r;
-    const int nbf = D.P * Lr;
-    for (int bi = threadIdx.x; bi < nbf; bi += blockDim.x) {
-      int p = bi / Lr;
-      int j = bi - p * Lr;
-      int k = j % Ns;
-      const C2<T>* s = src + p * LP;
-      C2<T>* d = dst + p * LP;
-      const int o0 = (j - k) * r + k;
-      int twstep = k * (L / (Ns * r));
-      if (RS == kRadixPow2) {
-        if (r == 8) butterfly<8, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L);
-        else if (r == 4) butterfly<4, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L);
-        else butterfly<2, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L);
-      } else if (RS == kRadix25) {
-        if (r == 8) butterfly<8, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L);
-        else if (r == 4) butterfly<4, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L);
-        else if (r == 2) butterfly<2, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L);
-        else butterfly<5, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L);
-      } else {
-        switch (r) {
-          case 8: butterfly<8, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L); break;
-          case 4: butterfly<4, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L); break;
-          case 2: butterfly<2, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L); break;
-          case 7: butterfly<7, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L); break;
-          case 5: butterfly<5, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L); break;
-          default: butterfly<3, T, INV>(s, j, Lr, d, o0, Ns, tw, twstep, L); break;
-        }
-      }
+    int Ns = hz ? 8 : 1;
+#pragma unroll
+    for (int ps = hz ? 1 : 0; ps < ct_npass(CL); ++ps) {
+      const int r = ct_radix(CL, ps);
+      one_pass<T, INV, RS>(src, dst, tw, r, CL, Ns, D.P, LP);
+      __syncthreads();
+      C2<T>* tmp = src;
+      src = dst;
+      dst = tmp;
+      Ns *= r;
     }
-    __syncthreads();
-    C2<T>* tmp = src;
-    src = dst;
-    dst = tmp;
-    Ns *= r;
+  } else {
+    const int L = D.L;
+    int Ns = 1;
+    int ps0 = 0;
+    if (!INV && half_zero && D.npass > 0 && D.radix[0] == 8) {
+      first_pass_half_zero<T>(src, dst, L, D.P, LP);
+      __syncthreads();
+      C2<T>* tmp = src;
+      src = dst;
+      dst = tmp;
+      Ns = 8;
+      ps0 = 1;
+    }
+    for (int ps = ps0; ps < D.npass; ++ps) {
+      const int r = D.radix[ps];
+      one_pass<T, INV, RS>(src, dst, tw, r, L, Ns, D.P, LP);
+      __syncthreads();
+      C2<T>* tmp = src;
+      src = dst;
+      dst = tmp;
+      Ns *= r;
+    }
   }
   return src;
 }
@@ -333,12 +393,12 @@ template <typename TO, typename T> __device__ __forceinline__ C2<TO> cvt2(C2<T> 
 }
 template <typename T> __device__ __forceinline__ C2<T> czero() { return mk<T>((T)0, (T)0); }
 
-template <typename T, typename TI, typename TO, int RS>
+template <typename T, typename TI, typename TO, int RS, int CL = 0>
 __global__ void __launch_bounds__(256, RS == kRadixAll ? 2 : 3)  // restricted radix sets fit 3 CTAs per SM
 rfft_cols_kernel(FftDesc D, int Nt, const TI* __restrict__ x, int64_t ld, int64_t xbs,
                  C2<TO>* __restrict__ X, int64_t Xbs, int64_t ncols, TwTabs tabs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int L = D.L, P = D.P, W2 = 2 * P, LP = fft_slots(L);
+  const int L = CL ? CL : D.L, P = D.P, W2 = 2 * P, LP = fft_slots(L);
   C2<T>* buf0 = reinterpret_cast<C2<T>*>(smem_raw);
   C2<T>* buf1 = buf0 + P * LP;
   const C2<T>* tw = twtab<T>(tabs);
@@ -373,7 +433,7 @@ rfft_cols_kernel(FftDesc D, int Nt, const TI* __restrict__ x, int64_t ld, int64_
     buf0[p * LP + sp(t)] = czero<T>();
   }
   __syncthreads();
-  C2<T>* Z = run_passes<T, false, RS>(D, buf0, buf1, tw, LP, 2 * Nt == L);
+  C2<T>* Z = run_passes<T, false, RS, CL>(D, buf0, buf1, tw, LP, 2 * Nt == L);
   // unpack the two real spectra of each pair and store bins 0..N_t
   const int nf = Nt + 1;
   for (int idx = threadIdx.x; idx < nf * W2; idx += blockDim.x) {
@@ -394,12 +454,12 @@ rfft_cols_kernel(FftDesc D, int Nt, const TI* __restrict__ x, int64_t ld, int64_
   }
 }
 
-template <typename T, typename TYI, typename TO, int RS>
+template <typename T, typename TYI, typename TO, int RS, int CL = 0>
 __global__ void __launch_bounds__(256, RS == kRadixAll ? 2 : 3)
 irfft_cols_kernel(FftDesc D, int Nt, const C2<TYI>* __restrict__ Y, int64_t ld, int64_t Ybs,
                   TO* __restrict__ y, int64_t ybs, int64_t ncols, double scale_d, TwTabs tabs, int ostride) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int L = D.L, P = D.P, W2 = 2 * P, LP = fft_slots(L);
+  const int L = CL ? CL : D.L, P = D.P, W2 = 2 * P, LP = fft_slots(L);
   C2<T>* buf0 = reinterpret_cast<C2<T>*>(smem_raw);
   C2<T>* buf1 = buf0 + P * LP;
   const C2<T>* tw = twtab<T>(tabs);
@@ -426,7 +486,7 @@ irfft_cols_kernel(FftDesc D, int Nt, const C2<TYI>* __restrict__ Y, int64_t ld, 
     }
   }
   __syncthreads();
-  C2<T>* Z = run_passes<T, true, RS>(D, buf0, buf1, tw, LP);
+  C2<T>* Z = run_passes<T, true, RS, CL>(D, buf0, buf1, tw, LP);
   // rows t = ostride (k + 1) - 1 only (every row when ostride == 1), stored as row k
   const int nout = Nt / ostride;
   for (int idx = threadIdx.x; idx < nout * W2; idx += blockDim.x) {
@@ -478,12 +538,37 @@ void launch_rfft_cols(const FftPlan& p, int Nt, const TI* x, int64_t ld, int64_t
                          200 * 1024);
   });
   const int rs = radix_set(p);
+  // the float-pair lengths of the headline sweep (512) and the batched workload (400) run
+  // kernels compiled for their length (L = 2 N_t, so the first pass is the zero-padded one)
+  constexpr bool ff = std::is_same<T, ffloat>::value;
+  const int cl = (ff && 2 * Nt == p.L && (p.L == 400 || p.L == 512)) ? p.L : 0;
+  if constexpr (ff) {
+    static PerDeviceOnce attr_cl;
+    attr_cl([] {
+      cudaFuncSetAttribute(rfft_cols_kernel<T, TI, TO, kRadix25, 400>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           200 * 1024);
+      cudaFuncSetAttribute(rfft_cols_kernel<T, TI, TO, kRadixPow2, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           200 * 1024);
+    });
+  }
   int64_t gx = (ncols + 2 * p.P - 1) / (2 * p.P);
   for (int64_t b0 = 0; b0 < B; b0 += 65535) {
     int64_t nb = B - b0 < 65535 ? B - b0 : 65535;
     dim3 grid((unsigned)gx, (unsigned)nb);
     const TI* xb = x + b0 * x_bstride;
     C2<TO>* Xb = X + b0 * X_bstride;
+    if constexpr (ff) {
+      if (cl == 400) {
+        rfft_cols_kernel<T, TI, TO, kRadix25, 400><<<grid, 256, smem, s>>>(D, Nt, xb, ld, x_bstride, Xb, X_bstride,
+                                                                           ncols, tabs_of(p));
+        continue;
+      }
+      if (cl == 512) {
+        rfft_cols_kernel<T, TI, TO, kRadixPow2, 512><<<grid, 256, smem, s>>>(D, Nt, xb, ld, x_bstride, Xb,
+                                                                             X_bstride, ncols, tabs_of(p));
+        continue;
+      }
+    }
     if (rs == kRadixPow2)
       rfft_cols_kernel<T, TI, TO, kRadixPow2><<<grid, 256, smem, s>>>(D, Nt, xb, ld, x_bstride, Xb, X_bstride, ncols,
                                                                       tabs_of(p));
@@ -514,12 +599,37 @@ void launch_irfft_cols(const FftPlan& p, int Nt, const C2<TYI>* X, int64_t ld, i
   });
   const int rs = radix_set(p);
   const int os = ostride < 1 ? 1 : ostride;
+  // compile-time lengths, as in launch_rfft_cols
+  constexpr bool ff = std::is_same<T, ffloat>::value;
+  const int cl = (ff && (p.L == 400 || p.L == 512)) ? p.L : 0;
+  if constexpr (ff) {
+    static PerDeviceOnce attr_cl;
+    attr_cl([] {
+      cudaFuncSetAttribute(irfft_cols_kernel<T, TYI, TO, kRadix25, 400>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      cudaFuncSetAttribute(irfft_cols_kernel<T, TYI, TO, kRadixPow2, 512>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    });
+  }
   int64_t gx = (ncols + 2 * p.P - 1) / (2 * p.P);
   for (int64_t b0 = 0; b0 < B; b0 += 65535) {
     int64_t nb = B - b0 < 65535 ? B - b0 : 65535;
     dim3 grid((unsigned)gx, (unsigned)nb);
     const C2<TYI>* Xb = X + b0 * X_bstride;
     TO* yb = y + b0 * y_bstride;
+    if constexpr (ff) {
+      if (cl == 400) {
+        irfft_cols_kernel<T, TYI, TO, kRadix25, 400><<<grid, 256, smem, s>>>(D, Nt, Xb, ld, X_bstride, yb,
+                                                                              y_bstride, ncols, scale, tabs_of(p), os);
+        continue;
+      }
+      if (cl == 512) {
+        irfft_cols_kernel<T, TYI, TO, kRadixPow2, 512><<<grid, 256, smem, s>>>(D, Nt, Xb, ld, X_bstride, yb,
+                                                                                y_bstride, ncols, scale, tabs_of(p),
+                                                                                os);
+        continue;
+      }
+    }
     if (rs == kRadixPow2)
       irfft_cols_kernel<T, TYI, TO, kRadixPow2><<<grid, 256, smem, s>>>(D, Nt, Xb, ld, X_bstride, yb, y_bstride,
                                                                         ncols, scale, tabs_of(p), os);

@@ -134,6 +134,7 @@ CASES = [
     ("L128_b6", 1024, 8, 4, 64, 6),
     ("L420", 700, 6, 3, 210, 2),
     ("L400_batched_shape", 4096, 100, 32, 200, 1),
+    ("L512_sweep_shape_ragged", 2051, 9, 3, 256, 2),  # the headline sweep's length, ragged column pairs
     ("L840_odd", 333, 7, 2, 420, 1),
     ("Nt1_gemv", 257, 5, 3, 1, 2),
     ("scalar", 1, 1, 1, 16, 2),
