@@ -476,8 +476,9 @@ void launch_prod_fwd_df64(const float4* Fhat, const double2* mhat, double2* part
     prod_fwd_df64_kernel<1, 8><<<grid, 256, smem, s>>>(Fhat, mhat, partial, nf, R, Nm, B, JC, nchunk);
 }
 
-// Adjoint product, double-FP32 arithmetic; thread owns j = j0 + tid + 256 v.
-template <int BG, int VPT>
+// Adjoint product, double-FP32 arithmetic; thread owns j = j0 + tid + 256 v.  AHEAD: each thread
+// loads F-hat's next row while it uses the current one (two rows in flight instead of one).
+template <int BG, int VPT, bool AHEAD = (BG >= 4)>
 __global__ void __launch_bounds__(256)
 prod_adj_df64_kernel(const float4* __restrict__ Fhat, const double2* __restrict__ dhat,
                      double2* __restrict__ mhat, int64_t nf, int64_t R, int64_t Nm, int64_t B) {
@@ -508,9 +509,9 @@ prod_adj_df64_kernel(const float4* __restrict__ Fhat, const double2* __restrict_
       sd[bb * RS + (i - i0)] = v;
     }
     __syncthreads();
-    // F-hat row ii of the tile; with several vectors per CTA the next row is loaded
-    // while this one is used (single vectors are HBM-bound and keep one row in flight)
-    constexpr bool kAhead = BG >= 4;
+    // F-hat row ii of the tile; with several vectors per CTA, or a grid too small to keep HBM
+    // busy with one row in flight per thread, the next row is loaded while this one is used
+    constexpr bool kAhead = AHEAD;
     float4 f[VPT], fn[VPT];
 #pragma unroll
     for (int v = 0; v < VPT; ++v) {
@@ -561,17 +562,17 @@ prod_adj_df64_kernel(const float4* __restrict__ Fhat, const double2* __restrict_
   }
 }
 
-template <int BG, int VPT>
+template <int BG, int VPT, bool AHEAD = (BG >= 4)>
 static void adj_df64_launch(const float4* Fhat, const double2* dhat, double2* mhat, int64_t nf, int64_t R,
                             int64_t Nm, int64_t B, cudaStream_t s) {
   size_t smem = sizeof(float4) * (size_t)BG * (R < kAdjRows ? R : kAdjRows);
   static PerDeviceOnce attr;  // 8 vectors x 512 staged rows take 64 KB
   attr([] {
-    cudaFuncSetAttribute(prod_adj_df64_kernel<BG, VPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(prod_adj_df64_kernel<BG, VPT, AHEAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(sizeof(float4) * BG * kAdjRows));
   });
   dim3 grid((unsigned)((Nm + 256 * VPT - 1) / (256 * VPT)), (unsigned)nf, (unsigned)((B + BG - 1) / BG));
-  prod_adj_df64_kernel<BG, VPT><<<grid, 256, smem, s>>>(Fhat, dhat, mhat, nf, R, Nm, B);
+  prod_adj_df64_kernel<BG, VPT, AHEAD><<<grid, 256, smem, s>>>(Fhat, dhat, mhat, nf, R, Nm, B);
 }
 
 void launch_prod_adj_df64(const float4* Fhat, const double2* dhat, double2* mhat, int64_t nf, int64_t R,
@@ -580,6 +581,9 @@ void launch_prod_adj_df64(const float4* Fhat, const double2* dhat, double2* mhat
     adj_df64_launch<8, 1>(Fhat, dhat, mhat, nf, R, Nm, B, s);
   else if (B >= 4)
     adj_df64_launch<4, 2>(Fhat, dhat, mhat, nf, R, Nm, B, s);
+  else if (nf * ((Nm + 1023) / 1024) < 4096)
+    // few CTAs (a short spatial axis, as the batched workload's 4,096 columns): two rows in flight
+    adj_df64_launch<1, 4, true>(Fhat, dhat, mhat, nf, R, Nm, B, s);
   else if (vpt == 2)
     adj_df64_launch<1, 2>(Fhat, dhat, mhat, nf, R, Nm, B, s);
   else if (vpt == 8)
