@@ -122,10 +122,43 @@ def load_peaks():
 
 
 # FP64 FFMA-pipe rate of this GB300 (TFLOP/s), from a DFMA throughput probe:
-# 2 DFMA per clock per SM x 152 SMs at the sustained clock.
+# 2 DFMA per clock per SM x 152 SMs at the sustained clock.  Used only when the live
+# measurement below fails.
 FP64_TFLOPS = 1.2
 # FP32 FFMA rate (TFLOP/s) from the same probe: 128 lanes/clk/SM x 152 SMs x 2 flop.
 FP32_TFLOPS = 75.0
+
+
+def measure_alu_peaks(dev):
+    """FP64 and FP32 (no TF32) GEMM throughput of the library GEMM on this GPU, best of 3
+    timed runs after one warm-up, with CUDA events: the denominators of the arithmetic-bound
+    tiers' rooflines, measured in the same run.  {"fp64_tflops", "fp32_tflops", "how"} or
+    None when the measurement fails (the probe constants then serve, and the JSON says so)."""
+    import torch
+    try:
+        tf32 = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = False
+        out = {}
+        for key, dt, n in (("fp64_tflops", torch.float64, 6144), ("fp32_tflops", torch.float32, 8192)):
+            a = torch.randn((n, n), dtype=dt, device=dev)
+            b = torch.randn((n, n), dtype=dt, device=dev)
+            torch.matmul(a, b)
+            torch.cuda.synchronize()
+            best = float("inf")
+            for _ in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b)
+                e1.record()
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            out[key] = 2.0 * n ** 3 / (best * 1e-3) / 1e12
+            del a, b
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        out["how"] = "torch.matmul FP64 6144^3 and FP32 (TF32 off) 8192^3, best of 3, CUDA events, this run"
+        return out
+    except Exception:
+        return None
 
 
 class Clocks:
@@ -390,6 +423,11 @@ def run_ours(args):
     props = torch.cuda.get_device_properties(dev)
     uuid = str(getattr(props, "uuid", ""))
 
+    alu = measure_alu_peaks(dev) if rank == 0 else None
+    fp64_peak = alu["fp64_tflops"] if alu else FP64_TFLOPS
+    fp32_peak = alu["fp32_tflops"] if alu else FP32_TFLOPS
+    alu_src = f"measured: {alu['how']}" if alu else "probe constant (the live measurement failed)"
+
     # dominant kernel: the per-frequency spectral products (forward and adjoint)
     def roofline(prof, csize, kind):
         (pf_ms, pf_n), (pa_ms, pa_n) = prof[0]["prod_fwd"], prof[0]["prod_adj"]
@@ -406,14 +444,13 @@ def run_ours(args):
         # arithmetic: f64 = 8 DP flop per element on the FP64 pipe; f32 = 4 FFMA; df64 = 48 FP32
         # instructions per element (4 float-pair multiply-accumulates of 12 operations)
         if kind == "f64":
-            work, peak, unit, src = 8.0 * elems, FP64_TFLOPS * 1e12, "TFLOP/s", \
-                "FP64 DFMA throughput probe (2 DFMA/clk/SM x 152 SMs)"
+            work, peak, unit, src = 8.0 * elems, fp64_peak * 1e12, "TFLOP/s", "FP64 GEMM rate, " + alu_src
         elif kind in ("f32", "f16"):
-            work, peak, unit, src = 8.0 * elems, FP32_TFLOPS * 1e12, "TFLOP/s", \
-                "FP32 FFMA: 128 lanes/clk/SM x 152 SMs x 2 flop at ~1.93 GHz (probe: 75 TFLOP/s)"
+            work, peak, unit, src = 8.0 * elems, fp32_peak * 1e12, "TFLOP/s", "FP32 GEMM rate, " + alu_src
         else:
-            work, peak, unit, src = 48.0 * elems, FP32_TFLOPS / 2 * 1e12, "Tinstr/s", \
-                "FP32 pipe issue: 128 lanes/clk/SM x 152 SMs at ~1.93 GHz (probe)"
+            # FP32 instructions: half the FP32 GEMM's flop rate (one FFMA = 2 flop)
+            work, peak, unit, src = 48.0 * elems, fp32_peak / 2 * 1e12, "Tinstr/s", \
+                "FP32 instruction rate = FP32 GEMM rate / 2, " + alu_src
         t_alu = work / peak
         traffic = ncu_traffic(f"{kind}_bytes_per_launch")
         share_total = sum(v[0] for v in prof[0].values())
@@ -493,6 +530,8 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clk,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in head["prof"][0].items()},
+        "alu_peaks": alu if alu else {"fp64_tflops": FP64_TFLOPS, "fp32_tflops": FP32_TFLOPS,
+                                      "how": "probe constants (the live measurement failed)"},
     }
     bpc64 = bytes_per_call(p, 8, 16)
 
