@@ -16,7 +16,9 @@ and rely on three facts that this file checks in plain numpy, independent of the
    the exact value up to the dropped bits of lo.
 
 Together they bound the product's error by the 47-bit truncation, which the GPU parity
-tests then confirm against the oracle (1e-12 and below)."""
+tests then confirm against the oracle (1e-12 and below).  The last tests restate the index
+arithmetic the kernels share: the forward product's side-by-side work split against its
+reduction, and the accumulation periods against the exact bound."""
 
 import numpy as np
 
@@ -222,3 +224,78 @@ def test_adjoint_digit_product_with_per_column_and_per_vector_scales():
     ref = d @ F.conj()
     got = D[:, 0::2].T + 1j * D[:, 1::2].T
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-12
+
+
+# ---------------------------------------------------------------- work split of the products
+# Python restatements of the index arithmetic the tensor-core products share between their
+# kernels (tc_digits.cu): which CTA takes which (frequency, row group, chunk) unit, where it
+# writes each partial tile, and where the fixed-order reduction looks for them; and the
+# accumulation periods both the MMA warp and the epilogue derive.
+
+def _fwd_side_by_side(nf, NRG, kpt, slots=152):
+    """The forward product's plan: units (w, chunk), each taken by NRG CTAs side by side."""
+    total = nf * kpt
+    groups = max(1, slots // NRG)
+    per = -(-total // groups)
+    ctas = -(-total // per) * NRG
+    span = (per + kpt - 1) // kpt + 1
+    return total, per, ctas, span
+
+
+def test_forward_side_by_side_split_covers_every_unit_once_and_the_reduction_finds_it():
+    import itertools
+    for nf, NRG, kpt in itertools.product([1, 5, 51, 201, 211], [1, 2, 3, 10, 18], [1, 7, 64, 256]):
+        total, per, ctas, span = _fwd_side_by_side(nf, NRG, kpt)
+        written, cover = {}, {}
+        for b in range(ctas):  # the kernel: CTA b takes row group b % NRG of units [(b / NRG) per, + per)
+            rg, q = b % NRG, b // NRG
+            u0, u1 = q * per, min(total, (q + 1) * per)
+            first = (q * per) // kpt
+            for u in range(u0, u1):
+                wt, c = divmod(u, kpt)
+                cover[(wt, rg, c)] = cover.get((wt, rg, c), 0) + 1
+                if u + 1 == u1 or (u + 1) // kpt != wt:  # the tile's last chunk in this CTA's share
+                    slot = wt - first
+                    assert 0 <= slot < span
+                    assert (b, slot) not in written
+                    written[(b, slot)] = (wt, rg)
+        assert len(cover) == nf * NRG * kpt and set(cover.values()) == {1}
+        found = set()
+        for w in range(nf):  # fwd_reduce_kernel: the CTA groups whose runs cover frequency w
+            for rg in range(NRG):
+                for q in range(w * kpt // per, ((w + 1) * kpt - 1) // per + 1):
+                    key = (q * NRG + rg, w - (q * per) // kpt)
+                    assert written.get(key) == (w, rg)
+                    found.add(key)
+        assert found == set(written)
+
+
+def _period_closes(k, ksteps, tail_cols, share_last, drain_k=12, period_cols=204):
+    if share_last:
+        return True
+    if (k + 1) % drain_k != 0:
+        return False
+    return not (k + 2 == ksteps and drain_k * 16 + tail_cols <= period_cols)
+
+
+def test_accumulation_periods_stay_within_the_exact_bound():
+    """Every period the schedule forms holds at most 204 data columns (so groups 0-4 sum exactly
+    in FP32), for K axes split into CTA shares at any K-step, and the batched adjoint's
+    2R = 200 drains once per unit."""
+    import random
+    rnd = random.Random(7)
+    for K in list(range(1, 700)) + [8192, 20000]:
+        ksteps = (K + 15) // 16
+        tail = K - 16 * (ksteps - 1)
+        cuts = sorted({0, ksteps} | {rnd.randrange(ksteps + 1) for _ in range(3)})
+        for a, b in zip(cuts, cuts[1:]):  # one CTA share: K-steps [a, b)
+            if a == b:
+                continue
+            start = a
+            for k in range(a, b):
+                if _period_closes(k, ksteps, tail, k + 1 == b):
+                    cols = sum(16 if j < ksteps - 1 else tail for j in range(start, k + 1))
+                    assert cols <= 204, (K, a, b, start, k)
+                    start = k + 1
+            assert start == b  # the share's last K-step closed its period
+    assert sum(_period_closes(k, 13, 8, k == 12) for k in range(13)) == 1
