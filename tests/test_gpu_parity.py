@@ -1143,7 +1143,7 @@ def test_elliptic_prior_full_inversion(store):
 @pytest.mark.parametrize("B", [1, 5, 20, 70], ids=["b1", "b5", "b20", "b70"])
 def test_explicit_inverse_online_solve(B):
     """bti_invert_K: x = K^{-1} d as one product with the explicit inverse, on the tensor
-    cores (six FP16 digit planes, exact per 128-column chunk) and, with tensor cores off,
+    cores (six FP16 digit planes, exact per accumulation period) and, with tensor cores off,
     in double-FP32 on the CUDA cores (4-, 16- and 64-wide right-hand-side tiles); stream-K
     partials summed in CTA order; a second 64-chunk at B = 70.  m_map matches the oracle,
     refinement brings it to the FP64 tolerance, a new factorisation returns to the
