@@ -45,14 +45,17 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-workload matrix-free solve block")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--case", choices=["sweep", "small", "digits_small", "factor_small"], default="sweep",
+    ap.add_argument("--case", choices=["sweep", "small", "digits_small", "factor_small", "online_batched"],
+                    default="sweep",
                     help="small: the sweep shape with N_m = 4096 and 16 vectors (2.2 GB of FP64 spectral "
                          "blocks, still far above L2) for ncu captures; implies --no-online, "
                          "--no-mixed, --no-cpu-baseline and --no-e2e.  digits_small: the batched "
                          "workload's shapes at N_t = 50 with 64 vectors, timing the tensor-core digit-plane "
                          "products (adjoint, forward, explicit inverse) once each, for ncu captures.  "
                          "factor_small: K of 8,192^2 factored by recursive halves and inverted on the tensor "
-                         "cores once each, for ncu captures")
+                         "cores once each, for ncu captures.  online_batched: the batched workload's tensor-core "
+                         "offline phase, then its online graph (64 vectors: FP64-level and FP32-level; one "
+                         "vector) timed a few times each, for the online phase's launch list")
     a = ap.parse_args()
     if a.case == "small":
         a.no_online = a.no_mixed = a.no_cpu_baseline = a.no_e2e = True
@@ -1036,6 +1039,58 @@ def digits_small(args):
     return 0
 
 
+def online_batched(args):
+    """The batched workload's online phase (N_m = 4,096, N_d = 100, N_t = 200, K 20,000^2): the
+    tensor-core offline phase (Gram, Cholesky, K^{-1}, digit planes of G, Q), then the online graph
+    with q_map = Q d_obs for 64 observation vectors at FP64 level and at FP32 level, and for one
+    vector, each replayed 3 times after one warm-up.  Prints one JSON line of times (ms)."""
+    import torch
+
+    import paper_2501_14911_gb300 as bti
+    from paper_2501_14911_gb300 import synthetic
+
+    dev = torch.device("cuda", 0)
+    p = synthetic.BATCHED
+    h = bti.Handle(p.Nm, p.Nd, p.Nq, p.Nt, device=dev)
+    h.set_blocks(bti.OP_F, torch.from_numpy(p.blocks_F()).to(dev), bti.DF64)
+    h.set_blocks(bti.OP_FQ, torch.from_numpy(p.blocks_Fq()).to(dev), bti.DF64)
+    h.set_prior_se_grid(p.gx, p.gy, p.ell, p.sigma_p, bti.DF64)
+    h.set_noise(p.sigma2)
+    h.set_dense_precision(bti.DF64)
+    h.build_K(p.col_block)
+    h.factor_K()
+    h.invert_K()
+    h.set_digit_planes(bti.OP_G, True)
+    h.build_Q()
+    h.set_online_qoi(True)
+    B = p.n_vectors
+    d = torch.from_numpy(p.vectors_d(B)).to(dev)
+    m = torch.empty((B, p.Nt, p.Nm), dtype=torch.float64, device=dev)
+    q = torch.empty((B, p.Nt, p.Nq), dtype=torch.float64, device=dev)
+    gs = torch.cuda.Stream(device=dev)
+    out = {"case": "online_batched_Nm4096_Nd100_Nt200", "vectors": B}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(gs):
+        h.set_stream(gs)
+        for key, nb, prec in (("fp64_level_ms", B, bti.DF64), ("fp32_level_ms", B, bti.F32),
+                              ("one_vector_ms", 1, bti.DF64)):
+            h.set_online_precision(prec)
+            h.online(d[:nb], m[:nb], q[:nb])
+            torch.cuda.synchronize()
+            e0.record(gs)
+            for _ in range(3):
+                h.online(d[:nb], m[:nb], q[:nb])
+            e1.record(gs)
+            torch.cuda.synchronize()
+            out[key] = e0.elapsed_time(e1) / 3
+        h.set_online_precision(bti.DF64)
+    torch.cuda.synchronize()
+    h.set_stream(torch.cuda.current_stream(dev))
+    h.close()
+    print(json.dumps(out))
+    return 0
+
+
 def factor_small(args):
     """The tensor-core Cholesky and inverse at a small size for ncu captures: K of 8,192^2
     (N_m = 1,024, N_d = 64, N_t = 128, noise variance 1), factored as one panel by recursive
@@ -1076,6 +1131,8 @@ def main():
         return digits_small(args)
     if args.case == "factor_small":
         return factor_small(args)
+    if args.case == "online_batched":
+        return online_batched(args)
     return run_ours(args)
 
 

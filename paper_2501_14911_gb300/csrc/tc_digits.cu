@@ -55,11 +55,17 @@ constexpr int kKiBox = 64;             // FP16 columns per tile of the planes in
 constexpr int kKiChunk = 128;          // columns per work chunk (the unit of stream-K and of tile skipping)
 constexpr int kDrainK = 12;            // K-steps (16 columns each) per accumulation period: 192 columns
 constexpr int kPeriodCols = 204;       // most data columns a period may hold (5 204 2^14 < 2^24)
-constexpr int kBx = 32;                // FP16 columns per TMA box in the pipeline (64 bytes, the swizzle width)
+// FP16 columns per TMA box in the pipeline: two 16-column K-steps (64-byte rows, the 64-byte
+// swizzle) in three stages.  One K-step per box (32-byte rows and swizzle, six stages in the same
+// shared memory) was measured slower: the adjoint of 64 vectors 0.75 -> 0.94 ms, twice the barrier
+// waits, commits and loads per K-step outweighing the finer release of stages.
+constexpr int kBx = 32;
+constexpr int kKPB = kBx / 16;         // K-steps per box
 constexpr int kBoxesPerChunk = kKiChunk / kBx;
-constexpr int kStages = 3;             // pipeline stages: one 32-column box of all six planes of both operands
+constexpr int kBoxesPerTile = kKiBox / kBx;  // boxes per 64-column memory tile
+constexpr int kStages = kBx == 32 ? 3 : 6;   // pipeline stages: one box of all six planes of both operands
 constexpr int kKiThreads = 320;        // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
-constexpr uint32_t kAPlane = kKiRows * kBx * 2;  // bytes of one A plane in a stage (128 rows x 64 B)
+constexpr uint32_t kAPlane = kKiRows * kBx * 2;  // bytes of one A plane in a stage (128 rows x 2 kBx B)
 constexpr uint32_t kAStage = kSl * kAPlane;       // 48 KB
 constexpr uint32_t kTmemCols = 512;    // six accumulator groups (6 N columns, N <= 64)
 constexpr long long kKiSpin = 1ll << 24;              // poll backstop of every wait
@@ -69,11 +75,12 @@ constexpr size_t dig_smem(int NC) { return 1024 + kStages * ((size_t)kAStage + (
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// K-major operand, 64-byte swizzle, 8-row groups 512 B apart (the layout TMA writes with
-// CU_TENSOR_MAP_SWIZZLE_64B for 64-byte rows); a K-step of 16 halves advances the start by 32 B
+// K-major operand with rows of 2 kBx bytes swizzled at that width (the layout TMA writes with
+// CU_TENSOR_MAP_SWIZZLE_32B or _64B), 8-row groups 16 kBx bytes apart; a K-step of 16 halves
+// advances the start by 32 B (descriptor swizzle modes: 6 = 32-byte, 4 = 64-byte)
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
-         ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)((16 * kBx) >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)(kBx == 32 ? 4 : 6) << 61);
 }
 
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
@@ -243,15 +250,14 @@ __device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, vo
 // it (plane S - 1 has one MMA, which reads A directly).  ad, bd: the descriptors of the stage's
 // plane 0 of A and of B at this K-step.  first: the K-step opens an accumulation period, so the
 // pairs (0, t), issued first, overwrite the groups.  Consecutive planes of a stage are kAPlane
-// bytes apart (512 in the descriptor's 16-byte units) for A and NC kBx 2 bytes for B; the
+// bytes apart (kAPlane / 16 in the descriptor's 16-byte units) for A and NC kBx 2 bytes for B; the
 // shared-memory addresses stay below 2^18, so the offsets add to the descriptors' address field
 // without carrying out of it.  Called by a whole warp.
-static_assert(kAPlane == 512 * 16, "A plane stride in descriptor units");
 template <int S> struct KStep;
 template <> struct KStep<4> {
   template <int NC>
   static __device__ __forceinline__ void issue(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, bool first) {
-    constexpr uint64_t bs = (uint64_t)((NC * kBx * 2) >> 4);
+    constexpr uint64_t bs = (uint64_t)((NC * kBx * 2) >> 4), as = (uint64_t)(kAPlane >> 4);
     asm volatile(
         "{\n"
         ".reg .pred e, pa, pt;\n"
@@ -260,13 +266,13 @@ template <> struct KStep<4> {
         "elect.sync _|e, 0xffffffff;\n"
         "setp.eq.u32 pa, %4, 0;\n"
         "setp.eq.u32 pt, %4, %4;\n"
-        "add.u64 a1, %1, 512;\n"
+        "add.u64 a1, %1, %11;\n"
         "add.u64 b1, %2, %5;\n"
         "add.u32 d1, %0, %8;\n"
-        "add.u64 a2, %1, 1024;\n"
+        "add.u64 a2, %1, %12;\n"
         "add.u64 b2, %2, %6;\n"
         "add.u32 d2, %0, %9;\n"
-        "add.u64 a3, %1, 1536;\n"
+        "add.u64 a3, %1, %13;\n"
         "add.u64 b3, %2, %7;\n"
         "add.u32 d3, %0, %10;\n"
         "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, %3, pa;\n"
@@ -281,14 +287,14 @@ template <> struct KStep<4> {
         "@e tcgen05.mma.cta_group::1.kind::f16 [d3], a3, %2, %3, pt;\n"
         "}\n"
         ::"r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(first ? 1u : 0u), "n"(1 * bs), "n"(2 * bs), "n"(3 * bs),
-          "n"(1 * NC), "n"(2 * NC), "n"(3 * NC)
+          "n"(1 * NC), "n"(2 * NC), "n"(3 * NC), "n"(1 * as), "n"(2 * as), "n"(3 * as)
         : "memory");
   }
 };
 template <> struct KStep<5> {
   template <int NC>
   static __device__ __forceinline__ void issue(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, bool first) {
-    constexpr uint64_t bs = (uint64_t)((NC * kBx * 2) >> 4);
+    constexpr uint64_t bs = (uint64_t)((NC * kBx * 2) >> 4), as = (uint64_t)(kAPlane >> 4);
     asm volatile(
         "{\n"
         ".reg .pred e, pa, pt;\n"
@@ -297,16 +303,16 @@ template <> struct KStep<5> {
         "elect.sync _|e, 0xffffffff;\n"
         "setp.eq.u32 pa, %4, 0;\n"
         "setp.eq.u32 pt, %4, %4;\n"
-        "add.u64 a1, %1, 512;\n"
+        "add.u64 a1, %1, %13;\n"
         "add.u64 b1, %2, %5;\n"
         "add.u32 d1, %0, %9;\n"
-        "add.u64 a2, %1, 1024;\n"
+        "add.u64 a2, %1, %14;\n"
         "add.u64 b2, %2, %6;\n"
         "add.u32 d2, %0, %10;\n"
-        "add.u64 a3, %1, 1536;\n"
+        "add.u64 a3, %1, %15;\n"
         "add.u64 b3, %2, %7;\n"
         "add.u32 d3, %0, %11;\n"
-        "add.u64 a4, %1, 2048;\n"
+        "add.u64 a4, %1, %16;\n"
         "add.u64 b4, %2, %8;\n"
         "add.u32 d4, %0, %12;\n"
         "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, %3, pa;\n"
@@ -326,14 +332,15 @@ template <> struct KStep<5> {
         "@e tcgen05.mma.cta_group::1.kind::f16 [d4], a4, %2, %3, pt;\n"
         "}\n"
         ::"r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(first ? 1u : 0u), "n"(1 * bs), "n"(2 * bs), "n"(3 * bs),
-          "n"(4 * bs), "n"(1 * NC), "n"(2 * NC), "n"(3 * NC), "n"(4 * NC)
+          "n"(4 * bs), "n"(1 * NC), "n"(2 * NC), "n"(3 * NC), "n"(4 * NC), "n"(1 * as), "n"(2 * as), "n"(3 * as),
+          "n"(4 * as)
         : "memory");
   }
 };
 template <> struct KStep<6> {
   template <int NC>
   static __device__ __forceinline__ void issue(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, bool first) {
-    constexpr uint64_t bs = (uint64_t)((NC * kBx * 2) >> 4);
+    constexpr uint64_t bs = (uint64_t)((NC * kBx * 2) >> 4), as = (uint64_t)(kAPlane >> 4);
     asm volatile(
         "{\n"
         ".reg .pred e, pa, pt;\n"
@@ -342,19 +349,19 @@ template <> struct KStep<6> {
         "elect.sync _|e, 0xffffffff;\n"
         "setp.eq.u32 pa, %4, 0;\n"
         "setp.eq.u32 pt, %4, %4;\n"
-        "add.u64 a1, %1, 512;\n"
+        "add.u64 a1, %1, %15;\n"
         "add.u64 b1, %2, %5;\n"
         "add.u32 d1, %0, %10;\n"
-        "add.u64 a2, %1, 1024;\n"
+        "add.u64 a2, %1, %16;\n"
         "add.u64 b2, %2, %6;\n"
         "add.u32 d2, %0, %11;\n"
-        "add.u64 a3, %1, 1536;\n"
+        "add.u64 a3, %1, %17;\n"
         "add.u64 b3, %2, %7;\n"
         "add.u32 d3, %0, %12;\n"
-        "add.u64 a4, %1, 2048;\n"
+        "add.u64 a4, %1, %18;\n"
         "add.u64 b4, %2, %8;\n"
         "add.u32 d4, %0, %13;\n"
-        "add.u64 a5, %1, 2560;\n"
+        "add.u64 a5, %1, %19;\n"
         "add.u64 b5, %2, %9;\n"
         "add.u32 d5, %0, %14;\n"
         "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, %3, pa;\n"
@@ -380,12 +387,13 @@ template <> struct KStep<6> {
         "@e tcgen05.mma.cta_group::1.kind::f16 [d5], a5, %2, %3, pt;\n"
         "}\n"
         ::"r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(first ? 1u : 0u), "n"(1 * bs), "n"(2 * bs), "n"(3 * bs),
-          "n"(4 * bs), "n"(5 * bs), "n"(1 * NC), "n"(2 * NC), "n"(3 * NC), "n"(4 * NC), "n"(5 * NC)
+          "n"(4 * bs), "n"(5 * bs), "n"(1 * NC), "n"(2 * NC), "n"(3 * NC), "n"(4 * NC), "n"(5 * NC), "n"(1 * as),
+          "n"(2 * as), "n"(3 * as), "n"(4 * as), "n"(5 * as)
         : "memory");
   }
 };
 
-// The K-step kk (0 or 1) of a stage whose plane 0 of A and of B sit at a0 and b0.
+// The K-step kk (below kKPB) of a stage whose plane 0 of A and of B sit at a0 and b0.
 template <int NC, int S>
 __device__ __forceinline__ void issue_kstep(uint32_t tmem, uint32_t a0, uint32_t b0, int kk, uint32_t idesc,
                                             bool first) {
@@ -734,11 +742,11 @@ sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
           ta = rg * a_rg;
           tb = rg * b_rg;
         }
-        const int nbox = (chunk_ksteps(c) + 1) / 2;
+        const int nbox = (chunk_ksteps(c) + kKPB - 1) / kKPB;
         for (int kb = 0; kb < nbox; ++kb, ++nbx) {
-          const int64_t gb = c * kBoxesPerChunk + kb;       // 32-column box along K
-          const int64_t blk = w * KB + (gb >> 1);            // (problem, 64-column memory tile)
-          const int x = (int)(gb & 1) * kBx;
+          const int64_t gb = c * kBoxesPerChunk + kb;            // box along K
+          const int64_t blk = w * KB + gb / kBoxesPerTile;        // (problem, 64-column memory tile)
+          const int x = (int)(gb % kBoxesPerTile) * kBx;
           const int arow = (int)(blk * a_blk + ta), brow = (int)(blk * b_blk + tb);
           const int st = nbx % kStages;
           if (nbx >= kStages && !mbar_wait(smem_u32(&empty[st]), ((nbx / kStages) - 1) & 1, abort_v)) {
@@ -782,14 +790,14 @@ sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
       for (it.init(tj, per, total, kpt, side); it.valid && ok; it.next(tj)) {
         const int nks = chunk_ksteps(it.c);
         const bool tile_end = it.last();
-        for (int kb = 0; kb < (nks + 1) / 2 && ok; ++kb, ++nbx) {
+        for (int kb = 0; kb < (nks + kKPB - 1) / kKPB && ok; ++kb, ++nbx) {
           const int st = nbx % kStages;
           if (!mbar_wait_warp(smem_u32(&full[st]), (nbx / kStages) & 1, abort_v)) {
             ok = false;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;");
-          for (int kk = 0; kk < 2 && 2 * kb + kk < nks; ++kk) {
+          for (int kk = 0; kk < kKPB && kKPB * kb + kk < nks; ++kk) {
             if (kp == 0 && dc > 0) {
               // the epilogue has drained the previous period's groups
               if (!mbar_wait_warp(smem_u32(&tfree), (dc - 1) & 1, abort_v)) {
@@ -800,8 +808,8 @@ sk_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
             }
             issue_kstep<NC, S>(tmem, smem_u32(sA + st * kAStage), smem_u32(sB + st * kBStage), kk, idesc, kp == 0);
             ++kp;
-            if (period_closes(it.c * (kKiChunk / 16) + 2 * kb + kk, ksteps, tail_cols,
-                              tile_end && 2 * kb + kk + 1 == nks)) {
+            if (period_closes(it.c * (kKiChunk / 16) + kKPB * kb + kk, ksteps, tail_cols,
+                              tile_end && kKPB * kb + kk + 1 == nks)) {
               commit_elect(smem_u32(&accf));
               ++dc;
               kp = 0;
@@ -895,8 +903,8 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 
 namespace {
 // Tensor map of six FP16 digit planes tiled by 64-column memory tiles: dims (64 columns, rows
-// tile-major, plane), one plane every plane_elems halves; the pipeline loads boxes of 32 columns
-// x box_rows rows with the 64-byte swizzle (x = 0 or 32 within a tile, 64 bytes, 16-byte aligned).
+// tile-major, plane), one plane every plane_elems halves; the pipeline loads boxes of kBx columns
+// x box_rows rows swizzled at their row width (x a multiple of kBx within a tile: 16-byte aligned).
 bool encode_planes(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap* tm, const void* planes, int64_t rows,
                    int64_t plane_elems, int box_rows) {
   const cuuint64_t dims[3] = {(cuuint64_t)kKiBox, (cuuint64_t)rows, (cuuint64_t)kSl};
@@ -904,7 +912,8 @@ bool encode_planes(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap* tm, const
   const cuuint32_t box[3] = {(cuuint32_t)kBx, (cuuint32_t)box_rows, 1};
   const cuuint32_t es[3] = {1, 1, 1};
   return enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<void*>(planes), dims, strides, box, es,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, kBx == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 }  // namespace
@@ -1272,14 +1281,14 @@ adj_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         const int w = (int)(unit / JT);
         const int KB = nchunk * (kKiChunk / kKiBox);
         for (int c = 0; c < nchunk && ok; ++c) {
-          const int nbox = (chunk_ksteps(c) + 1) / 2;
+          const int nbox = (chunk_ksteps(c) + kKPB - 1) / kKPB;
           for (int kb = 0; kb < nbox; ++kb, ++nbx) {
-            const int gb = c * kBoxesPerChunk + kb;  // 32-column box along K
-            // tiled planes: memory tile gb / 2 of frequency w starts at row (w KB + gb / 2) * rows
-            const int64_t tile = (int64_t)w * KB + (gb >> 1);
+            const int gb = c * kBoxesPerChunk + kb;  // box along K
+            // tiled planes: memory tile gb / kBoxesPerTile of frequency w starts at row (w KB + tile) rows
+            const int64_t tile = (int64_t)w * KB + gb / kBoxesPerTile;
             const int arow = (int)(tile * Nmp + (int64_t)jt * kKiRows);
             const int brow = (int)(tile * NBp + (int64_t)g * kKiN);
-            const int x = (gb & 1) * kBx;
+            const int x = (gb % kBoxesPerTile) * kBx;
             const int st = nbx % kStages;
             if (nbx >= kStages && !mbar_wait(smem_u32(&empty[st]), ((nbx / kStages) - 1) & 1, abort_v)) {
               ok = false;
@@ -1320,14 +1329,14 @@ adj_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
       for (int u = 0; u < nunits && ok; ++u) {
         for (int c = 0; c < nchunk && ok; ++c) {
           const int nks = chunk_ksteps(c);
-          for (int kb = 0; kb < (nks + 1) / 2 && ok; ++kb, ++nbx) {
+          for (int kb = 0; kb < (nks + kKPB - 1) / kKPB && ok; ++kb, ++nbx) {
             const int st = nbx % kStages;
             if (!mbar_wait_warp(smem_u32(&full[st]), (nbx / kStages) & 1, abort_v)) {
               ok = false;
               break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            for (int kk = 0; kk < 2 && 2 * kb + kk < nks; ++kk) {
+            for (int kk = 0; kk < kKPB && kKPB * kb + kk < nks; ++kk) {
               if (kp == 0 && dc > 0) {
                 if (!mbar_wait_warp(smem_u32(&tfree), (dc - 1) & 1, abort_v)) {
                   ok = false;
@@ -1337,8 +1346,8 @@ adj_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
               }
               issue_kstep<kKiN, S>(tmem, smem_u32(sA + st * kAStage), smem_u32(sB + st * kBStage), kk, idesc, kp == 0);
               ++kp;
-              if (period_closes(c * (kKiChunk / 16) + 2 * kb + kk, ksteps, tail_cols,
-                                c == nchunk - 1 && 2 * kb + kk + 1 == nks)) {
+              if (period_closes(c * (kKiChunk / 16) + kKPB * kb + kk, ksteps, tail_cols,
+                                c == nchunk - 1 && kKPB * kb + kk + 1 == nks)) {
                 commit_elect(smem_u32(&accf));
                 ++dc;
                 kp = 0;
