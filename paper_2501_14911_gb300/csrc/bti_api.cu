@@ -316,7 +316,7 @@ bti_status store_op(bti_ctx* h, bti_op opi, const double* blocks, bti_prec store
 
 // Forward FFT of B input vectors (io element type) into a spectrum of C2<T> elements.
 // The double-FP32 tier transforms in float pairs (FP64 accuracy on the FP32 pipes);
-// its spectra are stored as complex FP64.
+// its spectra stay float pairs (ffc: re_hi, re_lo, im_hi, im_lo) between its kernels.
 FftPlan tuned_plan(bti_ctx* h, const OpStore& o) {
   FftPlan p = h->plan;
   if (h->tune[o.prec].fft_p > 0 && h->tune[o.prec].fft_p <= p.P) p.P = h->tune[o.prec].fft_p;
@@ -329,13 +329,13 @@ void rfft_in(bti_ctx* h, const OpStore& o, const void* in, int64_t ld, int64_t b
   const int Nt = (int)h->Nt;
   cudaStream_t s = h->stream;
   const FftPlan plan = tuned_plan(h, o);
-  if (o.prec == BTI_P_DF64) {
+  if (o.prec == BTI_P_DF64) {  // spectra as float pairs (ffc), the double-FP32 tier's own format
     if (io == BTI_P_F64)
-      PROF(h, BTI_K_RFFT, (launch_rfft_cols<ffloat, double, double>(plan, Nt, (const double*)in, ld, bstride,
-                                                                     (double2*)X, Xbstride, ncols, B, s)));
+      PROF(h, BTI_K_RFFT, (launch_rfft_cols<ffloat, double, ffloat>(plan, Nt, (const double*)in, ld, bstride,
+                                                                     (ffc*)X, Xbstride, ncols, B, s)));
     else
-      PROF(h, BTI_K_RFFT, (launch_rfft_cols<ffloat, float, double>(plan, Nt, (const float*)in, ld, bstride,
-                                                                    (double2*)X, Xbstride, ncols, B, s)));
+      PROF(h, BTI_K_RFFT, (launch_rfft_cols<ffloat, float, ffloat>(plan, Nt, (const float*)in, ld, bstride,
+                                                                    (ffc*)X, Xbstride, ncols, B, s)));
   } else if (io == BTI_P_F64) {
     PROF(h, BTI_K_RFFT, (launch_rfft_cols<T, double, T>(plan, Nt, (const double*)in, ld, bstride, X, Xbstride,
                                                          ncols, B, s)));
@@ -354,12 +354,12 @@ void irfft_out(bti_ctx* h, const OpStore& o, const C2<T>* Y, int64_t ld, int64_t
   const FftPlan plan = tuned_plan(h, o);
   // 1/L, times the power of two the stored double-FP32 blocks were divided by (exact)
   const double scale = std::ldexp(1.0 / (double)h->L, o.pexp);
-  if (o.prec == BTI_P_DF64) {
+  if (o.prec == BTI_P_DF64) {  // float-pair spectra in
     if (io == BTI_P_F64)
-      PROF(h, BTI_K_IRFFT, (launch_irfft_cols<ffloat, double, double>(plan, Nt, (const double2*)Y, ld, Ybstride,
+      PROF(h, BTI_K_IRFFT, (launch_irfft_cols<ffloat, ffloat, double>(plan, Nt, (const ffc*)Y, ld, Ybstride,
                                                                        (double*)out, obstride, ncols, B, scale, s, os)));
     else
-      PROF(h, BTI_K_IRFFT, (launch_irfft_cols<ffloat, double, float>(plan, Nt, (const double2*)Y, ld, Ybstride,
+      PROF(h, BTI_K_IRFFT, (launch_irfft_cols<ffloat, ffloat, float>(plan, Nt, (const ffc*)Y, ld, Ybstride,
                                                                       (float*)out, obstride, ncols, B, scale, s, os)));
   } else if (io == BTI_P_F64) {
     PROF(h, BTI_K_IRFFT, (launch_irfft_cols<T, T, double>(plan, Nt, Y, ld, Ybstride, (double*)out, obstride,
@@ -412,7 +412,7 @@ bti_status apply_fwd_t(bti_ctx* h, const OpStore& o, const void* in, void* out, 
     h->prof_count[BTI_K_PROD_FWD] += nl - 1;
     if (e != cudaSuccess) return cuda_check(h, e, "tensor-core forward product (digit planes)");
   } else if (o.prec == BTI_P_DF64)
-    PROF(h, BTI_K_PROD_FWD, launch_prod_fwd_df64((const float4*)o.hat, (const double2*)mhat, (double2*)part, nf,
+    PROF(h, BTI_K_PROD_FWD, launch_prod_fwd_df64((const float4*)o.hat, (const float4*)mhat, (double2*)part, nf,
                                                  R, Nm, B, s, jc));
   else if (o.prec == BTI_P_F16)
     PROF(h, BTI_K_PROD_FWD, launch_prod_fwd_f16(o.hat, o.scale, (const float2*)mhat, (float2*)part, nf, R, Nm, B,
@@ -420,7 +420,12 @@ bti_status apply_fwd_t(bti_ctx* h, const OpStore& o, const void* in, void* out, 
   else
     PROF(h, BTI_K_PROD_FWD, (launch_prod_fwd<T, T>((const C2<T>*)o.hat, mhat, part, nf, R, Nm, B, s,
                                                    jc)));
-  if (!tc && !dig) PROF(h, BTI_K_REDUCE, (launch_reduce_chunks<T>(part, dhat, nf, R, Nm, B, s, jc)));
+  if (!tc && !dig) {
+    if (o.prec == BTI_P_DF64)  // FP64 sums of the chunks, stored as float pairs for the inverse FFT
+      PROF(h, BTI_K_REDUCE, launch_reduce_chunks_df64((const double2*)part, (float4*)dhat, nf, R, Nm, B, s, jc));
+    else
+      PROF(h, BTI_K_REDUCE, (launch_reduce_chunks<T>(part, dhat, nf, R, Nm, B, s, jc)));
+  }
   // the QoI map writes every qstride-th time step only (N_t / qstride rows per vector)
   const int os = (&o == &h->op[BTI_OP_FQ]) ? h->qstride : 1;
   irfft_out<T>(h, o, dhat, R, nf * R, out, (Nt / os) * R, R, B, io, os);
@@ -463,7 +468,7 @@ bti_status apply_adj_t(bti_ctx* h, const OpStore& o, const void* in, void* out, 
     h->prof_count[BTI_K_PROD_ADJ] += nl - 1;
     if (e != cudaSuccess) return cuda_check(h, e, "tensor-core adjoint product (digit planes)");
   } else if (o.prec == BTI_P_DF64)
-    PROF(h, BTI_K_PROD_ADJ, launch_prod_adj_df64((const float4*)o.hat, (const double2*)dhat, (double2*)mhat, nf,
+    PROF(h, BTI_K_PROD_ADJ, launch_prod_adj_df64((const float4*)o.hat, (const float4*)dhat, (float4*)mhat, nf,
                                                  R, Nm, B, s, h->tune[o.prec].vpt));
   else if (o.prec == BTI_P_F16)
     PROF(h, BTI_K_PROD_ADJ, launch_prod_adj_f16(o.hat, o.scale, (const float2*)dhat, (float2*)mhat, nf, R, Nm, B,
@@ -478,7 +483,7 @@ bti_status apply_adj_t(bti_ctx* h, const OpStore& o, const void* in, void* out, 
 // out = op(in) with an explicit store (an operator or its shadow copy); no argument checks
 bti_status apply_store(bti_ctx* h, const OpStore& o, bool adjoint, const void* in, void* out, int64_t B,
                        bti_prec io) {
-  if (double_path(o.prec))  // FP64 and double-FP32 tiers: FFT spectra in FP64
+  if (double_path(o.prec))  // FP64 and double-FP32 tiers: 16-byte spectra (FP64 complex, float-pair complex)
     return adjoint ? apply_adj_t<double>(h, o, in, out, B, io) : apply_fwd_t<double>(h, o, in, out, B, io);
   return adjoint ? apply_adj_t<float>(h, o, in, out, B, io) : apply_fwd_t<float>(h, o, in, out, B, io);
 }

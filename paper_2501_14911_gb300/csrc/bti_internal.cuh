@@ -172,9 +172,14 @@ size_t prod_fwd_partial_elems(int64_t nf, int64_t R, int64_t Nm, int64_t B);
 void launch_split_df64(void* hat, int64_t n, int pexp, cudaStream_t s);
 // *out = bit pattern of max |x[i]| (a non-negative double; a NaN input reads as a NaN)
 void launch_max_abs(const double* x, int64_t n, unsigned long long* out, cudaStream_t s);
-void launch_prod_fwd_df64(const float4* Fhat, const double2* mhat, double2* partial, int64_t nf,
+// The tier's vector spectra are float quads too (the pair FFTs' format): mhat and dhat below.
+// Forward partials stay complex FP64, summed in FP64 by launch_reduce_chunks_df64, which stores
+// each sum as a float quad.
+void launch_prod_fwd_df64(const float4* Fhat, const float4* mhat, double2* partial, int64_t nf,
                           int64_t R, int64_t Nm, int64_t B, cudaStream_t s, int jc = 0);
-void launch_prod_adj_df64(const float4* Fhat, const double2* dhat, double2* mhat, int64_t nf, int64_t R,
+void launch_reduce_chunks_df64(const double2* partial, float4* dhat, int64_t nf, int64_t R, int64_t Nm,
+                               int64_t B, cudaStream_t s, int jc = 0);
+void launch_prod_adj_df64(const float4* Fhat, const float4* dhat, float4* mhat, int64_t nf, int64_t R,
                           int64_t Nm, int64_t B, cudaStream_t s, int vpt = 0);
 // FP16 tier: spectral blocks as FP16 complex pairs with one FP32 power-of-two scale per row.
 // src [nf][rn][Nm] FP64 spectrum of rows i0 .. i0 + rn -> rows (w, i0 + r) of dst [nf][R][Nm]
@@ -319,8 +324,8 @@ int64_t cholesky_tc(double* A, int64_t n, int64_t P, double* Linv, double* work,
                     int* status, int* err, cudaStream_t s, cudaError_t* cerr, int drop_stage = -1);
 // Double-FP32 tier's adjoint product for B >= 16 on the tensor cores (tc_digits.cu): digit
 // planes of conj(F-hat)^T, K-major over (i, re/im), one exponent per (w, j); built once from
-// the float-quad blocks.  adj_digits_apply: dhat [B][nf][R], mhat [B][nf][N_m] complex FP64;
-// work of adj_digits_work_bytes bytes.
+// the float-quad blocks.  adj_digits_apply: dhat [B][nf][R], mhat [B][nf][N_m] float-quad
+// spectra; work of adj_digits_work_bytes bytes.
 size_t adj_digits_plane_elems(int64_t nf, int64_t R, int64_t Nm);
 size_t adj_digits_exp_elems(int64_t nf, int64_t Nm);
 bool adj_digits_supported(int64_t nf, int64_t R, int64_t Nm, int64_t B);
@@ -328,7 +333,7 @@ void adj_digits_prepare();
 int64_t adj_digits_build(const void* hat, int64_t nf, int64_t R, int64_t Nm, void* planes, int* ex, cudaStream_t s);
 size_t adj_digits_work_bytes(int64_t nf, int64_t R, int64_t B);
 // Forward products of the same tier for B >= 16 (tc_digits.cu): planes of F-hat K-major over
-// (j, re/im), one exponent per (w, i); mhat [B][nf][N_m] -> dhat [B][nf][R] complex FP64.
+// (j, re/im), one exponent per (w, i); mhat [B][nf][N_m] -> dhat [B][nf][R] float-quad spectra.
 size_t fwd_digits_plane_elems(int64_t nf, int64_t R, int64_t Nm);
 size_t fwd_digits_exp_elems(int64_t nf, int64_t R);
 bool fwd_digits_supported(int64_t nf, int64_t R, int64_t Nm, int64_t B);

@@ -17,6 +17,9 @@
 // a table computed in FP64 on the host with std::cos / std::sin.  The arithmetic
 // type T is float, double, or the double-FP32 pair (ffloat), which carries FP64-
 // level accuracy on the FP32 pipes (GB300 issues FP64 at 1/64 of the FP32 rate).
+// The pair transforms take and give their spectra as float pairs (re_hi, re_lo, im_hi,
+// im_lo): converting FP64 spectra to pairs on load and back on store kept the FP64 pipe
+// 62 % busy and cost 28-36 % of the transforms' time.
 #include "bti_internal.cuh"
 
 #include <cmath>
@@ -137,6 +140,65 @@ __device__ __forceinline__ C2<T> tw_get(const C2<T>* __restrict__ tw, int n) {
   return w;
 }
 
+// The butterflies' arithmetic.  For float pairs the sums and products inside a butterfly are
+// left unnormalised: the high parts are still summed by an exact two-sum and the products'
+// errors kept by FMA, but the low float is not folded back to |lo| <= ulp(hi) / 2 after every
+// operation (8 FP32 operations per sum instead of 11, 4 per product instead of 7, 16 per
+// complex-product part instead of 19).  Rounding the low floats costs about 2^-48 of the
+// operands' magnitude either way; each butterfly output is renormalised once, as it is stored.
+template <typename T> __device__ __forceinline__ C2<T> badd(C2<T> a, C2<T> b) { return cadd<T>(a, b); }
+template <typename T> __device__ __forceinline__ C2<T> bsub(C2<T> a, C2<T> b) { return csub<T>(a, b); }
+template <typename T> __device__ __forceinline__ C2<T> bmul(C2<T> a, C2<T> b) { return cmul<T>(a, b); }
+template <typename T> __device__ __forceinline__ C2<T> bscale(T c, C2<T> a) { return mk<T>(c * a.x, c * a.y); }
+template <typename T> __device__ __forceinline__ C2<T> bnorm(C2<T> a) { return a; }
+
+__device__ __forceinline__ ffloat ff_add_u(ffloat a, ffloat b) {
+  const float s = __fadd_rn(a.h, b.h);
+  const float bb = __fsub_rn(s, a.h);
+  const float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));
+  return ffloat(s, __fadd_rn(e, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ ffloat ff_mul_u(ffloat a, ffloat b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  return ffloat(p, e);
+}
+// x1 y1 - x2 y2 (sub) or x1 y1 + x2 y2: both high products exact, summed by two-sum
+__device__ __forceinline__ ffloat ff_dot2_u(ffloat x1, ffloat y1, ffloat x2, ffloat y2, bool sub) {
+  const float sg = sub ? -1.f : 1.f;
+  const float p1 = __fmul_rn(x1.h, y1.h);
+  const float p2 = __fmul_rn(sg * x2.h, y2.h);
+  float lo = __fmaf_rn(x1.h, y1.h, -p1);
+  lo = __fadd_rn(lo, __fmaf_rn(sg * x2.h, y2.h, -p2));
+  const float s = __fadd_rn(p1, p2);
+  const float bb = __fsub_rn(s, p1);
+  lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(p1, __fsub_rn(s, bb)), __fsub_rn(p2, bb)));
+  lo = __fmaf_rn(x1.h, y1.l, lo);
+  lo = __fmaf_rn(x1.l, y1.h, lo);
+  lo = __fmaf_rn(sg * x2.h, y2.l, lo);
+  lo = __fmaf_rn(sg * x2.l, y2.h, lo);
+  return ffloat(s, lo);
+}
+__device__ __forceinline__ ffloat ff_norm(ffloat a) {
+  const float h = __fadd_rn(a.h, a.l);
+  return ffloat(h, __fsub_rn(a.l, __fsub_rn(h, a.h)));
+}
+template <> __device__ __forceinline__ ffc badd<ffloat>(ffc a, ffc b) {
+  return mk<ffloat>(ff_add_u(a.x, b.x), ff_add_u(a.y, b.y));
+}
+template <> __device__ __forceinline__ ffc bsub<ffloat>(ffc a, ffc b) {
+  return mk<ffloat>(ff_add_u(a.x, -b.x), ff_add_u(a.y, -b.y));
+}
+template <> __device__ __forceinline__ ffc bmul<ffloat>(ffc a, ffc b) {
+  return mk<ffloat>(ff_dot2_u(a.x, b.x, a.y, b.y, true), ff_dot2_u(a.x, b.y, a.y, b.x, false));
+}
+template <> __device__ __forceinline__ ffc bscale<ffloat>(ffloat c, ffc a) {
+  return mk<ffloat>(ff_mul_u(c, a.x), ff_mul_u(c, a.y));
+}
+template <> __device__ __forceinline__ ffc bnorm<ffloat>(ffc a) { return mk<ffloat>(ff_norm(a.x), ff_norm(a.y)); }
+
 // multiply by -i (forward) or +i (inverse)
 template <typename T, bool INV>
 __device__ __forceinline__ C2<T> rot90(C2<T> a) {
@@ -150,12 +212,12 @@ __device__ __forceinline__ int sp(int n) { return n + (n >> 3); }
 
 template <typename T, bool INV>
 __device__ __forceinline__ void dft4(C2<T>& a0, C2<T>& a1, C2<T>& a2, C2<T>& a3) {
-  C2<T> t0 = cadd<T>(a0, a2), t1 = csub<T>(a0, a2);
-  C2<T> t2 = cadd<T>(a1, a3), t3 = rot90<T, INV>(csub<T>(a1, a3));
-  a0 = cadd<T>(t0, t2);
-  a2 = csub<T>(t0, t2);
-  a1 = cadd<T>(t1, t3);
-  a3 = csub<T>(t1, t3);
+  C2<T> t0 = badd<T>(a0, a2), t1 = bsub<T>(a0, a2);
+  C2<T> t2 = badd<T>(a1, a3), t3 = rot90<T, INV>(bsub<T>(a1, a3));
+  a0 = badd<T>(t0, t2);
+  a2 = bsub<T>(t0, t2);
+  a1 = badd<T>(t1, t3);
+  a3 = bsub<T>(t1, t3);
 }
 
 // One radix-R Stockham butterfly: inputs element i0 + q Lr of src, q < R; outputs element
@@ -168,10 +230,10 @@ __device__ __forceinline__ void butterfly(const C2<T>* src, int i0, int Lr, C2<T
   for (int q = 0; q < R; ++q) a[q] = src[sp(i0 + q * Lr)];
   if (twstep != 0) {
 #pragma unroll
-    for (int q = 1; q < R; ++q) a[q] = cmul<T>(a[q], tw_get<T, INV>(tw, q * twstep));
+    for (int q = 1; q < R; ++q) a[q] = bmul<T>(a[q], tw_get<T, INV>(tw, q * twstep));
   }
   if (R == 2) {
-    C2<T> b0 = cadd<T>(a[0], a[1]), b1 = csub<T>(a[0], a[1]);
+    C2<T> b0 = badd<T>(a[0], a[1]), b1 = bsub<T>(a[0], a[1]);
     a[0] = b0;
     a[1] = b1;
   } else if (R == 4) {
@@ -185,17 +247,17 @@ __device__ __forceinline__ void butterfly(const C2<T>* src, int i0, int Lr, C2<T
     const T h = (T)0.70710678118654752440084436210485;  // sqrt(1/2)
     C2<T> w1 = INV ? mk<T>(h, h) : mk<T>(h, -h);
     C2<T> w3 = INV ? mk<T>(-h, h) : mk<T>(-h, -h);
-    o1 = cmul<T>(o1, w1);
+    o1 = bmul<T>(o1, w1);
     o2 = rot90<T, INV>(o2);
-    o3 = cmul<T>(o3, w3);
-    a[0] = cadd<T>(e0, o0);
-    a[4] = csub<T>(e0, o0);
-    a[1] = cadd<T>(e1, o1);
-    a[5] = csub<T>(e1, o1);
-    a[2] = cadd<T>(e2, o2);
-    a[6] = csub<T>(e2, o2);
-    a[3] = cadd<T>(e3, o3);
-    a[7] = csub<T>(e3, o3);
+    o3 = bmul<T>(o3, w3);
+    a[0] = badd<T>(e0, o0);
+    a[4] = bsub<T>(e0, o0);
+    a[1] = badd<T>(e1, o1);
+    a[5] = bsub<T>(e1, o1);
+    a[2] = badd<T>(e2, o2);
+    a[6] = bsub<T>(e2, o2);
+    a[3] = badd<T>(e3, o3);
+    a[7] = bsub<T>(e3, o3);
   } else if (R == 5) {
     // radix 5 with constant twiddles: with t1 = a1 + a4, t2 = a2 + a3, t3 = a1 - a4,
     // t4 = a2 - a3, c_k = cos(2 pi k / 5) and s_k = sin(2 pi k / 5) (k = 1, 2), the outputs are
@@ -204,17 +266,17 @@ __device__ __forceinline__ void butterfly(const C2<T>* src, int i0, int Lr, C2<T
     // v2 = s2 t3 - s1 t4, since w^4 = conj(w) and w^3 = conj(w^2) for w = e^{-2 pi i / 5}
     const T c1 = (T)0.30901699437494742410229341718282, c2 = (T)-0.80901699437494742410229341718282;
     const T s1 = (T)0.95105651629515357211643933337938, s2 = (T)0.58778525229247312916870595463907;
-    const C2<T> t1 = cadd<T>(a[1], a[4]), t2 = cadd<T>(a[2], a[3]);
-    const C2<T> t3 = csub<T>(a[1], a[4]), t4 = csub<T>(a[2], a[3]);
-    const C2<T> u1 = cadd<T>(a[0], cadd<T>(mk<T>(c1 * t1.x, c1 * t1.y), mk<T>(c2 * t2.x, c2 * t2.y)));
-    const C2<T> u2 = cadd<T>(a[0], cadd<T>(mk<T>(c2 * t1.x, c2 * t1.y), mk<T>(c1 * t2.x, c1 * t2.y)));
-    const C2<T> v1 = rot90<T, INV>(cadd<T>(mk<T>(s1 * t3.x, s1 * t3.y), mk<T>(s2 * t4.x, s2 * t4.y)));
-    const C2<T> v2 = rot90<T, INV>(csub<T>(mk<T>(s2 * t3.x, s2 * t3.y), mk<T>(s1 * t4.x, s1 * t4.y)));
-    a[0] = cadd<T>(a[0], cadd<T>(t1, t2));
-    a[1] = cadd<T>(u1, v1);
-    a[4] = csub<T>(u1, v1);
-    a[2] = cadd<T>(u2, v2);
-    a[3] = csub<T>(u2, v2);
+    const C2<T> t1 = badd<T>(a[1], a[4]), t2 = badd<T>(a[2], a[3]);
+    const C2<T> t3 = bsub<T>(a[1], a[4]), t4 = bsub<T>(a[2], a[3]);
+    const C2<T> u1 = badd<T>(a[0], badd<T>(bscale<T>(c1, t1), bscale<T>(c2, t2)));
+    const C2<T> u2 = badd<T>(a[0], badd<T>(bscale<T>(c2, t1), bscale<T>(c1, t2)));
+    const C2<T> v1 = rot90<T, INV>(badd<T>(bscale<T>(s1, t3), bscale<T>(s2, t4)));
+    const C2<T> v2 = rot90<T, INV>(bsub<T>(bscale<T>(s2, t3), bscale<T>(s1, t4)));
+    a[0] = badd<T>(a[0], badd<T>(t1, t2));
+    a[1] = badd<T>(u1, v1);
+    a[4] = bsub<T>(u1, v1);
+    a[2] = badd<T>(u2, v2);
+    a[3] = bsub<T>(u2, v2);
   } else {
     // generic small DFT (R = 3, 7): b_m = sum_q a_q w_R^{q m}, w_R^n = tw[(n mod R) L / R]
     C2<T> b[R];
@@ -226,7 +288,7 @@ __device__ __forceinline__ void butterfly(const C2<T>* src, int i0, int Lr, C2<T
       for (int q = 1; q < R; ++q) {
         int e = (q * m) % R;
         C2<T> w = tw_get<T, INV>(tw, e * LR);
-        acc = cadd<T>(acc, cmul<T>(a[q], w));
+        acc = badd<T>(acc, bmul<T>(a[q], w));
       }
       b[m] = acc;
     }
@@ -234,7 +296,7 @@ __device__ __forceinline__ void butterfly(const C2<T>* src, int i0, int Lr, C2<T
     for (int m = 0; m < R; ++m) a[m] = b[m];
   }
 #pragma unroll
-  for (int m = 0; m < R; ++m) dst[sp(o0 + m * Ns)] = a[m];
+  for (int m = 0; m < R; ++m) dst[sp(o0 + m * Ns)] = bnorm<T>(a[m]);
 }
 
 // First radix-8 pass of a forward transform whose second half is zero padding
@@ -245,20 +307,20 @@ __device__ __forceinline__ void butterfly8_half_zero(const C2<T>* src, int i0, i
   const C2<T> a0 = src[sp(i0)], a1 = src[sp(i0 + Lr)], a2 = src[sp(i0 + 2 * Lr)], a3 = src[sp(i0 + 3 * Lr)];
   // even half: DFT4(a0, a2, 0, 0); odd half: DFT4(a1, a3, 0, 0)
   const C2<T> r2 = rot90<T, false>(a2), r3 = rot90<T, false>(a3);
-  C2<T> e0 = cadd<T>(a0, a2), e2 = csub<T>(a0, a2), e1 = cadd<T>(a0, r2), e3 = csub<T>(a0, r2);
-  C2<T> o0v = cadd<T>(a1, a3), o2 = csub<T>(a1, a3), o1 = cadd<T>(a1, r3), o3 = csub<T>(a1, r3);
+  C2<T> e0 = badd<T>(a0, a2), e2 = bsub<T>(a0, a2), e1 = badd<T>(a0, r2), e3 = bsub<T>(a0, r2);
+  C2<T> o0v = badd<T>(a1, a3), o2 = bsub<T>(a1, a3), o1 = badd<T>(a1, r3), o3 = bsub<T>(a1, r3);
   const T h = (T)0.70710678118654752440084436210485;  // sqrt(1/2)
-  o1 = cmul<T>(o1, mk<T>(h, -h));
+  o1 = bmul<T>(o1, mk<T>(h, -h));
   o2 = rot90<T, false>(o2);
-  o3 = cmul<T>(o3, mk<T>(-h, -h));
-  dst[sp(o0)] = cadd<T>(e0, o0v);
-  dst[sp(o0 + 4)] = csub<T>(e0, o0v);
-  dst[sp(o0 + 1)] = cadd<T>(e1, o1);
-  dst[sp(o0 + 5)] = csub<T>(e1, o1);
-  dst[sp(o0 + 2)] = cadd<T>(e2, o2);
-  dst[sp(o0 + 6)] = csub<T>(e2, o2);
-  dst[sp(o0 + 3)] = cadd<T>(e3, o3);
-  dst[sp(o0 + 7)] = csub<T>(e3, o3);
+  o3 = bmul<T>(o3, mk<T>(-h, -h));
+  dst[sp(o0)] = bnorm<T>(badd<T>(e0, o0v));
+  dst[sp(o0 + 4)] = bnorm<T>(bsub<T>(e0, o0v));
+  dst[sp(o0 + 1)] = bnorm<T>(badd<T>(e1, o1));
+  dst[sp(o0 + 5)] = bnorm<T>(bsub<T>(e1, o1));
+  dst[sp(o0 + 2)] = bnorm<T>(badd<T>(e2, o2));
+  dst[sp(o0 + 6)] = bnorm<T>(bsub<T>(e2, o2));
+  dst[sp(o0 + 3)] = bnorm<T>(badd<T>(e3, o3));
+  dst[sp(o0 + 7)] = bnorm<T>(bsub<T>(e3, o3));
 }
 
 // The radix sequence of a length L in fft_plan_make's order (8, 4, 2, 7, 5, 3), at compile time
@@ -650,8 +712,8 @@ INST_R(double, double, float)
 INST_R(double, float, double)
 INST_R(float, float, float)
 INST_R(float, double, float)
-INST_R(ffloat, double, double)
-INST_R(ffloat, float, double)
+INST_R(ffloat, double, ffloat)
+INST_R(ffloat, float, ffloat)
 #define INST_I(T, TYI, TO)                                                                             \
   template void launch_irfft_cols<T, TYI, TO>(const FftPlan&, int, const C2<TYI>*, int64_t, int64_t, TO*, \
                                               int64_t, int64_t, int64_t, double, cudaStream_t, int);
@@ -659,7 +721,7 @@ INST_I(double, double, double)
 INST_I(double, double, float)
 INST_I(float, float, float)
 INST_I(float, float, double)
-INST_I(ffloat, double, double)
-INST_I(ffloat, double, float)
+INST_I(ffloat, ffloat, double)
+INST_I(ffloat, ffloat, float)
 
 }  // namespace bti

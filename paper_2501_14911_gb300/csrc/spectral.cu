@@ -274,8 +274,9 @@ template void launch_prod_adj<float, float>(const float2*, const float2*, float2
 // The double-FP32 tier keeps FP64-level accuracy on the FP32 pipes instead:
 // every real number of a spectral block is stored as an unevaluated sum
 // hi + lo of two floats (|lo| <= ulp(hi) / 2, about 48 significant bits,
-// 16 bytes per complex element like FP64), the frequency-domain vector is split
-// the same way in shared memory, and products are accumulated in float pairs:
+// 16 bytes per complex element like FP64), the frequency-domain vectors come and
+// go in the same float-quad form (the pair FFTs' own), and products are accumulated
+// in float pairs:
 //   x * y = xh*yh (exact: rounded product plus its FMA error) + xh*yl + xl*yh,
 // with the high parts summed by Knuth's error-free two-sum and every error term
 // gathered in the low float.  The relative error of a sum of n terms is about
@@ -315,6 +316,13 @@ __device__ __forceinline__ void ff_add(float& ah, float& al, float bh, float bl)
 }
 
 __device__ __forceinline__ double ff_to_d(float h, float l) { return (double)h + (double)l; }
+
+// h + l as a normalised pair (|lo| <= ulp(hi) / 2) by Knuth's two-sum, whatever their magnitudes
+__device__ __forceinline__ ff two_sum(float h, float l) {
+  const float s = __fadd_rn(h, l);
+  const float bb = __fsub_rn(s, h);
+  return {s, __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(l, bb))};
+}
 
 }  // namespace
 
@@ -375,11 +383,11 @@ void launch_max_abs(const double* x, int64_t n, unsigned long long* out, cudaStr
 // to four independent float-pair accumulators so their two-sum chains overlap.
 template <int BG, int U>
 __global__ void __launch_bounds__(256)
-prod_fwd_df64_kernel(const float4* __restrict__ Fhat, const double2* __restrict__ mhat,
+prod_fwd_df64_kernel(const float4* __restrict__ Fhat, const float4* __restrict__ mhat,
                      double2* __restrict__ partial, int64_t nf, int64_t R, int64_t Nm, int64_t B,
                      int JC, int nchunk) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float4* sm = reinterpret_cast<float4*>(smem_raw);  // [BG][JC] split m-hat
+  float4* sm = reinterpret_cast<float4*>(smem_raw);  // [BG][JC] m-hat
   const int ch = blockIdx.x;
   const int64_t w = blockIdx.y;
   const int64_t b0 = (int64_t)blockIdx.z * BG;
@@ -387,13 +395,7 @@ prod_fwd_df64_kernel(const float4* __restrict__ Fhat, const double2* __restrict_
   const int jn = (int)((Nm - j0) < JC ? (Nm - j0) : JC);
   for (int idx = threadIdx.x; idx < BG * JC; idx += blockDim.x) {
     int bb = idx / JC, jj = idx - bb * JC;
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (jj < jn && b0 + bb < B) {
-      double2 x = mhat[((b0 + bb) * nf + w) * Nm + j0 + jj];
-      ff re = split_d(x.x), im = split_d(x.y);
-      v = make_float4(re.h, re.l, im.h, im.l);
-    }
-    sm[idx] = v;
+    sm[idx] = (jj < jn && b0 + bb < B) ? mhat[((b0 + bb) * nf + w) * Nm + j0 + jj] : make_float4(0.f, 0.f, 0.f, 0.f);
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -457,7 +459,7 @@ prod_fwd_df64_kernel(const float4* __restrict__ Fhat, const double2* __restrict_
   }
 }
 
-void launch_prod_fwd_df64(const float4* Fhat, const double2* mhat, double2* partial, int64_t nf,
+void launch_prod_fwd_df64(const float4* Fhat, const float4* mhat, double2* partial, int64_t nf,
                           int64_t R, int64_t Nm, int64_t B, cudaStream_t s, int jc) {
   // chunking identical to the FP64 tier (the reduce pass and workspace sizes are shared)
   int bg = fwd_bg<double>(B);
@@ -476,14 +478,39 @@ void launch_prod_fwd_df64(const float4* Fhat, const double2* mhat, double2* part
     prod_fwd_df64_kernel<1, 8><<<grid, 256, smem, s>>>(Fhat, mhat, partial, nf, R, Nm, B, JC, nchunk);
 }
 
+// dhat[b][w][i] = the chunk partials summed in FP64 in chunk order (as the FP64 tier), stored
+// as a float quad (hi = the sum rounded to FP32, lo = the rest rounded to FP32)
+__global__ void reduce_chunks_df64_kernel(const double2* __restrict__ partial, float4* __restrict__ dhat,
+                                          int64_t total, int64_t R, int nchunk) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const int64_t bw = idx / R, i = idx - bw * R;
+  const double2* p = partial + bw * nchunk * R + i;
+  double sr = 0, si = 0;
+  for (int c = 0; c < nchunk; ++c) {
+    const double2 v = p[(int64_t)c * R];
+    sr += v.x;
+    si += v.y;
+  }
+  const ff re = split_d(sr), im = split_d(si);
+  dhat[idx] = make_float4(re.h, re.l, im.h, im.l);
+}
+
+void launch_reduce_chunks_df64(const double2* partial, float4* dhat, int64_t nf, int64_t R, int64_t Nm,
+                               int64_t B, cudaStream_t s, int jc) {
+  const int nchunk = fwd_nchunk<double>(Nm, B, nullptr, jc);  // the forward product's chunking
+  const int64_t total = B * nf * R;
+  reduce_chunks_df64_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(partial, dhat, total, R, nchunk);
+}
+
 // Adjoint product, double-FP32 arithmetic; thread owns j = j0 + tid + 256 v.  AHEAD: each thread
 // loads F-hat's next row while it uses the current one (two rows in flight instead of one).
 template <int BG, int VPT, bool AHEAD = (BG >= 4)>
 __global__ void __launch_bounds__(256)
-prod_adj_df64_kernel(const float4* __restrict__ Fhat, const double2* __restrict__ dhat,
-                     double2* __restrict__ mhat, int64_t nf, int64_t R, int64_t Nm, int64_t B) {
+prod_adj_df64_kernel(const float4* __restrict__ Fhat, const float4* __restrict__ dhat,
+                     float4* __restrict__ mhat, int64_t nf, int64_t R, int64_t Nm, int64_t B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float4* sd = reinterpret_cast<float4*>(smem_raw);  // [BG][min(R, kAdjRows)] split d-hat
+  float4* sd = reinterpret_cast<float4*>(smem_raw);  // [BG][min(R, kAdjRows)] d-hat
   const int64_t w = blockIdx.y;
   const int64_t b0 = (int64_t)blockIdx.z * BG;
   const int64_t jbase = (int64_t)blockIdx.x * (256 * VPT) + threadIdx.x;
@@ -500,13 +527,7 @@ prod_adj_df64_kernel(const float4* __restrict__ Fhat, const double2* __restrict_
     if (i0 > 0) __syncthreads();  // the previous tile is consumed
     for (int64_t idx = threadIdx.x; idx < BG * rn; idx += blockDim.x) {
       int64_t bb = idx / rn, i = i0 + (idx - bb * rn);
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (b0 + bb < B) {
-        double2 x = dhat[((b0 + bb) * nf + w) * R + i];
-        ff re = split_d(x.x), im = split_d(x.y);
-        v = make_float4(re.h, re.l, im.h, im.l);
-      }
-      sd[bb * RS + (i - i0)] = v;
+      sd[bb * RS + (i - i0)] = (b0 + bb < B) ? dhat[((b0 + bb) * nf + w) * R + i] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
     // F-hat row ii of the tile; with several vectors per CTA, or a grid too small to keep HBM
@@ -556,14 +577,16 @@ prod_adj_df64_kernel(const float4* __restrict__ Fhat, const double2* __restrict_
 #pragma unroll
     for (int v = 0; v < VPT; ++v) {
       int64_t j = jbase + 256 * v;
-      if (j < Nm)
-        mhat[((b0 + bb) * nf + w) * Nm + j] = make_double2(ff_to_d(rh[bb][v], rl[bb][v]), ff_to_d(ih[bb][v], il[bb][v]));
+      if (j < Nm) {  // the accumulated low floats renormalised by a two-sum
+        const ff re = two_sum(rh[bb][v], rl[bb][v]), im = two_sum(ih[bb][v], il[bb][v]);
+        mhat[((b0 + bb) * nf + w) * Nm + j] = make_float4(re.h, re.l, im.h, im.l);
+      }
     }
   }
 }
 
 template <int BG, int VPT, bool AHEAD = (BG >= 4)>
-static void adj_df64_launch(const float4* Fhat, const double2* dhat, double2* mhat, int64_t nf, int64_t R,
+static void adj_df64_launch(const float4* Fhat, const float4* dhat, float4* mhat, int64_t nf, int64_t R,
                             int64_t Nm, int64_t B, cudaStream_t s) {
   size_t smem = sizeof(float4) * (size_t)BG * (R < kAdjRows ? R : kAdjRows);
   static PerDeviceOnce attr;  // 8 vectors x 512 staged rows take 64 KB
@@ -575,7 +598,7 @@ static void adj_df64_launch(const float4* Fhat, const double2* dhat, double2* mh
   prod_adj_df64_kernel<BG, VPT, AHEAD><<<grid, 256, smem, s>>>(Fhat, dhat, mhat, nf, R, Nm, B);
 }
 
-void launch_prod_adj_df64(const float4* Fhat, const double2* dhat, double2* mhat, int64_t nf, int64_t R,
+void launch_prod_adj_df64(const float4* Fhat, const float4* dhat, float4* mhat, int64_t nf, int64_t R,
                           int64_t Nm, int64_t B, cudaStream_t s, int vpt) {
   if (B >= 8)
     adj_df64_launch<8, 1>(Fhat, dhat, mhat, nf, R, Nm, B, s);

@@ -436,6 +436,23 @@ __device__ __forceinline__ double pair_to_double_scaled(float hi, float lo, int 
   return __longlong_as_double(bits);
 }
 
+// (hi + lo) 2^e as a normalised float pair, the double-FP32 tier's spectral format: a two-sum,
+// then both floats times 2^e as two exact power-of-two products (exponents e1 + e2 = e of one
+// sign, so no partial product leaves FP32's range unless the result does).  Below FP32's normal
+// range the low float, then the high one, lose bits like any FP32 value.  e is clamped to
+// [-252, 252], which changes no result that is neither zero nor infinite (|hi + lo| < 2^64).
+__device__ __forceinline__ float4 pair_scaled2(float hr, float lr, float hi, float li, int e) {
+  e = max(-252, min(252, e));
+  const int e1 = e >> 1, e2 = e - e1;  // each in [-126, 126]
+  const float p1 = __int_as_float((e1 + 127) << 23), p2 = __int_as_float((e2 + 127) << 23);
+  float sr = __fadd_rn(hr, lr), br = __fsub_rn(sr, hr);
+  float tr = __fadd_rn(__fsub_rn(hr, __fsub_rn(sr, br)), __fsub_rn(lr, br));
+  float si = __fadd_rn(hi, li), bi = __fsub_rn(si, hi);
+  float ti = __fadd_rn(__fsub_rn(hi, __fsub_rn(si, bi)), __fsub_rn(li, bi));
+  return make_float4(__fmul_rn(__fmul_rn(sr, p1), p2), __fmul_rn(__fmul_rn(tr, p1), p2),
+                     __fmul_rn(__fmul_rn(si, p1), p2), __fmul_rn(__fmul_rn(ti, p1), p2));
+}
+
 // Digit planes of rows 0 .. rows-1 (columns 0 .. n-1; columns n .. ldk-1 and rows rows ..
 // rows_pad-1 are written as zeros), one warp per row: ex[r] = the binary exponent of
 // max_j |X[r][j]| (frexp convention, max = f 2^e with f in [0.5, 1); 0 for a zero or padding
@@ -1178,13 +1195,16 @@ __global__ void adj_planes_kernel(const float4* __restrict__ hat, int64_t nf, in
 }
 
 // B planes of one call: one CTA per (w, b), b < NBp / 2 (rows past B are zeros).
-__global__ void adj_vec_planes_kernel(const double2* __restrict__ dhat, int64_t nf, int64_t R, int64_t B,
+__global__ void adj_vec_planes_kernel(const float4* __restrict__ dhat, int64_t nf, int64_t R, int64_t B,
                                       int64_t NBp, int64_t Kp, __half* __restrict__ planes, int* __restrict__ eb) {
   const int64_t w = blockIdx.x, b = blockIdx.y;
-  const double2* src = dhat + (b * nf + w) * R;
+  const float4* src = dhat + (b * nf + w) * R;  // float-pair spectra, joined in FP64 by integer operations
   unsigned long long mb = 0;
   if (b < B)
-    for (int64_t i = threadIdx.x; i < R; i += blockDim.x) mb = max(mb, max(abs_bits(src[i].x), abs_bits(src[i].y)));
+    for (int64_t i = threadIdx.x; i < R; i += blockDim.x) {
+      const float4 v = src[i];
+      mb = max(mb, max(abs_bits(pair_to_double_scaled(v.x, v.y, 0)), abs_bits(pair_to_double_scaled(v.z, v.w, 0))));
+    }
   __shared__ unsigned long long red[32];
   __shared__ int es;
   for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
@@ -1207,8 +1227,9 @@ __global__ void adj_vec_planes_kernel(const double2* __restrict__ dhat, int64_t 
   for (int64_t i = threadIdx.x; i < Kp / 2; i += blockDim.x) {
     long long vr = 0, vi = 0;
     if (b < B && i < R) {
-      vr = round_scaled(src[i].x, 47 - e);
-      vi = round_scaled(src[i].y, 47 - e);
+      const float4 v = src[i];
+      vr = round_scaled(pair_to_double_scaled(v.x, v.y, 0), 47 - e);
+      vi = round_scaled(pair_to_double_scaled(v.z, v.w, 0), 47 - e);
     }
     int dr[kSl], di[kSl];
     digits6(vr, dr);
@@ -1225,7 +1246,7 @@ __global__ void adj_vec_planes_kernel(const double2* __restrict__ dhat, int64_t 
 template <int S>
 __global__ void __launch_bounds__(kKiThreads, 1)
 adj_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-              const int* __restrict__ ea, const int* __restrict__ eb, double2* __restrict__ mhat, int nf,
+              const int* __restrict__ ea, const int* __restrict__ eb, float4* __restrict__ mhat, int nf,
               int64_t Nm, int64_t Nmp, int64_t NBp, int B, int nchunk, int JT, int NG, int64_t per, int64_t total,
               int ksteps, int tail_cols, int drop_stage, int* __restrict__ err) {
   constexpr uint32_t kBPlane = kKiN * kBx * 2, kBStage = kSl * kBPlane;
@@ -1397,8 +1418,7 @@ adj_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         const int b = n >> 1;
         if (j < Nm && b < B) {
           const int sh = ej + eb[w * NBp + n] - 14;
-          mhat[((int64_t)b * nf + w) * Nm + j] =
-              make_double2(pair_to_double_scaled(Sh[k], Sl[k], sh), pair_to_double_scaled(Sh[k + 1], Sl[k + 1], sh));
+          mhat[((int64_t)b * nf + w) * Nm + j] = pair_scaled2(Sh[k], Sl[k], Sh[k + 1], Sl[k + 1], sh);
         }
       }
 #pragma unroll
@@ -1461,7 +1481,7 @@ cudaError_t adj_digits_apply(const void* planes, const int* ea, int64_t nf, int6
     return cudaErrorInvalidValue;
   adj_digits_prepare();
   adj_vec_planes_kernel<<<dim3((unsigned)nf, (unsigned)(NBp / 2)), 128, 0, s>>>(
-      static_cast<const double2*>(dhat), nf, R, B, NBp, Kp, bpl, eb);
+      static_cast<const float4*>(dhat), nf, R, B, NBp, Kp, bpl, eb);
   const int JT = (int)(Nmp / kKiRows), NG = (int)(NBp / kKiN);
   // units (w, row tile), each taken by NG CTAs side by side (one per 64-column group of B)
   const int64_t total = nf * JT;
@@ -1470,7 +1490,7 @@ cudaError_t adj_digits_apply(const void* planes, const int* ea, int64_t nf, int6
   const int64_t ctas = (total + per - 1) / per * NG;
   auto kern = nplanes == 4 ? adj_tc_kernel<4> : (nplanes == 5 ? adj_tc_kernel<5> : adj_tc_kernel<6>);
   kern<<<(unsigned)ctas, kKiThreads, dig_smem(kKiN), s>>>(
-      tA, tB, ea, eb, static_cast<double2*>(mhat), (int)nf, Nm, Nmp, NBp, (int)B, (int)(Kp / kKiChunk), JT, NG, per,
+      tA, tB, ea, eb, static_cast<float4*>(mhat), (int)nf, Nm, Nmp, NBp, (int)B, (int)(Kp / kKiChunk), JT, NG, per,
       total, (int)((2 * R + 15) / 16), tail_cols(2 * R), drop_stage, err);
   *launches = 2;
   return cudaGetLastError();
@@ -1548,14 +1568,17 @@ __global__ void fwd_planes_kernel(const float4* __restrict__ hat, int64_t nf, in
 }
 
 // V planes of one call (vectors b0 .. b0 + nb - 1): one CTA per (w, b < 64); rows past nb zero
-__global__ void fwd_vec_planes_kernel(const double2* __restrict__ mhat, int64_t nf, int64_t Nm, int64_t b0, int64_t nb,
+__global__ void fwd_vec_planes_kernel(const float4* __restrict__ mhat, int64_t nf, int64_t Nm, int64_t b0, int64_t nb,
                                       int64_t Kp, __half* __restrict__ planes, int* __restrict__ ex) {
   const int64_t w = blockIdx.x, b = blockIdx.y;
   const int64_t KB = Kp / kKiBox;
-  const double2* src = mhat + ((b0 + b) * nf + w) * Nm;
+  const float4* src = mhat + ((b0 + b) * nf + w) * Nm;  // float-pair spectra, joined by integer operations
   unsigned long long mb = 0;
   if (b < nb)
-    for (int64_t j = threadIdx.x; j < Nm; j += blockDim.x) mb = max(mb, max(abs_bits(src[j].x), abs_bits(src[j].y)));
+    for (int64_t j = threadIdx.x; j < Nm; j += blockDim.x) {
+      const float4 v = src[j];
+      mb = max(mb, max(abs_bits(pair_to_double_scaled(v.x, v.y, 0)), abs_bits(pair_to_double_scaled(v.z, v.w, 0))));
+    }
   __shared__ unsigned long long red[32];
   __shared__ int es;
   for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
@@ -1575,8 +1598,9 @@ __global__ void fwd_vec_planes_kernel(const double2* __restrict__ mhat, int64_t 
   for (int64_t j = threadIdx.x; j < Kp / 2; j += blockDim.x) {
     long long vr = 0, vi = 0;
     if (b < nb && j < Nm) {
-      vr = round_scaled(src[j].x, 47 - e);
-      vi = round_scaled(src[j].y, 47 - e);
+      const float4 v = src[j];
+      vr = round_scaled(pair_to_double_scaled(v.x, v.y, 0), 47 - e);
+      vi = round_scaled(pair_to_double_scaled(v.z, v.w, 0), 47 - e);
     }
     int dr[kSl], di[kSl];
     digits6(vr, dr);
@@ -1591,7 +1615,7 @@ __global__ void fwd_vec_planes_kernel(const double2* __restrict__ mhat, int64_t 
 }
 
 // d-hat[b0 + b][w][i] = (D[2b][i], D[2b+1][i]) summed over the CTAs that covered tile (w, i / NC)
-__global__ void fwd_reduce_kernel(const double* __restrict__ part, double2* __restrict__ dhat, int64_t nf, int64_t R,
+__global__ void fwd_reduce_kernel(const double* __restrict__ part, float4* __restrict__ dhat, int64_t nf, int64_t R,
                                   int64_t b0, int64_t nb, int NC, int NRG, int64_t per, int64_t kpt, int span) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= nb * nf * R) return;
@@ -1607,7 +1631,10 @@ __global__ void fwd_reduce_kernel(const double* __restrict__ part, double2* __re
     re += P[2 * b];
     im += P[2 * b + 1];
   }
-  dhat[((b0 + b) * nf + w) * R + i] = make_double2(re, im);
+  // stored as float pairs (hi = the sum rounded to FP32, lo = the rest rounded to FP32)
+  const float rh = __double2float_rn(re), ih = __double2float_rn(im);
+  dhat[((b0 + b) * nf + w) * R + i] =
+      make_float4(rh, __double2float_rn(re - (double)rh), ih, __double2float_rn(im - (double)ih));
 }
 
 struct FwdPlan {
@@ -1680,7 +1707,7 @@ cudaError_t fwd_digits_apply(const void* planes, const int* ex, int64_t nf, int6
   kinv_tc_prepare();
   for (int64_t b0 = 0; b0 < B; b0 += 64) {
     const int64_t nb = B - b0 < 64 ? B - b0 : 64;
-    fwd_vec_planes_kernel<<<dim3((unsigned)nf, 64), 256, 0, s>>>(static_cast<const double2*>(mhat), nf, Nm, b0, nb,
+    fwd_vec_planes_kernel<<<dim3((unsigned)nf, 64), 256, 0, s>>>(static_cast<const float4*>(mhat), nf, Nm, b0, nb,
                                                                   p.Kp, vpl, ev);
     // tiles (w, rg): A rows (w KB + kb) 128, B rows (w KB + kb) R_pad + NC rg
     const int64_t ksteps = (2 * Nm + 15) / 16;
@@ -1693,7 +1720,7 @@ cudaError_t fwd_digits_apply(const void* planes, const int* ex, int64_t nf, int6
           tA, tB, ev, ex, part, p.per, p.total, p.kpt, p.span, p.NRG, kKiRows, 0, p.Rp, p.NC, kKiRows, 0, (int)p.Rp,
           p.NC, ksteps, tail_cols(2 * Nm), p.NRG, drop_stage, err, TileJob{});
     const int64_t tot = nb * nf * R;
-    fwd_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, static_cast<double2*>(dhat), nf, R, b0, nb,
+    fwd_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, static_cast<float4*>(dhat), nf, R, b0, nb,
                                                                    p.NC, p.NRG, p.per, p.kpt, p.span);
     *launches += 3;
   }
