@@ -436,7 +436,7 @@ def run_ours(args):
         (pf_ms, pf_n), (pa_ms, pa_n) = prof[0]["prod_fwd"], prof[0]["prod_adj"]
         nf = p.Nt + 1
         Fhat = nf * p.Nd * p.Nm * csize
-        mhat = nf * p.Nm * 16  # the frequency-domain vector (FP64 for f64/df64, read or written)
+        mhat = nf * p.Nm * 16  # the frequency-domain vector (complex FP64 for f64, float pairs for df64)
         if kind in ("f32", "f16"):
             mhat = nf * p.Nm * 8
         bytes_launch = Fhat + mhat
